@@ -1,0 +1,529 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle itself.
+
+Each test checks the oracle against a closed form, an invariant, a textbook
+special case, brute force written in float64 from the geometry, finite
+differences, or a published generator output.  None of them re-types the
+oracle's own formula in the same arithmetic.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import workloads
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------
+# helpers: independent float64 geometry
+# --------------------------------------------------------------------------
+
+def slab64(o, d, lo, hi, t_min, t_max):
+    """float64 slab clip of rays [n][3] against box [lo, hi]."""
+    o = o.astype(np.float64)
+    d = d.astype(np.float64)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        ta = (np.asarray(lo) - o) / d
+        tb = (np.asarray(hi) - o) / d
+    near = np.where(d == 0, -np.inf, np.minimum(ta, tb))
+    far = np.where(d == 0, np.inf, np.maximum(ta, tb))
+    outside = (d == 0) & ((o < np.asarray(lo)) | (o > np.asarray(hi)))
+    tn = np.maximum(near.max(axis=1), t_min)
+    tf = np.minimum(far.min(axis=1), t_max)
+    hit = (tn < tf) & ~outside.any(axis=1)
+    return tn, tf, hit
+
+
+def cell_of64(x, amin, amax, res, L, margin_cells=2e-3, margin_box=1e-5):
+    """float64 (level, flat cell index, ambiguous) of points x [..., 3]."""
+    amin = np.asarray(amin, np.float64)
+    amax = np.asarray(amax, np.float64)
+    cen = (amin + amax) / 2
+    half = (amax - amin) / 2
+    level = np.full(x.shape[:-1], -1, np.int64)
+    amb = np.zeros(x.shape[:-1], bool)
+    dev = np.abs(x - cen)
+    for l in range(L):
+        h = half * 2.0 ** l
+        inside = (dev <= h).all(-1)
+        near_face = (np.abs(dev - h) < margin_box).any(-1)
+        amb |= near_face & (level < 0)
+        level = np.where((level < 0) & inside, l, level)
+    idx = np.full(x.shape[:-1], -1, np.int64)
+    for l in range(L):
+        m = level == l
+        if not m.any():
+            continue
+        h = half * 2.0 ** l
+        lo = cen - h
+        w = 2 * h / res
+        u = (x[m] - lo) / w
+        fr = u - np.floor(u)
+        amb_m = ((fr < margin_cells) | (fr > 1 - margin_cells)).any(-1)
+        i = np.clip(np.floor(u).astype(np.int64), 0, res - 1)
+        idx[m] = l * res ** 3 + (i[:, 0] * res + i[:, 1]) * res + i[:, 2]
+        amb[m] |= amb_m
+    return level, idx, amb
+
+
+def lattice_check(orc, o, d, amin, amax, res, L, bits, step, max_steps, t_min, t_max):
+    """Brute force: every unambiguous lattice point is emitted iff its float64
+    midpoint lies in an occupied cell; every emitted sample is a lattice point."""
+    out = orc.march(o, d, amin, amax, res, L, bits, step, max_steps, t_min, t_max)
+    occ = workloads.unpack_bits(bits)
+    outer_lo = np.asarray(amin, np.float64) - (np.asarray(amax) - np.asarray(amin)) / 2 * (2 ** (L - 1) - 1)
+    outer_hi = np.asarray(amax, np.float64) + (np.asarray(amax) - np.asarray(amin)) / 2 * (2 ** (L - 1) - 1)
+    tn, tf, hit = slab64(o, d, outer_lo, outer_hi, t_min, t_max)
+    off = out["offsets"]
+    checked = 0
+    for r in range(o.shape[0]):
+        s, e = off[r], off[r + 1]
+        if not hit[r]:
+            # a grazing miss may still be a float32 hit; only exact misses are pinned
+            continue
+        k = np.arange(max_steps)
+        t0 = tn[r] + k * step
+        valid = t0 < tf[r]
+        amb_t = np.abs(t0 - tf[r]) < 1e-5
+        tm = t0 + step / 2
+        x = o[r].astype(np.float64) + d[r].astype(np.float64) * tm[:, None]
+        lev, idx, amb = cell_of64(x, amin, amax, res, L)
+        expect = valid & (lev >= 0) & occ[np.maximum(idx, 0)] & (idx >= 0)
+        amb = amb | amb_t
+        got = np.zeros(max_steps, bool)
+        ks = np.rint((out["t_starts"][s:e].astype(np.float64) - tn[r]) / step).astype(np.int64)
+        assert np.all(np.abs(out["t_starts"][s:e] - (tn[r] + ks * step)) < 1e-4), "not on the lattice"
+        assert np.all(np.abs(out["t_ends"][s:e] - out["t_starts"][s:e] - step) < 1e-5)
+        assert np.all(out["ray_indices"][s:e] == r)
+        assert np.all(np.diff(ks) > 0), "samples of a ray must be in increasing t"
+        got[ks] = True
+        bad = (got != expect) & ~amb
+        assert not bad.any(), f"ray {r}: lattice points {np.nonzero(bad)[0][:10]} disagree"
+        checked += int((~amb).sum())
+    assert checked > 0
+    return out
+
+
+# --------------------------------------------------------------------------
+# RNG
+# --------------------------------------------------------------------------
+
+def test_splitmix64_published_vector(orc):
+    vals = [int(l) for l in open(os.path.join(GOLDEN, "splitmix64_seed1234567.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert [orc.splitmix64_at(1234567, k) for k in range(5)] == vals
+
+
+# --------------------------------------------------------------------------
+# lattice march
+# --------------------------------------------------------------------------
+
+def test_level_geometry_is_box_scaled_about_centre(orc):
+    amin, amax = (-1.0, -2.0, 0.5), (3.0, 2.0, 1.5)
+    g = orc.level_geometry(amin, amax, 16, 4)
+    cen = (np.array(amin) + np.array(amax)) / 2
+    half = (np.array(amax) - np.array(amin)) / 2
+    for l in range(4):
+        np.testing.assert_allclose(g[l, 0], cen - half * 2 ** l, rtol=0, atol=1e-6)
+        np.testing.assert_allclose(g[l, 1], cen + half * 2 ** l, rtol=0, atol=1e-6)
+        np.testing.assert_allclose(g[l, 2] * g[l, 3], 1.0, rtol=1e-6)
+        np.testing.assert_allclose(g[l, 3], half * 2 ** (l + 1) / 16, rtol=1e-6)
+
+
+def test_uniform_special_case(orc):
+    """Sec. 3.1 "Uniform": with every cell occupied the estimator is uniform and the
+    samples are the regular lattice t_n + k*dt over [t_n, t_f]."""
+    w = workloads.c1_forward(512)
+    res = 8
+    bits = np.full(res ** 3 // 32, 0xFFFFFFFF, np.uint32)
+    step = 0.01
+    out = orc.march(w.rays_o, w.rays_d, (-1.5,) * 3, (1.5,) * 3, res, 1, bits, step, 4096, 0.0, 1e10)
+    tn, tf, hit = slab64(w.rays_o, w.rays_d, (-1.5,) * 3, (1.5,) * 3, 0.0, 1e10)
+    n = np.diff(out["offsets"])
+    for r in range(512):
+        if not hit[r]:
+            continue
+        span = (tf[r] - tn[r]) / step
+        # lattice points whose midpoint is inside the box: t_n + (k+1/2) dt <= t_f
+        expect = int(np.floor(span + 0.5))
+        if abs((span + 0.5) - round(span + 0.5)) < 1e-3:
+            assert abs(n[r] - expect) <= 1
+            continue
+        assert n[r] == expect, (r, n[r], expect)
+        t0 = out["t_starts"][out["offsets"][r]:out["offsets"][r + 1]]
+        np.testing.assert_allclose(t0, tn[r] + np.arange(n[r]) * step, rtol=0, atol=2e-5)
+    assert (n[~hit] == 0).all()
+
+
+def test_max_steps_caps_lattice_index(orc):
+    w = workloads.c1_forward(64)
+    bits = np.full(8 ** 3 // 32, 0xFFFFFFFF, np.uint32)
+    out = orc.march(w.rays_o, w.rays_d, (-1.5,) * 3, (1.5,) * 3, 8, 1, bits, 0.01, 17, 0.0, 1e10)
+    assert np.diff(out["offsets"]).max() <= 17
+
+
+def test_single_occupied_cell(orc):
+    """Only one cell occupied: exactly the lattice points whose midpoints fall in that
+    cell's box (float64 geometry) are emitted."""
+    res = 8
+    occ = np.zeros(res ** 3, bool)
+    i0, i1, i2 = 3, 4, 2
+    occ[(i0 * res + i1) * res + i2] = True
+    bits = workloads.pack_bits(occ)
+    g = workloads.rng(90)
+    w = 3.0 / res
+    centre = -1.5 + (np.array([i0, i1, i2]) + 0.5) * w
+    o = workloads._normalise(g.standard_normal((300, 3))) * 4.0
+    p = centre + g.uniform(-0.6 * w, 0.6 * w, size=(300, 3))
+    d = workloads._normalise(p - o)
+    lattice_check(orc, o.astype(np.float32), d.astype(np.float32), (-1.5,) * 3, (1.5,) * 3, res, 1,
+                  bits, 0.004, 2048, 0.0, 1e10)
+
+
+def test_brute_force_random_grids(orc):
+    """Random tiny grids (1-3 levels): the emitted set equals the float64 brute force."""
+    for seed, (res, L) in enumerate([(4, 1), (8, 2), (16, 3), (12, 2)]):
+        bits = workloads.random_bitfield(L, res, 100 + seed, p_block=0.5, block=2, p_cell=0.5)
+        g = workloads.rng(100 + seed, 1)
+        n = 120
+        o = workloads._normalise(g.standard_normal((n, 3))) * g.uniform(0.5, 6.0, size=(n, 1))
+        p = g.uniform(-1.5, 1.5, size=(n, 3))
+        d = workloads._normalise(p - o)
+        # axis-parallel rays and rays with a zero component
+        d[:10] = 0.0
+        d[np.arange(10), np.arange(10) % 3] = np.where(np.arange(10) % 2 == 0, 1.0, -1.0)
+        d[10:20, 1] = 0.0
+        d[10:20] = workloads._normalise(d[10:20])
+        lattice_check(orc, o.astype(np.float32), d.astype(np.float32), (-1.5,) * 3, (1.5,) * 3,
+                      res, L, bits, 0.02, 1024, 0.1, 1e10)
+
+
+def test_cascade_selects_finest_level(orc):
+    """Level 0 empty, level 1 full: samples exist only outside the level-0 box."""
+    res, L = 8, 2
+    occ = np.zeros(L * res ** 3, bool)
+    occ[res ** 3:] = True
+    bits = workloads.pack_bits(occ)
+    w = workloads.c1_forward(200)
+    o, d = w.rays_o * 1.5, w.rays_d  # origins at radius 6, outside level 1 ([-3,3]^3)
+    out = lattice_check(orc, o, d, (-1.5,) * 3, (1.5,) * 3, res, L, bits, 0.01, 2048, 0.0, 1e10)
+    m = 0.5 * (out["t_starts"].astype(np.float64) + out["t_ends"])
+    x = o[out["ray_indices"]].astype(np.float64) + d[out["ray_indices"]] * m[:, None]
+    dev = np.abs(x).max(axis=1)
+    assert (dev > 1.5 - 1e-5).all() and (dev < 3.0 + 1e-5).all()
+    assert out["offsets"][-1] > 1000
+
+
+def test_miss_and_inside_origin(orc):
+    bits = np.full(8 ** 3 // 32, 0xFFFFFFFF, np.uint32)
+    o = np.array([[5.0, 5.0, 5.0], [0.0, 0.0, 0.0], [0.0, 3.0, 0.0]], np.float32)
+    d = np.array([[1.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 0.0, 1.0]], np.float32)
+    out = orc.march(o, d, (-1.5,) * 3, (1.5,) * 3, 8, 1, bits, 0.01, 4096, 0.0, 1e10)
+    n = np.diff(out["offsets"])
+    assert n[0] == 0 and n[2] == 0
+    assert n[1] == 150  # from the origin (t_near = t_min = 0) to the face at 1.5
+    assert out["t_starts"][0] == 0.0
+
+
+def test_early_termination_cut(orc):
+    """No-gradient filtering (Sec. 4.2): the field-given march emits a prefix of the
+    field-less march, cut where the float64 optical depth of the emitted samples
+    first exceeds -ln(1e-4)."""
+    w = workloads.c1_forward(400)
+    bits, _ = orc.density_grid(w.grid, w.blobs)
+    m, g = w.march, w.grid
+    full = orc.march(w.rays_o, w.rays_d, g.aabb_min, g.aabb_max, g.res, g.n_levels, bits, m.step,
+                     m.max_steps, m.t_min, m.t_max)
+    cut = orc.march(w.rays_o, w.rays_d, g.aabb_min, g.aabb_max, g.res, g.n_levels, bits, m.step,
+                    m.max_steps, m.t_min, m.t_max, blobs=w.blobs, eps=1e-4)
+    thr = -math.log(1e-4)
+    sig, _ = orc.field_samples(w.rays_o, w.rays_d, full["ray_indices"], full["t_starts"],
+                               full["t_ends"], w.blobs)
+    tau = sig * (full["t_ends"].astype(np.float64) - full["t_starts"])
+    n_cut_total = 0
+    for r in range(400):
+        fs, fe = full["offsets"][r], full["offsets"][r + 1]
+        cs, ce = cut["offsets"][r], cut["offsets"][r + 1]
+        nc = ce - cs
+        assert nc <= fe - fs
+        np.testing.assert_array_equal(cut["t_starts"][cs:ce], full["t_starts"][fs:fs + nc])
+        P = np.concatenate([[0.0], np.cumsum(tau[fs:fe])])  # P[i] = depth before sample i
+        if nc > 0:
+            assert P[nc - 1] <= thr * (1 + 1e-5)
+        if nc < fe - fs:
+            n_cut_total += 1
+            assert P[nc] > thr * (1 - 1e-5)
+    assert n_cut_total > 10
+
+
+# --------------------------------------------------------------------------
+# compositing (Eq. 2) and gradient
+# --------------------------------------------------------------------------
+
+def test_homogeneous_slab_closed_form(orc):
+    """Constant sigma0 over N equal intervals: T_i = exp(-sigma0 dt i), opacity =
+    1 - exp(-sigma0 dt N), colour = c (1 - T_N) + bg T_N, depth = sum_i w_i m_i."""
+    N, dt, s0, t0 = 200, 0.01, 7.0, 2.0
+    k = np.arange(N)
+    ts = (t0 + k * dt).astype(np.float32)
+    te = (ts.astype(np.float64) + dt).astype(np.float32)
+    dts = te.astype(np.float64) - ts
+    c = np.array([0.2, 0.5, 0.9])
+    out = orc.render_fwd(np.array([0, N]), ts, te, np.full(N, s0), np.tile(c, (N, 1)),
+                         bg=(1.0, 1.0, 1.0))
+    L = dts.sum()
+    TN = math.exp(-s0 * L)
+    assert out["trans"][0] == pytest.approx(TN, rel=1e-12)
+    assert out["opacity"][0] == pytest.approx(1 - TN, rel=1e-12)
+    np.testing.assert_allclose(out["rgb"][0], c * (1 - TN) + TN, rtol=1e-12)
+    Ti = np.exp(-s0 * np.concatenate([[0.0], np.cumsum(dts)[:-1]]))
+    wi = Ti * (1 - np.exp(-s0 * dts))
+    np.testing.assert_allclose(out["weights"], wi, rtol=1e-11)
+    m = 0.5 * (ts.astype(np.float64) + te)
+    assert out["depth"][0] == pytest.approx((wi * m).sum(), rel=1e-12)
+
+
+def test_weights_sum_to_one_minus_transmittance(orc):
+    """Eq. 3: F(t) = 1 - T(t), i.e. sum of weights = 1 - T_N; T non-increasing."""
+    p = workloads.random_packed(500, 20)
+    out = orc.render_fwd(p["offsets"], p["t_starts"], p["t_ends"], p["sigmas"], p["rgbs"])
+    np.testing.assert_allclose(out["opacity"], 1 - out["trans"], rtol=0, atol=1e-13)
+    off = p["offsets"]
+    for r in range(500):
+        w = out["weights"][off[r]:off[r + 1]]
+        T = 1 - np.concatenate([[0.0], np.cumsum(w)])
+        assert np.all(np.diff(T) <= 1e-15)
+    empty = np.diff(off) == 0
+    assert empty.any()
+    np.testing.assert_array_equal(out["rgb"][empty], 1.0)
+    np.testing.assert_array_equal(out["opacity"][empty], 0.0)
+    np.testing.assert_array_equal(out["depth"][empty], 0.0)
+    np.testing.assert_array_equal(out["trans"][empty], 1.0)
+
+
+def test_line_integral_of_gaussian_blob(orc):
+    """T_N converges to exp(-int sigma dt) with the erf closed form of a Gaussian's
+    line integral as dt -> 0 (Eq. 2)."""
+    blobs = workloads.Blobs(mu=np.array([[0.1, -0.2, 0.05]], np.float32),
+                            std=np.array([0.25], np.float32), peak=np.array([3.0], np.float32),
+                            rgb=np.array([[0.3, 0.6, 0.9]], np.float32))
+    o = np.array([[-3.0, 0.1, 0.3]], np.float32)
+    d = workloads._normalise(np.array([[1.0, -0.05, -0.02]])).astype(np.float32)
+    tn, tf = 1.0, 5.0
+    # closed form: sigma along the ray is a 1-D Gaussian in t
+    mu, s, pk = blobs.mu[0].astype(np.float64), float(blobs.std[0]), float(blobs.peak[0])
+    oo, dd = o[0].astype(np.float64), d[0].astype(np.float64)
+    dd2 = dd @ dd
+    tstar = (mu - oo) @ dd / dd2
+    perp2 = np.sum((oo + tstar * dd - mu) ** 2)
+    sl = s / math.sqrt(dd2)
+    integral = pk * math.exp(-perp2 / (2 * s * s)) * sl * math.sqrt(math.pi / 2) * (
+        math.erf((tf - tstar) / (sl * math.sqrt(2))) - math.erf((tn - tstar) / (sl * math.sqrt(2))))
+    for step, tol in [(0.01, 2e-4), (0.002, 1e-5)]:
+        N = int(round((tf - tn) / step))
+        ts = (tn + np.arange(N) * step).astype(np.float32)
+        te = np.append(ts[1:], np.float32(tf))
+        sig, rgb = orc.field_samples(o, d, np.zeros(N, np.int32), ts, te, blobs)
+        out = orc.render_fwd(np.array([0, N]), ts, te, sig, rgb)
+        assert out["trans"][0] == pytest.approx(math.exp(-integral), rel=tol)
+        np.testing.assert_allclose(out["rgb"][0], blobs.rgb[0] * (1 - math.exp(-integral)) + math.exp(-integral), rtol=tol)
+
+
+def test_mask_mode_zeroes_weights_below_eps(orc):
+    """Samples whose transmittance fell below eps get w = 0 (Sec. 4.2 filtering);
+    T_N is the transmittance at the first masked sample."""
+    N, dt, s0 = 400, 0.01, 5.0
+    ts = (np.arange(N) * dt).astype(np.float32)
+    te = (ts.astype(np.float64) + dt).astype(np.float32)
+    out = orc.render_fwd(np.array([0, N]), ts, te, np.full(N, s0), np.full((N, 3), 0.5), eps=1e-4)
+    P = s0 * np.concatenate([[0.0], np.cumsum(te.astype(np.float64) - ts)])
+    first_masked = int(np.argmax(P[:N] > -math.log(1e-4)))
+    assert first_masked > 0
+    assert np.all(out["weights"][first_masked:] == 0)
+    assert np.all(out["weights"][:first_masked] > 0)
+    assert out["trans"][0] == pytest.approx(math.exp(-P[first_masked]), rel=1e-12)
+    assert out["trans"][0] < 1e-4
+
+
+def _fd_check(orc, p, eps, rays):
+    g = workloads.rng(31)
+    n = len(p["offsets"]) - 1
+    gC = g.standard_normal((n, 3))
+    gA = g.standard_normal(n)
+    gD = g.standard_normal(n)
+    sig = p["sigmas"].astype(np.float64)
+    rgb = p["rgbs"].astype(np.float64)
+    gs, gr = orc.render_bwd(p["offsets"], p["t_starts"], p["t_ends"], sig, rgb, gC, gA, gD, eps=eps)
+
+    def loss(s, c):
+        o = orc.render_fwd(p["offsets"], p["t_starts"], p["t_ends"], s, c, eps=eps)
+        return (o["rgb"] * gC).sum() + (o["opacity"] * gA).sum() + (o["depth"] * gD).sum()
+
+    off = p["offsets"]
+    n_checked = 0
+    for r in rays:
+        for i in range(off[r], off[r + 1]):
+            h = 1e-6 * max(1.0, abs(sig[i]))
+            sp, sm = sig.copy(), sig.copy()
+            sp[i] += h
+            sm[i] -= h
+            fd = (loss(sp, rgb) - loss(sm, rgb)) / (2 * h)
+            assert gs[i] == pytest.approx(fd, rel=1e-5, abs=1e-8), (r, i)
+            ch = i % 3
+            cp, cm = rgb.copy(), rgb.copy()
+            cp[i, ch] += 1e-6
+            cm[i, ch] -= 1e-6
+            fdc = (loss(sig, cp) - loss(sig, cm)) / 2e-6
+            assert gr[i, ch] == pytest.approx(fdc, rel=1e-5, abs=1e-8)
+            n_checked += 1
+    return n_checked
+
+
+def test_gradient_matches_finite_differences(orc):
+    """The adjoint equals central differences of the FP64 compositing (64 rays)."""
+    p = workloads.random_packed(64, 32, max_len=12, sigma_hi=30.0)
+    assert _fd_check(orc, p, 0.0, range(64)) > 100
+
+
+def test_gradient_mask_mode_finite_differences(orc):
+    """Mask mode: away from the cut the adjoint still equals central differences."""
+    p = workloads.random_packed(32, 33, max_len=40, sigma_hi=200.0, p_empty=0.0)
+    out = orc.render_fwd(p["offsets"], p["t_starts"], p["t_ends"], p["sigmas"], p["rgbs"], eps=1e-4)
+    assert (out["weights"] == 0).sum() > 50  # the mask is active
+    # skip rays whose depth prefix is within 1e-3 of the threshold at any sample
+    thr = -math.log(1e-4)
+    off = p["offsets"]
+    tau = p["sigmas"].astype(np.float64) * (p["t_ends"].astype(np.float64) - p["t_starts"])
+    rays = []
+    for r in range(32):
+        P = np.cumsum(tau[off[r]:off[r + 1]])
+        if P.size and np.min(np.abs(P - thr)) > 1e-3:
+            rays.append(r)
+    assert len(rays) > 10
+    _fd_check(orc, p, 1e-4, rays)
+
+
+# --------------------------------------------------------------------------
+# estimator update (Eq. 4) and its sample points
+# --------------------------------------------------------------------------
+
+def test_grid_points_centres_and_jitter(orc):
+    amin, amax, res, L = (-1.5,) * 3, (1.5,) * 3, 8, 2
+    c = orc.grid_points(amin, amax, res, L, jitter=False)
+    for l in range(L):
+        w = 3.0 * 2 ** l / res
+        lo = -1.5 * 2 ** l
+        idx = np.arange(res ** 3)
+        i = np.stack([idx // (res * res), (idx // res) % res, idx % res], -1)
+        np.testing.assert_allclose(c[l * res ** 3:(l + 1) * res ** 3], lo + (i + 0.5) * w, rtol=0, atol=1e-6)
+    j = orc.grid_points(amin, amax, res, L, seed=7, step=3, jitter=True)
+    for l in range(L):
+        w = 3.0 * 2 ** l / res
+        dev = (j[l * res ** 3:(l + 1) * res ** 3] - c[l * res ** 3:(l + 1) * res ** 3]) / w
+        assert dev.min() >= -0.5 - 1e-5 and dev.max() < 0.5 + 1e-5
+        assert abs(dev.mean()) < 0.02 and 0.08 < dev.var() < 0.093  # U(-1/2,1/2): var 1/12
+    j2 = orc.grid_points(amin, amax, res, L, seed=7, step=4, jitter=True)
+    assert not np.array_equal(j, j2)
+    np.testing.assert_array_equal(j, orc.grid_points(amin, amax, res, L, seed=7, step=3, jitter=True))
+    # the jitter of cell 0, axis 0 is the first published SplitMix64 output of the stream
+    u0 = (orc.splitmix64_at(7 ^ (3 << 32), 0) >> 40) / 2 ** 24
+    assert j[0, 0] == pytest.approx(-1.5 + u0 * 3.0 / res, abs=1e-6)
+
+
+def test_update_grid_ema_closed_form(orc):
+    """EMA of Sec. 3.1 (Eq. 4): constant input d gives e_k = g^k e_0 + (1-g^k) d."""
+    n = 64 * 32
+    g = workloads.rng(40)
+    e0 = g.uniform(0, 1, n).astype(np.float32)
+    d = g.uniform(0, 1, n).astype(np.float32)
+    e = e0
+    for _ in range(5):
+        e, bits, mean = orc.update_grid(e, d, 0.95, 0.01)
+    expect = 0.95 ** 5 * e0.astype(np.float64) + (1 - 0.95 ** 5) * d
+    np.testing.assert_allclose(e, expect, rtol=1e-5)
+    assert mean == pytest.approx(e.astype(np.float64).mean(), rel=1e-12)
+    e1, _, _ = orc.update_grid(e0, d, 0.0, 0.01)
+    np.testing.assert_array_equal(e1, d)
+
+
+def test_update_grid_threshold_and_bit_layout(orc):
+    """Binarisation 1[sigma > tau] (Table 1) with tau = 0.01 * mean, and the bit
+    layout: element c is bit c % 32 of word c // 32."""
+    n = 8 ** 3 * 2
+    dens = np.zeros(n, np.float32)
+    dens[[0, 33, 511, 700]] = [5.0, 1.0, 0.00005, 2.0]
+    e, bits, mean = orc.update_grid(np.zeros(n, np.float32), dens, 0.0, 0.01)
+    assert mean == pytest.approx(8.00005 / n, rel=1e-6)
+    thr = 0.01 * 8.00005 / n
+    assert thr > 0.00005  # cell 511 falls below 0.01 * mean
+    assert bits[0] == 1 and bits[1] == 2 and bits[15] == 0 and bits[21] == 1 << (700 % 32)
+    assert workloads.unpack_bits(bits).sum() == 3
+    _, bits_abs, _ = orc.update_grid(np.zeros(n, np.float32), dens, 0.0, 0.0, 1.5)
+    assert workloads.unpack_bits(bits_abs).sum() == 2
+
+
+# --------------------------------------------------------------------------
+# inverse transform sampling (Eq. 1 with F = 1 - T, Eq. 3)
+# --------------------------------------------------------------------------
+
+def test_sample_pdf_uniform_weights_give_linspace(orc):
+    """Sec. 3.1 "Uniform": constant PDF -> t_i = t_n + (t_f - t_n) u_i."""
+    n, nb, no = 50, 64, 32
+    g = workloads.rng(50)
+    tn = g.uniform(1, 2, n)
+    tf = tn + g.uniform(1, 3, n)
+    edges = (tn[:, None] + (tf - tn)[:, None] * np.linspace(0, 1, nb + 1)[None]).astype(np.float32)
+    out = orc.sample_pdf(edges, np.ones((n, nb), np.float32), no)
+    expect = tn[:, None] + (tf - tn)[:, None] * np.linspace(0, 1, no + 1)[None]
+    np.testing.assert_allclose(out, expect, rtol=0, atol=2e-6)
+    out0 = orc.sample_pdf(edges, np.zeros((n, nb), np.float32), no)
+    np.testing.assert_allclose(out0, expect, rtol=0, atol=2e-6)
+
+
+def test_sample_pdf_piecewise_constant_inverse(orc):
+    """Random piecewise-constant PDFs: outputs equal the analytic inverse CDF at
+    u = k/N, and are non-decreasing."""
+    n, nb, no = 40, 16, 24
+    g = workloads.rng(51)
+    edges = np.sort(g.uniform(0, 10, (n, nb + 1)), axis=1).astype(np.float32)
+    w = g.uniform(0, 1, (n, nb)).astype(np.float32)
+    w[g.random((n, nb)) < 0.3] = 0.0
+    w[:, 0] = np.maximum(w[:, 0], 0.1)
+    w[:, -1] = np.maximum(w[:, -1], 0.1)
+    out = orc.sample_pdf(edges, w, no)
+    for r in range(n):
+        e = edges[r].astype(np.float64)
+        F = np.concatenate([[0.0], np.cumsum(w[r].astype(np.float64))])
+        F /= F[-1]
+        for k in range(no + 1):
+            u = k / no
+            j = min(int(np.searchsorted(F, u, side="right")) - 1, nb - 1)
+            t = e[j] + (u - F[j]) / (F[j + 1] - F[j]) * (e[j + 1] - e[j])
+            if np.min(np.abs(F[1:-1] - u)) < 1e-6:
+                continue  # tie with a flat region boundary
+            assert out[r, k] == pytest.approx(t, rel=1e-5, abs=1e-5)
+        assert np.all(np.diff(out[r]) >= 0)
+
+
+def test_sample_pdf_single_bin_mass(orc):
+    """All mass in one bin: every sample lies in that bin, evenly spaced (Eq. 1)."""
+    nb, no = 10, 8
+    edges = np.linspace(0, 10, nb + 1, dtype=np.float32)[None]
+    w = np.zeros((1, nb), np.float32)
+    w[0, 4] = 2.5
+    out = orc.sample_pdf(edges, w, no)
+    np.testing.assert_allclose(out[0], np.linspace(4, 5, no + 1), atol=1e-6)
+
+
+def test_sample_pdf_stratified(orc):
+    n, nb, no = 200, 8, 16
+    edges = np.tile(np.linspace(0, 1, nb + 1, dtype=np.float32), (n, 1))
+    out = orc.sample_pdf(edges, np.ones((n, nb), np.float32), no, stratified=True, seed=5)
+    k = np.arange(no + 1)
+    assert np.all(out[:, 0] == 0) and np.all(out[:, -1] == 1)
+    inner = out[:, 1:-1] * no - k[None, 1:-1]  # = U_r, constant per ray, in [0, 1)
+    assert np.all(inner >= -1e-4) and np.all(inner < 1 + 1e-4)
+    assert np.allclose(inner, inner[:, :1], atol=1e-4)
+    assert 0.4 < inner[:, 0].mean() < 0.6
