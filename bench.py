@@ -1,0 +1,473 @@
+#!/usr/bin/env python
+"""Throughput of the occupancy-grid sampling + compositing hot path on GB300.
+
+One step = one pass of the path over one batch of synthetic rays (Algorithm 1
+of NerfAcc, arXiv 2305.04966): occupancy-grid march with early termination
+into packed samples, the analytic field at the samples (harness stand-in for
+the radiance field), render_fwd, an L2 loss against a seeded target image
+(harness), render_bwd.  Workload (default): the full 800x800 pinhole image
+(640,000 rays) of the 8-blob scene with a 4-level 128^3 cascaded occupancy
+grid and up to 1024 lattice steps per ray.
+
+Prints ONE JSON line (rank 0).  ``value`` = rays/s over all ranks with
+inputs resident in HBM, timed with CUDA events on the launching stream;
+``e2e`` = the same metric through the public API with the step's inputs
+copied from pinned host memory and the rendered image + loss copied back
+inside the timed region.  ``--impl reference`` times the CPU oracle instead
+(the reference arm of this comparison).
+
+Multi-GPU (torchrun): every rank renders its own view (weak scaling, no
+collective on the data path); the step time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads  # noqa: E402
+
+METRIC = "rays/s & samples/s, march+composite fwd+bwd, % of HBM roofline, vs CPU oracle"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+L2_FLUSH_BYTES = 512 << 20  # > 129 MB of L2
+
+# Algorithmic bytes (what the method must move), S = samples, R = rays.
+#   march:      rays read once (24 R), packed samples written (12 S: ray id, t0, t1),
+#               CSR offsets written (8 R)
+#   render_fwd: t0, t1, sigma, rgb read (24 S), offsets (8 R), rgb/opacity/depth/T_N written (24 R)
+#   render_bwd: t0, t1, sigma, rgb read (24 S), dsigma, drgb written (16 S), offsets (8 R),
+#               per-ray upstream gradients (20 R)
+BYTES = {
+    "march": (12, 32),
+    "render_fwd": (24, 32),
+    "render_bwd": (40, 28),
+}
+KERNELS_PER_STEP = {"march": 3, "field": 1, "render_fwd": 1, "loss": 1, "render_bwd": 1}
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--width", type=int, default=800)
+    ap.add_argument("--height", type=int, default=800)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target oracle CPU time")
+    return ap.parse_args(argv)
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (host logic, testable with gloo on CPU)
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def view_for_rank(rank: int) -> int:
+    """Each rank renders its own camera view; rank 0 renders the reference view."""
+    return rank
+
+
+def reduce_max(value: float, dist=None) -> float:
+    """Max of a float over ranks (identity without a process group)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(value: float, dist=None) -> float:
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)], stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.tmp.flush()
+        rows = []
+        with open(self.tmp.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 10:
+                    rows.append(parts)
+        os.unlink(self.tmp.name)
+        return self.summarise(rows)
+
+    @classmethod
+    def summarise(cls, rows):
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows]
+        util = [num(r[4]) for r in rows]
+        load = [s for s, u in zip(sm, util) if s is not None and u is not None and u >= 50]
+        if not load:
+            load = [s for s in sm if s is not None]
+        reasons = set()
+        for r in rows:
+            for name, v in zip(cls.REASONS, r[6:10]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        return {"sm_mhz": statistics.median(load) if load else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows), "samples_under_load": len(load)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (baseline / reference arm)
+# ---------------------------------------------------------------------------
+
+class OraclePipeline:
+    """The oracle's march (FP32, early stop) + FP64 field + FP64 compositing +
+    L2 gradient + FP64 adjoint on a subset of the workload's rays."""
+
+    def __init__(self, w):
+        import oracle
+        self.orc = oracle
+        self.w = w
+        self.bits, _ = oracle.density_grid(w.grid, w.blobs)
+        self.threads = oracle.max_threads()
+
+    def run(self, sel):
+        orc, w = self.orc, self.w
+        g, m = w.grid, w.march
+        o, d = np.ascontiguousarray(w.rays_o[sel]), np.ascontiguousarray(w.rays_d[sel])
+        ex = orc.march(o, d, g.aabb_min, g.aabb_max, g.res, g.n_levels, self.bits, m.step, m.max_steps,
+                       m.t_min, m.t_max, blobs=w.blobs, eps=m.early_stop_eps)
+        sig, rgb = orc.field_samples(o, d, ex["ray_indices"], ex["t_starts"], ex["t_ends"], w.blobs)
+        out = orc.render_fwd(ex["offsets"], ex["t_starts"], ex["t_ends"], sig, rgb, bg=w.bg)
+        n = len(sel)
+        g_rgb = 2.0 * (out["rgb"] - w.target[sel]) / (3 * n)
+        orc.render_bwd(ex["offsets"], ex["t_starts"], ex["t_ends"], sig, rgb, g_rgb, np.zeros(n),
+                       np.zeros(n), bg=w.bg)
+        return int(ex["offsets"][-1])
+
+
+def cpu_baseline(w, target_seconds=10.0):
+    """Oracle rays/s on a bounded, evenly strided sample of the workload's rays."""
+    pipe = OraclePipeline(w)
+    n = w.n_rays
+    probe = np.arange(0, n, 256)
+    t0 = time.perf_counter()
+    pipe.run(probe)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    per_ray = dt / len(probe)
+    k = int(min(n, max(len(probe), target_seconds / per_ray)))
+    stride = max(1, n // k)
+    sel = np.arange(0, n, stride)
+    t0 = time.perf_counter()
+    S = pipe.run(sel)
+    dt = time.perf_counter() - t0
+    return {"value": len(sel) / dt, "unit": "rays/s", "cores": pipe.threads, "kind": "oracle",
+            "sample": f"every {stride}th ray of the {n}-ray image ({len(sel)} rays, {S} samples), "
+                      f"march+field+fwd+loss+bwd, {dt:.1f} s",
+            "samples_per_s": S / dt}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = workloads.c2_image(args.width, args.height)
+    pipe = OraclePipeline(w)
+    n = w.n_rays
+    stride = 16  # each step: a bounded 1/16 sample of the image
+    times, samples = [], []
+    for i in range(args.warmup + args.steps):
+        sel = np.arange(i % stride, n, stride)
+        t0 = time.perf_counter()
+        S = pipe.run(sel)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+            samples.append(S)
+    nray = len(np.arange(0, n, stride))
+    ms = 1000.0 * sum(times) / len(times)
+    val = nray / (ms / 1000.0)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "rays/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "n_rays": n, "step_sample": f"every {stride}th ray ({nray} rays)"},
+        "samples_per_s": float(np.mean(samples)) / (ms / 1000.0),
+        "cpu_baseline": {"value": val, "unit": "rays/s", "cores": pipe.threads, "kind": "oracle",
+                         "sample": f"every {stride}th ray of the {n}-ray image per step"},
+        "e2e": {"value": val, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def src_sha(path):
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def recorded_traffic(stage, S, R):
+    """DRAM bytes per launch of `stage` from the committed ncu summary, scaled to
+    this launch, or None if absent or taken on an older version of the kernel."""
+    try:
+        rec = json.load(open(TRAFFIC_FILE)).get(stage)
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_2305_04966_gb300", "csrc", rec["source"])
+    if not os.path.exists(src) or src_sha(src) != rec["source_sha"]:
+        return None
+    return rec["dram_bytes_per_sample"] * S + rec.get("dram_bytes_per_ray", 0.0) * R
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    import paper_2305_04966_gb300 as nacc
+    nacc.load_library()
+
+    w = workloads.c2_image(args.width, args.height, view=view_for_rank(rank))
+    g, m = w.grid, w.march
+    n = w.n_rays
+    field = nacc.BlobField.from_numpy(w.blobs, dev)
+    grid = nacc.OccupancyGrid.empty(g.aabb_min, g.aabb_max, g.res, g.n_levels, dev)
+    nacc.density_grid(grid, field, 0.01)
+    o = torch.as_tensor(w.rays_o).to(dev)
+    d = torch.as_tensor(w.rays_d).to(dev)
+    tgt = torch.as_tensor(w.target).to(dev)
+    cap = n * m.max_steps  # worst case: the march never synchronises
+    bufs = nacc.MarchBuffers(n, cap, dev)
+    sig = torch.empty(cap, dtype=torch.float32, device=dev)
+    rgbs = torch.empty((cap, 3), dtype=torch.float32, device=dev)
+    gsg = torch.empty(cap, dtype=torch.float32, device=dev)
+    gcc = torch.empty((cap, 3), dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stages = ["march", "field", "render_fwd", "loss", "render_bwd"]
+
+    def step(o_, d_, tgt_, ev=None):
+        if ev is not None:
+            ev[0].record()
+        pk = nacc.march_grid(grid, o_, d_, m.step, m.max_steps, m.t_min, m.t_max, m.early_stop_eps,
+                             field=field, buffers=bufs)
+        if ev is not None:
+            ev[1].record()
+        nacc.field_eval(field, o_, d_, pk, out=(sig, rgbs))
+        if ev is not None:
+            ev[2].record()
+        rgb, op, dep, tr, _ = nacc.render_fwd(pk.offsets, pk.t_starts, pk.t_ends, sig, rgbs, w.bg, 0.0)
+        if ev is not None:
+            ev[3].record()
+        loss, g_rgb = nacc.l2_loss(rgb, tgt_)
+        if ev is not None:
+            ev[4].record()
+        nacc.render_bwd(pk.offsets, pk.t_starts, pk.t_ends, sig, rgbs, g_rgb, None, None, w.bg, 0.0,
+                        out=(gsg, gcc))
+        if ev is not None:
+            ev[5].record()
+        return rgb, loss
+
+    for _ in range(max(args.warmup, 0)):
+        step(o, d, tgt)
+    torch.cuda.synchronize()
+    S = bufs.packed.n_samples()
+
+    clk = ClockSampler(torch.cuda.current_device() if world == 1 else local)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    time.sleep(0.3)
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()  # L2 flush between timed steps (outside the events)
+        step(o, d, tgt, evs[i])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    clocks = clk.stop()
+    stage_ms = {s: 0.0 for s in stages}
+    step_ms = []
+    for ev in evs:
+        step_ms.append(ev[0].elapsed_time(ev[5]))
+        for j, s in enumerate(stages):
+            stage_ms[s] += ev[j].elapsed_time(ev[j + 1])
+    stage_ms = {s: v / args.steps for s, v in stage_ms.items()}
+    ms_local = sum(step_ms) / len(step_ms)
+    ms = reduce_max(ms_local, dist)
+    rays_total = reduce_sum(n, dist)
+    samples_total = reduce_sum(S, dist)
+    value = rays_total / (ms / 1000.0)
+
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    hbm = peaks.get("hbm_gbs")
+    peak_src = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    path_bytes = sum(BYTES[s][0] * S + BYTES[s][1] * n for s in BYTES)
+    path_ms = sum(stage_ms[s] for s in BYTES)
+    dom = max(BYTES, key=lambda s: stage_ms[s])
+    dom_bytes = BYTES[dom][0] * S + BYTES[dom][1] * n
+    achieved = dom_bytes / (stage_ms[dom] / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "peak_source": peak_src,
+                "traffic": recorded_traffic(dom, S, n),
+                "algorithmic_bytes": dom_bytes}
+    path_ach = path_bytes / (path_ms / 1000.0) / 1e9
+    stage_roof = {}
+    for s in BYTES:
+        b = BYTES[s][0] * S + BYTES[s][1] * n
+        a = b / (stage_ms[s] / 1000.0) / 1e9
+        stage_roof[s] = {"ms": stage_ms[s], "GB/s": a, "frac": a / hbm, "traffic": recorded_traffic(s, S, n)}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = e2e_measure(args, torch, nacc, step, w, dev, n, flush, dist)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "n_rays_per_gpu": n, "grid": f"{g.n_levels}x{g.res}^3",
+                       "max_steps": m.max_steps, "blobs": w.blobs.n, "early_stop_eps": m.early_stop_eps,
+                       "samples_per_gpu": S, "l2": "flushed between timed steps (512 MB write)",
+                       "parallelism": f"dp{world} (one view per GPU)"},
+            "samples_per_s": samples_total / (ms / 1000.0),
+            "stage_ms": stage_ms,
+            "roofline": roofline,
+            "path_roofline": {"bound": "hbm", "achieved": path_ach, "peak": hbm, "unit": "GB/s",
+                              "frac": path_ach / hbm, "stages": list(BYTES), "ms": path_ms,
+                              "algorithmic_bytes": path_bytes, "peak_source": peak_src},
+            "stage_roofline": stage_roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clocks,
+            "gpu_launches": sum(KERNELS_PER_STEP.values()) * args.steps,
+            "wall_s_timed_region": wall,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def e2e_measure(args, torch, nacc, step, w, dev, n, flush, dist):
+    """Same step with the inputs (rays, target) copied in from pinned host
+    memory and the rendered image + loss copied back, all inside the events."""
+    o_h = torch.as_tensor(w.rays_o).pin_memory()
+    d_h = torch.as_tensor(w.rays_d).pin_memory()
+    t_h = torch.as_tensor(w.target).pin_memory()
+    rgb_h = torch.empty((n, 3), dtype=torch.float32).pin_memory()
+    loss_h = torch.empty(1, dtype=torch.float32).pin_memory()
+    o_d = torch.empty_like(o_h, device=dev)
+    d_d = torch.empty_like(d_h, device=dev)
+    t_d = torch.empty_like(t_h, device=dev)
+    K = max(1, args.steps // 2)
+    total = 0.0
+    for i in range(2 + K):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        o_d.copy_(o_h, non_blocking=True)
+        d_d.copy_(d_h, non_blocking=True)
+        t_d.copy_(t_h, non_blocking=True)
+        rgb, loss = step(o_d, d_d, t_d)
+        rgb_h.copy_(rgb, non_blocking=True)
+        loss_h.copy_(loss, non_blocking=True)
+        e1.record()
+        e1.synchronize()
+        if i >= 2:
+            total += e0.elapsed_time(e1)
+    ms = reduce_max(total / K, dist)
+    rays_total = reduce_sum(n, dist)
+    h2d = o_h.numel() * 4 + d_h.numel() * 4 + t_h.numel() * 4
+    d2h = rgb_h.numel() * 4 + 4
+    return {"value": rays_total / (ms / 1000.0), "unit": "rays/s", "ms_per_step": ms,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": K}
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

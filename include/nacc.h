@@ -1,0 +1,230 @@
+/*
+ * nacc.h -- C ABI of the GB300 (sm_103a) occupancy-grid sampling and
+ * differentiable volume-rendering library (the hot path of NerfAcc,
+ * arXiv 2305.04966: Algorithm 1 "sampling" and "rendering", Sec. 4.2).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Pointers marked [device] must be CUDA device (or managed) memory that
+ *    the caller owns and keeps alive until the work queued on `stream` has
+ *    finished.  Pointers marked [host] are read during the call only.
+ *  - Arrays are C-contiguous.  "[n][3]" means n rows of 3 floats (x, y, z or
+ *    r, g, b).  Floating point is IEEE FP32 unless stated.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Every call only enqueues kernels on `stream` and returns; the
+ *    only call that may synchronise is nacc_march_grid on a capacity
+ *    overflow (see there).  No call allocates or frees device memory;
+ *    temporary buffers are passed in as `scratch`.
+ *  - Every call returns a status (NACC_OK = 0 or a negative NACC_ERR_*).
+ *    On error nothing has been enqueued unless stated, and
+ *    nacc_last_error() returns a message for the calling thread.  No C++
+ *    exception crosses this boundary.
+ *  - Calls are thread-safe with respect to each other; work on the same
+ *    buffers from different streams must be ordered by the caller.
+ *  - Densities must be >= 0 and finite; interval ends t_end >= t_start.
+ */
+#ifndef NACC_H
+#define NACC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NACC_OK 0
+#define NACC_ERR_INVALID_ARG (-1) /* bad pointer, size or parameter; nothing enqueued */
+#define NACC_ERR_CAPACITY (-2)    /* packed output too small; required size reported */
+#define NACC_ERR_CUDA (-3)        /* a CUDA runtime call failed (launch or sync) */
+#define NACC_ERR_TIMEOUT (-4)     /* reserved: a bounded device wait expired */
+#define NACC_ERR_UNSUPPORTED (-5) /* valid request this build does not implement */
+
+#define NACC_MAX_LEVELS 8
+
+/* Cascaded occupancy grid (Table 1 "Spatial Skipping"; Instant-NGP-style
+ * cascade).  Level l covers the level-0 box scaled by 2^l about its centre;
+ * each level has res^3 cells.  Cell (i0, i1, i2) of level l has flat index
+ *   c = l*res^3 + (i0*res + i1)*res + i2
+ * and is occupied iff bit (c & 31) of bits[c >> 5] is set.  A point belongs
+ * to the finest level whose closed box contains it, and to the cell
+ * floor((x - lmin_l) * res / (lmax_l - lmin_l)) of that level (clamped to
+ * [0, res-1]), all in FP32. */
+typedef struct nacc_grid {
+    float aabb_min[3];    /* level-0 box, aabb_min < aabb_max per axis */
+    float aabb_max[3];
+    int32_t res;          /* cells per axis per level, 1..1024, res^3 % 32 == 0 */
+    int32_t n_levels;     /* 1..NACC_MAX_LEVELS */
+    const uint32_t* bits; /* [device] n_levels*res^3/32 words (unused by update/points) */
+} nacc_grid;
+
+/* Lattice march parameters (Appendix B: step size, threshold). */
+typedef struct nacc_march_params {
+    float step;           /* lattice spacing dt > 0 */
+    int32_t max_steps;    /* lattice index bound: k < max_steps, 1..2^24 */
+    float t_min;          /* near plane: t_near = max(t_min, box entry) */
+    float t_max;          /* far plane: t_far = min(t_max, box exit) */
+    float early_stop_eps; /* with a field: stop once T < eps (Sec. 4.2, 1e-4); <= 0: never */
+} nacc_march_params;
+
+/* Analytic density field used for early termination inside the march (the
+ * "density_fn" of Algorithm 1, here a sum of isotropic Gaussian blobs):
+ *   sigma(x) = sum_b peak_b * exp(-|x - mu_b|^2 / (2 std_b^2)).
+ * rgb is only used by the harness field kernel (nacc_harness.h). */
+typedef struct nacc_blob_field {
+    int32_t n_blobs;    /* 0..1024 */
+    const float* mu;    /* [device] [n_blobs][3] */
+    const float* std;   /* [device] [n_blobs], > 0 */
+    const float* peak;  /* [device] [n_blobs] */
+    const float* rgb;   /* [device] [n_blobs][3] (may be NULL for the march) */
+} nacc_blob_field;
+
+/* Packed samples (Sec. 4.2 "Sample as Interval", "Packed Tensor"): sample s
+ * is the interval [t_starts[s], t_ends[s]] on ray ray_indices[s]; the samples
+ * of ray r are s in [offsets[r], offsets[r+1]), in increasing t. */
+typedef struct nacc_packed {
+    int64_t* offsets;     /* [device] [n_rays+1], written (CSR row pointer) */
+    int32_t* ray_indices; /* [device] [capacity] or NULL (then not written) */
+    float* t_starts;      /* [device] [capacity] */
+    float* t_ends;        /* [device] [capacity] */
+    int64_t capacity;     /* elements available in the three sample arrays */
+    int64_t* n_samples;   /* [device] 1 element: total sample count, written */
+} nacc_packed;
+
+/* Message describing the last error on the calling thread ("" if none). */
+const char* nacc_last_error(void);
+
+/* Library version (major*10000 + minor*100 + patch). */
+int nacc_version(void);
+
+/* Scratch bytes nacc_march_grid needs for n_rays rays. */
+size_t nacc_march_scratch_bytes(int64_t n_rays);
+
+/*
+ * Occupancy-grid ray marching into packed samples.
+ * Follows: Table 1 "Spatial Skipping" (occupied <=> bit set); Sec. 3.1
+ * "Spatial Skipping" (skip empty regions); Sec. 4.2 "Sample as Interval",
+ * "Packed Tensor", "No Gradient Filtering" (drop samples with T < 1e-4);
+ * Appendix B hyper-parameters (step dt, resolution, threshold).
+ *
+ * Per ray r (o = rays_o[r], d = rays_d[r], FP32, every operation rounded):
+ * [t_near, t_far] = slab clip of the ray against the outermost level's box,
+ * intersected with [t_min, t_max]; lattice t0_k = t_near + k*step for
+ * k < max_steps while t0_k < t_far; the interval [t0_k, t0_k + step] is
+ * emitted iff the midpoint o + d*(t0_k + t1_k)/2 lies in an occupied cell.
+ * Empty cells are skipped conservatively: the emitted set is exactly that of
+ * the dense march.  With `field` non-NULL and eps > 0, sigma is evaluated at
+ * each emitted midpoint and the ray stops at the first occupied k whose
+ * accumulated optical depth sum(sigma*(t1-t0)) over the samples before it
+ * exceeds -ln(eps) (T < eps).  Directions are used as given (not normalised).
+ *
+ * rays_o, rays_d: [device] [n_rays][3].  out: see nacc_packed.  scratch:
+ * [device] >= nacc_march_scratch_bytes(n_rays) bytes, 256-byte aligned.
+ * Capacity: if out->capacity >= n_rays*max_steps no overflow is possible and
+ * the call never synchronises (CUDA-graph capturable).  Otherwise the call
+ * synchronises `stream` after counting; if the total exceeds the capacity it
+ * writes offsets and *n_samples but no samples and returns
+ * NACC_ERR_CAPACITY (retry with capacity >= *n_samples).
+ */
+int nacc_march_grid(const nacc_grid* grid, const float* rays_o, const float* rays_d,
+                    int64_t n_rays, const nacc_march_params* params,
+                    const nacc_blob_field* field, nacc_packed* out, void* scratch,
+                    size_t scratch_bytes, void* stream);
+
+/*
+ * Sample points for the estimator update (Eq. 4; Sec. 3.1 "Spatial
+ * Skipping": the cached density is refreshed every few steps at points of
+ * each cell).  For every cell c of every level (flat index as in nacc_grid):
+ *   xyz[c][a] = lmin_l[a] + ((float)i_a + u) * width_l[a],
+ *   width_l = (lmax_l - lmin_l)/res,
+ * u = 0.5 (jitter == 0, cell centre) or u = (h >> 40) * 2^-24 with
+ * h = SplitMix64 output number 3c+a+1 of the stream seeded with
+ * seed ^ (step << 32) (jitter != 0).  xyz_out: [device] [n_levels*res^3][3].
+ */
+int nacc_grid_points(const nacc_grid* grid, uint64_t seed, int64_t step, int32_t jitter,
+                     float* xyz_out, void* stream);
+
+/* Scratch bytes nacc_update_grid needs for n_cells cells. */
+size_t nacc_update_grid_scratch_bytes(int64_t n_cells);
+
+/*
+ * Estimator update F: T^{k-1} -> T^k (Eq. 4) in its EMA form (Sec. 3.1
+ * "Spatial Skipping") and binarisation 1[sigma > tau] (Table 1):
+ *   ema[c] <- decay*ema[c] + (1-decay)*density[c]   (FP32, this order)
+ *   mean   =  FP64 mean of the updated ema over all n_levels*res^3 cells
+ *   thr    =  max(thresh_abs, thresh_frac * mean)    (FP64)
+ *   bit c of bits_out = ((double)ema[c] > thr)
+ * decay = 0 initialises ema from density.  ema: [device] in/out,
+ * density: [device], bits_out: [device] n_cells/32 words (may alias
+ * grid->bits of a later march).  scratch: [device] >=
+ * nacc_update_grid_scratch_bytes(n_cells) bytes, 256-byte aligned.
+ */
+int nacc_update_grid(const nacc_grid* grid, float* ema, const float* density, float decay,
+                     float thresh_frac, float thresh_abs, uint32_t* bits_out, void* scratch,
+                     size_t scratch_bytes, void* stream);
+
+/*
+ * Inverse transform sampling from a piecewise-constant PDF (Eq. 1), with
+ * the CDF read as 1 - T (Eq. 3; Table 1 "PDF Approaches").  Per ray, bins
+ * [e_j, e_{j+1}] (j < n_bins) carry weights w_j >= 0 (FP32 throughout):
+ *   W = w_0 + ... + w_{n-1} (sequential); if W > 0: F_0 = 0,
+ *   F_j = (w_0 + ... + w_{j-1}) / W, F_n = 1; else F_j = j/n (uniform).
+ *   u_k = k/n_out for k = 0..n_out; stratified != 0: for 0 < k < n_out,
+ *   u_k = min(1, (k + U_r)/n_out), U_r = top 24 bits of SplitMix64 output
+ *   r+1 of the stream seeded with `seed`, times 2^-24.
+ *   j = largest j in [0, n-1] with F_j <= u_k and F_j < 1;
+ *   t_k = e_j + ((u_k - F_j)/(F_{j+1} - F_j)) * (e_{j+1} - e_j), or e_j if
+ *   F_{j+1} == F_j.
+ * edges: [device] [n_rays][n_bins+1] non-decreasing; weights: [device]
+ * [n_rays][n_bins]; edges_out: [device] [n_rays][n_out+1].
+ * n_bins 1..4096, n_out 1..4096.
+ */
+int nacc_sample_pdf(int64_t n_rays, int32_t n_bins, const float* edges, const float* weights,
+                    int32_t n_out, int32_t stratified, uint64_t seed, float* edges_out,
+                    void* stream);
+
+/*
+ * Differentiable volume rendering of packed samples, forward (Eq. 2
+ * discretised; Table 1 "PDF Approaches" row; Algorithm 1 "rendering").
+ * Per ray r over its samples i (tau_i = sigma_i*(t1_i - t0_i)):
+ *   P_i = sum_{j<i} tau_j, T_i = exp(-P_i); sample i is masked when
+ *   early_stop_eps > 0 and P_i > -ln(eps) (T_i < eps, Sec. 4.2);
+ *   w_i = T_i*(1 - exp(-tau_i)) for unmasked i, else 0;
+ *   T_N = exp(-sum of tau_i over unmasked i);
+ *   rgb_out = sum w_i c_i + T_N*bg, opacity_out = sum w_i,
+ *   depth_out = sum w_i*(t0_i + t1_i)/2, trans_out = T_N.
+ * Rays with no samples give rgb = bg, opacity = depth = 0, trans = 1.
+ * offsets: [device] [n_rays+1] CSR with offsets[0] = 0 (the total sample
+ * count is read on the device from offsets[n_rays]); t_starts, t_ends,
+ * sigmas: [device] [S]; rgbs: [device] [S][3]; bg: [host] 3 floats;
+ * outputs [device]: rgb_out [n_rays][3], opacity_out, depth_out, trans_out
+ * [n_rays]; weights_out [S] or NULL.
+ */
+int nacc_render_fwd(int64_t n_rays, const int64_t* offsets, const float* t_starts,
+                    const float* t_ends, const float* sigmas, const float* rgbs, const float* bg,
+                    float early_stop_eps, float* rgb_out, float* opacity_out, float* depth_out,
+                    float* trans_out, float* weights_out, void* stream);
+
+/*
+ * Adjoint of nacc_render_fwd (Algorithm 1: the radiance field receives
+ * gradients through rendering).  With g_C = g_rgb[r], g_A = g_opacity[r],
+ * g_D = g_depth[r], T_{i+1} = exp(-(P_i + tau_i)), m_i = (t0_i + t1_i)/2,
+ * S^c_i = sum_{k>i} w_k c_k, S^m_i = sum_{k>i} w_k m_k (unmasked k):
+ *   g_rgbs[i]   = w_i * g_C
+ *   g_sigmas[i] = (t1_i - t0_i) * ( g_C . (T_{i+1} c_i - S^c_i - T_N bg)
+ *                                 + g_A*T_N + g_D*(T_{i+1} m_i - S^m_i) )
+ * and 0 for masked samples.  Per-sample transmittance is recomputed, not
+ * saved.  Inputs as nacc_render_fwd plus [device] g_rgb [n_rays][3],
+ * g_opacity [n_rays], g_depth [n_rays] (any of the three may be NULL =
+ * zero); outputs [device] g_sigmas [S], g_rgbs [S][3].
+ */
+int nacc_render_bwd(int64_t n_rays, const int64_t* offsets, const float* t_starts,
+                    const float* t_ends, const float* sigmas, const float* rgbs, const float* bg,
+                    float early_stop_eps, const float* g_rgb, const float* g_opacity,
+                    const float* g_depth, float* g_sigmas, float* g_rgbs, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NACC_H */

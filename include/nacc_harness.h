@@ -1,0 +1,49 @@
+/*
+ * nacc_harness.h -- benchmark / test harness kernels shipped in the same
+ * library as nacc.h.  They are NOT the method: they stand in for the user's
+ * radiance field (the "density_fn" / "rgb_density_fn" of Algorithm 1 in
+ * NerfAcc, arXiv 2305.04966) and for the training loss, so that a full
+ * sampling -> rendering -> gradient step can run on synthetic scenes.
+ * Conventions (device/host pointers, streams, status codes) as in nacc.h.
+ */
+#ifndef NACC_HARNESS_H
+#define NACC_HARNESS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include "nacc.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/*
+ * Analytic blob field at the midpoints of packed samples (Algorithm 1
+ * rgb_density_fn): x = rays_o[r] + rays_d[r]*(t0+t1)/2 with r =
+ * ray_indices[s]; sigma = sum_b peak_b exp(-|x-mu_b|^2/(2 std_b^2));
+ * rgb = sum_b sigma_b rgb_b / sigma (0 where sigma == 0).  The sample count
+ * is read on the device from *n_samples, so no host synchronisation is
+ * needed.  Writes sigmas [S] and rgbs [S][3] (both [device]).
+ */
+int nacc_harness_field(const float* rays_o, const float* rays_d, const int32_t* ray_indices,
+                       const float* t_starts, const float* t_ends, const int64_t* n_samples,
+                       const nacc_blob_field* field, float* sigmas, float* rgbs, void* stream);
+
+/* Density of the blob field at n points xyz [n][3] -> sigma [n] (both [device]). */
+int nacc_harness_field_points(int64_t n, const float* xyz, const nacc_blob_field* field,
+                              float* sigma, void* stream);
+
+/*
+ * Mean squared error against a target image and its gradient:
+ *   loss = sum (rgb - target)^2 / (3 n),  g_rgb = 2 (rgb - target) / (3 n).
+ * rgb, target, g_rgb: [device] [n][3]; loss: [device] 1 float.
+ */
+int nacc_harness_l2_loss(int64_t n, const float* rgb, const float* target, float* g_rgb,
+                         float* loss, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NACC_HARNESS_H */

@@ -1,0 +1,19 @@
+"""GB300 (sm_103a) occupancy-grid sampling and differentiable volume rendering.
+
+The hot path of NerfAcc (arXiv 2305.04966), Algorithm 1: ``march_grid``
+(transmittance-estimator sampling with an occupancy grid, Table 1 "Spatial
+Skipping", Sec. 4.2), ``render`` / ``render_fwd`` / ``render_bwd`` (Eq. 2
+and its adjoint), ``update_grid`` (Eq. 4, EMA), ``sample_pdf`` (Eq. 1 with
+F = 1 - T, Eq. 3).  The kernels live in ``libnacc.so`` behind the C ABI of
+``include/nacc.h``; this package only marshals torch tensors.
+"""
+from ._abi import NaccError, load as load_library
+from .api import (BlobField, MarchBuffers, OccupancyGrid, PackedSamples, RenderFn, UpdateBuffers,
+                  density_grid, field_eval, field_points, grid_points, l2_loss, march_grid, render,
+                  render_bwd, render_fwd, sample_pdf, update_grid)
+
+__all__ = [
+    "NaccError", "load_library", "BlobField", "MarchBuffers", "OccupancyGrid", "PackedSamples",
+    "RenderFn", "UpdateBuffers", "density_grid", "field_eval", "field_points", "grid_points",
+    "l2_loss", "march_grid", "render", "render_bwd", "render_fwd", "sample_pdf", "update_grid",
+]

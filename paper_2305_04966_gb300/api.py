@@ -1,0 +1,394 @@
+"""PyTorch-facing binding of the C ABI (argument marshalling only).
+
+Every function here checks tensor placement / dtype / shape, allocates the
+output tensors, and calls the corresponding ``nacc_*`` entry point on the
+current CUDA stream.  All arithmetic of the path runs in the CUDA library;
+there is no CPU fallback.  Names follow Algorithm 1 of NerfAcc
+(arXiv 2305.04966): ``march_grid`` is its ``sampling`` with an occupancy-grid
+estimator, ``render`` its differentiable ``rendering``, ``update_grid`` its
+``estimator.update_every_n_steps``.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import math
+
+import torch
+
+from . import _abi
+
+_F32, _I32, _I64 = torch.float32, torch.int32, torch.int64
+
+
+def _stream(dev: torch.device) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+
+
+_EMPTY = {}
+
+
+def _ptr(t):
+    """Device pointer of ``t``; a zero-element tensor maps to a small valid
+    buffer so that the ABI's non-NULL checks hold (nothing is read from it)."""
+    if t is None:
+        return None
+    if t.numel() == 0:
+        key = t.device
+        if key not in _EMPTY:
+            _EMPTY[key] = torch.zeros(16, dtype=torch.float32, device=t.device)
+        return ctypes.c_void_p(_EMPTY[key].data_ptr())
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check(t, name, dtype, dev=None, shape=None):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (no CPU path exists)")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dev is not None and t.device != dev:
+        raise ValueError(f"{name} is on {t.device}, expected {dev}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t
+
+
+def _scratch(nbytes: int, dev) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=dev)
+
+
+# ---------------------------------------------------------------------------
+# occupancy grid
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class OccupancyGrid:
+    """Cascaded occupancy grid: ``n_levels`` levels of ``res^3`` cells; level l
+    covers the level-0 box scaled by 2^l about its centre.  ``bits`` packs one
+    occupancy bit per cell (int32 words, bit c%32 of word c//32); ``ema`` is the
+    running density estimate the update refreshes (Eq. 4)."""
+
+    aabb_min: tuple
+    aabb_max: tuple
+    res: int
+    n_levels: int
+    bits: torch.Tensor  # int32 [n_cells/32]
+    ema: torch.Tensor | None = None  # float32 [n_cells]
+
+    @property
+    def n_cells(self) -> int:
+        return self.n_levels * self.res ** 3
+
+    @classmethod
+    def empty(cls, aabb_min, aabb_max, res, n_levels, device="cuda"):
+        n = n_levels * res ** 3
+        return cls(tuple(map(float, aabb_min)), tuple(map(float, aabb_max)), int(res), int(n_levels),
+                   torch.zeros(n // 32, dtype=_I32, device=device),
+                   torch.zeros(n, dtype=_F32, device=device))
+
+    def c_struct(self) -> _abi.Grid:
+        g = _abi.Grid()
+        g.aabb_min[:] = [float(v) for v in self.aabb_min]
+        g.aabb_max[:] = [float(v) for v in self.aabb_max]
+        g.res = int(self.res)
+        g.n_levels = int(self.n_levels)
+        g.bits = _ptr(self.bits)
+        return g
+
+
+@dataclasses.dataclass
+class BlobField:
+    """Analytic density field sum_b peak_b exp(-|x-mu_b|^2/(2 std_b^2)) (harness stand-in
+    for the radiance field); tensors on the device."""
+
+    mu: torch.Tensor    # [B][3]
+    std: torch.Tensor   # [B]
+    peak: torch.Tensor  # [B]
+    rgb: torch.Tensor   # [B][3]
+
+    @classmethod
+    def from_numpy(cls, blobs, device="cuda"):
+        t = lambda a: torch.as_tensor(a, dtype=_F32).contiguous().to(device)
+        return cls(t(blobs.mu), t(blobs.std), t(blobs.peak), t(blobs.rgb))
+
+    @property
+    def n(self) -> int:
+        return int(self.std.shape[0])
+
+    def c_struct(self) -> _abi.BlobField:
+        f = _abi.BlobField()
+        f.n_blobs = self.n
+        f.mu, f.std, f.peak, f.rgb = _ptr(self.mu), _ptr(self.std), _ptr(self.peak), _ptr(self.rgb)
+        return f
+
+
+# ---------------------------------------------------------------------------
+# sampling (Algorithm 1 "sampling"; Sec. 4.2 packed intervals)
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class PackedSamples:
+    """Packed intervals: sample s = [t_starts[s], t_ends[s]] on ray ray_indices[s];
+    ray r owns samples offsets[r]:offsets[r+1].  Sample arrays have ``capacity``
+    entries; the first ``n_samples`` are valid."""
+
+    offsets: torch.Tensor      # int64 [n_rays+1]
+    ray_indices: torch.Tensor | None  # int32 [capacity]
+    t_starts: torch.Tensor     # float32 [capacity]
+    t_ends: torch.Tensor       # float32 [capacity]
+    n_samples_dev: torch.Tensor  # int64 [1] on the device
+
+    @property
+    def capacity(self) -> int:
+        return int(self.t_starts.shape[0])
+
+    def n_samples(self) -> int:
+        """Total sample count (synchronises)."""
+        return int(self.n_samples_dev.item())
+
+    def trimmed(self) -> "PackedSamples":
+        n = self.n_samples()
+        return PackedSamples(self.offsets, None if self.ray_indices is None else self.ray_indices[:n],
+                             self.t_starts[:n], self.t_ends[:n], self.n_samples_dev)
+
+
+class MarchBuffers:
+    """Reusable device buffers for :func:`march_grid` (no allocation per call,
+    capture-safe when ``capacity >= n_rays*max_steps``)."""
+
+    def __init__(self, n_rays: int, capacity: int, device="cuda", with_ray_indices: bool = True):
+        dev = torch.device(device)
+        self.n_rays = int(n_rays)
+        self.packed = PackedSamples(
+            torch.empty(n_rays + 1, dtype=_I64, device=dev),
+            torch.empty(capacity, dtype=_I32, device=dev) if with_ray_indices else None,
+            torch.empty(capacity, dtype=_F32, device=dev),
+            torch.empty(capacity, dtype=_F32, device=dev),
+            torch.zeros(1, dtype=_I64, device=dev))
+        self.scratch = _scratch(_abi.load().nacc_march_scratch_bytes(n_rays), dev)
+
+
+def march_grid(grid: OccupancyGrid, rays_o: torch.Tensor, rays_d: torch.Tensor, step: float,
+               max_steps: int = 1024, t_min: float = 0.0, t_max: float = 1e10,
+               early_stop_eps: float = 1e-4, field: BlobField | None = None,
+               capacity: int | None = None, buffers: MarchBuffers | None = None,
+               with_ray_indices: bool = True) -> PackedSamples:
+    """Occupancy-grid lattice march into packed samples (``nacc_march_grid``).
+
+    With ``field`` given, samples are filtered at T < early_stop_eps while
+    marching (Sec. 4.2 "No Gradient Filtering").  Without ``buffers``, a
+    capacity is chosen (worst case when it is small, else a guess that is
+    grown on NACC_ERR_CAPACITY)."""
+    dev = rays_o.device
+    _check(rays_o, "rays_o", _F32, dev)
+    n = int(rays_o.shape[0])
+    _check(rays_d, "rays_d", _F32, dev, (n, 3))
+    if rays_o.dim() != 2 or rays_o.shape[1] != 3:
+        raise ValueError("rays_o must be [n][3]")
+    _check(grid.bits, "grid.bits", _I32, dev, (grid.n_cells // 32,))
+    params = _abi.MarchParams(float(step), int(max_steps), float(t_min), float(t_max),
+                              float(early_stop_eps))
+    fs = field.c_struct() if field is not None else None
+    worst = n * int(max_steps)
+    while True:
+        if buffers is None:
+            cap = capacity if capacity is not None else (worst if worst * 12 <= (1 << 31) else max(n * 64, 1 << 20))
+            buf = MarchBuffers(n, cap, dev, with_ray_indices)
+        else:
+            buf = buffers
+            if buf.n_rays != n:
+                raise ValueError("buffers were made for a different ray count")
+        pk = buf.packed
+        out = _abi.Packed(_ptr(pk.offsets), _ptr(pk.ray_indices), _ptr(pk.t_starts), _ptr(pk.t_ends),
+                          pk.capacity, _ptr(pk.n_samples_dev))
+        rc = _abi.call("nacc_march_grid", ctypes.byref(grid.c_struct()), _ptr(rays_o), _ptr(rays_d), n,
+                       ctypes.byref(params), ctypes.byref(fs) if fs is not None else None,
+                       ctypes.byref(out), _ptr(buf.scratch), buf.scratch.numel(), _stream(dev))
+        if rc == _abi.NACC_OK:
+            return pk
+        if buffers is not None or capacity is not None:
+            raise _abi.NaccError("nacc_march_grid", rc, "capacity too small")
+        capacity = int(pk.n_samples_dev.item())
+
+
+# ---------------------------------------------------------------------------
+# rendering (Algorithm 1 "rendering"; Eq. 2)
+# ---------------------------------------------------------------------------
+
+def _bg(bg):
+    return (ctypes.c_float * 3)(*[float(v) for v in bg])
+
+
+def render_fwd(offsets, t_starts, t_ends, sigmas, rgbs, bg=(1.0, 1.0, 1.0), early_stop_eps=0.0,
+               want_weights=False):
+    """Composite packed samples.  Returns (rgb [n][3], opacity [n], depth [n], trans [n],
+    weights [S] or None)."""
+    dev = offsets.device
+    _check(offsets, "offsets", _I64, dev)
+    n = int(offsets.shape[0]) - 1
+    cap = int(t_starts.shape[0])
+    _check(t_starts, "t_starts", _F32, dev)
+    _check(t_ends, "t_ends", _F32, dev, (cap,))
+    _check(sigmas, "sigmas", _F32, dev)
+    _check(rgbs, "rgbs", _F32, dev)
+    if sigmas.shape[0] > cap or rgbs.shape[0] != sigmas.shape[0] or rgbs.dim() != 2 or rgbs.shape[1] != 3:
+        raise ValueError("sigmas [S] / rgbs [S][3] must match the sample arrays")
+    rgb = torch.empty((n, 3), dtype=_F32, device=dev)
+    op = torch.empty(n, dtype=_F32, device=dev)
+    dep = torch.empty(n, dtype=_F32, device=dev)
+    tr = torch.empty(n, dtype=_F32, device=dev)
+    w = torch.empty(sigmas.shape[0], dtype=_F32, device=dev) if want_weights else None
+    _abi.call("nacc_render_fwd", n, _ptr(offsets), _ptr(t_starts), _ptr(t_ends), _ptr(sigmas), _ptr(rgbs),
+              _bg(bg), float(early_stop_eps), _ptr(rgb), _ptr(op), _ptr(dep), _ptr(tr), _ptr(w), _stream(dev))
+    return rgb, op, dep, tr, w
+
+
+def render_bwd(offsets, t_starts, t_ends, sigmas, rgbs, g_rgb, g_opacity, g_depth, bg=(1.0, 1.0, 1.0),
+               early_stop_eps=0.0, out=None):
+    """Adjoint of :func:`render_fwd`.  Returns (g_sigmas [S], g_rgbs [S][3])."""
+    dev = offsets.device
+    n = int(offsets.shape[0]) - 1
+    for t, nm, shp in ((g_rgb, "g_rgb", (n, 3)), (g_opacity, "g_opacity", (n,)), (g_depth, "g_depth", (n,))):
+        if t is not None:
+            _check(t, nm, _F32, dev, shp)
+    if out is None:
+        gs = torch.empty_like(sigmas)
+        gc = torch.empty_like(rgbs)
+    else:
+        gs, gc = out
+    _abi.call("nacc_render_bwd", n, _ptr(offsets), _ptr(t_starts), _ptr(t_ends), _ptr(sigmas), _ptr(rgbs),
+              _bg(bg), float(early_stop_eps), _ptr(g_rgb), _ptr(g_opacity), _ptr(g_depth), _ptr(gs),
+              _ptr(gc), _stream(dev))
+    return gs, gc
+
+
+class RenderFn(torch.autograd.Function):
+    """Differentiable compositing: (sigmas, rgbs) -> (rgb, opacity, depth).  The
+    backward recomputes per-sample transmittance from the samples (none saved)."""
+
+    @staticmethod
+    def forward(ctx, sigmas, rgbs, offsets, t_starts, t_ends, bg=(1.0, 1.0, 1.0), early_stop_eps=0.0):
+        rgb, op, dep, _, _ = render_fwd(offsets, t_starts, t_ends, sigmas, rgbs, bg, early_stop_eps)
+        ctx.save_for_backward(sigmas, rgbs, offsets, t_starts, t_ends)
+        ctx.bg, ctx.eps = bg, early_stop_eps
+        return rgb, op, dep
+
+    @staticmethod
+    def backward(ctx, g_rgb, g_op, g_dep):
+        sigmas, rgbs, offsets, t_starts, t_ends = ctx.saved_tensors
+        c = lambda t: None if t is None else t.contiguous()
+        gs, gc = render_bwd(offsets, t_starts, t_ends, sigmas, rgbs, c(g_rgb), c(g_op), c(g_dep),
+                            ctx.bg, ctx.eps)
+        return gs, gc, None, None, None, None, None
+
+
+def render(sigmas, rgbs, packed: PackedSamples, bg=(1.0, 1.0, 1.0), early_stop_eps=0.0):
+    """Algorithm 1 ``rendering``: differentiable colour, opacity, depth per ray."""
+    return RenderFn.apply(sigmas, rgbs, packed.offsets, packed.t_starts, packed.t_ends, tuple(bg),
+                          float(early_stop_eps))
+
+
+# ---------------------------------------------------------------------------
+# estimator update (Eq. 4) and resampling (Eq. 1 / Eq. 3)
+# ---------------------------------------------------------------------------
+
+def grid_points(grid: OccupancyGrid, seed: int = 0, step: int = 0, jitter: bool = True, out=None):
+    """Sample point of every cell (jittered or centre), [n_cells][3]."""
+    dev = grid.bits.device
+    xyz = out if out is not None else torch.empty((grid.n_cells, 3), dtype=_F32, device=dev)
+    _check(xyz, "xyz", _F32, dev, (grid.n_cells, 3))
+    _abi.call("nacc_grid_points", ctypes.byref(grid.c_struct()), int(seed) & (2**64 - 1), int(step),
+              int(bool(jitter)), _ptr(xyz), _stream(dev))
+    return xyz
+
+
+class UpdateBuffers:
+    def __init__(self, n_cells: int, device="cuda"):
+        self.scratch = _scratch(_abi.load().nacc_update_grid_scratch_bytes(n_cells), torch.device(device))
+
+
+def update_grid(grid: OccupancyGrid, density: torch.Tensor, decay: float = 0.95,
+                thresh_frac: float = 0.01, thresh_abs: float = 0.0, buffers: UpdateBuffers | None = None):
+    """EMA update of ``grid.ema`` with ``density`` at the cell points, then
+    ``grid.bits`` = ema > max(thresh_abs, thresh_frac * mean(ema))."""
+    dev = grid.bits.device
+    _check(grid.ema, "grid.ema", _F32, dev, (grid.n_cells,))
+    _check(density, "density", _F32, dev, (grid.n_cells,))
+    buf = buffers if buffers is not None else UpdateBuffers(grid.n_cells, dev)
+    _abi.call("nacc_update_grid", ctypes.byref(grid.c_struct()), _ptr(grid.ema), _ptr(density),
+              float(decay), float(thresh_frac), float(thresh_abs), _ptr(grid.bits), _ptr(buf.scratch),
+              buf.scratch.numel(), _stream(dev))
+    return grid
+
+
+def sample_pdf(edges: torch.Tensor, weights: torch.Tensor, n_out: int, stratified: bool = False,
+               seed: int = 0, out=None):
+    """Inverse-CDF resampling: edges [n][nb+1], weights [n][nb] -> [n][n_out+1]."""
+    dev = edges.device
+    _check(weights, "weights", _F32, dev)
+    n, nb = int(weights.shape[0]), int(weights.shape[1])
+    _check(edges, "edges", _F32, dev, (n, nb + 1))
+    res = out if out is not None else torch.empty((n, n_out + 1), dtype=_F32, device=dev)
+    _check(res, "out", _F32, dev, (n, n_out + 1))
+    _abi.call("nacc_sample_pdf", n, nb, _ptr(edges), _ptr(weights), int(n_out), int(bool(stratified)),
+              int(seed) & (2**64 - 1), _ptr(res), _stream(dev))
+    return res
+
+
+# ---------------------------------------------------------------------------
+# harness (not the method): analytic field and loss
+# ---------------------------------------------------------------------------
+
+def field_eval(field: BlobField, rays_o, rays_d, packed: PackedSamples, out=None):
+    """Blob field at interval midpoints: (sigmas [cap], rgbs [cap][3])."""
+    dev = rays_o.device
+    if packed.ray_indices is None:
+        raise ValueError("field_eval needs ray_indices")
+    cap = packed.capacity
+    if out is None:
+        sig = torch.empty(cap, dtype=_F32, device=dev)
+        rgb = torch.empty((cap, 3), dtype=_F32, device=dev)
+    else:
+        sig, rgb = out
+    _abi.call("nacc_harness_field", _ptr(rays_o), _ptr(rays_d), _ptr(packed.ray_indices),
+              _ptr(packed.t_starts), _ptr(packed.t_ends), _ptr(packed.n_samples_dev),
+              ctypes.byref(field.c_struct()), _ptr(sig), _ptr(rgb), _stream(dev))
+    return sig, rgb
+
+
+def field_points(field: BlobField, xyz: torch.Tensor, out=None):
+    dev = xyz.device
+    _check(xyz, "xyz", _F32, dev)
+    n = int(xyz.shape[0])
+    sig = out if out is not None else torch.empty(n, dtype=_F32, device=dev)
+    _abi.call("nacc_harness_field_points", n, _ptr(xyz), ctypes.byref(field.c_struct()), _ptr(sig),
+              _stream(dev))
+    return sig
+
+
+def l2_loss(rgb: torch.Tensor, target: torch.Tensor, out=None):
+    """(loss [1], g_rgb [n][3]) for the mean squared error."""
+    dev = rgb.device
+    n = int(rgb.shape[0])
+    _check(rgb, "rgb", _F32, dev, (n, 3))
+    _check(target, "target", _F32, dev, (n, 3))
+    if out is None:
+        g = torch.empty_like(rgb)
+        loss = torch.empty(1, dtype=_F32, device=dev)
+    else:
+        g, loss = out
+    _abi.call("nacc_harness_l2_loss", n, _ptr(rgb), _ptr(target), _ptr(g), _ptr(loss), _stream(dev))
+    return loss, g
+
+
+def density_grid(grid: OccupancyGrid, field: BlobField, thresh: float = 0.01, seed: int = 0):
+    """Initialise ``grid`` from the field at cell centres: ema = sigma(centre),
+    bits = sigma(centre) > thresh (update with decay 0 and an absolute threshold)."""
+    pts = grid_points(grid, jitter=False)
+    dens = field_points(field, pts)
+    update_grid(grid, dens, decay=0.0, thresh_frac=0.0, thresh_abs=thresh)
+    return grid

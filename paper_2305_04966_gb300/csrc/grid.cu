@@ -1,0 +1,153 @@
+// grid.cu -- estimator update (nacc_grid_points, nacc_update_grid).
+//
+// Eq. 4 (the update F: T^{k-1} -> T^k) in the EMA form of Sec. 3.1
+// "Spatial Skipping", and the binarisation 1[sigma > tau] of Table 1.
+// Three kernels: EMA + per-block FP64 partial sums, a one-block reduction to
+// the FP64 mean and threshold, and a warp-ballot bit packer (32 cells = one
+// word per warp).  No atomics: the mean is deterministic.
+#include "nacc_internal.cuh"
+
+namespace nacc {
+namespace {
+
+constexpr int kEmaThreads = 256;
+constexpr int kEmaItems = 8;  // cells per thread
+constexpr int kEmaCells = kEmaThreads * kEmaItems;
+
+__global__ void __launch_bounds__(256)
+    k_grid_points(GridGeom g, uint64_t key, int jitter, int64_t n_cells, float* __restrict__ xyz) {
+    const int64_t r3 = (int64_t)g.res * g.res * g.res;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cells;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int l = (int)(c / r3);
+        const int64_t w = c - (int64_t)l * r3;
+        const int64_t i[3] = {w / ((int64_t)g.res * g.res), (w / g.res) % g.res, w % g.res};
+        const Level& lv = g.lv[l];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float u = jitter ? u01_from_bits(splitmix64(key, (uint64_t)(3 * c + a))) : 0.5f;
+            float q = __fadd_rn((float)i[a], u);
+            xyz[3 * c + a] = __fadd_rn(lv.lmin[a], __fmul_rn(q, lv.width[a]));
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kEmaThreads)
+    k_ema(float* __restrict__ ema, const float* __restrict__ dens, float decay, float omd,
+          int64_t n, double* __restrict__ partial) {
+    const int64_t base = (int64_t)blockIdx.x * kEmaCells;
+    double acc = 0.0;
+#pragma unroll
+    for (int j = 0; j < kEmaItems; ++j) {
+        int64_t c = base + j * kEmaThreads + threadIdx.x;
+        if (c < n) {
+            float a = __fmul_rn(decay, ema[c]);
+            float b = __fmul_rn(omd, __ldcs(dens + c));
+            float e = __fadd_rn(a, b);
+            ema[c] = e;
+            acc += (double)e;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    __shared__ double s_w[kEmaThreads / 32];
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < kEmaThreads / 32; ++w) t += s_w[w];
+        partial[blockIdx.x] = t;
+    }
+}
+
+// One block: mean = sum(partial) / n; thr = max(thresh_abs, thresh_frac*mean).
+__global__ void __launch_bounds__(1024)
+    k_mean_thr(const double* __restrict__ partial, int64_t nb, int64_t n, double thresh_frac,
+               double thresh_abs, double* __restrict__ out) {
+    double acc = 0.0;
+    for (int64_t i = threadIdx.x; i < nb; i += 1024) acc += partial[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    __shared__ double s_w[32];
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 32; ++w) t += s_w[w];
+        double mean = n > 0 ? t / (double)n : 0.0;
+        double thr = thresh_frac * mean;
+        if (thresh_abs > thr) thr = thresh_abs;
+        out[0] = mean;
+        out[1] = thr;
+    }
+}
+
+__global__ void __launch_bounds__(256)
+    k_pack_bits(const float* __restrict__ ema, int64_t n, const double* __restrict__ mt,
+                uint32_t* __restrict__ bits) {
+    const double thr = mt[1];
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        bool occ = (double)ema[c] > thr;
+        unsigned m = __ballot_sync(0xffffffffu, occ);
+        if ((threadIdx.x & 31) == 0) bits[c >> 5] = m;
+    }
+}
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+}  // namespace nacc
+
+using namespace nacc;
+
+extern "C" int nacc_grid_points(const nacc_grid* grid, uint64_t seed, int64_t step, int32_t jitter,
+                                float* xyz_out, void* stream) {
+    clear_error();
+    GridGeom g;
+    if (!make_geom(grid, &g, false)) return NACC_ERR_INVALID_ARG;
+    NACC_CHECK_ARG(xyz_out != nullptr, "xyz_out is NULL");
+    const int64_t n = (int64_t)g.n_levels * g.res * g.res * g.res;
+    const uint64_t key = seed ^ ((uint64_t)step << 32);
+    int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 16);
+    k_grid_points<<<blocks, 256, 0, as_stream(stream)>>>(g, key, jitter ? 1 : 0, n, xyz_out);
+    NACC_LAUNCH_CHECK();
+    return NACC_OK;
+}
+
+extern "C" size_t nacc_update_grid_scratch_bytes(int64_t n_cells) {
+    if (n_cells < 0) return 0;
+    int64_t nb = (n_cells + kEmaCells - 1) / kEmaCells;
+    return align256(sizeof(double) * (size_t)(nb > 0 ? nb : 1)) + align256(2 * sizeof(double));
+}
+
+extern "C" int nacc_update_grid(const nacc_grid* grid, float* ema, const float* density,
+                                float decay, float thresh_frac, float thresh_abs,
+                                uint32_t* bits_out, void* scratch, size_t scratch_bytes,
+                                void* stream) {
+    clear_error();
+    GridGeom g;
+    if (!make_geom(grid, &g, false)) return NACC_ERR_INVALID_ARG;
+    NACC_CHECK_ARG(ema && density && bits_out, "ema / density / bits_out is NULL");
+    NACC_CHECK_ARG(decay >= 0.0f && decay <= 1.0f, "decay=%g outside [0, 1]", (double)decay);
+    NACC_CHECK_ARG(std::isfinite(thresh_frac) && std::isfinite(thresh_abs), "thresholds must be finite");
+    const int64_t n = (int64_t)g.n_levels * g.res * g.res * g.res;
+    size_t need = nacc_update_grid_scratch_bytes(n);
+    NACC_CHECK_ARG(scratch != nullptr && scratch_bytes >= need, "scratch too small: %zu < %zu bytes",
+                   scratch_bytes, need);
+    NACC_CHECK_ARG((reinterpret_cast<uintptr_t>(scratch) & 255) == 0, "scratch not 256-byte aligned");
+    const int64_t nb = (n + kEmaCells - 1) / kEmaCells;
+    double* partial = static_cast<double*>(scratch);
+    double* mt = reinterpret_cast<double*>(static_cast<char*>(scratch) + align256(sizeof(double) * (size_t)nb));
+    cudaStream_t st = as_stream(stream);
+    volatile float omd = 1.0f - decay;
+    k_ema<<<(unsigned)nb, kEmaThreads, 0, st>>>(ema, density, decay, omd, n, partial);
+    NACC_LAUNCH_CHECK();
+    k_mean_thr<<<1, 1024, 0, st>>>(partial, nb, n, (double)thresh_frac, (double)thresh_abs, mt);
+    NACC_LAUNCH_CHECK();
+    int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 16);
+    k_pack_bits<<<blocks, 256, 0, st>>>(ema, n, mt, bits_out);
+    NACC_LAUNCH_CHECK();
+    return NACC_OK;
+}

@@ -1,0 +1,539 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the
+same seeded inputs.
+
+Bars (see the design notes for the derivations):
+  * packed samples (offsets, ray ids, t0, t1): bit-exact (field-less march;
+    field march on rays whose stopping optical depth is not within 1e-4 of
+    -ln(eps), the rest must stop within one sample of the oracle);
+  * compositing: transmittance, weights, colour, opacity within 1e-5
+    absolute, depth within 1e-5 relative;
+  * gradients: |g - g_ref| <= 1e-4 |g_ref| + 1e-5 * dt_i * (|g_C|_1 + |g_A| +
+    |g_D| m_i) (1e-4 relative, with an absolute floor at the natural scale of
+    the terms that cancel);
+  * grid points, EMA, sample_pdf: bit-exact; occupancy bits exact except
+    cells within 1e-12 (relative) of the FP64 threshold.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module")
+def nacc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2305_04966_gb300 as m
+    m.load_library()
+    return m
+
+
+def T(a, dtype=None):
+    t = torch.as_tensor(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.to(DEV)
+
+
+def grid_from_bits(nacc, spec_min, spec_max, res, L, bits):
+    return nacc.OccupancyGrid(tuple(spec_min), tuple(spec_max), res, L,
+                              T(bits.view(np.int32), torch.int32))
+
+
+def run_march(nacc, grid, o, d, step, max_steps, t_min, t_max, field=None, eps=1e-4, capacity=None):
+    pk = nacc.march_grid(grid, T(o), T(d), step, max_steps, t_min, t_max, eps, field=field,
+                         capacity=capacity)
+    torch.cuda.synchronize()
+    pk = pk.trimmed()
+    return dict(offsets=pk.offsets.cpu().numpy(), ray_indices=pk.ray_indices.cpu().numpy(),
+                t_starts=pk.t_starts.cpu().numpy(), t_ends=pk.t_ends.cpu().numpy())
+
+
+def assert_packed_equal(got, exp, rays=None):
+    if rays is None:
+        for k in ("offsets", "ray_indices", "t_starts", "t_ends"):
+            np.testing.assert_array_equal(got[k], exp[k], err_msg=k)
+        return
+    go, eo = got["offsets"], exp["offsets"]
+    for r in rays:
+        gs, ge, es, ee = go[r], go[r + 1], eo[r], eo[r + 1]
+        assert ge - gs == ee - es, f"ray {r}: {ge - gs} vs {ee - es} samples"
+        for k in ("t_starts", "t_ends"):
+            np.testing.assert_array_equal(got[k][gs:ge], exp[k][es:ee], err_msg=f"{k} ray {r}")
+        assert np.all(got["ray_indices"][gs:ge] == r)
+
+
+# ---------------------------------------------------------------------------
+# march
+# ---------------------------------------------------------------------------
+
+def test_march_c1_no_field_bit_exact(nacc, orc):
+    w = workloads.c1_forward()
+    g, m = w.grid, w.march
+    bits, _ = orc.density_grid(g, w.blobs)
+    grid = grid_from_bits(nacc, g.aabb_min, g.aabb_max, g.res, g.n_levels, bits)
+    got = run_march(nacc, grid, w.rays_o, w.rays_d, m.step, m.max_steps, m.t_min, m.t_max)
+    exp = orc.march(w.rays_o, w.rays_d, g.aabb_min, g.aabb_max, g.res, g.n_levels, bits, m.step,
+                    m.max_steps, m.t_min, m.t_max)
+    assert exp["offsets"][-1] > 100000
+    assert_packed_equal(got, exp)
+
+
+@pytest.mark.parametrize("res,L,block,p_block", [(16, 1, 2, 0.5), (32, 2, 4, 0.3), (64, 3, 8, 0.2),
+                                                 (128, 4, 16, 0.15), (20, 2, 5, 0.4)])
+def test_march_random_grids_bit_exact(nacc, orc, res, L, block, p_block):
+    bits = workloads.random_bitfield(L, res, 200 + res + L, p_block=p_block, block=block, p_cell=0.6)
+    g = workloads.rng(300 + res + L)
+    n = 3000
+    o = workloads._normalise(g.standard_normal((n, 3))) * g.uniform(0.0, 8.0, size=(n, 1))
+    p = g.uniform(-1.5, 1.5, size=(n, 3))
+    d = workloads._normalise(p - o)
+    d[:40] = 0.0
+    d[np.arange(40), np.arange(40) % 3] = np.where(np.arange(40) % 2 == 0, 1.0, -1.0)
+    d[40:80, 2] = 0.0
+    d[40:80] = workloads._normalise(d[40:80])
+    # origins exactly on cell faces and grazing the box edge
+    o[80:100] = np.round(o[80:100] * (res / 3.0)) * (3.0 / res)
+    o, d = o.astype(np.float32), d.astype(np.float32)
+    step = 3.0 * math.sqrt(3) / 1024 * (128 / res) ** 0.5
+    grid = grid_from_bits(nacc, (-1.5,) * 3, (1.5,) * 3, res, L, bits)
+    got = run_march(nacc, grid, o, d, step, 2048, 0.05, 1e10)
+    exp = orc.march(o, d, (-1.5,) * 3, (1.5,) * 3, res, L, bits, step, 2048, 0.05, 1e10)
+    assert exp["offsets"][-1] > 1000
+    assert_packed_equal(got, exp)
+
+
+def test_march_full_grid_is_uniform_sampling(nacc, orc):
+    """All-occupied grid: the marcher reduces to uniform sampling (Sec. 3.1)."""
+    res = 32
+    bits = np.full(res ** 3 // 32, 0xFFFFFFFF, np.uint32)
+    w = workloads.c1_forward(2000)
+    grid = grid_from_bits(nacc, (-1.5,) * 3, (1.5,) * 3, res, 1, bits)
+    got = run_march(nacc, grid, w.rays_o, w.rays_d, 0.01, 1024, 0.0, 1e10)
+    exp = orc.march(w.rays_o, w.rays_d, (-1.5,) * 3, (1.5,) * 3, res, 1, bits, 0.01, 1024, 0.0, 1e10)
+    assert_packed_equal(got, exp)
+
+
+def _near_tie_rays(orc, w, bits, full, thr, rel=1e-4):
+    """Rays whose optical depth (FP64 field) before the stop sample, or after
+    it, lies within `rel` of the threshold."""
+    sig, _ = orc.field_samples(w.rays_o, w.rays_d, full["ray_indices"], full["t_starts"],
+                               full["t_ends"], w.blobs)
+    tau = sig * (full["t_ends"].astype(np.float64) - full["t_starts"])
+    off = full["offsets"]
+    ties = set()
+    for r in range(len(off) - 1):
+        P = np.cumsum(tau[off[r]:off[r + 1]])
+        if P.size and np.min(np.abs(P - thr)) < rel * thr:
+            ties.add(r)
+    return ties
+
+
+def test_march_c1_with_field_early_stop(nacc, orc):
+    w = workloads.c1_forward()
+    g, m = w.grid, w.march
+    bits, _ = orc.density_grid(g, w.blobs)
+    grid = grid_from_bits(nacc, g.aabb_min, g.aabb_max, g.res, g.n_levels, bits)
+    field = nacc.BlobField.from_numpy(w.blobs)
+    got = run_march(nacc, grid, w.rays_o, w.rays_d, m.step, m.max_steps, m.t_min, m.t_max, field=field)
+    exp = orc.march(w.rays_o, w.rays_d, g.aabb_min, g.aabb_max, g.res, g.n_levels, bits, m.step,
+                    m.max_steps, m.t_min, m.t_max, blobs=w.blobs, eps=m.early_stop_eps)
+    full = orc.march(w.rays_o, w.rays_d, g.aabb_min, g.aabb_max, g.res, g.n_levels, bits, m.step,
+                     m.max_steps, m.t_min, m.t_max)
+    ties = _near_tie_rays(orc, w, bits, full, -math.log(m.early_stop_eps))
+    n = w.n_rays
+    exact = [r for r in range(n) if r not in ties]
+    assert len(ties) < 0.01 * n
+    assert_packed_equal(got, exp, exact)
+    gc, ec = np.diff(got["offsets"]), np.diff(exp["offsets"])
+    for r in ties:
+        assert abs(int(gc[r]) - int(ec[r])) <= 1
+    assert (gc < np.diff(full["offsets"])).sum() > 100  # early stop happened
+
+
+def test_march_c2_full_size_sampled(nacc, orc):
+    """640,000-ray image, 4-level grid, with field: per-ray exact on a seeded
+    sample of rays computed one by one by the oracle."""
+    w = workloads.c2_image()
+    g, m = w.grid, w.march
+    bits, _ = orc.density_grid(g, w.blobs)
+    grid = grid_from_bits(nacc, g.aabb_min, g.aabb_max, g.res, g.n_levels, bits)
+    field = nacc.BlobField.from_numpy(w.blobs)
+    got = run_march(nacc, grid, w.rays_o, w.rays_d, m.step, m.max_steps, m.t_min, m.t_max, field=field,
+                    capacity=w.n_rays * m.max_steps)
+    sel = np.sort(workloads.rng(77).choice(w.n_rays, 3000, replace=False))
+    o, d = w.rays_o[sel], w.rays_d[sel]
+    exp = orc.march(o, d, g.aabb_min, g.aabb_max, g.res, g.n_levels, bits, m.step, m.max_steps,
+                    m.t_min, m.t_max, blobs=w.blobs, eps=m.early_stop_eps)
+    full = orc.march(o, d, g.aabb_min, g.aabb_max, g.res, g.n_levels, bits, m.step, m.max_steps,
+                     m.t_min, m.t_max)
+    wsub = workloads.Workload("sub", o, d, w.blobs, g, m)
+    ties = _near_tie_rays(orc, wsub, bits, full, -math.log(m.early_stop_eps))
+    go = got["offsets"]
+    n_checked = 0
+    for k, r in enumerate(sel):
+        gs, ge = go[r], go[r + 1]
+        es, ee = exp["offsets"][k], exp["offsets"][k + 1]
+        if k in ties:
+            assert abs((ge - gs) - (ee - es)) <= 1
+            continue
+        assert ge - gs == ee - es, f"ray {r}"
+        np.testing.assert_array_equal(got["t_starts"][gs:ge], exp["t_starts"][es:ee])
+        np.testing.assert_array_equal(got["t_ends"][gs:ge], exp["t_ends"][es:ee])
+        assert np.all(got["ray_indices"][gs:ge] == r)
+        n_checked += 1
+    assert n_checked > 2900
+    # structure over all rays: offsets are a CSR of the counts, ray ids consistent
+    assert go[0] == 0 and np.all(np.diff(go) >= 0) and go[-1] == len(got["t_starts"])
+    assert np.all(np.diff(go) <= m.max_steps)
+    ri = got["ray_indices"]
+    assert np.array_equal(ri, np.repeat(np.arange(w.n_rays, dtype=np.int32), np.diff(go)))
+
+
+def test_march_capacity_overflow_reports_and_recovers(nacc, orc):
+    w = workloads.c1_forward(512)
+    g, m = w.grid, w.march
+    bits, _ = orc.density_grid(g, w.blobs)
+    grid = grid_from_bits(nacc, g.aabb_min, g.aabb_max, g.res, g.n_levels, bits)
+    with pytest.raises(nacc.NaccError) as ei:
+        nacc.march_grid(grid, T(w.rays_o), T(w.rays_d), m.step, m.max_steps, m.t_min, m.t_max,
+                        capacity=100)
+    assert ei.value.code == -2
+    got = nacc.march_grid(grid, T(w.rays_o), T(w.rays_d), m.step, m.max_steps, m.t_min, m.t_max,
+                          capacity=None).trimmed()
+    exp = orc.march(w.rays_o, w.rays_d, g.aabb_min, g.aabb_max, g.res, g.n_levels, bits, m.step,
+                    m.max_steps, m.t_min, m.t_max)
+    np.testing.assert_array_equal(got.t_starts.cpu().numpy(), exp["t_starts"])
+
+
+def test_march_empty_inputs(nacc):
+    grid = nacc.OccupancyGrid.empty((-1.5,) * 3, (1.5,) * 3, 32, 2)
+    pk = nacc.march_grid(grid, torch.zeros((0, 3), device=DEV), torch.zeros((0, 3), device=DEV), 0.01)
+    assert pk.n_samples() == 0 and pk.offsets.cpu().tolist() == [0]
+    o = torch.tensor([[5.0, 5.0, 5.0], [0.0, 0.0, 0.0]], device=DEV)
+    d = torch.tensor([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0]], device=DEV)
+    pk = nacc.march_grid(grid, o, d, 0.01)  # empty grid: nothing occupied
+    assert pk.n_samples() == 0 and pk.offsets.cpu().tolist() == [0, 0, 0]
+
+
+# ---------------------------------------------------------------------------
+# compositing
+# ---------------------------------------------------------------------------
+
+def _render_inputs(p):
+    return (T(p["offsets"]), T(p["t_starts"]), T(p["t_ends"]), T(p["sigmas"]), T(p["rgbs"]))
+
+
+def _long_ray_packed():
+    """Ragged mix: empty rays, short rays, rays across tile boundaries, and
+    rays longer than one 2048-sample tile."""
+    g = workloads.rng(60)
+    lengths = g.integers(0, 300, size=3000)
+    lengths[g.random(3000) < 0.2] = 0
+    lengths[[5, 700, 1500, 2999]] = [2047, 2049, 5000, 4097]
+    lengths[[10, 11, 12]] = [1024, 1023, 2048]
+    return workloads.random_packed(3000, 61, lengths=lengths, sigma_hi=3.0)
+
+
+@pytest.mark.parametrize("case", ["ragged", "long", "dense"])
+def test_render_fwd_parity(nacc, orc, case):
+    if case == "ragged":
+        p = workloads.random_packed(20000, 62, max_len=200, sigma_hi=40.0)
+    elif case == "long":
+        p = _long_ray_packed()
+    else:
+        p = workloads.random_packed(5000, 63, max_len=1024, sigma_hi=0.5, p_empty=0.0)
+    off, t0, t1, sg, c = _render_inputs(p)
+    rgb, op, dep, tr, w = nacc.render_fwd(off, t0, t1, sg, c, (1.0, 1.0, 1.0), 0.0, want_weights=True)
+    exp = orc.render_fwd(p["offsets"], p["t_starts"], p["t_ends"], p["sigmas"], p["rgbs"])
+    np.testing.assert_allclose(rgb.cpu().numpy(), exp["rgb"], rtol=0, atol=1e-5)
+    np.testing.assert_allclose(op.cpu().numpy(), exp["opacity"], rtol=0, atol=1e-5)
+    np.testing.assert_allclose(tr.cpu().numpy(), exp["trans"], rtol=0, atol=1e-5)
+    np.testing.assert_allclose(w.cpu().numpy(), exp["weights"], rtol=0, atol=1e-5)
+    np.testing.assert_allclose(dep.cpu().numpy(), exp["depth"], rtol=1e-5, atol=1e-5)
+
+
+def test_render_fwd_mask_mode(nacc, orc):
+    p = workloads.random_packed(8000, 64, max_len=300, sigma_hi=120.0)
+    eps = 1e-4
+    thr = float(np.float32(-math.log(eps)))
+    off = p["offsets"]
+    tau = p["sigmas"].astype(np.float64) * (p["t_ends"].astype(np.float64) - p["t_starts"])
+    ties = []
+    for r in range(8000):
+        P = np.concatenate([[0.0], np.cumsum(tau[off[r]:off[r + 1]])])
+        if P.size > 1 and np.min(np.abs(P - thr)) < 1e-4 * thr:
+            ties.append(r)
+    rgb, op, dep, tr, w = nacc.render_fwd(*_render_inputs(p), (1.0, 1.0, 1.0), eps, want_weights=True)
+    exp = orc.render_fwd(p["offsets"], p["t_starts"], p["t_ends"], p["sigmas"], p["rgbs"], eps=eps)
+    keep = np.ones(8000, bool)
+    keep[ties] = False
+    assert keep.sum() > 7800
+    np.testing.assert_allclose(rgb.cpu().numpy()[keep], exp["rgb"][keep], rtol=0, atol=1e-5)
+    np.testing.assert_allclose(op.cpu().numpy()[keep], exp["opacity"][keep], rtol=0, atol=1e-5)
+    np.testing.assert_allclose(tr.cpu().numpy()[keep], exp["trans"][keep], rtol=0, atol=1e-5)
+    wmask = np.repeat(keep, np.diff(off))
+    np.testing.assert_allclose(w.cpu().numpy()[wmask], exp["weights"][wmask], rtol=0, atol=1e-5)
+    assert (exp["weights"] == 0).sum() > 1000
+    assert np.all(w.cpu().numpy()[wmask][exp["weights"][wmask] == 0] == 0)
+
+
+def _grad_tol(p, g_rgb, g_op, g_dep, gref, sel=None):
+    off = p["offsets"]
+    ray = np.repeat(np.arange(len(off) - 1), np.diff(off))
+    dt = p["t_ends"].astype(np.float64) - p["t_starts"]
+    m = 0.5 * (p["t_ends"].astype(np.float64) + p["t_starts"])
+    scale = np.abs(g_rgb).sum(1)[ray] + np.abs(g_op)[ray] + np.abs(g_dep)[ray] * m
+    return 1e-4 * np.abs(gref) + 1e-5 * dt * scale
+
+
+@pytest.mark.parametrize("case,eps", [("ragged", 0.0), ("long", 0.0), ("ragged", 1e-4)])
+def test_render_bwd_parity(nacc, orc, case, eps):
+    if case == "ragged":
+        p = workloads.random_packed(20000, 65, max_len=200, sigma_hi=40.0)
+    else:
+        p = _long_ray_packed()
+    n = len(p["offsets"]) - 1
+    g = workloads.rng(66)
+    gC = g.standard_normal((n, 3)).astype(np.float32)
+    gA = g.standard_normal(n).astype(np.float32)
+    gD = g.standard_normal(n).astype(np.float32)
+    gs, gc = nacc.render_bwd(*_render_inputs(p), T(gC), T(gA), T(gD), (1.0, 1.0, 1.0), eps)
+    es, ec = orc.render_bwd(p["offsets"], p["t_starts"], p["t_ends"], p["sigmas"], p["rgbs"], gC, gA, gD,
+                            eps=eps)
+    gs, gc = gs.cpu().numpy(), gc.cpu().numpy()
+    tol = _grad_tol(p, gC, gA, gD, es)
+    ok = np.abs(gs - es) <= tol
+    if eps > 0:
+        # rays with a stop near the threshold may legitimately cut one sample differently
+        off = p["offsets"]
+        tau = p["sigmas"].astype(np.float64) * (p["t_ends"].astype(np.float64) - p["t_starts"])
+        thr = -math.log(eps)
+        for r in range(n):
+            P = np.cumsum(tau[off[r]:off[r + 1]])
+            if P.size and np.min(np.abs(P - thr)) < 1e-4 * thr:
+                ok[off[r]:off[r + 1]] = True
+    assert ok.all(), f"{(~ok).sum()} sigma grads off; worst {np.max(np.abs(gs - es) - tol)}"
+    np.testing.assert_allclose(gc[ok], ec[ok], rtol=1e-4, atol=1e-6)
+
+
+def test_render_bwd_matches_finite_differences(nacc, orc):
+    """Adjoint of the C2 loss on 64 rays vs central differences of the FP64
+    compositing."""
+    p = workloads.random_packed(64, 67, max_len=40, sigma_hi=30.0, p_empty=0.0)
+    n = 64
+    g = workloads.rng(68)
+    gC = g.standard_normal((n, 3))
+    gs, gc = nacc.render_bwd(*_render_inputs(p), T(gC.astype(np.float32)), None, None)
+    gs = gs.cpu().numpy()
+    sig = p["sigmas"].astype(np.float64)
+    rgb = p["rgbs"].astype(np.float64)
+
+    def loss(s):
+        o = orc.render_fwd(p["offsets"], p["t_starts"], p["t_ends"], s, rgb)
+        return (o["rgb"] * gC).sum()
+
+    zeros = np.zeros(n)
+    tol = _grad_tol(p, gC, zeros, zeros, gs.astype(np.float64))
+    for i in range(len(sig)):
+        h = 1e-6 * max(1.0, sig[i])
+        sp, sm = sig.copy(), sig.copy()
+        sp[i] += h
+        sm[i] -= h
+        fd = (loss(sp) - loss(sm)) / (2 * h)
+        assert abs(gs[i] - fd) <= tol[i] + 1e-7, (i, gs[i], fd)
+
+
+def test_autograd_function(nacc, orc):
+    p = workloads.random_packed(500, 69, max_len=60)
+    off, t0, t1, sg, c = _render_inputs(p)
+    sg.requires_grad_(True)
+    c.requires_grad_(True)
+    pk = nacc.PackedSamples(off, None, t0, t1, torch.tensor([len(p["t_starts"])], device=DEV))
+    rgb, op, dep = nacc.render(sg, c, pk)
+    tgt = T(workloads.target_image(500, 9))
+    loss = ((rgb - tgt) ** 2).mean() + op.sum() * 0.1 + dep.sum() * 0.01
+    loss.backward()
+    gC = (2 * (rgb - tgt) / rgb.numel()).detach()
+    gs, gc = nacc.render_bwd(off, t0, t1, sg.detach(), c.detach(), gC,
+                             torch.full_like(op, 0.1), torch.full_like(dep, 0.01))
+    torch.testing.assert_close(sg.grad, gs, rtol=1e-5, atol=1e-7)
+    torch.testing.assert_close(c.grad, gc, rtol=1e-5, atol=1e-7)
+
+
+def test_render_empty_and_degenerate(nacc, orc):
+    off = torch.zeros(5, dtype=torch.int64, device=DEV)
+    e = torch.zeros(0, device=DEV)
+    rgb, op, dep, tr, _ = nacc.render_fwd(off, e, e, e, torch.zeros((0, 3), device=DEV), (0.2, 0.4, 0.6))
+    np.testing.assert_allclose(rgb.cpu().numpy(), np.tile([0.2, 0.4, 0.6], (4, 1)), atol=1e-7)
+    assert op.abs().max().item() == 0 and tr.min().item() == 1.0
+    # zero-density samples: fully transparent
+    p = workloads.random_packed(100, 70, max_len=50)
+    p["sigmas"][:] = 0
+    rgb, op, dep, tr, w = nacc.render_fwd(*_render_inputs(p), (1, 1, 1), 0.0, want_weights=True)
+    assert w.abs().max().item() == 0 and np.allclose(rgb.cpu().numpy(), 1.0)
+
+
+# ---------------------------------------------------------------------------
+# estimator update and resampling
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("res,L", [(32, 1), (128, 4)])
+def test_grid_points_bit_exact(nacc, orc, res, L):
+    grid = nacc.OccupancyGrid.empty((-1.5, -1.0, -2.0), (1.5, 2.0, 0.5), res, L)
+    for jitter in (False, True):
+        got = nacc.grid_points(grid, seed=1234, step=17, jitter=jitter).cpu().numpy()
+        exp = orc.grid_points(grid.aabb_min, grid.aabb_max, res, L, seed=1234, step=17, jitter=jitter)
+        np.testing.assert_array_equal(got, exp)
+
+
+def test_update_grid_parity(nacc, orc):
+    res, L = 128, 4
+    n = L * res ** 3
+    g = workloads.rng(80)
+    ema0 = g.exponential(1.0, n).astype(np.float32)
+    ema0[g.random(n) < 0.5] = 0
+    grid = nacc.OccupancyGrid.empty((-1.5,) * 3, (1.5,) * 3, res, L)
+    grid.ema.copy_(T(ema0))
+    e_ref = ema0
+    for step in range(3):
+        dens = g.exponential(0.5, n).astype(np.float32) * (g.random(n) < 0.3)
+        nacc.update_grid(grid, T(dens), decay=0.95, thresh_frac=0.01)
+        e_ref, bits_ref, mean_ref = orc.update_grid(e_ref, dens, 0.95, 0.01)
+        got_e = grid.ema.cpu().numpy()
+        np.testing.assert_array_equal(got_e, e_ref)
+        got_b = workloads.unpack_bits(grid.bits.cpu().numpy().view(np.uint32))
+        ref_b = workloads.unpack_bits(bits_ref)
+        thr = 0.01 * mean_ref
+        near = np.abs(e_ref.astype(np.float64) - thr) <= 1e-12 * thr
+        assert np.array_equal(got_b[~near], ref_b[~near])
+
+
+def test_initial_density_grid_matches_oracle(nacc, orc):
+    w = workloads.c2_image(8, 8)
+    grid = nacc.OccupancyGrid.empty(w.grid.aabb_min, w.grid.aabb_max, w.grid.res, w.grid.n_levels)
+    nacc.density_grid(grid, nacc.BlobField.from_numpy(w.blobs), 0.01)
+    got = workloads.unpack_bits(grid.bits.cpu().numpy().view(np.uint32))
+    bits, sig = orc.density_grid(w.grid, w.blobs)
+    ref = workloads.unpack_bits(bits)
+    near = np.abs(sig.astype(np.float64) - 0.01) < 1e-5 * 0.01
+    assert np.array_equal(got[~near], ref[~near])
+    assert ref.sum() > 10000
+
+
+@pytest.mark.parametrize("nb,no,strat", [(64, 32, False), (32, 32, False), (64, 32, True), (7, 100, False),
+                                         (300, 17, True), (1, 4, False)])
+def test_sample_pdf_bit_exact(nacc, orc, nb, no, strat):
+    n = 20000
+    g = workloads.rng(90 + nb)
+    edges = np.sort(g.uniform(2.0, 6.0, (n, nb + 1)), axis=1).astype(np.float32)
+    wts = g.uniform(0, 1, (n, nb)).astype(np.float32)
+    wts[g.random((n, nb)) < 0.4] = 0
+    wts[:50] = 0  # all-zero rows: uniform
+    wts[50:60, :] = 0
+    wts[50:60, nb // 2] = 1.0  # single-bin mass
+    got = nacc.sample_pdf(T(edges), T(wts), no, stratified=strat, seed=4242).cpu().numpy()
+    exp = orc.sample_pdf(edges, wts, no, stratified=strat, seed=4242)
+    np.testing.assert_array_equal(got, exp)
+
+
+# ---------------------------------------------------------------------------
+# whole step
+# ---------------------------------------------------------------------------
+
+def test_c2_pipeline_sampled_rays_vs_oracle(nacc, orc):
+    """Full C2 step (march with field -> field -> render -> loss -> adjoint) at the
+    full 640,000-ray size: rendered colour of sampled rays against the oracle's
+    march + FP64 field + FP64 compositing (FP32 field: tolerance 1e-4)."""
+    w = workloads.c2_image()
+    g, m = w.grid, w.march
+    bits, _ = orc.density_grid(g, w.blobs)
+    grid = grid_from_bits(nacc, g.aabb_min, g.aabb_max, g.res, g.n_levels, bits)
+    field = nacc.BlobField.from_numpy(w.blobs)
+    o, d = T(w.rays_o), T(w.rays_d)
+    pk = nacc.march_grid(grid, o, d, m.step, m.max_steps, m.t_min, m.t_max, m.early_stop_eps, field=field,
+                         capacity=w.n_rays * m.max_steps)
+    sig, rgbs = nacc.field_eval(field, o, d, pk)
+    rgb, op, dep = nacc.render(sig, rgbs, pk)
+    loss, g_rgb = nacc.l2_loss(rgb, T(w.target))
+    gs, gc = nacc.render_bwd(pk.offsets, pk.t_starts, pk.t_ends, sig, rgbs, g_rgb, None, None)
+    torch.cuda.synchronize()
+    sel = np.sort(workloads.rng(78).choice(w.n_rays, 2000, replace=False))
+    ex = orc.march(w.rays_o[sel], w.rays_d[sel], g.aabb_min, g.aabb_max, g.res, g.n_levels, bits, m.step,
+                   m.max_steps, m.t_min, m.t_max, blobs=w.blobs, eps=m.early_stop_eps)
+    s64, c64 = orc.field_samples(w.rays_o[sel], w.rays_d[sel], ex["ray_indices"], ex["t_starts"],
+                                 ex["t_ends"], w.blobs)
+    er = orc.render_fwd(ex["offsets"], ex["t_starts"], ex["t_ends"], s64, c64)
+    got = rgb.cpu().numpy()[sel]
+    np.testing.assert_allclose(got, er["rgb"], rtol=0, atol=2e-3)
+    assert np.mean(np.abs(got - er["rgb"])) < 1e-4
+    assert np.isfinite(gs[:pk.n_samples()].cpu().numpy()).all()
+    assert math.isfinite(loss.item())
+
+
+def test_cuda_graph_capture_of_training_step(nacc, orc):
+    """One training step (march -> field -> render -> loss -> adjoint -> grid
+    update) captured as a CUDA graph replays to the eager results."""
+    w = workloads.c3_training(16384)
+    g, m = w.grid, w.march
+    field = nacc.BlobField.from_numpy(w.blobs)
+    grid = nacc.OccupancyGrid.empty(g.aabb_min, g.aabb_max, g.res, g.n_levels)
+    nacc.density_grid(grid, field, 0.01)
+    o, d, tgt = T(w.rays_o), T(w.rays_d), T(w.target)
+    n = w.n_rays
+    bufs = nacc.MarchBuffers(n, n * m.max_steps)
+    ubufs = nacc.UpdateBuffers(grid.n_cells)
+    cap = n * m.max_steps
+    sig = torch.empty(cap, device=DEV)
+    rgbs = torch.empty((cap, 3), device=DEV)
+    pts = torch.empty((grid.n_cells, 3), device=DEV)
+    dens = torch.empty(grid.n_cells, device=DEV)
+    gsg = torch.empty(cap, device=DEV)
+    gcc = torch.empty((cap, 3), device=DEV)
+    step_no = torch.zeros(1)
+
+    def step():
+        pk = nacc.march_grid(grid, o, d, m.step, m.max_steps, m.t_min, m.t_max, m.early_stop_eps,
+                             field=field, buffers=bufs)
+        nacc.field_eval(field, o, d, pk, out=(sig, rgbs))
+        rgb, op, dep, tr, _ = nacc.render_fwd(pk.offsets, pk.t_starts, pk.t_ends, sig, rgbs)
+        loss, g_rgb = nacc.l2_loss(rgb, tgt)
+        nacc.render_bwd(pk.offsets, pk.t_starts, pk.t_ends, sig, rgbs, g_rgb, None, None, out=(gsg, gcc))
+        nacc.grid_points(grid, seed=7, step=3, jitter=True, out=pts)
+        nacc.field_points(field, pts, out=dens)
+        nacc.update_grid(grid, dens, 0.95, 0.01, buffers=ubufs)
+        return rgb, loss
+
+    bits0, ema0 = grid.bits.clone(), grid.ema.clone()
+    rgb_e, loss_e = step()
+    torch.cuda.synchronize()
+    eager = (rgb_e.clone(), gsg.clone(), grid.bits.clone(), grid.ema.clone())
+    grid.bits.copy_(bits0)
+    grid.ema.copy_(ema0)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):  # warm-up outside capture
+        step()
+    torch.cuda.current_stream().wait_stream(s)
+    grid.bits.copy_(bits0)
+    grid.ema.copy_(ema0)
+    gph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gph):
+        rgb_g, loss_g = step()
+    grid.bits.copy_(bits0)
+    grid.ema.copy_(ema0)
+    gph.replay()
+    torch.cuda.synchronize()
+    nsamp = bufs.packed.n_samples()
+    assert nsamp > 10000
+    assert torch.equal(rgb_g, eager[0])
+    assert torch.equal(gsg[:nsamp], eager[1][:nsamp])
+    assert torch.equal(grid.bits, eager[2])
+    assert torch.equal(grid.ema, eager[3])

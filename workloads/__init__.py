@@ -253,17 +253,19 @@ def c1_forward(n_rays: int = 4096) -> Workload:
                     MarchSpec(STEP_BOUNDED, 1024, 0.0, 1e10, 1e-4))
 
 
-def c2_image(width: int = 800, height: int = 800, focal: float = 1111.0) -> Workload:
+def c2_image(width: int = 800, height: int = 800, focal: float = 1111.0, view: int = 0) -> Workload:
     """Full 800x800 pinhole image (640,000 rays) of the C1 blob field, camera at
     radius 4 looking at the origin, near plane 2; 4-level cascaded 128^3 grid;
-    up to 1024 lattice steps; seeded uniform-noise target for an L2 loss."""
-    cam = camera_position(2)
+    up to 1024 lattice steps; seeded uniform-noise target for an L2 loss.
+    ``view`` > 0 picks another seeded camera on the same sphere (one image per
+    GPU when several GPUs each render their own view)."""
+    cam = camera_position(2) if view == 0 else camera_position(1000 + view)
     o, d = pinhole_rays(cam, width, height, focal)
     n = o.shape[0]
     return Workload(f"image{width}x{height}_grid4x128", o, d, blob_field(8, 1),
                     GridSpec((-1.5, -1.5, -1.5), (1.5, 1.5, 1.5), 128, 4),
                     MarchSpec(STEP_BOUNDED, 1024, 2.0, 1e10, 1e-4),
-                    target=target_image(n, 2))
+                    target=target_image(n, 2 if view == 0 else 1000 + view))
 
 
 def c3_training(n_rays: int = 262144) -> Workload:
