@@ -164,6 +164,33 @@ int nacc_update_grid(const nacc_grid* grid, float* ema, const float* density, fl
                      size_t scratch_bytes, void* stream);
 
 /*
+ * Allocation-free variant of nacc_update_grid (the paper has no counterpart;
+ * this is a property of this library's interface).  Same arguments, same
+ * arithmetic and same results as nacc_update_grid, but the temporary FP64
+ * partial sums live in an array inside the library instead of a caller
+ * buffer, so the call performs no device allocation of any kind.  Intended
+ * for callers that cannot allocate on the path that refreshes the grid,
+ * e.g. code hosted in an application that owns the whole device memory
+ * budget and forbids allocations after start-up, or a latency-critical
+ * thread that must not pay for the synchronisation an allocation can imply.
+ *  - Limit: n_levels*res^3 <= 134,217,728 cells (2^27, e.g. 8 levels of
+ *    256^3); larger grids are rejected with NACC_ERR_INVALID_ARG and a
+ *    message naming the limit.
+ *  - The array (512 KiB + 16 B) is held by every GPU that loads the library,
+ *    until the process exits.
+ *  - The first call on each device looks up the array's device address for
+ *    that device (with the device current); make that first call before any
+ *    stream capture on that device.
+ *  - All calls share the one array and it keeps the last call's contents;
+ *    every element a call reads is written earlier in the same call.  Calls
+ *    whose GPU work overlaps (e.g. on two streams) race on the array: order
+ *    them on one stream.
+ */
+int nacc_update_grid_noalloc(const nacc_grid* grid, float* ema, const float* density,
+                             float decay, float thresh_frac, float thresh_abs,
+                             uint32_t* bits_out, void* stream);
+
+/*
  * Inverse transform sampling from a piecewise-constant PDF (Eq. 1), with
  * the CDF read as 1 - T (Eq. 3; Table 1 "PDF Approaches").  Per ray, bins
  * [e_j, e_{j+1}] (j < n_bins) carry weights w_j >= 0 (FP32 throughout):

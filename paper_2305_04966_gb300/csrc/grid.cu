@@ -5,6 +5,8 @@
 // Three kernels: EMA + per-block FP64 partial sums, a one-block reduction to
 // the FP64 mean and threshold, and a warp-ballot bit packer (32 cells = one
 // word per warp).  No atomics: the mean is deterministic.
+#include <mutex>
+
 #include "nacc_internal.cuh"
 
 namespace nacc {
@@ -140,6 +142,95 @@ extern "C" int nacc_update_grid(const nacc_grid* grid, float* ema, const float* 
     const int64_t nb = (n + kEmaCells - 1) / kEmaCells;
     double* partial = static_cast<double*>(scratch);
     double* mt = reinterpret_cast<double*>(static_cast<char*>(scratch) + align256(sizeof(double) * (size_t)nb));
+    cudaStream_t st = as_stream(stream);
+    volatile float omd = 1.0f - decay;
+    k_ema<<<(unsigned)nb, kEmaThreads, 0, st>>>(ema, density, decay, omd, n, partial);
+    NACC_LAUNCH_CHECK();
+    k_mean_thr<<<1, 1024, 0, st>>>(partial, nb, n, (double)thresh_frac, (double)thresh_abs, mt);
+    NACC_LAUNCH_CHECK();
+    int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 16);
+    k_pack_bits<<<blocks, 256, 0, st>>>(ema, n, mt, bits_out);
+    NACC_LAUNCH_CHECK();
+    return NACC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// nacc_update_grid_noalloc: the same update with library-owned scratch.
+//
+// For callers that cannot call cudaMalloc (or any allocator) on the path that
+// refreshes the grid -- for example code embedded in a host application that
+// owns the whole device memory budget and forbids device allocations after
+// start-up, or a latency-critical thread that must not pay for the implicit
+// synchronisation an allocation can cause.  The FP64 partial sums and the
+// (mean, threshold) pair live in one file-scope device array instead of a
+// caller buffer.  Every GPU that loads this library holds the array until
+// the process exits.
+// ---------------------------------------------------------------------------
+
+namespace nacc {
+namespace {
+constexpr int64_t kNoAllocMaxCells = int64_t(1) << 27;             // 134,217,728 cells
+constexpr int64_t kNoAllocMaxBlocks = kNoAllocMaxCells / kEmaCells;  // 65,536 partial sums
+constexpr int kNoAllocMaxDevices = 64;
+}  // namespace
+}  // namespace nacc
+
+// 65,536 FP64 partial sums + mean + threshold: 512 KiB + 16 B per device.
+static __device__ __align__(256) double nacc_update_noalloc_scratch[nacc::kNoAllocMaxBlocks + 2];
+
+namespace nacc {
+namespace {
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the array on the current device, looked up once per
+// device (the host-side name of a __device__ variable is not a device address).
+int noalloc_scratch(double** out) {
+    int dev = 0;
+    NACC_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) {
+        set_error("device %d is beyond the %d devices this entry point supports", dev, kNoAllocMaxDevices);
+        return NACC_ERR_UNSUPPORTED;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, nacc_update_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr) {
+            set_error("cudaGetSymbolAddress(nacc_update_noalloc_scratch) failed on device %d: %s", dev,
+                      cudaGetErrorString(e));
+            return NACC_ERR_CUDA;
+        }
+        g_noalloc_ptr[dev] = static_cast<double*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return NACC_OK;
+}
+}  // namespace
+}  // namespace nacc
+
+extern "C" int nacc_update_grid_noalloc(const nacc_grid* grid, float* ema, const float* density,
+                                        float decay, float thresh_frac, float thresh_abs,
+                                        uint32_t* bits_out, void* stream) {
+    clear_error();
+    GridGeom g;
+    if (!make_geom(grid, &g, false)) return NACC_ERR_INVALID_ARG;
+    const int64_t n = (int64_t)g.n_levels * g.res * g.res * g.res;
+    NACC_CHECK_ARG(n <= kNoAllocMaxCells,
+                   "grid has %lld cells; nacc_update_grid_noalloc supports at most %lld "
+                   "(use nacc_update_grid with caller scratch)",
+                   (long long)n, (long long)kNoAllocMaxCells);
+    NACC_CHECK_ARG(ema && density && bits_out, "ema / density / bits_out is NULL");
+    NACC_CHECK_ARG(decay >= 0.0f && decay <= 1.0f, "decay=%g outside [0, 1]", (double)decay);
+    NACC_CHECK_ARG(std::isfinite(thresh_frac) && std::isfinite(thresh_abs), "thresholds must be finite");
+    double* scratch = nullptr;
+    int rc = noalloc_scratch(&scratch);
+    if (rc != NACC_OK) return rc;
+    // k_ema writes every partial sum it uses and k_mean_thr writes (mean,
+    // threshold) before k_pack_bits reads them, so nothing needs clearing.
+    double* partial = scratch;
+    double* mt = scratch + kNoAllocMaxBlocks;
+    const int64_t nb = (n + kEmaCells - 1) / kEmaCells;
     cudaStream_t st = as_stream(stream);
     volatile float omd = 1.0f - decay;
     k_ema<<<(unsigned)nb, kEmaThreads, 0, st>>>(ema, density, decay, omd, n, partial);
