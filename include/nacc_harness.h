@@ -42,6 +42,24 @@ int nacc_harness_field_points(int64_t n, const float* xyz, const nacc_blob_field
 int nacc_harness_l2_loss(int64_t n, const float* rgb, const float* target, float* g_rgb,
                          float* loss, void* stream);
 
+/*
+ * Device status of the bounded waits inside the library's streaming kernels
+ * (render_fwd / render_bwd).  Every wait on an mbarrier gives up after 2 s of
+ * GPU wall time; the kernel then records the expiry in a device status word
+ * and returns instead of hanging.  This call synchronises `stream`, reads and
+ * clears that word, and writes NACC_OK or NACC_ERR_TIMEOUT to *status_out
+ * [host].  Returns NACC_OK unless a CUDA call failed.
+ */
+int nacc_device_status(void* stream, int32_t* status_out);
+
+/*
+ * Diagnostics: launches one tiny kernel that waits, with the library's
+ * bounded-wait routine, on an mbarrier nothing will ever arrive on, giving up
+ * after limit_ns nanoseconds (0 < limit_ns <= 1e8).  The expiry is reported
+ * through nacc_device_status; the context stays usable.
+ */
+int nacc_selftest_wait_timeout(int64_t limit_ns, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -124,3 +124,14 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(_abi, "lib_path", lambda: str(tmp_path / "absent.so"))
     with pytest.raises(RuntimeError, match="missing"):
         _abi.load()
+
+
+def test_render_rejects_misaligned_sample_arrays(lib):
+    from paper_2305_04966_gb300 import _abi
+    bg = (ctypes.c_float * 3)(1, 1, 1)
+    ok, bad = 1 << 20, (1 << 20) + 4
+    rc = lib.nacc_render_fwd(4, ok, bad, ok, ok, ok, bg, 0.0, ok, ok, ok, ok, None, None)
+    assert rc == _abi.NACC_ERR_INVALID_ARG and b"16-byte" in lib.nacc_last_error()
+    rc = lib.nacc_render_bwd(4, ok, ok, ok, ok, bad, bg, 0.0, None, None, None, ok, ok, None)
+    assert rc == _abi.NACC_ERR_INVALID_ARG
+    assert lib.nacc_selftest_wait_timeout(0, None) == _abi.NACC_ERR_INVALID_ARG

@@ -537,3 +537,21 @@ def test_cuda_graph_capture_of_training_step(nacc, orc):
     assert torch.equal(gsg[:nsamp], eager[1][:nsamp])
     assert torch.equal(grid.bits, eager[2])
     assert torch.equal(grid.ema, eager[3])
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(nacc):
+    """A wait that can never be satisfied gives up, records NACC_ERR_TIMEOUT in
+    the device status word and returns; the next work on the GPU runs normally."""
+    import ctypes
+    from paper_2305_04966_gb300 import _abi
+    lib = nacc.load_library()
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    status = ctypes.c_int32(7)
+    assert lib.nacc_device_status(st, ctypes.byref(status)) == 0 and status.value == 0
+    assert lib.nacc_selftest_wait_timeout(2_000_000, st) == 0  # 2 ms
+    assert lib.nacc_device_status(st, ctypes.byref(status)) == 0
+    assert status.value == _abi.NACC_ERR_TIMEOUT
+    assert lib.nacc_device_status(st, ctypes.byref(status)) == 0 and status.value == 0  # cleared
+    p = workloads.random_packed(100, 71, max_len=30)
+    rgb, *_ = nacc.render_fwd(*_render_inputs(p))
+    assert torch.isfinite(rgb).all()
