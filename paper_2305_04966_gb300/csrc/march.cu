@@ -5,28 +5,42 @@
 // space), Sec. 4.2 "Sample as Interval" / "Packed Tensor" / "No Gradient
 // Filtering", Appendix B (step, resolution, threshold).
 //
-// One thread marches one ray.  The lattice arithmetic (t0, t1, midpoint,
-// position, level, cell) uses explicitly rounded FP32 intrinsics so that the
-// occupancy test of every lattice point is bit-identical to the dense-march
-// definition.  Empty cells are skipped with a DDA step that is conservative
-// by construction:
+// One thread marches one ray cell by cell.  At a lattice point the full
+// test runs (t0, t1, midpoint, position, level, cell, bit) in explicitly
+// rounded FP32 intrinsics, bit-identical to the dense-march definition; then
+// the exit of the cell is computed conservatively and every lattice point up
+// to it shares the cell, hence the occupancy:
 //   * along each axis the computed cell index is monotone in k (every
 //     rounding step is monotone), so inside a cell it can only change when
 //     the exact position crosses a face;
-//   * the skip target is the exit of the cell shrunk by 1/256 cell per face
-//     (and the entry of the next finer level's box grown by the same
-//     margin), far larger than the ~1e-5-cell error of the rounded position;
-//   * the resume index floor((t_exit - t_near)/dt) - 1 keeps 1.5 steps of
-//     slack on top.
-// So every skipped lattice point provably lies in the same empty cell and
-// the emitted set equals the dense march's.
+//   * the run ends at the exit of the cell shrunk by 1/256 cell per face (and
+//     at the entry of the next finer level's box grown by the same margin);
+//     a forward error analysis of the rounded position, face and exit time
+//     bounds their error by about 11u|o| + 15u|x|max (u = 2^-24), and the
+//     skip is taken only at levels where 16x that bound is below the margin
+//     (else the run is one point);
+//   * the run holds the lattice points whose rounded midpoint lies before the
+//     exit: k < floor(q + 1/2 - slack) with q = (t_exit - t_near)/dt and a
+//     slack of 1/64 step plus 2^-16 (|q| + |t_near|/dt) for the rounding of
+//     t0, t1, the midpoint and q (at least 16x their bound).
+// Empty runs are skipped; occupied runs are emitted point by point with only
+// their t0 / t1 arithmetic (plus the field for early termination), so the
+// emitted set equals the dense march's at a fraction of its cost.  With a
+// field the optical depth of the emitted samples is accumulated in lattice
+// order with one FP32 add per sample (the definition's order); the count
+// pass records where each ray stopped so the fill pass never evaluates the
+// field.  The fill pass buffers each lane's samples in shared memory and
+// flushes the 32 lanes' runs warp-cooperatively as coalesced stores.
 #include "nacc_internal.cuh"
 
 namespace nacc {
 namespace {
 
-constexpr int kMarchThreads = 128;
-constexpr float kSkipMargin = 1.0f / 256.0f;  // cells
+constexpr int kBlockThreads = 128;              // one ray per thread
+constexpr int kRaysPerBlock = kBlockThreads;    // rays per block-sum entry
+constexpr int kWarpsPerBlock = kBlockThreads / 32;
+constexpr int kBuf = 32;                        // lattice indices buffered per lane
+constexpr float kSkipMargin = 1.0f / 256.0f;    // cells
 
 struct MarchArgs {
     GridGeom g;
@@ -37,6 +51,9 @@ struct MarchArgs {
     int max_steps;
     float t_min, t_max;
     float thr;  // optical-depth threshold (+inf: no early stop)
+    float inv_step;  // 1/step, only for the conservative skip (never for lattice values)
+    int idx32;       // every flat cell index fits 32 bits
+    float skip_lim[NACC_MAX_LEVELS];  // skip allowed at level l iff max|o| <= skip_lim[l]
     nacc_blob_field field;
 };
 
@@ -51,11 +68,11 @@ __device__ __forceinline__ bool clip_ray(const Level& outer, const float o[3], c
             if (o[a] < outer.lmin[a] || o[a] > outer.lmax[a]) return false;
             continue;
         }
-        float inv = __fdiv_rn(1.0f, d[a]);
-        float ta = __fmul_rn(__fsub_rn(outer.lmin[a], o[a]), inv);
-        float tb = __fmul_rn(__fsub_rn(outer.lmax[a], o[a]), inv);
-        float lo = (ta < tb) ? ta : tb;
-        float hi = (ta < tb) ? tb : ta;
+        const float inv = __fdiv_rn(1.0f, d[a]);
+        const float ta = __fmul_rn(__fsub_rn(outer.lmin[a], o[a]), inv);
+        const float tb = __fmul_rn(__fsub_rn(outer.lmax[a], o[a]), inv);
+        const float lo = (ta < tb) ? ta : tb;
+        const float hi = (ta < tb) ? tb : ta;
         if (lo > near) near = lo;
         if (hi < far) far = hi;
     }
@@ -64,139 +81,216 @@ __device__ __forceinline__ bool clip_ray(const Level& outer, const float o[3], c
     return near < far;
 }
 
-// March one ray.  kCount: only count (and report the stop index); otherwise
-// write at out[base .. base+limit).  kField: early termination with the
-// staged blob field.  Returns the number of samples.
-template <bool kCount, bool kField>
-__device__ int march_ray(const MarchArgs& A, const BlobS* blobs, int64_t r, int kend, int limit,
-                         int64_t base, int32_t* ray_idx, float* t0s, float* t1s, int& kstop) {
-    float o[3], d[3];
+struct Ray {
+    float o[3], d[3], invd[3];
+    float tn, tf;
+    float omax;  // max |o|
+};
+
+// One lattice point: interval [t0, t1], midpoint position x, level l (L if
+// outside every level) and cell ic; returns the occupancy bit.
+__device__ __forceinline__ bool lattice_point(const MarchArgs& A, const Ray& R, int k, float& t0, float& t1,
+                                              float x[3], int& l, int ic[3]) {
+    t0 = __fadd_rn(R.tn, __fmul_rn((float)k, A.step));
+    t1 = __fadd_rn(t0, A.step);
+    const float tm = __fmul_rn(__fadd_rn(t0, t1), 0.5f);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) x[a] = __fadd_rn(R.o[a], __fmul_rn(R.d[a], tm));
+    const int L = A.g.n_levels;
+    for (l = 0; l < L; ++l) {
+        const Level& lv = A.g.lv[l];
+        if (x[0] >= lv.lmin[0] && x[0] <= lv.lmax[0] && x[1] >= lv.lmin[1] && x[1] <= lv.lmax[1] &&
+            x[2] >= lv.lmin[2] && x[2] <= lv.lmax[2])
+            break;
+    }
+    if (l == L) return false;
+    const Level& lv = A.g.lv[l];
+    const int res = A.g.res;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        o[a] = __ldg(&A.o[3 * r + a]);
-        d[a] = __ldg(&A.d[3 * r + a]);
+        const float u = __fmul_rn(__fsub_rn(x[a], lv.lmin[a]), lv.scale[a]);
+        const int c = (int)floorf(u);
+        ic[a] = c < 0 ? 0 : (c > res - 1 ? res - 1 : c);
     }
-    kstop = kend;
-    const int L = A.g.n_levels;
-    const int res = A.g.res;
-    float tn, tf;
-    if (!clip_ray(A.g.lv[L - 1], o, d, A.t_min, A.t_max, tn, tf)) return 0;
-    float invd[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) invd[a] = 1.0f / d[a];
+    if (A.idx32) {
+        const uint32_t r3 = (uint32_t)res * res * res;
+        const uint32_t idx = (uint32_t)l * r3 + ((uint32_t)ic[0] * res + ic[1]) * res + ic[2];
+        return (__ldg(&A.g.bits[idx >> 5]) >> (idx & 31)) & 1u;
+    }
     const uint64_t r3 = (uint64_t)res * res * res;
-    float tau = 0.0f;
-    int n = 0;
-    int k = 0;
-    while (k < kend) {
-        float t0 = __fadd_rn(tn, __fmul_rn((float)k, A.step));
-        if (!(t0 < tf)) break;
-        float t1 = __fadd_rn(t0, A.step);
-        float tm = __fmul_rn(__fadd_rn(t0, t1), 0.5f);
-        float x[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) x[a] = __fadd_rn(o[a], __fmul_rn(d[a], tm));
-        int l = 0;
-        for (; l < L; ++l) {
-            const Level& lv = A.g.lv[l];
-            if (x[0] >= lv.lmin[0] && x[0] <= lv.lmax[0] && x[1] >= lv.lmin[1] &&
-                x[1] <= lv.lmax[1] && x[2] >= lv.lmin[2] && x[2] <= lv.lmax[2])
-                break;
-        }
-        if (l == L) {  // outside every level (only possible at the ray's ends)
-            ++k;
-            continue;
-        }
-        const Level& lv = A.g.lv[l];
-        int ic[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            float u = __fmul_rn(__fsub_rn(x[a], lv.lmin[a]), lv.scale[a]);
-            int c = (int)floorf(u);
-            ic[a] = c < 0 ? 0 : (c > res - 1 ? res - 1 : c);
-        }
-        uint64_t idx = (uint64_t)l * r3 + ((uint64_t)ic[0] * res + ic[1]) * res + ic[2];
-        bool occ = (__ldg(&A.g.bits[idx >> 5]) >> (idx & 31)) & 1u;
-        if (occ) {
-            if (kField) {
-                if (tau > A.thr) {
-                    kstop = k;
-                    return n;
-                }
-            }
-            if (!kCount) {
-                if (n >= limit) return n;
-                if (ray_idx) ray_idx[base + n] = (int32_t)r;
-                t0s[base + n] = t0;
-                t1s[base + n] = t1;
-            }
-            ++n;
-            if (kField) {
-                float s = blob_sigma(blobs, A.field.n_blobs, x[0], x[1], x[2]);
-                tau = __fadd_rn(tau, __fmul_rn(s, __fsub_rn(t1, t0)));
-            }
-            ++k;
-        } else {
-            // Conservative exit of the empty cell (shrunk by kSkipMargin).
-            float ts = INFINITY;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                if (d[a] > 0.0f) {
-                    float face = lv.lmin[a] + ((float)ic[a] + (1.0f - kSkipMargin)) * lv.width[a];
-                    ts = fminf(ts, (face - o[a]) * invd[a]);
-                } else if (d[a] < 0.0f) {
-                    float face = lv.lmin[a] + ((float)ic[a] + kSkipMargin) * lv.width[a];
-                    ts = fminf(ts, (face - o[a]) * invd[a]);
-                }
-            }
-            if (l > 0) {  // do not skip into the next finer level's (grown) box
-                const Level& fl = A.g.lv[l - 1];
-                float tin = -INFINITY, tout = INFINITY;
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    float m = kSkipMargin * lv.width[a];
-                    float lo = fl.lmin[a] - m, hi = fl.lmax[a] + m;
-                    if (d[a] == 0.0f) {
-                        if (o[a] < lo || o[a] > hi) {
-                            tin = INFINITY;
-                            tout = -INFINITY;
-                        }
-                    } else {
-                        float ta = (lo - o[a]) * invd[a], tb = (hi - o[a]) * invd[a];
-                        tin = fmaxf(tin, fminf(ta, tb));
-                        tout = fminf(tout, fmaxf(ta, tb));
-                    }
-                }
-                if (tin <= tout && tout > tm) ts = fminf(ts, tin);
-            }
-            int kn = k + 1;
-            float q = (ts - tn) / A.step;
-            if (q > (float)(k + 2)) kn = (q < (float)kend) ? (int)floorf(q) - 1 : kend;
-            k = kn > k + 1 ? kn : k + 1;
-        }
-    }
-    return n;
+    const uint64_t idx = (uint64_t)l * r3 + ((uint64_t)ic[0] * res + ic[1]) * res + ic[2];
+    return (__ldg(&A.g.bits[idx >> 5]) >> (idx & 31)) & 1u;
 }
 
+// First lattice index that may leave the empty cell `ic` of level l holding
+// the point of lattice index k at midpoint tm (conservative, see the header).
+__device__ __forceinline__ int skip_target(const MarchArgs& A, const Ray& R, int k, float tm, int l,
+                                           const int ic[3], int kend) {
+    if (R.omax > A.skip_lim[l]) return k + 1;
+    const Level& lv = A.g.lv[l];
+    float ts = INFINITY;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (R.d[a] > 0.0f) {
+            const float face = lv.lmin[a] + ((float)ic[a] + (1.0f - kSkipMargin)) * lv.width[a];
+            ts = fminf(ts, (face - R.o[a]) * R.invd[a]);
+        } else if (R.d[a] < 0.0f) {
+            const float face = lv.lmin[a] + ((float)ic[a] + kSkipMargin) * lv.width[a];
+            ts = fminf(ts, (face - R.o[a]) * R.invd[a]);
+        }
+    }
+    if (l > 0) {  // do not skip into the next finer level's (grown) box
+        const Level& fl = A.g.lv[l - 1];
+        float tin = -INFINITY, tout = INFINITY;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float m = kSkipMargin * lv.width[a];
+            const float lo = fl.lmin[a] - m, hi = fl.lmax[a] + m;
+            if (R.d[a] == 0.0f) {
+                if (R.o[a] < lo || R.o[a] > hi) {
+                    tin = INFINITY;
+                    tout = -INFINITY;
+                }
+            } else {
+                const float ta = (lo - R.o[a]) * R.invd[a], tb = (hi - R.o[a]) * R.invd[a];
+                tin = fmaxf(tin, fminf(ta, tb));
+                tout = fminf(tout, fmaxf(ta, tb));
+            }
+        }
+        if (tin <= tout && tout > tm) ts = fminf(ts, tin);
+    }
+    const float q = (ts - R.tn) * A.inv_step;
+    const float slack = 0.015625f + 1.52587890625e-5f * (fabsf(R.tn) * A.inv_step + fminf(fabsf(q), 16777216.0f));
+    const float e = q + 0.5f - slack;  // exclusive run end (before flooring); NaN -> no skip
+    if (!(e >= (float)(k + 2))) return k + 1;
+    return e < (float)kend ? (int)floorf(e) : kend;
+}
+
+// Per-thread march state of one ray.
+struct Lane {
+    Ray R;
+    int k;        // next lattice index
+    int run_end;  // end (exclusive) of the current cell run
+    bool occ;     // the current run is occupied
+    bool done;
+    float tau;    // optical depth of the emitted samples (early stop)
+    int n;        // samples emitted
+};
+
+__device__ __forceinline__ bool lane_init(const MarchArgs& A, int64_t r, Lane& s) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        s.R.o[a] = __ldg(&A.o[3 * r + a]);
+        s.R.d[a] = __ldg(&A.d[3 * r + a]);
+        s.R.invd[a] = 1.0f / s.R.d[a];
+    }
+    s.R.omax = fmaxf(fabsf(s.R.o[0]), fmaxf(fabsf(s.R.o[1]), fabsf(s.R.o[2])));
+    s.k = 0;
+    s.run_end = 0;
+    s.occ = false;
+    s.tau = 0.0f;
+    s.n = 0;
+    s.done = !clip_ray(A.g.lv[A.g.n_levels - 1], s.R.o, s.R.d, A.t_min, A.t_max, s.R.tn, s.R.tf);
+    return !s.done;
+}
+
+// Advance the march of one ray: append the lattice indices of its occupied
+// points k < kend, in order, to buf[0..kBuf) (at most `limit` in total) and
+// return when the buffer is full or the ray is finished.
+__device__ void advance(const MarchArgs& A, Lane& s, int kend, int limit, int* buf, int& bn) {
+    const int L = A.g.n_levels;
+    while (!s.done && bn < kBuf) {
+        if (s.k >= s.run_end) {  // start a new cell run at s.k
+            if (s.k >= kend) {
+                s.done = true;
+                break;
+            }
+            float t0, t1, x[3];
+            int l, ic[3];
+            const bool occ = lattice_point(A, s.R, s.k, t0, t1, x, l, ic);
+            if (!(t0 < s.R.tf)) {
+                s.done = true;
+                break;
+            }
+            s.run_end =
+                l < L ? skip_target(A, s.R, s.k, __fmul_rn(__fadd_rn(t0, t1), 0.5f), l, ic, kend) : s.k + 1;
+            s.occ = occ;
+            if (!occ) {
+                s.k = s.run_end;
+                continue;
+            }
+        }
+        // lattice point s.k of an occupied run
+        const float t0 = __fadd_rn(s.R.tn, __fmul_rn((float)s.k, A.step));
+        if (!(t0 < s.R.tf)) {
+            s.done = true;
+            break;
+        }
+        buf[bn++] = s.k;
+        ++s.n;
+        ++s.k;
+        if (s.n >= limit) s.done = true;
+    }
+}
+
+// Count pass.  Each lane marches into its buffer; with a field the warp
+// then evaluates the density of the buffered samples together (converged)
+// and each lane folds them into its optical depth in lattice order, stopping
+// at the first sample whose depth before it exceeds the threshold.
 template <bool kField>
-__global__ void __launch_bounds__(kMarchThreads)
+__global__ void __launch_bounds__(kBlockThreads)
     k_march_count(MarchArgs A, int32_t* __restrict__ counts, int32_t* __restrict__ kstops,
                   long long* __restrict__ block_sums) {
     extern __shared__ BlobS s_blobs[];
-    if (kField) {
-        stage_blobs(s_blobs, A.field, false);
-        __syncthreads();
+    __shared__ int s_buf[kBlockThreads][kBuf + 1];
+    if (kField) stage_blobs(s_blobs, A.field, false);
+    __syncthreads();
+    const int64_t r = (int64_t)blockIdx.x * kBlockThreads + threadIdx.x;
+    Lane s;
+    s.done = true;
+    s.n = 0;
+    if (r < A.n) lane_init(A, r, s);
+    int* buf = s_buf[threadIdx.x];
+    int cnt = 0, kstop = A.max_steps;
+    float tau = 0.0f;
+    bool stopped = false;
+    while (true) {
+        int bn = 0;
+        if (!s.done && !stopped) advance(A, s, A.max_steps, 0x7fffffff, buf, bn);
+        if (!kField) {
+            cnt += bn;
+        } else {
+            __syncwarp();
+            int nmax = bn;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
+            for (int j = 0; j < nmax; ++j) {
+                if (j < bn && !stopped) {
+                    const int k = buf[j];
+                    const float t0 = __fadd_rn(s.R.tn, __fmul_rn((float)k, A.step));
+                    const float t1 = __fadd_rn(t0, A.step);
+                    if (tau > A.thr) {
+                        stopped = true;
+                        kstop = k;
+                    } else {
+                        const float tm = __fmul_rn(__fadd_rn(t0, t1), 0.5f);
+                        const float x0 = __fadd_rn(s.R.o[0], __fmul_rn(s.R.d[0], tm));
+                        const float x1 = __fadd_rn(s.R.o[1], __fmul_rn(s.R.d[1], tm));
+                        const float x2 = __fadd_rn(s.R.o[2], __fmul_rn(s.R.d[2], tm));
+                        const float sig = blob_sigma(s_blobs, A.field.n_blobs, x0, x1, x2);
+                        tau = __fadd_rn(tau, __fmul_rn(sig, __fsub_rn(t1, t0)));
+                        ++cnt;
+                    }
+                }
+            }
+        }
+        if (__all_sync(0xffffffffu, s.done || stopped)) break;
     }
-    int64_t r = (int64_t)blockIdx.x * kMarchThreads + threadIdx.x;
-    int cnt = 0;
     if (r < A.n) {
-        int ks = 0;
-        cnt = march_ray<true, kField>(A, s_blobs, r, A.max_steps, 0, 0, nullptr, nullptr, nullptr, ks);
         counts[r] = cnt;
-        kstops[r] = ks;
+        kstops[r] = kstop;
     }
-    // block total
-    __shared__ int s_w[kMarchThreads / 32];
+    __shared__ int s_w[kWarpsPerBlock];
     int v = cnt;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -205,7 +299,7 @@ __global__ void __launch_bounds__(kMarchThreads)
     if (threadIdx.x == 0) {
         long long t = 0;
 #pragma unroll
-        for (int w = 0; w < kMarchThreads / 32; ++w) t += s_w[w];
+        for (int w = 0; w < kWarpsPerBlock; ++w) t += s_w[w];
         block_sums[blockIdx.x] = t;
     }
 }
@@ -221,12 +315,12 @@ __global__ void __launch_bounds__(1024)
     if (threadIdx.x == 0) s_carry = 0;
     __syncthreads();
     for (int64_t base = 0; base < nb; base += 1024) {
-        int64_t i = base + threadIdx.x;
-        long long v = i < nb ? sums[i] : 0;
+        const int64_t i = base + threadIdx.x;
+        const long long v = i < nb ? sums[i] : 0;
         long long x = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            long long y = __shfl_up_sync(0xffffffffu, x, o);
+            const long long y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
         }
         if (lane == 31) s_w[wid] = x;
@@ -235,14 +329,14 @@ __global__ void __launch_bounds__(1024)
             long long w = s_w[lane];
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                long long y = __shfl_up_sync(0xffffffffu, w, o);
+                const long long y = __shfl_up_sync(0xffffffffu, w, o);
                 if (lane >= o) w += y;
             }
             s_w[lane] = w;  // inclusive over warps
         }
         __syncthreads();
-        long long carry = s_carry;
-        long long incl = x + (wid > 0 ? s_w[wid - 1] : 0);
+        const long long carry = s_carry;
+        const long long incl = x + (wid > 0 ? s_w[wid - 1] : 0);
         if (i < nb) sums[i] = carry + incl - v;
         __syncthreads();
         if (threadIdx.x == 1023) s_carry = carry + incl;
@@ -254,34 +348,61 @@ __global__ void __launch_bounds__(1024)
     }
 }
 
-__global__ void __launch_bounds__(kMarchThreads)
+__global__ void __launch_bounds__(kBlockThreads)
     k_march_fill(MarchArgs A, const int32_t* __restrict__ counts, const int32_t* __restrict__ kstops,
                  const long long* __restrict__ block_off, const int64_t* __restrict__ n_samples,
                  int64_t capacity, int64_t* __restrict__ offsets, int32_t* __restrict__ ray_idx,
                  float* __restrict__ t0s, float* __restrict__ t1s) {
-    int64_t r = (int64_t)blockIdx.x * kMarchThreads + threadIdx.x;
-    int cnt = r < A.n ? counts[r] : 0;
-    // block exclusive scan of counts
-    __shared__ int s_w[kMarchThreads / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t r = (int64_t)blockIdx.x * kBlockThreads + threadIdx.x;
+    const int cnt = r < A.n ? counts[r] : 0;
+    // block exclusive scan of the counts -> CSR offsets
+    __shared__ int s_w[kWarpsPerBlock];
     int x = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, x, o);
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
     }
     if (lane == 31) s_w[wid] = x;
     __syncthreads();
     int wbase = 0;
     for (int w = 0; w < wid; ++w) wbase += s_w[w];
-    long long off = block_off[blockIdx.x] + wbase + x - cnt;
-    if (r < A.n) {
-        offsets[r] = off;
-        bool fits = *n_samples <= capacity;
-        if (cnt > 0 && fits) {
-            int ks;
-            march_ray<false, false>(A, nullptr, r, kstops[r], cnt, off, ray_idx, t0s, t1s, ks);
+    long long pos = block_off[blockIdx.x] + wbase + x - cnt;
+    if (r < A.n) offsets[r] = pos;
+    if (*n_samples > capacity) return;  // overflow: offsets only (the whole grid agrees)
+    // per-lane buffers of lattice indices (row stride kBuf+1: conflict-free appends)
+    __shared__ int s_buf[kBlockThreads][kBuf + 1];
+    int* buf = s_buf[threadIdx.x];
+    Lane s;
+    s.done = true;
+    s.R.tn = 0.0f;
+    if (cnt > 0) lane_init(A, r, s);
+    const int kend = cnt > 0 ? kstops[r] : 0;
+    while (true) {
+        int bn = 0;
+        if (!s.done) advance(A, s, kend, cnt, buf, bn);
+        __syncwarp();
+        // flush every lane's buffered run with the whole warp (coalesced)
+        unsigned m = __ballot_sync(0xffffffffu, bn > 0);
+        while (m) {
+            const int j = __ffs(m) - 1;
+            m &= m - 1;
+            const int nj = __shfl_sync(0xffffffffu, bn, j);
+            const long long pj = __shfl_sync(0xffffffffu, pos, j);
+            const int rj = __shfl_sync(0xffffffffu, (int)r, j);
+            const float tnj = __shfl_sync(0xffffffffu, s.R.tn, j);
+            if (lane < nj) {
+                const int k = s_buf[(wid << 5) + j][lane];
+                const float t0 = __fadd_rn(tnj, __fmul_rn((float)k, A.step));
+                t0s[pj + lane] = t0;
+                t1s[pj + lane] = __fadd_rn(t0, A.step);
+                if (ray_idx) ray_idx[pj + lane] = rj;
+            }
         }
+        __syncwarp();
+        pos += bn;
+        if (__all_sync(0xffffffffu, s.done)) break;
     }
 }
 
@@ -294,7 +415,7 @@ using namespace nacc;
 
 extern "C" size_t nacc_march_scratch_bytes(int64_t n_rays) {
     if (n_rays < 0) return 0;
-    int64_t nb = (n_rays + kMarchThreads - 1) / kMarchThreads;
+    const int64_t nb = (n_rays + kRaysPerBlock - 1) / kRaysPerBlock;
     return align256(4 * (size_t)n_rays) * 2 + align256(8 * (size_t)(nb > 0 ? nb : 1));
 }
 
@@ -318,7 +439,7 @@ extern "C" int nacc_march_grid(const nacc_grid* grid, const float* rays_o, const
     NACC_CHECK_ARG(out->capacity == 0 || (out->t_starts && out->t_ends),
                    "out->t_starts / out->t_ends is NULL");
     NACC_CHECK_ARG(out->capacity < (int64_t(1) << 40), "capacity too large");
-    bool with_field = field != nullptr && field->n_blobs > 0 && params->early_stop_eps > 0.0f;
+    const bool with_field = field != nullptr && field->n_blobs > 0 && params->early_stop_eps > 0.0f;
     if (with_field) {
         NACC_CHECK_ARG(field->n_blobs <= kMaxBlobs, "n_blobs=%d > %d", field->n_blobs, kMaxBlobs);
         NACC_CHECK_ARG(field->mu && field->std && field->peak, "field mu/std/peak is NULL");
@@ -330,7 +451,7 @@ extern "C" int nacc_march_grid(const nacc_grid* grid, const float* rays_o, const
         return NACC_OK;
     }
     NACC_CHECK_ARG(rays_o && rays_d, "rays_o / rays_d is NULL");
-    size_t need = nacc_march_scratch_bytes(n_rays);
+    const size_t need = nacc_march_scratch_bytes(n_rays);
     NACC_CHECK_ARG(scratch != nullptr && scratch_bytes >= need,
                    "scratch too small: %zu < %zu bytes", scratch_bytes, need);
     NACC_CHECK_ARG((reinterpret_cast<uintptr_t>(scratch) & 255) == 0, "scratch not 256-byte aligned");
@@ -343,7 +464,21 @@ extern "C" int nacc_march_grid(const nacc_grid* grid, const float* rays_o, const
     A.t_min = params->t_min;
     A.t_max = params->t_max;
     A.thr = with_field ? tau_threshold(params->early_stop_eps) : INFINITY;
+    A.inv_step = 1.0f / params->step;
+    A.idx32 = ((uint64_t)A.g.n_levels * A.g.res * A.g.res * A.g.res) <= 0xffffffffull ? 1 : 0;
     A.field = with_field ? *field : nacc_blob_field{0, nullptr, nullptr, nullptr, nullptr};
+    for (int l = 0; l < NACC_MAX_LEVELS; ++l) {
+        A.skip_lim[l] = -1.0f;  // never skip
+        if (l >= A.g.n_levels) continue;
+        const Level& lv = A.g.lv[l];
+        double wmin = INFINITY, xmax = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            wmin = std::fmin(wmin, (double)lv.width[a]);
+            xmax = std::fmax(xmax, std::fmax(std::fabs((double)lv.lmin[a]), std::fabs((double)lv.lmax[a])));
+        }
+        const double lim = (wmin * kSkipMargin / (16.0 * 0x1p-24) - 15.0 * xmax) / 11.0;
+        if (lim > 0.0) A.skip_lim[l] = (float)lim;
+    }
 
     char* sp = static_cast<char*>(scratch);
     int32_t* counts = reinterpret_cast<int32_t*>(sp);
@@ -352,27 +487,26 @@ extern "C" int nacc_march_grid(const nacc_grid* grid, const float* rays_o, const
     sp += align256(4 * (size_t)n_rays);
     long long* bsums = reinterpret_cast<long long*>(sp);
 
-    int64_t nb = (n_rays + kMarchThreads - 1) / kMarchThreads;
+    const int64_t nb = (n_rays + kRaysPerBlock - 1) / kRaysPerBlock;
     NACC_CHECK_ARG(nb < (int64_t(1) << 31), "too many rays for one launch");
     if (with_field) {
-        size_t shm = sizeof(BlobS) * (size_t)A.field.n_blobs;
+        const size_t shm = sizeof(BlobS) * (size_t)A.field.n_blobs;
         if (shm > 48 * 1024)
             NACC_CUDA_TRY(cudaFuncSetAttribute(k_march_count<true>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-        k_march_count<true><<<(unsigned)nb, kMarchThreads, shm, st>>>(A, counts, kstops, bsums);
+        k_march_count<true><<<(unsigned)nb, kBlockThreads, shm, st>>>(A, counts, kstops, bsums);
     } else {
-        k_march_count<false><<<(unsigned)nb, kMarchThreads, 0, st>>>(A, counts, kstops, bsums);
+        k_march_count<false><<<(unsigned)nb, kBlockThreads, 0, st>>>(A, counts, kstops, bsums);
     }
     NACC_LAUNCH_CHECK();
     k_scan_block_sums<<<1, 1024, 0, st>>>(bsums, nb, out->offsets + n_rays, out->n_samples);
     NACC_LAUNCH_CHECK();
-    k_march_fill<<<(unsigned)nb, kMarchThreads, 0, st>>>(A, counts, kstops, bsums, out->n_samples,
-                                                          out->capacity, out->offsets,
-                                                          out->ray_indices, out->t_starts,
-                                                          out->t_ends);
+    k_march_fill<<<(unsigned)nb, kBlockThreads, 0, st>>>(A, counts, kstops, bsums, out->n_samples,
+                                                         out->capacity, out->offsets, out->ray_indices,
+                                                         out->t_starts, out->t_ends);
     NACC_LAUNCH_CHECK();
     // Overflow is impossible when the capacity covers every lattice point.
-    bool may_overflow = (double)out->capacity < (double)n_rays * (double)params->max_steps;
+    const bool may_overflow = (double)out->capacity < (double)n_rays * (double)params->max_steps;
     if (may_overflow) {
         int64_t total = 0;
         NACC_CUDA_TRY(cudaMemcpyAsync(&total, out->n_samples, sizeof(int64_t),
