@@ -40,6 +40,7 @@ constexpr int kBlockThreads = 128;              // one ray per thread
 constexpr int kRaysPerBlock = kBlockThreads;    // rays per block-sum entry
 constexpr int kWarpsPerBlock = kBlockThreads / 32;
 constexpr int kBuf = 32;                        // lattice indices buffered per lane
+constexpr int kRunSlots = 16;                   // recorded lattice runs per ray
 constexpr float kSkipMargin = 1.0f / 256.0f;    // cells
 
 struct MarchArgs {
@@ -217,10 +218,41 @@ __device__ __forceinline__ bool lane_init(const MarchArgs& A, int64_t r, Lane& s
     return !s.done;
 }
 
+// Record of a ray's occupied lattice ranges for the fill pass: runs that
+// continue one another are merged, up to kRunSlots ranges are stored as
+// {first k, count} in this ray's slots; n = -1 marks an overflow.
+struct RunRec {
+    int2* slots;
+    int n;
+    int k0, k1;  // pending range [k0, k1)
+};
+
+__device__ __forceinline__ void rec_flush(RunRec& q) {
+    if (q.k1 > q.k0 && q.n >= 0) {
+        if (q.n < kRunSlots)
+            q.slots[q.n++] = make_int2(q.k0, q.k1 - q.k0);
+        else
+            q.n = -1;
+    }
+}
+
+__device__ __forceinline__ void rec_run(RunRec& q, int k0, int k1) {
+    if (q.k1 == k0) {
+        q.k1 = k1;
+        return;
+    }
+    rec_flush(q);
+    q.k0 = k0;
+    q.k1 = k1;
+}
+
 // Advance the march of one ray: append the lattice indices of its occupied
 // points k < kend, in order, to buf[0..kBuf) (at most `limit` in total) and
-// return when the buffer is full or the ray is finished.
-__device__ void advance(const MarchArgs& A, Lane& s, int kend, int limit, int* buf, int& bn) {
+// return when the buffer is full or the ray is finished.  With a recorder,
+// every occupied cell run is also recorded whole: the emitted points are the
+// first n points of the recorded ranges, in order.
+template <bool kRec>
+__device__ void advance(const MarchArgs& A, Lane& s, int kend, int limit, int* buf, int& bn, RunRec* q) {
     const int L = A.g.n_levels;
     while (!s.done && bn < kBuf) {
         if (s.k >= s.run_end) {  // start a new cell run at s.k
@@ -242,6 +274,7 @@ __device__ void advance(const MarchArgs& A, Lane& s, int kend, int limit, int* b
                 s.k = s.run_end;
                 continue;
             }
+            if (kRec) rec_run(*q, s.k, s.run_end);
         }
         // lattice point s.k of an occupied run
         const float t0 = __fadd_rn(s.R.tn, __fmul_rn((float)s.k, A.step));
@@ -261,8 +294,9 @@ __device__ void advance(const MarchArgs& A, Lane& s, int kend, int limit, int* b
 // and each lane folds them into its optical depth in lattice order, stopping
 // at the first sample whose depth before it exceeds the threshold.
 template <bool kField>
-__global__ void __launch_bounds__(kBlockThreads)
+__global__ void __launch_bounds__(kBlockThreads, 10)
     k_march_count(MarchArgs A, int32_t* __restrict__ counts, int32_t* __restrict__ kstops,
+                  int32_t* __restrict__ nruns, float* __restrict__ tnear, int2* __restrict__ runs,
                   long long* __restrict__ block_sums) {
     extern __shared__ BlobS s_blobs[];
     __shared__ int s_buf[kBlockThreads][kBuf + 1];
@@ -276,14 +310,16 @@ __global__ void __launch_bounds__(kBlockThreads)
     Lane s;
     s.done = true;
     s.n = 0;
+    s.R.tn = 0.0f;
     if (r < A.n) lane_init(A, r, s);
+    RunRec q{runs + (r < A.n ? r : 0) * kRunSlots, 0, -1, -1};
     int* buf = s_buf[threadIdx.x];
     int cnt = 0, kstop = A.max_steps;
     float tau = 0.0f;
     bool stopped = false;
     while (true) {
         int bn = 0;
-        if (!s.done && !stopped) advance(A, s, A.max_steps, 0x7fffffff, buf, bn);
+        if (!s.done && !stopped) advance<true>(A, s, A.max_steps, 0x7fffffff, buf, bn, &q);
         if (!kField) {
             cnt += bn;
         } else {
@@ -314,8 +350,11 @@ __global__ void __launch_bounds__(kBlockThreads)
         if (__all_sync(0xffffffffu, s.done || stopped)) break;
     }
     if (r < A.n) {
+        rec_flush(q);
         counts[r] = cnt;
         kstops[r] = kstop;
+        nruns[r] = q.n;
+        tnear[r] = s.R.tn;
     }
     __shared__ int s_w[kWarpsPerBlock];
     int v = cnt;
@@ -375,11 +414,17 @@ __global__ void __launch_bounds__(1024)
     }
 }
 
+// Fill pass.  Rays whose runs were recorded are expanded warp-cooperatively,
+// one ray at a time: sample p of the ray is point p of its concatenated
+// ranges, written as coalesced stores.  Rays whose runs overflowed the slots
+// are re-marched per lane up to their recorded stop, without the field, and
+// flushed lane by lane with the whole warp.
 __global__ void __launch_bounds__(kBlockThreads)
     k_march_fill(MarchArgs A, const int32_t* __restrict__ counts, const int32_t* __restrict__ kstops,
-                 const long long* __restrict__ block_off, const int64_t* __restrict__ n_samples,
-                 int64_t capacity, int64_t* __restrict__ offsets, int32_t* __restrict__ ray_idx,
-                 float* __restrict__ t0s, float* __restrict__ t1s) {
+                 const int32_t* __restrict__ nruns, const float* __restrict__ tnear,
+                 const int2* __restrict__ runs, const long long* __restrict__ block_off,
+                 const int64_t* __restrict__ n_samples, int64_t capacity, int64_t* __restrict__ offsets,
+                 int32_t* __restrict__ ray_idx, float* __restrict__ t0s, float* __restrict__ t1s) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t r = (int64_t)blockIdx.x * kBlockThreads + threadIdx.x;
     const int cnt = r < A.n ? counts[r] : 0;
@@ -398,19 +443,57 @@ __global__ void __launch_bounds__(kBlockThreads)
     long long pos = block_off[blockIdx.x] + wbase + x - cnt;
     if (r < A.n) offsets[r] = pos;
     if (*n_samples > capacity) return;  // overflow: offsets only (the whole grid agrees)
+    const int nr = cnt > 0 ? nruns[r] : 0;
+    const float tn = cnt > 0 ? tnear[r] : 0.0f;
+    const int64_t r_lane0 = r - lane;
+
+    unsigned todo = __ballot_sync(0xffffffffu, nr > 0);
+    while (todo) {
+        const int j = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int cj = __shfl_sync(0xffffffffu, cnt, j);
+        const int nj = __shfl_sync(0xffffffffu, nr, j);
+        const long long pj = __shfl_sync(0xffffffffu, pos, j);
+        const float tnj = __shfl_sync(0xffffffffu, tn, j);
+        const int64_t rj = r_lane0 + j;
+        const int2 run = lane < nj ? runs[rj * kRunSlots + lane] : make_int2(0, 0);
+        int ex = run.y;  // -> exclusive prefix of the range lengths
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, ex, o);
+            if (lane >= o) ex += y;
+        }
+        ex -= run.y;
+        for (int p0 = 0; p0 < cj; p0 += 32) {
+            const int p = p0 + lane;
+            int k = p;
+            for (int i = 0; i < nj; ++i) {
+                const int ei = __shfl_sync(0xffffffffu, ex, i);
+                const int ki = __shfl_sync(0xffffffffu, run.x, i);
+                if (p >= ei) k = ki + (p - ei);
+            }
+            if (p < cj) {
+                const float t0 = __fadd_rn(tnj, __fmul_rn((float)k, A.step));
+                t0s[pj + p] = t0;
+                t1s[pj + p] = __fadd_rn(t0, A.step);
+                if (ray_idx) ray_idx[pj + p] = (int)rj;
+            }
+        }
+    }
+
+    if (!__any_sync(0xffffffffu, nr < 0)) return;
     // per-lane buffers of lattice indices (row stride kBuf+1: conflict-free appends)
     __shared__ int s_buf[kBlockThreads][kBuf + 1];
     int* buf = s_buf[threadIdx.x];
     Lane s;
     s.done = true;
     s.R.tn = 0.0f;
-    if (cnt > 0) lane_init(A, r, s);
-    const int kend = cnt > 0 ? kstops[r] : 0;
+    if (nr < 0) lane_init(A, r, s);
+    const int kend = nr < 0 ? kstops[r] : 0;
     while (true) {
         int bn = 0;
-        if (!s.done) advance(A, s, kend, cnt, buf, bn);
+        if (!s.done) advance<false>(A, s, kend, cnt, buf, bn, nullptr);
         __syncwarp();
-        // flush every lane's buffered run with the whole warp (coalesced)
         unsigned m = __ballot_sync(0xffffffffu, bn > 0);
         while (m) {
             const int j = __ffs(m) - 1;
@@ -443,7 +526,9 @@ using namespace nacc;
 extern "C" size_t nacc_march_scratch_bytes(int64_t n_rays) {
     if (n_rays < 0) return 0;
     const int64_t nb = (n_rays + kRaysPerBlock - 1) / kRaysPerBlock;
-    return align256(4 * (size_t)n_rays) * 2 + align256(8 * (size_t)(nb > 0 ? nb : 1));
+    // counts, kstops, nruns, tnear, block sums, run slots
+    return align256(4 * (size_t)n_rays) * 4 + align256(8 * (size_t)(nb > 0 ? nb : 1)) +
+           align256(sizeof(int2) * kRunSlots * (size_t)n_rays);
 }
 
 extern "C" int nacc_march_grid(const nacc_grid* grid, const float* rays_o, const float* rays_d,
@@ -512,7 +597,13 @@ extern "C" int nacc_march_grid(const nacc_grid* grid, const float* rays_o, const
     sp += align256(4 * (size_t)n_rays);
     int32_t* kstops = reinterpret_cast<int32_t*>(sp);
     sp += align256(4 * (size_t)n_rays);
+    int32_t* nruns = reinterpret_cast<int32_t*>(sp);
+    sp += align256(4 * (size_t)n_rays);
+    float* tnear = reinterpret_cast<float*>(sp);
+    sp += align256(4 * (size_t)n_rays);
     long long* bsums = reinterpret_cast<long long*>(sp);
+    sp += align256(8 * (size_t)((n_rays + kRaysPerBlock - 1) / kRaysPerBlock));
+    int2* runs = reinterpret_cast<int2*>(sp);
 
     const int64_t nb = (n_rays + kRaysPerBlock - 1) / kRaysPerBlock;
     NACC_CHECK_ARG(nb < (int64_t(1) << 31), "too many rays for one launch");
@@ -521,16 +612,18 @@ extern "C" int nacc_march_grid(const nacc_grid* grid, const float* rays_o, const
         if (shm > 48 * 1024)
             NACC_CUDA_TRY(cudaFuncSetAttribute(k_march_count<true>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-        k_march_count<true><<<(unsigned)nb, kBlockThreads, shm, st>>>(A, counts, kstops, bsums);
+        k_march_count<true><<<(unsigned)nb, kBlockThreads, shm, st>>>(A, counts, kstops, nruns, tnear, runs,
+                                                                        bsums);
     } else {
-        k_march_count<false><<<(unsigned)nb, kBlockThreads, 0, st>>>(A, counts, kstops, bsums);
+        k_march_count<false><<<(unsigned)nb, kBlockThreads, 0, st>>>(A, counts, kstops, nruns, tnear, runs,
+                                                                      bsums);
     }
     NACC_LAUNCH_CHECK();
     k_scan_block_sums<<<1, 1024, 0, st>>>(bsums, nb, out->offsets + n_rays, out->n_samples);
     NACC_LAUNCH_CHECK();
-    k_march_fill<<<(unsigned)nb, kBlockThreads, 0, st>>>(A, counts, kstops, bsums, out->n_samples,
-                                                         out->capacity, out->offsets, out->ray_indices,
-                                                         out->t_starts, out->t_ends);
+    k_march_fill<<<(unsigned)nb, kBlockThreads, 0, st>>>(A, counts, kstops, nruns, tnear, runs, bsums,
+                                                         out->n_samples, out->capacity, out->offsets,
+                                                         out->ray_indices, out->t_starts, out->t_ends);
     NACC_LAUNCH_CHECK();
     // Overflow is impossible when the capacity covers every lattice point.
     const bool may_overflow = (double)out->capacity < (double)n_rays * (double)params->max_steps;

@@ -110,6 +110,39 @@ def test_march_random_grids_bit_exact(nacc, orc, res, L, block, p_block):
     assert_packed_equal(got, exp)
 
 
+def _lattice_ranges(packed, step):
+    """Number of separate contiguous lattice ranges of each ray's samples."""
+    off, t0 = packed["offsets"], packed["t_starts"].astype(np.float64)
+    out = np.zeros(len(off) - 1, np.int64)
+    for r in range(len(off) - 1):
+        a, b = off[r], off[r + 1]
+        if b > a:
+            out[r] = 1 + int(np.count_nonzero(np.diff(t0[a:b]) > 1.5 * step))
+    return out
+
+
+def test_march_many_lattice_ranges_bit_exact(nacc, orc):
+    """A fine random grid splits rays into many separate lattice ranges: both
+    the rays whose ranges fit the fill pass's per-ray record (16) and the rays
+    that overflow it (re-marched) must match the definition."""
+    res, L = 64, 2
+    g = workloads.rng(4243)
+    occ = g.random((L, res, res, res)) < 0.5
+    occ[:, : res // 2] = True  # solid half (x < 0): few ranges per ray there
+    bits = workloads.pack_bits(occ.reshape(-1))
+    n = 2048
+    o = workloads._normalise(g.standard_normal((n, 3))) * 4.0
+    d = workloads._normalise(g.uniform(-1.2, 1.2, size=(n, 3)) - o)
+    o, d = o.astype(np.float32), d.astype(np.float32)
+    step = 3.0 / 256
+    grid = grid_from_bits(nacc, (-1.5,) * 3, (1.5,) * 3, res, L, bits)
+    got = run_march(nacc, grid, o, d, step, 1024, 0.0, 1e10)
+    exp = orc.march(o, d, (-1.5,) * 3, (1.5,) * 3, res, L, bits, step, 1024, 0.0, 1e10)
+    ranges = _lattice_ranges(exp, step)
+    assert np.count_nonzero(ranges > 16) > 100 and np.count_nonzero((ranges > 0) & (ranges <= 16)) > 100
+    assert_packed_equal(got, exp)
+
+
 def test_march_full_grid_is_uniform_sampling(nacc, orc):
     """All-occupied grid: the marcher reduces to uniform sampling (Sec. 3.1)."""
     res = 32
