@@ -23,6 +23,8 @@
 //     exit: k < floor(q + 1/2 - slack) with q = (t_exit - t_near)/dt and a
 //     slack of 1/64 step plus 2^-16 (|q| + |t_near|/dt) for the rounding of
 //     t0, t1, the midpoint and q (at least 16x their bound).
+// An empty cell inside an empty 8^3 block of cells (a per-call summary of the
+// bits) skips the whole block: the same argument holds for any box of cells.
 // Empty runs are skipped; occupied runs are emitted point by point with only
 // their t0 / t1 arithmetic (plus the field for early termination), so the
 // emitted set equals the dense march's at a fraction of its cost.  With a
@@ -41,6 +43,8 @@ constexpr int kRaysPerBlock = kBlockThreads;    // rays per block-sum entry
 constexpr int kWarpsPerBlock = kBlockThreads / 32;
 constexpr int kBuf = 32;                        // lattice indices buffered per lane
 constexpr int kRunSlots = 16;                   // recorded lattice runs per ray
+constexpr int kBlk = 8;                         // cells per edge of an empty-block summary entry
+constexpr size_t kBlockBitsBytes = size_t(NACC_MAX_LEVELS) * (1024 / kBlk) * (1024 / kBlk) * (1024 / kBlk) / 8;
 constexpr float kSkipMargin = 1.0f / 256.0f;    // cells
 
 struct MarchArgs {
@@ -55,6 +59,8 @@ struct MarchArgs {
     float inv_step;  // 1/step, only for the conservative skip (never for lattice values)
     int idx32;       // every flat cell index fits 32 bits
     float skip_lim[NACC_MAX_LEVELS];  // skip allowed at level l iff max|o| <= skip_lim[l]
+    const uint32_t* blk;  // empty-block summary: bit set iff any cell of the kBlk^3 block is occupied
+    int nb;               // blocks per axis, ceil(res / kBlk)
     nacc_blob_field field;
 };
 
@@ -123,20 +129,21 @@ __device__ __forceinline__ bool lattice_point(const MarchArgs& A, const Ray& R, 
     return (__ldg(&A.g.bits[idx >> 5]) >> (idx & 31)) & 1u;
 }
 
-// First lattice index that may leave the empty cell `ic` of level l holding
-// the point of lattice index k at midpoint tm (conservative, see the header).
+// First lattice index that may leave the box of cells lo[a] <= c_a <= hi[a]
+// of level l, holding the point of lattice index k at midpoint tm
+// (conservative, see the header).
 __device__ __forceinline__ int skip_target(const MarchArgs& A, const Ray& R, int k, float tm, int l,
-                                           const int ic[3], int kend) {
+                                           const int lo[3], const int hi[3], int kend) {
     if (R.omax > A.skip_lim[l]) return k + 1;
     const Level& lv = A.g.lv[l];
     float ts = INFINITY;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (R.d[a] > 0.0f) {
-            const float face = lv.lmin[a] + ((float)ic[a] + (1.0f - kSkipMargin)) * lv.width[a];
+            const float face = lv.lmin[a] + ((float)hi[a] + (1.0f - kSkipMargin)) * lv.width[a];
             ts = fminf(ts, (face - R.o[a]) * R.invd[a]);
         } else if (R.d[a] < 0.0f) {
-            const float face = lv.lmin[a] + ((float)ic[a] + kSkipMargin) * lv.width[a];
+            const float face = lv.lmin[a] + ((float)lo[a] + kSkipMargin) * lv.width[a];
             ts = fminf(ts, (face - R.o[a]) * R.invd[a]);
         }
     }
@@ -267,8 +274,23 @@ __device__ void advance(const MarchArgs& A, Lane& s, int kend, int limit, int* b
                 s.done = true;
                 break;
             }
-            s.run_end =
-                l < L ? skip_target(A, s.R, s.k, __fmul_rn(__fadd_rn(t0, t1), 0.5f), l, ic, kend) : s.k + 1;
+            if (l < L) {
+                int lo[3] = {ic[0], ic[1], ic[2]}, hi[3] = {ic[0], ic[1], ic[2]};
+                if (!occ && A.blk) {  // an empty cell in an empty block: skip the whole block
+                    const uint32_t b = ((uint32_t)l * A.nb + ic[0] / kBlk) * A.nb * A.nb +
+                                       (uint32_t)(ic[1] / kBlk) * A.nb + ic[2] / kBlk;
+                    if (!((__ldg(&A.blk[b >> 5]) >> (b & 31)) & 1u)) {
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            lo[a] = ic[a] / kBlk * kBlk;
+                            hi[a] = min(lo[a] + kBlk, A.g.res) - 1;
+                        }
+                    }
+                }
+                s.run_end = skip_target(A, s.R, s.k, __fmul_rn(__fadd_rn(t0, t1), 0.5f), l, lo, hi, kend);
+            } else {
+                s.run_end = s.k + 1;
+            }
             s.occ = occ;
             if (!occ) {
                 s.k = s.run_end;
@@ -287,6 +309,42 @@ __device__ void advance(const MarchArgs& A, Lane& s, int kend, int limit, int* b
         ++s.k;
         if (s.n >= limit) s.done = true;
     }
+}
+
+// Empty-block summary of the occupancy bits: one bit per kBlk^3 block of
+// cells of each level (partial blocks at the high edge when kBlk does not
+// divide res), set iff any cell of the block is occupied.  Block b =
+// (l*nb + bx)*nb*nb + by*nb + bz.  An acceleration structure only: a run
+// that stays inside an empty block skips every cell of it.
+__global__ void __launch_bounds__(256) k_block_summary(GridGeom g, int nb, uint32_t* __restrict__ blk) {
+    const uint64_t nblocks = (uint64_t)g.n_levels * nb * nb * nb;
+    const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool any = false;
+    if (b < nblocks) {
+        const int res = g.res;
+        const uint64_t per_level = (uint64_t)nb * nb * nb;
+        const int l = (int)(b / per_level);
+        const uint32_t rem = (uint32_t)(b % per_level);
+        const int bx = rem / (nb * nb), by = (rem / nb) % nb, bz = rem % nb;
+        const int x1 = min(bx * kBlk + kBlk, res), y1 = min(by * kBlk + kBlk, res);
+        const int z0 = bz * kBlk, nz = min(z0 + kBlk, res) - z0;
+        const uint64_t r3 = (uint64_t)res * res * res;
+        for (int x = bx * kBlk; x < x1 && !any; ++x) {
+            for (int y = by * kBlk; y < y1; ++y) {
+                const uint64_t i0 = (uint64_t)l * r3 + ((uint64_t)x * res + y) * res + z0;
+                const uint64_t w = i0 >> 5;
+                const int off = (int)(i0 & 31);
+                uint64_t bits = g.bits[w];
+                if (off + nz > 32) bits |= (uint64_t)g.bits[w + 1] << 32;
+                if ((bits >> off) & ((1ull << nz) - 1)) {
+                    any = true;
+                    break;
+                }
+            }
+        }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, any);
+    if ((threadIdx.x & 31) == 0 && b < nblocks) blk[b >> 5] = m;
 }
 
 // Count pass.  Each lane marches into its buffer; with a field the warp
@@ -528,7 +586,7 @@ extern "C" size_t nacc_march_scratch_bytes(int64_t n_rays) {
     const int64_t nb = (n_rays + kRaysPerBlock - 1) / kRaysPerBlock;
     // counts, kstops, nruns, tnear, block sums, run slots
     return align256(4 * (size_t)n_rays) * 4 + align256(8 * (size_t)(nb > 0 ? nb : 1)) +
-           align256(sizeof(int2) * kRunSlots * (size_t)n_rays);
+           align256(sizeof(int2) * kRunSlots * (size_t)n_rays) + kBlockBitsBytes;
 }
 
 extern "C" int nacc_march_grid(const nacc_grid* grid, const float* rays_o, const float* rays_d,
@@ -604,9 +662,18 @@ extern "C" int nacc_march_grid(const nacc_grid* grid, const float* rays_o, const
     long long* bsums = reinterpret_cast<long long*>(sp);
     sp += align256(8 * (size_t)((n_rays + kRaysPerBlock - 1) / kRaysPerBlock));
     int2* runs = reinterpret_cast<int2*>(sp);
+    sp += align256(sizeof(int2) * kRunSlots * (size_t)n_rays);
+    uint32_t* blk = reinterpret_cast<uint32_t*>(sp);
 
     const int64_t nb = (n_rays + kRaysPerBlock - 1) / kRaysPerBlock;
     NACC_CHECK_ARG(nb < (int64_t(1) << 31), "too many rays for one launch");
+    A.nb = (A.g.res + kBlk - 1) / kBlk;
+    A.blk = blk;
+    {
+        const uint64_t nblocks = (uint64_t)A.g.n_levels * A.nb * A.nb * A.nb;
+        k_block_summary<<<(unsigned)((nblocks + 255) / 256), 256, 0, st>>>(A.g, A.nb, blk);
+        NACC_LAUNCH_CHECK();
+    }
     if (with_field) {
         const size_t shm = sizeof(BlobS) * (size_t)A.field.n_blobs;
         if (shm > 48 * 1024)
