@@ -298,16 +298,23 @@ __device__ void advance(const MarchArgs& A, Lane& s, int kend, int limit, int* b
             }
             if (kRec) rec_run(*q, s.k, s.run_end);
         }
-        // lattice point s.k of an occupied run
-        const float t0 = __fadd_rn(s.R.tn, __fmul_rn((float)s.k, A.step));
-        if (!(t0 < s.R.tf)) {
-            s.done = true;
-            break;
+        // the points of the occupied run, as many as the buffer takes (one run
+        // per outer iteration keeps the run starts of the warp's lanes aligned)
+        const int n_emit = min(s.run_end - s.k, kBuf - bn);
+        for (int i = 0; i < n_emit; ++i) {
+            const float t0 = __fadd_rn(s.R.tn, __fmul_rn((float)s.k, A.step));
+            if (!(t0 < s.R.tf)) {
+                s.done = true;
+                break;
+            }
+            buf[bn++] = s.k;
+            ++s.n;
+            ++s.k;
+            if (s.n >= limit) {
+                s.done = true;
+                break;
+            }
         }
-        buf[bn++] = s.k;
-        ++s.n;
-        ++s.k;
-        if (s.n >= limit) s.done = true;
     }
 }
 
