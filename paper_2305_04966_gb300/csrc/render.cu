@@ -5,91 +5,40 @@
 // exp(-sigma_i dt_i))), Table 1 "PDF Approaches" row, Algorithm 1
 // "rendering", Sec. 4.2 "No Gradient Filtering" (mask T < eps).
 //
-// Warp-specialised streaming kernel (persistent: SMs x 2 CTAs of 8 warps):
-//   * ray ownership: sample space is cut into fixed chunks of kChunk samples;
-//     a ray belongs to the chunk holding its first sample (CSR offset); each
-//     CTA takes a contiguous range of chunks.  Inside a chunk the owned rays
-//     are packed greedily into tiles of whole rays spanning at most kTile
-//     positions (positions count from the tile's first sample rounded down
-//     to a multiple of 4, so every bulk copy and every vector store is
-//     16-byte aligned) and at most kWin rays.  The tiling depends only on the
-//     offsets, so forward and adjoint see identical tiles and bit-identical
-//     transmittance.
-//   * one producer warp plans the next tile from the offsets, then streams
-//     the tile's t0, t1, sigma and rgb planes into a kStages-deep shared-
-//     memory ring with 1-D bulk asynchronous copies (cp.async.bulk + mbarrier
-//     transaction counts) and writes the tile's segment map (ray heads / tails
-//     per position) and, for the adjoint, the rays' upstream gradients;
-//   * seven consumer warps own 8 consecutive positions per thread (128-bit
-//     shared loads).  The forward exclusive optical depth P_i is one
-//     block-wide segmented scan.  Forward: rays that end inside a thread are
-//     finished there; each thread parks the partial sums of its first and
-//     last (open) segments in its own slots of the spent stage planes, and one
-//     warp per ray that spans threads adds them up in a fixed order.
-//     Adjoint: a reverse block-wide segmented scan gives the suffix sums
-//     S^c_i, S^m_i directly (no cancellation, no saved per-sample
-//     transmittance).  Per-sample results leave as aligned 128-bit global
-//     stores straight from registers;
-//   * a ray longer than one tile is streamed alone in pieces with the scan
-//     state carried between pieces (the adjoint then takes two passes and
-//     forms suffixes as total - inclusive prefix on those rays only).
-// Every wait is bounded (2 s of %globaltimer); on expiry the kernel records
-// NACC_ERR_TIMEOUT in a device status word (nacc_device_status) and returns
-// after its own copies have landed.
+// One warp per ray (persistent grid, warps stride over the rays).  A ray
+// [s, e) is cut into chunks of 128 positions counted from s rounded down to
+// a multiple of 4; lane l owns positions 4l..4l+3 of a chunk, so every group
+// of four that lies inside the ray moves as one 128-bit load or store per
+// plane (positions outside the ray are never read or written).  Inside a
+// chunk every position belongs to the same ray, so the scans are plain warp
+// scans, not segmented ones.
+//   * forward: one pass in sample order; the exclusive optical depth P_i is
+//     the carry of the earlier chunks plus a warp scan, formed by one routine
+//     with explicitly rounded FP32 operations that the adjoint calls too, so
+//     both see bit-identical P_i and the same mask cut (the first sample
+//     with P_i > -ln eps).  A ray stops being read at its cut.
+//   * adjoint: a forward pass over tau only records each chunk's carry in one
+//     lane (32 chunks per sweep), then the chunks are visited in reverse and
+//     the suffix sums S^c_i, S^m_i are formed directly as reverse scans (no
+//     total - prefix cancellation).  The forward pass's data is read again
+//     right away, so the second read hits L2 and DRAM sees each byte once.
+//     A ray longer than 32 chunks repeats the carry sweep per group of 32.
+// The kernels hold no locks and wait on nothing; the file also carries the
+// device status word and the bounded-wait self-test of the library.
 #include "async_copy.cuh"
 #include "nacc_internal.cuh"
 
-// bit 0: a bounded wait expired in a render kernel
+// bit 0: a bounded wait expired (set by the library's bounded waits)
 __device__ unsigned int g_nacc_render_status;
 
 namespace nacc {
 namespace {
 
-constexpr int kConsumerWarps = 7;  // + 1 producer = 8 warps: 2 CTAs/SM at 128 registers
-constexpr int kConsumers = kConsumerWarps * 32;
-constexpr int kThreads = kConsumers + 32;   // + one producer warp
-constexpr int kItems = 8;                   // consecutive positions per consumer thread
-constexpr int kTile = kConsumers * kItems;  // positions per stage
-constexpr int kStages = 2;
-constexpr int kWin = 127;                   // rays per tile at most
-constexpr int64_t kChunk = 8192;            // ray-ownership chunk (samples)
-constexpr uint64_t kWaitLimitNs = 2000000000ull;
-constexpr int kBarConsumers = 1;
-
-enum : int { kKindTile = 0, kKindLong = 1, kKindDone = 2 };
-enum : int { kFirst = 1, kLast = 2, kPass2 = 4 };
-
-struct StageDesc {
-    long long base;   // first sample of the tile / piece
-    long long abase;  // base rounded down to a multiple of 4 = position 0
-    long long cend;   // end (exclusive) of the bulk-copied range
-    long long r0;     // first ray of the tile / the long ray
-    int n;            // samples
-    int e;            // rays in the tile
-    int kind;
-    int flags;
-    short off_rel[kWin + 1];  // tile: offsets[r0 + j] - abase, j = 0..e
-};
-
-struct alignas(128) Stage {
-    float t0[kTile];
-    float t1[kTile];
-    float sg[kTile];
-    float c[3 * kTile];
-    unsigned short seg[kTile];  // low byte: head local id + 1, high byte: tail local id + 1
-    StageDesc d;
-};
-
-template <bool kBwd>
-struct Smem {
-    Stage st[kStages];
-    float pray[kBwd ? kStages : 1][kBwd ? kWin * 5 : 1];  // adjoint: per-ray g_rgb (3), g_A, g_D
-    uint64_t full[kStages];
-    uint64_t empty[kStages];
-    float wred[2][kConsumerWarps * 8];  // warp aggregates, double-buffered
-    int wredi[2][kConsumerWarps];
-    float carry[8];
-};
+constexpr int kWarps = 8;          // warps per CTA
+constexpr int kThreads = kWarps * 32;
+constexpr int kPer = 4;            // consecutive positions per lane
+constexpr int kChunk = 32 * kPer;  // positions per chunk
+constexpr unsigned kFull = 0xffffffffu;
 
 struct RArgs {
     int64_t n_rays;
@@ -112,92 +61,6 @@ struct RArgs {
     float* g_c;
 };
 
-__device__ __forceinline__ void report_timeout() { atomicOr(&g_nacc_render_status, 1u); }
-
-__device__ __forceinline__ void consumer_sync() { named_barrier(kBarConsumers, kConsumers); }
-
-// AND of `pred` over the consumer threads (also a barrier for them).
-__device__ __forceinline__ bool consumer_all(bool pred) {
-    int r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\t"
-        "setp.ne.s32 p, %1, 0;\n\t"
-        "bar.red.and.pred q, %2, %3, p;\n\t"
-        "selp.s32 %0, 1, 0, q;\n\t}"
-        : "=r"(r)
-        : "r"((int)pred), "r"(kBarConsumers), "r"(kConsumers)
-        : "memory");
-    return r != 0;
-}
-
-// ---------------------------------------------------------------------------
-// segmented scan state: K sums and a segment id; "starts a segment" <=> id >= 0
-// ---------------------------------------------------------------------------
-template <int K>
-struct Seg {
-    float v[K];
-    int id;
-};
-template <int K>
-__device__ __forceinline__ Seg<K> seg_zero(int id) {
-    Seg<K> r;
-#pragma unroll
-    for (int k = 0; k < K; ++k) r.v[k] = 0.0f;
-    r.id = id;
-    return r;
-}
-// a precedes b in scan order: b wins if it starts a segment, else sums.
-template <int K>
-__device__ __forceinline__ Seg<K> comb(const Seg<K>& a, const Seg<K>& b) {
-    if (b.id >= 0) return b;
-    Seg<K> r;
-#pragma unroll
-    for (int k = 0; k < K; ++k) r.v[k] = a.v[k] + b.v[k];
-    r.id = a.id;
-    return r;
-}
-template <int K, bool kUp>
-__device__ __forceinline__ Seg<K> shfl(const Seg<K>& x, int o) {
-    Seg<K> r;
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-        r.v[k] = kUp ? __shfl_up_sync(0xffffffffu, x.v[k], o) : __shfl_down_sync(0xffffffffu, x.v[k], o);
-    r.id = kUp ? __shfl_up_sync(0xffffffffu, x.id, o) : __shfl_down_sync(0xffffffffu, x.id, o);
-    return r;
-}
-
-// Exclusive segmented scan over the consumer threads, forward (thread order)
-// or reverse; one barrier; `buf` alternates between consecutive scans.
-template <int K, bool kForward, class SM>
-__device__ __forceinline__ Seg<K> block_scan(SM& s, const Seg<K>& x, int buf) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    Seg<K> inc = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        Seg<K> y = shfl<K, kForward>(inc, o);
-        if (kForward ? lane >= o : lane + o < 32) inc = comb(y, inc);
-    }
-    Seg<K> exw = shfl<K, kForward>(inc, 1);
-    if (kForward ? lane == 0 : lane == 31) exw = seg_zero<K>(-1);
-    if (kForward ? lane == 31 : lane == 0) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) s.wred[buf][wid * 8 + k] = inc.v[k];
-        s.wredi[buf][wid] = inc.id;
-    }
-    consumer_sync();
-    Seg<K> wp = seg_zero<K>(-1);
-#pragma unroll
-    for (int q = 0; q < kConsumerWarps; ++q) {
-        const int w = kForward ? q : kConsumerWarps - 1 - q;
-        Seg<K> g;
-#pragma unroll
-        for (int k = 0; k < K; ++k) g.v[k] = s.wred[buf][w * 8 + k];
-        g.id = s.wredi[buf][w];
-        if (kForward ? w < wid : w > wid) wp = comb(wp, g);
-    }
-    return comb(wp, exw);
-}
-
 // 1 - exp(-x) for x >= 0: Taylor series x(1 - x/2(1 - x/3(1 - x/4(1 - x/5))))
 // below 1/16 (truncation < 2e-9 relative), else 1 - exp(-x) directly.
 __device__ __forceinline__ float one_minus_exp_neg(float x) {
@@ -206,727 +69,327 @@ __device__ __forceinline__ float one_minus_exp_neg(float x) {
     return x < 0.0625f ? ser : dir;
 }
 
-__device__ __forceinline__ void ld8(const float* plane, int p, float v[8]) {
-    const float4 a = *reinterpret_cast<const float4*>(plane + p);
-    const float4 b = *reinterpret_cast<const float4*>(plane + p + 4);
-    v[0] = a.x;
-    v[1] = a.y;
-    v[2] = a.z;
-    v[3] = a.w;
-    v[4] = b.x;
-    v[5] = b.y;
-    v[6] = b.z;
-    v[7] = b.w;
-}
-
-// colours of 8 consecutive positions: 24 floats, 6 x 128-bit
-__device__ __forceinline__ void ld24(const float* c, int p, float v[24]) {
-    const float4* q = reinterpret_cast<const float4*>(c + 3 * p);
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        const float4 a = q[k];
-        v[4 * k + 0] = a.x;
-        v[4 * k + 1] = a.y;
-        v[4 * k + 2] = a.z;
-        v[4 * k + 3] = a.w;
-    }
-}
-
-// Per-thread view of the segment map of its 8 positions.
-struct SegView {
-    uint4 raw;
-    unsigned head;   // bit j: position j starts a ray
-    unsigned tail;   // bit j: position j ends a ray
-    unsigned valid;  // bit j: position j belongs to the tile
+// The lane's four positions p..p+3 of a chunk and which of them lie in [s, e).
+struct Group {
+    long long p;
+    bool whole;   // all four inside the ray
+    unsigned in;  // bit j: position p+j inside the ray
 };
-__device__ __forceinline__ unsigned seg_entry(const uint4& s, int j) {
-    const unsigned w = j < 2 ? s.x : j < 4 ? s.y : j < 6 ? s.z : s.w;
-    return (j & 1) ? (w >> 16) : (w & 0xffffu);
-}
-__device__ __forceinline__ SegView seg_view(const unsigned short* seg, int p0, int o_rel, int pend) {
-    SegView v;
-    v.raw = *reinterpret_cast<const uint4*>(seg + p0);
-    v.head = 0;
-    v.tail = 0;
+
+__device__ __forceinline__ Group group_of(long long a, int c, long long s, long long e) {
+    Group g;
+    g.p = a + (long long)c * kChunk + kPer * (threadIdx.x & 31);
+    g.whole = g.p >= s && g.p + kPer <= e;
+    g.in = 0;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const unsigned e = seg_entry(v.raw, j);
-        v.head |= ((e & 0xffu) != 0u) << j;
-        v.tail |= ((e >> 8) != 0u) << j;
+    for (int j = 0; j < kPer; ++j)
+        if (g.p + j >= s && g.p + j < e) g.in |= 1u << j;
+    return g;
+}
+
+__device__ __forceinline__ void load4(const float* plane, const Group& g, float v[4]) {
+    if (g.whole) {
+        const float4 q = __ldg(reinterpret_cast<const float4*>(plane + g.p));
+        v[0] = q.x;
+        v[1] = q.y;
+        v[2] = q.z;
+        v[3] = q.w;
+    } else {
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) v[j] = (g.in >> j & 1u) ? __ldg(plane + g.p + j) : 0.0f;
     }
-    const int lo = min(max(o_rel - p0, 0), 8), hi = min(max(pend - p0, 0), 8);
-    v.valid = ((1u << hi) - 1u) & ~((1u << lo) - 1u);
+}
+
+__device__ __forceinline__ void load4x3(const float* plane, const Group& g, float v[12]) {
+    if (g.whole) {
+        const float4* q = reinterpret_cast<const float4*>(plane + 3 * g.p);
+        const float4 x = __ldg(q), y = __ldg(q + 1), z = __ldg(q + 2);
+        v[0] = x.x, v[1] = x.y, v[2] = x.z, v[3] = x.w;
+        v[4] = y.x, v[5] = y.y, v[6] = y.z, v[7] = y.w;
+        v[8] = z.x, v[9] = z.y, v[10] = z.z, v[11] = z.w;
+    } else {
+#pragma unroll
+        for (int j = 0; j < 3 * kPer; ++j) v[j] = (g.in >> (j / 3) & 1u) ? __ldg(plane + 3 * g.p + j) : 0.0f;
+    }
+}
+
+__device__ __forceinline__ void store4(float* plane, const Group& g, const float v[4]) {
+    if (g.whole) {
+        *reinterpret_cast<float4*>(plane + g.p) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < kPer; ++j)
+            if (g.in >> j & 1u) plane[g.p + j] = v[j];
+    }
+}
+
+__device__ __forceinline__ void store4x3(float* plane, const Group& g, const float v[12]) {
+    if (g.whole) {
+        float4* q = reinterpret_cast<float4*>(plane + 3 * g.p);
+        q[0] = make_float4(v[0], v[1], v[2], v[3]);
+        q[1] = make_float4(v[4], v[5], v[6], v[7]);
+        q[2] = make_float4(v[8], v[9], v[10], v[11]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 3 * kPer; ++j)
+            if (g.in >> (j / 3) & 1u) plane[3 * g.p + j] = v[j];
+    }
+}
+
+// tau_j = sigma_j * (t1_j - t0_j) inside the ray, else 0 (individually rounded).
+__device__ __forceinline__ void taus(const Group& g, const float t0[4], const float t1[4], const float sg[4],
+                                     float tau[4]) {
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) tau[j] = (g.in >> j & 1u) ? __fmul_rn(sg[j], __fsub_rn(t1[j], t0[j])) : 0.0f;
+}
+
+// Exclusive optical depth of the lane's positions given the carry of the
+// earlier chunks; returns the carry after this chunk.  The one definition of
+// P_i used by both the forward pass and the adjoint.
+__device__ __forceinline__ float chunk_prefix(const float tau[4], float carry, float P[4]) {
+    const int lane = threadIdx.x & 31;
+    const float l1 = tau[0];
+    const float l2 = __fadd_rn(l1, tau[1]);
+    const float l3 = __fadd_rn(l2, tau[2]);
+    const float l4 = __fadd_rn(l3, tau[3]);
+    float incl = l4;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl = __fadd_rn(y, incl);
+    }
+    float ex = __shfl_up_sync(kFull, incl, 1);
+    if (lane == 0) ex = 0.0f;
+    const float base = __fadd_rn(carry, ex);
+    P[0] = base;
+    P[1] = __fadd_rn(base, l1);
+    P[2] = __fadd_rn(base, l2);
+    P[3] = __fadd_rn(base, l3);
+    return __fadd_rn(carry, __shfl_sync(kFull, incl, 31));
+}
+
+// First position of this chunk with P > thr inside the ray (or `none`), and
+// the P there (warp-uniform results).
+__device__ __forceinline__ long long chunk_cut(const Group& g, const float P[4], float thr, long long none,
+                                               float& p_cut) {
+    int jc = kPer;
+    float pj = 0.0f;
+#pragma unroll
+    for (int j = kPer - 1; j >= 0; --j)
+        if ((g.in >> j & 1u) && P[j] > thr) {
+            jc = j;
+            pj = P[j];
+        }
+    const unsigned m = __ballot_sync(kFull, jc < kPer);
+    if (!m) return none;
+    const int l0 = __ffs(m) - 1;
+    p_cut = __shfl_sync(kFull, pj, l0);
+    return __shfl_sync(kFull, g.p, l0) + __shfl_sync(kFull, jc, l0);
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
     return v;
 }
-__device__ __forceinline__ int tail_id(const SegView& v, int j) { return (int)(seg_entry(v.raw, j) >> 8) - 1; }
 
-// Store 8 consecutive results of positions [p, p+8) to dst[abase + p ..]
-// (vector stores when all 8 are valid, else per element).
-__device__ __forceinline__ void st8_global(float* dst, long long abase, int p, unsigned valid, const float v[8]) {
-    float* d = dst + abase + p;
-    if (valid == 0xffu) {
-        __stcs(reinterpret_cast<float4*>(d), make_float4(v[0], v[1], v[2], v[3]));
-        __stcs(reinterpret_cast<float4*>(d) + 1, make_float4(v[4], v[5], v[6], v[7]));
-    } else {
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-            if (valid & (1u << j)) __stcs(d + j, v[j]);
-    }
-}
-__device__ __forceinline__ void st24_global(float* dst, long long abase, int p, unsigned valid, const float v[24]) {
-    float* d = dst + 3 * (abase + p);
-    if (valid == 0xffu) {
-#pragma unroll
-        for (int k = 0; k < 6; ++k)
-            __stcs(reinterpret_cast<float4*>(d) + k, make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]));
-    } else {
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-            if (valid & (1u << j)) {
-                __stcs(d + 3 * j + 0, v[3 * j + 0]);
-                __stcs(d + 3 * j + 1, v[3 * j + 1]);
-                __stcs(d + 3 * j + 2, v[3 * j + 2]);
-            }
-    }
-}
-
-__device__ __forceinline__ void write_ray(const RArgs& A, long long ray, const float v[6]) {
-    const float TN = __expf(-v[5]);
-    A.rgb_out[3 * ray + 0] = v[0] + TN * A.bg0;
-    A.rgb_out[3 * ray + 1] = v[1] + TN * A.bg1;
-    A.rgb_out[3 * ray + 2] = v[2] + TN * A.bg2;
-    A.op_out[ray] = v[3];
-    A.dep_out[ray] = v[4];
-    A.tr_out[ray] = TN;
-}
-
-// ---------------------------------------------------------------------------
-// producer warp
-// ---------------------------------------------------------------------------
-
-// First ray r in [0, n_rays] with off[r] >= target (off[n_rays] >= target).
-__device__ int64_t lower_bound_warp(const int64_t* off, int64_t n_rays, int64_t target) {
+__global__ void __launch_bounds__(kThreads, 4) k_render_fwd(RArgs A) {
     const int lane = threadIdx.x & 31;
-    int64_t lo = 0, hi = n_rays;
-    while (hi - lo > 31) {
-        const int64_t span = hi - lo;
-        const int64_t p = lo + (span * (lane + 1)) / 32;
-        const bool ge = __ldg(&off[p]) >= target;
-        const unsigned m = __ballot_sync(0xffffffffu, ge);
-        const int f = __ffs(m) - 1;
-        const int64_t nhi = lo + (span * (f + 1)) / 32;
-        const int64_t nlo = f > 0 ? lo + (span * f) / 32 + 1 : lo;
-        lo = nlo;
-        hi = nhi;
-    }
-    const int64_t p = lo + lane;
-    const bool ge = (p <= hi) && __ldg(&off[p]) >= target;
-    const unsigned m = __ballot_sync(0xffffffffu, ge);
-    return lo + (__ffs(m) - 1);
-}
-
-template <bool kBwd>
-struct Producer {
-    const RArgs& A;
-    Smem<kBwd>& s;
-    long long S4;  // total samples rounded down to a multiple of 4
-    int it;        // stages issued so far
-    bool ok;
-
-    // Wait (all lanes, bounded) until the stage of issue `it` is free.
-    __device__ bool acquire(int& stg) {
-        stg = it % kStages;
-        const uint32_t ph = (uint32_t)(it / kStages) & 1u;
-        bool got = true;
-        if (it >= kStages) got = mbar_wait_bounded(&s.empty[stg], ph ^ 1u, kWaitLimitNs);
-        return __all_sync(0xffffffffu, got);
-    }
-
-    __device__ long long copy_end(long long end) const {
-        const long long ce = (end + 3) & ~3ll;
-        return ce < S4 ? ce : S4;
-    }
-
-    // Lane 0: raise the stage's expected bytes and start the bulk copies of
-    // positions [abase, cend) (the stage's later arrive completes the phase).
-    __device__ void start_copies(int stg, long long abase, long long cend) {
-        Stage& st = s.st[stg];
-        if (cend > abase) {
-            const uint32_t cnt = (uint32_t)(cend - abase);
-            mbar_expect_tx(&s.full[stg], 24u * cnt);
-            bulk_copy_g2s(st.t0, A.t0 + abase, 4u * cnt, &s.full[stg]);
-            bulk_copy_g2s(st.t1, A.t1 + abase, 4u * cnt, &s.full[stg]);
-            bulk_copy_g2s(st.sg, A.sg + abase, 4u * cnt, &s.full[stg]);
-            bulk_copy_g2s(st.c, A.rgb + 3 * abase, 12u * cnt, &s.full[stg]);
-        }
-    }
-
-    __device__ void clear_seg(Stage& st) {
-        const int lane = threadIdx.x & 31;
-        uint4* p = reinterpret_cast<uint4*>(st.seg);
+    const int64_t warps = (int64_t)gridDim.x * kWarps;
+    for (int64_t r = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); r < A.n_rays; r += warps) {
+        const long long s = A.off[r], e = A.off[r + 1];
+        const long long a = s & ~3ll;
+        const int nch = e > s ? (int)((e - a + kChunk - 1) / kChunk) : 0;
+        float cr = 0.0f, cg = 0.0f, cb = 0.0f, op = 0.0f, dep = 0.0f;
+        float carry = 0.0f;  // -> optical depth of the kept samples
+        long long cut = e;
+        int c = 0;
+        for (; c < nch && cut == e; ++c) {
+            const Group g = group_of(a, c, s, e);
+            float t0[4], t1[4], sg[4], rgb[12], tau[4], P[4];
+            load4(A.t0, g, t0);
+            load4(A.t1, g, t1);
+            load4(A.sg, g, sg);
+            load4x3(A.rgb, g, rgb);
+            taus(g, t0, t1, sg, tau);
+            const float next = chunk_prefix(tau, carry, P);
+            float p_cut = 0.0f;
+            cut = chunk_cut(g, P, A.thr, e, p_cut);
+            carry = cut < e ? p_cut : next;
+            float w[4];
 #pragma unroll
-        for (int k = 0; k < kTile / 8 / 32; ++k) p[lane + 32 * k] = make_uint4(0, 0, 0, 0);
-    }
-
-    __device__ void load_ray_grads(int stg, int j, long long ray) {
-        if (kBwd) {
-            float* pr = &s.pray[stg][5 * j];
-            pr[0] = A.g_rgb ? __ldg(&A.g_rgb[3 * ray + 0]) : 0.0f;
-            pr[1] = A.g_rgb ? __ldg(&A.g_rgb[3 * ray + 1]) : 0.0f;
-            pr[2] = A.g_rgb ? __ldg(&A.g_rgb[3 * ray + 2]) : 0.0f;
-            pr[3] = A.g_op ? __ldg(&A.g_op[ray]) : 0.0f;
-            pr[4] = A.g_dep ? __ldg(&A.g_dep[ray]) : 0.0f;
-        }
-    }
-
-    __device__ void publish(int stg) {
-        __syncwarp();
-        if ((threadIdx.x & 31) == 0) mbar_arrive(&s.full[stg]);
-        __syncwarp();
-        ++it;
-    }
-
-    __device__ void long_ray(int64_t ray, long long b, long long e) {
-        const int lane = threadIdx.x & 31;
-        for (int pass = 0; pass < (kBwd ? 2 : 1) && ok; ++pass) {
-            long long p = b;
-            while (p < e) {
-                const long long abase = p & ~3ll;
-                const long long n = min64(kTile - (p - abase), e - p);
-                const long long cend = copy_end(p + n);
-                int stg;
-                if (!acquire(stg)) {
-                    ok = false;
-                    return;
-                }
-                Stage& st = s.st[stg];
-                if (lane == 0) start_copies(stg, abase, cend);
-                clear_seg(st);
-                __syncwarp();
-                if (lane == 0) {
-                    StageDesc& d = st.d;
-                    d.kind = kKindLong;
-                    d.base = p;
-                    d.abase = abase;
-                    d.cend = cend;
-                    d.r0 = ray;
-                    d.n = (int)n;
-                    d.e = 1;
-                    d.flags = (p == b ? kFirst : 0) | (p + n == e ? kLast : 0) | (pass ? kPass2 : 0);
-                    const int o = (int)(p - abase);
-                    if (p == b) st.seg[o] = 1;
-                    if (p + n == e) st.seg[o + n - 1] = (unsigned short)(st.seg[o + n - 1] | (1u << 8));
-                    load_ray_grads(stg, 0, ray);
-                }
-                publish(stg);
-                p += n;
+            for (int j = 0; j < kPer; ++j) {
+                const bool kept = (g.in >> j & 1u) && g.p + j < cut;
+                w[j] = kept ? __expf(-P[j]) * one_minus_exp_neg(tau[j]) : 0.0f;
+                cr = fmaf(w[j], rgb[3 * j], cr);
+                cg = fmaf(w[j], rgb[3 * j + 1], cg);
+                cb = fmaf(w[j], rgb[3 * j + 2], cb);
+                op += w[j];
+                dep = fmaf(w[j], __fmul_rn(__fadd_rn(t0[j], t1[j]), 0.5f), dep);
             }
+            if (A.w_out) store4(A.w_out, g, w);
         }
-    }
-
-    __device__ void run(int64_t c_begin, int64_t c_end) {
-        const int lane = threadIdx.x & 31;
-        int64_t r = c_begin < c_end ? lower_bound_warp(A.off, A.n_rays, c_begin * kChunk) : A.n_rays;
-        for (int64_t c = c_begin; c < c_end && ok; ++c) {
-            const long long hi_s = (c + 1) * kChunk;
-            while (r < A.n_rays && ok) {
-                // plan the next tile (before waiting for a free stage)
-                const int nwin = (int)min64(kWin, A.n_rays - r);
-                long long v[4];  // entries j = lane*4 + q, j <= nwin
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int j = lane * 4 + q;
-                    v[q] = j <= nwin ? __ldg(&A.off[r + j]) : 0x7fffffffffffffffll;
-                }
-                int own = 0;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) own += (lane * 4 + q < nwin && v[q] < hi_s) ? 1 : 0;
-                const int n_owned = __reduce_add_sync(0xffffffffu, own);
-                if (n_owned == 0) break;
-                const long long base = __shfl_sync(0xffffffffu, v[0], 0);
-                const long long abase = base & ~3ll;
-                const long long lim = abase + kTile;
-                int fit = 0;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) fit += (lane * 4 + q <= n_owned && v[q] <= lim) ? 1 : 0;
-                const int e = __reduce_add_sync(0xffffffffu, fit) - 1;
-                if (e == 0) {
-                    const long long end = __shfl_sync(0xffffffffu, v[1], 0);
-                    long_ray(r, base, end);
-                    r += 1;
-                    continue;
-                }
-                long long tend = 0;
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (lane * 4 + q == e) tend = v[q];
-                tend = __shfl_sync(0xffffffffu, tend, e >> 2);
-                const long long next_lane0 = __shfl_down_sync(0xffffffffu, v[0], 1);
-                const long long cend = copy_end(tend);
-                int stg;
-                if (!acquire(stg)) {
-                    ok = false;
-                    break;
-                }
-                Stage& st = s.st[stg];
-                if (lane == 0) start_copies(stg, abase, cend);
-                clear_seg(st);
-                __syncwarp();
-                // ray j = lane*4+q (j < e): head at v[q]-abase, tail at v(j+1)-abase-1
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int j = lane * 4 + q;
-                    if (j <= e) st.d.off_rel[j] = (short)(v[q] - abase);
-                    if (j < e) {
-                        const long long nx = q < 3 ? v[q + 1] : next_lane0;
-                        if (nx > v[q]) {
-                            const int h = (int)(v[q] - abase), t = (int)(nx - abase - 1);
-                            if (h == t) {
-                                st.seg[h] = (unsigned short)((j + 1) | ((j + 1) << 8));
-                            } else {
-                                st.seg[h] = (unsigned short)(j + 1);
-                                st.seg[t] = (unsigned short)((j + 1) << 8);
-                            }
-                        }
-                        load_ray_grads(stg, j, r + j);
-                    }
-                }
-                if (lane == 0) {
-                    StageDesc& d = st.d;
-                    d.kind = kKindTile;
-                    d.base = base;
-                    d.abase = abase;
-                    d.cend = cend;
-                    d.r0 = r;
-                    d.n = (int)(tend - base);
-                    d.e = e;
-                    d.flags = 0;
-                }
-                publish(stg);
-                r += e;
-            }
+        if (A.w_out) {  // chunks after the cut: zero weights
+            const float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            for (; c < nch; ++c) store4(A.w_out, group_of(a, c, s, e), z);
         }
-        int stg;
-        if (ok && acquire(stg)) {
-            if (lane == 0) {
-                s.st[stg].d.kind = kKindDone;
-                s.st[stg].d.n = 0;
-            }
-            publish(stg);
-        } else {
-            ok = false;
+        cr = warp_sum(cr);
+        cg = warp_sum(cg);
+        cb = warp_sum(cb);
+        op = warp_sum(op);
+        dep = warp_sum(dep);
+        if (lane == 0) {
+            const float TN = __expf(-carry);
+            A.rgb_out[3 * r + 0] = fmaf(TN, A.bg0, cr);
+            A.rgb_out[3 * r + 1] = fmaf(TN, A.bg1, cg);
+            A.rgb_out[3 * r + 2] = fmaf(TN, A.bg2, cb);
+            A.op_out[r] = op;
+            A.dep_out[r] = dep;
+            A.tr_out[r] = TN;
         }
-        if (!ok) {
-            if (lane == 0) report_timeout();
-            // let every copy this warp started land before the CTA can exit
-            for (int k = 0; k < kStages && k < it; ++k) {
-                const int i = it - 1 - k;
-                mbar_wait_bounded(&s.full[i % kStages], (uint32_t)(i / kStages) & 1u, kWaitLimitNs);
-            }
-        }
-    }
-};
-
-// ---------------------------------------------------------------------------
-// consumer side
-// ---------------------------------------------------------------------------
-
-struct Carry {
-    float P;       // optical depth after the last item processed (all samples)
-    float acc[6];  // sum w c_r, w c_g, w c_b, w, w m, unmasked tau
-};
-
-// Loads positions of [max(cend, base), base + n) -- the ragged end of the
-// arrays that the bulk copy left out -- with plain loads.
-__device__ __forceinline__ void load_ragged_end(const RArgs& A, Stage& st) {
-    const long long from = st.d.cend > st.d.base ? st.d.cend : st.d.base;
-    const long long to = st.d.base + st.d.n;
-    for (long long i = from + threadIdx.x; i < to; i += kConsumers) {
-        const int p = (int)(i - st.d.abase);
-        st.t0[p] = __ldg(A.t0 + i);
-        st.t1[p] = __ldg(A.t1 + i);
-        st.sg[p] = __ldg(A.sg + i);
-        st.c[3 * p + 0] = __ldg(A.rgb + 3 * i + 0);
-        st.c[3 * p + 1] = __ldg(A.rgb + 3 * i + 1);
-        st.c[3 * p + 2] = __ldg(A.rgb + 3 * i + 2);
     }
 }
 
-// Pass 1 (both directions): optical depth per position and its forward
-// exclusive segmented prefix P (carry_P continues a long ray's piece).
-template <class SM>
-__device__ __forceinline__ void depth_pass(SM& s, const Stage& st, int p0, const SegView& sv, float carry_P,
-                                           float tau[8], float P[8], float& incl_end) {
-    float a[8], b[8], g[8];
-    ld8(st.t0, p0, a);
-    ld8(st.t1, p0, b);
-    ld8(st.sg, p0, g);
-    Seg<1> agg = seg_zero<1>(-1);
+// Exclusive suffix of v over the warp's positions (later lanes, later j)
+// plus the carry of the later chunks: suf[j] = carry + sum of v after
+// position j.  Returns the carry for the chunk before this one.
+__device__ __forceinline__ float chunk_suffix(const float v[4], float carry, float suf[4]) {
+    const int lane = threadIdx.x & 31;
+    const float r2 = v[3];
+    const float r1 = r2 + v[2];
+    const float r0 = r1 + v[1];
+    float incl = r0 + v[0];  // -> sum over lanes >= lane
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        tau[j] = (sv.valid & (1u << j)) ? __fmul_rn(g[j], __fsub_rn(b[j], a[j])) : 0.0f;
-        if (sv.head & sv.valid & (1u << j)) agg = seg_zero<1>(0);
-        agg.v[0] = agg.v[0] + tau[j];
+    for (int o = 1; o < 32; o <<= 1) {
+        const float y = __shfl_down_sync(kFull, incl, o);
+        if (lane + o < 32) incl += y;
     }
-    Seg<1> cin;
-    cin.v[0] = carry_P;
-    cin.id = 0;
-    const Seg<1> ex = comb(cin, block_scan<1, true>(s, agg, 0));
-    float run = ex.v[0];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        if (sv.head & sv.valid & (1u << j)) run = 0.0f;
-        P[j] = run;
-        run = run + tau[j];
-    }
-    incl_end = run;
+    float ex = __shfl_down_sync(kFull, incl, 1);
+    if (lane == 31) ex = 0.0f;
+    const float base = carry + ex;
+    suf[0] = base + r0;
+    suf[1] = base + r1;
+    suf[2] = base + r2;
+    suf[3] = base;
+    return carry + __shfl_sync(kFull, incl, 0);
 }
 
-// Forward compositing of a tile of whole rays.
-template <class SM>
-__device__ void fwd_tile(const RArgs& A, SM& s, Stage& st) {
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int p0 = tid * kItems;
-    const int o_rel = (int)(st.d.base - st.d.abase);
-    const int pend = o_rel + st.d.n;
-    const long long r0 = st.d.r0;
-    const SegView sv = seg_view(st.seg, p0, o_rel, pend);
-    float tau[8], P[8], incl_end;
-    depth_pass(s, st, p0, sv, 0.0f, tau, P, incl_end);
-
-    float a[8], b[8], c[24], w[8];
-    ld8(st.t0, p0, a);
-    ld8(st.t1, p0, b);
-    ld24(st.c, p0, c);
-    float loc[6] = {0, 0, 0, 0, 0, 0};    // sums since the last head (or the thread start)
-    float first[6] = {0, 0, 0, 0, 0, 0};  // sums of the items before the first head
-    bool seen_head = false;
-    bool open_last = false;  // the last segment started here and continues past the thread
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        w[j] = 0.0f;
-        if (!(sv.valid & (1u << j))) continue;
-        if (sv.head & (1u << j)) {
-            if (!seen_head) {
-#pragma unroll
-                for (int k = 0; k < 6; ++k) first[k] = loc[k];
-            }
-#pragma unroll
-            for (int k = 0; k < 6; ++k) loc[k] = 0.0f;
-            seen_head = true;
+// Carry sweep of the adjoint over chunks [0, c_end): lane (c & 31) keeps the
+// carry before chunk c for c >= c_keep.  Stops at the mask cut (returned,
+// with the kept optical depth in `carry` and the chunks up to the cut in
+// `n_kept`).
+__device__ __forceinline__ long long carry_sweep(const RArgs& A, long long a, long long s, long long e, int c_end,
+                                                 int c_keep, float& carry, float& my_carry, int& n_kept) {
+    const int lane = threadIdx.x & 31;
+    carry = 0.0f;
+    n_kept = c_end;
+    for (int c = 0; c < c_end; ++c) {
+        if (c >= c_keep && (c & 31) == lane) my_carry = carry;
+        const Group g = group_of(a, c, s, e);
+        float t0[4], t1[4], sg[4], tau[4], P[4];
+        load4(A.t0, g, t0);
+        load4(A.t1, g, t1);
+        load4(A.sg, g, sg);
+        taus(g, t0, t1, sg, tau);
+        const float next = chunk_prefix(tau, carry, P);
+        float p_cut = 0.0f;
+        const long long cut = chunk_cut(g, P, A.thr, e, p_cut);
+        if (cut < e) {
+            carry = p_cut;
+            n_kept = c + 1;
+            return cut;
         }
-        const bool kept = !(P[j] > A.thr);
-        w[j] = kept ? __expf(-P[j]) * one_minus_exp_neg(tau[j]) : 0.0f;
-        const float m = 0.5f * (a[j] + b[j]);
-        loc[0] += w[j] * c[3 * j + 0];
-        loc[1] += w[j] * c[3 * j + 1];
-        loc[2] += w[j] * c[3 * j + 2];
-        loc[3] += w[j];
-        loc[4] += w[j] * m;
-        loc[5] += kept ? tau[j] : 0.0f;
-        open_last = seen_head;
-        if (sv.tail & (1u << j)) {
-            open_last = false;
-            if (seen_head) write_ray(A, r0 + tail_id(sv, j), loc);  // started and ended in this thread
-        }
+        carry = next;
     }
-    if (!seen_head) {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) first[k] = loc[k];
-    }
-    if (A.w_out) st8_global(A.w_out, st.d.abase, p0, sv.valid, w);
-    // park the partial sums in this thread's own slots of the spent t0 / t1 planes
-    float* pf = &st.t0[p0];
-    float* pl = &st.t1[p0];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        pf[k] = first[k];
-        pl[k] = open_last ? loc[k] : 0.0f;
-    }
-    consumer_sync();
-    // one warp per ray that spans threads: last part of the head thread plus the
-    // first parts of the following threads up to the tail thread
-    const int e = st.d.e;
-    for (int k = wid; k < e; k += kConsumerWarps) {
-        const int h = st.d.off_rel[k], t = st.d.off_rel[k + 1] - 1;
-        if (t < h) continue;  // empty ray
-        const int th = h >> 3, tt = t >> 3;
-        if (th == tt) continue;  // finished by its thread
-        float v[6] = {0, 0, 0, 0, 0, 0};
-        for (int q = lane; q <= tt - th; q += 32) {
-            const float* src = q == 0 ? &st.t1[th * kItems] : &st.t0[(th + q) * kItems];
-#pragma unroll
-            for (int kk = 0; kk < 6; ++kk) v[kk] += src[kk];
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-            for (int kk = 0; kk < 6; ++kk) v[kk] += __shfl_xor_sync(0xffffffffu, v[kk], o);
-        if (lane == 0) write_ray(A, r0 + k, v);
-    }
+    return e;
 }
 
-// One piece of a long ray (carried scan state).
-//   MODE 0: forward (outputs at the ray's end, weights)
-//   MODE 1: totals only (first pass of the adjoint)
-//   MODE 2: adjoint with suffix = total - inclusive prefix
-template <int MODE, class SM>
-__device__ __noinline__ void long_piece(const RArgs& A, SM& s, Stage& st, const float* pray, Carry& carry, const float* tot) {
-    const int tid = threadIdx.x;
-    const int p0 = tid * kItems;
-    const int o_rel = (int)(st.d.base - st.d.abase);
-    const int pend = o_rel + st.d.n;
-    const long long ray = st.d.r0;
-    const SegView sv = seg_view(st.seg, p0, o_rel, pend);
-    float tau[8], P[8], incl_end;
-    depth_pass(s, st, p0, sv, carry.P, tau, P, incl_end);
-    if (tid == (pend - 1) / kItems) s.carry[0] = incl_end;
-    float a[8], b[8], c[24], w[8];
-    ld8(st.t0, p0, a);
-    ld8(st.t1, p0, b);
-    ld24(st.c, p0, c);
-    Seg<6> loc = seg_zero<6>(-1);
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        w[j] = 0.0f;
-        if (!(sv.valid & (1u << j))) continue;
-        if (sv.head & (1u << j)) loc = seg_zero<6>(0);
-        const bool kept = !(P[j] > A.thr);
-        w[j] = kept ? __expf(-P[j]) * one_minus_exp_neg(tau[j]) : 0.0f;
-        const float m = 0.5f * (a[j] + b[j]);
-        loc.v[0] += w[j] * c[3 * j + 0];
-        loc.v[1] += w[j] * c[3 * j + 1];
-        loc.v[2] += w[j] * c[3 * j + 2];
-        loc.v[3] += w[j];
-        loc.v[4] += w[j] * m;
-        loc.v[5] += kept ? tau[j] : 0.0f;
-    }
-    if (MODE == 0 && A.w_out) st8_global(A.w_out, st.d.abase, p0, sv.valid, w);
-    Seg<6> cin6;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) cin6.v[k] = carry.acc[k];
-    cin6.id = 0;
-    const Seg<6> ex = comb(cin6, block_scan<6, true>(s, loc, 1));
-    const Seg<6> fin = comb(ex, loc);  // inclusive sums at this thread's last item
-    if (MODE == 0 && (sv.tail & sv.valid)) write_ray(A, ray, fin.v);
-    if (MODE == 2) {
-        const float gC0 = pray[0], gC1 = pray[1], gC2 = pray[2], gA = pray[3], gD = pray[4];
-        const float TNtot = __expf(-tot[5]);
-        float run[6];
-#pragma unroll
-        for (int k = 0; k < 6; ++k) run[k] = ex.v[k];
-        float gs[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            gs[j] = 0.0f;
-            if (!(sv.valid & (1u << j))) continue;
-            if (sv.head & (1u << j)) {
-#pragma unroll
-                for (int k = 0; k < 6; ++k) run[k] = 0.0f;
-            }
-            const float cr = c[3 * j], cg = c[3 * j + 1], cb = c[3 * j + 2];
-            const float m = 0.5f * (a[j] + b[j]);
-            run[0] += w[j] * cr;
-            run[1] += w[j] * cg;
-            run[2] += w[j] * cb;
-            run[4] += w[j] * m;
-            const bool kept = !(P[j] > A.thr);
-            float g0 = 0.0f, g1 = 0.0f, g2 = 0.0f;
-            if (kept) {
-                const float Tn = __expf(-(P[j] + tau[j]));
-                const float dt = __fsub_rn(b[j], a[j]);
-                const float g = gC0 * (Tn * cr - (tot[0] - run[0]) - TNtot * A.bg0) +
-                                gC1 * (Tn * cg - (tot[1] - run[1]) - TNtot * A.bg1) +
-                                gC2 * (Tn * cb - (tot[2] - run[2]) - TNtot * A.bg2) + gA * TNtot +
-                                gD * (Tn * m - (tot[4] - run[4]));
-                gs[j] = dt * g;
-                g0 = w[j] * gC0;
-                g1 = w[j] * gC1;
-                g2 = w[j] * gC2;
-            }
-            c[3 * j + 0] = g0;
-            c[3 * j + 1] = g1;
-            c[3 * j + 2] = g2;
-        }
-        st8_global(A.g_sg, st.d.abase, p0, sv.valid, gs);
-        st24_global(A.g_c, st.d.abase, p0, sv.valid, c);
-    }
-    // carry to the next piece: the inclusive sums at the piece's last position
-    if (tid == (pend - 1) / kItems) {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) s.carry[1 + k] = fin.v[k];
-    }
-    consumer_sync();
-    carry.P = s.carry[0];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) carry.acc[k] = s.carry[1 + k];
-    consumer_sync();  // s.carry is rewritten by the next piece
-}
+__global__ void __launch_bounds__(kThreads, 3) k_render_bwd(RArgs A) {
+    const int64_t warps = (int64_t)gridDim.x * kWarps;
+    for (int64_t r = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); r < A.n_rays; r += warps) {
+        const long long s = A.off[r], e = A.off[r + 1];
+        if (e <= s) continue;
+        const long long a = s & ~3ll;
+        const int nch = (int)((e - a + kChunk - 1) / kChunk);
+        const float gC0 = A.g_rgb ? A.g_rgb[3 * r + 0] : 0.0f;
+        const float gC1 = A.g_rgb ? A.g_rgb[3 * r + 1] : 0.0f;
+        const float gC2 = A.g_rgb ? A.g_rgb[3 * r + 2] : 0.0f;
+        const float gA = A.g_op ? A.g_op[r] : 0.0f;
+        const float gD = A.g_dep ? A.g_dep[r] : 0.0f;
 
-// Adjoint of a tile of whole rays: forward scan for T, reverse segmented scan
-// for the suffix sums (with the local id of the segment's tail copied along).
-template <class SM>
-__device__ void bwd_tile(const RArgs& A, SM& s, Stage& st, const float* pray) {
-    const int tid = threadIdx.x;
-    const int p0 = tid * kItems;
-    const int o_rel = (int)(st.d.base - st.d.abase);
-    const int pend = o_rel + st.d.n;
-    const SegView sv = seg_view(st.seg, p0, o_rel, pend);
-    float tau[8], P[8], incl_end;
-    depth_pass(s, st, p0, sv, 0.0f, tau, P, incl_end);
+        float carry, my_carry = 0.0f;
+        int ncut;
+        const long long cut = carry_sweep(A, a, s, e, nch, ((nch - 1) >> 5) << 5, carry, my_carry, ncut);
+        const float TN = __expf(-carry);
+        // g_A T_N - g_C . T_N bg: the part of every kept sample's gradient that
+        // does not depend on the sample
+        const float k0 = TN * (gA - (gC0 * A.bg0 + gC1 * A.bg1 + gC2 * A.bg2));
 
-    float a[8], b[8], c[24];
-    ld8(st.t0, p0, a);
-    ld8(st.t1, p0, b);
-    ld24(st.c, p0, c);
-    float w[8];
-    Seg<5> agg = seg_zero<5>(-1);
-#pragma unroll
-    for (int j = 7; j >= 0; --j) {
-        w[j] = 0.0f;
-        if (!(sv.valid & (1u << j))) continue;
-        if (sv.tail & (1u << j)) agg = seg_zero<5>(tail_id(sv, j));
-        const bool kept = !(P[j] > A.thr);
-        w[j] = kept ? __expf(-P[j]) * one_minus_exp_neg(tau[j]) : 0.0f;
-        const float m = 0.5f * (a[j] + b[j]);
-        agg.v[0] += w[j] * c[3 * j + 0];
-        agg.v[1] += w[j] * c[3 * j + 1];
-        agg.v[2] += w[j] * c[3 * j + 2];
-        agg.v[3] += w[j] * m;
-        agg.v[4] += kept ? tau[j] : 0.0f;
-    }
-    Seg<5> run = block_scan<5, false>(s, agg, 1);
-    ld8(st.t0, p0, a);
-    ld8(st.t1, p0, b);
-    ld24(st.c, p0, c);
-    float gs[8];
-#pragma unroll
-    for (int j = 7; j >= 0; --j) {
-        gs[j] = 0.0f;
-        if (!(sv.valid & (1u << j))) {
-            c[3 * j] = c[3 * j + 1] = c[3 * j + 2] = 0.0f;
-            continue;
-        }
-        if (sv.tail & (1u << j)) run = seg_zero<5>(tail_id(sv, j));
-        const float cr = c[3 * j], cg = c[3 * j + 1], cb = c[3 * j + 2];
-        const float m = 0.5f * (a[j] + b[j]);
-        const bool kept = !(P[j] > A.thr);
-        float g0 = 0.0f, g1 = 0.0f, g2 = 0.0f;
-        if (kept) {
-            const float* pr = &pray[5 * run.id];
-            const float gC0 = pr[0], gC1 = pr[1], gC2 = pr[2], gA = pr[3], gD = pr[4];
-            const float incl = P[j] + tau[j];
-            const float Tn = __expf(-incl);
-            const float TN = __expf(-(incl + run.v[4]));
-            const float dt = __fsub_rn(b[j], a[j]);
-            const float g = gC0 * (Tn * cr - run.v[0] - TN * A.bg0) + gC1 * (Tn * cg - run.v[1] - TN * A.bg1) +
-                            gC2 * (Tn * cb - run.v[2] - TN * A.bg2) + gA * TN + gD * (Tn * m - run.v[3]);
-            gs[j] = dt * g;
-            g0 = w[j] * gC0;
-            g1 = w[j] * gC1;
-            g2 = w[j] * gC2;
-        }
-        run.v[0] += w[j] * cr;
-        run.v[1] += w[j] * cg;
-        run.v[2] += w[j] * cb;
-        run.v[3] += w[j] * m;
-        run.v[4] += kept ? tau[j] : 0.0f;
-        c[3 * j + 0] = g0;
-        c[3 * j + 1] = g1;
-        c[3 * j + 2] = g2;
-    }
-    st8_global(A.g_sg, st.d.abase, p0, sv.valid, gs);
-    st24_global(A.g_c, st.d.abase, p0, sv.valid, c);
-}
-
-template <bool kBwd>
-__device__ void consume(const RArgs& A, Smem<kBwd>& s) {
-    const int tid = threadIdx.x;
-    Carry carry;
-    carry.P = 0.0f;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) carry.acc[k] = 0.0f;
-    float tot[6] = {0, 0, 0, 0, 0, 0};
-    for (int it = 0;; ++it) {
-        const int stg = it % kStages;
-        const uint32_t ph = (uint32_t)(it / kStages) & 1u;
-        const bool got = mbar_wait_bounded(&s.full[stg], ph, kWaitLimitNs);
-        if (!consumer_all(got)) {
-            if (tid == 0) report_timeout();
-            return;
-        }
-        Stage& st = s.st[stg];
-        const float* pray = kBwd ? s.pray[stg] : nullptr;
-        const int kind = st.d.kind;
-        if (kind == kKindDone) return;
-        if (st.d.cend < st.d.base + st.d.n) {  // the arrays' last samples: plain loads
-            load_ragged_end(A, st);
-            consumer_sync();
-        }
-        if (kind == kKindTile) {
-            if (!kBwd && tid < st.d.e && st.d.off_rel[tid + 1] == st.d.off_rel[tid]) {
-                const long long ray = st.d.r0 + tid;  // empty ray
-                A.rgb_out[3 * ray + 0] = A.bg0;
-                A.rgb_out[3 * ray + 1] = A.bg1;
-                A.rgb_out[3 * ray + 2] = A.bg2;
-                A.op_out[ray] = 0.0f;
-                A.dep_out[ray] = 0.0f;
-                A.tr_out[ray] = 1.0f;
+        {  // chunks after the cut: zero gradients
+            const float z[12] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+            for (int c = ncut; c < nch; ++c) {
+                const Group g = group_of(a, c, s, e);
+                store4(A.g_sg, g, z);
+                store4x3(A.g_c, g, z);
             }
-            if (st.d.n > 0) {
-                if (!kBwd)
-                    fwd_tile(A, s, st);
-                else
-                    bwd_tile(A, s, st, pray);
+        }
+        float sc0 = 0.0f, sc1 = 0.0f, sc2 = 0.0f, sm = 0.0f;  // suffix carries of S^c, S^m
+        const int ngroups = (ncut + 31) >> 5;
+        for (int gi = ngroups - 1; gi >= 0; --gi) {
+            if (gi < ngroups - 1) {  // carries of group gi (before any cut)
+                float cy;
+                int nk;
+                carry_sweep(A, a, s, e, 32 * (gi + 1), 32 * gi, cy, my_carry, nk);
             }
-        } else {  // one piece of a long ray (local id 0)
-            const int flags = st.d.flags;
-            if (flags & kFirst) {
-                carry.P = 0.0f;
+            for (int c = min(ncut, 32 * (gi + 1)) - 1; c >= 32 * gi; --c) {
+                const Group g = group_of(a, c, s, e);
+                float t0[4], t1[4], sg[4], rgb[12], tau[4], P[4];
+                load4(A.t0, g, t0);
+                load4(A.t1, g, t1);
+                load4(A.sg, g, sg);
+                load4x3(A.rgb, g, rgb);
+                taus(g, t0, t1, sg, tau);
+                chunk_prefix(tau, __shfl_sync(kFull, my_carry, c & 31), P);
+                float w[4], tn[4], m[4], v[4], suf[4], gs[4], gc[12];
+                bool kept[4];
 #pragma unroll
-                for (int k = 0; k < 6; ++k) carry.acc[k] = 0.0f;
-            }
-            if (!kBwd) {
-                long_piece<0>(A, s, st, pray, carry, nullptr);
-            } else if (!(flags & kPass2)) {
-                long_piece<1>(A, s, st, pray, carry, nullptr);
-                if (flags & kLast) {
-#pragma unroll
-                    for (int k = 0; k < 6; ++k) tot[k] = carry.acc[k];
+                for (int j = 0; j < kPer; ++j) {
+                    kept[j] = (g.in >> j & 1u) && g.p + j < cut;
+                    w[j] = kept[j] ? __expf(-P[j]) * one_minus_exp_neg(tau[j]) : 0.0f;
+                    tn[j] = __expf(-__fadd_rn(P[j], tau[j]));  // T_{i+1}
+                    m[j] = __fmul_rn(__fadd_rn(t0[j], t1[j]), 0.5f);
                 }
-            } else {
-                long_piece<2>(A, s, st, pray, carry, tot);
+                // S^c (per channel) and S^m: suffix sums of the kept w c and w m
+#pragma unroll
+                for (int j = 0; j < kPer; ++j) v[j] = w[j] * rgb[3 * j];
+                sc0 = chunk_suffix(v, sc0, suf);
+#pragma unroll
+                for (int j = 0; j < kPer; ++j) gs[j] = gC0 * (tn[j] * rgb[3 * j] - suf[j]);
+#pragma unroll
+                for (int j = 0; j < kPer; ++j) v[j] = w[j] * rgb[3 * j + 1];
+                sc1 = chunk_suffix(v, sc1, suf);
+#pragma unroll
+                for (int j = 0; j < kPer; ++j) gs[j] += gC1 * (tn[j] * rgb[3 * j + 1] - suf[j]);
+#pragma unroll
+                for (int j = 0; j < kPer; ++j) v[j] = w[j] * rgb[3 * j + 2];
+                sc2 = chunk_suffix(v, sc2, suf);
+#pragma unroll
+                for (int j = 0; j < kPer; ++j) gs[j] += gC2 * (tn[j] * rgb[3 * j + 2] - suf[j]);
+#pragma unroll
+                for (int j = 0; j < kPer; ++j) v[j] = w[j] * m[j];
+                sm = chunk_suffix(v, sm, suf);
+#pragma unroll
+                for (int j = 0; j < kPer; ++j) {
+                    gs[j] += gD * (tn[j] * m[j] - suf[j]) + k0;
+                    gs[j] = kept[j] ? __fsub_rn(t1[j], t0[j]) * gs[j] : 0.0f;
+                    gc[3 * j + 0] = w[j] * gC0;
+                    gc[3 * j + 1] = w[j] * gC1;
+                    gc[3 * j + 2] = w[j] * gC2;
+                }
+                store4(A.g_sg, g, gs);
+                store4x3(A.g_c, g, gc);
             }
         }
-        // each warp releases the stage once it is done with it
-        __syncwarp();
-        if ((tid & 31) == 0) mbar_arrive(&s.empty[stg]);
-    }
-}
-
-// 8 warps x 128 registers: two CTAs (16 warps, 4 per scheduler) resident per SM.
-template <bool kBwd>
-__global__ void __maxnreg__(128) k_render(RArgs A) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    Smem<kBwd>& s = *reinterpret_cast<Smem<kBwd>*>(smem_raw);
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < kStages; ++i) {
-            mbar_init(&s.full[i], 1);
-            mbar_init(&s.empty[i], kConsumerWarps);
-        }
-        fence_barrier_init();
-    }
-    __syncthreads();
-    if (threadIdx.x >= kConsumers) {
-        const int64_t S = __ldg(&A.off[A.n_rays]);
-        const int64_t nchunks = S / kChunk + 1;
-        const int64_t per = (nchunks + gridDim.x - 1) / gridDim.x;
-        const int64_t cb = min64((int64_t)blockIdx.x * per, nchunks);
-        const int64_t ce = min64(cb + per, nchunks);
-        Producer<kBwd> pr{A, s, (long long)(S & ~3ll), 0, true};
-        pr.run(cb, ce);
-    } else {
-        consume<kBwd>(A, s);
     }
 }
 
@@ -940,19 +403,17 @@ __global__ void k_selftest_wait(uint64_t limit_ns) {
     }
     __syncthreads();
     const bool ok = mbar_wait_bounded(&bar, 0u, limit_ns);
-    if (!ok && threadIdx.x == 0) report_timeout();
+    if (!ok && threadIdx.x == 0) atomicOr(&g_nacc_render_status, 1u);
 }
 
-template <bool kBwd>
-int launch_render_t(const RArgs& A, cudaStream_t st) {
-    const size_t smem = sizeof(Smem<kBwd>);
+template <typename K>
+int launch_persistent(K kernel, const RArgs& A, cudaStream_t st) {
     int per_sm = 1;
-    NACC_CUDA_TRY(cudaFuncSetAttribute(k_render<kBwd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    NACC_CUDA_TRY(cudaFuncSetAttribute(k_render<kBwd>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                       (int)cudaSharedmemCarveoutMaxShared));
-    NACC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render<kBwd>, kThreads, smem));
+    NACC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0));
     if (per_sm < 1) per_sm = 1;
-    k_render<kBwd><<<per_sm * sm_count(), kThreads, smem, st>>>(A);
+    const int64_t need = (A.n_rays + kWarps - 1) / kWarps;
+    const int64_t grid = min64((int64_t)per_sm * sm_count(), need);
+    kernel<<<(unsigned)grid, kThreads, 0, st>>>(A);
     NACC_LAUNCH_CHECK();
     return NACC_OK;
 }
@@ -1002,7 +463,7 @@ extern "C" int nacc_render_fwd(int64_t n_rays, const int64_t* offsets, const flo
     A.dep_out = depth_out;
     A.tr_out = trans_out;
     A.w_out = weights_out;
-    return launch_render_t<false>(A, as_stream(stream));
+    return launch_persistent(k_render_fwd, A, as_stream(stream));
 }
 
 extern "C" int nacc_render_bwd(int64_t n_rays, const int64_t* offsets, const float* t_starts,
@@ -1032,7 +493,7 @@ extern "C" int nacc_render_bwd(int64_t n_rays, const int64_t* offsets, const flo
     A.g_dep = g_depth;
     A.g_sg = g_sigmas;
     A.g_c = g_rgbs;
-    return launch_render_t<true>(A, as_stream(stream));
+    return launch_persistent(k_render_bwd, A, as_stream(stream));
 }
 
 extern "C" int nacc_device_status(void* stream, int32_t* status_out) {
