@@ -19,8 +19,9 @@
 //     with P_i > -ln eps).  A ray stops being read at its cut.
 //   * adjoint: a forward pass over tau only records each chunk's carry in one
 //     lane (32 chunks per sweep), then the chunks are visited in reverse and
-//     the suffix sums S^c_i, S^m_i are formed directly as reverse scans (no
-//     total - prefix cancellation).  The forward pass's data is read again
+//     the suffix sums are formed directly as one reverse scan (no total -
+//     prefix cancellation): g_C and g_D are constant along a ray, so
+//     g_C . S^c_i + g_D S^m_i is the suffix sum of w_k (g_C . c_k + g_D m_k).  The forward pass's data is read again
 //     right away, so the second read hits L2 and DRAM sees each byte once.
 //     A ray longer than 32 chunks repeats the carry sweep per group of 32.
 // The kernels hold no locks and wait on nothing; the file also carries the
@@ -304,7 +305,7 @@ __device__ __forceinline__ long long carry_sweep(const RArgs& A, long long a, lo
     return e;
 }
 
-__global__ void __launch_bounds__(kThreads, 3) k_render_bwd(RArgs A) {
+__global__ void __launch_bounds__(kThreads, 4) k_render_bwd(RArgs A) {
     const int64_t warps = (int64_t)gridDim.x * kWarps;
     for (int64_t r = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); r < A.n_rays; r += warps) {
         const long long s = A.off[r], e = A.off[r + 1];
@@ -333,7 +334,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_render_bwd(RArgs A) {
                 store4x3(A.g_c, g, z);
             }
         }
-        float sc0 = 0.0f, sc1 = 0.0f, sc2 = 0.0f, sm = 0.0f;  // suffix carries of S^c, S^m
+        // g_C . S^c_i + g_D S^m_i = U_i, the suffix sum of u_k = w_k q_k with
+        // q_k = g_C . c_k + g_D m_k (g_C, g_D are constant along the ray), so
+        // g_sigma_i = dt_i (T_{i+1} q_i - U_i + k0): one reverse scan.
+        float uc = 0.0f;  // suffix carry of U
         const int ngroups = (ncut + 31) >> 5;
         for (int gi = ngroups - 1; gi >= 0; --gi) {
             if (gi < ngroups - 1) {  // carries of group gi (before any cut)
@@ -350,38 +354,21 @@ __global__ void __launch_bounds__(kThreads, 3) k_render_bwd(RArgs A) {
                 load4x3(A.rgb, g, rgb);
                 taus(g, t0, t1, sg, tau);
                 chunk_prefix(tau, __shfl_sync(kFull, my_carry, c & 31), P);
-                float w[4], tn[4], m[4], v[4], suf[4], gs[4], gc[12];
-                bool kept[4];
+                float w[4], q[4], u[4], U[4], gs[4], gc[12];
+                unsigned kept = 0;
 #pragma unroll
                 for (int j = 0; j < kPer; ++j) {
-                    kept[j] = (g.in >> j & 1u) && g.p + j < cut;
-                    w[j] = kept[j] ? __expf(-P[j]) * one_minus_exp_neg(tau[j]) : 0.0f;
-                    tn[j] = __expf(-__fadd_rn(P[j], tau[j]));  // T_{i+1}
-                    m[j] = __fmul_rn(__fadd_rn(t0[j], t1[j]), 0.5f);
+                    if ((g.in >> j & 1u) && g.p + j < cut) kept |= 1u << j;
+                    w[j] = (kept >> j & 1u) ? __expf(-P[j]) * one_minus_exp_neg(tau[j]) : 0.0f;
+                    const float m = __fmul_rn(__fadd_rn(t0[j], t1[j]), 0.5f);
+                    q[j] = fmaf(gC0, rgb[3 * j], fmaf(gC1, rgb[3 * j + 1], fmaf(gC2, rgb[3 * j + 2], gD * m)));
+                    u[j] = w[j] * q[j];
                 }
-                // S^c (per channel) and S^m: suffix sums of the kept w c and w m
-#pragma unroll
-                for (int j = 0; j < kPer; ++j) v[j] = w[j] * rgb[3 * j];
-                sc0 = chunk_suffix(v, sc0, suf);
-#pragma unroll
-                for (int j = 0; j < kPer; ++j) gs[j] = gC0 * (tn[j] * rgb[3 * j] - suf[j]);
-#pragma unroll
-                for (int j = 0; j < kPer; ++j) v[j] = w[j] * rgb[3 * j + 1];
-                sc1 = chunk_suffix(v, sc1, suf);
-#pragma unroll
-                for (int j = 0; j < kPer; ++j) gs[j] += gC1 * (tn[j] * rgb[3 * j + 1] - suf[j]);
-#pragma unroll
-                for (int j = 0; j < kPer; ++j) v[j] = w[j] * rgb[3 * j + 2];
-                sc2 = chunk_suffix(v, sc2, suf);
-#pragma unroll
-                for (int j = 0; j < kPer; ++j) gs[j] += gC2 * (tn[j] * rgb[3 * j + 2] - suf[j]);
-#pragma unroll
-                for (int j = 0; j < kPer; ++j) v[j] = w[j] * m[j];
-                sm = chunk_suffix(v, sm, suf);
+                uc = chunk_suffix(u, uc, U);
 #pragma unroll
                 for (int j = 0; j < kPer; ++j) {
-                    gs[j] += gD * (tn[j] * m[j] - suf[j]) + k0;
-                    gs[j] = kept[j] ? __fsub_rn(t1[j], t0[j]) * gs[j] : 0.0f;
+                    const float tn = __expf(-__fadd_rn(P[j], tau[j]));  // T_{i+1}
+                    gs[j] = (kept >> j & 1u) ? __fsub_rn(t1[j], t0[j]) * (tn * q[j] - U[j] + k0) : 0.0f;
                     gc[3 * j + 0] = w[j] * gC0;
                     gc[3 * j + 1] = w[j] * gC1;
                     gc[3 * j + 2] = w[j] * gC2;
