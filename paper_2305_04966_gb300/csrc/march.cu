@@ -174,27 +174,34 @@ __device__ __forceinline__ int skip_target(const MarchArgs& A, const Ray& R, int
     return e < (float)kend ? (int)floorf(e) : kend;
 }
 
-// Early-stop density: the blob field of the harness evaluated with fused
-// multiply-adds and the hardware base-2 exponent (exp(a) = 2^(a log2 e), the
-// coefficient pre-scaled by log2 e at staging).  Its relative error, a few
-// 1e-6, moves only stopping decisions whose optical depth is within that of
-// the threshold.
 __device__ __forceinline__ float ex2_approx(float a) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(a));
     return y;
 }
 
-__device__ __forceinline__ float sigma_early_stop(const BlobS* s, int n, float x, float y, float z) {
-    float acc = 0.0f;
-#pragma unroll 4
+// Early-stop density: the blob field of the harness evaluated with fused
+// multiply-adds and the hardware base-2 exponent (exp(a) = 2^(a log2 e), the
+// coefficient pre-scaled by log2 e at staging), at two points per blob load
+// (two buffered samples of a lane share every shared-memory read of the blob
+// parameters).  Its relative error, a few 1e-6, moves only stopping
+// decisions whose optical depth is within that of the threshold.
+__device__ __forceinline__ void sigma_early_stop2(const BlobS* s, int n, const float xa[3], const float xb[3],
+                                                  float& sa, float& sb) {
+    float acc_a = 0.0f, acc_b = 0.0f;
+#pragma unroll 2
     for (int b = 0; b < n; ++b) {
-        const BlobS v = s[b];
-        const float dx = x - v.mx, dy = y - v.my, dz = z - v.mz;
-        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-        acc = fmaf(v.peak, ex2_approx(r2 * v.coef), acc);
+        const float4 v = *reinterpret_cast<const float4*>(&s[b].mx);  // centre, coefficient
+        const float pk = s[b].peak;
+        const float ax = xa[0] - v.x, ay = xa[1] - v.y, az = xa[2] - v.z;
+        const float bx = xb[0] - v.x, by = xb[1] - v.y, bz = xb[2] - v.z;
+        const float ra = fmaf(az, az, fmaf(ay, ay, ax * ax));
+        const float rb = fmaf(bz, bz, fmaf(by, by, bx * bx));
+        acc_a = fmaf(pk, ex2_approx(ra * v.w), acc_a);
+        acc_b = fmaf(pk, ex2_approx(rb * v.w), acc_b);
     }
-    return acc;
+    sa = acc_a;
+    sb = acc_b;
 }
 
 // Per-thread march state of one ray.
@@ -359,7 +366,7 @@ __global__ void __launch_bounds__(256) k_block_summary(GridGeom g, int nb, uint3
 // and each lane folds them into its optical depth in lattice order, stopping
 // at the first sample whose depth before it exceeds the threshold.
 template <bool kField>
-__global__ void __launch_bounds__(kBlockThreads, 10)
+__global__ void __launch_bounds__(kBlockThreads, 8)
     k_march_count(MarchArgs A, int32_t* __restrict__ counts, int32_t* __restrict__ kstops,
                   int32_t* __restrict__ nruns, float* __restrict__ tnear, int2* __restrict__ runs,
                   long long* __restrict__ block_sums) {
@@ -392,22 +399,41 @@ __global__ void __launch_bounds__(kBlockThreads, 10)
             int nmax = bn;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
-            for (int j = 0; j < nmax; ++j) {
+            // two buffered samples per step; the depth is still folded in one
+            // sample at a time, in lattice order (a density evaluated for a
+            // sample past the stop is discarded)
+            for (int j = 0; j < nmax; j += 2) {
                 if (j < bn && !stopped) {
-                    const int k = buf[j];
-                    const float t0 = __fadd_rn(s.R.tn, __fmul_rn((float)k, A.step));
-                    const float t1 = __fadd_rn(t0, A.step);
+                    const bool two = j + 1 < bn;
+                    const int ka = buf[j], kb = two ? buf[j + 1] : ka;
+                    const float ta0 = __fadd_rn(s.R.tn, __fmul_rn((float)ka, A.step));
+                    const float ta1 = __fadd_rn(ta0, A.step);
+                    const float tb0 = __fadd_rn(s.R.tn, __fmul_rn((float)kb, A.step));
+                    const float tb1 = __fadd_rn(tb0, A.step);
+                    const float tma = 0.5f * (ta0 + ta1), tmb = 0.5f * (tb0 + tb1);
+                    float xa[3], xb[3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        xa[a] = fmaf(s.R.d[a], tma, s.R.o[a]);
+                        xb[a] = fmaf(s.R.d[a], tmb, s.R.o[a]);
+                    }
+                    float sga, sgb;
+                    sigma_early_stop2(s_blobs, A.field.n_blobs, xa, xb, sga, sgb);
                     if (tau > A.thr) {
                         stopped = true;
-                        kstop = k;
+                        kstop = ka;
                     } else {
-                        const float tm = __fmul_rn(__fadd_rn(t0, t1), 0.5f);
-                        const float x0 = __fadd_rn(s.R.o[0], __fmul_rn(s.R.d[0], tm));
-                        const float x1 = __fadd_rn(s.R.o[1], __fmul_rn(s.R.d[1], tm));
-                        const float x2 = __fadd_rn(s.R.o[2], __fmul_rn(s.R.d[2], tm));
-                        const float sig = sigma_early_stop(s_blobs, A.field.n_blobs, x0, x1, x2);
-                        tau = __fadd_rn(tau, __fmul_rn(sig, __fsub_rn(t1, t0)));
+                        tau = __fadd_rn(tau, __fmul_rn(sga, __fsub_rn(ta1, ta0)));
                         ++cnt;
+                        if (two) {
+                            if (tau > A.thr) {
+                                stopped = true;
+                                kstop = kb;
+                            } else {
+                                tau = __fadd_rn(tau, __fmul_rn(sgb, __fsub_rn(tb1, tb0)));
+                                ++cnt;
+                            }
+                        }
                     }
                 }
             }
