@@ -60,6 +60,16 @@ int nacc_device_status(void* stream, int32_t* status_out);
  */
 int nacc_selftest_wait_timeout(int64_t limit_ns, void* stream);
 
+/*
+ * Diagnostics: timing of the count pass of nacc_march_grid.  While set (by
+ * the calling host thread), every nacc_march_grid call of that thread records
+ * `before` on its stream just before the count kernel and `after` just after
+ * it, so the caller can read the kernel's duration with cudaEventElapsedTime.
+ * before, after: cudaEvent_t handles created by the caller (NULL, NULL turns
+ * the recording off).  The events are not owned by the library.
+ */
+int nacc_set_march_count_events(void* before, void* after);
+
 #ifdef __cplusplus
 }
 #endif

@@ -64,6 +64,7 @@ SIGNATURES = {
     "nacc_harness_l2_loss": (c_i32, [c_i64, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "nacc_device_status": (c_i32, [c_vp, P(c_i32)]),
     "nacc_selftest_wait_timeout": (c_i32, [c_i64, c_vp]),
+    "nacc_set_march_count_events": (c_i32, [c_vp, c_vp]),
 }
 
 _lib = None

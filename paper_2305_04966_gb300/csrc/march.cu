@@ -609,6 +609,9 @@ __global__ void __launch_bounds__(kBlockThreads)
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// Caller-owned events recorded around the count kernel (diagnostics).
+thread_local cudaEvent_t g_count_ev[2] = {nullptr, nullptr};
+
 }  // namespace
 }  // namespace nacc
 
@@ -707,6 +710,7 @@ extern "C" int nacc_march_grid(const nacc_grid* grid, const float* rays_o, const
         k_block_summary<<<(unsigned)((nblocks + 255) / 256), 256, 0, st>>>(A.g, A.nb, blk);
         NACC_LAUNCH_CHECK();
     }
+    if (g_count_ev[0]) NACC_CUDA_TRY(cudaEventRecord(g_count_ev[0], st));
     if (with_field) {
         const size_t shm = sizeof(BlobS) * (size_t)A.field.n_blobs;
         if (shm > 48 * 1024)
@@ -719,6 +723,7 @@ extern "C" int nacc_march_grid(const nacc_grid* grid, const float* rays_o, const
                                                                       bsums);
     }
     NACC_LAUNCH_CHECK();
+    if (g_count_ev[1]) NACC_CUDA_TRY(cudaEventRecord(g_count_ev[1], st));
     k_scan_block_sums<<<1, 1024, 0, st>>>(bsums, nb, out->offsets + n_rays, out->n_samples);
     NACC_LAUNCH_CHECK();
     k_march_fill<<<(unsigned)nb, kBlockThreads, 0, st>>>(A, counts, kstops, nruns, tnear, runs, bsums,
@@ -738,5 +743,13 @@ extern "C" int nacc_march_grid(const nacc_grid* grid, const float* rays_o, const
             return NACC_ERR_CAPACITY;
         }
     }
+    return NACC_OK;
+}
+
+extern "C" int nacc_set_march_count_events(void* before, void* after) {
+    clear_error();
+    NACC_CHECK_ARG((before == nullptr) == (after == nullptr), "give both events or neither");
+    g_count_ev[0] = static_cast<cudaEvent_t>(before);
+    g_count_ev[1] = static_cast<cudaEvent_t>(after);
     return NACC_OK;
 }

@@ -135,3 +135,9 @@ def test_render_rejects_misaligned_sample_arrays(lib):
     rc = lib.nacc_render_bwd(4, ok, ok, ok, ok, bad, bg, 0.0, None, None, None, ok, ok, None)
     assert rc == _abi.NACC_ERR_INVALID_ARG
     assert lib.nacc_selftest_wait_timeout(0, None) == _abi.NACC_ERR_INVALID_ARG
+
+
+def test_march_count_event_hook_arguments(lib):
+    from paper_2305_04966_gb300 import _abi
+    assert lib.nacc_set_march_count_events(1 << 20, None) == _abi.NACC_ERR_INVALID_ARG
+    assert lib.nacc_set_march_count_events(None, None) == _abi.NACC_OK
