@@ -68,6 +68,7 @@ def parse_args(argv=None):
     ap.add_argument("--height", type=int, default=800)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-aux", action="store_true", help="skip the grid-update / sample_pdf timings")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target oracle CPU time")
     return ap.parse_args(argv)
 
@@ -301,6 +302,53 @@ def count_pass_flop(S: int, n_blobs: int) -> float:
     return float(S) * (11 * n_blobs + 14)
 
 
+def aux_measure(torch, nacc, dev, flush, hbm, steps=10):
+    """The path's other boundary calls at the C3 / C4 sizes, each timed alone
+    with CUDA events (L2 flushed before each call): the jittered cell points
+    and the EMA grid update of a 4x128^3 grid (8,388,608 cells), and inverse-
+    CDF resampling of 262,144 rays from 64 bins to 32 (stratified).  Inputs are
+    seeded synthetic tensors; the algorithmic bytes are per cell / per ray."""
+    g = torch.Generator(device=dev)
+    g.manual_seed(0x5EED)
+    grid = nacc.OccupancyGrid.empty((-1.5,) * 3, (1.5,) * 3, 128, 4, dev)
+    nc = grid.n_cells
+    dens = torch.rand(nc, generator=g, device=dev) * 10.0
+    ubuf = nacc.UpdateBuffers(nc, dev)
+    pts = torch.empty((nc, 3), dtype=torch.float32, device=dev)
+    nr, nb, no = 262144, 64, 32
+    edges = 2.0 + 4.0 * torch.sort(torch.rand((nr, nb + 1), generator=g, device=dev), dim=1).values
+    weights = torch.rand((nr, nb), generator=g, device=dev)
+    outp = torch.empty((nr, no + 1), dtype=torch.float32, device=dev)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        evs = []
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs) / steps
+
+    def entry(ms, nbytes, **kw):
+        gbs = nbytes / (ms / 1000.0) / 1e9
+        return dict(kw, ms=ms, algorithmic_bytes=nbytes, **{"GB/s": gbs}, frac=gbs / hbm)
+
+    t_pts = timed(lambda: nacc.grid_points(grid, 7, 1, True, out=pts))
+    t_upd = timed(lambda: nacc.update_grid(grid, dens, 0.95, 0.01, 0.0, buffers=ubuf))
+    t_pdf = timed(lambda: nacc.sample_pdf(edges, weights, no, True, 5, out=outp))
+    return {
+        "grid_points": entry(t_pts, 12 * nc, cells=nc, bytes_per_cell=12),
+        "update_grid": entry(t_upd, 16.125 * nc, cells=nc, bytes_per_cell=16.125),
+        "sample_pdf": entry(t_pdf, (4 * (2 * nb + 1) + 4 * (no + 1)) * nr, rays=nr, bins=nb, n_out=no,
+                            bytes_per_ray=4 * (2 * nb + 1) + 4 * (no + 1)),
+    }
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -433,6 +481,9 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e:
         e2e = e2e_measure(args, torch, nacc, step, w, dev, n, flush, dist)
+    aux = None
+    if rank == 0 and not args.no_aux:
+        aux = aux_measure(torch, nacc, dev, flush, hbm)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -454,6 +505,7 @@ def run_ours(args):
                               "frac": path_ach / hbm, "stages": list(BYTES), "ms": path_ms,
                               "algorithmic_bytes": path_bytes, "peak_source": peak_src},
             "stage_roofline": stage_roof,
+            "aux": aux,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clocks,

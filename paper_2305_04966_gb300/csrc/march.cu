@@ -38,7 +38,7 @@
 namespace nacc {
 namespace {
 
-constexpr int kBlockThreads = 128;              // one ray per thread
+constexpr int kBlockThreads = 32;               // one ray per thread; one warp per block
 constexpr int kRaysPerBlock = kBlockThreads;    // rays per block-sum entry
 constexpr int kWarpsPerBlock = kBlockThreads / 32;
 constexpr int kBuf = 32;                        // lattice indices buffered per lane
@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(256) k_block_summary(GridGeom g, int nb, uint3
 // and each lane folds them into its optical depth in lattice order, stopping
 // at the first sample whose depth before it exceeds the threshold.
 template <bool kField>
-__global__ void __launch_bounds__(kBlockThreads, 8)
+__global__ void __launch_bounds__(kBlockThreads, 32)
     k_march_count(MarchArgs A, int32_t* __restrict__ counts, int32_t* __restrict__ kstops,
                   int32_t* __restrict__ nruns, float* __restrict__ tnear, int2* __restrict__ runs,
                   long long* __restrict__ block_sums) {
