@@ -176,7 +176,7 @@ int nacc_update_grid(const nacc_grid* grid, float* ema, const float* density, fl
  *  - Limit: n_levels*res^3 <= 134,217,728 cells (2^27, e.g. 8 levels of
  *    256^3); larger grids are rejected with NACC_ERR_INVALID_ARG and a
  *    message naming the limit.
- *  - The array (512 KiB + 16 B) is held by every GPU that loads the library,
+ *  - The array (512 KiB + 24 B) is held by every GPU that loads the library,
  *    until the process exits.
  *  - The first call on each device looks up the array's device address for
  *    that device (with the device current); make that first call before any

@@ -16,14 +16,17 @@ constexpr int kEmaThreads = 256;
 constexpr int kEmaItems = 8;  // cells per thread
 constexpr int kEmaCells = kEmaThreads * kEmaItems;
 
+template <typename I>  // index type: uint32_t when every cell index fits, else int64_t
 __global__ void __launch_bounds__(256)
     k_grid_points(GridGeom g, uint64_t key, int jitter, int64_t n_cells, float* __restrict__ xyz) {
-    const int64_t r3 = (int64_t)g.res * g.res * g.res;
+    const I res = (I)g.res, r2 = res * res, r3 = r2 * res;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cells;
          c += (int64_t)gridDim.x * blockDim.x) {
-        const int l = (int)(c / r3);
-        const int64_t w = c - (int64_t)l * r3;
-        const int64_t i[3] = {w / ((int64_t)g.res * g.res), (w / g.res) % g.res, w % g.res};
+        const I ci = (I)c;
+        const int l = (int)(ci / r3);
+        const I w = ci - (I)l * r3;
+        const I x = w / r2, yz = w - x * r2, y = yz / res;
+        const int64_t i[3] = {(int64_t)x, (int64_t)y, (int64_t)(yz - y * res)};
         const Level& lv = g.lv[l];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -63,6 +66,65 @@ __global__ void __launch_bounds__(kEmaThreads)
     }
 }
 
+// The same EMA with 128-bit accesses (ema, dens 16-byte aligned; n a
+// multiple of 4): thread t of block b owns the float4 groups
+// b*kEmaCells/4 + j*kEmaThreads + t, j < kEmaItems/4 -- the same cells per
+// block, so the per-block partial sums cover the same cells.
+__global__ void __launch_bounds__(kEmaThreads)
+    k_ema4(float* __restrict__ ema, const float* __restrict__ dens, float decay, float omd, int64_t n,
+           double* __restrict__ partial) {
+    const int64_t base = (int64_t)blockIdx.x * (kEmaCells / 4);
+    const int64_t n4 = n / 4;
+    float4* e4 = reinterpret_cast<float4*>(ema);
+    const float4* d4 = reinterpret_cast<const float4*>(dens);
+    float4 ev[kEmaItems / 4], dv[kEmaItems / 4];
+#pragma unroll
+    for (int j = 0; j < kEmaItems / 4; ++j) {
+        const int64_t q = base + j * kEmaThreads + threadIdx.x;
+        if (q < n4) {
+            ev[j] = e4[q];
+            dv[j] = __ldcs(d4 + q);
+        }
+    }
+    // the thread's 8 cells summed in FP32 with Neumaier's compensation, then
+    // converted to FP64 once (error ~n u^2 of the sum: FP64-grade without a
+    // slow FP64 conversion and add per cell)
+    float sh = 0.0f, sc = 0.0f;
+    auto add = [&](float v) {
+        const float t = sh + v;
+        sc += fabsf(sh) >= fabsf(v) ? (sh - t) + v : (v - t) + sh;
+        sh = t;
+    };
+#pragma unroll
+    for (int j = 0; j < kEmaItems / 4; ++j) {
+        const int64_t q = base + j * kEmaThreads + threadIdx.x;
+        if (q < n4) {
+            float4 r;
+            r.x = __fadd_rn(__fmul_rn(decay, ev[j].x), __fmul_rn(omd, dv[j].x));
+            r.y = __fadd_rn(__fmul_rn(decay, ev[j].y), __fmul_rn(omd, dv[j].y));
+            r.z = __fadd_rn(__fmul_rn(decay, ev[j].z), __fmul_rn(omd, dv[j].z));
+            r.w = __fadd_rn(__fmul_rn(decay, ev[j].w), __fmul_rn(omd, dv[j].w));
+            e4[q] = r;
+            add(r.x);
+            add(r.y);
+            add(r.z);
+            add(r.w);
+        }
+    }
+    double acc = (double)sh + (double)sc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    __shared__ double s_w[kEmaThreads / 32];
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < kEmaThreads / 32; ++w) t += s_w[w];
+        partial[blockIdx.x] = t;
+    }
+}
+
 // One block: mean = sum(partial) / n; thr = max(thresh_abs, thresh_frac*mean).
 __global__ void __launch_bounds__(1024)
     k_mean_thr(const double* __restrict__ partial, int64_t nb, int64_t n, double thresh_frac,
@@ -80,21 +142,78 @@ __global__ void __launch_bounds__(1024)
         double mean = n > 0 ? t / (double)n : 0.0;
         double thr = thresh_frac * mean;
         if (thresh_abs > thr) thr = thresh_abs;
+        // largest float <= thr: for a float e, (double)e > thr <=> e > thr32
+        float thr32 = (float)thr;
+        if ((double)thr32 > thr) thr32 = nextafterf(thr32, -INFINITY);
         out[0] = mean;
         out[1] = thr;
+        out[2] = (double)thr32;
     }
 }
 
 __global__ void __launch_bounds__(256)
     k_pack_bits(const float* __restrict__ ema, int64_t n, const double* __restrict__ mt,
                 uint32_t* __restrict__ bits) {
-    const double thr = mt[1];
+    const float thr = (float)mt[2];
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n;
          c += (int64_t)gridDim.x * blockDim.x) {
-        bool occ = (double)ema[c] > thr;
+        bool occ = ema[c] > thr;
         unsigned m = __ballot_sync(0xffffffffu, occ);
         if ((threadIdx.x & 31) == 0) bits[c >> 5] = m;
     }
+}
+
+// The same packing with each thread building its own word from 32
+// consecutive cells read as eight float4 (ema 16-byte aligned, n a multiple
+// of 32).
+__global__ void __launch_bounds__(256)
+    k_pack_bits4(const float* __restrict__ ema, int64_t n, const double* __restrict__ mt,
+                 uint32_t* __restrict__ bits) {
+    const float thr = (float)mt[2];
+    const int64_t words = n / 32;
+    const float4* e4 = reinterpret_cast<const float4*>(ema);
+    for (int64_t wd = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; wd < words;
+         wd += (int64_t)gridDim.x * blockDim.x) {
+        float4 v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = __ldcs(e4 + 8 * wd + j);
+        uint32_t m = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            m |= (v[j].x > thr ? 1u : 0u) << (4 * j);
+            m |= (v[j].y > thr ? 1u : 0u) << (4 * j + 1);
+            m |= (v[j].z > thr ? 1u : 0u) << (4 * j + 2);
+            m |= (v[j].w > thr ? 1u : 0u) << (4 * j + 3);
+        }
+        bits[wd] = m;
+    }
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+// EMA -> mean and threshold -> bits, on caller scratch or the library's own.
+int launch_update(float* ema, const float* density, float decay, int64_t n, double thresh_frac,
+                  double thresh_abs, uint32_t* bits_out, double* partial, double* mt, cudaStream_t st) {
+    const int64_t nb = (n + kEmaCells - 1) / kEmaCells;
+    volatile float omd = 1.0f - decay;
+    const bool vec = aligned16(ema) && aligned16(density) && n % 4 == 0;
+    if (vec)
+        k_ema4<<<(unsigned)nb, kEmaThreads, 0, st>>>(ema, density, decay, omd, n, partial);
+    else
+        k_ema<<<(unsigned)nb, kEmaThreads, 0, st>>>(ema, density, decay, omd, n, partial);
+    NACC_LAUNCH_CHECK();
+    k_mean_thr<<<1, 1024, 0, st>>>(partial, nb, n, thresh_frac, thresh_abs, mt);
+    NACC_LAUNCH_CHECK();
+    if (aligned16(ema)) {
+        const int64_t words = n / 32;
+        const int blocks = (int)std::min<int64_t>((words + 255) / 256, (int64_t)sm_count() * 8);
+        k_pack_bits4<<<blocks, 256, 0, st>>>(ema, n, mt, bits_out);
+    } else {
+        const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 16);
+        k_pack_bits<<<blocks, 256, 0, st>>>(ema, n, mt, bits_out);
+    }
+    NACC_LAUNCH_CHECK();
+    return NACC_OK;
 }
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -113,7 +232,10 @@ extern "C" int nacc_grid_points(const nacc_grid* grid, uint64_t seed, int64_t st
     const int64_t n = (int64_t)g.n_levels * g.res * g.res * g.res;
     const uint64_t key = seed ^ ((uint64_t)step << 32);
     int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 16);
-    k_grid_points<<<blocks, 256, 0, as_stream(stream)>>>(g, key, jitter ? 1 : 0, n, xyz_out);
+    if (n <= (int64_t)0xffffffffll)
+        k_grid_points<uint32_t><<<blocks, 256, 0, as_stream(stream)>>>(g, key, jitter ? 1 : 0, n, xyz_out);
+    else
+        k_grid_points<int64_t><<<blocks, 256, 0, as_stream(stream)>>>(g, key, jitter ? 1 : 0, n, xyz_out);
     NACC_LAUNCH_CHECK();
     return NACC_OK;
 }
@@ -121,7 +243,7 @@ extern "C" int nacc_grid_points(const nacc_grid* grid, uint64_t seed, int64_t st
 extern "C" size_t nacc_update_grid_scratch_bytes(int64_t n_cells) {
     if (n_cells < 0) return 0;
     int64_t nb = (n_cells + kEmaCells - 1) / kEmaCells;
-    return align256(sizeof(double) * (size_t)(nb > 0 ? nb : 1)) + align256(2 * sizeof(double));
+    return align256(sizeof(double) * (size_t)(nb > 0 ? nb : 1)) + align256(3 * sizeof(double));
 }
 
 extern "C" int nacc_update_grid(const nacc_grid* grid, float* ema, const float* density,
@@ -142,16 +264,8 @@ extern "C" int nacc_update_grid(const nacc_grid* grid, float* ema, const float* 
     const int64_t nb = (n + kEmaCells - 1) / kEmaCells;
     double* partial = static_cast<double*>(scratch);
     double* mt = reinterpret_cast<double*>(static_cast<char*>(scratch) + align256(sizeof(double) * (size_t)nb));
-    cudaStream_t st = as_stream(stream);
-    volatile float omd = 1.0f - decay;
-    k_ema<<<(unsigned)nb, kEmaThreads, 0, st>>>(ema, density, decay, omd, n, partial);
-    NACC_LAUNCH_CHECK();
-    k_mean_thr<<<1, 1024, 0, st>>>(partial, nb, n, (double)thresh_frac, (double)thresh_abs, mt);
-    NACC_LAUNCH_CHECK();
-    int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 16);
-    k_pack_bits<<<blocks, 256, 0, st>>>(ema, n, mt, bits_out);
-    NACC_LAUNCH_CHECK();
-    return NACC_OK;
+    return launch_update(ema, density, decay, n, (double)thresh_frac, (double)thresh_abs, bits_out, partial, mt,
+                         as_stream(stream));
 }
 
 // ---------------------------------------------------------------------------
@@ -175,8 +289,8 @@ constexpr int kNoAllocMaxDevices = 64;
 }  // namespace
 }  // namespace nacc
 
-// 65,536 FP64 partial sums + mean + threshold: 512 KiB + 16 B per device.
-static __device__ __align__(256) double nacc_update_noalloc_scratch[nacc::kNoAllocMaxBlocks + 2];
+// 65,536 FP64 partial sums + mean + threshold (FP64 and FP32): 512 KiB + 24 B per device.
+static __device__ __align__(256) double nacc_update_noalloc_scratch[nacc::kNoAllocMaxBlocks + 3];
 
 namespace nacc {
 namespace {
@@ -230,15 +344,6 @@ extern "C" int nacc_update_grid_noalloc(const nacc_grid* grid, float* ema, const
     // threshold) before k_pack_bits reads them, so nothing needs clearing.
     double* partial = scratch;
     double* mt = scratch + kNoAllocMaxBlocks;
-    const int64_t nb = (n + kEmaCells - 1) / kEmaCells;
-    cudaStream_t st = as_stream(stream);
-    volatile float omd = 1.0f - decay;
-    k_ema<<<(unsigned)nb, kEmaThreads, 0, st>>>(ema, density, decay, omd, n, partial);
-    NACC_LAUNCH_CHECK();
-    k_mean_thr<<<1, 1024, 0, st>>>(partial, nb, n, (double)thresh_frac, (double)thresh_abs, mt);
-    NACC_LAUNCH_CHECK();
-    int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 16);
-    k_pack_bits<<<blocks, 256, 0, st>>>(ema, n, mt, bits_out);
-    NACC_LAUNCH_CHECK();
-    return NACC_OK;
+    return launch_update(ema, density, decay, n, (double)thresh_frac, (double)thresh_abs, bits_out, partial, mt,
+                         as_stream(stream));
 }

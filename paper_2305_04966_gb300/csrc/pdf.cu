@@ -5,8 +5,8 @@
 // One thread per ray walks bins and outputs together (both are monotone), so
 // no per-ray CDF array is stored: F_j is formed on the fly with exactly the
 // sequential FP32 prefix sums of the definition, and the bin of u_k is the
-// largest j with F_j <= u_k and F_j < 1.  The rows of a CTA's rays are
-// staged through shared memory with coalesced loads when they fit.
+// largest j with F_j <= u_k and F_j < 1.  The weight rows of a CTA's rays
+// are staged through shared memory with coalesced loads when they fit.
 #include "nacc_internal.cuh"
 
 namespace nacc {
@@ -25,46 +25,70 @@ struct PdfArgs {
     int staged;  // rows staged in shared memory
 };
 
-__global__ void __launch_bounds__(kPdfThreads) k_sample_pdf(PdfArgs A) {
-    extern __shared__ float s_rows[];
-    const int nb = A.n_bins, no = A.n_out;
-    const int ew = nb + 1, ww = nb;
-    const int64_t r0 = (int64_t)blockIdx.x * kPdfThreads;
-    const int64_t left = A.n_rays - r0;
-    const int nr = left < kPdfThreads ? (int)left : kPdfThreads;
-    const float* E;
-    const float* W;
-    int es, ws;  // row strides
-    if (A.staged) {
-        // stage rows [r0, r0+nr): edges then weights, row strides ew|1, ww|1 (odd: no conflicts)
-        const int se = ew | 1, sw = ww | 1;
-        float* sE = s_rows;
-        float* sW = s_rows + kPdfThreads * se;
-        const float* gE = A.edges + r0 * ew;
-        const float* gW = A.weights + r0 * ww;
-        for (int q = threadIdx.x; q < nr * ew; q += kPdfThreads) {
-            int rr = q / ew;
-            sE[rr * se + (q - rr * ew)] = __ldcs(gE + q);
+// Copies nr contiguous rows of length w between global memory (row stride
+// w) and shared memory (row stride ws), in either direction, with eight
+// accesses in flight per thread.  Equal strides: one flat copy.  Otherwise
+// each warp copies 32-column pieces of whole rows (one division per piece).
+template <bool kToShared>
+__device__ __forceinline__ void copy_rows(float* g, int nr, int w, float* s, int ws) {
+    constexpr int kU = 8;
+    if (ws == w) {
+        const int n = nr * w;
+        for (int q0 = threadIdx.x; q0 < n; q0 += kU * kPdfThreads) {
+            float v[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int q = q0 + u * kPdfThreads;
+                if (q < n) v[u] = kToShared ? __ldcs(g + q) : s[q];
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int q = q0 + u * kPdfThreads;
+                if (q < n) {
+                    if (kToShared)
+                        s[q] = v[u];
+                    else
+                        g[q] = v[u];
+                }
+            }
         }
-        for (int q = threadIdx.x; q < nr * ww; q += kPdfThreads) {
-            int rr = q / ww;
-            sW[rr * sw + (q - rr * ww)] = __ldcs(gW + q);
-        }
-        __syncthreads();
-        E = sE + threadIdx.x * se;
-        W = sW + threadIdx.x * sw;
-        es = se;
-        ws = sw;
-    } else {
-        E = A.edges + (r0 + threadIdx.x) * ew;
-        W = A.weights + (r0 + threadIdx.x) * ww;
-        es = ew;
-        ws = ww;
+        return;
     }
-    (void)es;
-    (void)ws;
-    if (threadIdx.x >= nr) return;
-    const int64_t r = r0 + threadIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = kPdfThreads / 32;
+    const int nch = (w + 31) / 32, items = nr * nch;
+    for (int i0 = wid; i0 < items; i0 += kU * nw) {
+        float v[kU];
+        int gi[kU], si[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int i = i0 + u * nw;
+            gi[u] = -1;
+            if (i < items) {
+                const int rr = i / nch;
+                const int col = (i - rr * nch) * 32 + lane;
+                if (col < w) {
+                    gi[u] = rr * w + col;
+                    si[u] = rr * ws + col;
+                    v[u] = kToShared ? __ldcs(g + gi[u]) : s[si[u]];
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            if (gi[u] >= 0) {
+                if (kToShared)
+                    s[si[u]] = v[u];
+                else
+                    g[gi[u]] = v[u];
+            }
+        }
+    }
+}
+
+// The walk of one ray; outputs to `o` (shared memory) or, if NULL, to the
+// ray's global output row.
+__device__ __forceinline__ void sample_one(const PdfArgs& A, int64_t r, const float* E, const float* W, float* o) {
+    const int nb = A.n_bins, no = A.n_out;
     float tot = 0.0f;
     for (int j = 0; j < nb; ++j) tot = __fadd_rn(tot, W[j]);
     const bool uni = !(tot > 0.0f);
@@ -81,7 +105,7 @@ __global__ void __launch_bounds__(kPdfThreads) k_sample_pdf(PdfArgs A) {
         return __fdiv_rn(c, tot);
     };
     float Fn = F_of(1, cn);
-    float* out = A.out + r * (no + 1);
+    float* out = o ? o : A.out + r * (no + 1);
     for (int k = 0; k <= no; ++k) {
         float u = __fdiv_rn((float)k, fno);
         if (A.stratified && k > 0 && k < no) {
@@ -107,6 +131,31 @@ __global__ void __launch_bounds__(kPdfThreads) k_sample_pdf(PdfArgs A) {
     }
 }
 
+__global__ void __launch_bounds__(kPdfThreads) k_sample_pdf(PdfArgs A) {
+    extern __shared__ float s_rows[];
+    const int nb = A.n_bins;
+    const int ew = nb + 1, ww = nb;
+    const int64_t r0 = (int64_t)blockIdx.x * kPdfThreads;
+    const int64_t left = A.n_rays - r0;
+    const int nr = left < kPdfThreads ? (int)left : kPdfThreads;
+    const float* E;
+    const float* W;
+    // the weights, read in sequence by the walk, are staged (row stride
+    // ww|1, odd: no bank conflicts); the edges are read twice per output
+    // straight from global memory (each row stays in L1), the outputs are
+    // stored directly: small shared memory keeps many warps resident
+    E = A.edges + (r0 + threadIdx.x) * ew;
+    if (A.staged) {
+        const int sw = ww | 1;
+        copy_rows<true>(const_cast<float*>(A.weights + r0 * ww), nr, ww, s_rows, sw);
+        __syncthreads();
+        W = s_rows + threadIdx.x * sw;
+    } else {
+        W = A.weights + (r0 + threadIdx.x) * ww;
+    }
+    if (threadIdx.x < nr) sample_one(A, r0 + threadIdx.x, E, W, nullptr);
+}
+
 }  // namespace
 }  // namespace nacc
 
@@ -122,7 +171,7 @@ extern "C" int nacc_sample_pdf(int64_t n_rays, int32_t n_bins, const float* edge
     if (n_rays == 0) return NACC_OK;
     NACC_CHECK_ARG(edges && weights && edges_out, "edges / weights / edges_out is NULL");
     PdfArgs A{n_rays, n_bins, n_out, edges, weights, edges_out, stratified ? 1 : 0, seed, 0};
-    size_t shm = (size_t)kPdfThreads * (size_t)(((n_bins + 1) | 1) + (n_bins | 1)) * sizeof(float);
+    size_t shm = (size_t)kPdfThreads * (size_t)(n_bins | 1) * sizeof(float);
     if (shm <= 96 * 1024) {
         A.staged = 1;
         if (shm > 48 * 1024)
