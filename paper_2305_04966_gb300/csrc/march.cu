@@ -23,8 +23,9 @@
 //     exit: k < floor(q + 1/2 - slack) with q = (t_exit - t_near)/dt and a
 //     slack of 1/64 step plus 2^-16 (|q| + |t_near|/dt) for the rounding of
 //     t0, t1, the midpoint and q (at least 16x their bound).
-// An empty cell inside an empty 8^3 block of cells (a per-call summary of the
-// bits) skips the whole block: the same argument holds for any box of cells.
+// A cell inside an empty (or a fully occupied) 8^3 block of cells (per-call
+// summaries of the bits) runs to the block's exit: the same argument holds
+// for any box of cells whose bits all agree.
 // Empty runs are skipped; occupied runs are emitted point by point with only
 // their t0 / t1 arithmetic (plus the field for early termination), so the
 // emitted set equals the dense march's at a fraction of its cost.  With a
@@ -59,7 +60,8 @@ struct MarchArgs {
     float inv_step;  // 1/step, only for the conservative skip (never for lattice values)
     int idx32;       // every flat cell index fits 32 bits
     float skip_lim[NACC_MAX_LEVELS];  // skip allowed at level l iff max|o| <= skip_lim[l]
-    const uint32_t* blk;  // empty-block summary: bit set iff any cell of the kBlk^3 block is occupied
+    const uint32_t* blk;   // block summary: bit set iff any cell of the kBlk^3 block is occupied
+    const uint32_t* blkf;  // block summary: bit set iff every cell of the block is occupied
     int nb;               // blocks per axis, ceil(res / kBlk)
     nacc_blob_field field;
 };
@@ -283,10 +285,12 @@ __device__ void advance(const MarchArgs& A, Lane& s, int kend, int limit, int* b
             }
             if (l < L) {
                 int lo[3] = {ic[0], ic[1], ic[2]}, hi[3] = {ic[0], ic[1], ic[2]};
-                if (!occ && A.blk) {  // an empty cell in an empty block: skip the whole block
+                if (A.blk) {  // a cell in an empty (or a full) block: the run spans the block
                     const uint32_t b = ((uint32_t)l * A.nb + ic[0] / kBlk) * A.nb * A.nb +
                                        (uint32_t)(ic[1] / kBlk) * A.nb + ic[2] / kBlk;
-                    if (!((__ldg(&A.blk[b >> 5]) >> (b & 31)) & 1u)) {
+                    const uint32_t* sum = occ ? A.blkf : A.blk;
+                    const bool bit = (__ldg(&sum[b >> 5]) >> (b & 31)) & 1u;
+                    if (occ == bit) {
 #pragma unroll
                         for (int a = 0; a < 3; ++a) {
                             lo[a] = ic[a] / kBlk * kBlk;
@@ -330,10 +334,11 @@ __device__ void advance(const MarchArgs& A, Lane& s, int kend, int limit, int* b
 // divide res), set iff any cell of the block is occupied.  Block b =
 // (l*nb + bx)*nb*nb + by*nb + bz.  An acceleration structure only: a run
 // that stays inside an empty block skips every cell of it.
-__global__ void __launch_bounds__(256) k_block_summary(GridGeom g, int nb, uint32_t* __restrict__ blk) {
+__global__ void __launch_bounds__(256)
+    k_block_summary(GridGeom g, int nb, uint32_t* __restrict__ blk, uint32_t* __restrict__ blkf) {
     const uint64_t nblocks = (uint64_t)g.n_levels * nb * nb * nb;
     const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    bool any = false;
+    bool any = false, all = b < nblocks;
     if (b < nblocks) {
         const int res = g.res;
         const uint64_t per_level = (uint64_t)nb * nb * nb;
@@ -343,22 +348,26 @@ __global__ void __launch_bounds__(256) k_block_summary(GridGeom g, int nb, uint3
         const int x1 = min(bx * kBlk + kBlk, res), y1 = min(by * kBlk + kBlk, res);
         const int z0 = bz * kBlk, nz = min(z0 + kBlk, res) - z0;
         const uint64_t r3 = (uint64_t)res * res * res;
-        for (int x = bx * kBlk; x < x1 && !any; ++x) {
+        const uint64_t mask = (1ull << nz) - 1;
+        for (int x = bx * kBlk; x < x1; ++x) {
             for (int y = by * kBlk; y < y1; ++y) {
                 const uint64_t i0 = (uint64_t)l * r3 + ((uint64_t)x * res + y) * res + z0;
                 const uint64_t w = i0 >> 5;
                 const int off = (int)(i0 & 31);
                 uint64_t bits = g.bits[w];
                 if (off + nz > 32) bits |= (uint64_t)g.bits[w + 1] << 32;
-                if ((bits >> off) & ((1ull << nz) - 1)) {
-                    any = true;
-                    break;
-                }
+                const uint64_t row = (bits >> off) & mask;
+                any = any || row != 0;
+                all = all && row == mask;
             }
         }
     }
     const unsigned m = __ballot_sync(0xffffffffu, any);
-    if ((threadIdx.x & 31) == 0 && b < nblocks) blk[b >> 5] = m;
+    const unsigned mf = __ballot_sync(0xffffffffu, all);
+    if ((threadIdx.x & 31) == 0 && b < nblocks) {
+        blk[b >> 5] = m;
+        blkf[b >> 5] = mf;
+    }
 }
 
 // Count pass.  Each lane marches into its buffer; with a field the warp
@@ -622,7 +631,7 @@ extern "C" size_t nacc_march_scratch_bytes(int64_t n_rays) {
     const int64_t nb = (n_rays + kRaysPerBlock - 1) / kRaysPerBlock;
     // counts, kstops, nruns, tnear, block sums, run slots
     return align256(4 * (size_t)n_rays) * 4 + align256(8 * (size_t)(nb > 0 ? nb : 1)) +
-           align256(sizeof(int2) * kRunSlots * (size_t)n_rays) + kBlockBitsBytes;
+           align256(sizeof(int2) * kRunSlots * (size_t)n_rays) + 2 * kBlockBitsBytes;
 }
 
 extern "C" int nacc_march_grid(const nacc_grid* grid, const float* rays_o, const float* rays_d,
@@ -700,14 +709,16 @@ extern "C" int nacc_march_grid(const nacc_grid* grid, const float* rays_o, const
     int2* runs = reinterpret_cast<int2*>(sp);
     sp += align256(sizeof(int2) * kRunSlots * (size_t)n_rays);
     uint32_t* blk = reinterpret_cast<uint32_t*>(sp);
+    uint32_t* blkf = reinterpret_cast<uint32_t*>(sp + kBlockBitsBytes);
 
     const int64_t nb = (n_rays + kRaysPerBlock - 1) / kRaysPerBlock;
     NACC_CHECK_ARG(nb < (int64_t(1) << 31), "too many rays for one launch");
     A.nb = (A.g.res + kBlk - 1) / kBlk;
     A.blk = blk;
+    A.blkf = blkf;
     {
         const uint64_t nblocks = (uint64_t)A.g.n_levels * A.nb * A.nb * A.nb;
-        k_block_summary<<<(unsigned)((nblocks + 255) / 256), 256, 0, st>>>(A.g, A.nb, blk);
+        k_block_summary<<<(unsigned)((nblocks + 255) / 256), 256, 0, st>>>(A.g, A.nb, blk, blkf);
         NACC_LAUNCH_CHECK();
     }
     if (g_count_ev[0]) NACC_CUDA_TRY(cudaEventRecord(g_count_ev[0], st));
