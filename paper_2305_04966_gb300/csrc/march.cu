@@ -206,6 +206,54 @@ __device__ __forceinline__ void sigma_early_stop2(const BlobS* s, int n, const f
     sb = acc_b;
 }
 
+// Early-stop density for fields of few blobs, set up per ray: along the ray
+// x(t) = o + t d, |x(t) - mu_b|^2 = |d|^2 (t - t*_b)^2 + p_b^2 with the
+// closest approach t*_b = (mu_b - o).d / |d|^2 and p_b^2 = |(mu_b - o) x d|^2
+// / |d|^2 (cross product: no cancellation near the centre).  Each lane keeps
+// {A_b = c_b |d|^2, t*_b, C_b = c_b p_b^2, peak_b} (c_b the log2-scaled
+// coefficient) in shared memory, and a sample costs one 128-bit load, three
+// FP32 operations, one exp2 and one FMA per blob.  Rounding of t - t*_b is
+// of the order of that of the position in the direct form.
+constexpr int kRayBlobsMax = 16;
+
+__device__ __forceinline__ void ray_blobs_setup(const BlobS* sb, int n, const float o[3], const float d[3],
+                                                float4* q) {
+    const int lane = threadIdx.x & 31;
+    const float dd = fmaf(d[2], d[2], fmaf(d[1], d[1], d[0] * d[0]));
+    const float idd = dd > 0.0f ? 1.0f / dd : 0.0f;
+    for (int b = 0; b < n; ++b) {
+        const BlobS v = sb[b];
+        const float m0 = v.mx - o[0], m1 = v.my - o[1], m2 = v.mz - o[2];
+        float ts, pp;
+        if (dd > 0.0f) {
+            const float md = fmaf(m2, d[2], fmaf(m1, d[1], m0 * d[0]));
+            const float cx = fmaf(m1, d[2], -m2 * d[1]);
+            const float cy = fmaf(m2, d[0], -m0 * d[2]);
+            const float cz = fmaf(m0, d[1], -m1 * d[0]);
+            ts = md * idd;
+            pp = fmaf(cz, cz, fmaf(cy, cy, cx * cx)) * idd;
+        } else {  // a ray that does not move: the distance is |mu - o|
+            ts = 0.0f;
+            pp = fmaf(m2, m2, fmaf(m1, m1, m0 * m0));
+        }
+        q[b * 32 + lane] = make_float4(v.coef * dd, ts, v.coef * pp, v.peak);
+    }
+}
+
+__device__ __forceinline__ void sigma_ray2(const float4* q, int n, float ta, float tb, float& sa, float& sb) {
+    const int lane = threadIdx.x & 31;
+    float acc_a = 0.0f, acc_b = 0.0f;
+#pragma unroll 4
+    for (int b = 0; b < n; ++b) {
+        const float4 v = q[b * 32 + lane];
+        const float ua = ta - v.y, ub = tb - v.y;
+        acc_a = fmaf(v.w, ex2_approx(fmaf(v.x * ua, ua, v.z)), acc_a);
+        acc_b = fmaf(v.w, ex2_approx(fmaf(v.x * ub, ub, v.z)), acc_b);
+    }
+    sa = acc_a;
+    sb = acc_b;
+}
+
 // Per-thread march state of one ray.
 struct Lane {
     Ray R;
@@ -374,13 +422,15 @@ __global__ void __launch_bounds__(256)
 // then evaluates the density of the buffered samples together (converged)
 // and each lane folds them into its optical depth in lattice order, stopping
 // at the first sample whose depth before it exceeds the threshold.
-template <bool kField>
+// kField: 0 no field, 1 blobs read per sample, 2 per-ray closed form (few blobs).
+template <int kField>
 __global__ void __launch_bounds__(kBlockThreads, 32)
     k_march_count(MarchArgs A, int32_t* __restrict__ counts, int32_t* __restrict__ kstops,
                   int32_t* __restrict__ nruns, float* __restrict__ tnear, int2* __restrict__ runs,
                   long long* __restrict__ block_sums) {
     extern __shared__ BlobS s_blobs[];
     __shared__ int s_buf[kBlockThreads][kBuf + 1];
+    float4* s_q = reinterpret_cast<float4*>(s_blobs + A.field.n_blobs);  // kField 2: [blob][lane]
     if (kField) {
         stage_blobs(s_blobs, A.field, false);
         for (int b = threadIdx.x; b < A.field.n_blobs; b += blockDim.x)
@@ -392,7 +442,8 @@ __global__ void __launch_bounds__(kBlockThreads, 32)
     s.done = true;
     s.n = 0;
     s.R.tn = 0.0f;
-    if (r < A.n) lane_init(A, r, s);
+    if (r < A.n && lane_init(A, r, s) && kField == 2)
+        ray_blobs_setup(s_blobs, A.field.n_blobs, s.R.o, s.R.d, s_q);
     RunRec q{runs + (r < A.n ? r : 0) * kRunSlots, 0, -1, -1};
     int* buf = s_buf[threadIdx.x];
     int cnt = 0, kstop = A.max_steps;
@@ -420,14 +471,18 @@ __global__ void __launch_bounds__(kBlockThreads, 32)
                     const float tb0 = __fadd_rn(s.R.tn, __fmul_rn((float)kb, A.step));
                     const float tb1 = __fadd_rn(tb0, A.step);
                     const float tma = 0.5f * (ta0 + ta1), tmb = 0.5f * (tb0 + tb1);
-                    float xa[3], xb[3];
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        xa[a] = fmaf(s.R.d[a], tma, s.R.o[a]);
-                        xb[a] = fmaf(s.R.d[a], tmb, s.R.o[a]);
-                    }
                     float sga, sgb;
-                    sigma_early_stop2(s_blobs, A.field.n_blobs, xa, xb, sga, sgb);
+                    if (kField == 2) {
+                        sigma_ray2(s_q, A.field.n_blobs, tma, tmb, sga, sgb);
+                    } else {
+                        float xa[3], xb[3];
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            xa[a] = fmaf(s.R.d[a], tma, s.R.o[a]);
+                            xb[a] = fmaf(s.R.d[a], tmb, s.R.o[a]);
+                        }
+                        sigma_early_stop2(s_blobs, A.field.n_blobs, xa, xb, sga, sgb);
+                    }
                     if (tau > A.thr) {
                         stopped = true;
                         kstop = ka;
@@ -722,16 +777,17 @@ extern "C" int nacc_march_grid(const nacc_grid* grid, const float* rays_o, const
         NACC_LAUNCH_CHECK();
     }
     if (g_count_ev[0]) NACC_CUDA_TRY(cudaEventRecord(g_count_ev[0], st));
-    if (with_field) {
+    if (with_field && A.field.n_blobs <= kRayBlobsMax) {
+        const size_t shm = (sizeof(BlobS) + 32 * sizeof(float4)) * (size_t)A.field.n_blobs;
+        k_march_count<2><<<(unsigned)nb, kBlockThreads, shm, st>>>(A, counts, kstops, nruns, tnear, runs, bsums);
+    } else if (with_field) {
         const size_t shm = sizeof(BlobS) * (size_t)A.field.n_blobs;
         if (shm > 48 * 1024)
-            NACC_CUDA_TRY(cudaFuncSetAttribute(k_march_count<true>,
+            NACC_CUDA_TRY(cudaFuncSetAttribute(k_march_count<1>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-        k_march_count<true><<<(unsigned)nb, kBlockThreads, shm, st>>>(A, counts, kstops, nruns, tnear, runs,
-                                                                        bsums);
+        k_march_count<1><<<(unsigned)nb, kBlockThreads, shm, st>>>(A, counts, kstops, nruns, tnear, runs, bsums);
     } else {
-        k_march_count<false><<<(unsigned)nb, kBlockThreads, 0, st>>>(A, counts, kstops, nruns, tnear, runs,
-                                                                      bsums);
+        k_march_count<0><<<(unsigned)nb, kBlockThreads, 0, st>>>(A, counts, kstops, nruns, tnear, runs, bsums);
     }
     NACC_LAUNCH_CHECK();
     if (g_count_ev[1]) NACC_CUDA_TRY(cudaEventRecord(g_count_ev[1], st));

@@ -13,6 +13,7 @@ Bars (see the design notes for the derivations):
   * grid points, EMA, sample_pdf: bit-exact; occupancy bits exact except
     cells within 1e-12 (relative) of the FP64 threshold.
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -169,8 +170,14 @@ def _near_tie_rays(orc, w, bits, full, thr, rel=1e-4):
     return ties
 
 
-def test_march_c1_with_field_early_stop(nacc, orc):
+@pytest.mark.parametrize("field_blobs", [8, 64])
+def test_march_c1_with_field_early_stop(nacc, orc, field_blobs):
+    """C1 rays with the 8-blob C1 field (the per-ray closed form of the density
+    for few blobs) and with the 64-blob C3 field (the density read per sample)."""
     w = workloads.c1_forward()
+    if field_blobs == 64:
+        w = dataclasses.replace(w, blobs=workloads.c3_training(64).blobs)
+    assert w.blobs.n == field_blobs
     g, m = w.grid, w.march
     bits, _ = orc.density_grid(g, w.blobs)
     grid = grid_from_bits(nacc, g.aabb_min, g.aabb_max, g.res, g.n_levels, bits)
@@ -183,7 +190,7 @@ def test_march_c1_with_field_early_stop(nacc, orc):
     ties = _near_tie_rays(orc, w, bits, full, -math.log(m.early_stop_eps))
     n = w.n_rays
     exact = [r for r in range(n) if r not in ties]
-    assert len(ties) < 0.01 * n
+    assert len(ties) < 0.02 * n  # 0.5 % with 8 blobs, 1.6 % with 64
     assert_packed_equal(got, exp, exact)
     gc, ec = np.diff(got["offsets"]), np.diff(exp["offsets"])
     for r in ties:
