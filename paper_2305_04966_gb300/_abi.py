@@ -61,6 +61,7 @@ SIGNATURES = {
                                 c_vp, c_vp, c_vp, c_vp]),
     "nacc_harness_field": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, P(BlobField), c_vp, c_vp, c_vp]),
     "nacc_harness_field_points": (c_i32, [c_i64, c_vp, P(BlobField), c_vp, c_vp]),
+    "nacc_harness_field_rays": (c_i32, [c_vp, c_vp, c_i64, c_vp, c_vp, c_vp, P(BlobField), c_vp, c_vp, c_vp]),
     "nacc_harness_l2_loss": (c_i32, [c_i64, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "nacc_device_status": (c_i32, [c_vp, P(c_i32)]),
     "nacc_selftest_wait_timeout": (c_i32, [c_i64, c_vp]),

@@ -343,17 +343,27 @@ def sample_pdf(edges: torch.Tensor, weights: torch.Tensor, n_out: int, stratifie
 # harness (not the method): analytic field and loss
 # ---------------------------------------------------------------------------
 
-def field_eval(field: BlobField, rays_o, rays_d, packed: PackedSamples, out=None):
-    """Blob field at interval midpoints: (sigmas [cap], rgbs [cap][3])."""
+def field_eval(field: BlobField, rays_o, rays_d, packed: PackedSamples, out=None, per_sample=False):
+    """Blob field at interval midpoints: (sigmas [cap], rgbs [cap][3]).
+
+    By default one warp per ray through the CSR offsets
+    (``nacc_harness_field_rays``, up to 256 blobs); ``per_sample`` (or more
+    blobs) uses one thread per sample through ``ray_indices``."""
     dev = rays_o.device
-    if packed.ray_indices is None:
-        raise ValueError("field_eval needs ray_indices")
     cap = packed.capacity
     if out is None:
         sig = torch.empty(cap, dtype=_F32, device=dev)
         rgb = torch.empty((cap, 3), dtype=_F32, device=dev)
     else:
         sig, rgb = out
+    if not per_sample and field.n <= 256:
+        n = int(rays_o.shape[0])
+        _abi.call("nacc_harness_field_rays", _ptr(rays_o), _ptr(rays_d), n, _ptr(packed.offsets),
+                  _ptr(packed.t_starts), _ptr(packed.t_ends), ctypes.byref(field.c_struct()), _ptr(sig),
+                  _ptr(rgb), _stream(dev))
+        return sig, rgb
+    if packed.ray_indices is None:
+        raise ValueError("field_eval per sample needs ray_indices")
     _abi.call("nacc_harness_field", _ptr(rays_o), _ptr(rays_d), _ptr(packed.ray_indices),
               _ptr(packed.t_starts), _ptr(packed.t_ends), _ptr(packed.n_samples_dev),
               ctypes.byref(field.c_struct()), _ptr(sig), _ptr(rgb), _stream(dev))

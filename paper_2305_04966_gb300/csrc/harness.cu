@@ -6,6 +6,12 @@
 namespace nacc {
 namespace {
 
+__device__ __forceinline__ float ex2_approx(float a) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(a));
+    return y;
+}
+
 __global__ void __launch_bounds__(256)
     k_field(const float* __restrict__ o, const float* __restrict__ d, const int32_t* __restrict__ ri,
             const float* __restrict__ t0, const float* __restrict__ t1,
@@ -38,6 +44,114 @@ __global__ void __launch_bounds__(256)
         __stcs(rgb + 3 * i, cr * inv);
         __stcs(rgb + 3 * i + 1, cg * inv);
         __stcs(rgb + 3 * i + 2, cb * inv);
+    }
+}
+
+// The blob field at the sample midpoints of a packed set, one warp per ray
+// (persistent grid).  On the ray x(t) = o + t d blob b contributes peak_b
+// 2^(A_b (t - t*_b)^2 + C_b) with A_b = c_b |d|^2, C_b = c_b p_b^2, c_b the
+// log2-scaled coefficient, t*_b the closest approach and p_b the distance
+// there (cross product, no cancellation): set up once per ray by the lanes,
+// then each lane evaluates four consecutive samples per chunk (128-bit
+// loads of t0, t1; 128-bit stores of sigma and rgb for groups inside the
+// ray, scalar accesses at its ends).
+constexpr int kFieldWarps = 8;
+constexpr int kFieldRayBlobs = 256;  // per-warp shared table limit
+
+__global__ void __launch_bounds__(kFieldWarps * 32)
+    k_field_rays(const float* __restrict__ o, const float* __restrict__ d, int64_t n_rays,
+                 const int64_t* __restrict__ off, const float* __restrict__ t0, const float* __restrict__ t1,
+                 nacc_blob_field f, float* __restrict__ sig, float* __restrict__ rgb) {
+    extern __shared__ float4 s_dyn[];
+    const int nb = f.n_blobs;
+    BlobS* sb = reinterpret_cast<BlobS*>(s_dyn + kFieldWarps * nb);
+    stage_blobs(sb, f, true);
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) sb[b].coef *= 1.4426950408889634f;  // log2 e
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float4* q = s_dyn + wid * nb;
+    const int64_t warps = (int64_t)gridDim.x * kFieldWarps;
+    for (int64_t r = (int64_t)blockIdx.x * kFieldWarps + wid; r < n_rays; r += warps) {
+        const long long s = off[r], e = off[r + 1];
+        if (e <= s) continue;
+        const float ox = __ldg(o + 3 * r), oy = __ldg(o + 3 * r + 1), oz = __ldg(o + 3 * r + 2);
+        const float dx = __ldg(d + 3 * r), dy = __ldg(d + 3 * r + 1), dz = __ldg(d + 3 * r + 2);
+        const float dd = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        const float idd = dd > 0.0f ? 1.0f / dd : 0.0f;
+        for (int b = lane; b < nb; b += 32) {
+            const BlobS v = sb[b];
+            const float m0 = v.mx - ox, m1 = v.my - oy, m2 = v.mz - oz;
+            float ts, pp;
+            if (dd > 0.0f) {
+                const float cx = fmaf(m1, dz, -m2 * dy), cy = fmaf(m2, dx, -m0 * dz), cz = fmaf(m0, dy, -m1 * dx);
+                ts = fmaf(m2, dz, fmaf(m1, dy, m0 * dx)) * idd;
+                pp = fmaf(cz, cz, fmaf(cy, cy, cx * cx)) * idd;
+            } else {
+                ts = 0.0f;
+                pp = fmaf(m2, m2, fmaf(m1, m1, m0 * m0));
+            }
+            q[b] = make_float4(v.coef * dd, ts, v.coef * pp, v.peak);
+        }
+        __syncwarp();
+        const long long a = s & ~3ll;
+        for (long long p = a + 4 * lane; p < e; p += 128) {
+            const bool whole = p >= s && p + 4 <= e;
+            float ta[4], tb[4];
+            if (whole) {
+                const float4 u = __ldcs(reinterpret_cast<const float4*>(t0 + p));
+                const float4 w = __ldcs(reinterpret_cast<const float4*>(t1 + p));
+                ta[0] = u.x, ta[1] = u.y, ta[2] = u.z, ta[3] = u.w;
+                tb[0] = w.x, tb[1] = w.y, tb[2] = w.z, tb[3] = w.w;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const bool in = p + j >= s && p + j < e;
+                    ta[j] = in ? t0[p + j] : 0.0f;
+                    tb[j] = in ? t1[p + j] : 0.0f;
+                }
+            }
+            float tm[4], sg[4] = {0.0f, 0.0f, 0.0f, 0.0f}, c[12] = {};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) tm[j] = 0.5f * (ta[j] + tb[j]);
+            for (int b = 0; b < nb; ++b) {
+                const float4 v = q[b];
+                const BlobS& w = sb[b];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float u = tm[j] - v.y;
+                    const float sj = v.w * ex2_approx(fmaf(v.x * u, u, v.z));
+                    sg[j] += sj;
+                    c[3 * j] = fmaf(sj, w.r, c[3 * j]);
+                    c[3 * j + 1] = fmaf(sj, w.g, c[3 * j + 1]);
+                    c[3 * j + 2] = fmaf(sj, w.b, c[3 * j + 2]);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float inv = sg[j] > 0.0f ? 1.0f / sg[j] : 0.0f;
+                c[3 * j] *= inv;
+                c[3 * j + 1] *= inv;
+                c[3 * j + 2] *= inv;
+            }
+            if (whole) {
+                __stcs(reinterpret_cast<float4*>(sig + p), make_float4(sg[0], sg[1], sg[2], sg[3]));
+                float4* q4 = reinterpret_cast<float4*>(rgb + 3 * p);
+                __stcs(q4, make_float4(c[0], c[1], c[2], c[3]));
+                __stcs(q4 + 1, make_float4(c[4], c[5], c[6], c[7]));
+                __stcs(q4 + 2, make_float4(c[8], c[9], c[10], c[11]));
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (p + j >= s && p + j < e) {
+                        sig[p + j] = sg[j];
+                        rgb[3 * (p + j)] = c[3 * j];
+                        rgb[3 * (p + j) + 1] = c[3 * j + 1];
+                        rgb[3 * (p + j) + 2] = c[3 * j + 2];
+                    }
+                }
+            }
+        }
+        __syncwarp();  // the next ray's set-up rewrites q
     }
 }
 
@@ -86,6 +200,33 @@ int check_field(const nacc_blob_field* f, bool rgb) {
 }  // namespace nacc
 
 using namespace nacc;
+
+extern "C" int nacc_harness_field_rays(const float* rays_o, const float* rays_d, int64_t n_rays,
+                                       const int64_t* offsets, const float* t_starts, const float* t_ends,
+                                       const nacc_blob_field* field, float* sigmas, float* rgbs, void* stream) {
+    clear_error();
+    int rc = check_field(field, true);
+    if (rc != NACC_OK) return rc;
+    NACC_CHECK_ARG(n_rays >= 0 && n_rays < (int64_t(1) << 40), "n_rays=%lld out of range", (long long)n_rays);
+    if (n_rays == 0) return NACC_OK;
+    NACC_CHECK_ARG(rays_o && rays_d && offsets && t_starts && t_ends && sigmas && rgbs, "a pointer argument is NULL");
+    NACC_CHECK_ARG(field->n_blobs <= kFieldRayBlobs, "n_blobs=%d > %d (use nacc_harness_field)", field->n_blobs,
+                   kFieldRayBlobs);
+    auto a16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+    NACC_CHECK_ARG(a16(t_starts) && a16(t_ends) && a16(sigmas) && a16(rgbs),
+                   "t_starts, t_ends, sigmas and rgbs must be 16-byte aligned");
+    const size_t shm = (sizeof(float4) * kFieldWarps + sizeof(BlobS)) * (size_t)field->n_blobs;
+    if (shm > 48 * 1024)
+        NACC_CUDA_TRY(cudaFuncSetAttribute(k_field_rays, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    int per_sm = 1;
+    NACC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_field_rays, kFieldWarps * 32, shm));
+    if (per_sm < 1) per_sm = 1;
+    const int64_t grid = min64((int64_t)per_sm * sm_count(), (n_rays + kFieldWarps - 1) / kFieldWarps);
+    k_field_rays<<<(unsigned)grid, kFieldWarps * 32, shm, as_stream(stream)>>>(
+        rays_o, rays_d, n_rays, offsets, t_starts, t_ends, *field, sigmas, rgbs);
+    NACC_LAUNCH_CHECK();
+    return NACC_OK;
+}
 
 extern "C" int nacc_harness_field(const float* rays_o, const float* rays_d, const int32_t* ray_indices,
                                   const float* t_starts, const float* t_ends,

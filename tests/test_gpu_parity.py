@@ -488,6 +488,32 @@ def test_sample_pdf_bit_exact(nacc, orc, nb, no, strat):
 # whole step
 # ---------------------------------------------------------------------------
 
+@pytest.mark.parametrize("field_blobs", [8, 64])
+@pytest.mark.parametrize("per_sample", [False, True])
+def test_field_eval_matches_oracle_field(nacc, orc, field_blobs, per_sample):
+    """Harness field at the midpoints of a packed set (C1 rays through the
+    C1 grid, ragged): the warp-per-ray closed form and the per-sample form
+    against the oracle's FP64 field."""
+    w = workloads.c1_forward()
+    if field_blobs == 64:
+        w = dataclasses.replace(w, blobs=workloads.c3_training(64).blobs)
+    g, m = w.grid, w.march
+    bits, _ = orc.density_grid(g, w.blobs)
+    ex = orc.march(w.rays_o, w.rays_d, g.aabb_min, g.aabb_max, g.res, g.n_levels, bits, m.step,
+                   m.max_steps, m.t_min, m.t_max)
+    S = int(ex["offsets"][-1])
+    assert S > 100000
+    pk = nacc.PackedSamples(T(ex["offsets"]), T(ex["ray_indices"]), T(ex["t_starts"]), T(ex["t_ends"]),
+                            torch.tensor([S], device=DEV))
+    field = nacc.BlobField.from_numpy(w.blobs)
+    sig, rgb = nacc.field_eval(field, T(w.rays_o), T(w.rays_d), pk, per_sample=per_sample)
+    s64, c64 = orc.field_samples(w.rays_o, w.rays_d, ex["ray_indices"], ex["t_starts"], ex["t_ends"], w.blobs)
+    sig, rgb = sig[:S].cpu().numpy(), rgb[:S].cpu().numpy()
+    np.testing.assert_allclose(sig, s64, rtol=1e-4, atol=1e-30)
+    ok = s64 > 1e-20
+    np.testing.assert_allclose(rgb[ok], c64[ok], rtol=1e-4, atol=1e-6)
+
+
 def test_c2_pipeline_sampled_rays_vs_oracle(nacc, orc):
     """Full C2 step (march with field -> field -> render -> loss -> adjoint) at the
     full 640,000-ray size: rendered colour of sampled rays against the oracle's
