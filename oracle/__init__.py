@@ -248,3 +248,6 @@ def density_grid(grid_spec, blobs, thresh=0.01, n_threads=None):
     occ = sig > thresh
     words = occ.reshape(-1, 32).astype(np.uint64) << np.arange(32, dtype=np.uint64)
     return words.sum(axis=1).astype(np.uint32), sig.astype(np.float32)
+
+
+from . import proposal  # noqa: E402  (density-proposal network oracle)

@@ -527,3 +527,72 @@ def test_sample_pdf_stratified(orc):
     assert np.all(inner >= -1e-4) and np.all(inner < 1 + 1e-4)
     assert np.allclose(inner, inner[:, :1], atol=1e-4)
     assert 0.4 < inner[:, 0].mean() < 0.6
+
+
+# ---------------------------------------------------------------------------
+# density-proposal network oracle (oracle/proposal.py)
+# ---------------------------------------------------------------------------
+
+def test_proposal_encoding_closed_forms():
+    from oracle import proposal as P
+    e = P.encode(np.array([[0.0, 0.5, 1.0 / 3.0]]))[0]
+    assert e.shape == (64,) and np.all(e[51:] == 0.0)
+    np.testing.assert_allclose(e[0:3], [0.0, 0.5, 1.0 / 3.0], rtol=0, atol=0)
+    s3 = math.sqrt(3.0) / 2.0
+    for k in range(8):
+        sx, cx, sy, cy, sz, cz = e[3 + 6 * k: 9 + 6 * k]
+        assert sx == 0.0 and cx == 1.0                                   # x = 0
+        # y = 1/2: angle 2^k pi/2 -> (1, 0) for k = 0, (0, -1) for k = 1, (0, 1) after
+        np.testing.assert_allclose([sy, cy], [(1, 0), (0, -1)][k] if k < 2 else (0, 1), atol=1e-12)
+        # z = 1/3: angle 2^k pi/3; 2^k mod 6 cycles 1, 2, 4, 2, 4, ... (sin = +-sqrt3/2, cos = +-1/2)
+        m = (2 ** k) % 6
+        exp = {1: (s3, 0.5), 2: (s3, -0.5), 4: (-s3, -0.5)}[m]
+        np.testing.assert_allclose([sz, cz], exp, atol=1e-12)
+
+
+def test_proposal_forward_hand_built_network():
+    """W1 copies x, y, z, b1 = 1/2, W2 = identity, w3 sums the first three
+    units, b3 = -1: density = softplus(sum_j relu(x_j + 1/2) - 1)."""
+    from oracle import proposal as P
+    W1 = np.zeros((64, 64), np.float32)
+    W1[0, 0] = W1[1, 1] = W1[2, 2] = 1.0
+    w3 = np.zeros(64, np.float32)
+    w3[:3] = 1.0
+    p = {"W1": W1, "b1": np.full(64, 0.5, np.float32), "W2": np.eye(64, dtype=np.float32),
+         "b2": np.zeros(64, np.float32), "w3": w3, "b3": np.array([-1.0], np.float32)}
+    x = np.array([[0.25, -0.5, 1.0], [-1.0, -0.75, 0.0], [0.5, 0.5, 0.5]])  # exact in bfloat16
+    z = np.maximum(x + 0.5, 0.0).sum(1) - 1.0
+    np.testing.assert_allclose(P.forward(p, x)["sigma"], np.log1p(np.exp(z)), rtol=1e-15)
+
+
+def test_proposal_gradients_match_finite_differences():
+    from oracle import proposal as P
+    g0 = np.random.default_rng(11)
+    x = g0.uniform(-1.5, 1.5, (64, 3))
+    t = g0.uniform(0.0, 5.0, 64)
+    p = P.init_params(3)
+    p["b1"] = g0.uniform(-0.2, 0.2, 64).astype(np.float32)
+    p["b2"] = g0.uniform(-0.2, 0.2, 64).astype(np.float32)
+    _, g = P.loss_and_grads(p, x, t, round_bf16=False)
+    picks = [("b3", (0,)), ("w3", (5,)), ("w3", (40,)), ("b2", (7,)), ("W2", (3, 9)), ("W2", (60, 1)),
+             ("b1", (12,)), ("W1", (4, 0)), ("W1", (30, 17)), ("W1", (63, 50))]
+    for name, idx in picks:
+        q = {k: v.astype(np.float64) for k, v in p.items()}
+        h = 1e-6
+        q[name][idx] += h
+        lp = P.loss_and_grads(q, x, t, round_bf16=False)[0]
+        q[name][idx] -= 2 * h
+        lm = P.loss_and_grads(q, x, t, round_bf16=False)[0]
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - g[name][idx]) <= 1e-6 * max(1.0, abs(fd)), (name, idx, fd, g[name][idx])
+
+
+def test_proposal_adam_first_step_closed_form():
+    """First step: m_hat = g, v_hat = g^2, so p -= lr g / (|g| + eps)."""
+    from oracle import proposal as P
+    p = {"b1": np.array([1.0, -2.0, 0.5], np.float32)}
+    g = {"b1": np.array([0.3, -0.01, 0.0])}
+    st = {}
+    P.adam_step(p, g, st, lr=0.01)
+    exp = np.array([1.0, -2.0, 0.5]) - 0.01 * g["b1"] / (np.abs(g["b1"]) + 1e-8)
+    np.testing.assert_allclose(p["b1"], exp.astype(np.float32), rtol=0, atol=0)
