@@ -55,10 +55,10 @@ int nacc_harness_l2_loss(int64_t n, const float* rgb, const float* target, float
                          float* loss, void* stream);
 
 /*
- * Device status of the bounded waits inside the library's streaming kernels
- * (render_fwd / render_bwd).  Every wait on an mbarrier gives up after 2 s of
- * GPU wall time; the kernel then records the expiry in a device status word
- * and returns instead of hanging.  This call synchronises `stream`, reads and
+ * Device status of the bounded waits inside the library's kernels (the
+ * proposal network's tensor-core kernels and the wait self-test).  Every
+ * wait on an mbarrier gives up after 2 s of GPU wall time; the kernel then
+ * records the expiry in a device status word and returns instead of hanging.  This call synchronises `stream`, reads and
  * clears that word, and writes NACC_OK or NACC_ERR_TIMEOUT to *status_out
  * [host].  Returns NACC_OK unless a CUDA call failed.
  */

@@ -1,4 +1,5 @@
-"""ctypes declarations of the C ABI in ``include/nacc.h`` / ``include/nacc_harness.h``.
+"""ctypes declarations of the C ABI in ``include/nacc.h``, ``include/nacc_harness.h``
+and ``include/nacc_proposal.h``.
 
 Loads the in-tree ``libnacc.so``.  There is no fallback: if the library is
 missing or fails to load, every entry point raises.
@@ -66,7 +67,15 @@ SIGNATURES = {
     "nacc_device_status": (c_i32, [c_vp, P(c_i32)]),
     "nacc_selftest_wait_timeout": (c_i32, [c_i64, c_vp]),
     "nacc_set_march_count_events": (c_i32, [c_vp, c_vp]),
+    "nacc_mlp_sync": (c_i32, [c_vp, c_vp, c_vp]),
+    "nacc_mlp_forward": (c_i32, [c_i64, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "nacc_mlp_train_grads": (c_i32, [c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "nacc_mlp_adam": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, c_f32, c_f32, c_f32, c_f32, c_vp, c_vp]),
+    "nacc_mlp_encode": (c_i32, [c_i64, c_vp, c_vp, c_vp]),
 }
+
+MLP_PARAMS = 8385
+MLP_WEIGHTS = 8256
 
 _lib = None
 

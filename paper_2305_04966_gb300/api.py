@@ -402,3 +402,84 @@ def density_grid(grid: OccupancyGrid, field: BlobField, thresh: float = 0.01, se
     dens = field_points(field, pts)
     update_grid(grid, dens, decay=0.0, thresh_frac=0.0, thresh_abs=thresh)
     return grid
+
+
+# ---------------------------------------------------------------------------
+# learned density proposal (Table 1 "PDF Approaches"; nacc_proposal.h)
+# ---------------------------------------------------------------------------
+
+class ProposalMLP:
+    """The proposal network: FP32 master parameters (layout of
+    ``nacc_proposal.h``), their BF16 weight copy used by the tensor-core
+    kernels, Adam moments and a gradient accumulator, all on one device."""
+
+    def __init__(self, params: torch.Tensor):
+        dev = params.device
+        _check(params, "params", _F32, dev, (_abi.MLP_PARAMS,))
+        self.params = params.contiguous()
+        self.weights = torch.empty(_abi.MLP_WEIGHTS, dtype=torch.int16, device=dev)
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.grads = torch.zeros_like(self.params)
+        self.loss_sum = torch.zeros(1, dtype=_F32, device=dev)
+        self.step = 0
+        self.sync()
+
+    @classmethod
+    def init(cls, seed: int = 7, device="cuda"):
+        """Uniform(+-1/sqrt(fan_in)) weights (fan-in 51 for the encoding, the
+        padding columns of W1 zero), zero biases."""
+        g = torch.Generator().manual_seed(seed)
+        p = torch.zeros(_abi.MLP_PARAMS, dtype=_F32)
+        W1 = (torch.rand((64, 64), generator=g, dtype=torch.float64) * 2 - 1) / math.sqrt(51)
+        W1[:, 51:] = 0
+        p[0:4096] = W1.reshape(-1).float()
+        p[4160:8256] = ((torch.rand(4096, generator=g, dtype=torch.float64) * 2 - 1) / 8.0).float()
+        p[8320:8384] = ((torch.rand(64, generator=g, dtype=torch.float64) * 2 - 1) / 8.0).float()
+        return cls(p.to(device))
+
+    def sync(self):
+        _abi.call("nacc_mlp_sync", _ptr(self.params), _ptr(self.weights), _stream(self.params.device))
+
+    def forward(self, xyz: torch.Tensor, out=None) -> torch.Tensor:
+        dev = xyz.device
+        n = int(xyz.shape[0])
+        _check(xyz, "xyz", _F32, dev, (n, 3))
+        sig = out if out is not None else torch.empty(n, dtype=_F32, device=dev)
+        _abi.call("nacc_mlp_forward", n, _ptr(xyz), _ptr(self.params), _ptr(self.weights), _ptr(sig),
+                  _stream(dev))
+        return sig
+
+    def accumulate_grads(self, xyz: torch.Tensor, target: torch.Tensor):
+        """Adds dL/dparams of L = mean (density - target)^2 into ``grads``
+        and sum (density - target)^2 into ``loss_sum``."""
+        dev = xyz.device
+        n = int(xyz.shape[0])
+        _check(xyz, "xyz", _F32, dev, (n, 3))
+        _check(target, "target", _F32, dev, (n,))
+        _abi.call("nacc_mlp_train_grads", n, _ptr(xyz), _ptr(target), _ptr(self.params), _ptr(self.weights),
+                  _ptr(self.grads), _ptr(self.loss_sum), _stream(dev))
+
+    def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        self.step += 1
+        _abi.call("nacc_mlp_adam", _ptr(self.params), _ptr(self.grads), _ptr(self.m), _ptr(self.v), self.step,
+                  float(lr), float(beta1), float(beta2), float(eps), _ptr(self.weights),
+                  _stream(self.params.device))
+
+    def train_step(self, xyz, target, lr=1e-3) -> torch.Tensor:
+        """One fused forward/adjoint pass and an Adam step; returns the batch's
+        mean squared error (a device tensor, read before the step)."""
+        self.loss_sum.zero_()
+        self.accumulate_grads(xyz, target)
+        loss = self.loss_sum / xyz.shape[0]
+        self.adam(lr)
+        return loss
+
+
+def mlp_encode(xyz: torch.Tensor) -> torch.Tensor:
+    """Diagnostics: the FP32 frequency encoding [n][64] of points [n][3]."""
+    dev = xyz.device
+    n = int(xyz.shape[0])
+    enc = torch.empty((n, 64), dtype=_F32, device=dev)
+    _abi.call("nacc_mlp_encode", n, _ptr(xyz), _ptr(enc), _stream(dev))
+    return enc

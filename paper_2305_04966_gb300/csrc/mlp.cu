@@ -1,0 +1,527 @@
+// mlp.cu -- the learned density proposal (nacc_proposal.h): frequency
+// encoding and a 3-layer width-64 MLP whose two 64x64 layers run on the
+// tcgen05 tensor cores (BF16 operands in shared memory, FP32 accumulators in
+// tensor memory), plus its fused adjoint and Adam.
+//
+// Table 1 "PDF Approaches" and Sec. 3.2 of NerfAcc (arXiv 2305.04966): a
+// small network predicts density; its transmittance gives the PDF that
+// inverse transform sampling (Eq. 1) resamples.
+//
+// Forward (persistent CTAs of 128 threads, 128 points per tile, thread t =
+// point t of the tile): the thread encodes its point into row t of a
+// K-major, 128-byte-swizzled BF16 tile; one thread issues the four
+// K = 16 MMAs of a layer (M = 128 points, N = 64 units, K = 64); every warp
+// reads its 32 rows of the accumulator back from tensor memory, adds the
+// bias, applies ReLU and writes the next layer's BF16 input row; the last
+// layer (64 -> 1) is a dot product on the CUDA cores, then softplus.
+//
+// Adjoint (same tiles): delta3 = dL/dz3, delta2 = delta3 w3 * [h2 > 0] and
+// delta1 = (delta2 W2) * [h1 > 0] (an M = 128 MMA against W2^T); the weight
+// gradients dW2 = delta2^T h1 and dW1 = delta1^T e are M = 64 MMAs with K =
+// the 128 points of the tile, accumulated in tensor memory over all tiles of
+// the CTA (their operands are written transposed into shared memory, so
+// every MMA uses the same K-major layout).  Bias and w3 gradients are column
+// sums on the CUDA cores.  Waits on MMA completion are bounded (2 s).
+#include <cuda_bf16.h>
+
+#include "../../include/nacc_proposal.h"
+#include "nacc_internal.cuh"
+#include "tcgen05.cuh"
+
+// bit 0: a bounded wait expired in a proposal-network kernel
+__device__ unsigned int g_nacc_mlp_status;
+
+namespace nacc {
+namespace {
+
+constexpr int kTile = 128;
+constexpr int kThreads = 128;
+constexpr uint64_t kWaitNs = 2000000000ull;
+constexpr int oW1 = 0, oB1 = 4096, oW2 = 4160, oB2 = 8256, oW3 = 8320, oB3 = 8384;
+constexpr int wW1 = 0, wW2 = 4096, wW3 = 8192;
+constexpr uint32_t kTileBytes = 16384;  // 128 rows x 128 bytes
+constexpr uint32_t kWBytes = 8192;      // 64 rows x 128 bytes
+
+__device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
+    return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
+}
+
+__device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// e(x): [x, y, z, (sin, cos)(2^k pi x_a) for k = 0..7, a = 0..2], zero-padded to 64.
+// sin/cos of pi x_a and of 16 pi x_a (sincospif, exact argument scaling by 16)
+// anchor the bands; the others follow by the double-angle formulas.
+__device__ __forceinline__ void encode_point(float x, float y, float z, float e[64]) {
+    e[0] = x;
+    e[1] = y;
+    e[2] = z;
+    const float c[3] = {x, y, z};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float s, co;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (k == 0) sincospif(c[a], &s, &co);
+            if (k == 4) sincospif(16.0f * c[a], &s, &co);
+            e[3 + 6 * k + 2 * a] = s;
+            e[4 + 6 * k + 2 * a] = co;
+            const float s2 = 2.0f * s * co;
+            const float c2 = (co - s) * (co + s);
+            s = s2;
+            co = c2;
+        }
+    }
+#pragma unroll
+    for (int i = 51; i < 64; ++i) e[i] = 0.0f;
+}
+
+// Row r (64 values -> BF16) of a K-major SW128 tile.
+__device__ __forceinline__ void store_row(uint8_t* tile, int r, const float v[64]) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        uint4 q;
+        q.x = pack_bf16x2(v[8 * c + 0], v[8 * c + 1]);
+        q.y = pack_bf16x2(v[8 * c + 2], v[8 * c + 3]);
+        q.z = pack_bf16x2(v[8 * c + 4], v[8 * c + 5]);
+        q.w = pack_bf16x2(v[8 * c + 6], v[8 * c + 7]);
+        *reinterpret_cast<uint4*>(tile + (r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4)) = q;
+    }
+}
+
+// Column p (64 values, one per row) of a [64 rows][128 K] tile made of two
+// K-major SW128 sub-tiles of 64 K each (the transposed operands).
+__device__ __forceinline__ void store_col(uint8_t* tile2, int p, const float v[64]) {
+    uint8_t* sub = tile2 + (p >> 6) * kWBytes;
+#pragma unroll
+    for (int i = 0; i < 64; ++i)
+        *reinterpret_cast<__nv_bfloat16*>(sub + tc::sw128_offset(i, p & 63)) = __float2bfloat16_rn(v[i]);
+}
+
+__device__ __forceinline__ float load_elem(const uint8_t* tile, int r, int k) {
+    return __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(tile + tc::sw128_offset(r, k)));
+}
+
+// Accumulator row (this thread's lane) of a 128 x 64 FP32 tile in tensor memory.
+__device__ __forceinline__ void tmem_row64(uint32_t taddr, float v[64]) {
+    tc::tmem_ld16(taddr, v);
+    tc::tmem_ld16(taddr + 16, v + 16);
+    tc::tmem_ld16(taddr + 32, v + 32);
+    tc::tmem_ld16(taddr + 48, v + 48);
+    tc::tmem_wait_ld();
+}
+
+// Make this thread's shared-memory writes visible to the tensor cores and
+// order them (and earlier tensor-memory reads) before the MMA issue.
+__device__ __forceinline__ void sync_for_mma() {
+    fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+}
+
+__device__ __forceinline__ bool wait_mma(uint64_t* bar, uint32_t& phase) {
+    const bool ok = __syncthreads_and(mbar_wait_bounded(bar, phase & 1u, kWaitNs));
+    ++phase;
+    tc::fence_after_sync();
+    return ok;
+}
+
+__device__ __forceinline__ float softplus(float z) { return z > 20.0f ? z : log1pf(expf(z)); }
+
+__device__ __forceinline__ void load_weight_tile(uint8_t* dst, const uint16_t* w, bool transpose) {
+    for (int i = threadIdx.x; i < 4096; i += blockDim.x) {
+        const int a = i >> 6, b = i & 63;  // w[a][b]
+        const int r = transpose ? b : a, k = transpose ? a : b;
+        *reinterpret_cast<uint16_t*>(dst + tc::sw128_offset(r, k)) = w[i];
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_mlp_forward(int64_t n, const float* __restrict__ xyz,
+                                                          const float* __restrict__ P,
+                                                          const uint16_t* __restrict__ Wb,
+                                                          float* __restrict__ sigma) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* base = align1024(smem_raw);
+    uint8_t* sW1 = base;
+    uint8_t* sW2 = base + kWBytes;
+    uint8_t* sX = base + 2 * kWBytes;
+    __shared__ float sB1[64], sB2[64], sW3[64];
+    __shared__ float sB3;
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tbase;
+    const int t = threadIdx.x, warp = t >> 5;
+    load_weight_tile(sW1, Wb + wW1, false);
+    load_weight_tile(sW2, Wb + wW2, false);
+    if (t < 64) {
+        sB1[t] = P[oB1 + t];
+        sB2[t] = P[oB2 + t];
+        sW3[t] = __bfloat162float(__ushort_as_bfloat16(Wb[wW3 + t]));
+    }
+    if (t == 0) {
+        sB3 = P[oB3];
+        mbar_init(&bar, 1);
+        fence_barrier_init();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(&tbase, 64);
+        tc::tmem_relinquish();
+    }
+    sync_for_mma();
+    const uint32_t tm = tbase, row = tm + ((uint32_t)(warp * 32) << 16);
+    const uint32_t idesc = tc::idesc_bf16_f32(128, 64);
+    const uint64_t dX = tc::sw128_desc(smem_u32(sX)), dW1 = tc::sw128_desc(smem_u32(sW1)),
+                   dW2 = tc::sw128_desc(smem_u32(sW2));
+    uint32_t phase = 0;
+    bool ok = true;
+    const int64_t ntiles = (n + kTile - 1) / kTile;
+    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const int64_t p = tile * kTile + t;
+        float v[64];
+        if (p < n)
+            encode_point(xyz[3 * p], xyz[3 * p + 1], xyz[3 * p + 2], v);
+        else
+#pragma unroll
+            for (int i = 0; i < 64; ++i) v[i] = 0.0f;
+        store_row(sX, t, v);
+        sync_for_mma();
+        if (t == 0) {
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) tc::mma_bf16(tm, dX + 2 * ks, dW1 + 2 * ks, idesc, ks > 0);
+            tc::mma_commit(&bar);
+        }
+        if (!(ok = wait_mma(&bar, phase))) break;
+        tmem_row64(row, v);
+#pragma unroll
+        for (int i = 0; i < 64; ++i) v[i] = fmaxf(v[i] + sB1[i], 0.0f);
+        store_row(sX, t, v);
+        sync_for_mma();
+        if (t == 0) {
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) tc::mma_bf16(tm, dX + 2 * ks, dW2 + 2 * ks, idesc, ks > 0);
+            tc::mma_commit(&bar);
+        }
+        if (!(ok = wait_mma(&bar, phase))) break;
+        tmem_row64(row, v);
+        float z = sB3;
+#pragma unroll
+        for (int i = 0; i < 64; ++i) z = fmaf(sW3[i], bf16_round(fmaxf(v[i] + sB2[i], 0.0f)), z);
+        if (p < n) sigma[p] = softplus(z);
+        tc::fence_before_sync();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tm, 64);
+    if (!ok && t == 0) atomicOr(&g_nacc_mlp_status, 1u);
+}
+
+// Shared-memory map of the training kernel (offsets from a 1 KiB-aligned base).
+constexpr uint32_t tW1 = 0, tW2 = 8192, tW2T = 16384;       // 64 x 64 weight tiles
+constexpr uint32_t tE = 24576;                              // 128 x 64: e, later h2 (point-major)
+constexpr uint32_t tET = tE + kTileBytes;                   // 64 x 128: e^T
+constexpr uint32_t tH1 = tET + kTileBytes;                  // 128 x 64: h1
+constexpr uint32_t tH1T = tH1 + kTileBytes;                 // 64 x 128: h1^T
+constexpr uint32_t tD2 = tH1T + kTileBytes;                 // 128 x 64: delta2, later delta1
+constexpr uint32_t tD2T = tD2 + kTileBytes;                 // 64 x 128: delta2^T
+constexpr uint32_t tD1T = tD2T + kTileBytes;                // 64 x 128: delta1^T
+constexpr uint32_t kTrainSmem = tD1T + kTileBytes + 1024;   // + alignment slack
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_mlp_train(int64_t n, const float* __restrict__ xyz, const float* __restrict__ target,
+                const float* __restrict__ P, const uint16_t* __restrict__ Wb, float* __restrict__ G,
+                float* __restrict__ loss_sum, float two_over_n) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* base = align1024(smem_raw);
+    __shared__ float sB1[64], sB2[64], sW3[64], sD3[kTile];
+    __shared__ float sB3;
+    __shared__ float sRed[kThreads / 32][2];
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tbase;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    load_weight_tile(base + tW1, Wb + wW1, false);
+    load_weight_tile(base + tW2, Wb + wW2, false);
+    load_weight_tile(base + tW2T, Wb + wW2, true);
+    if (t < 64) {
+        sB1[t] = P[oB1 + t];
+        sB2[t] = P[oB2 + t];
+        sW3[t] = __bfloat162float(__ushort_as_bfloat16(Wb[wW3 + t]));
+    }
+    if (t == 0) {
+        sB3 = P[oB3];
+        mbar_init(&bar, 1);
+        fence_barrier_init();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(&tbase, 256);  // [0,64) layer outputs, [64,128) delta1, [128,192) dW2, [192,256) dW1
+        tc::tmem_relinquish();
+    }
+    sync_for_mma();
+    const uint32_t tm = tbase, row = tm + ((uint32_t)(warp * 32) << 16);
+    const uint32_t id128 = tc::idesc_bf16_f32(128, 64), id64 = tc::idesc_bf16_f32(64, 64);
+    const uint64_t dE = tc::sw128_desc(smem_u32(base + tE)), dH1 = tc::sw128_desc(smem_u32(base + tH1)),
+                   dD2 = tc::sw128_desc(smem_u32(base + tD2)), dW1 = tc::sw128_desc(smem_u32(base + tW1)),
+                   dW2 = tc::sw128_desc(smem_u32(base + tW2)), dW2T = tc::sw128_desc(smem_u32(base + tW2T));
+    const int j = t & 63, half = t >> 6;  // column-sum role: unit j over points [64 half, 64 half + 64)
+    float acc_w3 = 0.0f, acc_b2 = 0.0f, acc_b1 = 0.0f, acc_b3 = 0.0f, acc_loss = 0.0f;
+    uint32_t phase = 0;
+    bool ok = true, first = true;
+    const int64_t ntiles = (n + kTile - 1) / kTile;
+    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const int64_t p = tile * kTile + t;
+        const bool valid = p < n;
+        float v[64], h[64];
+        if (valid)
+            encode_point(xyz[3 * p], xyz[3 * p + 1], xyz[3 * p + 2], v);
+        else
+#pragma unroll
+            for (int i = 0; i < 64; ++i) v[i] = 0.0f;
+        store_row(base + tE, t, v);
+        store_col(base + tET, t, v);
+        sync_for_mma();
+        if (t == 0) {  // layer 1
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) tc::mma_bf16(tm, dE + 2 * ks, dW1 + 2 * ks, id128, ks > 0);
+            tc::mma_commit(&bar);
+        }
+        if (!(ok = wait_mma(&bar, phase))) break;
+        tmem_row64(row, v);
+#pragma unroll
+        for (int i = 0; i < 64; ++i) v[i] = fmaxf(v[i] + sB1[i], 0.0f);  // h1
+        store_row(base + tH1, t, v);
+        store_col(base + tH1T, t, v);
+        sync_for_mma();
+        if (t == 0) {  // layer 2
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) tc::mma_bf16(tm, dH1 + 2 * ks, dW2 + 2 * ks, id128, ks > 0);
+            tc::mma_commit(&bar);
+        }
+        if (!(ok = wait_mma(&bar, phase))) break;
+        tmem_row64(row, v);
+        float z = sB3;
+#pragma unroll
+        for (int i = 0; i < 64; ++i) {
+            h[i] = bf16_round(fmaxf(v[i] + sB2[i], 0.0f));  // h2
+            z = fmaf(sW3[i], h[i], z);
+        }
+        float d3 = 0.0f;
+        if (valid) {
+            const float dd = softplus(z) - target[p];
+            acc_loss = fmaf(dd, dd, acc_loss);
+            d3 = two_over_n * dd / (1.0f + expf(-z));
+        }
+        acc_b3 += d3;
+        sD3[t] = d3;
+        store_row(base + tE, t, h);  // h2 (e's tile is free: layer 1 has completed)
+#pragma unroll
+        for (int i = 0; i < 64; ++i) v[i] = h[i] > 0.0f ? d3 * sW3[i] : 0.0f;  // delta2
+        store_row(base + tD2, t, v);
+        store_col(base + tD2T, t, v);
+        sync_for_mma();
+        if (t == 0) {
+            // delta1 before the mask: delta2 W2  (B = W2^T, K-major over layer-2 units)
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) tc::mma_bf16(tm + 64, dD2 + 2 * ks, dW2T + 2 * ks, id128, ks > 0);
+            // dW2 += delta2^T h1 over the tile's 128 points (M = 64 units, K = points)
+#pragma unroll
+            for (int ks = 0; ks < 8; ++ks) {
+                const uint32_t sub = (uint32_t)(ks >> 2) * kWBytes;
+                tc::mma_bf16(tm + 128, tc::sw128_desc(smem_u32(base + tD2T + sub)) + 2 * (ks & 3),
+                             tc::sw128_desc(smem_u32(base + tH1T + sub)) + 2 * (ks & 3), id64, !first || ks > 0);
+            }
+            tc::mma_commit(&bar);
+        }
+        // column sums while the tensor cores work: dw3_j = sum delta3 h2_j, db2_j = sum delta2_j
+        for (int q = 64 * half; q < 64 * half + 64; ++q) {
+            acc_w3 = fmaf(sD3[q], load_elem(base + tE, q, j), acc_w3);
+            acc_b2 += load_elem(base + tD2, q, j);
+        }
+        if (!(ok = wait_mma(&bar, phase))) break;
+        tmem_row64(row + 64, v);
+        const uint8_t* h1row = base + tH1;
+#pragma unroll
+        for (int i = 0; i < 64; ++i) v[i] = load_elem(h1row, t, i) > 0.0f ? v[i] : 0.0f;  // delta1
+        __syncthreads();  // every column-sum read of delta2 is done before delta1 overwrites it
+        store_row(base + tD2, t, v);
+        store_col(base + tD1T, t, v);
+        sync_for_mma();
+        if (t == 0) {  // dW1 += delta1^T e
+#pragma unroll
+            for (int ks = 0; ks < 8; ++ks) {
+                const uint32_t sub = (uint32_t)(ks >> 2) * kWBytes;
+                tc::mma_bf16(tm + 192, tc::sw128_desc(smem_u32(base + tD1T + sub)) + 2 * (ks & 3),
+                             tc::sw128_desc(smem_u32(base + tET + sub)) + 2 * (ks & 3), id64, !first || ks > 0);
+            }
+            tc::mma_commit(&bar);
+        }
+        for (int q = 64 * half; q < 64 * half + 64; ++q) acc_b1 += load_elem(base + tD2, q, j);
+        if (!(ok = wait_mma(&bar, phase))) break;
+        first = false;
+    }
+    // weight gradients: M = 64 accumulators, row m in lane (m % 16) + 32 (m / 16)
+    if (ok && !first) {  // block-uniform: every lane of each warp takes part in the loads
+        const int m = 16 * warp + lane;
+        float g[64];
+        tmem_row64(row + 128, g);
+        if (lane < 16)
+            for (int i = 0; i < 64; ++i) atomicAdd(&G[oW2 + 64 * m + i], g[i]);
+        tmem_row64(row + 192, g);
+        if (lane < 16)
+            for (int i = 0; i < 64; ++i) atomicAdd(&G[oW1 + 64 * m + i], g[i]);
+    }
+    if (ok) {
+        atomicAdd(&G[oW3 + j], acc_w3);
+        atomicAdd(&G[oB2 + j], acc_b2);
+        atomicAdd(&G[oB1 + j], acc_b1);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            acc_b3 += __shfl_xor_sync(0xffffffffu, acc_b3, o);
+            acc_loss += __shfl_xor_sync(0xffffffffu, acc_loss, o);
+        }
+        if (lane == 0) {
+            sRed[warp][0] = acc_b3;
+            sRed[warp][1] = acc_loss;
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (ok && t == 0) {
+        float b3 = 0.0f, l = 0.0f;
+        for (int w = 0; w < kThreads / 32; ++w) {
+            b3 += sRed[w][0];
+            l += sRed[w][1];
+        }
+        atomicAdd(&G[oB3], b3);
+        atomicAdd(loss_sum, l);
+    }
+    if (warp == 0) tc::tmem_dealloc(tm, 256);
+    if (!ok && t == 0) atomicOr(&g_nacc_mlp_status, 1u);
+}
+
+__global__ void k_mlp_adam(float* __restrict__ P, float* __restrict__ G, float* __restrict__ m,
+                           float* __restrict__ v, float lr, float b1, float b2, float eps, float bc1, float bc2,
+                           uint16_t* __restrict__ Wb) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < NACC_MLP_PARAMS; i += gridDim.x * blockDim.x) {
+        const float g = G[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * g;
+        const float vi = b2 * v[i] + (1.0f - b2) * g * g;
+        m[i] = mi;
+        v[i] = vi;
+        const float p = P[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+        P[i] = p;
+        G[i] = 0.0f;
+        const uint16_t pb = __bfloat16_as_ushort(__float2bfloat16_rn(p));
+        if (i < oB1)
+            Wb[wW1 + i] = pb;
+        else if (i >= oW2 && i < oB2)
+            Wb[wW2 + (i - oW2)] = pb;
+        else if (i >= oW3 && i < oB3)
+            Wb[wW3 + (i - oW3)] = pb;
+    }
+}
+
+__global__ void k_mlp_sync(const float* __restrict__ P, uint16_t* __restrict__ Wb) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < NACC_MLP_WEIGHTS; i += gridDim.x * blockDim.x) {
+        const int src = i < wW2 ? oW1 + i : (i < wW3 ? oW2 + (i - wW2) : oW3 + (i - wW3));
+        Wb[i] = __bfloat16_as_ushort(__float2bfloat16_rn(P[src]));
+    }
+}
+
+__global__ void k_mlp_encode(int64_t n, const float* __restrict__ xyz, float* __restrict__ enc) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        float e[64];
+        encode_point(xyz[3 * p], xyz[3 * p + 1], xyz[3 * p + 2], e);
+        for (int i = 0; i < 64; ++i) enc[64 * p + i] = e[i];
+    }
+}
+
+int persistent_ctas(const void* kernel, int threads, size_t shm, int64_t tiles) {
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, shm) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    return (int)min64((int64_t)per_sm * sm_count(), tiles > 0 ? tiles : 1);
+}
+
+}  // namespace
+
+unsigned int mlp_take_status() {
+    unsigned int v = 0, zero = 0;
+    if (cudaMemcpyFromSymbol(&v, g_nacc_mlp_status, sizeof(v)) != cudaSuccess) return 0;
+    cudaMemcpyToSymbol(g_nacc_mlp_status, &zero, sizeof(zero));
+    return v;
+}
+
+}  // namespace nacc
+
+using namespace nacc;
+
+extern "C" int nacc_mlp_sync(const float* params, uint16_t* weights, void* stream) {
+    clear_error();
+    NACC_CHECK_ARG(params && weights, "params / weights is NULL");
+    k_mlp_sync<<<33, 256, 0, as_stream(stream)>>>(params, weights);
+    NACC_LAUNCH_CHECK();
+    return NACC_OK;
+}
+
+extern "C" int nacc_mlp_forward(int64_t n, const float* xyz, const float* params, const uint16_t* weights,
+                                float* sigma, void* stream) {
+    clear_error();
+    NACC_CHECK_ARG(n >= 0 && n < (int64_t(1) << 40), "n=%lld out of range", (long long)n);
+    if (n == 0) return NACC_OK;
+    NACC_CHECK_ARG(xyz && params && weights && sigma, "a pointer argument is NULL");
+    const size_t shm = 2 * kWBytes + kTileBytes + 1024;
+    NACC_CUDA_TRY(cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    const int64_t tiles = (n + kTile - 1) / kTile;
+    // at most 8 CTAs of 64 tensor-memory columns share an SM's 512 columns
+    int grid = persistent_ctas((const void*)k_mlp_forward, kThreads, shm, tiles);
+    grid = (int)min64(grid, (int64_t)8 * sm_count());
+    k_mlp_forward<<<grid, kThreads, shm, as_stream(stream)>>>(n, xyz, params, weights, sigma);
+    NACC_LAUNCH_CHECK();
+    return NACC_OK;
+}
+
+extern "C" int nacc_mlp_train_grads(int64_t n, const float* xyz, const float* target, const float* params,
+                                    const uint16_t* weights, float* grads, float* loss_sum, void* stream) {
+    clear_error();
+    NACC_CHECK_ARG(n >= 0 && n < (int64_t(1) << 40), "n=%lld out of range", (long long)n);
+    if (n == 0) return NACC_OK;
+    NACC_CHECK_ARG(xyz && target && params && weights && grads && loss_sum, "a pointer argument is NULL");
+    NACC_CUDA_TRY(
+        cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrainSmem));
+    const int64_t tiles = (n + kTile - 1) / kTile;
+    // one CTA per SM (256 tensor-memory columns each, 138 KiB of shared memory)
+    const int grid = (int)min64((int64_t)sm_count(), tiles);
+    k_mlp_train<<<grid, kThreads, kTrainSmem, as_stream(stream)>>>(n, xyz, target, params, weights, grads,
+                                                                   loss_sum, (float)(2.0 / (double)n));
+    NACC_LAUNCH_CHECK();
+    return NACC_OK;
+}
+
+extern "C" int nacc_mlp_adam(float* params, float* grads, float* m, float* v, int64_t step, float lr, float beta1,
+                             float beta2, float eps, uint16_t* weights, void* stream) {
+    clear_error();
+    NACC_CHECK_ARG(params && grads && m && v && weights, "a pointer argument is NULL");
+    NACC_CHECK_ARG(step >= 1, "step=%lld must be >= 1", (long long)step);
+    NACC_CHECK_ARG(beta1 >= 0.0f && beta1 < 1.0f && beta2 >= 0.0f && beta2 < 1.0f, "betas outside [0, 1)");
+    const float bc1 = (float)(1.0 - std::pow((double)beta1, (double)step));
+    const float bc2 = (float)(1.0 - std::pow((double)beta2, (double)step));
+    k_mlp_adam<<<33, 256, 0, as_stream(stream)>>>(params, grads, m, v, lr, beta1, beta2, eps, bc1, bc2, weights);
+    NACC_LAUNCH_CHECK();
+    return NACC_OK;
+}
+
+extern "C" int nacc_mlp_encode(int64_t n, const float* xyz, float* enc, void* stream) {
+    clear_error();
+    NACC_CHECK_ARG(n >= 0 && n < (int64_t(1) << 40), "n=%lld out of range", (long long)n);
+    if (n == 0) return NACC_OK;
+    NACC_CHECK_ARG(xyz && enc, "xyz / enc is NULL");
+    const int blocks = (int)min64((n + 255) / 256, (int64_t)sm_count() * 8);
+    k_mlp_encode<<<blocks, 256, 0, as_stream(stream)>>>(n, xyz, enc);
+    NACC_LAUNCH_CHECK();
+    return NACC_OK;
+}

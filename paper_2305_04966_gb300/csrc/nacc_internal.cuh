@@ -9,6 +9,7 @@
 
 #include "../../include/nacc.h"
 #include "../../include/nacc_harness.h"
+#include "../../include/nacc_proposal.h"
 
 namespace nacc {
 
@@ -18,6 +19,7 @@ namespace nacc {
 void set_error(const char* fmt, ...);
 void clear_error();
 int sm_count();  // multiprocessors of the current device (cached per device)
+unsigned int mlp_take_status();  // reads and clears the proposal network's device status word
 
 #define NACC_CHECK_ARG(cond, ...)                      \
     do {                                               \

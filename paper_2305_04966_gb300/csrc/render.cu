@@ -491,6 +491,7 @@ extern "C" int nacc_device_status(void* stream, int32_t* status_out) {
     NACC_CUDA_TRY(cudaMemcpyFromSymbol(&v, g_nacc_render_status, sizeof(v)));
     const unsigned int zero = 0;
     NACC_CUDA_TRY(cudaMemcpyToSymbol(g_nacc_render_status, &zero, sizeof(zero)));
+    v |= mlp_take_status();
     *status_out = (v & 1u) ? NACC_ERR_TIMEOUT : NACC_OK;
     return NACC_OK;
 }
