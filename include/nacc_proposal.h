@@ -60,6 +60,43 @@ int nacc_mlp_train_grads(int64_t n, const float* xyz, const float* target, const
 int nacc_mlp_adam(float* params, float* grads, float* m, float* v, int64_t step, float lr, float beta1,
                   float beta2, float eps, uint16_t* weights, void* stream);
 
+/*
+ * Density at the midpoints of the bins of rays: point (r, j) = o_r + t d_r
+ * with t = (edges[r][j] + edges[r][j+1]) / 2 (FP32) -> sigma [n_rays][n_bins];
+ * edges [n_rays][n_bins+1].  Same network and precision as nacc_mlp_forward.
+ */
+int nacc_mlp_forward_rays(int64_t n_rays, int32_t n_bins, const float* rays_o, const float* rays_d,
+                          const float* edges, const float* params, const uint16_t* weights, float* sigma,
+                          void* stream);
+
+/*
+ * Initial bins of the proposal estimator: [t_near, t_far] = slab clip of
+ * each ray against the box of the grid's level 0 (individually rounded FP32,
+ * as in nacc_march_grid), intersected with [t_min, t_max], cut into n_bins
+ * equal bins: edges[r][j] = t_near + (t_far - t_near) * (j / n_bins) (each
+ * operation rounded), edges[r][n_bins] = t_far.  A ray that misses gets
+ * t_near = t_far = max(t_min, 0) (empty bins).  edges [n_rays][n_bins+1].
+ */
+int nacc_uniform_edges(const nacc_grid* grid, const float* rays_o, const float* rays_d, int64_t n_rays,
+                       float t_min, float t_max, int32_t n_bins, float* edges, void* stream);
+
+/*
+ * Transmittance weights of densities on a dense bin layout (Eq. 2 /
+ * Table 1 "PDF Approaches"): tau_j = sigma_j (e_{j+1} - e_j), P_j = sum_{i<j}
+ * tau_i, w_j = exp(-P_j) (1 - exp(-tau_j)) (FP32); trans_out [n_rays] (may
+ * be NULL) = exp(-sum tau).  sigmas, weights [n_rays][n_bins].
+ */
+int nacc_dense_weights(int64_t n_rays, int32_t n_bins, const float* edges, const float* sigmas, float* weights,
+                       float* trans_out, void* stream);
+
+/*
+ * The bins as packed samples (nacc_packed layout without ray_indices):
+ * offsets[r] = r * n_bins, t_starts[r*n_bins + j] = edges[r][j], t_ends =
+ * edges[r][j+1], *n_samples = n_rays * n_bins (all [device]).
+ */
+int nacc_edges_to_packed(int64_t n_rays, int32_t n_bins, const float* edges, int64_t* offsets, float* t_starts,
+                         float* t_ends, int64_t* n_samples, void* stream);
+
 /* Diagnostics: the FP32 encoding e(x) of n points -> enc [n][64]. */
 int nacc_mlp_encode(int64_t n, const float* xyz, float* enc, void* stream);
 

@@ -118,3 +118,29 @@ def adam_step(params: dict, grads: dict, state: dict, lr=1e-3, b1=0.9, b2=0.999,
         v[...] = b2 * v + (1 - b2) * gk * gk
         mh, vh = m / (1 - b1 ** t), v / (1 - b2 ** t)
         params[k] = (params[k].astype(np.float64) - lr * mh / (np.sqrt(vh) + eps)).astype(np.float32)
+
+
+def exact_optical_depth(rays_o, rays_d, t_near, t_far, mu, std, peak) -> np.ndarray:
+    """Integral of the blob field's density along each ray over [t_near,
+    t_far] (FP64).  Along x(t) = o + t d a blob's density is a 1-D Gaussian
+    in t: peak exp(-p^2 / 2 s^2) exp(-(t - t*)^2 / 2 s_l^2) with t* the
+    closest approach, p the distance there and s_l = s / |d|; its integral
+    is the difference of two error functions (Eq. 2 with T = exp(-integral))."""
+    from math import erf, pi, sqrt
+    o, d = np.asarray(rays_o, np.float64), np.asarray(rays_d, np.float64)
+    out = np.zeros(o.shape[0])
+    for i in range(o.shape[0]):
+        dd = d[i] @ d[i]
+        if not (t_far[i] > t_near[i]) or dd == 0.0:
+            continue
+        acc = 0.0
+        for b in range(len(peak)):
+            m = np.asarray(mu[b], np.float64) - o[i]
+            ts = (m @ d[i]) / dd
+            p2 = max(m @ m - ts * ts * dd, 0.0)
+            s = float(std[b])
+            sl = s / sqrt(dd)
+            acc += float(peak[b]) * np.exp(-p2 / (2 * s * s)) * sl * sqrt(pi / 2) * (
+                erf((t_far[i] - ts) / (sl * sqrt(2))) - erf((t_near[i] - ts) / (sl * sqrt(2))))
+        out[i] = acc
+    return out

@@ -8,13 +8,14 @@ F = 1 - T, Eq. 3).  The kernels live in ``libnacc.so`` behind the C ABI of
 ``include/nacc.h``; this package only marshals torch tensors.
 """
 from ._abi import NaccError, load as load_library
-from .api import (BlobField, MarchBuffers, OccupancyGrid, PackedSamples, ProposalMLP, RenderFn,
-                  UpdateBuffers, density_grid, field_eval, field_points, grid_points, l2_loss, march_grid,
-                  mlp_encode, render, render_bwd, render_fwd, sample_pdf, update_grid)
+from .api import (BlobField, MarchBuffers, OccupancyGrid, PackedSamples, ProposalMLP, ProposalSampler, RenderFn,
+                  UpdateBuffers, dense_weights, density_grid, edges_to_packed, field_eval, field_points,
+                  grid_points, l2_loss, march_grid, mlp_encode, render, render_bwd, render_fwd, sample_pdf,
+                  uniform_edges, update_grid)
 
 __all__ = [
     "NaccError", "load_library", "BlobField", "MarchBuffers", "OccupancyGrid", "PackedSamples",
     "RenderFn", "UpdateBuffers", "density_grid", "field_eval", "field_points", "grid_points",
     "l2_loss", "march_grid", "render", "render_bwd", "render_fwd", "sample_pdf", "update_grid",
-    "ProposalMLP", "mlp_encode",
+    "ProposalMLP", "ProposalSampler", "mlp_encode", "uniform_edges", "dense_weights", "edges_to_packed",
 ]

@@ -72,6 +72,10 @@ SIGNATURES = {
     "nacc_mlp_train_grads": (c_i32, [c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "nacc_mlp_adam": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, c_f32, c_f32, c_f32, c_f32, c_vp, c_vp]),
     "nacc_mlp_encode": (c_i32, [c_i64, c_vp, c_vp, c_vp]),
+    "nacc_mlp_forward_rays": (c_i32, [c_i64, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "nacc_uniform_edges": (c_i32, [P(Grid), c_vp, c_vp, c_i64, c_f32, c_f32, c_i32, c_vp, c_vp]),
+    "nacc_dense_weights": (c_i32, [c_i64, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "nacc_edges_to_packed": (c_i32, [c_i64, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
 }
 
 MLP_PARAMS = 8385

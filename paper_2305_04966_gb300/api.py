@@ -450,6 +450,16 @@ class ProposalMLP:
                   _stream(dev))
         return sig
 
+    def forward_rays(self, rays_o, rays_d, edges: torch.Tensor, out=None) -> torch.Tensor:
+        """Density at the bin midpoints of rays: edges [n][nb+1] -> [n][nb]."""
+        dev = edges.device
+        n, nb = int(edges.shape[0]), int(edges.shape[1]) - 1
+        _check(edges, "edges", _F32, dev, (n, nb + 1))
+        sig = out if out is not None else torch.empty((n, nb), dtype=_F32, device=dev)
+        _abi.call("nacc_mlp_forward_rays", n, nb, _ptr(rays_o), _ptr(rays_d), _ptr(edges), _ptr(self.params),
+                  _ptr(self.weights), _ptr(sig), _stream(dev))
+        return sig
+
     def accumulate_grads(self, xyz: torch.Tensor, target: torch.Tensor):
         """Adds dL/dparams of L = mean (density - target)^2 into ``grads``
         and sum (density - target)^2 into ``loss_sum``."""
@@ -474,6 +484,76 @@ class ProposalMLP:
         loss = self.loss_sum / xyz.shape[0]
         self.adam(lr)
         return loss
+
+
+def uniform_edges(grid: OccupancyGrid, rays_o, rays_d, n_bins: int, t_min: float = 0.0, t_max: float = 1e10,
+                  out=None) -> torch.Tensor:
+    """Initial bins of the proposal estimator: n_bins equal bins of each ray's
+    clip against the box of the grid's level 0 -> edges [n][n_bins+1]."""
+    dev = rays_o.device
+    n = int(rays_o.shape[0])
+    _check(rays_o, "rays_o", _F32, dev, (n, 3))
+    _check(rays_d, "rays_d", _F32, dev, (n, 3))
+    e = out if out is not None else torch.empty((n, n_bins + 1), dtype=_F32, device=dev)
+    _check(e, "edges", _F32, dev, (n, n_bins + 1))
+    _abi.call("nacc_uniform_edges", ctypes.byref(grid.c_struct()), _ptr(rays_o), _ptr(rays_d), n, float(t_min),
+              float(t_max), int(n_bins), _ptr(e), _stream(dev))
+    return e
+
+
+def dense_weights(edges: torch.Tensor, sigmas: torch.Tensor, out=None, trans=None) -> torch.Tensor:
+    """w_j = T_j (1 - exp(-sigma_j dt_j)) on a dense [n][n_bins] layout (Eq. 2)."""
+    dev = edges.device
+    n, nb = int(sigmas.shape[0]), int(sigmas.shape[1])
+    _check(edges, "edges", _F32, dev, (n, nb + 1))
+    _check(sigmas, "sigmas", _F32, dev, (n, nb))
+    w = out if out is not None else torch.empty((n, nb), dtype=_F32, device=dev)
+    _abi.call("nacc_dense_weights", n, nb, _ptr(edges), _ptr(sigmas), _ptr(w), _ptr(trans) if trans is not None
+              else None, _stream(dev))
+    return w
+
+
+def edges_to_packed(edges: torch.Tensor, out: PackedSamples | None = None) -> PackedSamples:
+    """Bins [n][nb+1] -> packed samples (nb per ray, no ray_indices)."""
+    dev = edges.device
+    n, nb = int(edges.shape[0]), int(edges.shape[1]) - 1
+    if out is None:
+        out = PackedSamples(torch.empty(n + 1, dtype=torch.int64, device=dev), None,
+                            torch.empty(n * nb, dtype=_F32, device=dev), torch.empty(n * nb, dtype=_F32, device=dev),
+                            torch.empty(1, dtype=torch.int64, device=dev))
+    _abi.call("nacc_edges_to_packed", n, nb, _ptr(edges), _ptr(out.offsets), _ptr(out.t_starts), _ptr(out.t_ends),
+              _ptr(out.n_samples_dev), _stream(dev))
+    return out
+
+
+class ProposalSampler:
+    """The learned-proposal estimator (Table 1 "PDF Approaches"): n0 uniform
+    bins per ray; for each round, the proposal density at the bin midpoints,
+    its transmittance weights (Eq. 2) and inverse transform sampling (Eq. 1)
+    to the next round's bins; the last round's bins become the packed samples
+    the radiance field and the renderer consume.  Rounds (64, 32) then 32
+    final samples by default."""
+
+    def __init__(self, mlp: ProposalMLP, grid: OccupancyGrid, n_rays: int, rounds=(64, 32), n_final: int = 32,
+                 device="cuda"):
+        self.mlp, self.grid, self.rounds, self.n_final = mlp, grid, tuple(rounds), int(n_final)
+        dev = torch.device(device)
+        self.n_rays = int(n_rays)
+        sizes = list(self.rounds) + [self.n_final]
+        self.edges = [torch.empty((n_rays, nb + 1), dtype=_F32, device=dev) for nb in sizes]
+        self.sig = [torch.empty((n_rays, nb), dtype=_F32, device=dev) for nb in self.rounds]
+        self.w = [torch.empty((n_rays, nb), dtype=_F32, device=dev) for nb in self.rounds]
+        self.packed = edges_to_packed(self.edges[-1])
+
+    def sample(self, rays_o, rays_d, t_min: float = 0.0, t_max: float = 1e10, stratified: bool = False,
+               seed: int = 0) -> PackedSamples:
+        e = uniform_edges(self.grid, rays_o, rays_d, self.rounds[0], t_min, t_max, out=self.edges[0])
+        for i, nb in enumerate(self.rounds):
+            s = self.mlp.forward_rays(rays_o, rays_d, e, out=self.sig[i])
+            w = dense_weights(e, s, out=self.w[i])
+            n_next = self.rounds[i + 1] if i + 1 < len(self.rounds) else self.n_final
+            e = sample_pdf(e, w, n_next, stratified, seed + i, out=self.edges[i + 1])
+        return edges_to_packed(e, out=self.packed)
 
 
 def mlp_encode(xyz: torch.Tensor) -> torch.Tensor:

@@ -141,8 +141,34 @@ __device__ __forceinline__ void load_weight_tile(uint8_t* dst, const uint16_t* w
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_mlp_forward(int64_t n, const float* __restrict__ xyz,
-                                                          const float* __restrict__ P,
+// Where the points come from: an array xyz [n][3], or the midpoints of the
+// bins of rays (point p = bin p % nb of ray p / nb, x = o + t d with t the
+// midpoint of edges [ray][bin], [ray][bin + 1]).
+struct PointSrc {
+    const float* xyz;
+    const float* o;
+    const float* d;
+    const float* edges;
+    int nb;
+};
+
+__device__ __forceinline__ void point_of(const PointSrc& S, int64_t p, float& x, float& y, float& z) {
+    if (S.xyz) {
+        x = S.xyz[3 * p];
+        y = S.xyz[3 * p + 1];
+        z = S.xyz[3 * p + 2];
+        return;
+    }
+    const int64_t r = p / S.nb;
+    const int64_t b = p - r * S.nb;
+    const float* e = S.edges + r * (S.nb + 1) + b;
+    const float t = 0.5f * (e[0] + e[1]);
+    x = fmaf(S.d[3 * r], t, S.o[3 * r]);
+    y = fmaf(S.d[3 * r + 1], t, S.o[3 * r + 1]);
+    z = fmaf(S.d[3 * r + 2], t, S.o[3 * r + 2]);
+}
+
+__global__ void __launch_bounds__(kThreads) k_mlp_forward(int64_t n, PointSrc S, const float* __restrict__ P,
                                                           const uint16_t* __restrict__ Wb,
                                                           float* __restrict__ sigma) {
     extern __shared__ uint8_t smem_raw[];
@@ -182,11 +208,14 @@ __global__ void __launch_bounds__(kThreads) k_mlp_forward(int64_t n, const float
     for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         const int64_t p = tile * kTile + t;
         float v[64];
-        if (p < n)
-            encode_point(xyz[3 * p], xyz[3 * p + 1], xyz[3 * p + 2], v);
-        else
+        if (p < n) {
+            float x, y, z;
+            point_of(S, p, x, y, z);
+            encode_point(x, y, z, v);
+        } else {
 #pragma unroll
             for (int i = 0; i < 64; ++i) v[i] = 0.0f;
+        }
         store_row(sX, t, v);
         sync_for_mma();
         if (t == 0) {
@@ -468,21 +497,43 @@ extern "C" int nacc_mlp_sync(const float* params, uint16_t* weights, void* strea
     return NACC_OK;
 }
 
-extern "C" int nacc_mlp_forward(int64_t n, const float* xyz, const float* params, const uint16_t* weights,
-                                float* sigma, void* stream) {
-    clear_error();
-    NACC_CHECK_ARG(n >= 0 && n < (int64_t(1) << 40), "n=%lld out of range", (long long)n);
-    if (n == 0) return NACC_OK;
-    NACC_CHECK_ARG(xyz && params && weights && sigma, "a pointer argument is NULL");
+namespace nacc {
+namespace {
+int launch_forward(int64_t n, const PointSrc& S, const float* params, const uint16_t* weights, float* sigma,
+                   cudaStream_t st) {
     const size_t shm = 2 * kWBytes + kTileBytes + 1024;
     NACC_CUDA_TRY(cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
     const int64_t tiles = (n + kTile - 1) / kTile;
     // at most 8 CTAs of 64 tensor-memory columns share an SM's 512 columns
     int grid = persistent_ctas((const void*)k_mlp_forward, kThreads, shm, tiles);
     grid = (int)min64(grid, (int64_t)8 * sm_count());
-    k_mlp_forward<<<grid, kThreads, shm, as_stream(stream)>>>(n, xyz, params, weights, sigma);
+    k_mlp_forward<<<grid, kThreads, shm, st>>>(n, S, params, weights, sigma);
     NACC_LAUNCH_CHECK();
     return NACC_OK;
+}
+}  // namespace
+}  // namespace nacc
+
+extern "C" int nacc_mlp_forward_rays(int64_t n_rays, int32_t n_bins, const float* rays_o, const float* rays_d,
+                                     const float* edges, const float* params, const uint16_t* weights,
+                                     float* sigma, void* stream) {
+    clear_error();
+    NACC_CHECK_ARG(n_rays >= 0 && n_rays < (int64_t(1) << 34), "n_rays=%lld out of range", (long long)n_rays);
+    NACC_CHECK_ARG(n_bins >= 1 && n_bins <= 4096, "n_bins=%d outside [1, 4096]", n_bins);
+    if (n_rays == 0) return NACC_OK;
+    NACC_CHECK_ARG(rays_o && rays_d && edges && params && weights && sigma, "a pointer argument is NULL");
+    PointSrc S{nullptr, rays_o, rays_d, edges, n_bins};
+    return launch_forward(n_rays * n_bins, S, params, weights, sigma, as_stream(stream));
+}
+
+extern "C" int nacc_mlp_forward(int64_t n, const float* xyz, const float* params, const uint16_t* weights,
+                                float* sigma, void* stream) {
+    clear_error();
+    NACC_CHECK_ARG(n >= 0 && n < (int64_t(1) << 40), "n=%lld out of range", (long long)n);
+    if (n == 0) return NACC_OK;
+    NACC_CHECK_ARG(xyz && params && weights && sigma, "a pointer argument is NULL");
+    PointSrc S{xyz, nullptr, nullptr, nullptr, 1};
+    return launch_forward(n, S, params, weights, sigma, as_stream(stream));
 }
 
 extern "C" int nacc_mlp_train_grads(int64_t n, const float* xyz, const float* target, const float* params,

@@ -126,3 +126,103 @@ def test_training_fits_the_blob_field(nacc, P):
     first = float(losses[0].item())
     last = float(torch.stack(losses[-20:]).mean().item())
     assert math.isfinite(last) and last < first / 10.0, (first, last)
+
+
+# ---------------------------------------------------------------------------
+# proposal sampling pipeline
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+def _c1_rays_with_misses(n=4096):
+    w = workloads.c1_forward(n)
+    o, d = w.rays_o.copy(), w.rays_d.copy()
+    d[:64] = -d[:64]  # pointing away from the box: misses
+    return o, d
+
+
+def _edges_oracle(orc, o, d, nb, t_min=0.0, t_max=1e10):
+    tn, tf, hit = orc.ray_clip(o, d, (-1.5,) * 3, (1.5,) * 3, 32, 1, t_min, t_max)
+    tn = np.where(hit, tn, np.float32(max(t_min, 0.0))).astype(np.float32)
+    tf = np.where(hit, tf, tn).astype(np.float32)
+    span = (tf - tn).astype(np.float32)
+    frac = (np.arange(nb, dtype=np.float32) / np.float32(nb)).astype(np.float32)
+    e = (tn[:, None] + (span[:, None] * frac[None, :]).astype(np.float32)).astype(np.float32)
+    return np.concatenate([e, tf[:, None]], 1)
+
+
+def test_uniform_edges_bit_exact(nacc, orc):
+    o, d = _c1_rays_with_misses()
+    grid = nacc.OccupancyGrid.empty((-1.5,) * 3, (1.5,) * 3, 32, 1, DEV)
+    got = nacc.uniform_edges(grid, torch.as_tensor(o, device=DEV), torch.as_tensor(d, device=DEV), 64).cpu().numpy()
+    np.testing.assert_array_equal(got, _edges_oracle(orc, o, d, 64))
+
+
+def test_dense_weights_match_oracle(nacc, orc):
+    g = workloads.rng(98)
+    n, nb = 3000, 64
+    e = np.sort(g.uniform(1.0, 6.0, (n, nb + 1)), axis=1).astype(np.float32)
+    s = (g.exponential(3.0, (n, nb)) * (g.random((n, nb)) < 0.4)).astype(np.float32)
+    tr = torch.empty(n, device=DEV)
+    got = nacc.dense_weights(torch.as_tensor(e, device=DEV), torch.as_tensor(s, device=DEV), trans=tr).cpu().numpy()
+    off = np.arange(n + 1, dtype=np.int64) * nb
+    exp = orc.render_fwd(off, e[:, :-1].reshape(-1), e[:, 1:].reshape(-1), s.reshape(-1), np.zeros((n * nb, 3)))
+    np.testing.assert_allclose(got.reshape(-1), exp["weights"], rtol=0, atol=1e-5)
+    np.testing.assert_allclose(tr.cpu().numpy(), exp["trans"], rtol=0, atol=1e-5)
+
+
+def test_edges_to_packed_exact(nacc):
+    g = workloads.rng(99)
+    e = np.sort(g.uniform(0.0, 5.0, (777, 33)), axis=1).astype(np.float32)
+    pk = nacc.edges_to_packed(torch.as_tensor(e, device=DEV))
+    assert pk.n_samples() == 777 * 32
+    np.testing.assert_array_equal(pk.offsets.cpu().numpy(), np.arange(778) * 32)
+    np.testing.assert_array_equal(pk.t_starts.cpu().numpy(), e[:, :-1].reshape(-1))
+    np.testing.assert_array_equal(pk.t_ends.cpu().numpy(), e[:, 1:].reshape(-1))
+
+
+def _midpoints(o, d, e):
+    t = (0.5 * (e[:, :-1].astype(np.float64) + e[:, 1:])).astype(np.float32)
+    return (o[:, None, :] + d[:, None, :] * t[:, :, None]).reshape(-1, 3)
+
+
+def test_forward_rays_matches_oracle(nacc, P, orc):
+    o, d = _c1_rays_with_misses(2048)
+    p = _params(P, 100)
+    mlp = nacc.ProposalMLP(torch.as_tensor(_flat(p), device=DEV))
+    e = _edges_oracle(orc, o, d, 64)
+    got = mlp.forward_rays(torch.as_tensor(o, device=DEV), torch.as_tensor(d, device=DEV),
+                           torch.as_tensor(e, device=DEV)).cpu().numpy().reshape(-1)
+    exp = P.forward(p, _midpoints(o, d, e))["sigma"]
+    rel = np.abs(got - exp) / np.maximum(np.abs(exp), 1e-3)
+    assert np.median(rel) < 1e-4 and np.mean(rel) < 3e-3 and rel.max() < 5e-2, (np.median(rel), rel.mean(), rel.max())
+
+
+def test_sampler_matches_oracle_composition(nacc, P, orc):
+    """Two rounds (64 -> 32 -> 32 bins) of proposal density, weights and
+    inverse-CDF resampling against the same chain of oracle functions."""
+    o, d = _c1_rays_with_misses(2048)
+    n = o.shape[0]
+    p = _params(P, 101)
+    p["b3"] = np.array([1.0], np.float32)  # some opacity for untrained weights
+    mlp = nacc.ProposalMLP(torch.as_tensor(_flat(p), device=DEV))
+    grid = nacc.OccupancyGrid.empty((-1.5,) * 3, (1.5,) * 3, 32, 1, DEV)
+    sampler = nacc.ProposalSampler(mlp, grid, n, rounds=(64, 32), n_final=32, device=DEV)
+    pk = sampler.sample(torch.as_tensor(o, device=DEV), torch.as_tensor(d, device=DEV))
+    got = np.stack([pk.t_starts.cpu().numpy().reshape(n, 32), pk.t_ends.cpu().numpy().reshape(n, 32)])
+    e = _edges_oracle(orc, o, d, 64)
+    for nb, n_next in ((64, 32), (32, 32)):
+        s = P.forward(p, _midpoints(o, d, e))["sigma"]
+        off = np.arange(n + 1, dtype=np.int64) * nb
+        w = orc.render_fwd(off, e[:, :-1].reshape(-1), e[:, 1:].reshape(-1), s, np.zeros((n * nb, 3)))["weights"]
+        e = orc.sample_pdf(e, w.reshape(n, nb).astype(np.float32), n_next)
+    exp = np.stack([e[:, :-1], e[:, 1:]])
+    span = np.maximum(e[:, -1] - e[:, 0], 1e-6)[None, :, None]
+    err = np.abs(got - exp) / span
+    assert np.quantile(err, 0.99) < 2e-3 and err.mean() < 2e-4, (np.quantile(err, 0.99), err.mean(), err.max())
+    np.testing.assert_array_equal(got[:, :64], exp[:, :64])  # misses: empty bins, identical

@@ -596,3 +596,21 @@ def test_proposal_adam_first_step_closed_form():
     P.adam_step(p, g, st, lr=0.01)
     exp = np.array([1.0, -2.0, 0.5]) - 0.01 * g["b1"] / (np.abs(g["b1"]) + 1e-8)
     np.testing.assert_allclose(p["b1"], exp.astype(np.float32), rtol=0, atol=0)
+
+
+def test_exact_optical_depth_matches_fine_quadrature(orc):
+    """The closed-form line integral of the 8-blob field equals the oracle's
+    FP64 compositing of a fine lattice (Eq. 2, dt -> 0) on a few rays."""
+    from oracle import proposal as P
+    w = workloads.c1_forward(6)
+    tn, tf, hit = orc.ray_clip(w.rays_o, w.rays_d, (-1.5,) * 3, (1.5,) * 3, 128, 1, 0.0, 1e10)
+    exact = P.exact_optical_depth(w.rays_o, w.rays_d, tn.astype(np.float64), tf.astype(np.float64),
+                                  w.blobs.mu, w.blobs.std, w.blobs.peak)
+    for r in np.nonzero(hit)[0]:
+        N = 40000
+        ts = np.linspace(tn[r], tf[r], N + 1)
+        t0, t1 = ts[:-1].astype(np.float32), ts[1:].astype(np.float32)
+        sig, rgb = orc.field_samples(w.rays_o[r:r + 1], w.rays_d[r:r + 1], np.zeros(N, np.int32), t0, t1, w.blobs)
+        out = orc.render_fwd(np.array([0, N]), t0, t1, sig, rgb)
+        assert -math.log(out["trans"][0]) == pytest.approx(exact[r], rel=2e-4, abs=1e-6)
+    assert hit.sum() >= 3
