@@ -349,6 +349,126 @@ def aux_measure(torch, nacc, dev, flush, hbm, steps=10):
     }
 
 
+def proposal_measure(torch, nacc, dev, flush, steps=5, train_steps=1024, batch=65536, n_pairs=1 << 24,
+                     sample_rays=2000):
+    """The learned-proposal path beside the plain grid path on the 262,144-ray
+    training batch (100 cameras, 64-blob field).  The proposal network is
+    first trained (timed, outside the step) on n_pairs (xyz, density) pairs
+    drawn along the batch's rays: uniform t in each ray's clip of the scene
+    box, density from the analytic field; train_steps Adam steps of batch
+    points.  Then each path renders the batch: grid = march with early stop
+    + field + render_fwd; proposal = two rounds (64 -> 32 -> 32 bins) + field
+    + render_fwd.  Returns rays/s of both, and their final transmittance on
+    a fixed sample of rays (the exact values come from the CPU leg)."""
+    w = workloads.c3_training()
+    g, m = w.grid, w.march
+    n = w.n_rays
+    field = nacc.BlobField.from_numpy(w.blobs, dev)
+    grid = nacc.OccupancyGrid.empty(g.aabb_min, g.aabb_max, g.res, g.n_levels, dev)
+    nacc.density_grid(grid, field, 0.01)
+    box = nacc.OccupancyGrid.empty(g.aabb_min, g.aabb_max, 32, 1, dev)
+    o = torch.as_tensor(w.rays_o).to(dev)
+    d = torch.as_tensor(w.rays_d).to(dev)
+    # training pairs
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(0x5EED + 4)
+    e1 = nacc.uniform_edges(box, o, d, 1, m.t_min, m.t_max)
+    ri = torch.randint(0, n, (n_pairs,), generator=gen, device=dev)
+    u = torch.rand(n_pairs, generator=gen, device=dev)
+    t = e1[ri, 0] + u * (e1[ri, 1] - e1[ri, 0])
+    xyz = (o[ri] + d[ri] * t[:, None]).contiguous()
+    sig = nacc.field_points(field, xyz)
+    mlp = nacc.ProposalMLP.init(seed=11, device=dev)
+    perm = torch.randperm(n_pairs, generator=gen, device=dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    losses = []
+    for it in range(train_steps):
+        j = (it * batch) % n_pairs
+        idx = perm[j:j + batch]
+        lr = 3e-3 if it < train_steps // 2 else 1e-3
+        losses.append(mlp.train_step(xyz[idx].contiguous(), sig[idx].contiguous(), lr=lr))
+    b.record()
+    torch.cuda.synchronize()
+    train_ms = a.elapsed_time(b)
+    loss_first, loss_last = float(losses[0].item()), float(torch.stack(losses[-16:]).mean().item())
+    del xyz, sig, ri, u, t, perm
+
+    bufs = nacc.MarchBuffers(n, n * m.max_steps, dev)
+    fs = torch.empty(n * m.max_steps, device=dev)
+    fc = torch.empty((n * m.max_steps, 3), device=dev)
+    sampler = nacc.ProposalSampler(mlp, box, n, rounds=(64, 32), n_final=32, device=dev)
+    ps = torch.empty(n * 32, device=dev)
+    pc = torch.empty((n * 32, 3), device=dev)
+    bg = w.bg
+
+    def grid_path():
+        pk = nacc.march_grid(grid, o, d, m.step, m.max_steps, m.t_min, m.t_max, m.early_stop_eps, field=field,
+                             buffers=bufs)
+        nacc.field_eval(field, o, d, pk, out=(fs, fc))
+        return nacc.render_fwd(pk.offsets, pk.t_starts, pk.t_ends, fs, fc, bg, 0.0)[3]
+
+    def prop_path():
+        pk = sampler.sample(o, d, m.t_min, m.t_max)
+        nacc.field_eval(field, o, d, pk, out=(ps, pc))
+        return nacc.render_fwd(pk.offsets, pk.t_starts, pk.t_ends, ps, pc, bg, 0.0)[3]
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        tot = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            a.record()
+            out = fn()
+            b.record()
+            torch.cuda.synchronize()
+            tot += a.elapsed_time(b)
+        return tot / steps, out
+
+    grid_ms, T_grid = timed(grid_path)
+    prop_ms, T_prop = timed(prop_path)
+    sel = np.linspace(0, n - 1, sample_rays).astype(np.int64)
+    return {
+        "workload": w.name, "n_rays": n,
+        "grid_path": {"rays/s": n / (grid_ms / 1e3), "ms": grid_ms, "samples": bufs.packed.n_samples(),
+                      "early_stop_eps": m.early_stop_eps},
+        "proposal_path": {"rays/s": n / (prop_ms / 1e3), "ms": prop_ms, "samples": n * 32,
+                          "rounds": [64, 32], "final_samples_per_ray": 32},
+        "training": {"pairs": n_pairs, "steps": train_steps, "batch": batch, "ms": train_ms,
+                     "mse_first": loss_first, "mse_last": loss_last},
+        # the two paths integrate over different ranges (cascade vs scene box):
+        # this difference includes the density outside the scene box
+        "T_abs_diff_proposal_vs_grid": {"mean": float((T_prop - T_grid).abs().mean()),
+                                        "p99": float((T_prop - T_grid).abs().quantile(0.99))},
+        "_sample": {"rays": sel, "T_grid": T_grid.cpu().numpy()[sel], "T_prop": T_prop.cpu().numpy()[sel],
+                    "w": w},
+    }
+
+
+def proposal_exact_error(prop):
+    """CPU leg: the exact transmittance of the sampled rays (oracle closed
+    form of the blob field's line integral) over each path's own range --
+    the cascade's outermost box for the grid path, the scene box for the
+    proposal's bins -- and each path's error against it."""
+    import oracle
+    from oracle import proposal as P
+    s = prop.pop("_sample")
+    w, sel = s["w"], s["rays"]
+    o, d = w.rays_o[sel], w.rays_d[sel]
+    out = {"rays": int(len(sel))}
+    for name, levels, Tp in (("grid", w.grid.n_levels, s["T_grid"]), ("proposal", 1, s["T_prop"])):
+        tn, tf, hit = oracle.ray_clip(o, d, w.grid.aabb_min, w.grid.aabb_max, w.grid.res, levels, w.march.t_min,
+                                      w.march.t_max)
+        tau = P.exact_optical_depth(o, d, tn.astype(np.float64), np.where(hit, tf, tn).astype(np.float64),
+                                    w.blobs.mu, w.blobs.std, w.blobs.peak)
+        err = np.abs(Tp - np.exp(-tau))
+        out[name + "_mean_abs"] = float(err.mean())
+        out[name + "_p99"] = float(np.quantile(err, 0.99))
+        out[name + "_range"] = "outermost cascade box" if levels > 1 else "scene box (level 0)"
+    prop["T_error_vs_exact"] = out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -484,6 +604,11 @@ def run_ours(args):
     aux = None
     if rank == 0 and not args.no_aux:
         aux = aux_measure(torch, nacc, dev, flush, hbm)
+        aux["proposal"] = proposal_measure(torch, nacc, dev, flush)
+        if args.no_cpu_baseline:
+            aux["proposal"].pop("_sample")
+        else:
+            proposal_exact_error(aux["proposal"])
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
