@@ -320,6 +320,11 @@ def aux_measure(torch, nacc, dev, flush, hbm, steps=10):
     weights = torch.rand((nr, nb), generator=g, device=dev)
     outp = torch.empty((nr, no + 1), dtype=torch.float32, device=dev)
 
+    def comb_path():
+        pk = combined.sample(o, d, m.t_min, m.t_max)
+        nacc.field_eval(field, o, d, pk, out=(ps, pc))
+        return nacc.render_fwd(pk.offsets, pk.t_starts, pk.t_ends, ps, pc, bg, 0.0)[3]
+
     def timed(fn):
         for _ in range(3):
             fn()
@@ -351,11 +356,13 @@ def aux_measure(torch, nacc, dev, flush, hbm, steps=10):
 
 def proposal_measure(torch, nacc, dev, flush, steps=5, train_steps=1024, batch=65536, n_pairs=1 << 24,
                      sample_rays=2000):
-    """The learned-proposal path beside the plain grid path on the 262,144-ray
-    training batch (100 cameras, 64-blob field).  The proposal network is
+    """The learned-proposal path and the combined path (grid range + proposal)
+    beside the plain grid path on the 262,144-ray training batch (100
+    cameras, 64-blob field).  The proposal network is
     first trained (timed, outside the step) on n_pairs (xyz, density) pairs
-    drawn along the batch's rays: uniform t in each ray's clip of the scene
-    box, density from the analytic field; train_steps Adam steps of batch
+    drawn along the batch's rays -- uniform t in each ray's clip of the scene
+    box for half of them, in its occupied grid range for the other half --
+    with the density of the analytic field; train_steps Adam steps of batch
     points.  Then each path renders the batch: grid = march with early stop
     + field + render_fwd; proposal = two rounds (64 -> 32 -> 32 bins) + field
     + render_fwd.  Returns rays/s of both, and their final transmittance on
@@ -372,10 +379,16 @@ def proposal_measure(torch, nacc, dev, flush, steps=5, train_steps=1024, batch=6
     # training pairs
     gen = torch.Generator(device=dev)
     gen.manual_seed(0x5EED + 4)
+    # half of the pairs along each ray's scene-box range (where the proposal
+    # path samples), half along its occupied grid range (where the combined
+    # path samples: the cascade reaches past the scene box)
     e1 = nacc.uniform_edges(box, o, d, 1, m.t_min, m.t_max)
+    lo, hi = nacc.occupied_range(grid, o, d, m.step, m.max_steps, m.t_min, m.t_max)
     ri = torch.randint(0, n, (n_pairs,), generator=gen, device=dev)
     u = torch.rand(n_pairs, generator=gen, device=dev)
-    t = e1[ri, 0] + u * (e1[ri, 1] - e1[ri, 0])
+    a0 = torch.where(torch.arange(n_pairs, device=dev) < n_pairs // 2, e1[ri, 0], lo[ri])
+    a1 = torch.where(torch.arange(n_pairs, device=dev) < n_pairs // 2, e1[ri, 1], hi[ri])
+    t = a0 + u * (a1 - a0)
     xyz = (o[ri] + d[ri] * t[:, None]).contiguous()
     sig = nacc.field_points(field, xyz)
     mlp = nacc.ProposalMLP.init(seed=11, device=dev)
@@ -392,12 +405,13 @@ def proposal_measure(torch, nacc, dev, flush, steps=5, train_steps=1024, batch=6
     torch.cuda.synchronize()
     train_ms = a.elapsed_time(b)
     loss_first, loss_last = float(losses[0].item()), float(torch.stack(losses[-16:]).mean().item())
-    del xyz, sig, ri, u, t, perm
+    del xyz, sig, ri, u, t, perm, a0, a1
 
     bufs = nacc.MarchBuffers(n, n * m.max_steps, dev)
     fs = torch.empty(n * m.max_steps, device=dev)
     fc = torch.empty((n * m.max_steps, 3), device=dev)
     sampler = nacc.ProposalSampler(mlp, box, n, rounds=(64, 32), n_final=32, device=dev)
+    combined = nacc.CombinedSampler(mlp, grid, n, m.step, m.max_steps, rounds=(64, 32), n_final=32, device=dev)
     ps = torch.empty(n * 32, device=dev)
     pc = torch.empty((n * 32, 3), device=dev)
     bg = w.bg
@@ -410,6 +424,11 @@ def proposal_measure(torch, nacc, dev, flush, steps=5, train_steps=1024, batch=6
 
     def prop_path():
         pk = sampler.sample(o, d, m.t_min, m.t_max)
+        nacc.field_eval(field, o, d, pk, out=(ps, pc))
+        return nacc.render_fwd(pk.offsets, pk.t_starts, pk.t_ends, ps, pc, bg, 0.0)[3]
+
+    def comb_path():
+        pk = combined.sample(o, d, m.t_min, m.t_max)
         nacc.field_eval(field, o, d, pk, out=(ps, pc))
         return nacc.render_fwd(pk.offsets, pk.t_starts, pk.t_ends, ps, pc, bg, 0.0)[3]
 
@@ -428,6 +447,7 @@ def proposal_measure(torch, nacc, dev, flush, steps=5, train_steps=1024, batch=6
 
     grid_ms, T_grid = timed(grid_path)
     prop_ms, T_prop = timed(prop_path)
+    comb_ms, T_comb = timed(comb_path)
     sel = np.linspace(0, n - 1, sample_rays).astype(np.int64)
     return {
         "workload": w.name, "n_rays": n,
@@ -435,6 +455,9 @@ def proposal_measure(torch, nacc, dev, flush, steps=5, train_steps=1024, batch=6
                       "early_stop_eps": m.early_stop_eps},
         "proposal_path": {"rays/s": n / (prop_ms / 1e3), "ms": prop_ms, "samples": n * 32,
                           "rounds": [64, 32], "final_samples_per_ray": 32},
+        "combined_path": {"rays/s": n / (comb_ms / 1e3), "ms": comb_ms, "samples": n * 32,
+                          "rounds": [64, 32], "final_samples_per_ray": 32,
+                          "initial_range": "first to last occupied lattice point of the grid"},
         "training": {"pairs": n_pairs, "steps": train_steps, "batch": batch, "ms": train_ms,
                      "mse_first": loss_first, "mse_last": loss_last},
         # the two paths integrate over different ranges (cascade vs scene box):
@@ -442,7 +465,7 @@ def proposal_measure(torch, nacc, dev, flush, steps=5, train_steps=1024, batch=6
         "T_abs_diff_proposal_vs_grid": {"mean": float((T_prop - T_grid).abs().mean()),
                                         "p99": float((T_prop - T_grid).abs().quantile(0.99))},
         "_sample": {"rays": sel, "T_grid": T_grid.cpu().numpy()[sel], "T_prop": T_prop.cpu().numpy()[sel],
-                    "w": w},
+                    "T_comb": T_comb.cpu().numpy()[sel], "w": w},
     }
 
 
@@ -457,7 +480,8 @@ def proposal_exact_error(prop):
     w, sel = s["w"], s["rays"]
     o, d = w.rays_o[sel], w.rays_d[sel]
     out = {"rays": int(len(sel))}
-    for name, levels, Tp in (("grid", w.grid.n_levels, s["T_grid"]), ("proposal", 1, s["T_prop"])):
+    for name, levels, Tp in (("grid", w.grid.n_levels, s["T_grid"]), ("proposal", 1, s["T_prop"]),
+                             ("combined", w.grid.n_levels, s["T_comb"])):
         tn, tf, hit = oracle.ray_clip(o, d, w.grid.aabb_min, w.grid.aabb_max, w.grid.res, levels, w.march.t_min,
                                       w.march.t_max)
         tau = P.exact_optical_depth(o, d, tn.astype(np.float64), np.where(hit, tf, tn).astype(np.float64),

@@ -97,6 +97,28 @@ int nacc_dense_weights(int64_t n_rays, int32_t n_bins, const float* edges, const
 int nacc_edges_to_packed(int64_t n_rays, int32_t n_bins, const float* edges, int64_t* offsets, float* t_starts,
                          float* t_ends, int64_t* n_samples, void* stream);
 
+/*
+ * Combined estimator (the occupancy grid stacked on the proposal network):
+ * the occupied range of each ray -- t0 of its first and t1 of its last
+ * occupied lattice point, i.e. of the samples nacc_march_grid would emit
+ * without a field (same FP32 lattice definition) -- into t_lo, t_hi
+ * [n_rays] ([device]).  A ray with no occupied point gets t_lo = t_hi =
+ * t_near, or max(t_min, 0) if it misses the grid.  params->early_stop_eps
+ * is ignored.  scratch: [device] >= nacc_occupied_range_scratch_bytes(),
+ * 256-byte aligned (the grid's block summaries).
+ */
+size_t nacc_occupied_range_scratch_bytes(void);
+int nacc_occupied_range(const nacc_grid* grid, const float* rays_o, const float* rays_d, int64_t n_rays,
+                        const nacc_march_params* params, float* t_lo, float* t_hi, void* scratch,
+                        size_t scratch_bytes, void* stream);
+
+/*
+ * n_bins equal bins of [t_lo[r], t_hi[r]] per ray, the arithmetic of
+ * nacc_uniform_edges -> edges [n_rays][n_bins+1].
+ */
+int nacc_range_edges(int64_t n_rays, const float* t_lo, const float* t_hi, int32_t n_bins, float* edges,
+                     void* stream);
+
 /* Diagnostics: the FP32 encoding e(x) of n points -> enc [n][64]. */
 int nacc_mlp_encode(int64_t n, const float* xyz, float* enc, void* stream);
 

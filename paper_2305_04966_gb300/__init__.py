@@ -8,7 +8,8 @@ F = 1 - T, Eq. 3).  The kernels live in ``libnacc.so`` behind the C ABI of
 ``include/nacc.h``; this package only marshals torch tensors.
 """
 from ._abi import NaccError, load as load_library
-from .api import (BlobField, MarchBuffers, OccupancyGrid, PackedSamples, ProposalMLP, ProposalSampler, RenderFn,
+from .api import (BlobField, CombinedSampler, MarchBuffers, OccupancyGrid, PackedSamples, ProposalMLP,
+                  ProposalSampler, RenderFn, occupied_range, range_edges,
                   UpdateBuffers, dense_weights, density_grid, edges_to_packed, field_eval, field_points,
                   grid_points, l2_loss, march_grid, mlp_encode, render, render_bwd, render_fwd, sample_pdf,
                   uniform_edges, update_grid)
@@ -18,4 +19,5 @@ __all__ = [
     "RenderFn", "UpdateBuffers", "density_grid", "field_eval", "field_points", "grid_points",
     "l2_loss", "march_grid", "render", "render_bwd", "render_fwd", "sample_pdf", "update_grid",
     "ProposalMLP", "ProposalSampler", "mlp_encode", "uniform_edges", "dense_weights", "edges_to_packed",
+    "CombinedSampler", "occupied_range", "range_edges",
 ]

@@ -76,6 +76,9 @@ SIGNATURES = {
     "nacc_uniform_edges": (c_i32, [P(Grid), c_vp, c_vp, c_i64, c_f32, c_f32, c_i32, c_vp, c_vp]),
     "nacc_dense_weights": (c_i32, [c_i64, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "nacc_edges_to_packed": (c_i32, [c_i64, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "nacc_occupied_range_scratch_bytes": (c_sz, []),
+    "nacc_occupied_range": (c_i32, [P(Grid), c_vp, c_vp, c_i64, P(MarchParams), c_vp, c_vp, c_vp, c_sz, c_vp]),
+    "nacc_range_edges": (c_i32, [c_i64, c_vp, c_vp, c_i32, c_vp, c_vp]),
 }
 
 MLP_PARAMS = 8385

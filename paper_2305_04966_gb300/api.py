@@ -548,12 +548,64 @@ class ProposalSampler:
     def sample(self, rays_o, rays_d, t_min: float = 0.0, t_max: float = 1e10, stratified: bool = False,
                seed: int = 0) -> PackedSamples:
         e = uniform_edges(self.grid, rays_o, rays_d, self.rounds[0], t_min, t_max, out=self.edges[0])
+        return self.resample(rays_o, rays_d, e, stratified, seed)
+
+    def resample(self, rays_o, rays_d, e: torch.Tensor, stratified: bool = False, seed: int = 0) -> PackedSamples:
+        """The proposal rounds from given initial bins e [n][rounds[0]+1]."""
         for i, nb in enumerate(self.rounds):
             s = self.mlp.forward_rays(rays_o, rays_d, e, out=self.sig[i])
             w = dense_weights(e, s, out=self.w[i])
             n_next = self.rounds[i + 1] if i + 1 < len(self.rounds) else self.n_final
             e = sample_pdf(e, w, n_next, stratified, seed + i, out=self.edges[i + 1])
         return edges_to_packed(e, out=self.packed)
+
+
+def occupied_range(grid: OccupancyGrid, rays_o, rays_d, step: float, max_steps: int = 1024, t_min: float = 0.0,
+                   t_max: float = 1e10, out=None, scratch=None):
+    """t0 of the first and t1 of the last occupied lattice point of each ray
+    (``nacc_occupied_range``): (t_lo [n], t_hi [n])."""
+    dev = rays_o.device
+    n = int(rays_o.shape[0])
+    _check(rays_o, "rays_o", _F32, dev, (n, 3))
+    _check(rays_d, "rays_d", _F32, dev, (n, 3))
+    lo, hi = out if out is not None else (torch.empty(n, dtype=_F32, device=dev), torch.empty(n, dtype=_F32, device=dev))
+    if scratch is None:
+        scratch = _scratch(_abi.load().nacc_occupied_range_scratch_bytes(), dev)
+    params = _abi.MarchParams(float(step), int(max_steps), float(t_min), float(t_max), 0.0)
+    _abi.call("nacc_occupied_range", ctypes.byref(grid.c_struct()), _ptr(rays_o), _ptr(rays_d), n,
+              ctypes.byref(params), _ptr(lo), _ptr(hi), _ptr(scratch), scratch.numel(), _stream(dev))
+    return lo, hi
+
+
+def range_edges(t_lo: torch.Tensor, t_hi: torch.Tensor, n_bins: int, out=None) -> torch.Tensor:
+    """n_bins equal bins of [t_lo, t_hi] per ray -> edges [n][n_bins+1]."""
+    dev = t_lo.device
+    n = int(t_lo.shape[0])
+    e = out if out is not None else torch.empty((n, n_bins + 1), dtype=_F32, device=dev)
+    _abi.call("nacc_range_edges", n, _ptr(t_lo), _ptr(t_hi), int(n_bins), _ptr(e), _stream(dev))
+    return e
+
+
+class CombinedSampler(ProposalSampler):
+    """Occupancy grid stacked on the proposal network: the grid gives each
+    ray's occupied range (first to last occupied lattice point), the proposal
+    rounds resample inside it."""
+
+    def __init__(self, mlp: ProposalMLP, grid: OccupancyGrid, n_rays: int, step: float, max_steps: int = 1024,
+                 rounds=(64, 32), n_final: int = 32, device="cuda"):
+        super().__init__(mlp, grid, n_rays, rounds, n_final, device)
+        self.step, self.max_steps = float(step), int(max_steps)
+        dev = torch.device(device)
+        self.lo = torch.empty(n_rays, dtype=_F32, device=dev)
+        self.hi = torch.empty(n_rays, dtype=_F32, device=dev)
+        self.scratch = _scratch(_abi.load().nacc_occupied_range_scratch_bytes(), dev)
+
+    def sample(self, rays_o, rays_d, t_min: float = 0.0, t_max: float = 1e10, stratified: bool = False,
+               seed: int = 0) -> PackedSamples:
+        occupied_range(self.grid, rays_o, rays_d, self.step, self.max_steps, t_min, t_max, out=(self.lo, self.hi),
+                       scratch=self.scratch)
+        e = range_edges(self.lo, self.hi, self.rounds[0], out=self.edges[0])
+        return self.resample(rays_o, rays_d, e, stratified, seed)
 
 
 def mlp_encode(xyz: torch.Tensor) -> torch.Tensor:

@@ -671,6 +671,68 @@ __global__ void __launch_bounds__(kBlockThreads)
     }
 }
 
+// The occupied range of each ray for the combined estimator: t0 of its first
+// and t1 of its last occupied lattice point (the march's emitted set
+// without a field: the same lattice definition).  Walks cell runs only (the
+// block summaries skip empty and fully occupied blocks) and never emits a
+// point: the last occupied point of a run is min(run end, K_end) - 1 with
+// K_end the first lattice index that is not visited (t0 >= t_far or
+// max_steps).  A ray with no occupied point gets t_lo = t_hi = t_near
+// (max(t_min, 0) if it misses).
+__global__ void __launch_bounds__(kBlockThreads) k_occupied_range(MarchArgs A, float* __restrict__ t_lo,
+                                                                  float* __restrict__ t_hi) {
+    const int64_t r = (int64_t)blockIdx.x * kBlockThreads + threadIdx.x;
+    if (r >= A.n) return;
+    Lane s;
+    const bool hit = lane_init(A, r, s);
+    int first = -1, last = -1;
+    if (hit) {
+        auto t0_of = [&](int k) { return __fadd_rn(s.R.tn, __fmul_rn((float)k, A.step)); };
+        // K_end = min(max_steps, first k with t0 >= t_far): estimate, then step (t0 is monotone in k)
+        const float q = (s.R.tf - s.R.tn) * A.inv_step;
+        int ke = q < (float)A.max_steps ? (int)fmaxf(floorf(q) - 2.0f, 0.0f) : A.max_steps;
+        for (int it = 0; it < 8 && ke > 0 && !(t0_of(ke - 1) < s.R.tf); ++it) --ke;
+        while (ke < A.max_steps && t0_of(ke) < s.R.tf) ++ke;
+        const int L = A.g.n_levels;
+        int k = 0;
+        while (k < ke) {
+            float t0, t1, x[3];
+            int l, ic[3];
+            const bool occ = lattice_point(A, s.R, k, t0, t1, x, l, ic);
+            int run_end = k + 1;
+            if (l < L) {
+                int lo[3] = {ic[0], ic[1], ic[2]}, hi[3] = {ic[0], ic[1], ic[2]};
+                if (A.blk) {
+                    const uint32_t b = ((uint32_t)l * A.nb + ic[0] / kBlk) * A.nb * A.nb +
+                                       (uint32_t)(ic[1] / kBlk) * A.nb + ic[2] / kBlk;
+                    const uint32_t* sum = occ ? A.blkf : A.blk;
+                    if (occ == (bool)((__ldg(&sum[b >> 5]) >> (b & 31)) & 1u)) {
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            lo[a] = ic[a] / kBlk * kBlk;
+                            hi[a] = min(lo[a] + kBlk, A.g.res) - 1;
+                        }
+                    }
+                }
+                run_end = skip_target(A, s.R, k, __fmul_rn(__fadd_rn(t0, t1), 0.5f), l, lo, hi, ke);
+            }
+            if (occ) {
+                if (first < 0) first = k;
+                last = min(run_end, ke) - 1;
+            }
+            k = run_end;
+        }
+    }
+    if (first < 0) {
+        const float t = hit ? s.R.tn : fmaxf(A.t_min, 0.0f);
+        t_lo[r] = t;
+        t_hi[r] = t;
+    } else {
+        t_lo[r] = __fadd_rn(s.R.tn, __fmul_rn((float)first, A.step));
+        t_hi[r] = __fadd_rn(__fadd_rn(s.R.tn, __fmul_rn((float)last, A.step)), A.step);
+    }
+}
+
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Caller-owned events recorded around the count kernel (diagnostics).
@@ -810,6 +872,64 @@ extern "C" int nacc_march_grid(const nacc_grid* grid, const float* rays_o, const
             return NACC_ERR_CAPACITY;
         }
     }
+    return NACC_OK;
+}
+
+extern "C" size_t nacc_occupied_range_scratch_bytes(void) { return 2 * kBlockBitsBytes; }
+
+extern "C" int nacc_occupied_range(const nacc_grid* grid, const float* rays_o, const float* rays_d, int64_t n_rays,
+                                   const nacc_march_params* params, float* t_lo, float* t_hi, void* scratch,
+                                   size_t scratch_bytes, void* stream) {
+    clear_error();
+    MarchArgs A;
+    if (!make_geom(grid, &A.g, true)) return NACC_ERR_INVALID_ARG;
+    NACC_CHECK_ARG(params != nullptr, "params is NULL");
+    NACC_CHECK_ARG(n_rays >= 0 && n_rays < (int64_t(1) << 40), "n_rays=%lld out of range", (long long)n_rays);
+    NACC_CHECK_ARG(params->step > 0.0f && std::isfinite(params->step), "step must be finite and > 0");
+    NACC_CHECK_ARG(params->max_steps >= 1 && params->max_steps <= (1 << 24), "max_steps=%d outside [1, 2^24]",
+                   params->max_steps);
+    NACC_CHECK_ARG(!std::isnan(params->t_min) && !std::isnan(params->t_max), "t_min/t_max is NaN");
+    if (n_rays == 0) return NACC_OK;
+    NACC_CHECK_ARG(rays_o && rays_d && t_lo && t_hi, "a pointer argument is NULL");
+    NACC_CHECK_ARG(scratch != nullptr && scratch_bytes >= 2 * kBlockBitsBytes, "scratch too small: %zu < %zu bytes",
+                   scratch_bytes, 2 * kBlockBitsBytes);
+    NACC_CHECK_ARG((reinterpret_cast<uintptr_t>(scratch) & 255) == 0, "scratch not 256-byte aligned");
+    A.o = rays_o;
+    A.d = rays_d;
+    A.n = n_rays;
+    A.step = params->step;
+    A.max_steps = params->max_steps;
+    A.t_min = params->t_min;
+    A.t_max = params->t_max;
+    A.thr = INFINITY;
+    A.inv_step = 1.0f / params->step;
+    A.idx32 = ((uint64_t)A.g.n_levels * A.g.res * A.g.res * A.g.res) <= 0xffffffffull ? 1 : 0;
+    A.field = nacc_blob_field{0, nullptr, nullptr, nullptr, nullptr};
+    A.nb = (A.g.res + kBlk - 1) / kBlk;
+    A.blk = static_cast<uint32_t*>(scratch);
+    A.blkf = reinterpret_cast<uint32_t*>(static_cast<char*>(scratch) + kBlockBitsBytes);
+    for (int l = 0; l < NACC_MAX_LEVELS; ++l) {
+        A.skip_lim[l] = -1.0f;
+        if (l >= A.g.n_levels) continue;
+        const Level& lv = A.g.lv[l];
+        double wmin = INFINITY, xmax = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            wmin = std::fmin(wmin, (double)lv.width[a]);
+            xmax = std::fmax(xmax, std::fmax(std::fabs((double)lv.lmin[a]), std::fabs((double)lv.lmax[a])));
+        }
+        const double lim = (wmin * kSkipMargin / (16.0 * 0x1p-24) - 15.0 * xmax) / 11.0;
+        if (lim > 0.0) A.skip_lim[l] = (float)lim;
+    }
+    const int64_t nb = (n_rays + kBlockThreads - 1) / kBlockThreads;
+    NACC_CHECK_ARG(nb < (int64_t(1) << 31), "too many rays for one launch");
+    {
+        const uint64_t nblocks = (uint64_t)A.g.n_levels * A.nb * A.nb * A.nb;
+        k_block_summary<<<(unsigned)((nblocks + 255) / 256), 256, 0, as_stream(stream)>>>(
+            A.g, A.nb, const_cast<uint32_t*>(A.blk), const_cast<uint32_t*>(A.blkf));
+        NACC_LAUNCH_CHECK();
+    }
+    k_occupied_range<<<(unsigned)nb, kBlockThreads, 0, as_stream(stream)>>>(A, t_lo, t_hi);
+    NACC_LAUNCH_CHECK();
     return NACC_OK;
 }
 

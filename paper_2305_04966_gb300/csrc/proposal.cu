@@ -49,6 +49,17 @@ __global__ void k_uniform_edges(GridGeom g, const float* __restrict__ o, const f
     }
 }
 
+__global__ void k_range_edges(const float* __restrict__ lo, const float* __restrict__ hi, int64_t n, int nb,
+                              float* __restrict__ edges) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        const float tn = lo[r], tf = hi[r];
+        const float span = __fsub_rn(tf, tn);
+        float* e = edges + r * (nb + 1);
+        for (int j = 0; j < nb; ++j) e[j] = __fadd_rn(tn, __fmul_rn(span, __fdiv_rn((float)j, (float)nb)));
+        e[nb] = tf;
+    }
+}
+
 // One warp per ray: tau_j = sigma_j (e_{j+1} - e_j), exclusive prefix P_j by
 // warp scans (carry across 32-bin chunks), w_j = exp(-P_j) (1 - exp(-tau_j)).
 __global__ void __launch_bounds__(256) k_dense_weights(int64_t n, int nb, const float* __restrict__ edges,
@@ -115,6 +126,19 @@ extern "C" int nacc_uniform_edges(const nacc_grid* grid, const float* rays_o, co
     NACC_CHECK_ARG(rays_o && rays_d && edges, "a pointer argument is NULL");
     const int blocks = (int)min64((n_rays + 255) / 256, (int64_t)sm_count() * 8);
     k_uniform_edges<<<blocks, 256, 0, as_stream(stream)>>>(g, rays_o, rays_d, n_rays, t_min, t_max, n_bins, edges);
+    NACC_LAUNCH_CHECK();
+    return NACC_OK;
+}
+
+extern "C" int nacc_range_edges(int64_t n_rays, const float* t_lo, const float* t_hi, int32_t n_bins, float* edges,
+                                void* stream) {
+    clear_error();
+    NACC_CHECK_ARG(n_rays >= 0 && n_rays < (int64_t(1) << 40), "n_rays=%lld out of range", (long long)n_rays);
+    NACC_CHECK_ARG(n_bins >= 1 && n_bins <= 4096, "n_bins=%d outside [1, 4096]", n_bins);
+    if (n_rays == 0) return NACC_OK;
+    NACC_CHECK_ARG(t_lo && t_hi && edges, "a pointer argument is NULL");
+    const int blocks = (int)min64((n_rays + 255) / 256, (int64_t)sm_count() * 8);
+    k_range_edges<<<blocks, 256, 0, as_stream(stream)>>>(t_lo, t_hi, n_rays, n_bins, edges);
     NACC_LAUNCH_CHECK();
     return NACC_OK;
 }

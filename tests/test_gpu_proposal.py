@@ -226,3 +226,85 @@ def test_sampler_matches_oracle_composition(nacc, P, orc):
     err = np.abs(got - exp) / span
     assert np.quantile(err, 0.99) < 2e-3 and err.mean() < 2e-4, (np.quantile(err, 0.99), err.mean(), err.max())
     np.testing.assert_array_equal(got[:, :64], exp[:, :64])  # misses: empty bins, identical
+
+
+# ---------------------------------------------------------------------------
+# combined estimator: occupancy grid + proposal network
+# ---------------------------------------------------------------------------
+
+def _grid(nacc, bits, res, L):
+    return nacc.OccupancyGrid((-1.5,) * 3, (1.5,) * 3, res, L, torch.as_tensor(bits.view(np.int32)).to(DEV))
+
+
+@pytest.mark.parametrize("case", ["c1", "cascade"])
+def test_occupied_range_bit_exact(nacc, orc, case):
+    o, d = _c1_rays_with_misses(3000)
+    if case == "c1":
+        w = workloads.c1_forward()
+        res, L = w.grid.res, w.grid.n_levels
+        bits, _ = orc.density_grid(w.grid, w.blobs)
+        step, tmin = w.march.step, 0.0
+    else:
+        res, L = 64, 4
+        bits = workloads.random_bitfield(L, res, 555, p_block=0.3, block=4, p_cell=0.6)
+        step, tmin = 3.0 * math.sqrt(3) / 512, 0.5
+        o = o * 2.0  # origins out to radius 8: through the outer levels
+        o[:64] *= 4.0  # the 64 rays pointing away start at radius 32: they miss the +-12 outer box
+    got_lo, got_hi = nacc.occupied_range(_grid(nacc, bits, res, L), torch.as_tensor(o, device=DEV),
+                                         torch.as_tensor(d, device=DEV), step, 1024, tmin, 1e10)
+    ex = orc.march(o, d, (-1.5,) * 3, (1.5,) * 3, res, L, bits, step, 1024, tmin, 1e10)
+    tn, tf, hit = orc.ray_clip(o, d, (-1.5,) * 3, (1.5,) * 3, res, L, tmin, 1e10)
+    off = ex["offsets"]
+    cnt = np.diff(off)
+    lo = np.where(hit, tn, np.float32(max(tmin, 0.0))).astype(np.float32)
+    hi = lo.copy()
+    has = cnt > 0
+    lo[has] = ex["t_starts"][off[:-1][has]]
+    hi[has] = ex["t_ends"][off[1:][has] - 1]
+    assert has.sum() > 500 and (~has).sum() > 50
+    np.testing.assert_array_equal(got_lo.cpu().numpy(), lo)
+    np.testing.assert_array_equal(got_hi.cpu().numpy(), hi)
+
+
+def test_range_edges_exact(nacc):
+    g = workloads.rng(102)
+    lo = g.uniform(0.0, 3.0, 1000).astype(np.float32)
+    hi = (lo + g.uniform(0.0, 2.0, 1000) * (g.random(1000) < 0.9)).astype(np.float32)
+    got = nacc.range_edges(torch.as_tensor(lo, device=DEV), torch.as_tensor(hi, device=DEV), 64).cpu().numpy()
+    span = (hi - lo).astype(np.float32)
+    frac = (np.arange(64, dtype=np.float32) / np.float32(64)).astype(np.float32)
+    exp = np.concatenate([(lo[:, None] + (span[:, None] * frac).astype(np.float32)).astype(np.float32), hi[:, None]], 1)
+    np.testing.assert_array_equal(got, exp)
+
+
+def test_combined_sampler_matches_oracle_composition(nacc, P, orc):
+    w = workloads.c1_forward(2048)
+    o, d = w.rays_o, w.rays_d
+    n = o.shape[0]
+    bits, _ = orc.density_grid(w.grid, w.blobs)
+    p = _params(P, 103)
+    p["b3"] = np.array([1.0], np.float32)
+    mlp = nacc.ProposalMLP(torch.as_tensor(_flat(p), device=DEV))
+    grid = _grid(nacc, bits, w.grid.res, w.grid.n_levels)
+    cs = nacc.CombinedSampler(mlp, grid, n, w.march.step, 1024, rounds=(64, 32), n_final=32, device=DEV)
+    pk = cs.sample(torch.as_tensor(o, device=DEV), torch.as_tensor(d, device=DEV))
+    got = np.stack([pk.t_starts.cpu().numpy().reshape(n, 32), pk.t_ends.cpu().numpy().reshape(n, 32)])
+    ex = orc.march(o, d, (-1.5,) * 3, (1.5,) * 3, w.grid.res, 1, bits, w.march.step, 1024, 0.0, 1e10)
+    tn, tf, hit = orc.ray_clip(o, d, (-1.5,) * 3, (1.5,) * 3, w.grid.res, 1, 0.0, 1e10)
+    off, cnt = ex["offsets"], np.diff(ex["offsets"])
+    lo = np.where(hit, tn, np.float32(0.0)).astype(np.float32)
+    hi = lo.copy()
+    lo[cnt > 0] = ex["t_starts"][off[:-1][cnt > 0]]
+    hi[cnt > 0] = ex["t_ends"][off[1:][cnt > 0] - 1]
+    span0 = (hi - lo).astype(np.float32)
+    frac = (np.arange(64, dtype=np.float32) / np.float32(64)).astype(np.float32)
+    e = np.concatenate([(lo[:, None] + (span0[:, None] * frac).astype(np.float32)).astype(np.float32), hi[:, None]], 1)
+    for nb, n_next in ((64, 32), (32, 32)):
+        s = P.forward(p, _midpoints(o, d, e))["sigma"]
+        off2 = np.arange(n + 1, dtype=np.int64) * nb
+        wts = orc.render_fwd(off2, e[:, :-1].reshape(-1), e[:, 1:].reshape(-1), s, np.zeros((n * nb, 3)))["weights"]
+        e = orc.sample_pdf(e, wts.reshape(n, nb).astype(np.float32), n_next)
+    exp = np.stack([e[:, :-1], e[:, 1:]])
+    span = np.maximum(e[:, -1] - e[:, 0], 1e-6)[None, :, None]
+    err = np.abs(got - exp) / span
+    assert np.quantile(err, 0.99) < 2e-3 and err.mean() < 2e-4, (np.quantile(err, 0.99), err.mean(), err.max())
