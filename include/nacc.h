@@ -164,6 +164,42 @@ int nacc_update_grid(const nacc_grid* grid, float* ema, const float* density, fl
                      size_t scratch_bytes, void* stream);
 
 /*
+ * Estimator update for dynamic scenes (Sec. 5 "Dynamic NeRFs": one grid
+ * shared by all frames marks the maximum occupancy over the timestamps): as
+ * nacc_update_grid with density[c] = max over f < n_frames of
+ * densities[f * n_cells + c].  n_frames = 1 is nacc_update_grid.
+ */
+int nacc_update_grid_frames(const nacc_grid* grid, float* ema, const float* densities, int32_t n_frames,
+                            float decay, float thresh_frac, float thresh_abs, uint32_t* bits_out, void* scratch,
+                            size_t scratch_bytes, void* stream);
+
+/*
+ * Estimator updated by gradient descent through the rendering loss (the
+ * Plenoxels variant of Sec. 3.1 "Spatial Skipping"): the grid holds a density
+ * per cell.  nacc_grid_density_lookup writes sigma_out[i] = density of the
+ * cell of sample i's midpoint -- tm = (t0 + t1) * 0.5, x = o + d * tm, the
+ * finest level whose box holds x, clamped cell, the FP32 definition of
+ * nacc_march_grid -- or 0 outside every level.  nacc_grid_density_backward
+ * adds g_sigma[i] into g_density[cell of i] (atomic FP32 adds: the order of
+ * the additions is not fixed).  The sample count is read on the device from
+ * *n_samples.  All arrays [device].
+ */
+int nacc_grid_density_lookup(const nacc_grid* grid, const float* density, const float* rays_o, const float* rays_d,
+                             const int32_t* ray_indices, const float* t_starts, const float* t_ends,
+                             const int64_t* n_samples, float* sigma_out, void* stream);
+int nacc_grid_density_backward(const nacc_grid* grid, const float* rays_o, const float* rays_d,
+                               const int32_t* ray_indices, const float* t_starts, const float* t_ends,
+                               const int64_t* n_samples, const float* g_sigma, float* g_density, void* stream);
+
+/*
+ * One gradient step of that grid: density[c] = max(density[c] - lr *
+ * g_density[c], 0) (FP32, rounded in this order), g_density[c] = 0, bit c of
+ * bits_out = (density[c] > thresh).
+ */
+int nacc_update_grid_sgd(const nacc_grid* grid, float* density, float* g_density, float lr, float thresh,
+                         uint32_t* bits_out, void* stream);
+
+/*
  * Allocation-free variant of nacc_update_grid (the paper has no counterpart;
  * this is a property of this library's interface).  Same arguments, same
  * arithmetic and same results as nacc_update_grid, but the temporary FP64

@@ -251,3 +251,4 @@ def density_grid(grid_spec, blobs, thresh=0.01, n_threads=None):
 
 
 from . import proposal  # noqa: E402  (density-proposal network oracle)
+from . import grid_variants  # noqa: E402  (estimator-update variants)

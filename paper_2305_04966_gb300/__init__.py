@@ -12,12 +12,14 @@ from .api import (BlobField, CombinedSampler, MarchBuffers, OccupancyGrid, Packe
                   ProposalSampler, RenderFn, occupied_range, range_edges,
                   UpdateBuffers, dense_weights, density_grid, edges_to_packed, field_eval, field_points,
                   grid_points, l2_loss, march_grid, mlp_encode, render, render_bwd, render_fwd, sample_pdf,
-                  uniform_edges, update_grid)
+                  uniform_edges, update_grid, update_grid_frames, grid_density_lookup, grid_density_backward,
+                  update_grid_sgd)
 
 __all__ = [
     "NaccError", "load_library", "BlobField", "MarchBuffers", "OccupancyGrid", "PackedSamples",
     "RenderFn", "UpdateBuffers", "density_grid", "field_eval", "field_points", "grid_points",
     "l2_loss", "march_grid", "render", "render_bwd", "render_fwd", "sample_pdf", "update_grid",
     "ProposalMLP", "ProposalSampler", "mlp_encode", "uniform_edges", "dense_weights", "edges_to_packed",
-    "CombinedSampler", "occupied_range", "range_edges",
+    "CombinedSampler", "occupied_range", "range_edges", "update_grid_frames", "grid_density_lookup",
+    "grid_density_backward", "update_grid_sgd",
 ]

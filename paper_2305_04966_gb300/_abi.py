@@ -55,6 +55,10 @@ SIGNATURES = {
     "nacc_update_grid_scratch_bytes": (c_sz, [c_i64]),
     "nacc_update_grid": (c_i32, [P(Grid), c_vp, c_vp, c_f32, c_f32, c_f32, c_vp, c_vp, c_sz, c_vp]),
     "nacc_update_grid_noalloc": (c_i32, [P(Grid), c_vp, c_vp, c_f32, c_f32, c_f32, c_vp, c_vp]),
+    "nacc_update_grid_frames": (c_i32, [P(Grid), c_vp, c_vp, c_i32, c_f32, c_f32, c_f32, c_vp, c_vp, c_sz, c_vp]),
+    "nacc_grid_density_lookup": (c_i32, [P(Grid), c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "nacc_grid_density_backward": (c_i32, [P(Grid), c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "nacc_update_grid_sgd": (c_i32, [P(Grid), c_vp, c_vp, c_f32, c_f32, c_vp, c_vp]),
     "nacc_sample_pdf": (c_i32, [c_i64, c_i32, c_vp, c_vp, c_i32, c_i32, c_u64, c_vp, c_vp]),
     "nacc_render_fwd": (c_i32, [c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, P(c_f32), c_f32, c_vp, c_vp,
                                 c_vp, c_vp, c_vp, c_vp]),

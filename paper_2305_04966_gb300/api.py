@@ -325,6 +325,48 @@ def update_grid(grid: OccupancyGrid, density: torch.Tensor, decay: float = 0.95,
     return grid
 
 
+def update_grid_frames(grid: OccupancyGrid, densities: torch.Tensor, decay: float = 0.95,
+                       thresh_frac: float = 0.01, thresh_abs: float = 0.0, buffers: UpdateBuffers | None = None):
+    """Dynamic scenes: the EMA update with the per-cell maximum over frames of
+    ``densities`` [n_frames][n_cells] (one grid for all timestamps)."""
+    dev = grid.bits.device
+    nf = int(densities.shape[0])
+    _check(densities, "densities", _F32, dev, (nf, grid.n_cells))
+    buf = buffers if buffers is not None else UpdateBuffers(grid.n_cells, dev)
+    _abi.call("nacc_update_grid_frames", ctypes.byref(grid.c_struct()), _ptr(grid.ema), _ptr(densities), nf,
+              float(decay), float(thresh_frac), float(thresh_abs), _ptr(grid.bits), _ptr(buf.scratch),
+              buf.scratch.numel(), _stream(dev))
+    return grid
+
+
+def grid_density_lookup(grid: OccupancyGrid, density: torch.Tensor, rays_o, rays_d, packed: PackedSamples,
+                        out=None) -> torch.Tensor:
+    """SGD-updated grid: density of each sample's cell -> [capacity]."""
+    dev = density.device
+    sig = out if out is not None else torch.empty(packed.capacity, dtype=_F32, device=dev)
+    _abi.call("nacc_grid_density_lookup", ctypes.byref(grid.c_struct()), _ptr(density), _ptr(rays_o),
+              _ptr(rays_d), _ptr(packed.ray_indices), _ptr(packed.t_starts), _ptr(packed.t_ends),
+              _ptr(packed.n_samples_dev), _ptr(sig), _stream(dev))
+    return sig
+
+
+def grid_density_backward(grid: OccupancyGrid, rays_o, rays_d, packed: PackedSamples, g_sigma: torch.Tensor,
+                          g_density: torch.Tensor) -> torch.Tensor:
+    """Adds each sample's dL/dsigma into its cell's entry of ``g_density``."""
+    _abi.call("nacc_grid_density_backward", ctypes.byref(grid.c_struct()), _ptr(rays_o), _ptr(rays_d),
+              _ptr(packed.ray_indices), _ptr(packed.t_starts), _ptr(packed.t_ends), _ptr(packed.n_samples_dev),
+              _ptr(g_sigma), _ptr(g_density), _stream(g_density.device))
+    return g_density
+
+
+def update_grid_sgd(grid: OccupancyGrid, density: torch.Tensor, g_density: torch.Tensor, lr: float,
+                    thresh: float = 0.01) -> OccupancyGrid:
+    """density = max(density - lr g, 0), g = 0, bits = density > thresh."""
+    _abi.call("nacc_update_grid_sgd", ctypes.byref(grid.c_struct()), _ptr(density), _ptr(g_density), float(lr),
+              float(thresh), _ptr(grid.bits), _stream(density.device))
+    return grid
+
+
 def sample_pdf(edges: torch.Tensor, weights: torch.Tensor, n_out: int, stratified: bool = False,
                seed: int = 0, out=None):
     """Inverse-CDF resampling: edges [n][nb+1], weights [n][nb] -> [n][n_out+1]."""

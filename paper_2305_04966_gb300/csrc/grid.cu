@@ -39,15 +39,17 @@ __global__ void __launch_bounds__(256)
 
 __global__ void __launch_bounds__(kEmaThreads)
     k_ema(float* __restrict__ ema, const float* __restrict__ dens, float decay, float omd,
-          int64_t n, double* __restrict__ partial) {
+          int64_t n, double* __restrict__ partial, int n_frames) {
     const int64_t base = (int64_t)blockIdx.x * kEmaCells;
     double acc = 0.0;
 #pragma unroll
     for (int j = 0; j < kEmaItems; ++j) {
         int64_t c = base + j * kEmaThreads + threadIdx.x;
         if (c < n) {
+            float dc = __ldcs(dens + c);
+            for (int f = 1; f < n_frames; ++f) dc = fmaxf(dc, __ldcs(dens + (int64_t)f * n + c));
             float a = __fmul_rn(decay, ema[c]);
-            float b = __fmul_rn(omd, __ldcs(dens + c));
+            float b = __fmul_rn(omd, dc);
             float e = __fadd_rn(a, b);
             ema[c] = e;
             acc += (double)e;
@@ -70,9 +72,12 @@ __global__ void __launch_bounds__(kEmaThreads)
 // multiple of 4): thread t of block b owns the float4 groups
 // b*kEmaCells/4 + j*kEmaThreads + t, j < kEmaItems/4 -- the same cells per
 // block, so the per-block partial sums cover the same cells.
+// n_frames > 1 (dynamic scenes): the density fed to the EMA is the maximum
+// over the frames dens[f * n + c] (the grid marks the maximum occupancy over
+// all timestamps).
 __global__ void __launch_bounds__(kEmaThreads)
     k_ema4(float* __restrict__ ema, const float* __restrict__ dens, float decay, float omd, int64_t n,
-           double* __restrict__ partial) {
+           double* __restrict__ partial, int n_frames) {
     const int64_t base = (int64_t)blockIdx.x * (kEmaCells / 4);
     const int64_t n4 = n / 4;
     float4* e4 = reinterpret_cast<float4*>(ema);
@@ -84,6 +89,13 @@ __global__ void __launch_bounds__(kEmaThreads)
         if (q < n4) {
             ev[j] = e4[q];
             dv[j] = __ldcs(d4 + q);
+            for (int f = 1; f < n_frames; ++f) {
+                const float4 u = __ldcs(d4 + (int64_t)f * n4 + q);
+                dv[j].x = fmaxf(dv[j].x, u.x);
+                dv[j].y = fmaxf(dv[j].y, u.y);
+                dv[j].z = fmaxf(dv[j].z, u.z);
+                dv[j].w = fmaxf(dv[j].w, u.w);
+            }
         }
     }
     // the thread's 8 cells summed in FP32 with Neumaier's compensation, then
@@ -193,14 +205,15 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 
 
 // EMA -> mean and threshold -> bits, on caller scratch or the library's own.
 int launch_update(float* ema, const float* density, float decay, int64_t n, double thresh_frac,
-                  double thresh_abs, uint32_t* bits_out, double* partial, double* mt, cudaStream_t st) {
+                  double thresh_abs, uint32_t* bits_out, double* partial, double* mt, cudaStream_t st,
+                  int n_frames = 1) {
     const int64_t nb = (n + kEmaCells - 1) / kEmaCells;
     volatile float omd = 1.0f - decay;
     const bool vec = aligned16(ema) && aligned16(density) && n % 4 == 0;
     if (vec)
-        k_ema4<<<(unsigned)nb, kEmaThreads, 0, st>>>(ema, density, decay, omd, n, partial);
+        k_ema4<<<(unsigned)nb, kEmaThreads, 0, st>>>(ema, density, decay, omd, n, partial, n_frames);
     else
-        k_ema<<<(unsigned)nb, kEmaThreads, 0, st>>>(ema, density, decay, omd, n, partial);
+        k_ema<<<(unsigned)nb, kEmaThreads, 0, st>>>(ema, density, decay, omd, n, partial, n_frames);
     NACC_LAUNCH_CHECK();
     k_mean_thr<<<1, 1024, 0, st>>>(partial, nb, n, thresh_frac, thresh_abs, mt);
     NACC_LAUNCH_CHECK();
@@ -214,6 +227,67 @@ int launch_update(float* ema, const float* density, float decay, int64_t n, doub
     }
     NACC_LAUNCH_CHECK();
     return NACC_OK;
+}
+
+// Cell of a packed sample's midpoint, the lattice march's FP32 definition:
+// tm = (t0 + t1) * 0.5, x = o + d * tm, level = finest level whose box holds
+// x, cell = clamp(floor((x - lmin) * scale)); flat index
+// l*res^3 + (x*res + y)*res + z, or -1 outside every level.
+__device__ __forceinline__ int64_t sample_cell(const GridGeom& g, const float* __restrict__ o,
+                                               const float* __restrict__ d, int64_t r, float t0, float t1) {
+    const float tm = __fmul_rn(__fadd_rn(t0, t1), 0.5f);
+    float x[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) x[a] = __fadd_rn(o[3 * r + a], __fmul_rn(d[3 * r + a], tm));
+    int l = 0;
+    for (; l < g.n_levels; ++l) {
+        const Level& lv = g.lv[l];
+        if (x[0] >= lv.lmin[0] && x[0] <= lv.lmax[0] && x[1] >= lv.lmin[1] && x[1] <= lv.lmax[1] &&
+            x[2] >= lv.lmin[2] && x[2] <= lv.lmax[2])
+            break;
+    }
+    if (l == g.n_levels) return -1;
+    const Level& lv = g.lv[l];
+    int64_t ic[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int c = (int)floorf(__fmul_rn(__fsub_rn(x[a], lv.lmin[a]), lv.scale[a]));
+        ic[a] = c < 0 ? 0 : (c > g.res - 1 ? g.res - 1 : c);
+    }
+    const int64_t res = g.res;
+    return (int64_t)l * res * res * res + (ic[0] * res + ic[1]) * res + ic[2];
+}
+
+// SGD-updated grid (the estimator's density updated by gradient descent
+// through the rendering loss): density of each sample's cell, and the
+// adjoint: the sample's dL/dsigma added into its cell.
+template <bool kBackward>
+__global__ void __launch_bounds__(256)
+    k_grid_samples(GridGeom g, const float* __restrict__ o, const float* __restrict__ d,
+                   const int32_t* __restrict__ ri, const float* __restrict__ t0, const float* __restrict__ t1,
+                   const int64_t* __restrict__ n_samples, const float* __restrict__ dens_or_gsig,
+                   float* __restrict__ out) {
+    const int64_t S = *n_samples;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < S; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = sample_cell(g, o, d, ri[i], t0[i], t1[i]);
+        if (kBackward) {
+            if (c >= 0) atomicAdd(out + c, dens_or_gsig[i]);
+        } else {
+            out[i] = c >= 0 ? dens_or_gsig[c] : 0.0f;
+        }
+    }
+}
+
+// density = max(density - lr * grad, 0), grad = 0, bits = density > thresh.
+__global__ void __launch_bounds__(256) k_grid_sgd(float* __restrict__ dens, float* __restrict__ grad, int64_t n,
+                                                  float lr, float thresh, uint32_t* __restrict__ bits) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+        const float v = fmaxf(__fsub_rn(dens[c], __fmul_rn(lr, grad[c])), 0.0f);
+        dens[c] = v;
+        grad[c] = 0.0f;
+        const unsigned m = __ballot_sync(0xffffffffu, v > thresh);
+        if ((threadIdx.x & 31) == 0) bits[c >> 5] = m;
+    }
 }
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -346,4 +420,82 @@ extern "C" int nacc_update_grid_noalloc(const nacc_grid* grid, float* ema, const
     double* mt = scratch + kNoAllocMaxBlocks;
     return launch_update(ema, density, decay, n, (double)thresh_frac, (double)thresh_abs, bits_out, partial, mt,
                          as_stream(stream));
+}
+
+extern "C" int nacc_update_grid_frames(const nacc_grid* grid, float* ema, const float* densities, int32_t n_frames,
+                                       float decay, float thresh_frac, float thresh_abs, uint32_t* bits_out,
+                                       void* scratch, size_t scratch_bytes, void* stream) {
+    clear_error();
+    GridGeom g;
+    if (!make_geom(grid, &g, false)) return NACC_ERR_INVALID_ARG;
+    NACC_CHECK_ARG(ema && densities && bits_out, "ema / densities / bits_out is NULL");
+    NACC_CHECK_ARG(n_frames >= 1 && n_frames <= 4096, "n_frames=%d outside [1, 4096]", n_frames);
+    NACC_CHECK_ARG(decay >= 0.0f && decay <= 1.0f, "decay=%g outside [0, 1]", (double)decay);
+    NACC_CHECK_ARG(std::isfinite(thresh_frac) && std::isfinite(thresh_abs), "thresholds must be finite");
+    const int64_t n = (int64_t)g.n_levels * g.res * g.res * g.res;
+    const size_t need = nacc_update_grid_scratch_bytes(n);
+    NACC_CHECK_ARG(scratch != nullptr && scratch_bytes >= need, "scratch too small: %zu < %zu bytes", scratch_bytes,
+                   need);
+    NACC_CHECK_ARG((reinterpret_cast<uintptr_t>(scratch) & 255) == 0, "scratch not 256-byte aligned");
+    const int64_t nb = (n + kEmaCells - 1) / kEmaCells;
+    double* partial = static_cast<double*>(scratch);
+    double* mt = reinterpret_cast<double*>(static_cast<char*>(scratch) + align256(sizeof(double) * (size_t)nb));
+    return launch_update(ema, densities, decay, n, (double)thresh_frac, (double)thresh_abs, bits_out, partial, mt,
+                         as_stream(stream), n_frames);
+}
+
+namespace nacc {
+namespace {
+int grid_samples_args(const nacc_grid* grid, GridGeom* g, const float* rays_o, const float* rays_d,
+                      const int32_t* ray_indices, const float* t_starts, const float* t_ends,
+                      const int64_t* n_samples) {
+    if (!make_geom(grid, g, false)) return NACC_ERR_INVALID_ARG;
+    NACC_CHECK_ARG(rays_o && rays_d && ray_indices && t_starts && t_ends && n_samples, "a pointer argument is NULL");
+    return NACC_OK;
+}
+}  // namespace
+}  // namespace nacc
+
+extern "C" int nacc_grid_density_lookup(const nacc_grid* grid, const float* density, const float* rays_o,
+                                        const float* rays_d, const int32_t* ray_indices, const float* t_starts,
+                                        const float* t_ends, const int64_t* n_samples, float* sigma_out,
+                                        void* stream) {
+    clear_error();
+    GridGeom g;
+    int rc = grid_samples_args(grid, &g, rays_o, rays_d, ray_indices, t_starts, t_ends, n_samples);
+    if (rc != NACC_OK) return rc;
+    NACC_CHECK_ARG(density && sigma_out, "density / sigma_out is NULL");
+    k_grid_samples<false><<<sm_count() * 8, 256, 0, as_stream(stream)>>>(g, rays_o, rays_d, ray_indices, t_starts,
+                                                                        t_ends, n_samples, density, sigma_out);
+    NACC_LAUNCH_CHECK();
+    return NACC_OK;
+}
+
+extern "C" int nacc_grid_density_backward(const nacc_grid* grid, const float* rays_o, const float* rays_d,
+                                          const int32_t* ray_indices, const float* t_starts, const float* t_ends,
+                                          const int64_t* n_samples, const float* g_sigma, float* g_density,
+                                          void* stream) {
+    clear_error();
+    GridGeom g;
+    int rc = grid_samples_args(grid, &g, rays_o, rays_d, ray_indices, t_starts, t_ends, n_samples);
+    if (rc != NACC_OK) return rc;
+    NACC_CHECK_ARG(g_sigma && g_density, "g_sigma / g_density is NULL");
+    k_grid_samples<true><<<sm_count() * 8, 256, 0, as_stream(stream)>>>(g, rays_o, rays_d, ray_indices, t_starts,
+                                                                       t_ends, n_samples, g_sigma, g_density);
+    NACC_LAUNCH_CHECK();
+    return NACC_OK;
+}
+
+extern "C" int nacc_update_grid_sgd(const nacc_grid* grid, float* density, float* g_density, float lr, float thresh,
+                                    uint32_t* bits_out, void* stream) {
+    clear_error();
+    GridGeom g;
+    if (!make_geom(grid, &g, false)) return NACC_ERR_INVALID_ARG;
+    NACC_CHECK_ARG(density && g_density && bits_out, "density / g_density / bits_out is NULL");
+    NACC_CHECK_ARG(std::isfinite(lr) && std::isfinite(thresh), "lr / thresh must be finite");
+    const int64_t n = (int64_t)g.n_levels * g.res * g.res * g.res;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 16);
+    k_grid_sgd<<<blocks, 256, 0, as_stream(stream)>>>(density, g_density, n, lr, thresh, bits_out);
+    NACC_LAUNCH_CHECK();
+    return NACC_OK;
 }

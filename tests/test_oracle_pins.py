@@ -614,3 +614,53 @@ def test_exact_optical_depth_matches_fine_quadrature(orc):
         out = orc.render_fwd(np.array([0, N]), t0, t1, sig, rgb)
         assert -math.log(out["trans"][0]) == pytest.approx(exact[r], rel=2e-4, abs=1e-6)
     assert hit.sum() >= 3
+
+
+# ---------------------------------------------------------------------------
+# estimator-update variants (oracle/grid_variants.py)
+# ---------------------------------------------------------------------------
+
+def test_sample_cells_of_cell_centres_and_of_march_samples(orc):
+    """A sample whose ray does not move (d = 0) sits at o: at a cell centre
+    its cell is that cell.  Every sample the oracle march emits lies in an
+    occupied cell (the lattice definition both share)."""
+    from oracle import grid_variants as G
+    res, L = 16, 3
+    geom = orc.level_geometry((-1.5,) * 3, (1.5,) * 3, res, L)
+    centres = orc.grid_points((-1.5,) * 3, (1.5,) * 3, res, L, jitter=False)
+    n = centres.shape[0]
+    cells = G.sample_cells(centres, np.zeros((n, 3), np.float32), np.arange(n), np.zeros(n, np.float32),
+                           np.ones(n, np.float32), geom, res)
+    # a centre belongs to the finest level whose box (half-width 1.5 * 2^l) holds it:
+    # its own cell when that is its own level, else a cell of that finer level
+    lvl = np.arange(n) // res ** 3
+    finest = np.argmax(np.abs(centres).max(1)[:, None] <= 1.5 * 2.0 ** np.arange(L)[None, :], axis=1)
+    own = cells == np.arange(n)
+    assert own[finest == lvl].all()
+    assert np.array_equal(cells[finest < lvl] // res ** 3, finest[finest < lvl]) and (finest < lvl).sum() > 100
+    bits = workloads.random_bitfield(L, res, 31, p_block=0.5, block=4, p_cell=0.5)
+    w = workloads.c1_forward(500)
+    ex = orc.march(w.rays_o, w.rays_d, (-1.5,) * 3, (1.5,) * 3, res, L, bits, 0.02, 1024, 0.0, 1e10)
+    c = G.sample_cells(w.rays_o, w.rays_d, ex["ray_indices"], ex["t_starts"], ex["t_ends"], geom, res)
+    occ = workloads.unpack_bits(bits)
+    assert len(c) > 1000 and (c >= 0).all() and occ[c].all()
+
+
+def test_density_scatter_is_the_adjoint_of_lookup():
+    """<lookup(density), g> = <density, backward(g)> for any density and g."""
+    from oracle import grid_variants as G
+    g0 = np.random.default_rng(5)
+    cells = g0.integers(-1, 50, 400)
+    dens = g0.standard_normal(50)
+    gs = g0.standard_normal(400)
+    lhs = float(G.density_lookup(dens, cells).astype(np.float64) @ gs)
+    rhs = float(dens.astype(np.float32).astype(np.float64) @ G.density_backward(gs, cells, 50))
+    assert lhs == pytest.approx(rhs, rel=1e-12)
+
+
+def test_sgd_step_and_frames_max_hand_examples():
+    from oracle import grid_variants as G
+    d, b = G.sgd_step(np.array([1.0, 0.5, 0.02, 3.0], np.float32), np.array([0.5, 2.0, -0.25, 0.0]), 0.5, 0.1)
+    np.testing.assert_array_equal(d, np.array([0.75, 0.0, 0.145, 3.0], np.float32))
+    np.testing.assert_array_equal(b, [True, False, True, True])
+    np.testing.assert_array_equal(G.frames_max([[1.0, 5.0, 0.0], [2.0, -1.0, 0.0], [0.5, 4.0, 3.0]]), [2.0, 5.0, 3.0])
