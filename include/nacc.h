@@ -131,6 +131,31 @@ int nacc_march_grid(const nacc_grid* grid, const float* rays_o, const float* ray
                     const nacc_blob_field* field, nacc_packed* out, void* scratch,
                     size_t scratch_bytes, void* stream);
 
+/* Scratch bytes nacc_march_unbounded needs for n_rays rays. */
+size_t nacc_march_unbounded_scratch_bytes(int64_t n_rays);
+
+/*
+ * Lattice marching for unbounded scenes (Sec. 3.2 "Handling Unbounded
+ * Scenes": sampling in s-space through a bijection Phi: s -> t).  Per ray,
+ * for k = 0..K-1 (K = params->max_steps), FP32 with every operation rounded:
+ *   s0 = k / K, s1 = (k+1) / K,  t = 1 / (a * (1 - s) + b * s),
+ *   a = 1 / t_near, b = 1 / t_far  (t_near = params->t_min > 0, t_far =
+ *   params->t_max finite: the disparity-linear Phi),
+ *   tm = (t0 + t1) * 0.5, x = o + d * tm, c = contract(x):
+ *   m = max|x_a|; c = x if m <= 1 else x * ((2 - 1/m) * (1/m)),
+ * and [t0, t1] is emitted iff the cell of c (finest level whose box holds c,
+ * clamped cell, as in nacc_march_grid) is occupied.  The grid covers the
+ * contracted cube (e.g. 4 levels around [-0.25, 0.25]^3 reach [-2, 2]^3).
+ * There is no ray-box clip.  Early termination as in nacc_march_grid, with
+ * the field at x; the early-stop density keeps the blobs whose integral
+ * along the ray line exceeds 1e-7 (peak >= 0 expected).  Every lattice point
+ * is tested (no skipping).  Outputs, scratch and capacity as
+ * nacc_march_grid (scratch >= nacc_march_unbounded_scratch_bytes(n_rays)).
+ */
+int nacc_march_unbounded(const nacc_grid* grid, const float* rays_o, const float* rays_d, int64_t n_rays,
+                         const nacc_march_params* params, const nacc_blob_field* field, nacc_packed* out,
+                         void* scratch, size_t scratch_bytes, void* stream);
+
 /*
  * Sample points for the estimator update (Eq. 4; Sec. 3.1 "Spatial
  * Skipping": the cached density is refreshed every few steps at points of

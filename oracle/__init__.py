@@ -81,6 +81,13 @@ def lib():
         L.orc_update_grid.argtypes = [i64, vp, vp, f32, f32, f32, vp, vp]
         L.orc_sample_pdf.restype = None
         L.orc_sample_pdf.argtypes = [i64, i32, vp, vp, i32, i32, u64, vp, i32]
+        L.orc_march_unbounded.restype = i32
+        L.orc_march_unbounded.argtypes = [i64, vp, vp, vp, vp, i32, i32, vp, i32, f32, f32, i32, vp, vp, vp, f32,
+                                          vp, vp, vp, vp, vp, i32]
+        L.orc_s_to_t.restype = f32
+        L.orc_s_to_t.argtypes = [f32, f32, f32]
+        L.orc_contract_points.restype = None
+        L.orc_contract_points.argtypes = [i64, vp, vp]
         L.orc_max_threads.restype = i32
         L.orc_max_threads.argtypes = []
         _lib = L
@@ -153,6 +160,73 @@ def march(rays_o, rays_d, aabb_min, aabb_max, res, n_levels, bits, step, max_ste
     L.orc_march(*args, _ptr(counts2), _ptr(offsets), _ptr(ri), _ptr(t0), _ptr(t1), nt)
     assert np.array_equal(counts, counts2)
     return dict(offsets=offsets, ray_indices=ri, t_starts=t0, t_ends=t1)
+
+
+def s_to_t(s, t_near, t_far):
+    """Disparity-linear s -> t (FP32 definition of the unbounded lattice)."""
+    L = lib()
+    return np.array([L.orc_s_to_t(float(v), float(t_near), float(t_far)) for v in np.ravel(s)], np.float32)
+
+
+def contract(xyz):
+    """L-infinity contraction of points [n][3] into [-2, 2]^3 (FP32 definition)."""
+    x = _c(xyz, np.float32).reshape(-1, 3)
+    out = np.zeros_like(x)
+    lib().orc_contract_points(x.shape[0], _ptr(x), _ptr(out))
+    return out
+
+
+def march_unbounded(rays_o, rays_d, aabb_min, aabb_max, res, n_levels, bits, K, t_near, t_far, blobs=None,
+                    eps=1e-4, n_threads=None):
+    """Unbounded-scene march: K uniform steps in s mapped to t by the
+    disparity-linear bijection, occupancy of the contracted midpoint.  Same
+    return value as :func:`march`."""
+    o, d = _c(rays_o, np.float32), _c(rays_d, np.float32)
+    n = o.shape[0]
+    bits = _c(bits, np.uint32)
+    amin, amax = _c(aabb_min, np.float32), _c(aabb_max, np.float32)
+    if blobs is not None:
+        nb, mu, sd, pk = blobs.n, _c(blobs.mu, np.float32), _c(blobs.std, np.float32), _c(blobs.peak, np.float32)
+    else:
+        nb, mu, sd, pk = 0, None, None, None
+    counts = np.zeros(n, np.int64)
+    nt = _threads(n_threads)
+    L = lib()
+    args = (n, _ptr(o), _ptr(d), _ptr(amin), _ptr(amax), res, n_levels, _ptr(bits), K, t_near, t_far, nb, _ptr(mu),
+            _ptr(sd), _ptr(pk), eps)
+    if L.orc_march_unbounded(*args, _ptr(counts), None, None, None, None, nt) != 0:
+        raise ValueError("orc_march_unbounded: invalid arguments")
+    offsets = np.zeros(n + 1, np.int64)
+    np.cumsum(counts, out=offsets[1:])
+    S = int(offsets[-1])
+    ri, t0, t1 = np.zeros(S, np.int32), np.zeros(S, np.float32), np.zeros(S, np.float32)
+    counts2 = np.zeros(n, np.int64)
+    L.orc_march_unbounded(*args, _ptr(counts2), _ptr(offsets), _ptr(ri), _ptr(t0), _ptr(t1), nt)
+    assert np.array_equal(counts, counts2)
+    return dict(offsets=offsets, ray_indices=ri, t_starts=t0, t_ends=t1)
+
+
+def uncontract(c):
+    """Inverse of :func:`contract` in FP64: y with m' = max|y_a| > 1 maps back to
+    y * (m / m') with m = 1 / (2 - m') (m' < 2)."""
+    y = np.asarray(c, np.float64).reshape(-1, 3)
+    mp = np.abs(y).max(1)
+    out = y.copy()
+    far = mp > 1.0
+    m = 1.0 / np.maximum(2.0 - mp[far], 1e-300)
+    out[far] = y[far] * (m / mp[far])[:, None]
+    return out
+
+
+def density_grid_contracted(grid_spec, blobs, thresh=0.01, n_threads=None):
+    """Occupancy bits of a grid over the contracted space: cell centres (in
+    contracted coordinates) mapped back to the scene, FP64 field > thresh."""
+    pts = grid_points(grid_spec.aabb_min, grid_spec.aabb_max, grid_spec.res, grid_spec.n_levels, jitter=False,
+                      n_threads=n_threads)
+    sig = field_points(uncontract(pts).astype(np.float32), blobs, n_threads)
+    occ = sig > thresh
+    w = occ.reshape(-1, 32).astype(np.uint64) * (np.uint64(1) << np.arange(32, dtype=np.uint64))
+    return w.sum(1).astype(np.uint32), sig
 
 
 def field_samples(rays_o, rays_d, ray_indices, t_starts, t_ends, blobs, n_threads=None):

@@ -251,6 +251,105 @@ static int64_t orc_march_ray(const float o[3], const float d[3], const orc_level
     return n;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Unbounded scenes: sampling in s-space and a contracted grid               */
+/* ------------------------------------------------------------------------ */
+
+/* Disparity-linear bijection s in [0, 1] -> t in [t_near, t_far]:
+ * 1/t = (1 - s)/t_near + s/t_far, as FP32 operations in this order:
+ * a = 1/t_near, b = 1/t_far, t = 1 / (a * (1 - s) + b * s)
+ * (both ends exact up to the reciprocal's rounding, no cancellation). */
+float orc_s_to_t(float s, float t_near, float t_far)
+{
+    float a = 1.0f / t_near;
+    float b = 1.0f / t_far;
+    float den = a * (1.0f - s) + b * s;
+    return 1.0f / den;
+}
+
+/* L-infinity contraction: c(x) = x if max|x_a| <= 1, else
+ * (2 - 1/m) x / m with m = max|x_a|, as inv = 1/m, f = 2 - inv, g = f * inv,
+ * c_a = x_a * g (FP32, each rounded). */
+void orc_contract(const float x[3], float c[3])
+{
+    float ax = fabsf(x[0]), ay = fabsf(x[1]), az = fabsf(x[2]);
+    float m = ax > ay ? ax : ay;
+    m = m > az ? m : az;
+    if (m <= 1.0f) {
+        c[0] = x[0];
+        c[1] = x[1];
+        c[2] = x[2];
+        return;
+    }
+    float inv = 1.0f / m;
+    float f = 2.0f - inv;
+    float g = f * inv;
+    for (int a = 0; a < 3; ++a) c[a] = x[a] * g;
+}
+
+void orc_contract_points(int64_t n, const float* xyz, float* out)
+{
+    for (int64_t i = 0; i < n; ++i) orc_contract(&xyz[3 * i], &out[3 * i]);
+}
+
+/* One ray of the unbounded march: for k = 0..K-1, s0 = k / K, s1 = (k+1) / K
+ * (FP32 divisions), t0 = Phi(s0), t1 = Phi(s1), tm = (t0 + t1) * 0.5,
+ * x = o + d * tm; the sample is emitted iff the cell of c(x) is occupied,
+ * with the same early-stop rule as the bounded march (sigma at x). */
+static int64_t orc_march_unb_ray(const float o[3], const float d[3], const orc_level* lv, int L, int res,
+                                 const uint32_t* bits, int K, float t_near, float t_far,
+                                 const orc_march_field* fld, int64_t base, int32_t ray, int32_t* ray_idx,
+                                 float* t0s, float* t1s)
+{
+    float tau = 0.0f;
+    int64_t n = 0;
+    for (int k = 0; k < K; ++k) {
+        float s0 = (float)k / (float)K, s1 = (float)(k + 1) / (float)K;
+        float t0 = orc_s_to_t(s0, t_near, t_far), t1 = orc_s_to_t(s1, t_near, t_far);
+        float tm = (t0 + t1) * 0.5f;
+        float x[3], c[3];
+        for (int a = 0; a < 3; ++a) x[a] = o[a] + d[a] * tm;
+        orc_contract(x, c);
+        if (!orc_occupied(c, lv, L, res, bits)) continue;
+        if (fld && tau > fld->thr) break;
+        if (t0s) {
+            ray_idx[base + n] = ray;
+            t0s[base + n] = t0;
+            t1s[base + n] = t1;
+        }
+        ++n;
+        if (fld) {
+            float sg = orc_sigma_f32(x, fld->n_blobs, fld->mu, fld->stdv, fld->peak);
+            float dt = t1 - t0;
+            tau = tau + sg * dt;
+        }
+    }
+    return n;
+}
+
+int orc_march_unbounded(int64_t n_rays, const float* rays_o, const float* rays_d, const float* aabb_min,
+                        const float* aabb_max, int res, int n_levels, const uint32_t* bits, int K, float t_near,
+                        float t_far, int n_blobs, const float* mu, const float* stdv, const float* peak, float eps,
+                        int64_t* counts, const int64_t* offsets, int32_t* ray_idx, float* t0s, float* t1s,
+                        int n_threads)
+{
+    if (n_levels < 1 || n_levels > ORC_MAX_LEVELS || res < 1 || K < 1 || !(t_near > 0.0f) || !(t_far > t_near) ||
+        !isfinite(t_far))
+        return -1;
+    orc_level lv[ORC_MAX_LEVELS];
+    orc_levels(aabb_min, aabb_max, res, n_levels, lv);
+    orc_march_field fld = {n_blobs, mu, stdv, peak, orc_tau_threshold(eps)};
+    const orc_march_field* f = n_blobs > 0 ? &fld : NULL;
+#pragma omp parallel for schedule(dynamic, 64) num_threads(n_threads)
+    for (int64_t r = 0; r < n_rays; ++r) {
+        int64_t base = offsets ? offsets[r] : 0;
+        counts[r] = orc_march_unb_ray(&rays_o[3 * r], &rays_d[3 * r], lv, n_levels, res, bits, K, t_near, t_far, f,
+                                      base, (int32_t)r, offsets ? ray_idx : NULL, offsets ? t0s : NULL,
+                                      offsets ? t1s : NULL);
+    }
+    return 0;
+}
+
 /* counts[r] = number of samples of ray r.  If `offsets` is non-NULL also write
  * the samples of ray r at [offsets[r], offsets[r]+counts[r]).  n_blobs == 0:
  * no field, no early stop.  Returns 0, or -1 on invalid arguments. */

@@ -219,6 +219,41 @@ def march_grid(grid: OccupancyGrid, rays_o: torch.Tensor, rays_d: torch.Tensor, 
 # rendering (Algorithm 1 "rendering"; Eq. 2)
 # ---------------------------------------------------------------------------
 
+def march_unbounded(grid: OccupancyGrid, rays_o: torch.Tensor, rays_d: torch.Tensor, max_steps: int = 1024,
+                    t_near: float = 0.2, t_far: float = 1000.0, early_stop_eps: float = 1e-4,
+                    field: BlobField | None = None, capacity: int | None = None,
+                    buffers: MarchBuffers | None = None, with_ray_indices: bool = True) -> PackedSamples:
+    """Unbounded-scene march (``nacc_march_unbounded``): max_steps uniform
+    steps in s mapped to [t_near, t_far] by the disparity-linear bijection,
+    occupancy of the contracted midpoint."""
+    dev = rays_o.device
+    n = int(rays_o.shape[0])
+    _check(rays_o, "rays_o", _F32, dev, (n, 3))
+    _check(rays_d, "rays_d", _F32, dev, (n, 3))
+    _check(grid.bits, "grid.bits", _I32, dev, (grid.n_cells // 32,))
+    params = _abi.MarchParams(0.0, int(max_steps), float(t_near), float(t_far), float(early_stop_eps))
+    fs = field.c_struct() if field is not None else None
+    worst = n * int(max_steps)
+    scratch = _scratch(_abi.load().nacc_march_unbounded_scratch_bytes(n), dev)
+    while True:
+        if buffers is None:
+            cap = capacity if capacity is not None else (worst if worst * 12 <= (1 << 31) else max(n * 64, 1 << 20))
+            buf = MarchBuffers(n, cap, dev, with_ray_indices)
+        else:
+            buf = buffers
+        pk = buf.packed
+        out = _abi.Packed(_ptr(pk.offsets), _ptr(pk.ray_indices), _ptr(pk.t_starts), _ptr(pk.t_ends),
+                          pk.capacity, _ptr(pk.n_samples_dev))
+        rc = _abi.call("nacc_march_unbounded", ctypes.byref(grid.c_struct()), _ptr(rays_o), _ptr(rays_d), n,
+                       ctypes.byref(params), ctypes.byref(fs) if fs is not None else None, ctypes.byref(out),
+                       _ptr(scratch), scratch.numel(), _stream(dev))
+        if rc == _abi.NACC_OK:
+            return pk
+        if buffers is not None or capacity is not None:
+            raise _abi.NaccError("nacc_march_unbounded", rc, "capacity too small")
+        capacity = int(pk.n_samples_dev.item())
+
+
 def _bg(bg):
     return (ctypes.c_float * 3)(*[float(v) for v in bg])
 

@@ -1,0 +1,343 @@
+// march_unbounded.cu -- lattice marching for unbounded scenes
+// (nacc_march_unbounded): sampling in s-space and an occupancy grid over the
+// contracted space.
+//
+// Sec. 3.2 "Handling Unbounded Scenes": a bijection Phi: s in [0, 1] ->
+// t in [t_near, t_far] makes the samples coarser with distance; the lattice
+// is uniform in s.  Phi is disparity-linear: 1/t = (1 - s)/t_near + s/t_far.
+// The grid is looked up at c(x), the L-infinity contraction of the sample's
+// midpoint into [-2, 2]^3.  Every lattice point is tested (the contraction
+// mixes the axes, so the per-axis monotonicity behind the bounded march's
+// cell runs does not hold); the early stop is the bounded march's rule with
+// the field at the uncontracted point.
+//
+// The early-stop density of a ray keeps only the blobs whose integral along
+// the whole ray line is above 1e-7 (a bound on everything dropped: at most
+// 1e-7 per blob of optical depth), in a per-lane table of the closed form
+// peak_b 2^(A_b (t - t*_b)^2 + C_b); a ray with more than kTable such blobs
+// sums every blob directly.
+#include "nacc_internal.cuh"
+
+namespace nacc {
+namespace {
+
+constexpr int kThreads = 32;  // one warp per block
+constexpr int kTable = 48;
+constexpr float kCullEps = 1e-7f;
+
+struct UArgs {
+    GridGeom g;
+    const float* o;
+    const float* d;
+    int64_t n;
+    int K;
+    float inv_tn, inv_tf;  // 1/t_near, 1/t_far
+    float thr;
+    nacc_blob_field field;
+};
+
+__device__ __forceinline__ float ex2_approx(float a) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(a));
+    return y;
+}
+
+// t = 1 / (a (1 - s) + b s) with a = 1/t_near, b = 1/t_far, each operation rounded.
+__device__ __forceinline__ float s_to_t(const UArgs& A, float s) {
+    return __fdiv_rn(1.0f, __fadd_rn(__fmul_rn(A.inv_tn, __fsub_rn(1.0f, s)), __fmul_rn(A.inv_tf, s)));
+}
+
+__device__ __forceinline__ void lattice(const UArgs& A, int k, float& t0, float& t1) {
+    t0 = s_to_t(A, __fdiv_rn((float)k, (float)A.K));
+    t1 = s_to_t(A, __fdiv_rn((float)(k + 1), (float)A.K));
+}
+
+// Occupancy of the cell of c(x), x the midpoint of [t0, t1] on the ray.
+__device__ __forceinline__ bool occupied(const UArgs& A, const float o[3], const float d[3], float t0, float t1,
+                                         float x[3]) {
+    const float tm = __fmul_rn(__fadd_rn(t0, t1), 0.5f);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) x[a] = __fadd_rn(o[a], __fmul_rn(d[a], tm));
+    const float m = fmaxf(fmaxf(fabsf(x[0]), fabsf(x[1])), fabsf(x[2]));
+    float c[3] = {x[0], x[1], x[2]};
+    if (m > 1.0f) {  // c = (2 - 1/m) x / m
+        const float inv = __fdiv_rn(1.0f, m);
+        const float g = __fmul_rn(__fsub_rn(2.0f, inv), inv);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) c[a] = __fmul_rn(x[a], g);
+    }
+    const int L = A.g.n_levels;
+    int l = 0;
+    for (; l < L; ++l) {
+        const Level& lv = A.g.lv[l];
+        if (c[0] >= lv.lmin[0] && c[0] <= lv.lmax[0] && c[1] >= lv.lmin[1] && c[1] <= lv.lmax[1] &&
+            c[2] >= lv.lmin[2] && c[2] <= lv.lmax[2])
+            break;
+    }
+    if (l == L) return false;
+    const Level& lv = A.g.lv[l];
+    const int res = A.g.res;
+    int64_t ic[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int q = (int)floorf(__fmul_rn(__fsub_rn(c[a], lv.lmin[a]), lv.scale[a]));
+        ic[a] = q < 0 ? 0 : (q > res - 1 ? res - 1 : q);
+    }
+    const int64_t idx = (int64_t)l * res * res * res + (ic[0] * res + ic[1]) * res + ic[2];
+    return (__ldg(&A.g.bits[idx >> 5]) >> (idx & 31)) & 1u;
+}
+
+// The per-ray table: blobs with integral bound > kCullEps along the line,
+// {A_b, t*_b, C_b + log2 peak_b} (log2-scaled).  Returns the count, or -1 if
+// more than kTable blobs qualify.
+__device__ int build_table(const nacc_blob_field& f, const float o[3], const float d[3], float* tA, float* tT,
+                           float* tC) {
+    const int lane = threadIdx.x & 31;
+    const float dd = fmaf(d[2], d[2], fmaf(d[1], d[1], d[0] * d[0]));
+    const float idd = dd > 0.0f ? 1.0f / dd : 0.0f;
+    const float ilen = dd > 0.0f ? rsqrtf(dd) : 0.0f;
+    int n = 0;
+    for (int b = 0; b < f.n_blobs; ++b) {
+        const float pk = __ldg(f.peak + b);
+        if (!(pk > 0.0f)) continue;
+        const float sd = __ldg(f.std + b);
+        const float m0 = __ldg(f.mu + 3 * b) - o[0], m1 = __ldg(f.mu + 3 * b + 1) - o[1],
+                    m2 = __ldg(f.mu + 3 * b + 2) - o[2];
+        const float coef2 = -0.72134752f / (sd * sd);  // -log2(e) / 2
+        float ts, pp;
+        if (dd > 0.0f) {
+            const float cx = fmaf(m1, d[2], -m2 * d[1]), cy = fmaf(m2, d[0], -m0 * d[2]), cz = fmaf(m0, d[1], -m1 * d[0]);
+            ts = fmaf(m2, d[2], fmaf(m1, d[1], m0 * d[0])) * idd;
+            pp = fmaf(cz, cz, fmaf(cy, cy, cx * cx)) * idd;
+        } else {
+            ts = 0.0f;
+            pp = fmaf(m2, m2, fmaf(m1, m1, m0 * m0));
+        }
+        const float lp = __log2f(pk);
+        const float C = fmaf(coef2, pp, lp);
+        // integral of peak 2^(A u^2 + C') over the line <= 2^C sqrt(2 pi) sd / |d|
+        const float bound = dd > 0.0f ? ex2_approx(C) * 2.5066283f * sd * ilen : ex2_approx(C) * 1e30f;
+        if (!(bound > kCullEps)) continue;
+        if (n == kTable) return -1;
+        tA[n * 32 + lane] = coef2 * dd;
+        tT[n * 32 + lane] = ts;
+        tC[n * 32 + lane] = C;
+        ++n;
+    }
+    return n;
+}
+
+__device__ __forceinline__ float sigma_all(const nacc_blob_field& f, const float x[3]) {
+    float s = 0.0f;
+    for (int b = 0; b < f.n_blobs; ++b) {
+        const float sd = __ldg(f.std + b);
+        const float dx = x[0] - __ldg(f.mu + 3 * b), dy = x[1] - __ldg(f.mu + 3 * b + 1),
+                    dz = x[2] - __ldg(f.mu + 3 * b + 2);
+        s = fmaf(__ldg(f.peak + b), __expf(-fmaf(dz, dz, fmaf(dy, dy, dx * dx)) / (2.0f * sd * sd)), s);
+    }
+    return s;
+}
+
+template <bool kField>
+__global__ void __launch_bounds__(kThreads) k_unb_count(UArgs A, int32_t* __restrict__ counts,
+                                                        int32_t* __restrict__ kstops,
+                                                        long long* __restrict__ block_sums) {
+    __shared__ float tA[kField ? kTable * 32 : 1], tT[kField ? kTable * 32 : 1], tC[kField ? kTable * 32 : 1];
+    const int lane = threadIdx.x & 31;
+    const int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    int cnt = 0, kstop = A.K;
+    if (r < A.n) {
+        const float o[3] = {A.o[3 * r], A.o[3 * r + 1], A.o[3 * r + 2]};
+        const float d[3] = {A.d[3 * r], A.d[3 * r + 1], A.d[3 * r + 2]};
+        int nt = 0;
+        if (kField) nt = build_table(A.field, o, d, tA, tT, tC);
+        float tau = 0.0f;
+        for (int k = 0; k < A.K; ++k) {
+            float t0, t1, x[3];
+            lattice(A, k, t0, t1);
+            if (!occupied(A, o, d, t0, t1, x)) continue;
+            if (kField) {
+                if (tau > A.thr) {
+                    kstop = k;
+                    break;
+                }
+                float sg = 0.0f;
+                if (nt >= 0) {
+                    const float tm = 0.5f * (t0 + t1);
+                    for (int b = 0; b < nt; ++b) {
+                        const float u = tm - tT[b * 32 + lane];
+                        sg += ex2_approx(fmaf(tA[b * 32 + lane] * u, u, tC[b * 32 + lane]));
+                    }
+                } else {
+                    sg = sigma_all(A.field, x);
+                }
+                tau = __fadd_rn(tau, __fmul_rn(sg, __fsub_rn(t1, t0)));
+            }
+            ++cnt;
+        }
+        counts[r] = cnt;
+        kstops[r] = kstop;
+    }
+    int v = cnt;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) block_sums[blockIdx.x] = v;
+}
+
+// One block: exclusive scan of the block totals in place; total -> *n_samples, offsets[n].
+__global__ void __launch_bounds__(1024) k_unb_scan(long long* __restrict__ sums, int64_t nb,
+                                                   int64_t* __restrict__ off_last, int64_t* __restrict__ n_samples) {
+    __shared__ long long s_w[32];
+    __shared__ long long s_carry;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < nb; base += 1024) {
+        const int64_t i = base + threadIdx.x;
+        const long long v = i < nb ? sums[i] : 0;
+        long long x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_w[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            long long w = s_w[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            s_w[lane] = w;
+        }
+        __syncthreads();
+        const long long carry = s_carry;
+        const long long incl = x + (wid > 0 ? s_w[wid - 1] : 0);
+        if (i < nb) sums[i] = carry + incl - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) s_carry = carry + incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        *off_last = s_carry;
+        *n_samples = s_carry;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_unb_fill(UArgs A, const int32_t* __restrict__ counts,
+                                                       const int32_t* __restrict__ kstops,
+                                                       const long long* __restrict__ block_off,
+                                                       const int64_t* __restrict__ n_samples, int64_t capacity,
+                                                       int64_t* __restrict__ offsets, int32_t* __restrict__ ray_idx,
+                                                       float* __restrict__ t0s, float* __restrict__ t1s) {
+    const int lane = threadIdx.x & 31;
+    const int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    const int cnt = r < A.n ? counts[r] : 0;
+    int x = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    long long pos = block_off[blockIdx.x] + x - cnt;
+    if (r < A.n) offsets[r] = pos;
+    if (*n_samples > capacity || cnt == 0) return;
+    const float o[3] = {A.o[3 * r], A.o[3 * r + 1], A.o[3 * r + 2]};
+    const float d[3] = {A.d[3 * r], A.d[3 * r + 1], A.d[3 * r + 2]};
+    const int kend = kstops[r];
+    int written = 0;
+    for (int k = 0; k < kend && written < cnt; ++k) {
+        float t0, t1, xx[3];
+        lattice(A, k, t0, t1);
+        if (!occupied(A, o, d, t0, t1, xx)) continue;
+        t0s[pos] = t0;
+        t1s[pos] = t1;
+        if (ray_idx) ray_idx[pos] = (int32_t)r;
+        ++pos;
+        ++written;
+    }
+}
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+}  // namespace nacc
+
+using namespace nacc;
+
+extern "C" size_t nacc_march_unbounded_scratch_bytes(int64_t n_rays) {
+    if (n_rays < 0) return 0;
+    const int64_t nb = (n_rays + kThreads - 1) / kThreads;
+    return align256(4 * (size_t)n_rays) * 2 + align256(8 * (size_t)(nb > 0 ? nb : 1));
+}
+
+extern "C" int nacc_march_unbounded(const nacc_grid* grid, const float* rays_o, const float* rays_d, int64_t n_rays,
+                                    const nacc_march_params* params, const nacc_blob_field* field, nacc_packed* out,
+                                    void* scratch, size_t scratch_bytes, void* stream) {
+    clear_error();
+    UArgs A;
+    if (!make_geom(grid, &A.g, true)) return NACC_ERR_INVALID_ARG;
+    NACC_CHECK_ARG(params != nullptr && out != nullptr, "params / out is NULL");
+    NACC_CHECK_ARG(n_rays >= 0 && n_rays < (int64_t(1) << 40), "n_rays=%lld out of range", (long long)n_rays);
+    NACC_CHECK_ARG(params->max_steps >= 1 && params->max_steps <= (1 << 24), "max_steps=%d outside [1, 2^24]",
+                   params->max_steps);
+    NACC_CHECK_ARG(params->t_min > 0.0f && std::isfinite(params->t_max) && params->t_max > params->t_min,
+                   "need 0 < t_min < t_max < inf (t_near, t_far of the s-lattice)");
+    NACC_CHECK_ARG(out->offsets && out->n_samples, "out->offsets / out->n_samples is NULL");
+    NACC_CHECK_ARG(out->capacity >= 0 && (out->capacity == 0 || (out->t_starts && out->t_ends)),
+                   "out->t_starts / out->t_ends is NULL");
+    const bool with_field = field != nullptr && field->n_blobs > 0 && params->early_stop_eps > 0.0f;
+    if (with_field) {
+        NACC_CHECK_ARG(field->n_blobs <= kMaxBlobs, "n_blobs=%d > %d", field->n_blobs, kMaxBlobs);
+        NACC_CHECK_ARG(field->mu && field->std && field->peak, "field mu/std/peak is NULL");
+    }
+    cudaStream_t st = as_stream(stream);
+    if (n_rays == 0) {
+        NACC_CUDA_TRY(cudaMemsetAsync(out->offsets, 0, sizeof(int64_t), st));
+        NACC_CUDA_TRY(cudaMemsetAsync(out->n_samples, 0, sizeof(int64_t), st));
+        return NACC_OK;
+    }
+    NACC_CHECK_ARG(rays_o && rays_d, "rays_o / rays_d is NULL");
+    const size_t need = nacc_march_unbounded_scratch_bytes(n_rays);
+    NACC_CHECK_ARG(scratch && scratch_bytes >= need, "scratch too small: %zu < %zu bytes", scratch_bytes, need);
+    NACC_CHECK_ARG((reinterpret_cast<uintptr_t>(scratch) & 255) == 0, "scratch not 256-byte aligned");
+    A.o = rays_o;
+    A.d = rays_d;
+    A.n = n_rays;
+    A.K = params->max_steps;
+    A.inv_tn = 1.0f / params->t_min;
+    A.inv_tf = 1.0f / params->t_max;
+    A.thr = with_field ? tau_threshold(params->early_stop_eps) : INFINITY;
+    A.field = with_field ? *field : nacc_blob_field{0, nullptr, nullptr, nullptr, nullptr};
+    char* sp = static_cast<char*>(scratch);
+    int32_t* counts = reinterpret_cast<int32_t*>(sp);
+    sp += align256(4 * (size_t)n_rays);
+    int32_t* kstops = reinterpret_cast<int32_t*>(sp);
+    sp += align256(4 * (size_t)n_rays);
+    long long* bsums = reinterpret_cast<long long*>(sp);
+    const int64_t nb = (n_rays + kThreads - 1) / kThreads;
+    NACC_CHECK_ARG(nb < (int64_t(1) << 31), "too many rays for one launch");
+    if (with_field)
+        k_unb_count<true><<<(unsigned)nb, kThreads, 0, st>>>(A, counts, kstops, bsums);
+    else
+        k_unb_count<false><<<(unsigned)nb, kThreads, 0, st>>>(A, counts, kstops, bsums);
+    NACC_LAUNCH_CHECK();
+    k_unb_scan<<<1, 1024, 0, st>>>(bsums, nb, out->offsets + n_rays, out->n_samples);
+    NACC_LAUNCH_CHECK();
+    k_unb_fill<<<(unsigned)nb, kThreads, 0, st>>>(A, counts, kstops, bsums, out->n_samples, out->capacity, out->offsets,
+                                                  out->ray_indices, out->t_starts, out->t_ends);
+    NACC_LAUNCH_CHECK();
+    const bool may_overflow = (double)out->capacity < (double)n_rays * (double)params->max_steps;
+    if (may_overflow) {
+        int64_t total = 0;
+        NACC_CUDA_TRY(cudaMemcpyAsync(&total, out->n_samples, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        NACC_CUDA_TRY(cudaStreamSynchronize(st));
+        if (total > out->capacity) {
+            set_error("packed capacity %lld < %lld samples", (long long)out->capacity, (long long)total);
+            return NACC_ERR_CAPACITY;
+        }
+    }
+    return NACC_OK;
+}

@@ -1,0 +1,188 @@
+"""GPU parity of the unbounded-scene march (Sec. 3.2): s-lattice uniform in
+[0, 1], disparity-linear map to [t_near, t_far], occupancy of the contracted
+midpoint.
+
+Bars: without a field the packed samples are bit-exact against the oracle;
+with the early stop, bit-exact on rays whose optical depth does not come
+within 1e-4 (relative) of -ln(eps), the rest stop within one sample.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module")
+def nacc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2305_04966_gb300 as m
+    m.load_library()
+    return m
+
+
+def _T(a, dtype=None):
+    t = torch.as_tensor(np.ascontiguousarray(a))
+    return (t.to(dtype) if dtype is not None else t).to(DEV)
+
+
+def _grid(nacc, g, bits):
+    return nacc.OccupancyGrid(tuple(g.aabb_min), tuple(g.aabb_max), g.res, g.n_levels,
+                              _T(bits.view(np.int32), torch.int32))
+
+
+def _run(nacc, grid, w, K, field=None, capacity=None, with_ray_indices=True):
+    pk = nacc.march_unbounded(grid, _T(w.rays_o), _T(w.rays_d), K, w.march.t_min, w.march.t_max,
+                              w.march.early_stop_eps, field=field, capacity=capacity,
+                              with_ray_indices=with_ray_indices)
+    torch.cuda.synchronize()
+    pk = pk.trimmed()
+    return dict(offsets=pk.offsets.cpu().numpy(),
+                ray_indices=None if pk.ray_indices is None else pk.ray_indices.cpu().numpy(),
+                t_starts=pk.t_starts.cpu().numpy(), t_ends=pk.t_ends.cpu().numpy())
+
+
+def _oracle(orc, w, bits, K, blobs=None):
+    g, m = w.grid, w.march
+    return orc.march_unbounded(w.rays_o, w.rays_d, g.aabb_min, g.aabb_max, g.res, g.n_levels, bits, K,
+                               m.t_min, m.t_max, blobs=blobs, eps=m.early_stop_eps)
+
+
+def _equal(got, exp, rays=None):
+    if rays is None:
+        for k in ("offsets", "ray_indices", "t_starts", "t_ends"):
+            np.testing.assert_array_equal(got[k], exp[k], err_msg=k)
+        return
+    go, eo = got["offsets"], exp["offsets"]
+    for r in rays:
+        gs, ge, es, ee = go[r], go[r + 1], eo[r], eo[r + 1]
+        assert ge - gs == ee - es, f"ray {r}: {ge - gs} vs {ee - es} samples"
+        for k in ("t_starts", "t_ends"):
+            np.testing.assert_array_equal(got[k][gs:ge], exp[k][es:ee], err_msg=f"{k} ray {r}")
+        assert np.all(got["ray_indices"][gs:ge] == r)
+
+
+@pytest.fixture(scope="module")
+def small_c5(orc):
+    """Two 64x16 cameras of the 16-camera ring, grid 4 x 32^3 over the contracted cube."""
+    w = workloads.c5_unbounded(n_cams=2, width=64, height=16, res=32)
+    bits, _ = orc.density_grid_contracted(w.grid, w.blobs)
+    return w, bits
+
+
+@pytest.mark.parametrize("K", [1024, 333])
+def test_unbounded_no_field_bit_exact(nacc, orc, small_c5, K):
+    w, bits = small_c5
+    got = _run(nacc, _grid(nacc, w.grid, bits), w, K, field=None)
+    exp = _oracle(orc, w, bits, K)
+    assert exp["offsets"][-1] > 10 * w.n_rays
+    _equal(got, exp)
+
+
+@pytest.mark.parametrize("res,L,seed", [(16, 4, 1), (20, 3, 2), (32, 1, 3)])
+def test_unbounded_random_grids_bit_exact(nacc, orc, res, L, seed):
+    """Random block-structured occupancy over the contracted cube; rays from
+    inside and outside the unit cube, axis-aligned and zero directions."""
+    bits = workloads.random_bitfield(L, res, 500 + seed, p_block=0.3, block=4 if res % 4 == 0 else 5, p_cell=0.6)
+    g = workloads.rng(600 + seed)
+    n = 3000
+    o = workloads._normalise(g.standard_normal((n, 3))) * g.uniform(0.0, 30.0, size=(n, 1))
+    d = workloads._normalise(g.standard_normal((n, 3)))
+    d[:30] = 0.0
+    d[np.arange(30), np.arange(30) % 3] = np.where(np.arange(30) % 2 == 0, 1.0, -1.0)
+    d[30:40] = 0.0  # degenerate direction: every sample at the origin
+    w = workloads.Workload("random", o.astype(np.float32), d.astype(np.float32), None,
+                           workloads.GridSpec((-0.5,) * 3, (0.5,) * 3, res, L),
+                           workloads.MarchSpec(0.0, 512, 0.05, 500.0, 1e-4))
+    got = _run(nacc, _grid(nacc, w.grid, bits), w, 512)
+    exp = _oracle(orc, w, bits, 512)
+    assert exp["offsets"][-1] > 1000
+    _equal(got, exp)
+
+
+def test_unbounded_full_grid_is_the_s_lattice(nacc, orc, small_c5):
+    """All-occupied grid: every ray gets all K samples, t_k = Phi(k / K)."""
+    w, bits = small_c5
+    K = 256
+    full = np.full_like(bits, 0xFFFFFFFF)
+    got = _run(nacc, _grid(nacc, w.grid, full), w, K)
+    assert np.array_equal(np.diff(got["offsets"]), np.full(w.n_rays, K))
+    s = (np.arange(K + 1, dtype=np.float32) / np.float32(K)).astype(np.float32)
+    t = orc.s_to_t(s, w.march.t_min, w.march.t_max)
+    np.testing.assert_array_equal(got["t_starts"].reshape(w.n_rays, K), np.broadcast_to(t[:-1], (w.n_rays, K)))
+    np.testing.assert_array_equal(got["t_ends"].reshape(w.n_rays, K), np.broadcast_to(t[1:], (w.n_rays, K)))
+
+
+def _near_tie_rays(orc, w, full, thr, rel=1e-4):
+    sig, _ = orc.field_samples(w.rays_o, w.rays_d, full["ray_indices"], full["t_starts"], full["t_ends"], w.blobs)
+    tau = sig * (full["t_ends"].astype(np.float64) - full["t_starts"])
+    off = full["offsets"]
+    ties = set()
+    for r in range(len(off) - 1):
+        P = np.cumsum(tau[off[r]:off[r + 1]])
+        if P.size and np.min(np.abs(P - thr)) < rel * thr:
+            ties.add(r)
+    return ties
+
+
+def _check_early_stop(nacc, orc, w, bits, K):
+    grid = _grid(nacc, w.grid, bits)
+    got = _run(nacc, grid, w, K, field=nacc.BlobField.from_numpy(w.blobs))
+    exp = _oracle(orc, w, bits, K, blobs=w.blobs)
+    full = _oracle(orc, w, bits, K)
+    ties = _near_tie_rays(orc, w, full, -math.log(w.march.early_stop_eps))
+    exact = [r for r in range(w.n_rays) if r not in ties]
+    assert len(ties) < 0.02 * w.n_rays
+    _equal(got, exp, exact)
+    gc, ec = np.diff(got["offsets"]), np.diff(exp["offsets"])
+    for r in ties:
+        assert abs(int(gc[r]) - int(ec[r])) <= 1
+    stopped = int((ec < np.diff(full["offsets"])).sum())
+    assert stopped > 0.2 * w.n_rays
+    return stopped
+
+
+def test_unbounded_early_stop_culled_table(nacc, orc, small_c5):
+    """The ring workload's 256-blob field: each ray keeps 16-42 blobs in its table."""
+    w, bits = small_c5
+    _check_early_stop(nacc, orc, w, bits, 1024)
+
+
+def test_unbounded_early_stop_dense_field_direct_sum(nacc, orc):
+    """256 blobs packed within radius 2.5: most rays keep more than the table
+    holds and sum every blob per sample."""
+    w = workloads.c5_unbounded(n_cams=2, width=32, height=16, res=32)
+    blobs = workloads.ball_blob_field(256, 7, radius=2.5, std_lo=0.15, std_hi=0.3, peak=20.0)
+    w = workloads.dataclasses.replace(w, blobs=blobs)
+    # same culling bound as the kernel, in FP64: rays with more than 48 blobs
+    o, d = w.rays_o.astype(np.float64), w.rays_d.astype(np.float64)
+    mu, sd, pk = blobs.mu.astype(np.float64), blobs.std.astype(np.float64), blobs.peak.astype(np.float64)
+    rel = mu[None] - o[:, None]
+    pp = (np.cross(rel, np.broadcast_to(d[:, None], rel.shape)) ** 2).sum(-1) / (d * d).sum(1)[:, None]
+    bound = pk[None] * np.exp(-pp / (2 * sd[None] ** 2)) * math.sqrt(2 * math.pi) * sd[None]
+    assert (bound > 1e-7).sum(1).max() > 60
+    bits, _ = orc.density_grid_contracted(w.grid, blobs)
+    _check_early_stop(nacc, orc, w, bits, 512)
+
+
+def test_unbounded_capacity_and_empty(nacc, orc, small_c5):
+    w, bits = small_c5
+    grid = _grid(nacc, w.grid, bits)
+    exp = _oracle(orc, w, bits, 1024)
+    S = int(exp["offsets"][-1])
+    with pytest.raises(nacc.NaccError):
+        _run(nacc, grid, w, 1024, capacity=S - 1)
+    got = _run(nacc, grid, w, 1024, capacity=S)
+    _equal(got, exp)
+    got = _run(nacc, grid, w, 1024, with_ray_indices=False)
+    np.testing.assert_array_equal(got["t_starts"], exp["t_starts"])
+    empty = workloads.dataclasses.replace(w, rays_o=w.rays_o[:0], rays_d=w.rays_d[:0])
+    got = _run(nacc, grid, empty, 1024)
+    assert got["offsets"].tolist() == [0] and got["t_starts"].size == 0

@@ -664,3 +664,78 @@ def test_sgd_step_and_frames_max_hand_examples():
     np.testing.assert_array_equal(d, np.array([0.75, 0.0, 0.145, 3.0], np.float32))
     np.testing.assert_array_equal(b, [True, False, True, True])
     np.testing.assert_array_equal(G.frames_max([[1.0, 5.0, 0.0], [2.0, -1.0, 0.0], [0.5, 4.0, 3.0]]), [2.0, 5.0, 3.0])
+
+
+# ---------------------------------------------------------------------------
+# unbounded scenes: contraction, s -> t, s-lattice march
+# ---------------------------------------------------------------------------
+
+def test_contraction_closed_forms(orc):
+    g0 = np.random.default_rng(7)
+    inner = g0.uniform(-1.0, 1.0, (200, 3)).astype(np.float32)
+    np.testing.assert_array_equal(orc.contract(inner), inner)  # identity inside the unit cube
+    v = g0.uniform(-1.0, 1.0, (200, 3))
+    v /= np.abs(v).max(1, keepdims=True)  # max|v_a| = 1
+    lam = g0.uniform(1.0, 1e4, 200)
+    x = (v * lam[:, None]).astype(np.float32)
+    c = orc.contract(x).astype(np.float64)
+    lam32 = np.abs(x).max(1).astype(np.float64)
+    np.testing.assert_allclose(c, x * ((2.0 - 1.0 / lam32) / lam32)[:, None], rtol=3e-7, atol=1e-7)
+    assert np.all(np.abs(c) < 2.0) and np.all(np.abs(c).max(1) >= 1.0)
+    # the FP64 inverse of the FP32 image: 2 - 1/lam carries a rounding of ~1e-7,
+    # amplified by lam in the inverse
+    err = np.abs(orc.uncontract(c) - x).max(1) / lam32
+    assert np.all(err <= 3e-7 * lam32 + 1e-6), err.max()
+
+
+def test_s_to_t_is_disparity_linear(orc):
+    tn, tf = 0.2, 1000.0
+    s = np.linspace(0.0, 1.0, 257)
+    t = orc.s_to_t(s, tn, tf).astype(np.float64)
+    assert t[0] == pytest.approx(tn, rel=2e-7) and t[-1] == pytest.approx(tf, rel=2e-7)
+    assert np.all(np.diff(t) > 0)
+    np.testing.assert_allclose(1.0 / t, (1 - s) / tn + s / tf, rtol=1e-6)
+
+
+def test_unbounded_march_full_grid_emits_every_lattice_point(orc):
+    w = workloads.c5_unbounded(n_cams=1, width=16, height=8, res=16)
+    bits = np.full(w.grid.n_cells // 32, 0xFFFFFFFF, np.uint32)
+    K = 64
+    ex = orc.march_unbounded(w.rays_o, w.rays_d, w.grid.aabb_min, w.grid.aabb_max, 16, 4, bits, K, 0.2, 1000.0)
+    assert np.all(np.diff(ex["offsets"]) == K)
+    s = (np.arange(K, dtype=np.float32) / np.float32(K)).astype(np.float32)
+    np.testing.assert_array_equal(ex["t_starts"][:K], orc.s_to_t(s, 0.2, 1000.0))
+
+
+def test_unbounded_march_matches_fp64_geometry(orc):
+    """Samples away from cell faces: emitted iff the FP64 contracted midpoint
+    falls in an occupied cell of the finest level holding it."""
+    w = workloads.c5_unbounded(n_cams=2, width=24, height=8, res=16)
+    res, L, K = 16, 4, 128
+    bits = workloads.random_bitfield(L, res, 77, p_block=0.5, block=4, p_cell=0.5)
+    occ = workloads.unpack_bits(bits)
+    ex = orc.march_unbounded(w.rays_o, w.rays_d, w.grid.aabb_min, w.grid.aabb_max, res, L, bits, K, 0.2, 1000.0)
+    geom = orc.level_geometry(w.grid.aabb_min, w.grid.aabb_max, res, L).astype(np.float64)
+    s = np.arange(K + 1) / K
+    tt = 1.0 / ((1 - s) / 0.2 + s / 1000.0)
+    got = set(zip(ex["ray_indices"].tolist(), ex["t_starts"].tolist()))
+    t0s = orc.s_to_t(s[:-1], 0.2, 1000.0)
+    checked = 0
+    for r in range(w.n_rays):
+        o, d = w.rays_o[r].astype(np.float64), w.rays_d[r].astype(np.float64)
+        for k in range(K):
+            x = o + d * 0.5 * (tt[k] + tt[k + 1])
+            m = np.abs(x).max()
+            c = x if m <= 1 else x * (2 - 1 / m) / m
+            lv = next((l for l in range(L) if np.all(c >= geom[l, 0]) and np.all(c <= geom[l, 1])), None)
+            if lv is None:
+                assert (r, float(t0s[k])) not in got
+                continue
+            u = (c - geom[lv, 0]) * geom[lv, 2]
+            if np.min(np.abs(u - np.round(u))) < 1e-3:
+                continue  # within rounding of a face
+            ic = np.clip(np.floor(u).astype(int), 0, res - 1)
+            idx = lv * res ** 3 + (ic[0] * res + ic[1]) * res + ic[2]
+            assert bool(occ[idx]) == ((r, float(t0s[k])) in got), (r, k)
+            checked += 1
+    assert checked > 5000

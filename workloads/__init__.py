@@ -278,6 +278,51 @@ def c3_training(n_rays: int = 262144) -> Workload:
                     target=target_image(n_rays, 3))
 
 
+def ball_blob_field(n_blobs: int, config_id: int, radius: float = 20.0, std_lo: float = 0.1, std_hi: float = 0.3,
+                    peak: float = 50.0) -> Blobs:
+    """Blobs for an unbounded scene: centres uniform in a ball of ``radius``
+    (r = radius * U^(1/3), uniform direction), std U[std_lo, std_hi] scaled by
+    (1 + r/4) so that far blobs stay a few pixels wide, constant peak, colours
+    uniform in [0,1]^3."""
+    g = rng(config_id, 1)
+    r = radius * g.random(n_blobs) ** (1.0 / 3.0)
+    mu = _normalise(g.standard_normal((n_blobs, 3))) * r[:, None]
+    std = g.uniform(std_lo, std_hi, size=n_blobs) * (1.0 + r / 4.0)
+    rgb = g.uniform(0.0, 1.0, size=(n_blobs, 3))
+    return Blobs(mu=mu.astype(np.float32), std=std.astype(np.float32), peak=np.full(n_blobs, peak, np.float32),
+                 rgb=rgb.astype(np.float32))
+
+
+def ring_cameras(n_cams: int, radius: float = 4.0, height: float = 0.5) -> np.ndarray:
+    """Camera centres evenly spaced on a horizontal circle, all looking at the origin."""
+    a = 2.0 * math.pi * np.arange(n_cams) / n_cams
+    return np.stack([radius * np.cos(a), np.full(n_cams, height), radius * np.sin(a)], axis=-1)
+
+
+# Unbounded scenes: lattice of 1024 steps in s in [0, 1], mapped to t in
+# [T_NEAR_UNBOUNDED, T_FAR_UNBOUNDED]; the grid covers the contracted cube
+# [-2, 2]^3 as 4 cascaded levels around [-0.25, 0.25]^3.
+T_NEAR_UNBOUNDED = 0.2
+T_FAR_UNBOUNDED = 1000.0
+
+
+def c5_unbounded(n_cams: int = 16, width: int = 1024, height: int = 256, res: int = 256) -> Workload:
+    """16 inward-facing 1024x256 cameras (90 degree horizontal field of view) on
+    a radius-4 ring over a 256-blob field spread across radius 20; 4-level
+    cascaded res^3 grid over the contracted space; 4,194,304 rays."""
+    focal = width / 2.0  # tan(45 deg) = 1
+    os_, ds_ = [], []
+    for c in ring_cameras(n_cams):
+        o, d = pinhole_rays(c, width, height, focal)
+        os_.append(o)
+        ds_.append(d)
+    o, d = np.concatenate(os_), np.concatenate(ds_)
+    return Workload(f"unbounded{n_cams}x{width}x{height}_blobs256_grid4x{res}", o, d, ball_blob_field(256, 5),
+                    GridSpec((-0.25, -0.25, -0.25), (0.25, 0.25, 0.25), res, 4),
+                    MarchSpec(0.0, 1024, T_NEAR_UNBOUNDED, T_FAR_UNBOUNDED, 1e-4),
+                    target=target_image(o.shape[0], 5))
+
+
 def subsample(w: Workload, every: int, offset: int = 0) -> Workload:
     """Every ``every``-th ray of a workload (a bounded sample for CPU timing)."""
     sl = slice(offset, None, every)
