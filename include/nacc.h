@@ -131,8 +131,9 @@ int nacc_march_grid(const nacc_grid* grid, const float* rays_o, const float* ray
                     const nacc_blob_field* field, nacc_packed* out, void* scratch,
                     size_t scratch_bytes, void* stream);
 
-/* Scratch bytes nacc_march_unbounded needs for n_rays rays. */
-size_t nacc_march_unbounded_scratch_bytes(int64_t n_rays);
+/* Scratch bytes nacc_march_unbounded needs for n_rays rays and a lattice of
+ * max_steps points (0 for invalid arguments). */
+size_t nacc_march_unbounded_scratch_bytes(int64_t n_rays, int32_t max_steps);
 
 /*
  * Lattice marching for unbounded scenes (Sec. 3.2 "Handling Unbounded
@@ -150,11 +151,24 @@ size_t nacc_march_unbounded_scratch_bytes(int64_t n_rays);
  * the field at x; the early-stop density keeps the blobs whose integral
  * along the ray line exceeds 1e-7 (peak >= 0 expected).  Every lattice point
  * is tested (no skipping).  Outputs, scratch and capacity as
- * nacc_march_grid (scratch >= nacc_march_unbounded_scratch_bytes(n_rays)).
+ * nacc_march_grid (scratch >= nacc_march_unbounded_scratch_bytes(n_rays,
+ * max_steps)).
  */
 int nacc_march_unbounded(const nacc_grid* grid, const float* rays_o, const float* rays_d, int64_t n_rays,
                          const nacc_march_params* params, const nacc_blob_field* field, nacc_packed* out,
                          void* scratch, size_t scratch_bytes, void* stream);
+
+/*
+ * Inverse of the contraction of nacc_march_unbounded (Sec. 3.2), to evaluate
+ * the scene at points of the contracted grid (e.g. the cell points of
+ * nacc_grid_points for the estimator update).  Per point, FP32 with every
+ * operation rounded: m' = max|c_a|; x = c if m' <= 1, else
+ *   inv = 1 / (2 - min(m', 2 - 2^-23)),  x_a = c_a * (inv / m').
+ * Points with m' >= 2 (outside the contracted cube) map to the image of
+ * m' = 2 - 2^-23 (|x| about 8.4e6 m'), not to infinity.
+ * c_in, x_out: [device] [n][3] float32 (may alias).  Errors: n < 0, NULL pointers.
+ */
+int nacc_uncontract_points(int64_t n, const float* c_in, float* x_out, void* stream);
 
 /*
  * Sample points for the estimator update (Eq. 4; Sec. 3.1 "Spatial

@@ -88,6 +88,8 @@ def lib():
         L.orc_s_to_t.argtypes = [f32, f32, f32]
         L.orc_contract_points.restype = None
         L.orc_contract_points.argtypes = [i64, vp, vp]
+        L.orc_uncontract_points.restype = None
+        L.orc_uncontract_points.argtypes = [i64, vp, vp]
         L.orc_max_threads.restype = i32
         L.orc_max_threads.argtypes = []
         _lib = L
@@ -218,12 +220,21 @@ def uncontract(c):
     return out
 
 
+def uncontract32(c):
+    """Inverse contraction in FP32 (the definition the grid update uses):
+    x = c * (inv / m'), inv = 1 / (2 - min(m', 2 - 2^-23)) for m' = max|c_a| > 1."""
+    y = _c(c, np.float32).reshape(-1, 3)
+    out = np.zeros_like(y)
+    lib().orc_uncontract_points(y.shape[0], _ptr(y), _ptr(out))
+    return out
+
+
 def density_grid_contracted(grid_spec, blobs, thresh=0.01, n_threads=None):
     """Occupancy bits of a grid over the contracted space: cell centres (in
-    contracted coordinates) mapped back to the scene, FP64 field > thresh."""
+    contracted coordinates) mapped back to the scene (FP32), FP64 field > thresh."""
     pts = grid_points(grid_spec.aabb_min, grid_spec.aabb_max, grid_spec.res, grid_spec.n_levels, jitter=False,
                       n_threads=n_threads)
-    sig = field_points(uncontract(pts).astype(np.float32), blobs, n_threads)
+    sig = field_points(uncontract32(pts), blobs, n_threads)
     occ = sig > thresh
     w = occ.reshape(-1, 32).astype(np.uint64) * (np.uint64(1) << np.arange(32, dtype=np.uint64))
     return w.sum(1).astype(np.uint32), sig

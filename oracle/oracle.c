@@ -292,6 +292,28 @@ void orc_contract_points(int64_t n, const float* xyz, float* out)
     for (int64_t i = 0; i < n; ++i) orc_contract(&xyz[3 * i], &out[3 * i]);
 }
 
+/* Inverse contraction in FP32 (the scene point of a grid point): m' = max|c_a|;
+ * x = c if m' <= 1, else x_a = c_a * (inv / m') with
+ * inv = 1 / (2 - min(m', largest float below 2)). */
+void orc_uncontract_points(int64_t n, const float* c, float* x)
+{
+    const float mmax = 1.99999988f;
+    for (int64_t i = 0; i < n; ++i) {
+        const float* ci = &c[3 * i];
+        float ax = fabsf(ci[0]), ay = fabsf(ci[1]), az = fabsf(ci[2]);
+        float mp = ax > ay ? ax : ay;
+        mp = mp > az ? mp : az;
+        float g = 1.0f;
+        if (mp > 1.0f) {
+            float mc = mp < mmax ? mp : mmax;
+            float den = 2.0f - mc;
+            float inv = 1.0f / den;
+            g = inv / mp;
+        }
+        for (int a = 0; a < 3; ++a) x[3 * i + a] = ci[a] * g;
+    }
+}
+
 /* One ray of the unbounded march: for k = 0..K-1, s0 = k / K, s1 = (k+1) / K
  * (FP32 divisions), t0 = Phi(s0), t1 = Phi(s1), tm = (t0 + t1) * 0.5,
  * x = o + d * tm; the sample is emitted iff the cell of c(x) is occupied,

@@ -52,9 +52,10 @@ SIGNATURES = {
     "nacc_march_grid": (c_i32, [P(Grid), c_vp, c_vp, c_i64, P(MarchParams), P(BlobField), P(Packed),
                                 c_vp, c_sz, c_vp]),
     "nacc_grid_points": (c_i32, [P(Grid), c_u64, c_i64, c_i32, c_vp, c_vp]),
-    "nacc_march_unbounded_scratch_bytes": (c_sz, [c_i64]),
+    "nacc_march_unbounded_scratch_bytes": (c_sz, [c_i64, c_i32]),
     "nacc_march_unbounded": (c_i32, [P(Grid), c_vp, c_vp, c_i64, P(MarchParams), P(BlobField), P(Packed),
                                      c_vp, c_sz, c_vp]),
+    "nacc_uncontract_points": (c_i32, [c_i64, c_vp, c_vp, c_vp]),
     "nacc_update_grid_scratch_bytes": (c_sz, [c_i64]),
     "nacc_update_grid": (c_i32, [P(Grid), c_vp, c_vp, c_f32, c_f32, c_f32, c_vp, c_vp, c_sz, c_vp]),
     "nacc_update_grid_noalloc": (c_i32, [P(Grid), c_vp, c_vp, c_f32, c_f32, c_f32, c_vp, c_vp]),

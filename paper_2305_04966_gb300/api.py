@@ -234,7 +234,7 @@ def march_unbounded(grid: OccupancyGrid, rays_o: torch.Tensor, rays_d: torch.Ten
     params = _abi.MarchParams(0.0, int(max_steps), float(t_near), float(t_far), float(early_stop_eps))
     fs = field.c_struct() if field is not None else None
     worst = n * int(max_steps)
-    scratch = _scratch(_abi.load().nacc_march_unbounded_scratch_bytes(n), dev)
+    scratch = _scratch(_abi.load().nacc_march_unbounded_scratch_bytes(n, int(max_steps)), dev)
     while True:
         if buffers is None:
             cap = capacity if capacity is not None else (worst if worst * 12 <= (1 << 31) else max(n * 64, 1 << 20))
@@ -252,6 +252,26 @@ def march_unbounded(grid: OccupancyGrid, rays_o: torch.Tensor, rays_d: torch.Ten
         if buffers is not None or capacity is not None:
             raise _abi.NaccError("nacc_march_unbounded", rc, "capacity too small")
         capacity = int(pk.n_samples_dev.item())
+
+
+def uncontract_points(c: torch.Tensor, out=None) -> torch.Tensor:
+    """Scene points of contracted points [n][3] (``nacc_uncontract_points``)."""
+    dev = c.device
+    n = int(c.shape[0])
+    _check(c, "c", _F32, dev, (n, 3))
+    x = out if out is not None else torch.empty_like(c)
+    _check(x, "out", _F32, dev, (n, 3))
+    _abi.call("nacc_uncontract_points", n, _ptr(c), _ptr(x), _stream(dev))
+    return x
+
+
+def density_grid_unbounded(grid: OccupancyGrid, field: BlobField, thresh: float = 0.01):
+    """Initialise a grid over the contracted space from the field at the scene
+    points of the cell centres (bits = sigma > thresh)."""
+    pts = uncontract_points(grid_points(grid, jitter=False))
+    dens = field_points(field, pts)
+    update_grid(grid, dens, decay=0.0, thresh_frac=0.0, thresh_abs=thresh)
+    return grid
 
 
 def _bg(bg):

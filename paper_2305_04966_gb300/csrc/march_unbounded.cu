@@ -16,22 +16,29 @@
 // 1e-7 per blob of optical depth), in a per-lane table of the closed form
 // peak_b 2^(A_b (t - t*_b)^2 + C_b); a ray with more than kTable such blobs
 // sums every blob directly.
+#include <algorithm>
+
 #include "nacc_internal.cuh"
 
 namespace nacc {
 namespace {
 
-constexpr int kThreads = 32;  // one warp per block
+constexpr int kThreads = 128;  // rays per block (4 warps)
+constexpr int kWarps = kThreads / 32;
 constexpr int kTable = 48;
+constexpr int kRunSlots = 16;  // recorded runs of consecutive lattice points per ray
+constexpr int kBatch = 4;      // lattice points whose grid words are loaded together
 constexpr float kCullEps = 1e-7f;
+constexpr float kMaxContracted = 1.99999988f;  // largest float below 2
+constexpr size_t kFieldSmem = 3 * kTable * kThreads * sizeof(float);
 
 struct UArgs {
     GridGeom g;
     const float* o;
     const float* d;
+    const float* tt;  // t_k = Phi(k / K), k = 0..K
     int64_t n;
     int K;
-    float inv_tn, inv_tf;  // 1/t_near, 1/t_far
     float thr;
     nacc_blob_field field;
 };
@@ -42,29 +49,28 @@ __device__ __forceinline__ float ex2_approx(float a) {
     return y;
 }
 
-// t = 1 / (a (1 - s) + b s) with a = 1/t_near, b = 1/t_far, each operation rounded.
-__device__ __forceinline__ float s_to_t(const UArgs& A, float s) {
-    return __fdiv_rn(1.0f, __fadd_rn(__fmul_rn(A.inv_tn, __fsub_rn(1.0f, s)), __fmul_rn(A.inv_tf, s)));
+// t = 1 / (a (1 - s) + b s) with a = 1/t_near, b = 1/t_far, s = k / K, each operation rounded.
+__global__ void __launch_bounds__(256) k_unb_table(int K, float inv_tn, float inv_tf, float* __restrict__ tt) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= K; k += gridDim.x * blockDim.x) {
+        const float s = __fdiv_rn((float)k, (float)K);
+        tt[k] = __fdiv_rn(1.0f, __fadd_rn(__fmul_rn(inv_tn, __fsub_rn(1.0f, s)), __fmul_rn(inv_tf, s)));
+    }
 }
 
-__device__ __forceinline__ void lattice(const UArgs& A, int k, float& t0, float& t1) {
-    t0 = s_to_t(A, __fdiv_rn((float)k, (float)A.K));
-    t1 = s_to_t(A, __fdiv_rn((float)(k + 1), (float)A.K));
-}
-
-// Occupancy of the cell of c(x), x the midpoint of [t0, t1] on the ray.
-__device__ __forceinline__ bool occupied(const UArgs& A, const float o[3], const float d[3], float t0, float t1,
-                                         float x[3]) {
+// Flat cell index of c(x), x the midpoint of [t0, t1] on the ray, in the
+// finest level whose box holds it; -1 outside every level.
+__device__ __forceinline__ int64_t cell_index(const UArgs& A, const float o[3], const float d[3], float t0,
+                                              float t1) {
     const float tm = __fmul_rn(__fadd_rn(t0, t1), 0.5f);
+    float c[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) x[a] = __fadd_rn(o[a], __fmul_rn(d[a], tm));
-    const float m = fmaxf(fmaxf(fabsf(x[0]), fabsf(x[1])), fabsf(x[2]));
-    float c[3] = {x[0], x[1], x[2]};
-    if (m > 1.0f) {  // c = (2 - 1/m) x / m
+    for (int a = 0; a < 3; ++a) c[a] = __fadd_rn(o[a], __fmul_rn(d[a], tm));
+    const float m = fmaxf(fmaxf(fabsf(c[0]), fabsf(c[1])), fabsf(c[2]));
+    if (m > 1.0f) {  // c = x (2 - 1/m) / m
         const float inv = __fdiv_rn(1.0f, m);
         const float g = __fmul_rn(__fsub_rn(2.0f, inv), inv);
 #pragma unroll
-        for (int a = 0; a < 3; ++a) c[a] = __fmul_rn(x[a], g);
+        for (int a = 0; a < 3; ++a) c[a] = __fmul_rn(c[a], g);
     }
     const int L = A.g.n_levels;
     int l = 0;
@@ -74,7 +80,7 @@ __device__ __forceinline__ bool occupied(const UArgs& A, const float o[3], const
             c[2] >= lv.lmin[2] && c[2] <= lv.lmax[2])
             break;
     }
-    if (l == L) return false;
+    if (l == L) return -1;
     const Level& lv = A.g.lv[l];
     const int res = A.g.res;
     int64_t ic[3];
@@ -83,16 +89,64 @@ __device__ __forceinline__ bool occupied(const UArgs& A, const float o[3], const
         const int q = (int)floorf(__fmul_rn(__fsub_rn(c[a], lv.lmin[a]), lv.scale[a]));
         ic[a] = q < 0 ? 0 : (q > res - 1 ? res - 1 : q);
     }
-    const int64_t idx = (int64_t)l * res * res * res + (ic[0] * res + ic[1]) * res + ic[2];
-    return (__ldg(&A.g.bits[idx >> 5]) >> (idx & 31)) & 1u;
+    return (int64_t)l * res * res * res + (ic[0] * res + ic[1]) * res + ic[2];
+}
+
+// Occupancy of lattice points kb..kb+kBatch-1 (bit j set = point kb+j
+// occupied; points >= K are not); t[0..kBatch] receives t_kb..t_(kb+kBatch).
+__device__ __forceinline__ unsigned batch_mask(const UArgs& A, const float o[3], const float d[3], int kb,
+                                               float t[kBatch + 1]) {
+#pragma unroll
+    for (int j = 0; j <= kBatch; ++j) t[j] = __ldg(A.tt + min(kb + j, A.K));
+    int64_t idx[kBatch];
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j) idx[j] = kb + j < A.K ? cell_index(A, o, d, t[j], t[j + 1]) : -1;
+    unsigned m = 0;
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j) {
+        const uint32_t w = idx[j] >= 0 ? __ldg(&A.g.bits[idx[j] >> 5]) : 0u;
+        m |= ((w >> (idx[j] & 31)) & 1u) << j;
+    }
+    return m;
+}
+
+// Runs of consecutive emitted points: merged while they continue one
+// another; up to kRunSlots stored as {first k, count}; n = -1 on overflow.
+struct RunRec {
+    int2* slots;
+    int n;
+    int k0, k1;
+};
+
+__device__ __forceinline__ void rec_point(RunRec& q, int k) {
+    if (q.k1 == k) {
+        q.k1 = k + 1;
+        return;
+    }
+    if (q.k1 > q.k0 && q.n >= 0) {
+        if (q.n < kRunSlots)
+            q.slots[q.n++] = make_int2(q.k0, q.k1 - q.k0);
+        else
+            q.n = -1;
+    }
+    q.k0 = k;
+    q.k1 = k + 1;
+}
+
+__device__ __forceinline__ void rec_flush(RunRec& q) {
+    if (q.k1 > q.k0 && q.n >= 0) {
+        if (q.n < kRunSlots)
+            q.slots[q.n++] = make_int2(q.k0, q.k1 - q.k0);
+        else
+            q.n = -1;
+    }
 }
 
 // The per-ray table: blobs with integral bound > kCullEps along the line,
-// {A_b, t*_b, C_b + log2 peak_b} (log2-scaled).  Returns the count, or -1 if
-// more than kTable blobs qualify.
+// {A_b, t*_b, C_b + log2 peak_b} (log2-scaled), column `tid` of [kTable][kThreads]
+// arrays.  Returns the count, or -1 if more than kTable blobs qualify.
 __device__ int build_table(const nacc_blob_field& f, const float o[3], const float d[3], float* tA, float* tT,
                            float* tC) {
-    const int lane = threadIdx.x & 31;
     const float dd = fmaf(d[2], d[2], fmaf(d[1], d[1], d[0] * d[0]));
     const float idd = dd > 0.0f ? 1.0f / dd : 0.0f;
     const float ilen = dd > 0.0f ? rsqrtf(dd) : 0.0f;
@@ -119,9 +173,9 @@ __device__ int build_table(const nacc_blob_field& f, const float o[3], const flo
         const float bound = dd > 0.0f ? ex2_approx(C) * 2.5066283f * sd * ilen : ex2_approx(C) * 1e30f;
         if (!(bound > kCullEps)) continue;
         if (n == kTable) return -1;
-        tA[n * 32 + lane] = coef2 * dd;
-        tT[n * 32 + lane] = ts;
-        tC[n * 32 + lane] = C;
+        tA[n * kThreads] = coef2 * dd;
+        tT[n * kThreads] = ts;
+        tC[n * kThreads] = C;
         ++n;
     }
     return n;
@@ -138,50 +192,83 @@ __device__ __forceinline__ float sigma_all(const nacc_blob_field& f, const float
     return s;
 }
 
+// Count pass: per ray (one thread), the number of emitted points, the
+// lattice index where the early stop ended the walk, and the runs.
 template <bool kField>
 __global__ void __launch_bounds__(kThreads) k_unb_count(UArgs A, int32_t* __restrict__ counts,
-                                                        int32_t* __restrict__ kstops,
-                                                        long long* __restrict__ block_sums) {
-    __shared__ float tA[kField ? kTable * 32 : 1], tT[kField ? kTable * 32 : 1], tC[kField ? kTable * 32 : 1];
-    const int lane = threadIdx.x & 31;
-    const int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    int cnt = 0, kstop = A.K;
+                                                        int32_t* __restrict__ kstops, int32_t* __restrict__ nruns,
+                                                        int2* __restrict__ runs, long long* __restrict__ block_sums) {
+    extern __shared__ float s_tab[];  // kField: tA, tT, tC, each [kTable][kThreads]
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int64_t r = (int64_t)blockIdx.x * kThreads + tid;
+    int cnt = 0;
     if (r < A.n) {
         const float o[3] = {A.o[3 * r], A.o[3 * r + 1], A.o[3 * r + 2]};
         const float d[3] = {A.d[3 * r], A.d[3 * r + 1], A.d[3 * r + 2]};
+        float* tA = s_tab + tid;
+        float* tT = tA + kTable * kThreads;
+        float* tC = tT + kTable * kThreads;
         int nt = 0;
         if (kField) nt = build_table(A.field, o, d, tA, tT, tC);
+        RunRec q{runs + r * kRunSlots, 0, -1, -1};
         float tau = 0.0f;
-        for (int k = 0; k < A.K; ++k) {
-            float t0, t1, x[3];
-            lattice(A, k, t0, t1);
-            if (!occupied(A, o, d, t0, t1, x)) continue;
-            if (kField) {
-                if (tau > A.thr) {
-                    kstop = k;
-                    break;
-                }
-                float sg = 0.0f;
-                if (nt >= 0) {
-                    const float tm = 0.5f * (t0 + t1);
-                    for (int b = 0; b < nt; ++b) {
-                        const float u = tm - tT[b * 32 + lane];
-                        sg += ex2_approx(fmaf(tA[b * 32 + lane] * u, u, tC[b * 32 + lane]));
+        int kstop = A.K;
+        for (int kb = 0; kb < A.K; kb += kBatch) {
+            float t[kBatch + 1];
+            unsigned m = batch_mask(A, o, d, kb, t);
+            bool stop = false;
+            while (m) {
+                const int j = __ffs(m) - 1;
+                m &= m - 1;
+                const int k = kb + j;
+                if (kField) {
+                    if (tau > A.thr) {
+                        kstop = k;
+                        stop = true;
+                        break;
                     }
-                } else {
-                    sg = sigma_all(A.field, x);
+                    float t0 = t[0], t1 = t[1];
+#pragma unroll
+                    for (int i = 1; i < kBatch; ++i)
+                        if (j == i) t0 = t[i], t1 = t[i + 1];
+                    float sg = 0.0f;
+                    if (nt >= 0) {
+                        const float tm = 0.5f * (t0 + t1);
+                        for (int b = 0; b < nt; ++b) {
+                            const float u = tm - tT[b * kThreads];
+                            sg += ex2_approx(fmaf(tA[b * kThreads] * u, u, tC[b * kThreads]));
+                        }
+                    } else {
+                        const float tm = __fmul_rn(__fadd_rn(t0, t1), 0.5f);
+                        float x[3];
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) x[a] = __fadd_rn(o[a], __fmul_rn(d[a], tm));
+                        sg = sigma_all(A.field, x);
+                    }
+                    tau = __fadd_rn(tau, __fmul_rn(sg, __fsub_rn(t1, t0)));
                 }
-                tau = __fadd_rn(tau, __fmul_rn(sg, __fsub_rn(t1, t0)));
+                rec_point(q, k);
+                ++cnt;
             }
-            ++cnt;
+            if (stop) break;
         }
+        rec_flush(q);
         counts[r] = cnt;
         kstops[r] = kstop;
+        nruns[r] = q.n;
     }
+    __shared__ int s_w[kWarps];
     int v = cnt;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) block_sums[blockIdx.x] = v;
+    if (lane == 0) s_w[wid] = v;
+    __syncthreads();
+    if (tid == 0) {
+        long long t = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) t += s_w[w];
+        block_sums[blockIdx.x] = t;
+    }
 }
 
 // One block: exclusive scan of the block totals in place; total -> *n_samples, offsets[n].
@@ -226,37 +313,104 @@ __global__ void __launch_bounds__(1024) k_unb_scan(long long* __restrict__ sums,
     }
 }
 
+// Fill pass.  Recorded rays are expanded one at a time by their warp (sample
+// p of a ray is point p of its concatenated runs; coalesced stores); rays
+// whose runs overflowed the slots re-walk the lattice per lane up to their
+// recorded stop.
 __global__ void __launch_bounds__(kThreads) k_unb_fill(UArgs A, const int32_t* __restrict__ counts,
                                                        const int32_t* __restrict__ kstops,
+                                                       const int32_t* __restrict__ nruns,
+                                                       const int2* __restrict__ runs,
                                                        const long long* __restrict__ block_off,
                                                        const int64_t* __restrict__ n_samples, int64_t capacity,
                                                        int64_t* __restrict__ offsets, int32_t* __restrict__ ray_idx,
                                                        float* __restrict__ t0s, float* __restrict__ t1s) {
-    const int lane = threadIdx.x & 31;
-    const int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int64_t r = (int64_t)blockIdx.x * kThreads + tid;
     const int cnt = r < A.n ? counts[r] : 0;
+    __shared__ int s_w[kWarps];
     int x = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const int y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
     }
-    long long pos = block_off[blockIdx.x] + x - cnt;
+    if (lane == 31) s_w[wid] = x;
+    __syncthreads();
+    int wbase = 0;
+    for (int w = 0; w < wid; ++w) wbase += s_w[w];
+    long long pos = block_off[blockIdx.x] + wbase + x - cnt;
     if (r < A.n) offsets[r] = pos;
-    if (*n_samples > capacity || cnt == 0) return;
+    if (*n_samples > capacity) return;  // overflow: offsets only (the whole grid agrees)
+    const int nr = cnt > 0 ? nruns[r] : 0;
+    const int64_t r_lane0 = r - lane;
+
+    unsigned todo = __ballot_sync(0xffffffffu, nr > 0);
+    while (todo) {
+        const int j = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int cj = __shfl_sync(0xffffffffu, cnt, j);
+        const int nj = __shfl_sync(0xffffffffu, nr, j);
+        const long long pj = __shfl_sync(0xffffffffu, pos, j);
+        const int64_t rj = r_lane0 + j;
+        const int2 run = lane < nj ? runs[rj * kRunSlots + lane] : make_int2(0, 0);
+        int ex = run.y;  // -> exclusive prefix of the run lengths
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, ex, o);
+            if (lane >= o) ex += y;
+        }
+        ex -= run.y;
+        for (int p0 = 0; p0 < cj; p0 += 32) {
+            const int p = p0 + lane;
+            int k = p;
+            for (int i = 0; i < nj; ++i) {
+                const int ei = __shfl_sync(0xffffffffu, ex, i);
+                const int ki = __shfl_sync(0xffffffffu, run.x, i);
+                if (p >= ei) k = ki + (p - ei);
+            }
+            if (p < cj) {
+                t0s[pj + p] = __ldg(A.tt + k);
+                t1s[pj + p] = __ldg(A.tt + k + 1);
+                if (ray_idx) ray_idx[pj + p] = (int32_t)rj;
+            }
+        }
+    }
+
+    if (nr >= 0) return;
     const float o[3] = {A.o[3 * r], A.o[3 * r + 1], A.o[3 * r + 2]};
     const float d[3] = {A.d[3 * r], A.d[3 * r + 1], A.d[3 * r + 2]};
     const int kend = kstops[r];
     int written = 0;
-    for (int k = 0; k < kend && written < cnt; ++k) {
-        float t0, t1, xx[3];
-        lattice(A, k, t0, t1);
-        if (!occupied(A, o, d, t0, t1, xx)) continue;
-        t0s[pos] = t0;
-        t1s[pos] = t1;
-        if (ray_idx) ray_idx[pos] = (int32_t)r;
-        ++pos;
-        ++written;
+    for (int kb = 0; kb < kend && written < cnt; kb += kBatch) {
+        float t[kBatch + 1];
+        unsigned m = batch_mask(A, o, d, kb, t);
+        while (m && written < cnt) {
+            const int j = __ffs(m) - 1;
+            m &= m - 1;
+            if (kb + j >= kend) break;
+            t0s[pos] = __ldg(A.tt + kb + j);
+            t1s[pos] = __ldg(A.tt + kb + j + 1);
+            if (ray_idx) ray_idx[pos] = (int32_t)r;
+            ++pos;
+            ++written;
+        }
+    }
+}
+
+// x = c if m' = max|c_a| <= 1, else c * (inv / m'), inv = 1 / (2 - min(m', 2 - 2^-23)).
+__global__ void __launch_bounds__(256) k_uncontract(int64_t n, const float* __restrict__ c, float* __restrict__ x) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float c0 = c[3 * i], c1 = c[3 * i + 1], c2 = c[3 * i + 2];
+        const float mp = fmaxf(fmaxf(fabsf(c0), fabsf(c1)), fabsf(c2));
+        float g = 1.0f;
+        if (mp > 1.0f) {
+            const float inv = __fdiv_rn(1.0f, __fsub_rn(2.0f, fminf(mp, kMaxContracted)));
+            g = __fdiv_rn(inv, mp);
+        }
+        x[3 * i] = __fmul_rn(c0, g);
+        x[3 * i + 1] = __fmul_rn(c1, g);
+        x[3 * i + 2] = __fmul_rn(c2, g);
     }
 }
 
@@ -267,10 +421,11 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 using namespace nacc;
 
-extern "C" size_t nacc_march_unbounded_scratch_bytes(int64_t n_rays) {
-    if (n_rays < 0) return 0;
+extern "C" size_t nacc_march_unbounded_scratch_bytes(int64_t n_rays, int32_t max_steps) {
+    if (n_rays < 0 || max_steps < 1) return 0;
     const int64_t nb = (n_rays + kThreads - 1) / kThreads;
-    return align256(4 * (size_t)n_rays) * 2 + align256(8 * (size_t)(nb > 0 ? nb : 1));
+    return align256(4 * (size_t)n_rays) * 3 + align256(sizeof(int2) * kRunSlots * (size_t)n_rays) +
+           align256(8 * (size_t)(nb > 0 ? nb : 1)) + align256(4 * ((size_t)max_steps + 1));
 }
 
 extern "C" int nacc_march_unbounded(const nacc_grid* grid, const float* rays_o, const float* rays_d, int64_t n_rays,
@@ -300,15 +455,15 @@ extern "C" int nacc_march_unbounded(const nacc_grid* grid, const float* rays_o, 
         return NACC_OK;
     }
     NACC_CHECK_ARG(rays_o && rays_d, "rays_o / rays_d is NULL");
-    const size_t need = nacc_march_unbounded_scratch_bytes(n_rays);
+    const size_t need = nacc_march_unbounded_scratch_bytes(n_rays, params->max_steps);
     NACC_CHECK_ARG(scratch && scratch_bytes >= need, "scratch too small: %zu < %zu bytes", scratch_bytes, need);
     NACC_CHECK_ARG((reinterpret_cast<uintptr_t>(scratch) & 255) == 0, "scratch not 256-byte aligned");
+    const int64_t nb = (n_rays + kThreads - 1) / kThreads;
+    NACC_CHECK_ARG(nb < (int64_t(1) << 31), "too many rays for one launch");
     A.o = rays_o;
     A.d = rays_d;
     A.n = n_rays;
     A.K = params->max_steps;
-    A.inv_tn = 1.0f / params->t_min;
-    A.inv_tf = 1.0f / params->t_max;
     A.thr = with_field ? tau_threshold(params->early_stop_eps) : INFINITY;
     A.field = with_field ? *field : nacc_blob_field{0, nullptr, nullptr, nullptr, nullptr};
     char* sp = static_cast<char*>(scratch);
@@ -316,18 +471,34 @@ extern "C" int nacc_march_unbounded(const nacc_grid* grid, const float* rays_o, 
     sp += align256(4 * (size_t)n_rays);
     int32_t* kstops = reinterpret_cast<int32_t*>(sp);
     sp += align256(4 * (size_t)n_rays);
+    int32_t* nruns = reinterpret_cast<int32_t*>(sp);
+    sp += align256(4 * (size_t)n_rays);
+    int2* runs = reinterpret_cast<int2*>(sp);
+    sp += align256(sizeof(int2) * kRunSlots * (size_t)n_rays);
     long long* bsums = reinterpret_cast<long long*>(sp);
-    const int64_t nb = (n_rays + kThreads - 1) / kThreads;
-    NACC_CHECK_ARG(nb < (int64_t(1) << 31), "too many rays for one launch");
-    if (with_field)
-        k_unb_count<true><<<(unsigned)nb, kThreads, 0, st>>>(A, counts, kstops, bsums);
-    else
-        k_unb_count<false><<<(unsigned)nb, kThreads, 0, st>>>(A, counts, kstops, bsums);
+    sp += align256(8 * (size_t)nb);
+    float* tt = reinterpret_cast<float*>(sp);
+    A.tt = tt;
+    {
+        const int K = A.K;
+        const int blocks = (int)std::min<int64_t>(((int64_t)K + 1 + 255) / 256, (int64_t)sm_count() * 4);
+        k_unb_table<<<blocks, 256, 0, st>>>(K, 1.0f / params->t_min, 1.0f / params->t_max, tt);
+        NACC_LAUNCH_CHECK();
+    }
+    if (with_field) {
+        static_assert(kFieldSmem <= 227 * 1024, "field table exceeds shared memory");
+        NACC_CUDA_TRY(cudaFuncSetAttribute(k_unb_count<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)kFieldSmem));
+        k_unb_count<true><<<(unsigned)nb, kThreads, kFieldSmem, st>>>(A, counts, kstops, nruns, runs, bsums);
+    } else {
+        k_unb_count<false><<<(unsigned)nb, kThreads, 0, st>>>(A, counts, kstops, nruns, runs, bsums);
+    }
     NACC_LAUNCH_CHECK();
     k_unb_scan<<<1, 1024, 0, st>>>(bsums, nb, out->offsets + n_rays, out->n_samples);
     NACC_LAUNCH_CHECK();
-    k_unb_fill<<<(unsigned)nb, kThreads, 0, st>>>(A, counts, kstops, bsums, out->n_samples, out->capacity, out->offsets,
-                                                  out->ray_indices, out->t_starts, out->t_ends);
+    k_unb_fill<<<(unsigned)nb, kThreads, 0, st>>>(A, counts, kstops, nruns, runs, bsums, out->n_samples,
+                                                  out->capacity, out->offsets, out->ray_indices, out->t_starts,
+                                                  out->t_ends);
     NACC_LAUNCH_CHECK();
     const bool may_overflow = (double)out->capacity < (double)n_rays * (double)params->max_steps;
     if (may_overflow) {
@@ -339,5 +510,16 @@ extern "C" int nacc_march_unbounded(const nacc_grid* grid, const float* rays_o, 
             return NACC_ERR_CAPACITY;
         }
     }
+    return NACC_OK;
+}
+
+extern "C" int nacc_uncontract_points(int64_t n, const float* c_in, float* x_out, void* stream) {
+    clear_error();
+    NACC_CHECK_ARG(n >= 0, "n=%lld < 0", (long long)n);
+    if (n == 0) return NACC_OK;
+    NACC_CHECK_ARG(c_in && x_out, "c_in / x_out is NULL");
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 16);
+    k_uncontract<<<blocks, 256, 0, as_stream(stream)>>>(n, c_in, x_out);
+    NACC_LAUNCH_CHECK();
     return NACC_OK;
 }

@@ -107,6 +107,37 @@ def test_unbounded_random_grids_bit_exact(nacc, orc, res, L, seed):
     _equal(got, exp)
 
 
+def _runs(packed, t_lattice):
+    """Number of runs of consecutive lattice points of each ray's samples."""
+    k = np.searchsorted(t_lattice, packed["t_starts"])
+    off = packed["offsets"]
+    return np.array([1 + int(np.count_nonzero(np.diff(k[off[r]:off[r + 1]]) != 1)) if off[r + 1] > off[r] else 0
+                     for r in range(len(off) - 1)])
+
+
+def test_unbounded_many_runs_bit_exact(nacc, orc):
+    """A fine random grid breaks rays into many runs: rays whose runs fit the
+    count pass's record (16) and rays that overflow it (re-walked) both match."""
+    res, L = 64, 3
+    g = workloads.rng(4343)
+    occ = g.random((L, res, res, res)) < 0.5
+    occ[:, : res // 2] = True
+    bits = workloads.pack_bits(occ.reshape(-1))
+    n = 2048
+    o = workloads._normalise(g.standard_normal((n, 3))) * g.uniform(0.0, 3.0, size=(n, 1))
+    d = workloads._normalise(g.standard_normal((n, 3)))
+    K = 768
+    w = workloads.Workload("runs", o.astype(np.float32), d.astype(np.float32), None,
+                           workloads.GridSpec((-0.5,) * 3, (0.5,) * 3, res, L),
+                           workloads.MarchSpec(0.0, K, 0.05, 100.0, 1e-4))
+    got = _run(nacc, _grid(nacc, w.grid, bits), w, K)
+    exp = _oracle(orc, w, bits, K)
+    s = (np.arange(K + 1, dtype=np.float32) / np.float32(K)).astype(np.float32)
+    runs = _runs(exp, orc.s_to_t(s, 0.05, 100.0))
+    assert np.count_nonzero(runs > 16) > 100 and np.count_nonzero((runs > 0) & (runs <= 16)) > 100
+    _equal(got, exp)
+
+
 def test_unbounded_full_grid_is_the_s_lattice(nacc, orc, small_c5):
     """All-occupied grid: every ray gets all K samples, t_k = Phi(k / K)."""
     w, bits = small_c5
@@ -186,3 +217,27 @@ def test_unbounded_capacity_and_empty(nacc, orc, small_c5):
     empty = workloads.dataclasses.replace(w, rays_o=w.rays_o[:0], rays_d=w.rays_d[:0])
     got = _run(nacc, grid, empty, 1024)
     assert got["offsets"].tolist() == [0] and got["t_starts"].size == 0
+
+
+def test_uncontract_points_bit_exact(nacc, orc):
+    g0 = np.random.default_rng(11)
+    c = g0.uniform(-2.05, 2.05, (100003, 3)).astype(np.float32)
+    c[:5] = [[2.0, 0.0, 0.0], [0.3, -2.0, 1.0], [1.0, 1.0, 1.0], [0.0, 0.0, 0.0], [-1.0000001, 0.2, 0.1]]
+    got = nacc.uncontract_points(_T(c)).cpu().numpy()
+    np.testing.assert_array_equal(got, orc.uncontract32(c))
+    assert nacc.uncontract_points(_T(c[:0])).shape == (0, 3)
+
+
+def test_density_grid_unbounded_matches_oracle(nacc, orc, small_c5):
+    """Grid over the contracted space from the field at the scene points of
+    the cell centres: bits exact except cells whose density is within 1e-5
+    (relative) of the threshold (FP32 field on the device, FP64 in the oracle)."""
+    w, bits = small_c5
+    _, sig = orc.density_grid_contracted(w.grid, w.blobs)
+    grid = nacc.OccupancyGrid.empty(w.grid.aabb_min, w.grid.aabb_max, w.grid.res, w.grid.n_levels)
+    nacc.density_grid_unbounded(grid, nacc.BlobField.from_numpy(w.blobs), 0.01)
+    got = workloads.unpack_bits(grid.bits.cpu().numpy().view(np.uint32))
+    ref = workloads.unpack_bits(bits)
+    near = np.abs(sig - 0.01) < 1e-5 * 0.01
+    assert np.array_equal(got[~near], ref[~near])
+    assert 0.02 < ref.mean() < 0.5

@@ -688,6 +688,31 @@ def test_contraction_closed_forms(orc):
     assert np.all(err <= 3e-7 * lam32 + 1e-6), err.max()
 
 
+def test_uncontract32_inverts_the_contraction(orc):
+    """The FP32 inverse against the FP64 closed form y * (1 / (2 - m')) / m',
+    the identity inside the unit cube, the clamp at m' >= 2 and a round trip."""
+    g0 = np.random.default_rng(8)
+    inner = g0.uniform(-1.0, 1.0, (100, 3)).astype(np.float32)
+    np.testing.assert_array_equal(orc.uncontract32(inner), inner)
+    v = g0.uniform(-1.0, 1.0, (300, 3))
+    v /= np.abs(v).max(1, keepdims=True)
+    mp = g0.uniform(1.0, 1.999, 300)
+    c = (v * mp[:, None]).astype(np.float32)
+    m32 = np.abs(c).max(1).astype(np.float64)
+    x = orc.uncontract32(c).astype(np.float64)
+    ref = c * ((1.0 / (2.0 - m32)) / m32)[:, None]
+    # three FP32 roundings, the first (2 - m') exact by Sterbenz
+    np.testing.assert_allclose(x, ref, rtol=4e-7, atol=0)
+    assert np.all(np.abs(x).max(1) >= 1.0)
+    np.testing.assert_allclose(orc.contract(x.astype(np.float32)), c, rtol=0, atol=2e-6)
+    edge = np.array([[2.0, 0.5, -1.0], [-3.0, 0.0, 0.0]], np.float32)
+    xe = orc.uncontract32(edge).astype(np.float64)
+    big = 1.0 / (2.0 - np.float64(np.float32(1.99999988)))  # 2^23
+    assert big == 2.0 ** 23
+    np.testing.assert_allclose(xe[0], edge[0] * (big / 2.0), rtol=1e-7)
+    np.testing.assert_allclose(xe[1], edge[1] * (big / 3.0), rtol=1e-7)
+
+
 def test_s_to_t_is_disparity_linear(orc):
     tn, tf = 0.2, 1000.0
     s = np.linspace(0.0, 1.0, 257)
