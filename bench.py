@@ -69,6 +69,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-aux", action="store_true", help="skip the grid-update / sample_pdf timings")
+    ap.add_argument("--no-unbounded", action="store_true", help="skip the unbounded-scene comparison")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target oracle CPU time")
     return ap.parse_args(argv)
 
@@ -493,6 +494,174 @@ def proposal_exact_error(prop):
     prop["T_error_vs_exact"] = out
 
 
+def unbounded_measure(torch, nacc, dev, flush, steps=3, grid_K=(512, 1024, 2048),
+                      prop_cfg=(((64, 32), 32), ((128, 64), 64), ((256, 128), 128)), train_steps=2048,
+                      batch=65536, n_pairs=1 << 24, sample_rays=1500):
+    """Unbounded scenes: 4,194,304 rays from 16 inward-facing 1024x256 cameras
+    over 256 blobs spread across radius 20, space contracted into [-2, 2]^3.
+    Both estimators run the whole training step (sampling + field + render
+    fwd + L2 loss + render bwd):
+      grid: the 4x256^3 grid over the contracted space (initialised from the
+            field at the cell centres' scene points), the s-lattice march with
+            early stop, at several lattice sizes K;
+      proposal: the proposal network (trained first on (contracted point,
+            density) pairs uniform in s along the rays, timed outside the
+            step), rounds of inverse-CDF resampling from bins uniform in s, at
+            several bin counts.
+    Each configuration's final transmittance on a fixed sample of rays is
+    compared (CPU leg) with the exact line integral over [t_near, t_far]; the
+    proposal rounds driven by the exact density give the sampler's own bound."""
+    w = workloads.c5_unbounded()
+    m = w.march
+    n = w.n_rays
+    field = nacc.BlobField.from_numpy(w.blobs, dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    grid = nacc.OccupancyGrid.empty(w.grid.aabb_min, w.grid.aabb_max, w.grid.res, w.grid.n_levels, dev)
+    a.record()
+    nacc.density_grid_unbounded(grid, field, 0.01)
+    b.record()
+    torch.cuda.synchronize()
+    init_ms = a.elapsed_time(b)
+    occ = workloads.unpack_bits(grid.bits.cpu().numpy().view(np.uint32)).reshape(w.grid.n_levels, -1).mean(1)
+    o = torch.as_tensor(w.rays_o).to(dev)
+    d = torch.as_tensor(w.rays_d).to(dev)
+    tgt = torch.as_tensor(w.target).to(dev)
+    sel = np.linspace(0, n - 1, sample_rays).astype(np.int64)
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        tot = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            a.record()
+            out = fn()
+            b.record()
+            torch.cuda.synchronize()
+            tot += a.elapsed_time(b)
+        return tot / steps, out
+
+    def train_tail(pk, sig, rgbs, gs, gc):
+        nacc.field_eval(field, o, d, pk, out=(sig, rgbs))
+        rgb, _, _, tr, _ = nacc.render_fwd(pk.offsets, pk.t_starts, pk.t_ends, sig, rgbs, w.bg, 0.0)
+        _, g_rgb = nacc.l2_loss(rgb, tgt)
+        nacc.render_bwd(pk.offsets, pk.t_starts, pk.t_ends, sig, rgbs, g_rgb, None, None, w.bg, 0.0, out=(gs, gc))
+        return tr
+
+    out = {"workload": w.name, "n_rays": n, "grid_spec": f"{w.grid.n_levels}x{w.grid.res}^3 over [-2,2]^3",
+           "t_near": m.t_min, "t_far": m.t_max, "grid_init_ms": init_ms,
+           "occupied_fraction_per_level": [float(v) for v in occ], "grid": [], "proposal": [], "_T": {}}
+    for K in grid_K:
+        pk = nacc.march_unbounded(grid, o, d, K, m.t_min, m.t_max, m.early_stop_eps, field=field)
+        S = pk.n_samples()
+        del pk
+        bufs = nacc.MarchBuffers(n, S, dev)
+        sig = torch.empty(S, device=dev)
+        rgbs = torch.empty((S, 3), device=dev)
+        gs, gc = torch.empty_like(sig), torch.empty_like(rgbs)
+
+        def march():
+            return nacc.march_unbounded(grid, o, d, K, m.t_min, m.t_max, m.early_stop_eps, field=field,
+                                        buffers=bufs)
+
+        ms, tr = timed(lambda: train_tail(march(), sig, rgbs, gs, gc))
+        march_ms, _ = timed(march)
+        out["grid"].append({"K": K, "samples": S, "samples_per_ray": S / n, "step_ms": ms, "march_ms": march_ms,
+                            "rays/s": n / (ms / 1e3)})
+        out["_T"][f"grid K={K}"] = tr.cpu().numpy()[sel]
+        del bufs, sig, rgbs, gs, gc
+        torch.cuda.empty_cache()
+
+    # training pairs: uniform s along random rays, density of the field there
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(0x5EED + 5)
+    ri = torch.randint(0, n, (n_pairs,), generator=gen, device=dev)
+    s = torch.rand(n_pairs, generator=gen, device=dev)
+    t = 1.0 / ((1.0 / m.t_min) * (1.0 - s) + (1.0 / m.t_max) * s)
+    x = (o[ri] + d[ri] * t[:, None]).contiguous()
+    target = nacc.field_points(field, x)
+    c = nacc.contract_points(x)
+    del x, ri, s, t
+    perm = torch.randperm(n_pairs, generator=gen, device=dev)
+    mlp = nacc.ProposalMLP.init(seed=12, device=dev)
+    losses = []
+    a.record()
+    for it in range(train_steps):
+        j = (it * batch) % n_pairs
+        idx = perm[j:j + batch]
+        losses.append(mlp.train_step(c[idx].contiguous(), target[idx].contiguous(),
+                                     lr=3e-3 if it < train_steps // 2 else 1e-3))
+    b.record()
+    torch.cuda.synchronize()
+    out["training"] = {"pairs": n_pairs, "steps": train_steps, "batch": batch, "ms": a.elapsed_time(b),
+                       "mse_first": float(losses[0].item()), "mse_last": float(torch.stack(losses[-16:]).mean()),
+                       "target_variance": float(target.var())}
+    del c, target, perm, losses
+
+    for rounds, nf in prop_cfg:
+        sampler = nacc.UnboundedProposalSampler(mlp, n, m.t_min, m.t_max, rounds=rounds, n_final=nf, device=dev)
+        S = n * nf
+        sig = torch.empty(S, device=dev)
+        rgbs = torch.empty((S, 3), device=dev)
+        gs, gc = torch.empty_like(sig), torch.empty_like(rgbs)
+        ms, tr = timed(lambda: train_tail(sampler.sample(o, d), sig, rgbs, gs, gc))
+        samp_ms, _ = timed(lambda: sampler.sample(o, d))
+        name = f"proposal {list(rounds)}->{nf}"
+        out["proposal"].append({"rounds": list(rounds), "final_samples_per_ray": nf, "samples": S, "step_ms": ms,
+                                "sampler_ms": samp_ms, "rays/s": n / (ms / 1e3)})
+        out["_T"][name] = tr.cpu().numpy()[sel]
+        # the same rounds driven by the exact density at the bin midpoints
+        e = nacc.phi_edges(n, rounds[0], m.t_min, m.t_max, dev)
+        for i, nb in enumerate(rounds):
+            tm = 0.5 * (e[:, :-1] + e[:, 1:])
+            sg = torch.empty((n, nb), device=dev)
+            for c0 in range(0, n, 1 << 19):
+                c1 = min(n, c0 + (1 << 19))
+                xm = (o[c0:c1, None, :] + d[c0:c1, None, :] * tm[c0:c1, :, None]).reshape(-1, 3).contiguous()
+                sg[c0:c1] = nacc.field_points(field, xm).reshape(c1 - c0, nb)
+            wts = nacc.dense_weights(e, sg)
+            e = nacc.sample_pdf(e, wts, rounds[i + 1] if i + 1 < len(rounds) else nf)
+        pk = nacc.edges_to_packed(e)
+        sig2, rgb2 = nacc.field_eval(field, o, d, pk)
+        out["_T"][f"exact-density {list(rounds)}->{nf}"] = nacc.render_fwd(
+            pk.offsets, pk.t_starts, pk.t_ends, sig2, rgb2, w.bg, 0.0)[3].cpu().numpy()[sel]
+        del sampler, sig, rgbs, gs, gc, e, tm, sg, wts, pk, sig2, rgb2
+        torch.cuda.empty_cache()
+    out["_sample"] = {"rays": sel, "w": w}
+    return out
+
+
+def unbounded_exact_error(unb):
+    """CPU leg: the exact transmittance of the sampled rays over [t_near,
+    t_far] (oracle closed form), each configuration's error against it, and
+    the fastest configuration of each estimator within the error of the grid
+    at K = 1024."""
+    from oracle import proposal as P
+    s = unb.pop("_sample")
+    Ts = unb.pop("_T")
+    w, sel = s["w"], s["rays"]
+    k = len(sel)
+    tau = P.exact_optical_depth(w.rays_o[sel], w.rays_d[sel], np.full(k, w.march.t_min), np.full(k, w.march.t_max),
+                                w.blobs.mu, w.blobs.std, w.blobs.peak)
+    Tex = np.exp(-tau)
+    err = {name: {"mean_abs": float(np.abs(T - Tex).mean()), "p99": float(np.quantile(np.abs(T - Tex), 0.99))}
+           for name, T in Ts.items()}
+    unb["T_error_vs_exact"] = {"rays": k, "exact_T_mean": float(Tex.mean()), **err}
+    for row in unb["grid"]:
+        row["T_mean_abs_err"] = err[f"grid K={row['K']}"]["mean_abs"]
+    for row in unb["proposal"]:
+        row["T_mean_abs_err"] = err[f"proposal {row['rounds']}->{row['final_samples_per_ray']}"]["mean_abs"]
+    target = next((r["T_mean_abs_err"] for r in unb["grid"] if r["K"] == 1024), None)
+    eq = {"target_T_mean_abs_err": target}
+    for est in ("grid", "proposal"):
+        ok = [r for r in unb[est] if target is not None and r["T_mean_abs_err"] <= target * 1.0001]
+        best = max(ok, key=lambda r: r["rays/s"]) if ok else None
+        eq[est] = None if best is None else {"rays/s": best["rays/s"], "T_mean_abs_err": best["T_mean_abs_err"],
+                                             "config": {kk: best[kk] for kk in best if kk in ("K", "rounds",
+                                                        "final_samples_per_ray")}}
+    unb["equal_error"] = eq
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -633,6 +802,13 @@ def run_ours(args):
             aux["proposal"].pop("_sample")
         else:
             proposal_exact_error(aux["proposal"])
+        if not args.no_unbounded:
+            aux["unbounded"] = unbounded_measure(torch, nacc, dev, flush)
+            if args.no_cpu_baseline:
+                aux["unbounded"].pop("_sample")
+                aux["unbounded"].pop("_T")
+            else:
+                unbounded_exact_error(aux["unbounded"])
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -119,6 +119,33 @@ int nacc_occupied_range(const nacc_grid* grid, const float* rays_o, const float*
 int nacc_range_edges(int64_t n_rays, const float* t_lo, const float* t_hi, int32_t n_bins, float* edges,
                      void* stream);
 
+/*
+ * Unbounded scenes (Sec. 3.2): the proposal density at the contracted bin
+ * midpoints, c(o + t d) with t as in nacc_mlp_forward_rays and c the
+ * contraction of nacc_march_unbounded (FP32, each operation rounded:
+ * m = max|x_a|, x * ((2 - 1/m) * (1/m)) if m > 1).  The network's input
+ * domain is the contracted cube [-2, 2]^3.  Arguments as nacc_mlp_forward_rays.
+ */
+int nacc_mlp_forward_rays_contracted(int64_t n_rays, int32_t n_bins, const float* rays_o, const float* rays_d,
+                                     const float* edges, const float* params, const uint16_t* weights,
+                                     float* sigma, void* stream);
+
+/*
+ * The contraction itself for n points (e.g. the training inputs of the
+ * proposal network for unbounded scenes): x_in, c_out [device] [n][3]
+ * (may alias).
+ */
+int nacc_contract_points(int64_t n, const float* x_in, float* c_out, void* stream);
+
+/*
+ * Initial bins of the proposal estimator for unbounded scenes: uniform in
+ * s, mapped to t by the disparity-linear Phi of nacc_march_unbounded:
+ * edges[r][j] = 1 / (a (1 - s_j) + b s_j), s_j = j / n_bins, a = 1/t_near,
+ * b = 1/t_far (FP32, each operation rounded), the same row for every ray.
+ * edges: [device] [n_rays][n_bins+1].  Requires 0 < t_near < t_far < inf.
+ */
+int nacc_phi_edges(int64_t n_rays, int32_t n_bins, float t_near, float t_far, float* edges, void* stream);
+
 /* Diagnostics: the FP32 encoding e(x) of n points -> enc [n][64]. */
 int nacc_mlp_encode(int64_t n, const float* xyz, float* enc, void* stream);
 

@@ -13,7 +13,8 @@ from .api import (BlobField, CombinedSampler, MarchBuffers, OccupancyGrid, Packe
                   UpdateBuffers, dense_weights, density_grid, edges_to_packed, field_eval, field_points,
                   grid_points, l2_loss, march_grid, mlp_encode, render, render_bwd, render_fwd, sample_pdf,
                   uniform_edges, update_grid, update_grid_frames, grid_density_lookup, grid_density_backward,
-                  update_grid_sgd, march_unbounded, uncontract_points, density_grid_unbounded)
+                  update_grid_sgd, march_unbounded, uncontract_points, density_grid_unbounded,
+                  contract_points, phi_edges, UnboundedProposalSampler)
 
 __all__ = [
     "NaccError", "load_library", "BlobField", "MarchBuffers", "OccupancyGrid", "PackedSamples",
@@ -22,5 +23,5 @@ __all__ = [
     "ProposalMLP", "ProposalSampler", "mlp_encode", "uniform_edges", "dense_weights", "edges_to_packed",
     "CombinedSampler", "occupied_range", "range_edges", "update_grid_frames", "grid_density_lookup",
     "grid_density_backward", "update_grid_sgd", "march_unbounded", "uncontract_points",
-    "density_grid_unbounded",
+    "density_grid_unbounded", "contract_points", "phi_edges", "UnboundedProposalSampler",
 ]

@@ -81,6 +81,9 @@ SIGNATURES = {
     "nacc_mlp_adam": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, c_f32, c_f32, c_f32, c_f32, c_vp, c_vp]),
     "nacc_mlp_encode": (c_i32, [c_i64, c_vp, c_vp, c_vp]),
     "nacc_mlp_forward_rays": (c_i32, [c_i64, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "nacc_mlp_forward_rays_contracted": (c_i32, [c_i64, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "nacc_contract_points": (c_i32, [c_i64, c_vp, c_vp, c_vp]),
+    "nacc_phi_edges": (c_i32, [c_i64, c_i32, c_f32, c_f32, c_vp, c_vp]),
     "nacc_uniform_edges": (c_i32, [P(Grid), c_vp, c_vp, c_i64, c_f32, c_f32, c_i32, c_vp, c_vp]),
     "nacc_dense_weights": (c_i32, [c_i64, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "nacc_edges_to_packed": (c_i32, [c_i64, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),

@@ -547,14 +547,19 @@ class ProposalMLP:
                   _stream(dev))
         return sig
 
-    def forward_rays(self, rays_o, rays_d, edges: torch.Tensor, out=None) -> torch.Tensor:
-        """Density at the bin midpoints of rays: edges [n][nb+1] -> [n][nb]."""
+    def forward_rays(self, rays_o, rays_d, edges: torch.Tensor, out=None, contracted: bool = False) -> torch.Tensor:
+        """Density at the bin midpoints of rays: edges [n][nb+1] -> [n][nb]
+        (``contracted``: at the contracted midpoints, for unbounded scenes)."""
         dev = edges.device
         n, nb = int(edges.shape[0]), int(edges.shape[1]) - 1
         _check(edges, "edges", _F32, dev, (n, nb + 1))
+        _check(rays_o, "rays_o", _F32, dev, (n, 3))
+        _check(rays_d, "rays_d", _F32, dev, (n, 3))
         sig = out if out is not None else torch.empty((n, nb), dtype=_F32, device=dev)
-        _abi.call("nacc_mlp_forward_rays", n, nb, _ptr(rays_o), _ptr(rays_d), _ptr(edges), _ptr(self.params),
-                  _ptr(self.weights), _ptr(sig), _stream(dev))
+        _check(sig, "out", _F32, dev, (n, nb))
+        fn = "nacc_mlp_forward_rays_contracted" if contracted else "nacc_mlp_forward_rays"
+        _abi.call(fn, n, nb, _ptr(rays_o), _ptr(rays_d), _ptr(edges), _ptr(self.params), _ptr(self.weights),
+                  _ptr(sig), _stream(dev))
         return sig
 
     def accumulate_grads(self, xyz: torch.Tensor, target: torch.Tensor):
@@ -581,6 +586,26 @@ class ProposalMLP:
         loss = self.loss_sum / xyz.shape[0]
         self.adam(lr)
         return loss
+
+
+def contract_points(x: torch.Tensor, out=None) -> torch.Tensor:
+    """The L-infinity contraction of points [n][3] into [-2, 2]^3 (``nacc_contract_points``)."""
+    dev = x.device
+    n = int(x.shape[0])
+    _check(x, "x", _F32, dev, (n, 3))
+    c = out if out is not None else torch.empty_like(x)
+    _check(c, "out", _F32, dev, (n, 3))
+    _abi.call("nacc_contract_points", n, _ptr(x), _ptr(c), _stream(dev))
+    return c
+
+
+def phi_edges(n_rays: int, n_bins: int, t_near: float, t_far: float, device="cuda", out=None) -> torch.Tensor:
+    """Bins uniform in s mapped to t by the disparity-linear Phi -> edges [n_rays][n_bins+1]."""
+    e = out if out is not None else torch.empty((n_rays, n_bins + 1), dtype=_F32, device=device)
+    dev = e.device
+    _check(e, "edges", _F32, dev, (n_rays, n_bins + 1))
+    _abi.call("nacc_phi_edges", int(n_rays), int(n_bins), float(t_near), float(t_far), _ptr(e), _stream(dev))
+    return e
 
 
 def uniform_edges(grid: OccupancyGrid, rays_o, rays_d, n_bins: int, t_min: float = 0.0, t_max: float = 1e10,
@@ -641,6 +666,7 @@ class ProposalSampler:
         self.sig = [torch.empty((n_rays, nb), dtype=_F32, device=dev) for nb in self.rounds]
         self.w = [torch.empty((n_rays, nb), dtype=_F32, device=dev) for nb in self.rounds]
         self.packed = edges_to_packed(self.edges[-1])
+        self.contracted = False
 
     def sample(self, rays_o, rays_d, t_min: float = 0.0, t_max: float = 1e10, stratified: bool = False,
                seed: int = 0) -> PackedSamples:
@@ -650,11 +676,28 @@ class ProposalSampler:
     def resample(self, rays_o, rays_d, e: torch.Tensor, stratified: bool = False, seed: int = 0) -> PackedSamples:
         """The proposal rounds from given initial bins e [n][rounds[0]+1]."""
         for i, nb in enumerate(self.rounds):
-            s = self.mlp.forward_rays(rays_o, rays_d, e, out=self.sig[i])
+            s = self.mlp.forward_rays(rays_o, rays_d, e, out=self.sig[i], contracted=self.contracted)
             w = dense_weights(e, s, out=self.w[i])
             n_next = self.rounds[i + 1] if i + 1 < len(self.rounds) else self.n_final
             e = sample_pdf(e, w, n_next, stratified, seed + i, out=self.edges[i + 1])
         return edges_to_packed(e, out=self.packed)
+
+
+class UnboundedProposalSampler(ProposalSampler):
+    """The proposal estimator for unbounded scenes (Sec. 3.2): initial bins
+    uniform in s over [t_near, t_far] (disparity-linear Phi), the network
+    evaluated at the contracted bin midpoints; the rounds and the inverse
+    transform sampling act on the bins in t."""
+
+    def __init__(self, mlp: ProposalMLP, n_rays: int, t_near: float, t_far: float, rounds=(64, 32),
+                 n_final: int = 32, device="cuda"):
+        super().__init__(mlp, None, n_rays, rounds, n_final, device)
+        self.t_near, self.t_far = float(t_near), float(t_far)
+        self.contracted = True
+
+    def sample(self, rays_o, rays_d, stratified: bool = False, seed: int = 0) -> PackedSamples:
+        e = phi_edges(self.n_rays, self.rounds[0], self.t_near, self.t_far, out=self.edges[0])
+        return self.resample(rays_o, rays_d, e, stratified, seed)
 
 
 def occupied_range(grid: OccupancyGrid, rays_o, rays_d, step: float, max_steps: int = 1024, t_min: float = 0.0,

@@ -37,6 +37,7 @@ struct UArgs {
     const float* o;
     const float* d;
     const float* tt;  // t_k = Phi(k / K), k = 0..K
+    const float* tm;  // (t_k + t_k+1) * 0.5, k = 0..K-1
     int64_t n;
     int K;
     float thr;
@@ -49,25 +50,33 @@ __device__ __forceinline__ float ex2_approx(float a) {
     return y;
 }
 
-// t = 1 / (a (1 - s) + b s) with a = 1/t_near, b = 1/t_far, s = k / K, each operation rounded.
-__global__ void __launch_bounds__(256) k_unb_table(int K, float inv_tn, float inv_tf, float* __restrict__ tt) {
+__device__ __forceinline__ float phi(int k, int K, float inv_tn, float inv_tf) {
+    const float s = __fdiv_rn((float)k, (float)K);
+    return __fdiv_rn(1.0f, __fadd_rn(__fmul_rn(inv_tn, __fsub_rn(1.0f, s)), __fmul_rn(inv_tf, s)));
+}
+
+// t_k = 1 / (a (1 - s) + b s) with a = 1/t_near, b = 1/t_far, s = k / K, each
+// operation rounded, and the midpoints (t_k + t_k+1) * 0.5.
+__global__ void __launch_bounds__(256) k_unb_table(int K, float inv_tn, float inv_tf, float* __restrict__ tt,
+                                                   float* __restrict__ tm) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= K; k += gridDim.x * blockDim.x) {
-        const float s = __fdiv_rn((float)k, (float)K);
-        tt[k] = __fdiv_rn(1.0f, __fadd_rn(__fmul_rn(inv_tn, __fsub_rn(1.0f, s)), __fmul_rn(inv_tf, s)));
+        const float t0 = phi(k, K, inv_tn, inv_tf);
+        tt[k] = t0;
+        if (k < K) tm[k] = __fmul_rn(__fadd_rn(t0, phi(k + 1, K, inv_tn, inv_tf)), 0.5f);
     }
 }
 
-// Flat cell index of c(x), x the midpoint of [t0, t1] on the ray, in the
-// finest level whose box holds it; -1 outside every level.
-__device__ __forceinline__ int64_t cell_index(const UArgs& A, const float o[3], const float d[3], float t0,
-                                              float t1) {
-    const float tm = __fmul_rn(__fadd_rn(t0, t1), 0.5f);
+// Flat cell index of c(x), x = o + d tm on the ray, in the finest level whose
+// box holds it; -1 (all ones for unsigned I) outside every level.  I is
+// uint32_t when every cell index fits.
+template <typename I>
+__device__ __forceinline__ I cell_index(const UArgs& A, const float o[3], const float d[3], float tm) {
     float c[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) c[a] = __fadd_rn(o[a], __fmul_rn(d[a], tm));
     const float m = fmaxf(fmaxf(fabsf(c[0]), fabsf(c[1])), fabsf(c[2]));
-    if (m > 1.0f) {  // c = x (2 - 1/m) / m
-        const float inv = __fdiv_rn(1.0f, m);
+    if (m > 1.0f) {  // c = x (2 - 1/m) / m; the reciprocal correctly rounded, as 1.0f / m
+        const float inv = __frcp_rn(m);
         const float g = __fmul_rn(__fsub_rn(2.0f, inv), inv);
 #pragma unroll
         for (int a = 0; a < 3; ++a) c[a] = __fmul_rn(c[a], g);
@@ -80,31 +89,32 @@ __device__ __forceinline__ int64_t cell_index(const UArgs& A, const float o[3], 
             c[2] >= lv.lmin[2] && c[2] <= lv.lmax[2])
             break;
     }
-    if (l == L) return -1;
+    if (l == L) return (I)-1;
     const Level& lv = A.g.lv[l];
-    const int res = A.g.res;
-    int64_t ic[3];
+    const I res = (I)A.g.res;
+    I ic[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const int q = (int)floorf(__fmul_rn(__fsub_rn(c[a], lv.lmin[a]), lv.scale[a]));
-        ic[a] = q < 0 ? 0 : (q > res - 1 ? res - 1 : q);
+        ic[a] = (I)(q < 0 ? 0 : (q > A.g.res - 1 ? A.g.res - 1 : q));
     }
-    return (int64_t)l * res * res * res + (ic[0] * res + ic[1]) * res + ic[2];
+    return (I)l * res * res * res + (ic[0] * res + ic[1]) * res + ic[2];
 }
 
 // Occupancy of lattice points kb..kb+kBatch-1 (bit j set = point kb+j
 // occupied; points >= K are not); t[0..kBatch] receives t_kb..t_(kb+kBatch).
+template <typename I>
 __device__ __forceinline__ unsigned batch_mask(const UArgs& A, const float o[3], const float d[3], int kb,
                                                float t[kBatch + 1]) {
 #pragma unroll
     for (int j = 0; j <= kBatch; ++j) t[j] = __ldg(A.tt + min(kb + j, A.K));
-    int64_t idx[kBatch];
+    I idx[kBatch];
 #pragma unroll
-    for (int j = 0; j < kBatch; ++j) idx[j] = kb + j < A.K ? cell_index(A, o, d, t[j], t[j + 1]) : -1;
+    for (int j = 0; j < kBatch; ++j) idx[j] = kb + j < A.K ? cell_index<I>(A, o, d, __ldg(A.tm + kb + j)) : (I)-1;
     unsigned m = 0;
 #pragma unroll
     for (int j = 0; j < kBatch; ++j) {
-        const uint32_t w = idx[j] >= 0 ? __ldg(&A.g.bits[idx[j] >> 5]) : 0u;
+        const uint32_t w = idx[j] != (I)-1 ? __ldg(&A.g.bits[idx[j] >> 5]) : 0u;
         m |= ((w >> (idx[j] & 31)) & 1u) << j;
     }
     return m;
@@ -193,8 +203,10 @@ __device__ __forceinline__ float sigma_all(const nacc_blob_field& f, const float
 }
 
 // Count pass: per ray (one thread), the number of emitted points, the
-// lattice index where the early stop ended the walk, and the runs.
-template <bool kField>
+// lattice index where the early stop ended the walk, and the runs.  With a
+// field, the density of every point of a batch is summed in one pass over
+// the ray's table; the stop rule then runs point by point.
+template <bool kField, typename I>
 __global__ void __launch_bounds__(kThreads) k_unb_count(UArgs A, int32_t* __restrict__ counts,
                                                         int32_t* __restrict__ kstops, int32_t* __restrict__ nruns,
                                                         int2* __restrict__ runs, long long* __restrict__ block_sums) {
@@ -215,37 +227,48 @@ __global__ void __launch_bounds__(kThreads) k_unb_count(UArgs A, int32_t* __rest
         int kstop = A.K;
         for (int kb = 0; kb < A.K; kb += kBatch) {
             float t[kBatch + 1];
-            unsigned m = batch_mask(A, o, d, kb, t);
+            unsigned m = batch_mask<I>(A, o, d, kb, t);
+            if (!m) continue;
+            float sg[kBatch];
+            if (kField) {
+#pragma unroll
+                for (int j = 0; j < kBatch; ++j) sg[j] = 0.0f;
+                if (nt >= 0) {
+                    float tmv[kBatch];
+#pragma unroll
+                    for (int j = 0; j < kBatch; ++j) tmv[j] = 0.5f * (t[j] + t[j + 1]);
+                    for (int b = 0; b < nt; ++b) {
+                        const float a = tA[b * kThreads], ts = tT[b * kThreads], cc = tC[b * kThreads];
+#pragma unroll
+                        for (int j = 0; j < kBatch; ++j) {
+                            const float u = tmv[j] - ts;
+                            sg[j] += ex2_approx(fmaf(a * u, u, cc));
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < kBatch; ++j) {
+                        if (!((m >> j) & 1u)) continue;
+                        const float tmj = __fmul_rn(__fadd_rn(t[j], t[j + 1]), 0.5f);
+                        float x[3];
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) x[a] = __fadd_rn(o[a], __fmul_rn(d[a], tmj));
+                        sg[j] = sigma_all(A.field, x);
+                    }
+                }
+            }
             bool stop = false;
-            while (m) {
-                const int j = __ffs(m) - 1;
-                m &= m - 1;
+#pragma unroll
+            for (int j = 0; j < kBatch; ++j) {
+                if (stop || !((m >> j) & 1u)) continue;
                 const int k = kb + j;
                 if (kField) {
                     if (tau > A.thr) {
                         kstop = k;
                         stop = true;
-                        break;
+                        continue;
                     }
-                    float t0 = t[0], t1 = t[1];
-#pragma unroll
-                    for (int i = 1; i < kBatch; ++i)
-                        if (j == i) t0 = t[i], t1 = t[i + 1];
-                    float sg = 0.0f;
-                    if (nt >= 0) {
-                        const float tm = 0.5f * (t0 + t1);
-                        for (int b = 0; b < nt; ++b) {
-                            const float u = tm - tT[b * kThreads];
-                            sg += ex2_approx(fmaf(tA[b * kThreads] * u, u, tC[b * kThreads]));
-                        }
-                    } else {
-                        const float tm = __fmul_rn(__fadd_rn(t0, t1), 0.5f);
-                        float x[3];
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) x[a] = __fadd_rn(o[a], __fmul_rn(d[a], tm));
-                        sg = sigma_all(A.field, x);
-                    }
-                    tau = __fadd_rn(tau, __fmul_rn(sg, __fsub_rn(t1, t0)));
+                    tau = __fadd_rn(tau, __fmul_rn(sg[j], __fsub_rn(t[j + 1], t[j])));
                 }
                 rec_point(q, k);
                 ++cnt;
@@ -384,7 +407,7 @@ __global__ void __launch_bounds__(kThreads) k_unb_fill(UArgs A, const int32_t* _
     int written = 0;
     for (int kb = 0; kb < kend && written < cnt; kb += kBatch) {
         float t[kBatch + 1];
-        unsigned m = batch_mask(A, o, d, kb, t);
+        unsigned m = batch_mask<int64_t>(A, o, d, kb, t);
         while (m && written < cnt) {
             const int j = __ffs(m) - 1;
             m &= m - 1;
@@ -414,6 +437,33 @@ __global__ void __launch_bounds__(256) k_uncontract(int64_t n, const float* __re
     }
 }
 
+// c = x if m = max|x_a| <= 1, else x * ((2 - 1/m) * (1/m)).
+__global__ void __launch_bounds__(256) k_contract(int64_t n, const float* __restrict__ x, float* __restrict__ c) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float x0 = x[3 * i], x1 = x[3 * i + 1], x2 = x[3 * i + 2];
+        const float m = fmaxf(fmaxf(fabsf(x0), fabsf(x1)), fabsf(x2));
+        float g = 1.0f;
+        if (m > 1.0f) {
+            const float inv = __fdiv_rn(1.0f, m);
+            g = __fmul_rn(__fsub_rn(2.0f, inv), inv);
+        }
+        c[3 * i] = m > 1.0f ? __fmul_rn(x0, g) : x0;
+        c[3 * i + 1] = m > 1.0f ? __fmul_rn(x1, g) : x1;
+        c[3 * i + 2] = m > 1.0f ? __fmul_rn(x2, g) : x2;
+    }
+}
+
+// edges[r][j] = Phi(j / n_bins), the s-lattice of n_bins bins, for every ray.
+__global__ void __launch_bounds__(256) k_phi_edges(int64_t n_rays, int nb, float inv_tn, float inv_tf,
+                                                   float* __restrict__ edges) {
+    const int64_t total = n_rays * (nb + 1);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(i % (nb + 1));
+        const float s = __fdiv_rn((float)j, (float)nb);
+        edges[i] = __fdiv_rn(1.0f, __fadd_rn(__fmul_rn(inv_tn, __fsub_rn(1.0f, s)), __fmul_rn(inv_tf, s)));
+    }
+}
+
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
@@ -425,7 +475,8 @@ extern "C" size_t nacc_march_unbounded_scratch_bytes(int64_t n_rays, int32_t max
     if (n_rays < 0 || max_steps < 1) return 0;
     const int64_t nb = (n_rays + kThreads - 1) / kThreads;
     return align256(4 * (size_t)n_rays) * 3 + align256(sizeof(int2) * kRunSlots * (size_t)n_rays) +
-           align256(8 * (size_t)(nb > 0 ? nb : 1)) + align256(4 * ((size_t)max_steps + 1));
+           align256(8 * (size_t)(nb > 0 ? nb : 1)) + align256(4 * ((size_t)max_steps + 1)) +
+           align256(4 * (size_t)max_steps);
 }
 
 extern "C" int nacc_march_unbounded(const nacc_grid* grid, const float* rays_o, const float* rays_d, int64_t n_rays,
@@ -478,20 +529,31 @@ extern "C" int nacc_march_unbounded(const nacc_grid* grid, const float* rays_o, 
     long long* bsums = reinterpret_cast<long long*>(sp);
     sp += align256(8 * (size_t)nb);
     float* tt = reinterpret_cast<float*>(sp);
+    sp += align256(4 * ((size_t)A.K + 1));
+    float* tm = reinterpret_cast<float*>(sp);
     A.tt = tt;
+    A.tm = tm;
     {
         const int K = A.K;
         const int blocks = (int)std::min<int64_t>(((int64_t)K + 1 + 255) / 256, (int64_t)sm_count() * 4);
-        k_unb_table<<<blocks, 256, 0, st>>>(K, 1.0f / params->t_min, 1.0f / params->t_max, tt);
+        k_unb_table<<<blocks, 256, 0, st>>>(K, 1.0f / params->t_min, 1.0f / params->t_max, tt, tm);
         NACC_LAUNCH_CHECK();
     }
-    if (with_field) {
-        static_assert(kFieldSmem <= 227 * 1024, "field table exceeds shared memory");
-        NACC_CUDA_TRY(cudaFuncSetAttribute(k_unb_count<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    // 32-bit cell indices when every index (and the all-ones "outside") fits
+    const bool idx32 = (int64_t)A.g.n_levels * A.g.res * A.g.res * A.g.res < (int64_t(1) << 32) - 1;
+    static_assert(kFieldSmem <= 227 * 1024, "field table exceeds shared memory");
+    if (with_field && idx32) {
+        NACC_CUDA_TRY(cudaFuncSetAttribute(k_unb_count<true, uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)kFieldSmem));
-        k_unb_count<true><<<(unsigned)nb, kThreads, kFieldSmem, st>>>(A, counts, kstops, nruns, runs, bsums);
+        k_unb_count<true, uint32_t><<<(unsigned)nb, kThreads, kFieldSmem, st>>>(A, counts, kstops, nruns, runs, bsums);
+    } else if (with_field) {
+        NACC_CUDA_TRY(cudaFuncSetAttribute(k_unb_count<true, int64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)kFieldSmem));
+        k_unb_count<true, int64_t><<<(unsigned)nb, kThreads, kFieldSmem, st>>>(A, counts, kstops, nruns, runs, bsums);
+    } else if (idx32) {
+        k_unb_count<false, uint32_t><<<(unsigned)nb, kThreads, 0, st>>>(A, counts, kstops, nruns, runs, bsums);
     } else {
-        k_unb_count<false><<<(unsigned)nb, kThreads, 0, st>>>(A, counts, kstops, nruns, runs, bsums);
+        k_unb_count<false, int64_t><<<(unsigned)nb, kThreads, 0, st>>>(A, counts, kstops, nruns, runs, bsums);
     }
     NACC_LAUNCH_CHECK();
     k_unb_scan<<<1, 1024, 0, st>>>(bsums, nb, out->offsets + n_rays, out->n_samples);
@@ -520,6 +582,32 @@ extern "C" int nacc_uncontract_points(int64_t n, const float* c_in, float* x_out
     NACC_CHECK_ARG(c_in && x_out, "c_in / x_out is NULL");
     const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 16);
     k_uncontract<<<blocks, 256, 0, as_stream(stream)>>>(n, c_in, x_out);
+    NACC_LAUNCH_CHECK();
+    return NACC_OK;
+}
+
+extern "C" int nacc_contract_points(int64_t n, const float* x_in, float* c_out, void* stream) {
+    clear_error();
+    NACC_CHECK_ARG(n >= 0, "n=%lld < 0", (long long)n);
+    if (n == 0) return NACC_OK;
+    NACC_CHECK_ARG(x_in && c_out, "x_in / c_out is NULL");
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 16);
+    k_contract<<<blocks, 256, 0, as_stream(stream)>>>(n, x_in, c_out);
+    NACC_LAUNCH_CHECK();
+    return NACC_OK;
+}
+
+extern "C" int nacc_phi_edges(int64_t n_rays, int32_t n_bins, float t_near, float t_far, float* edges,
+                              void* stream) {
+    clear_error();
+    NACC_CHECK_ARG(n_rays >= 0 && n_rays < (int64_t(1) << 34), "n_rays=%lld out of range", (long long)n_rays);
+    NACC_CHECK_ARG(n_bins >= 1 && n_bins <= 4096, "n_bins=%d outside [1, 4096]", n_bins);
+    NACC_CHECK_ARG(t_near > 0.0f && std::isfinite(t_far) && t_far > t_near, "need 0 < t_near < t_far < inf");
+    if (n_rays == 0) return NACC_OK;
+    NACC_CHECK_ARG(edges, "edges is NULL");
+    const int64_t total = n_rays * (n_bins + 1);
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)sm_count() * 16);
+    k_phi_edges<<<blocks, 256, 0, as_stream(stream)>>>(n_rays, n_bins, 1.0f / t_near, 1.0f / t_far, edges);
     NACC_LAUNCH_CHECK();
     return NACC_OK;
 }

@@ -150,6 +150,7 @@ struct PointSrc {
     const float* d;
     const float* edges;
     int nb;
+    int contract;  // rays: feed c(x), the L-infinity contraction of the bin midpoint
 };
 
 __device__ __forceinline__ void point_of(const PointSrc& S, int64_t p, float& x, float& y, float& z) {
@@ -166,6 +167,16 @@ __device__ __forceinline__ void point_of(const PointSrc& S, int64_t p, float& x,
     x = fmaf(S.d[3 * r], t, S.o[3 * r]);
     y = fmaf(S.d[3 * r + 1], t, S.o[3 * r + 1]);
     z = fmaf(S.d[3 * r + 2], t, S.o[3 * r + 2]);
+    if (S.contract) {
+        const float m = fmaxf(fmaxf(fabsf(x), fabsf(y)), fabsf(z));
+        if (m > 1.0f) {  // x (2 - 1/m) / m
+            const float inv = __fdiv_rn(1.0f, m);
+            const float g = __fmul_rn(__fsub_rn(2.0f, inv), inv);
+            x = __fmul_rn(x, g);
+            y = __fmul_rn(y, g);
+            z = __fmul_rn(z, g);
+        }
+    }
 }
 
 __global__ void __launch_bounds__(kThreads) k_mlp_forward(int64_t n, PointSrc S, const float* __restrict__ P,
@@ -514,16 +525,31 @@ int launch_forward(int64_t n, const PointSrc& S, const float* params, const uint
 }  // namespace
 }  // namespace nacc
 
-extern "C" int nacc_mlp_forward_rays(int64_t n_rays, int32_t n_bins, const float* rays_o, const float* rays_d,
-                                     const float* edges, const float* params, const uint16_t* weights,
-                                     float* sigma, void* stream) {
+namespace nacc {
+namespace {
+int forward_rays(int64_t n_rays, int32_t n_bins, const float* rays_o, const float* rays_d, const float* edges,
+                 const float* params, const uint16_t* weights, float* sigma, int contract, void* stream) {
     clear_error();
     NACC_CHECK_ARG(n_rays >= 0 && n_rays < (int64_t(1) << 34), "n_rays=%lld out of range", (long long)n_rays);
     NACC_CHECK_ARG(n_bins >= 1 && n_bins <= 4096, "n_bins=%d outside [1, 4096]", n_bins);
     if (n_rays == 0) return NACC_OK;
     NACC_CHECK_ARG(rays_o && rays_d && edges && params && weights && sigma, "a pointer argument is NULL");
-    PointSrc S{nullptr, rays_o, rays_d, edges, n_bins};
+    PointSrc S{nullptr, rays_o, rays_d, edges, n_bins, contract};
     return launch_forward(n_rays * n_bins, S, params, weights, sigma, as_stream(stream));
+}
+}  // namespace
+}  // namespace nacc
+
+extern "C" int nacc_mlp_forward_rays(int64_t n_rays, int32_t n_bins, const float* rays_o, const float* rays_d,
+                                     const float* edges, const float* params, const uint16_t* weights,
+                                     float* sigma, void* stream) {
+    return forward_rays(n_rays, n_bins, rays_o, rays_d, edges, params, weights, sigma, 0, stream);
+}
+
+extern "C" int nacc_mlp_forward_rays_contracted(int64_t n_rays, int32_t n_bins, const float* rays_o,
+                                                const float* rays_d, const float* edges, const float* params,
+                                                const uint16_t* weights, float* sigma, void* stream) {
+    return forward_rays(n_rays, n_bins, rays_o, rays_d, edges, params, weights, sigma, 1, stream);
 }
 
 extern "C" int nacc_mlp_forward(int64_t n, const float* xyz, const float* params, const uint16_t* weights,
@@ -532,7 +558,7 @@ extern "C" int nacc_mlp_forward(int64_t n, const float* xyz, const float* params
     NACC_CHECK_ARG(n >= 0 && n < (int64_t(1) << 40), "n=%lld out of range", (long long)n);
     if (n == 0) return NACC_OK;
     NACC_CHECK_ARG(xyz && params && weights && sigma, "a pointer argument is NULL");
-    PointSrc S{xyz, nullptr, nullptr, nullptr, 1};
+    PointSrc S{xyz, nullptr, nullptr, nullptr, 1, 0};
     return launch_forward(n, S, params, weights, sigma, as_stream(stream));
 }
 

@@ -241,3 +241,89 @@ def test_density_grid_unbounded_matches_oracle(nacc, orc, small_c5):
     near = np.abs(sig - 0.01) < 1e-5 * 0.01
     assert np.array_equal(got[~near], ref[~near])
     assert 0.02 < ref.mean() < 0.5
+
+
+# ---------------------------------------------------------------------------
+# learned proposal for unbounded scenes
+# ---------------------------------------------------------------------------
+
+def test_contract_points_bit_exact(nacc, orc):
+    g0 = np.random.default_rng(12)
+    x = (g0.standard_normal((50001, 3)) * g0.lognormal(0.0, 2.0, (50001, 1))).astype(np.float32)
+    x[:4] = [[1.0, -1.0, 0.5], [0.0, 0.0, 0.0], [1.0000001, 0.0, 0.0], [-3e7, 1.0, 2.0]]
+    got = nacc.contract_points(_T(x)).cpu().numpy()
+    np.testing.assert_array_equal(got, orc.contract(x))
+
+
+@pytest.mark.parametrize("nb", [1, 64, 1000])
+def test_phi_edges_bit_exact(nacc, orc, nb):
+    e = nacc.phi_edges(37, nb, 0.2, 1000.0).cpu().numpy()
+    s = (np.arange(nb + 1, dtype=np.float32) / np.float32(nb)).astype(np.float32)
+    row = orc.s_to_t(s, 0.2, 1000.0)
+    np.testing.assert_array_equal(e, np.broadcast_to(row, (37, nb + 1)))
+
+
+def _proposal_params(seed):
+    from oracle import proposal as P
+    p = P.init_params(seed)
+    g = np.random.default_rng(seed + 1)
+    p["b1"] = g.uniform(-0.3, 0.3, 64).astype(np.float32)
+    p["b2"] = g.uniform(-0.3, 0.3, 64).astype(np.float32)
+    p["b3"] = np.array([0.2], np.float32)
+    flat = np.concatenate([p["W1"].reshape(-1), p["b1"], p["W2"].reshape(-1), p["b2"], p["w3"], p["b3"]])
+    return p, flat.astype(np.float32)
+
+
+def _contracted_midpoints(orc, o, d, e):
+    """FP32 midpoints o + d t (t = (e_j + e_j+1) / 2, one FMA per axis as the
+    kernel's point source) then the oracle's FP32 contraction."""
+    t = (0.5 * (e[:, :-1].astype(np.float64) + e[:, 1:])).astype(np.float32)
+    x = (o[:, None, :].astype(np.float64) + d[:, None, :].astype(np.float64) * t[:, :, None]).astype(np.float32)
+    return orc.contract(x.reshape(-1, 3))
+
+
+def test_forward_rays_contracted_matches_oracle(nacc, orc, small_c5):
+    from oracle import proposal as P
+    w, _ = small_c5
+    o, d = w.rays_o[:1024], w.rays_d[:1024]
+    p, flat = _proposal_params(120)
+    mlp = nacc.ProposalMLP(_T(flat))
+    e = nacc.phi_edges(o.shape[0], 64, w.march.t_min, w.march.t_max).cpu().numpy()
+    got = mlp.forward_rays(_T(o), _T(d), _T(e), contracted=True).cpu().numpy().reshape(-1)
+    c = _contracted_midpoints(orc, o, d, e)
+    assert np.abs(c).max() < 2.0 and np.abs(c).max() > 1.9
+    exp = P.forward(p, c)["sigma"]
+    rel = np.abs(got - exp) / np.maximum(np.abs(exp), 1e-3)
+    assert np.median(rel) < 1e-4 and np.mean(rel) < 3e-3 and rel.max() < 5e-2, (np.median(rel), rel.mean(), rel.max())
+
+
+def test_unbounded_sampler_matches_oracle_composition(nacc, orc, small_c5):
+    """Phi bins (64) -> contracted proposal density -> weights -> inverse CDF
+    (32) -> again -> 32 final bins, against the same chain of oracle functions."""
+    from oracle import proposal as P
+    w, _ = small_c5
+    o, d = w.rays_o[:1536], w.rays_d[:1536]
+    n = o.shape[0]
+    p, flat = _proposal_params(121)
+    p["b3"] = np.array([-1.0], np.float32)
+    flat[-1] = -1.0
+    mlp = nacc.ProposalMLP(_T(flat))
+    sampler = nacc.UnboundedProposalSampler(mlp, n, w.march.t_min, w.march.t_max, rounds=(64, 32), n_final=32,
+                                            device=DEV)
+    pk = sampler.sample(_T(o), _T(d))
+    got = np.stack([pk.t_starts.cpu().numpy().reshape(n, 32), pk.t_ends.cpu().numpy().reshape(n, 32)])
+    s = (np.arange(65, dtype=np.float32) / np.float32(64)).astype(np.float32)
+    e = np.broadcast_to(orc.s_to_t(s, w.march.t_min, w.march.t_max), (n, 65)).astype(np.float32)
+    for nb, n_next in ((64, 32), (32, 32)):
+        sg = P.forward(p, _contracted_midpoints(orc, o, d, e))["sigma"]
+        off = np.arange(n + 1, dtype=np.int64) * nb
+        wts = orc.render_fwd(off, e[:, :-1].reshape(-1), e[:, 1:].reshape(-1), sg, np.zeros((n * nb, 3)))["weights"]
+        e = orc.sample_pdf(e, wts.reshape(n, nb).astype(np.float32), n_next)
+    exp = np.stack([e[:, :-1], e[:, 1:]])
+
+    def s_of(t):  # inverse of Phi, in FP64: the bins' positions in s
+        a, b = 1.0 / w.march.t_min, 1.0 / w.march.t_max
+        return (1.0 / t.astype(np.float64) - a) / (b - a)
+
+    err = np.abs(s_of(got) - s_of(exp))
+    assert np.quantile(err, 0.99) < 2e-3 and err.mean() < 2e-4, (np.quantile(err, 0.99), err.mean(), err.max())
