@@ -69,7 +69,11 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-aux", action="store_true", help="skip the grid-update / sample_pdf timings")
-    ap.add_argument("--no-unbounded", action="store_true", help="skip the unbounded-scene comparison")
+    ap.add_argument("--aux-legs", default="update,proposal,unbounded",
+                    help="comma list of auxiliary legs: update (grid update / sample_pdf timings), proposal "
+                         "(learned and combined estimators), unbounded (grid vs proposal on unbounded scenes)")
+    ap.add_argument("--unbounded-cams", type=int, default=16,
+                    help="cameras of the unbounded-scene leg (16 = the 4,194,304-ray workload)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target oracle CPU time")
     return ap.parse_args(argv)
 
@@ -494,7 +498,7 @@ def proposal_exact_error(prop):
     prop["T_error_vs_exact"] = out
 
 
-def unbounded_measure(torch, nacc, dev, flush, steps=3, grid_K=(512, 1024, 2048),
+def unbounded_measure(torch, nacc, dev, flush, n_cams=16, steps=3, grid_K=(512, 1024, 2048),
                       prop_cfg=(((64, 32), 32), ((128, 64), 64), ((256, 128), 128)), train_steps=2048,
                       batch=65536, n_pairs=1 << 24, sample_rays=1500):
     """Unbounded scenes: 4,194,304 rays from 16 inward-facing 1024x256 cameras
@@ -511,9 +515,10 @@ def unbounded_measure(torch, nacc, dev, flush, steps=3, grid_K=(512, 1024, 2048)
     Each configuration's final transmittance on a fixed sample of rays is
     compared (CPU leg) with the exact line integral over [t_near, t_far]; the
     proposal rounds driven by the exact density give the sampler's own bound."""
-    w = workloads.c5_unbounded()
+    w = workloads.c5_unbounded(n_cams=n_cams)
     m = w.march
     n = w.n_rays
+    n_pairs = min(n_pairs, 4 * n)
     field = nacc.BlobField.from_numpy(w.blobs, dev)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     grid = nacc.OccupancyGrid.empty(w.grid.aabb_min, w.grid.aabb_max, w.grid.res, w.grid.n_levels, dev)
@@ -796,14 +801,16 @@ def run_ours(args):
         e2e = e2e_measure(args, torch, nacc, step, w, dev, n, flush, dist)
     aux = None
     if rank == 0 and not args.no_aux:
-        aux = aux_measure(torch, nacc, dev, flush, hbm)
-        aux["proposal"] = proposal_measure(torch, nacc, dev, flush)
-        if args.no_cpu_baseline:
-            aux["proposal"].pop("_sample")
-        else:
-            proposal_exact_error(aux["proposal"])
-        if not args.no_unbounded:
-            aux["unbounded"] = unbounded_measure(torch, nacc, dev, flush)
+        legs = set(filter(None, args.aux_legs.split(",")))
+        aux = aux_measure(torch, nacc, dev, flush, hbm) if "update" in legs else {}
+        if "proposal" in legs:
+            aux["proposal"] = proposal_measure(torch, nacc, dev, flush)
+            if args.no_cpu_baseline:
+                aux["proposal"].pop("_sample")
+            else:
+                proposal_exact_error(aux["proposal"])
+        if "unbounded" in legs:
+            aux["unbounded"] = unbounded_measure(torch, nacc, dev, flush, n_cams=args.unbounded_cams)
             if args.no_cpu_baseline:
                 aux["unbounded"].pop("_sample")
                 aux["unbounded"].pop("_T")

@@ -55,8 +55,15 @@ __global__ void __launch_bounds__(256)
 // then each lane evaluates four consecutive samples per chunk (128-bit
 // loads of t0, t1; 128-bit stores of sigma and rgb for groups inside the
 // ray, scalar accesses at its ends).
+//
+// Fields of more than kCullAbove blobs keep, per ray, only the blobs whose
+// integral along the whole ray line is above kCullEps (bound: peak 2^C_b
+// sqrt(2 pi) sd / |d|); each dropped blob changes sigma by at most
+// peak 2^C_b <= kCullEps |d| / (sqrt(2 pi) sd) at any point of the ray.
 constexpr int kFieldWarps = 8;
 constexpr int kFieldRayBlobs = 256;  // per-warp shared table limit
+constexpr int kCullAbove = 64;
+constexpr float kCullEps = 1e-7f;
 
 __global__ void __launch_bounds__(kFieldWarps * 32)
     k_field_rays(const float* __restrict__ o, const float* __restrict__ d, int64_t n_rays,
@@ -78,19 +85,38 @@ __global__ void __launch_bounds__(kFieldWarps * 32)
         const float dx = __ldg(d + 3 * r), dy = __ldg(d + 3 * r + 1), dz = __ldg(d + 3 * r + 2);
         const float dd = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
         const float idd = dd > 0.0f ? 1.0f / dd : 0.0f;
-        for (int b = lane; b < nb; b += 32) {
-            const BlobS v = sb[b];
-            const float m0 = v.mx - ox, m1 = v.my - oy, m2 = v.mz - oz;
-            float ts, pp;
-            if (dd > 0.0f) {
-                const float cx = fmaf(m1, dz, -m2 * dy), cy = fmaf(m2, dx, -m0 * dz), cz = fmaf(m0, dy, -m1 * dx);
-                ts = fmaf(m2, dz, fmaf(m1, dy, m0 * dx)) * idd;
-                pp = fmaf(cz, cz, fmaf(cy, cy, cx * cx)) * idd;
-            } else {
-                ts = 0.0f;
-                pp = fmaf(m2, m2, fmaf(m1, m1, m0 * m0));
+        const float ilen = dd > 0.0f ? rsqrtf(dd) : 0.0f;
+        // table entries {A_b, t*_b, C_b, b}, compacted in blob order
+        int nt = 0;
+        for (int b0 = 0; b0 < nb; b0 += 32) {
+            const int b = b0 + lane;
+            bool keep = false;
+            float4 ent;
+            if (b < nb) {
+                const BlobS v = sb[b];
+                const float m0 = v.mx - ox, m1 = v.my - oy, m2 = v.mz - oz;
+                float ts, pp;
+                if (dd > 0.0f) {
+                    const float cx = fmaf(m1, dz, -m2 * dy), cy = fmaf(m2, dx, -m0 * dz),
+                                cz = fmaf(m0, dy, -m1 * dx);
+                    ts = fmaf(m2, dz, fmaf(m1, dy, m0 * dx)) * idd;
+                    pp = fmaf(cz, cz, fmaf(cy, cy, cx * cx)) * idd;
+                } else {
+                    ts = 0.0f;
+                    pp = fmaf(m2, m2, fmaf(m1, m1, m0 * m0));
+                }
+                ent = make_float4(v.coef * dd, ts, v.coef * pp, __int_as_float(b));
+                keep = true;
+                if (nb > kCullAbove) {
+                    const float sd = sqrtf(-0.72134752f / v.coef);  // coef = -log2(e) / (2 sd^2)
+                    const float peak_line = v.peak * ex2_approx(ent.z);
+                    const float bound = dd > 0.0f ? peak_line * 2.5066283f * sd * ilen : peak_line * 1e30f;
+                    keep = bound > kCullEps;
+                }
             }
-            q[b] = make_float4(v.coef * dd, ts, v.coef * pp, v.peak);
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            if (keep) q[nt + __popc(bal & ((1u << lane) - 1u))] = ent;
+            nt += __popc(bal);
         }
         __syncwarp();
         const long long a = s & ~3ll;
@@ -113,13 +139,13 @@ __global__ void __launch_bounds__(kFieldWarps * 32)
             float tm[4], sg[4] = {0.0f, 0.0f, 0.0f, 0.0f}, c[12] = {};
 #pragma unroll
             for (int j = 0; j < 4; ++j) tm[j] = 0.5f * (ta[j] + tb[j]);
-            for (int b = 0; b < nb; ++b) {
-                const float4 v = q[b];
-                const BlobS& w = sb[b];
+            for (int i = 0; i < nt; ++i) {
+                const float4 v = q[i];
+                const BlobS& w = sb[__float_as_int(v.w)];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const float u = tm[j] - v.y;
-                    const float sj = v.w * ex2_approx(fmaf(v.x * u, u, v.z));
+                    const float sj = w.peak * ex2_approx(fmaf(v.x * u, u, v.z));
                     sg[j] += sj;
                     c[3 * j] = fmaf(sj, w.r, c[3 * j]);
                     c[3 * j + 1] = fmaf(sj, w.g, c[3 * j + 1]);

@@ -11,11 +11,16 @@
 // cell runs does not hold); the early stop is the bounded march's rule with
 // the field at the uncontracted point.
 //
-// The early-stop density of a ray keeps only the blobs whose integral along
-// the whole ray line is above 1e-7 (a bound on everything dropped: at most
-// 1e-7 per blob of optical depth), in a per-lane table of the closed form
-// peak_b 2^(A_b (t - t*_b)^2 + C_b); a ray with more than kTable such blobs
-// sums every blob directly.
+// Passes: a table of t_k and of the midpoints; the count (one thread per
+// ray, every lattice point, 4 grid words in flight, runs of consecutive
+// points recorded); with a field, the early stop (one warp per ray over its
+// occupied points, 32 at a time); the scan of the block totals; the fill
+// (recorded runs expanded by the warp, coalesced stores).  The early-stop
+// density of a ray keeps only the blobs whose integral along the whole ray
+// line is above 1e-7 (a bound on everything dropped: at most 1e-7 per blob
+// of optical depth), in the warp's shared table of the closed form
+// peak_b 2^(A_b (t - t*_b)^2 + C_b); a ray with more than kStopTable such
+// blobs sums every blob directly.
 #include <algorithm>
 
 #include "nacc_internal.cuh"
@@ -25,12 +30,11 @@ namespace {
 
 constexpr int kThreads = 128;  // rays per block (4 warps)
 constexpr int kWarps = kThreads / 32;
-constexpr int kTable = 48;
+constexpr int kStopTable = 256;  // early-stop table entries per ray (one warp's shared table)
 constexpr int kRunSlots = 16;  // recorded runs of consecutive lattice points per ray
 constexpr int kBatch = 4;      // lattice points whose grid words are loaded together
 constexpr float kCullEps = 1e-7f;
 constexpr float kMaxContracted = 1.99999988f;  // largest float below 2
-constexpr size_t kFieldSmem = 3 * kTable * kThreads * sizeof(float);
 
 struct UArgs {
     GridGeom g;
@@ -152,43 +156,60 @@ __device__ __forceinline__ void rec_flush(RunRec& q) {
     }
 }
 
-// The per-ray table: blobs with integral bound > kCullEps along the line,
-// {A_b, t*_b, C_b + log2 peak_b} (log2-scaled), column `tid` of [kTable][kThreads]
-// arrays.  Returns the count, or -1 if more than kTable blobs qualify.
-__device__ int build_table(const nacc_blob_field& f, const float o[3], const float d[3], float* tA, float* tT,
-                           float* tC) {
+// The early-stop table of one ray, built by its warp: the blobs whose
+// integral along the whole ray line exceeds kCullEps (bound peak 2^C
+// sqrt(2 pi) sd / |d|), as {A_b, t*_b, C_b + log2 peak_b} (log2-scaled:
+// density peak_b 2^(A_b (t - t*_b)^2 + C_b)), in blob order.  Returns the
+// count, or -1 if more than kStopTable blobs qualify.
+__device__ int build_warp_table(const nacc_blob_field& f, const float o[3], const float d[3], float4* tab,
+                                int lane) {
     const float dd = fmaf(d[2], d[2], fmaf(d[1], d[1], d[0] * d[0]));
     const float idd = dd > 0.0f ? 1.0f / dd : 0.0f;
     const float ilen = dd > 0.0f ? rsqrtf(dd) : 0.0f;
     int n = 0;
-    for (int b = 0; b < f.n_blobs; ++b) {
-        const float pk = __ldg(f.peak + b);
-        if (!(pk > 0.0f)) continue;
-        const float sd = __ldg(f.std + b);
-        const float m0 = __ldg(f.mu + 3 * b) - o[0], m1 = __ldg(f.mu + 3 * b + 1) - o[1],
-                    m2 = __ldg(f.mu + 3 * b + 2) - o[2];
-        const float coef2 = -0.72134752f / (sd * sd);  // -log2(e) / 2
-        float ts, pp;
-        if (dd > 0.0f) {
-            const float cx = fmaf(m1, d[2], -m2 * d[1]), cy = fmaf(m2, d[0], -m0 * d[2]), cz = fmaf(m0, d[1], -m1 * d[0]);
-            ts = fmaf(m2, d[2], fmaf(m1, d[1], m0 * d[0])) * idd;
-            pp = fmaf(cz, cz, fmaf(cy, cy, cx * cx)) * idd;
-        } else {
-            ts = 0.0f;
-            pp = fmaf(m2, m2, fmaf(m1, m1, m0 * m0));
+    for (int b0 = 0; b0 < f.n_blobs; b0 += 32) {
+        const int b = b0 + lane;
+        bool keep = false;
+        float4 ent = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (b < f.n_blobs) {
+            const float pk = __ldg(f.peak + b);
+            if (pk > 0.0f) {
+                const float sd = __ldg(f.std + b);
+                const float m0 = __ldg(f.mu + 3 * b) - o[0], m1 = __ldg(f.mu + 3 * b + 1) - o[1],
+                            m2 = __ldg(f.mu + 3 * b + 2) - o[2];
+                const float coef2 = -0.72134752f / (sd * sd);  // -log2(e) / 2
+                float ts, pp;
+                if (dd > 0.0f) {
+                    const float cx = fmaf(m1, d[2], -m2 * d[1]), cy = fmaf(m2, d[0], -m0 * d[2]),
+                                cz = fmaf(m0, d[1], -m1 * d[0]);
+                    ts = fmaf(m2, d[2], fmaf(m1, d[1], m0 * d[0])) * idd;
+                    pp = fmaf(cz, cz, fmaf(cy, cy, cx * cx)) * idd;
+                } else {
+                    ts = 0.0f;
+                    pp = fmaf(m2, m2, fmaf(m1, m1, m0 * m0));
+                }
+                const float C = fmaf(coef2, pp, __log2f(pk));
+                const float bound = dd > 0.0f ? ex2_approx(C) * 2.5066283f * sd * ilen : ex2_approx(C) * 1e30f;
+                keep = bound > kCullEps;
+                ent = make_float4(coef2 * dd, ts, C, 0.0f);
+            }
         }
-        const float lp = __log2f(pk);
-        const float C = fmaf(coef2, pp, lp);
-        // integral of peak 2^(A u^2 + C') over the line <= 2^C sqrt(2 pi) sd / |d|
-        const float bound = dd > 0.0f ? ex2_approx(C) * 2.5066283f * sd * ilen : ex2_approx(C) * 1e30f;
-        if (!(bound > kCullEps)) continue;
-        if (n == kTable) return -1;
-        tA[n * kThreads] = coef2 * dd;
-        tT[n * kThreads] = ts;
-        tC[n * kThreads] = C;
-        ++n;
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        const int pos = n + __popc(bal & ((1u << lane) - 1u));
+        if (keep && pos < kStopTable) tab[pos] = ent;
+        n += __popc(bal);
     }
-    return n;
+    return n <= kStopTable ? n : -1;
+}
+
+__device__ __forceinline__ float sigma_table(const float4* tab, int nt, float tm) {
+    float s = 0.0f;
+    for (int b = 0; b < nt; ++b) {
+        const float4 v = tab[b];
+        const float u = tm - v.y;
+        s += ex2_approx(fmaf(v.x * u, u, v.z));
+    }
+    return s;
 }
 
 __device__ __forceinline__ float sigma_all(const nacc_blob_field& f, const float x[3]) {
@@ -202,82 +223,32 @@ __device__ __forceinline__ float sigma_all(const nacc_blob_field& f, const float
     return s;
 }
 
-// Count pass: per ray (one thread), the number of emitted points, the
-// lattice index where the early stop ended the walk, and the runs.  With a
-// field, the density of every point of a batch is summed in one pass over
-// the ray's table; the stop rule then runs point by point.
-template <bool kField, typename I>
+// Count pass: per ray (one thread), the number of occupied lattice points
+// and their runs.
+template <typename I>
 __global__ void __launch_bounds__(kThreads) k_unb_count(UArgs A, int32_t* __restrict__ counts,
                                                         int32_t* __restrict__ kstops, int32_t* __restrict__ nruns,
                                                         int2* __restrict__ runs, long long* __restrict__ block_sums) {
-    extern __shared__ float s_tab[];  // kField: tA, tT, tC, each [kTable][kThreads]
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int64_t r = (int64_t)blockIdx.x * kThreads + tid;
     int cnt = 0;
     if (r < A.n) {
         const float o[3] = {A.o[3 * r], A.o[3 * r + 1], A.o[3 * r + 2]};
         const float d[3] = {A.d[3 * r], A.d[3 * r + 1], A.d[3 * r + 2]};
-        float* tA = s_tab + tid;
-        float* tT = tA + kTable * kThreads;
-        float* tC = tT + kTable * kThreads;
-        int nt = 0;
-        if (kField) nt = build_table(A.field, o, d, tA, tT, tC);
         RunRec q{runs + r * kRunSlots, 0, -1, -1};
-        float tau = 0.0f;
-        int kstop = A.K;
         for (int kb = 0; kb < A.K; kb += kBatch) {
             float t[kBatch + 1];
-            unsigned m = batch_mask<I>(A, o, d, kb, t);
-            if (!m) continue;
-            float sg[kBatch];
-            if (kField) {
-#pragma unroll
-                for (int j = 0; j < kBatch; ++j) sg[j] = 0.0f;
-                if (nt >= 0) {
-                    float tmv[kBatch];
-#pragma unroll
-                    for (int j = 0; j < kBatch; ++j) tmv[j] = 0.5f * (t[j] + t[j + 1]);
-                    for (int b = 0; b < nt; ++b) {
-                        const float a = tA[b * kThreads], ts = tT[b * kThreads], cc = tC[b * kThreads];
-#pragma unroll
-                        for (int j = 0; j < kBatch; ++j) {
-                            const float u = tmv[j] - ts;
-                            sg[j] += ex2_approx(fmaf(a * u, u, cc));
-                        }
-                    }
-                } else {
-#pragma unroll
-                    for (int j = 0; j < kBatch; ++j) {
-                        if (!((m >> j) & 1u)) continue;
-                        const float tmj = __fmul_rn(__fadd_rn(t[j], t[j + 1]), 0.5f);
-                        float x[3];
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) x[a] = __fadd_rn(o[a], __fmul_rn(d[a], tmj));
-                        sg[j] = sigma_all(A.field, x);
-                    }
-                }
-            }
-            bool stop = false;
+            const unsigned m = batch_mask<I>(A, o, d, kb, t);
 #pragma unroll
             for (int j = 0; j < kBatch; ++j) {
-                if (stop || !((m >> j) & 1u)) continue;
-                const int k = kb + j;
-                if (kField) {
-                    if (tau > A.thr) {
-                        kstop = k;
-                        stop = true;
-                        continue;
-                    }
-                    tau = __fadd_rn(tau, __fmul_rn(sg[j], __fsub_rn(t[j + 1], t[j])));
-                }
-                rec_point(q, k);
+                if (!((m >> j) & 1u)) continue;
+                rec_point(q, kb + j);
                 ++cnt;
             }
-            if (stop) break;
         }
         rec_flush(q);
         counts[r] = cnt;
-        kstops[r] = kstop;
+        kstops[r] = A.K;
         nruns[r] = q.n;
     }
     __shared__ int s_w[kWarps];
@@ -285,6 +256,142 @@ __global__ void __launch_bounds__(kThreads) k_unb_count(UArgs A, int32_t* __rest
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if (lane == 0) s_w[wid] = v;
+    __syncthreads();
+    if (tid == 0) {
+        long long t = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) t += s_w[w];
+        block_sums[blockIdx.x] = t;
+    }
+}
+
+// Early stop (after the count pass): one warp per ray, the block's rays in
+// turn.  The ray's occupied points are visited 32 at a time in lattice order
+// (from the recorded runs, or by walking the lattice when the runs
+// overflowed); each lane adds one point's sigma dt, a warp scan gives the
+// optical depth before each point, and the first point whose depth before
+// it exceeds the threshold ends the ray: its count and stop index are cut
+// there and the block's total is rewritten.
+template <typename I>
+__global__ void __launch_bounds__(kThreads) k_unb_stop(UArgs A, int32_t* __restrict__ counts,
+                                                       int32_t* __restrict__ kstops,
+                                                       const int32_t* __restrict__ nruns,
+                                                       const int2* __restrict__ runs,
+                                                       long long* __restrict__ block_sums) {
+    __shared__ float4 s_tab[kWarps][kStopTable];
+    __shared__ int s_w[kWarps];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    float4* tab = s_tab[wid];
+    const int64_t rbase = (int64_t)blockIdx.x * kThreads + wid * 32;
+    int wsum = 0;
+    for (int i = 0; i < 32; ++i) {
+        const int64_t r = rbase + i;
+        if (r >= A.n) break;
+        const int cnt = counts[r];
+        if (cnt == 0) continue;
+        const float o[3] = {A.o[3 * r], A.o[3 * r + 1], A.o[3 * r + 2]};
+        const float d[3] = {A.d[3 * r], A.d[3 * r + 1], A.d[3 * r + 2]};
+        const int nt = build_warp_table(A.field, o, d, tab, lane);
+        __syncwarp();
+        const int nr = nruns[r];
+        int cut = cnt, kstop = A.K;
+        float carry = 0.0f;
+        if (nr >= 0) {
+            const int2 run = lane < nr ? runs[r * kRunSlots + lane] : make_int2(0, 0);
+            int ex = run.y;
+#pragma unroll
+            for (int o2 = 1; o2 < 32; o2 <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, ex, o2);
+                if (lane >= o2) ex += y;
+            }
+            ex -= run.y;
+            for (int p0 = 0; p0 < cnt; p0 += 32) {
+                const int p = p0 + lane;
+                int k = 0;
+                for (int j = 0; j < nr; ++j) {
+                    const int ej = __shfl_sync(0xffffffffu, ex, j);
+                    const int kj = __shfl_sync(0xffffffffu, run.x, j);
+                    if (p >= ej) k = kj + (p - ej);
+                }
+                float tau = 0.0f;
+                if (p < cnt) {
+                    const float t0 = __ldg(A.tt + k), t1 = __ldg(A.tt + k + 1);
+                    float sg;
+                    if (nt >= 0) {
+                        sg = sigma_table(tab, nt, 0.5f * (t0 + t1));
+                    } else {
+                        const float tm = __ldg(A.tm + k);
+                        const float x[3] = {__fadd_rn(o[0], __fmul_rn(d[0], tm)), __fadd_rn(o[1], __fmul_rn(d[1], tm)),
+                                            __fadd_rn(o[2], __fmul_rn(d[2], tm))};
+                        sg = sigma_all(A.field, x);
+                    }
+                    tau = __fmul_rn(sg, __fsub_rn(t1, t0));
+                }
+                float x = tau;
+#pragma unroll
+                for (int o2 = 1; o2 < 32; o2 <<= 1) {
+                    const float y = __shfl_up_sync(0xffffffffu, x, o2);
+                    if (lane >= o2) x += y;
+                }
+                const unsigned over = __ballot_sync(0xffffffffu, p < cnt && carry + (x - tau) > A.thr);
+                if (over) {
+                    const int j = __ffs(over) - 1;
+                    cut = p0 + j;
+                    kstop = __shfl_sync(0xffffffffu, k, j);
+                    break;
+                }
+                carry += __shfl_sync(0xffffffffu, x, 31);
+            }
+        } else {
+            int seen = 0;
+            for (int kb = 0; kb < A.K && seen < cnt; kb += 32) {
+                const int k = kb + lane;
+                bool occ = false;
+                if (k < A.K) {
+                    const I idx = cell_index<I>(A, o, d, __ldg(A.tm + k));
+                    occ = idx != (I)-1 && ((__ldg(&A.g.bits[idx >> 5]) >> (idx & 31)) & 1u);
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, occ);
+                if (!m) continue;
+                float tau = 0.0f;
+                if (occ) {
+                    const float t0 = __ldg(A.tt + k), t1 = __ldg(A.tt + k + 1);
+                    float sg;
+                    if (nt >= 0) {
+                        sg = sigma_table(tab, nt, 0.5f * (t0 + t1));
+                    } else {
+                        const float tm = __ldg(A.tm + k);
+                        const float x[3] = {__fadd_rn(o[0], __fmul_rn(d[0], tm)), __fadd_rn(o[1], __fmul_rn(d[1], tm)),
+                                            __fadd_rn(o[2], __fmul_rn(d[2], tm))};
+                        sg = sigma_all(A.field, x);
+                    }
+                    tau = __fmul_rn(sg, __fsub_rn(t1, t0));
+                }
+                float x = tau;
+#pragma unroll
+                for (int o2 = 1; o2 < 32; o2 <<= 1) {
+                    const float y = __shfl_up_sync(0xffffffffu, x, o2);
+                    if (lane >= o2) x += y;
+                }
+                const unsigned over = __ballot_sync(0xffffffffu, occ && carry + (x - tau) > A.thr);
+                if (over) {
+                    const int j = __ffs(over) - 1;
+                    cut = seen + __popc(m & ((1u << j) - 1u));
+                    kstop = kb + j;
+                    break;
+                }
+                seen += __popc(m);
+                carry += __shfl_sync(0xffffffffu, x, 31);
+            }
+        }
+        if (lane == 0) {
+            counts[r] = cut;
+            kstops[r] = kstop;
+        }
+        wsum += cut;
+        __syncwarp();  // the next ray rewrites the table
+    }
+    if (lane == 0) s_w[wid] = wsum;
     __syncthreads();
     if (tid == 0) {
         long long t = 0;
@@ -541,21 +648,18 @@ extern "C" int nacc_march_unbounded(const nacc_grid* grid, const float* rays_o, 
     }
     // 32-bit cell indices when every index (and the all-ones "outside") fits
     const bool idx32 = (int64_t)A.g.n_levels * A.g.res * A.g.res * A.g.res < (int64_t(1) << 32) - 1;
-    static_assert(kFieldSmem <= 227 * 1024, "field table exceeds shared memory");
-    if (with_field && idx32) {
-        NACC_CUDA_TRY(cudaFuncSetAttribute(k_unb_count<true, uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)kFieldSmem));
-        k_unb_count<true, uint32_t><<<(unsigned)nb, kThreads, kFieldSmem, st>>>(A, counts, kstops, nruns, runs, bsums);
-    } else if (with_field) {
-        NACC_CUDA_TRY(cudaFuncSetAttribute(k_unb_count<true, int64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)kFieldSmem));
-        k_unb_count<true, int64_t><<<(unsigned)nb, kThreads, kFieldSmem, st>>>(A, counts, kstops, nruns, runs, bsums);
-    } else if (idx32) {
-        k_unb_count<false, uint32_t><<<(unsigned)nb, kThreads, 0, st>>>(A, counts, kstops, nruns, runs, bsums);
-    } else {
-        k_unb_count<false, int64_t><<<(unsigned)nb, kThreads, 0, st>>>(A, counts, kstops, nruns, runs, bsums);
-    }
+    if (idx32)
+        k_unb_count<uint32_t><<<(unsigned)nb, kThreads, 0, st>>>(A, counts, kstops, nruns, runs, bsums);
+    else
+        k_unb_count<int64_t><<<(unsigned)nb, kThreads, 0, st>>>(A, counts, kstops, nruns, runs, bsums);
     NACC_LAUNCH_CHECK();
+    if (with_field) {
+        if (idx32)
+            k_unb_stop<uint32_t><<<(unsigned)nb, kThreads, 0, st>>>(A, counts, kstops, nruns, runs, bsums);
+        else
+            k_unb_stop<int64_t><<<(unsigned)nb, kThreads, 0, st>>>(A, counts, kstops, nruns, runs, bsums);
+        NACC_LAUNCH_CHECK();
+    }
     k_unb_scan<<<1, 1024, 0, st>>>(bsums, nb, out->offsets + n_rays, out->n_samples);
     NACC_LAUNCH_CHECK();
     k_unb_fill<<<(unsigned)nb, kThreads, 0, st>>>(A, counts, kstops, nruns, runs, bsums, out->n_samples,

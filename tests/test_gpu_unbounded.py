@@ -327,3 +327,24 @@ def test_unbounded_sampler_matches_oracle_composition(nacc, orc, small_c5):
 
     err = np.abs(s_of(got) - s_of(exp))
     assert np.quantile(err, 0.99) < 2e-3 and err.mean() < 2e-4, (np.quantile(err, 0.99), err.mean(), err.max())
+
+
+def test_field_eval_culled_256_blobs(nacc, orc, small_c5):
+    """The harness field with the unbounded scene's 256 blobs (per-ray culling
+    above 64 blobs) against the oracle's FP64 field on the oracle's samples:
+    sigma within 1e-4 relative plus the culling bound (1e-7 |d| / (sqrt(2 pi)
+    std) per dropped blob, summed over all blobs), colour where sigma > 1."""
+    w, bits = small_c5
+    ex = _oracle(orc, w, bits, 1024)
+    S = int(ex["offsets"][-1])
+    pk = nacc.PackedSamples(_T(ex["offsets"]), _T(ex["ray_indices"]), _T(ex["t_starts"]), _T(ex["t_ends"]),
+                            torch.tensor([S], device=DEV))
+    sig, rgb = nacc.field_eval(nacc.BlobField.from_numpy(w.blobs), _T(w.rays_o), _T(w.rays_d), pk)
+    s64, c64 = orc.field_samples(w.rays_o, w.rays_d, ex["ray_indices"], ex["t_starts"], ex["t_ends"], w.blobs)
+    sig, rgb = sig[:S].cpu().numpy(), rgb[:S].cpu().numpy()
+    dlen = np.linalg.norm(w.rays_d, axis=1)[ex["ray_indices"]]
+    cull = np.sum(1e-7 / (math.sqrt(2 * math.pi) * w.blobs.std.astype(np.float64))) * dlen
+    assert np.all(np.abs(sig - s64) <= 1e-4 * s64 + cull), np.max(np.abs(sig - s64) - 1e-4 * s64 - cull)
+    ok = s64 > 1.0
+    assert ok.sum() > 1000
+    np.testing.assert_allclose(rgb[ok], c64[ok], rtol=1e-3, atol=1e-4)
