@@ -41,6 +41,7 @@ constexpr int oW1 = 0, oB1 = 4096, oW2 = 4160, oB2 = 8256, oW3 = 8320, oB3 = 838
 constexpr int wW1 = 0, wW2 = 4096, wW3 = 8192;
 constexpr uint32_t kTileBytes = 16384;  // 128 rows x 128 bytes
 constexpr uint32_t kWBytes = 8192;      // 64 rows x 128 bytes
+constexpr uint32_t kW3Bytes = 2048;     // 16 rows x 128 bytes (N = 16 tile of the 64 -> 1 layer)
 
 __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
     return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
@@ -53,31 +54,40 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-// e(x): [x, y, z, (sin, cos)(2^k pi x_a) for k = 0..7, a = 0..2], zero-padded to 64.
-// sin/cos of pi x_a and of 16 pi x_a (sincospif, exact argument scaling by 16)
-// anchor the bands; the others follow by the double-angle formulas.
-__device__ __forceinline__ void encode_point(float x, float y, float z, float e[64]) {
+// e(x): [x, y, z, (sin, cos)(2^k pi x_a) for k = 0..7, a = 0..2], padded to 64
+// with `pad` (0; the forward kernel puts ones in columns 51 and 52, which
+// carry layer 1's bias).  sin(2^k pi x) = sin(2 pi f) with f the phase
+// 2^(k-1) x reduced exactly to [-1/2, 1/2] (power-of-two scaling and
+// u - rint(u) are exact in FP32); the hardware sine and cosine of 2 pi f
+// (|2 pi f| <= pi) then have an absolute error below 1e-6.
+__device__ __forceinline__ void encode_point(float x, float y, float z, float e[64], float pad51 = 0.0f) {
     e[0] = x;
     e[1] = y;
     e[2] = z;
     const float c[3] = {x, y, z};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        float s, co;
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            if (k == 0) sincospif(c[a], &s, &co);
-            if (k == 4) sincospif(16.0f * c[a], &s, &co);
+            const float u = c[a] * (0.5f * (float)(1 << k));
+            const float f = u - rintf(u);
+            float s, co;
+            __sincosf(6.28318531f * f, &s, &co);
             e[3 + 6 * k + 2 * a] = s;
             e[4 + 6 * k + 2 * a] = co;
-            const float s2 = 2.0f * s * co;
-            const float c2 = (co - s) * (co + s);
-            s = s2;
-            co = c2;
         }
     }
+    e[51] = pad51;
+    e[52] = pad51;
 #pragma unroll
-    for (int i = 51; i < 64; ++i) e[i] = 0.0f;
+    for (int i = 53; i < 64; ++i) e[i] = 0.0f;
+}
+
+// Two FP32 values -> BF16x2 (round to nearest even) with ReLU: lo in the low half.
+__device__ __forceinline__ uint32_t pack_relu_bf16x2(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
 }
 
 // Row r (64 values -> BF16) of a K-major SW128 tile.
@@ -179,6 +189,49 @@ __device__ __forceinline__ void point_of(const PointSrc& S, int64_t p, float& x,
     }
 }
 
+// Layer 1's weight tile with its bias in the encoding's padding columns 51
+// and 52 (which the forward kernel sets to one): b1 = hi + lo, hi = bf16(b1),
+// lo = bf16(b1 - hi) (b1 to about 2^-17 relative; the definition's padding
+// weights multiply zeros, so replacing them changes nothing else).
+__device__ __forceinline__ void load_w1_bias_tile(uint8_t* dst, const uint16_t* w, const float* P) {
+    for (int i = threadIdx.x; i < 4096; i += blockDim.x) {
+        const int a = i >> 6, b = i & 63;
+        uint16_t v = w[i];
+        if (b == 51 || b == 52) {
+            const float b1 = P[oB1 + a];
+            const __nv_bfloat16 hi = __float2bfloat16_rn(b1);
+            const __nv_bfloat16 h = b == 51 ? hi : __float2bfloat16_rn(b1 - __bfloat162float(hi));
+            v = *reinterpret_cast<const uint16_t*>(&h);
+        }
+        *reinterpret_cast<uint16_t*>(dst + tc::sw128_offset(a, b)) = v;
+    }
+}
+
+// 32 accumulator columns (this thread's row) -> + bias (or none) -> ReLU ->
+// BF16, into 16-byte chunks c0, c0+1, c0+2, c0+3 of row r of a SW128 tile.
+__device__ __forceinline__ void relu_pack32(uint32_t taddr, const float* bias, uint8_t* tile, int r, int c0) {
+    float v[32];
+    tc::tmem_ld16(taddr, v);
+    tc::tmem_ld16(taddr + 16, v + 16);
+    tc::tmem_wait_ld();
+    if (bias) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] += bias[i];
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        uint4 q;
+        q.x = pack_relu_bf16x2(v[8 * c + 0], v[8 * c + 1]);
+        q.y = pack_relu_bf16x2(v[8 * c + 2], v[8 * c + 3]);
+        q.z = pack_relu_bf16x2(v[8 * c + 4], v[8 * c + 5]);
+        q.w = pack_relu_bf16x2(v[8 * c + 6], v[8 * c + 7]);
+        *reinterpret_cast<uint4*>(tile + (r >> 3) * 1024 + (r & 7) * 128 + (((c0 + c) ^ (r & 7)) << 4)) = q;
+    }
+}
+
+// Forward.  Per tile: encode -> MMA (layer 1, bias folded) -> ReLU/BF16 ->
+// MMA (layer 2) -> + b2, ReLU/BF16 -> MMA (64 -> 1 as N = 16 with w3 in row
+// 0 of the B tile) -> + b3, softplus.
 __global__ void __launch_bounds__(kThreads) k_mlp_forward(int64_t n, PointSrc S, const float* __restrict__ P,
                                                           const uint16_t* __restrict__ Wb,
                                                           float* __restrict__ sigma) {
@@ -187,18 +240,18 @@ __global__ void __launch_bounds__(kThreads) k_mlp_forward(int64_t n, PointSrc S,
     uint8_t* sW1 = base;
     uint8_t* sW2 = base + kWBytes;
     uint8_t* sX = base + 2 * kWBytes;
-    __shared__ float sB1[64], sB2[64], sW3[64];
+    uint8_t* sW3 = sX + kTileBytes;  // 16 rows x 128 bytes
+    __shared__ float sB2[64];
     __shared__ float sB3;
     __shared__ uint64_t bar;
     __shared__ uint32_t tbase;
     const int t = threadIdx.x, warp = t >> 5;
-    load_weight_tile(sW1, Wb + wW1, false);
+    load_w1_bias_tile(sW1, Wb + wW1, P);
     load_weight_tile(sW2, Wb + wW2, false);
-    if (t < 64) {
-        sB1[t] = P[oB1 + t];
-        sB2[t] = P[oB2 + t];
-        sW3[t] = __bfloat162float(__ushort_as_bfloat16(Wb[wW3 + t]));
-    }
+    for (int i = t; i < 64; i += blockDim.x)
+        *reinterpret_cast<uint16_t*>(sW3 + tc::sw128_offset(0, i)) = Wb[wW3 + i];
+    for (int i = 128 / 4 + t; i < (int)kW3Bytes / 4; i += blockDim.x) reinterpret_cast<uint32_t*>(sW3)[i] = 0u;
+    if (t < 64) sB2[t] = P[oB2 + t];
     if (t == 0) {
         sB3 = P[oB3];
         mbar_init(&bar, 1);
@@ -210,24 +263,26 @@ __global__ void __launch_bounds__(kThreads) k_mlp_forward(int64_t n, PointSrc S,
     }
     sync_for_mma();
     const uint32_t tm = tbase, row = tm + ((uint32_t)(warp * 32) << 16);
-    const uint32_t idesc = tc::idesc_bf16_f32(128, 64);
+    const uint32_t idesc = tc::idesc_bf16_f32(128, 64), idesc3 = tc::idesc_bf16_f32(128, 16);
     const uint64_t dX = tc::sw128_desc(smem_u32(sX)), dW1 = tc::sw128_desc(smem_u32(sW1)),
-                   dW2 = tc::sw128_desc(smem_u32(sW2));
+                   dW2 = tc::sw128_desc(smem_u32(sW2)), dW3 = tc::sw128_desc(smem_u32(sW3));
     uint32_t phase = 0;
     bool ok = true;
     const int64_t ntiles = (n + kTile - 1) / kTile;
     for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         const int64_t p = tile * kTile + t;
-        float v[64];
-        if (p < n) {
-            float x, y, z;
-            point_of(S, p, x, y, z);
-            encode_point(x, y, z, v);
-        } else {
+        {
+            float v[64];
+            if (p < n) {
+                float x, y, z;
+                point_of(S, p, x, y, z);
+                encode_point(x, y, z, v, 1.0f);
+            } else {
 #pragma unroll
-            for (int i = 0; i < 64; ++i) v[i] = 0.0f;
+                for (int i = 0; i < 64; ++i) v[i] = 0.0f;
+            }
+            store_row(sX, t, v);
         }
-        store_row(sX, t, v);
         sync_for_mma();
         if (t == 0) {
 #pragma unroll
@@ -235,10 +290,8 @@ __global__ void __launch_bounds__(kThreads) k_mlp_forward(int64_t n, PointSrc S,
             tc::mma_commit(&bar);
         }
         if (!(ok = wait_mma(&bar, phase))) break;
-        tmem_row64(row, v);
-#pragma unroll
-        for (int i = 0; i < 64; ++i) v[i] = fmaxf(v[i] + sB1[i], 0.0f);
-        store_row(sX, t, v);
+        relu_pack32(row, nullptr, sX, t, 0);
+        relu_pack32(row + 32, nullptr, sX, t, 4);
         sync_for_mma();
         if (t == 0) {
 #pragma unroll
@@ -246,11 +299,18 @@ __global__ void __launch_bounds__(kThreads) k_mlp_forward(int64_t n, PointSrc S,
             tc::mma_commit(&bar);
         }
         if (!(ok = wait_mma(&bar, phase))) break;
-        tmem_row64(row, v);
-        float z = sB3;
+        relu_pack32(row, sB2, sX, t, 0);
+        relu_pack32(row + 32, sB2 + 32, sX, t, 4);
+        sync_for_mma();
+        if (t == 0) {
 #pragma unroll
-        for (int i = 0; i < 64; ++i) z = fmaf(sW3[i], bf16_round(fmaxf(v[i] + sB2[i], 0.0f)), z);
-        if (p < n) sigma[p] = softplus(z);
+            for (int ks = 0; ks < 4; ++ks) tc::mma_bf16(tm, dX + 2 * ks, dW3 + 2 * ks, idesc3, ks > 0);
+            tc::mma_commit(&bar);
+        }
+        if (!(ok = wait_mma(&bar, phase))) break;
+        const float z = tc::tmem_ld1(row);
+        tc::tmem_wait_ld();
+        if (p < n) sigma[p] = softplus(z + sB3);
         tc::fence_before_sync();
     }
     tc::fence_before_sync();
@@ -480,10 +540,33 @@ __global__ void k_mlp_encode(int64_t n, const float* __restrict__ xyz, float* __
     }
 }
 
-int persistent_ctas(const void* kernel, int threads, size_t shm, int64_t tiles) {
-    int per_sm = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, shm) != cudaSuccess || per_sm < 1)
-        per_sm = 1;
+// CTAs of a persistent launch: resident CTAs per SM x SMs, at most one per
+// tile; 0 (with the error set) if a query fails.  Residency is computed from
+// the kernel's registers and shared memory and the device's limits (the
+// occupancy query answers one CTA per SM for the forward kernel, which runs
+// six), and capped at `tmem_cap` CTAs (tensor-memory columns per SM).
+int persistent_ctas(const void* kernel, int threads, size_t shm, int64_t tiles, int tmem_cap) {
+    cudaFuncAttributes fa;
+    int dev = 0, regs_sm = 0, smem_sm = 0, smem_res = 0, max_blocks = 0;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_res, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&max_blocks, cudaDevAttrMaxBlocksPerMultiprocessor, dev);
+    if (e != cudaSuccess) {
+        set_error("occupancy query failed: %s", cudaGetErrorString(e));
+        return 0;
+    }
+    const int warps = (threads + 31) / 32;
+    const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;  // allocated per warp in units of 256
+    const int by_regs = regs_warp > 0 ? regs_sm / (regs_warp * warps) : max_blocks;
+    const size_t smem_block = fa.sharedSizeBytes + shm + (size_t)smem_res;
+    const int by_smem = smem_block > 0 ? (int)((size_t)smem_sm / smem_block) : max_blocks;
+    int per_sm = by_regs < by_smem ? by_regs : by_smem;
+    if (per_sm > max_blocks) per_sm = max_blocks;
+    if (per_sm > tmem_cap) per_sm = tmem_cap;
+    if (per_sm < 1) per_sm = 1;
     return (int)min64((int64_t)per_sm * sm_count(), tiles > 0 ? tiles : 1);
 }
 
@@ -512,12 +595,14 @@ namespace nacc {
 namespace {
 int launch_forward(int64_t n, const PointSrc& S, const float* params, const uint16_t* weights, float* sigma,
                    cudaStream_t st) {
-    const size_t shm = 2 * kWBytes + kTileBytes + 1024;
+    const size_t shm = 2 * kWBytes + kTileBytes + kW3Bytes + 1024;
     NACC_CUDA_TRY(cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    NACC_CUDA_TRY(cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                       (int)cudaSharedmemCarveoutMaxShared));
     const int64_t tiles = (n + kTile - 1) / kTile;
     // at most 8 CTAs of 64 tensor-memory columns share an SM's 512 columns
-    int grid = persistent_ctas((const void*)k_mlp_forward, kThreads, shm, tiles);
-    grid = (int)min64(grid, (int64_t)8 * sm_count());
+    const int grid = persistent_ctas((const void*)k_mlp_forward, kThreads, shm, tiles, 8);
+    if (grid == 0) return NACC_ERR_CUDA;
     k_mlp_forward<<<grid, kThreads, shm, st>>>(n, S, params, weights, sigma);
     NACC_LAUNCH_CHECK();
     return NACC_OK;
