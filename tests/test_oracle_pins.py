@@ -764,3 +764,34 @@ def test_unbounded_march_matches_fp64_geometry(orc):
             assert bool(occ[idx]) == ((r, float(t0s[k])) in got), (r, k)
             checked += 1
     assert checked > 5000
+
+
+def test_unbounded_early_termination_cut(orc):
+    """The unbounded march with the field emits a prefix of its field-less
+    march, cut where the float64 optical depth of the emitted samples first
+    exceeds -ln(1e-4) (Sec. 4.2 filtering on the s-lattice of Sec. 3.2)."""
+    w = workloads.c5_unbounded(n_cams=2, width=32, height=8, res=32)
+    bits, _ = orc.density_grid_contracted(w.grid, w.blobs)
+    g, m = w.grid, w.march
+    K = 512
+    full = orc.march_unbounded(w.rays_o, w.rays_d, g.aabb_min, g.aabb_max, g.res, g.n_levels, bits, K,
+                               m.t_min, m.t_max)
+    cut = orc.march_unbounded(w.rays_o, w.rays_d, g.aabb_min, g.aabb_max, g.res, g.n_levels, bits, K,
+                              m.t_min, m.t_max, blobs=w.blobs, eps=1e-4)
+    thr = -math.log(1e-4)
+    sig, _ = orc.field_samples(w.rays_o, w.rays_d, full["ray_indices"], full["t_starts"], full["t_ends"], w.blobs)
+    tau = sig * (full["t_ends"].astype(np.float64) - full["t_starts"])
+    n_cut = 0
+    for r in range(w.n_rays):
+        fs, fe = full["offsets"][r], full["offsets"][r + 1]
+        cs, ce = cut["offsets"][r], cut["offsets"][r + 1]
+        nc = ce - cs
+        assert nc <= fe - fs
+        np.testing.assert_array_equal(cut["t_starts"][cs:ce], full["t_starts"][fs:fs + nc])
+        P = np.concatenate([[0.0], np.cumsum(tau[fs:fe])])
+        if nc > 0:
+            assert P[nc - 1] <= thr * (1 + 1e-5)
+        if nc < fe - fs:
+            n_cut += 1
+            assert P[nc] > thr * (1 - 1e-5)
+    assert n_cut > 100
