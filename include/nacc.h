@@ -70,6 +70,11 @@ typedef struct nacc_march_params {
 /* Analytic density field used for early termination inside the march (the
  * "density_fn" of Algorithm 1, here a sum of isotropic Gaussian blobs):
  *   sigma(x) = sum_b peak_b * exp(-|x - mu_b|^2 / (2 std_b^2)).
+ * The march evaluates it with fused multiply-adds and the hardware exp2
+ * (relative error a few 1e-6); for fields of at most 16 blobs each ray keeps
+ * only the blobs whose integral along the ray line exceeds 1e-7, so a
+ * dropped blob changes the optical depth by at most 1e-7.  These only move
+ * stops whose depth lies within that of the threshold.
  * rgb is only used by the harness field kernel (nacc_harness.h). */
 typedef struct nacc_blob_field {
     int32_t n_blobs;    /* 0..1024 */

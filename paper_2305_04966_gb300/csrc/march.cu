@@ -216,11 +216,18 @@ __device__ __forceinline__ void sigma_early_stop2(const BlobS* s, int n, const f
 // of the order of that of the position in the direct form.
 constexpr int kRayBlobsMax = 16;
 
-__device__ __forceinline__ void ray_blobs_setup(const BlobS* sb, int n, const float o[3], const float d[3],
-                                                float4* q) {
+// Blobs whose integral along the whole ray line is at most kCullEps
+// (bound peak 2^C sqrt(2 pi) std / |d|, C = c_b p_b^2) are left out of the
+// ray's table: each changes the optical depth by at most kCullEps.
+constexpr float kCullEps = 1e-7f;
+
+__device__ __forceinline__ int ray_blobs_setup(const BlobS* sb, int n, const float o[3], const float d[3],
+                                               float4* q) {
     const int lane = threadIdx.x & 31;
     const float dd = fmaf(d[2], d[2], fmaf(d[1], d[1], d[0] * d[0]));
     const float idd = dd > 0.0f ? 1.0f / dd : 0.0f;
+    const float ilen = dd > 0.0f ? rsqrtf(dd) : 0.0f;
+    int nq = 0;
     for (int b = 0; b < n; ++b) {
         const BlobS v = sb[b];
         const float m0 = v.mx - o[0], m1 = v.my - o[1], m2 = v.mz - o[2];
@@ -236,8 +243,15 @@ __device__ __forceinline__ void ray_blobs_setup(const BlobS* sb, int n, const fl
             ts = 0.0f;
             pp = fmaf(m2, m2, fmaf(m1, m1, m0 * m0));
         }
-        q[b * 32 + lane] = make_float4(v.coef * dd, ts, v.coef * pp, v.peak);
+        const float C = v.coef * pp;
+        if (dd > 0.0f) {
+            const float sd = sqrtf(-0.72134752f / v.coef);  // coef = -log2(e) / (2 std^2)
+            if (!(v.peak * ex2_approx(C) * 2.5066283f * sd * ilen > kCullEps)) continue;
+        }
+        q[nq * 32 + lane] = make_float4(v.coef * dd, ts, C, v.peak);
+        ++nq;
     }
+    return nq;
 }
 
 __device__ __forceinline__ void sigma_ray2(const float4* q, int n, float ta, float tb, float& sa, float& sb) {
@@ -442,8 +456,9 @@ __global__ void __launch_bounds__(kBlockThreads, 32)
     s.done = true;
     s.n = 0;
     s.R.tn = 0.0f;
+    int nq = 0;  // kField 2: blobs in this ray's table
     if (r < A.n && lane_init(A, r, s) && kField == 2)
-        ray_blobs_setup(s_blobs, A.field.n_blobs, s.R.o, s.R.d, s_q);
+        nq = ray_blobs_setup(s_blobs, A.field.n_blobs, s.R.o, s.R.d, s_q);
     RunRec q{runs + (r < A.n ? r : 0) * kRunSlots, 0, -1, -1};
     int* buf = s_buf[threadIdx.x];
     int cnt = 0, kstop = A.max_steps;
@@ -473,7 +488,7 @@ __global__ void __launch_bounds__(kBlockThreads, 32)
                     const float tma = 0.5f * (ta0 + ta1), tmb = 0.5f * (tb0 + tb1);
                     float sga, sgb;
                     if (kField == 2) {
-                        sigma_ray2(s_q, A.field.n_blobs, tma, tmb, sga, sgb);
+                        sigma_ray2(s_q, nq, tma, tmb, sga, sgb);
                     } else {
                         float xa[3], xb[3];
 #pragma unroll

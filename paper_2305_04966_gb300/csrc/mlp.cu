@@ -134,8 +134,11 @@ __device__ __forceinline__ void sync_for_mma() {
     tc::fence_after_sync();
 }
 
+// Thread 0 waits (bounded) for the MMA completion; the others wait at the
+// CTA barrier instead of polling, then order their tensor-memory reads after it.
 __device__ __forceinline__ bool wait_mma(uint64_t* bar, uint32_t& phase) {
-    const bool ok = __syncthreads_and(mbar_wait_bounded(bar, phase & 1u, kWaitNs));
+    const bool mine = threadIdx.x == 0 ? mbar_wait_bounded(bar, phase & 1u, kWaitNs) : true;
+    const bool ok = __syncthreads_and(mine);
     ++phase;
     tc::fence_after_sync();
     return ok;
@@ -161,6 +164,7 @@ struct PointSrc {
     const float* edges;
     int nb;
     int contract;  // rays: feed c(x), the L-infinity contraction of the bin midpoint
+    int p32;       // rays: n_rays * nb < 2^32
 };
 
 __device__ __forceinline__ void point_of(const PointSrc& S, int64_t p, float& x, float& y, float& z) {
@@ -170,8 +174,15 @@ __device__ __forceinline__ void point_of(const PointSrc& S, int64_t p, float& x,
         z = S.xyz[3 * p + 2];
         return;
     }
-    const int64_t r = p / S.nb;
-    const int64_t b = p - r * S.nb;
+    int64_t r, b;
+    if (S.p32) {  // every point index fits 32 bits: the cheaper division
+        const uint32_t q = (uint32_t)p / (uint32_t)S.nb;
+        r = q;
+        b = (uint32_t)p - q * (uint32_t)S.nb;
+    } else {
+        r = p / S.nb;
+        b = p - r * S.nb;
+    }
     const float* e = S.edges + r * (S.nb + 1) + b;
     const float t = 0.5f * (e[0] + e[1]);
     x = fmaf(S.d[3 * r], t, S.o[3 * r]);
@@ -619,7 +630,7 @@ int forward_rays(int64_t n_rays, int32_t n_bins, const float* rays_o, const floa
     NACC_CHECK_ARG(n_bins >= 1 && n_bins <= 4096, "n_bins=%d outside [1, 4096]", n_bins);
     if (n_rays == 0) return NACC_OK;
     NACC_CHECK_ARG(rays_o && rays_d && edges && params && weights && sigma, "a pointer argument is NULL");
-    PointSrc S{nullptr, rays_o, rays_d, edges, n_bins, contract};
+    PointSrc S{nullptr, rays_o, rays_d, edges, n_bins, contract, n_rays * n_bins < (int64_t(1) << 32) ? 1 : 0};
     return launch_forward(n_rays * n_bins, S, params, weights, sigma, as_stream(stream));
 }
 }  // namespace
@@ -643,7 +654,7 @@ extern "C" int nacc_mlp_forward(int64_t n, const float* xyz, const float* params
     NACC_CHECK_ARG(n >= 0 && n < (int64_t(1) << 40), "n=%lld out of range", (long long)n);
     if (n == 0) return NACC_OK;
     NACC_CHECK_ARG(xyz && params && weights && sigma, "a pointer argument is NULL");
-    PointSrc S{xyz, nullptr, nullptr, nullptr, 1, 0};
+    PointSrc S{xyz, nullptr, nullptr, nullptr, 1, 0, 1};
     return launch_forward(n, S, params, weights, sigma, as_stream(stream));
 }
 
