@@ -65,7 +65,28 @@ constexpr int kFieldRayBlobs = 256;  // per-warp shared table limit
 constexpr int kCullAbove = 64;
 constexpr float kCullEps = 1e-7f;
 
-__global__ void __launch_bounds__(kFieldWarps * 32)
+// t0, t1 of positions p..p+3 of the ray's range [s, e) (zero outside it);
+// true if all four lie inside (one 128-bit load per plane).
+__device__ __forceinline__ bool load_t4(const float* __restrict__ t0, const float* __restrict__ t1, long long p,
+                                        long long s, long long e, float ta[4], float tb[4]) {
+    const bool whole = p >= s && p + 4 <= e;
+    if (whole) {
+        const float4 u = __ldcs(reinterpret_cast<const float4*>(t0 + p));
+        const float4 w = __ldcs(reinterpret_cast<const float4*>(t1 + p));
+        ta[0] = u.x, ta[1] = u.y, ta[2] = u.z, ta[3] = u.w;
+        tb[0] = w.x, tb[1] = w.y, tb[2] = w.z, tb[3] = w.w;
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const bool in = p + j >= s && p + j < e;
+            ta[j] = in ? t0[p + j] : 0.0f;
+            tb[j] = in ? t1[p + j] : 0.0f;
+        }
+    }
+    return whole;
+}
+
+__global__ void __launch_bounds__(kFieldWarps * 32, 4)
     k_field_rays(const float* __restrict__ o, const float* __restrict__ d, int64_t n_rays,
                  const int64_t* __restrict__ off, const float* __restrict__ t0, const float* __restrict__ t1,
                  nacc_blob_field f, float* __restrict__ sig, float* __restrict__ rgb) {
@@ -81,6 +102,11 @@ __global__ void __launch_bounds__(kFieldWarps * 32)
     for (int64_t r = (int64_t)blockIdx.x * kFieldWarps + wid; r < n_rays; r += warps) {
         const long long s = off[r], e = off[r + 1];
         if (e <= s) continue;
+        // the first chunk's loads are in flight during the table set-up; each
+        // chunk's compute overlaps the next chunk's loads
+        long long p = (s & ~3ll) + 4 * lane;
+        float ta[4], tb[4];
+        bool whole = p < e ? load_t4(t0, t1, p, s, e, ta, tb) : false;
         const float ox = __ldg(o + 3 * r), oy = __ldg(o + 3 * r + 1), oz = __ldg(o + 3 * r + 2);
         const float dx = __ldg(d + 3 * r), dy = __ldg(d + 3 * r + 1), dz = __ldg(d + 3 * r + 2);
         const float dd = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
@@ -119,26 +145,12 @@ __global__ void __launch_bounds__(kFieldWarps * 32)
             nt += __popc(bal);
         }
         __syncwarp();
-        const long long a = s & ~3ll;
-        for (long long p = a + 4 * lane; p < e; p += 128) {
-            const bool whole = p >= s && p + 4 <= e;
-            float ta[4], tb[4];
-            if (whole) {
-                const float4 u = __ldcs(reinterpret_cast<const float4*>(t0 + p));
-                const float4 w = __ldcs(reinterpret_cast<const float4*>(t1 + p));
-                ta[0] = u.x, ta[1] = u.y, ta[2] = u.z, ta[3] = u.w;
-                tb[0] = w.x, tb[1] = w.y, tb[2] = w.z, tb[3] = w.w;
-            } else {
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const bool in = p + j >= s && p + j < e;
-                    ta[j] = in ? t0[p + j] : 0.0f;
-                    tb[j] = in ? t1[p + j] : 0.0f;
-                }
-            }
+        for (; p < e; p += 128) {
             float tm[4], sg[4] = {0.0f, 0.0f, 0.0f, 0.0f}, c[12] = {};
 #pragma unroll
             for (int j = 0; j < 4; ++j) tm[j] = 0.5f * (ta[j] + tb[j]);
+            const bool cur_whole = whole;
+            if (p + 128 < e) whole = load_t4(t0, t1, p + 128, s, e, ta, tb);
             for (int i = 0; i < nt; ++i) {
                 const float4 v = q[i];
                 const BlobS& w = sb[__float_as_int(v.w)];
@@ -159,7 +171,7 @@ __global__ void __launch_bounds__(kFieldWarps * 32)
                 c[3 * j + 1] *= inv;
                 c[3 * j + 2] *= inv;
             }
-            if (whole) {
+            if (cur_whole) {
                 __stcs(reinterpret_cast<float4*>(sig + p), make_float4(sg[0], sg[1], sg[2], sg[3]));
                 float4* q4 = reinterpret_cast<float4*>(rgb + 3 * p);
                 __stcs(q4, make_float4(c[0], c[1], c[2], c[3]));
