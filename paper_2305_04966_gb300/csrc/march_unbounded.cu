@@ -156,13 +156,24 @@ __device__ __forceinline__ void rec_flush(RunRec& q) {
     }
 }
 
+// Per-blob constants of the early-stop table, staged once per block:
+// {mu_x, mu_y, mu_z, c} with c = -log2(e) / (2 std^2), and {log2 peak,
+// sqrt(2 pi) std} (peak <= 0: log2 peak = -inf, never kept).
+constexpr int kStageBlobs = 256;  // blobs staged in shared memory; more are read from global memory
+
+__device__ __forceinline__ void blob_consts(const nacc_blob_field& f, int b, float4& m, float2& k) {
+    const float sd = __ldg(f.std + b), pk = __ldg(f.peak + b);
+    m = make_float4(__ldg(f.mu + 3 * b), __ldg(f.mu + 3 * b + 1), __ldg(f.mu + 3 * b + 2), -0.72134752f / (sd * sd));
+    k = make_float2(pk > 0.0f ? __log2f(pk) : -INFINITY, 2.5066283f * sd);
+}
+
 // The early-stop table of one ray, built by its warp: the blobs whose
 // integral along the whole ray line exceeds kCullEps (bound peak 2^C
 // sqrt(2 pi) sd / |d|), as {A_b, t*_b, C_b + log2 peak_b} (log2-scaled:
 // density peak_b 2^(A_b (t - t*_b)^2 + C_b)), in blob order.  Returns the
 // count, or -1 if more than kStopTable blobs qualify.
-__device__ int build_warp_table(const nacc_blob_field& f, const float o[3], const float d[3], float4* tab,
-                                int lane) {
+__device__ int build_warp_table(const nacc_blob_field& f, const float4* sm, const float2* sk, const float o[3],
+                                const float d[3], float4* tab, int lane) {
     const float dd = fmaf(d[2], d[2], fmaf(d[1], d[1], d[0] * d[0]));
     const float idd = dd > 0.0f ? 1.0f / dd : 0.0f;
     const float ilen = dd > 0.0f ? rsqrtf(dd) : 0.0f;
@@ -172,27 +183,29 @@ __device__ int build_warp_table(const nacc_blob_field& f, const float o[3], cons
         bool keep = false;
         float4 ent = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         if (b < f.n_blobs) {
-            const float pk = __ldg(f.peak + b);
-            if (pk > 0.0f) {
-                const float sd = __ldg(f.std + b);
-                const float m0 = __ldg(f.mu + 3 * b) - o[0], m1 = __ldg(f.mu + 3 * b + 1) - o[1],
-                            m2 = __ldg(f.mu + 3 * b + 2) - o[2];
-                const float coef2 = -0.72134752f / (sd * sd);  // -log2(e) / 2
-                float ts, pp;
-                if (dd > 0.0f) {
-                    const float cx = fmaf(m1, d[2], -m2 * d[1]), cy = fmaf(m2, d[0], -m0 * d[2]),
-                                cz = fmaf(m0, d[1], -m1 * d[0]);
-                    ts = fmaf(m2, d[2], fmaf(m1, d[1], m0 * d[0])) * idd;
-                    pp = fmaf(cz, cz, fmaf(cy, cy, cx * cx)) * idd;
-                } else {
-                    ts = 0.0f;
-                    pp = fmaf(m2, m2, fmaf(m1, m1, m0 * m0));
-                }
-                const float C = fmaf(coef2, pp, __log2f(pk));
-                const float bound = dd > 0.0f ? ex2_approx(C) * 2.5066283f * sd * ilen : ex2_approx(C) * 1e30f;
-                keep = bound > kCullEps;
-                ent = make_float4(coef2 * dd, ts, C, 0.0f);
+            float4 mc;
+            float2 kc;
+            if (b < kStageBlobs) {
+                mc = sm[b];
+                kc = sk[b];
+            } else {
+                blob_consts(f, b, mc, kc);
             }
+            const float m0 = mc.x - o[0], m1 = mc.y - o[1], m2 = mc.z - o[2];
+            float ts, pp;
+            if (dd > 0.0f) {
+                const float cx = fmaf(m1, d[2], -m2 * d[1]), cy = fmaf(m2, d[0], -m0 * d[2]),
+                            cz = fmaf(m0, d[1], -m1 * d[0]);
+                ts = fmaf(m2, d[2], fmaf(m1, d[1], m0 * d[0])) * idd;
+                pp = fmaf(cz, cz, fmaf(cy, cy, cx * cx)) * idd;
+            } else {
+                ts = 0.0f;
+                pp = fmaf(m2, m2, fmaf(m1, m1, m0 * m0));
+            }
+            const float C = fmaf(mc.w, pp, kc.x);
+            const float bound = dd > 0.0f ? ex2_approx(C) * kc.y * ilen : ex2_approx(C) * 1e30f;
+            keep = bound > kCullEps;
+            ent = make_float4(mc.w * dd, ts, C, 0.0f);
         }
         const unsigned bal = __ballot_sync(0xffffffffu, keep);
         const int pos = n + __popc(bal & ((1u << lane) - 1u));
@@ -279,9 +292,13 @@ __global__ void __launch_bounds__(kThreads) k_unb_stop(UArgs A, int32_t* __restr
                                                        const int2* __restrict__ runs,
                                                        long long* __restrict__ block_sums) {
     __shared__ float4 s_tab[kWarps][kStopTable];
+    __shared__ float4 s_bm[kStageBlobs];
+    __shared__ float2 s_bk[kStageBlobs];
     __shared__ int s_w[kWarps];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     float4* tab = s_tab[wid];
+    for (int b = tid; b < min(A.field.n_blobs, kStageBlobs); b += kThreads) blob_consts(A.field, b, s_bm[b], s_bk[b]);
+    __syncthreads();
     const int64_t rbase = (int64_t)blockIdx.x * kThreads + wid * 32;
     int wsum = 0;
     for (int i = 0; i < 32; ++i) {
@@ -291,7 +308,7 @@ __global__ void __launch_bounds__(kThreads) k_unb_stop(UArgs A, int32_t* __restr
         if (cnt == 0) continue;
         const float o[3] = {A.o[3 * r], A.o[3 * r + 1], A.o[3 * r + 2]};
         const float d[3] = {A.d[3 * r], A.d[3 * r + 1], A.d[3 * r + 2]};
-        const int nt = build_warp_table(A.field, o, d, tab, lane);
+        const int nt = build_warp_table(A.field, s_bm, s_bk, o, d, tab, lane);
         __syncwarp();
         const int nr = nruns[r];
         int cut = cnt, kstop = A.K;
