@@ -69,8 +69,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-aux", action="store_true", help="skip the grid-update / sample_pdf timings")
-    ap.add_argument("--aux-legs", default="update,proposal,unbounded",
-                    help="comma list of auxiliary legs: update (grid update / sample_pdf timings), proposal "
+    ap.add_argument("--aux-legs", default="update,step,proposal,unbounded",
+                    help="comma list of auxiliary legs: update (grid update / sample_pdf timings), step (the "
+                         "training batch's whole step incl. the grid update as one CUDA graph), proposal "
                          "(learned and combined estimators), unbounded (grid vs proposal on unbounded scenes)")
     ap.add_argument("--unbounded-cams", type=int, default=16,
                     help="cameras of the unbounded-scene leg (16 = the 4,194,304-ray workload)")
@@ -188,49 +189,166 @@ class ClockSampler:
 
 class OraclePipeline:
     """The oracle's march (FP32, early stop) + FP64 field + FP64 compositing +
-    L2 gradient + FP64 adjoint on a subset of the workload's rays."""
+    L2 gradient + FP64 adjoint on a subset of the workload's rays; per-stage
+    wall times of the last run in ``stage_s``."""
 
-    def __init__(self, w):
+    def __init__(self, w, threads=None, unbounded=False):
         import oracle
         self.orc = oracle
         self.w = w
-        self.bits, _ = oracle.density_grid(w.grid, w.blobs)
-        self.threads = oracle.max_threads()
+        self.unbounded = unbounded
+        if unbounded:
+            self.bits, _ = oracle.density_grid_contracted(w.grid, w.blobs)
+        else:
+            self.bits, _ = oracle.density_grid(w.grid, w.blobs)
+        self.threads = oracle.max_threads() if threads is None else int(threads)
+        self.stage_s = {}
 
     def run(self, sel):
-        orc, w = self.orc, self.w
+        orc, w, nt = self.orc, self.w, self.threads
         g, m = w.grid, w.march
         o, d = np.ascontiguousarray(w.rays_o[sel]), np.ascontiguousarray(w.rays_d[sel])
-        ex = orc.march(o, d, g.aabb_min, g.aabb_max, g.res, g.n_levels, self.bits, m.step, m.max_steps,
-                       m.t_min, m.t_max, blobs=w.blobs, eps=m.early_stop_eps)
-        sig, rgb = orc.field_samples(o, d, ex["ray_indices"], ex["t_starts"], ex["t_ends"], w.blobs)
-        out = orc.render_fwd(ex["offsets"], ex["t_starts"], ex["t_ends"], sig, rgb, bg=w.bg)
+        t = [time.perf_counter()]
+        if self.unbounded:
+            ex = orc.march_unbounded(o, d, g.aabb_min, g.aabb_max, g.res, g.n_levels, self.bits, m.max_steps,
+                                     m.t_min, m.t_max, blobs=w.blobs, eps=m.early_stop_eps, n_threads=nt)
+        else:
+            ex = orc.march(o, d, g.aabb_min, g.aabb_max, g.res, g.n_levels, self.bits, m.step, m.max_steps,
+                           m.t_min, m.t_max, blobs=w.blobs, eps=m.early_stop_eps, n_threads=nt)
+        t.append(time.perf_counter())
+        sig, rgb = orc.field_samples(o, d, ex["ray_indices"], ex["t_starts"], ex["t_ends"], w.blobs, n_threads=nt)
+        t.append(time.perf_counter())
+        out = orc.render_fwd(ex["offsets"], ex["t_starts"], ex["t_ends"], sig, rgb, bg=w.bg, n_threads=nt)
+        t.append(time.perf_counter())
         n = len(sel)
         g_rgb = 2.0 * (out["rgb"] - w.target[sel]) / (3 * n)
         orc.render_bwd(ex["offsets"], ex["t_starts"], ex["t_ends"], sig, rgb, g_rgb, np.zeros(n),
-                       np.zeros(n), bg=w.bg)
+                       np.zeros(n), bg=w.bg, n_threads=nt)
+        t.append(time.perf_counter())
+        self.stage_s = dict(zip(("march", "field", "render_fwd", "render_bwd"), np.diff(t).tolist()))
         return int(ex["offsets"][-1])
 
 
-def cpu_baseline(w, target_seconds=10.0):
-    """Oracle rays/s on a bounded, evenly strided sample of the workload's rays."""
-    pipe = OraclePipeline(w)
-    n = w.n_rays
+def _timed_sample(pipe, n, target_seconds):
+    """Strided sample of the n rays sized for ~target_seconds of oracle work."""
     probe = np.arange(0, n, 256)
     t0 = time.perf_counter()
     pipe.run(probe)
-    dt = max(time.perf_counter() - t0, 1e-3)
-    per_ray = dt / len(probe)
+    per_ray = max(time.perf_counter() - t0, 1e-3) / len(probe)
     k = int(min(n, max(len(probe), target_seconds / per_ray)))
     stride = max(1, n // k)
     sel = np.arange(0, n, stride)
     t0 = time.perf_counter()
     S = pipe.run(sel)
-    dt = time.perf_counter() - t0
+    return sel, stride, S, time.perf_counter() - t0
+
+
+def cpu_baseline(w, target_seconds=10.0):
+    """Oracle rays/s on a bounded, evenly strided sample of the workload's
+    rays, on all host cores and (a smaller sample) on one core, with the
+    per-stage split of the all-core run."""
+    pipe = OraclePipeline(w)
+    n = w.n_rays
+    sel, stride, S, dt = _timed_sample(pipe, n, target_seconds)
+    stages = {k: v for k, v in pipe.stage_s.items()}
+    one = OraclePipeline(w, threads=1)
+    sel1, stride1, S1, dt1 = _timed_sample(one, n, target_seconds / 4)
     return {"value": len(sel) / dt, "unit": "rays/s", "cores": pipe.threads, "kind": "oracle",
             "sample": f"every {stride}th ray of the {n}-ray image ({len(sel)} rays, {S} samples), "
                       f"march+field+fwd+loss+bwd, {dt:.1f} s",
-            "samples_per_s": S / dt}
+            "samples_per_s": S / dt,
+            "stage_s": stages,
+            "single_core": {"value": len(sel1) / dt1, "unit": "rays/s", "cores": 1,
+                            "sample": f"every {stride1}th ray ({len(sel1)} rays, {S1} samples), {dt1:.1f} s",
+                            "stage_s": one.stage_s}}
+
+
+def cpu_baseline_unbounded(n_cams=16, target_seconds=5.0, res=64):
+    """The oracle on a strided ray subset of the unbounded-scene workload,
+    reported per ray and labelled as a subset.  Its grid is built by the
+    oracle itself at 4 x res^3 (the workload's 4 x 256^3 grid would take the
+    host minutes to evaluate); the march's cost is the K lattice points per
+    ray either way."""
+    w = workloads.c5_unbounded(n_cams=n_cams, res=res)
+    pipe = OraclePipeline(w, unbounded=True)
+    sel, stride, S, dt = _timed_sample(pipe, w.n_rays, target_seconds)
+    return {"value": len(sel) / dt, "unit": "rays/s", "cores": pipe.threads, "kind": "oracle",
+            "sample": f"subset: every {stride}th ray of the {w.n_rays}-ray workload ({len(sel)} rays, {S} samples), "
+                      f"grid 4x{res}^3, unbounded march (K = {w.march.max_steps}) + field + fwd + loss + bwd, "
+                      f"{dt:.1f} s",
+            "stage_s": pipe.stage_s}
+
+
+def training_step_measure(torch, nacc, dev, flush, steps=10):
+    """The training batch's whole step -- march (early stop) -> field ->
+    render_fwd -> L2 -> render_bwd -> grid points -> field at the points ->
+    grid update (EMA, threshold, bits) -- captured as one CUDA graph and
+    replayed; eager launches timed beside it.  262,144 rays, 64 blobs,
+    4 x 128^3 grid."""
+    w = workloads.c3_training()
+    g, m = w.grid, w.march
+    n = w.n_rays
+    field = nacc.BlobField.from_numpy(w.blobs, dev)
+    grid = nacc.OccupancyGrid.empty(g.aabb_min, g.aabb_max, g.res, g.n_levels, dev)
+    nacc.density_grid(grid, field, 0.01)
+    o = torch.as_tensor(w.rays_o).to(dev)
+    d = torch.as_tensor(w.rays_d).to(dev)
+    tgt = torch.as_tensor(w.target).to(dev)
+    cap = n * m.max_steps
+    bufs = nacc.MarchBuffers(n, cap, dev)
+    ubufs = nacc.UpdateBuffers(grid.n_cells, dev)
+    sig = torch.empty(cap, device=dev)
+    rgbs = torch.empty((cap, 3), device=dev)
+    gsg = torch.empty(cap, device=dev)
+    gcc = torch.empty((cap, 3), device=dev)
+    pts = torch.empty((grid.n_cells, 3), device=dev)
+    dens = torch.empty(grid.n_cells, device=dev)
+
+    def step():
+        pk = nacc.march_grid(grid, o, d, m.step, m.max_steps, m.t_min, m.t_max, m.early_stop_eps, field=field,
+                             buffers=bufs)
+        nacc.field_eval(field, o, d, pk, out=(sig, rgbs))
+        rgb, _, _, _, _ = nacc.render_fwd(pk.offsets, pk.t_starts, pk.t_ends, sig, rgbs, w.bg, 0.0)
+        loss, g_rgb = nacc.l2_loss(rgb, tgt)
+        nacc.render_bwd(pk.offsets, pk.t_starts, pk.t_ends, sig, rgbs, g_rgb, None, None, w.bg, 0.0, out=(gsg, gcc))
+        nacc.grid_points(grid, seed=7, step=1, jitter=True, out=pts)
+        nacc.field_points(field, pts, out=dens)
+        nacc.update_grid(grid, dens, 0.95, 0.01, buffers=ubufs)
+        return loss
+
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        tot = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            tot += a.elapsed_time(b)
+        return tot / steps
+
+    eager_ms = timed(step)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        step()
+    torch.cuda.current_stream().wait_stream(s)
+    gph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gph):
+        step()
+    graph_ms = timed(gph.replay)
+    S = bufs.packed.n_samples()
+    out = {"workload": w.name, "n_rays": n, "samples": S, "cells": grid.n_cells,
+           "kernels_per_step": KERNELS_PER_STEP["march"] + 4 + 5,
+           "graph": {"ms": graph_ms, "rays/s": n / (graph_ms / 1e3), "samples/s": S / (graph_ms / 1e3)},
+           "eager": {"ms": eager_ms, "rays/s": n / (eager_ms / 1e3)}}
+    del gph, bufs, sig, rgbs, gsg, gcc, pts, dens
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_reference(args):
@@ -803,6 +921,8 @@ def run_ours(args):
     if rank == 0 and not args.no_aux:
         legs = set(filter(None, args.aux_legs.split(",")))
         aux = aux_measure(torch, nacc, dev, flush, hbm) if "update" in legs else {}
+        if "step" in legs:
+            aux["training_step"] = training_step_measure(torch, nacc, dev, flush)
         if "proposal" in legs:
             aux["proposal"] = proposal_measure(torch, nacc, dev, flush)
             if args.no_cpu_baseline:
@@ -816,6 +936,7 @@ def run_ours(args):
                 aux["unbounded"].pop("_T")
             else:
                 unbounded_exact_error(aux["unbounded"])
+                aux["unbounded"]["cpu_baseline"] = cpu_baseline_unbounded(args.unbounded_cams)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
