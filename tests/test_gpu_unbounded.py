@@ -348,3 +348,49 @@ def test_field_eval_culled_256_blobs(nacc, orc, small_c5):
     ok = s64 > 1.0
     assert ok.sum() > 1000
     np.testing.assert_allclose(rgb[ok], c64[ok], rtol=1e-3, atol=1e-4)
+
+
+def _gather_rays(pk, rays):
+    """Samples of the given rays of a device-resident packed set, copied out
+    ray by ray (the full set is too large to copy)."""
+    off = pk.offsets.cpu().numpy()
+    idx = np.concatenate([np.arange(off[r], off[r + 1]) for r in rays]).astype(np.int64)
+    it = torch.as_tensor(idx, device=DEV)
+    cnt = np.array([off[r + 1] - off[r] for r in rays], np.int64)
+    return dict(offsets=np.concatenate([[0], np.cumsum(cnt)]), t_starts=pk.t_starts[it].cpu().numpy(),
+                t_ends=pk.t_ends[it].cpu().numpy(), ray_indices=pk.ray_indices[it].cpu().numpy())
+
+
+def test_unbounded_full_size_sampled(nacc, orc):
+    """The 4,194,304-ray workload on a full 4 x 256^3 grid over the contracted
+    space (seeded block-structured bits: building the field's grid on the CPU
+    would take minutes), marched whole on the GPU as the bench launches it;
+    3,000 strided rays compared with the oracle: bit-exact without a field;
+    with the 256-blob field, bit-exact outside ties."""
+    w = workloads.c5_unbounded()
+    g, m = w.grid, w.march
+    bits = workloads.random_bitfield(g.n_levels, g.res, 505, p_block=0.15, block=8, p_cell=0.7)
+    grid = _grid(nacc, g, bits)
+    o, d = _T(w.rays_o), _T(w.rays_d)
+    sel = np.linspace(0, w.n_rays - 1, 3000).astype(np.int64)
+    sub = workloads.dataclasses.replace(w, rays_o=np.ascontiguousarray(w.rays_o[sel]),
+                                        rays_d=np.ascontiguousarray(w.rays_d[sel]),
+                                        target=None)
+    full = _oracle(orc, sub, bits, m.max_steps)
+    for field in (None, nacc.BlobField.from_numpy(w.blobs)):
+        pk = nacc.march_unbounded(grid, o, d, m.max_steps, m.t_min, m.t_max, m.early_stop_eps, field=field)
+        torch.cuda.synchronize()
+        got = _gather_rays(pk, sel)
+        got["ray_indices"] = np.repeat(np.arange(len(sel), dtype=np.int32), np.diff(got["offsets"]))
+        if field is None:
+            assert pk.n_samples() > 50 * w.n_rays
+            _equal(got, full)
+            continue
+        exp = _oracle(orc, sub, bits, m.max_steps, blobs=w.blobs)
+        ties = _near_tie_rays(orc, sub, full, -math.log(m.early_stop_eps))
+        assert len(ties) < 0.02 * len(sel)
+        _equal(got, exp, [r for r in range(len(sel)) if r not in ties])
+        gc, ec = np.diff(got["offsets"]), np.diff(exp["offsets"])
+        assert all(abs(int(gc[r]) - int(ec[r])) <= 1 for r in ties)
+        del pk
+        torch.cuda.empty_cache()
