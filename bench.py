@@ -572,7 +572,39 @@ def proposal_measure(torch, nacc, dev, flush, steps=5, train_steps=1024, batch=6
     prop_ms, T_prop = timed(prop_path)
     comb_ms, T_comb = timed(comb_path)
     sel = np.linspace(0, n - 1, sample_rays).astype(np.int64)
+
+    # equal-error sweep: the grid path on coarser lattices (step x mult over the
+    # same distance), the proposal path with more bins
+    sweep_T = {}
+    grid_sweep, prop_sweep = [], []
+    for mult in (1, 2, 4, 8, 16, 32):
+        st, ks = m.step * mult, (m.max_steps + mult - 1) // mult
+
+        def gp():
+            pk = nacc.march_grid(grid, o, d, st, ks, m.t_min, m.t_max, m.early_stop_eps, field=field, buffers=bufs)
+            nacc.field_eval(field, o, d, pk, out=(fs, fc))
+            return nacc.render_fwd(pk.offsets, pk.t_starts, pk.t_ends, fs, fc, bg, 0.0)[3]
+
+        ms_, T_ = timed(gp)
+        grid_sweep.append({"step": st, "max_steps": ks, "samples": bufs.packed.n_samples(), "ms": ms_,
+                           "rays/s": n / (ms_ / 1e3)})
+        sweep_T[f"grid step x{mult}"] = T_.cpu().numpy()[sel]
+    for rounds, nf in (((64, 32), 32), ((128, 64), 64), ((256, 128), 128)):
+        smp = nacc.ProposalSampler(mlp, box, n, rounds=rounds, n_final=nf, device=dev)
+        ps2 = torch.empty(n * nf, device=dev)
+        pc2 = torch.empty((n * nf, 3), device=dev)
+
+        def pp():
+            pk = smp.sample(o, d, m.t_min, m.t_max)
+            nacc.field_eval(field, o, d, pk, out=(ps2, pc2))
+            return nacc.render_fwd(pk.offsets, pk.t_starts, pk.t_ends, ps2, pc2, bg, 0.0)[3]
+
+        ms_, T_ = timed(pp)
+        prop_sweep.append({"rounds": list(rounds), "final_samples_per_ray": nf, "ms": ms_, "rays/s": n / (ms_ / 1e3)})
+        sweep_T[f"proposal {list(rounds)}->{nf}"] = T_.cpu().numpy()[sel]
+        del smp, ps2, pc2
     return {
+        "grid_sweep": grid_sweep, "proposal_sweep": prop_sweep,
         "workload": w.name, "n_rays": n,
         "grid_path": {"rays/s": n / (grid_ms / 1e3), "ms": grid_ms, "samples": bufs.packed.n_samples(),
                       "early_stop_eps": m.early_stop_eps},
@@ -588,7 +620,7 @@ def proposal_measure(torch, nacc, dev, flush, steps=5, train_steps=1024, batch=6
         "T_abs_diff_proposal_vs_grid": {"mean": float((T_prop - T_grid).abs().mean()),
                                         "p99": float((T_prop - T_grid).abs().quantile(0.99))},
         "_sample": {"rays": sel, "T_grid": T_grid.cpu().numpy()[sel], "T_prop": T_prop.cpu().numpy()[sel],
-                    "T_comb": T_comb.cpu().numpy()[sel], "w": w},
+                    "T_comb": T_comb.cpu().numpy()[sel], "w": w, "sweep": sweep_T},
     }
 
 
@@ -614,6 +646,32 @@ def proposal_exact_error(prop):
         out[name + "_p99"] = float(np.quantile(err, 0.99))
         out[name + "_range"] = "outermost cascade box" if levels > 1 else "scene box (level 0)"
     prop["T_error_vs_exact"] = out
+    # the sweep, each path against the exact depth over its own range
+    Tex = {}
+    for levels in (1, w.grid.n_levels):
+        tn, tf, hit = oracle.ray_clip(o, d, w.grid.aabb_min, w.grid.aabb_max, w.grid.res, levels, w.march.t_min,
+                                      w.march.t_max)
+        Tex[levels] = np.exp(-P.exact_optical_depth(o, d, tn.astype(np.float64),
+                                                    np.where(hit, tf, tn).astype(np.float64), w.blobs.mu,
+                                                    w.blobs.std, w.blobs.peak))
+    mults = (1, 2, 4, 8, 16, 32)
+    for row, mult in zip(prop["grid_sweep"], mults):
+        e = np.abs(s["sweep"][f"grid step x{mult}"] - Tex[w.grid.n_levels])
+        row["T_mean_abs_err"], row["T_p99_abs_err"] = float(e.mean()), float(np.quantile(e, 0.99))
+    for row in prop["proposal_sweep"]:
+        e = np.abs(s["sweep"][f"proposal {row['rounds']}->{row['final_samples_per_ray']}"] - Tex[1])
+        row["T_mean_abs_err"], row["T_p99_abs_err"] = float(e.mean()), float(np.quantile(e, 0.99))
+    # at each proposal configuration's error: the fastest grid configuration
+    # that is at least as accurate
+    eq = []
+    for row in prop["proposal_sweep"]:
+        ok = [g for g in prop["grid_sweep"] if g["T_mean_abs_err"] <= row["T_mean_abs_err"]]
+        best = max(ok, key=lambda g: g["rays/s"]) if ok else None
+        eq.append({"proposal": {"rounds": row["rounds"], "final": row["final_samples_per_ray"],
+                                "rays/s": row["rays/s"], "T_mean_abs_err": row["T_mean_abs_err"]},
+                   "grid": None if best is None else {"step": best["step"], "rays/s": best["rays/s"],
+                                                      "T_mean_abs_err": best["T_mean_abs_err"]}})
+    prop["equal_error"] = eq
 
 
 def unbounded_measure(torch, nacc, dev, flush, n_cams=16, steps=3, grid_K=(512, 1024, 2048),
