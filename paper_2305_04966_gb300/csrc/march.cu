@@ -23,9 +23,10 @@
 //     exit: k < floor(q + 1/2 - slack) with q = (t_exit - t_near)/dt and a
 //     slack of 1/64 step plus 2^-16 (|q| + |t_near|/dt) for the rounding of
 //     t0, t1, the midpoint and q (at least 16x their bound).
-// A cell inside an empty (or a fully occupied) 8^3 block of cells (per-call
-// summaries of the bits) runs to the block's exit: the same argument holds
-// for any box of cells whose bits all agree.
+// A cell inside an empty (or a fully occupied) block of cells runs to the
+// block's exit -- its 16^3 block if that is uniform, else its 4^3 block if
+// that is (per-call summaries of the bits): the same argument holds for any
+// box of cells whose bits all agree.
 // Empty runs are skipped; occupied runs are emitted point by point with only
 // their t0 / t1 arithmetic (plus the field for early termination), so the
 // emitted set equals the dense march's at a fraction of its cost.  With a
@@ -44,8 +45,11 @@ constexpr int kRaysPerBlock = kBlockThreads;    // rays per block-sum entry
 constexpr int kWarpsPerBlock = kBlockThreads / 32;
 constexpr int kBuf = 32;                        // lattice indices buffered per lane
 constexpr int kRunSlots = 16;                   // recorded lattice runs per ray
-constexpr int kBlk = 8;                         // cells per edge of an empty-block summary entry
-constexpr size_t kBlockBitsBytes = size_t(NACC_MAX_LEVELS) * (1024 / kBlk) * (1024 / kBlk) * (1024 / kBlk) / 8;
+constexpr int kLogC = 4, kLogF = 2;             // block summaries: coarse 16^3 and fine 4^3 cells
+constexpr size_t summary_bytes(int log) {       // one any- or all-bitfield, 8 levels of 1024^3 cells
+    return size_t(NACC_MAX_LEVELS) * (size_t(1024) >> log) * (size_t(1024) >> log) * (size_t(1024) >> log) / 8;
+}
+constexpr size_t kBlockBitsBytes = 2 * summary_bytes(kLogC) + 2 * summary_bytes(kLogF);
 constexpr float kSkipMargin = 1.0f / 256.0f;    // cells
 
 struct MarchArgs {
@@ -60,9 +64,12 @@ struct MarchArgs {
     float inv_step;  // 1/step, only for the conservative skip (never for lattice values)
     int idx32;       // every flat cell index fits 32 bits
     float skip_lim[NACC_MAX_LEVELS];  // skip allowed at level l iff max|o| <= skip_lim[l]
-    const uint32_t* blk;   // block summary: bit set iff any cell of the kBlk^3 block is occupied
-    const uint32_t* blkf;  // block summary: bit set iff every cell of the block is occupied
-    int nb;               // blocks per axis, ceil(res / kBlk)
+    // block summaries (NULL: none): bit set iff any (all) cells of the block are occupied
+    const uint32_t* c_any;  // coarse blocks of (1 << kLogC)^3 cells
+    const uint32_t* c_all;
+    const uint32_t* f_any;  // fine blocks of (1 << kLogF)^3 cells
+    const uint32_t* f_all;
+    int nbc, nbf;           // blocks per axis
     nacc_blob_field field;
 };
 
@@ -329,6 +336,36 @@ __device__ __forceinline__ void rec_run(RunRec& q, int k0, int k1) {
 // return when the buffer is full or the ray is finished.  With a recorder,
 // every occupied cell run is also recorded whole: the emitted points are the
 // first n points of the recorded ranges, in order.
+// The box of cells a run starting in cell ic of level l (occupancy occ)
+// may span: the cell's coarse block if all its cells share occ, else its
+// fine block if they do, else the cell alone.
+__device__ __forceinline__ void run_box(const MarchArgs& A, int l, const int ic[3], bool occ, int lo[3],
+                                        int hi[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) lo[a] = hi[a] = ic[a];
+    if (!A.c_any) return;
+    int log = kLogC;
+    {
+        const uint32_t nbc = (uint32_t)A.nbc;
+        const uint32_t b = (((uint32_t)l * nbc + (uint32_t)(ic[0] >> kLogC)) * nbc + (uint32_t)(ic[1] >> kLogC)) * nbc +
+                           (uint32_t)(ic[2] >> kLogC);
+        const uint32_t* sum = occ ? A.c_all : A.c_any;
+        if (occ != (bool)((__ldg(&sum[b >> 5]) >> (b & 31)) & 1u)) {
+            const uint32_t nbf = (uint32_t)A.nbf;
+            const uint32_t f = (((uint32_t)l * nbf + (uint32_t)(ic[0] >> kLogF)) * nbf + (uint32_t)(ic[1] >> kLogF)) *
+                                   nbf + (uint32_t)(ic[2] >> kLogF);
+            const uint32_t* fs = occ ? A.f_all : A.f_any;
+            if (occ != (bool)((__ldg(&fs[f >> 5]) >> (f & 31)) & 1u)) return;
+            log = kLogF;
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = (ic[a] >> log) << log;
+        hi[a] = min(lo[a] + (1 << log), A.g.res) - 1;
+    }
+}
+
 template <bool kRec>
 __device__ void advance(const MarchArgs& A, Lane& s, int kend, int limit, int* buf, int& bn, RunRec* q) {
     const int L = A.g.n_levels;
@@ -346,20 +383,8 @@ __device__ void advance(const MarchArgs& A, Lane& s, int kend, int limit, int* b
                 break;
             }
             if (l < L) {
-                int lo[3] = {ic[0], ic[1], ic[2]}, hi[3] = {ic[0], ic[1], ic[2]};
-                if (A.blk) {  // a cell in an empty (or a full) block: the run spans the block
-                    const uint32_t b = ((uint32_t)l * A.nb + ic[0] / kBlk) * A.nb * A.nb +
-                                       (uint32_t)(ic[1] / kBlk) * A.nb + ic[2] / kBlk;
-                    const uint32_t* sum = occ ? A.blkf : A.blk;
-                    const bool bit = (__ldg(&sum[b >> 5]) >> (b & 31)) & 1u;
-                    if (occ == bit) {
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            lo[a] = ic[a] / kBlk * kBlk;
-                            hi[a] = min(lo[a] + kBlk, A.g.res) - 1;
-                        }
-                    }
-                }
+                int lo[3], hi[3];
+                run_box(A, l, ic, occ, lo, hi);  // a cell in a uniform block: the run spans the block
                 s.run_end = skip_target(A, s.R, s.k, __fmul_rn(__fadd_rn(t0, t1), 0.5f), l, lo, hi, kend);
             } else {
                 s.run_end = s.k + 1;
@@ -396,8 +421,10 @@ __device__ void advance(const MarchArgs& A, Lane& s, int kend, int limit, int* b
 // divide res), set iff any cell of the block is occupied.  Block b =
 // (l*nb + bx)*nb*nb + by*nb + bz.  An acceleration structure only: a run
 // that stays inside an empty block skips every cell of it.
+template <int kLog>
 __global__ void __launch_bounds__(256)
     k_block_summary(GridGeom g, int nb, uint32_t* __restrict__ blk, uint32_t* __restrict__ blkf) {
+    constexpr int kBlk = 1 << kLog;
     const uint64_t nblocks = (uint64_t)g.n_levels * nb * nb * nb;
     const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool any = false, all = b < nblocks;
@@ -716,19 +743,8 @@ __global__ void __launch_bounds__(kBlockThreads) k_occupied_range(MarchArgs A, f
             const bool occ = lattice_point(A, s.R, k, t0, t1, x, l, ic);
             int run_end = k + 1;
             if (l < L) {
-                int lo[3] = {ic[0], ic[1], ic[2]}, hi[3] = {ic[0], ic[1], ic[2]};
-                if (A.blk) {
-                    const uint32_t b = ((uint32_t)l * A.nb + ic[0] / kBlk) * A.nb * A.nb +
-                                       (uint32_t)(ic[1] / kBlk) * A.nb + ic[2] / kBlk;
-                    const uint32_t* sum = occ ? A.blkf : A.blk;
-                    if (occ == (bool)((__ldg(&sum[b >> 5]) >> (b & 31)) & 1u)) {
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            lo[a] = ic[a] / kBlk * kBlk;
-                            hi[a] = min(lo[a] + kBlk, A.g.res) - 1;
-                        }
-                    }
-                }
+                int lo[3], hi[3];
+                run_box(A, l, ic, occ, lo, hi);
                 run_end = skip_target(A, s.R, k, __fmul_rn(__fadd_rn(t0, t1), 0.5f), l, lo, hi, ke);
             }
             if (occ) {
@@ -750,6 +766,28 @@ __global__ void __launch_bounds__(kBlockThreads) k_occupied_range(MarchArgs A, f
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// Points A's block summaries into `mem` (kBlockBitsBytes) and rebuilds them from the bits.
+int build_summaries(MarchArgs& A, void* mem, cudaStream_t st) {
+    char* p = static_cast<char*>(mem);
+    uint32_t* c_any = reinterpret_cast<uint32_t*>(p);
+    uint32_t* c_all = reinterpret_cast<uint32_t*>(p + summary_bytes(kLogC));
+    uint32_t* f_any = reinterpret_cast<uint32_t*>(p + 2 * summary_bytes(kLogC));
+    uint32_t* f_all = reinterpret_cast<uint32_t*>(p + 2 * summary_bytes(kLogC) + summary_bytes(kLogF));
+    A.nbc = (A.g.res + (1 << kLogC) - 1) >> kLogC;
+    A.nbf = (A.g.res + (1 << kLogF) - 1) >> kLogF;
+    A.c_any = c_any;
+    A.c_all = c_all;
+    A.f_any = f_any;
+    A.f_all = f_all;
+    const uint64_t ncb = (uint64_t)A.g.n_levels * A.nbc * A.nbc * A.nbc;
+    k_block_summary<kLogC><<<(unsigned)((ncb + 255) / 256), 256, 0, st>>>(A.g, A.nbc, c_any, c_all);
+    NACC_LAUNCH_CHECK();
+    const uint64_t nfb = (uint64_t)A.g.n_levels * A.nbf * A.nbf * A.nbf;
+    k_block_summary<kLogF><<<(unsigned)((nfb + 255) / 256), 256, 0, st>>>(A.g, A.nbf, f_any, f_all);
+    NACC_LAUNCH_CHECK();
+    return NACC_OK;
+}
+
 // Caller-owned events recorded around the count kernel (diagnostics).
 thread_local cudaEvent_t g_count_ev[2] = {nullptr, nullptr};
 
@@ -763,7 +801,7 @@ extern "C" size_t nacc_march_scratch_bytes(int64_t n_rays) {
     const int64_t nb = (n_rays + kRaysPerBlock - 1) / kRaysPerBlock;
     // counts, kstops, nruns, tnear, block sums, run slots
     return align256(4 * (size_t)n_rays) * 4 + align256(8 * (size_t)(nb > 0 ? nb : 1)) +
-           align256(sizeof(int2) * kRunSlots * (size_t)n_rays) + 2 * kBlockBitsBytes;
+           align256(sizeof(int2) * kRunSlots * (size_t)n_rays) + kBlockBitsBytes;
 }
 
 extern "C" int nacc_march_grid(const nacc_grid* grid, const float* rays_o, const float* rays_d,
@@ -840,18 +878,11 @@ extern "C" int nacc_march_grid(const nacc_grid* grid, const float* rays_o, const
     sp += align256(8 * (size_t)((n_rays + kRaysPerBlock - 1) / kRaysPerBlock));
     int2* runs = reinterpret_cast<int2*>(sp);
     sp += align256(sizeof(int2) * kRunSlots * (size_t)n_rays);
-    uint32_t* blk = reinterpret_cast<uint32_t*>(sp);
-    uint32_t* blkf = reinterpret_cast<uint32_t*>(sp + kBlockBitsBytes);
-
     const int64_t nb = (n_rays + kRaysPerBlock - 1) / kRaysPerBlock;
     NACC_CHECK_ARG(nb < (int64_t(1) << 31), "too many rays for one launch");
-    A.nb = (A.g.res + kBlk - 1) / kBlk;
-    A.blk = blk;
-    A.blkf = blkf;
     {
-        const uint64_t nblocks = (uint64_t)A.g.n_levels * A.nb * A.nb * A.nb;
-        k_block_summary<<<(unsigned)((nblocks + 255) / 256), 256, 0, st>>>(A.g, A.nb, blk, blkf);
-        NACC_LAUNCH_CHECK();
+        const int rc = build_summaries(A, sp, st);
+        if (rc != NACC_OK) return rc;
     }
     if (g_count_ev[0]) NACC_CUDA_TRY(cudaEventRecord(g_count_ev[0], st));
     if (with_field && A.field.n_blobs <= kRayBlobsMax) {
@@ -890,7 +921,7 @@ extern "C" int nacc_march_grid(const nacc_grid* grid, const float* rays_o, const
     return NACC_OK;
 }
 
-extern "C" size_t nacc_occupied_range_scratch_bytes(void) { return 2 * kBlockBitsBytes; }
+extern "C" size_t nacc_occupied_range_scratch_bytes(void) { return kBlockBitsBytes; }
 
 extern "C" int nacc_occupied_range(const nacc_grid* grid, const float* rays_o, const float* rays_d, int64_t n_rays,
                                    const nacc_march_params* params, float* t_lo, float* t_hi, void* scratch,
@@ -906,8 +937,8 @@ extern "C" int nacc_occupied_range(const nacc_grid* grid, const float* rays_o, c
     NACC_CHECK_ARG(!std::isnan(params->t_min) && !std::isnan(params->t_max), "t_min/t_max is NaN");
     if (n_rays == 0) return NACC_OK;
     NACC_CHECK_ARG(rays_o && rays_d && t_lo && t_hi, "a pointer argument is NULL");
-    NACC_CHECK_ARG(scratch != nullptr && scratch_bytes >= 2 * kBlockBitsBytes, "scratch too small: %zu < %zu bytes",
-                   scratch_bytes, 2 * kBlockBitsBytes);
+    NACC_CHECK_ARG(scratch != nullptr && scratch_bytes >= kBlockBitsBytes, "scratch too small: %zu < %zu bytes",
+                   scratch_bytes, kBlockBitsBytes);
     NACC_CHECK_ARG((reinterpret_cast<uintptr_t>(scratch) & 255) == 0, "scratch not 256-byte aligned");
     A.o = rays_o;
     A.d = rays_d;
@@ -920,9 +951,6 @@ extern "C" int nacc_occupied_range(const nacc_grid* grid, const float* rays_o, c
     A.inv_step = 1.0f / params->step;
     A.idx32 = ((uint64_t)A.g.n_levels * A.g.res * A.g.res * A.g.res) <= 0xffffffffull ? 1 : 0;
     A.field = nacc_blob_field{0, nullptr, nullptr, nullptr, nullptr};
-    A.nb = (A.g.res + kBlk - 1) / kBlk;
-    A.blk = static_cast<uint32_t*>(scratch);
-    A.blkf = reinterpret_cast<uint32_t*>(static_cast<char*>(scratch) + kBlockBitsBytes);
     for (int l = 0; l < NACC_MAX_LEVELS; ++l) {
         A.skip_lim[l] = -1.0f;
         if (l >= A.g.n_levels) continue;
@@ -938,10 +966,8 @@ extern "C" int nacc_occupied_range(const nacc_grid* grid, const float* rays_o, c
     const int64_t nb = (n_rays + kBlockThreads - 1) / kBlockThreads;
     NACC_CHECK_ARG(nb < (int64_t(1) << 31), "too many rays for one launch");
     {
-        const uint64_t nblocks = (uint64_t)A.g.n_levels * A.nb * A.nb * A.nb;
-        k_block_summary<<<(unsigned)((nblocks + 255) / 256), 256, 0, as_stream(stream)>>>(
-            A.g, A.nb, const_cast<uint32_t*>(A.blk), const_cast<uint32_t*>(A.blkf));
-        NACC_LAUNCH_CHECK();
+        const int rc = build_summaries(A, scratch, as_stream(stream));
+        if (rc != NACC_OK) return rc;
     }
     k_occupied_range<<<(unsigned)nb, kBlockThreads, 0, as_stream(stream)>>>(A, t_lo, t_hi);
     NACC_LAUNCH_CHECK();
