@@ -764,6 +764,37 @@ __global__ void __launch_bounds__(kBlockThreads) k_occupied_range(MarchArgs A, f
     }
 }
 
+// The coarse summary from the fine one: a coarse block is any- (all-)
+// occupied iff any (every) fine block inside it is; fine blocks past the
+// grid's edge do not exist.
+__global__ void __launch_bounds__(256)
+    k_coarse_summary(int n_levels, int nbc, int nbf, const uint32_t* __restrict__ f_any,
+                     const uint32_t* __restrict__ f_all, uint32_t* __restrict__ c_any, uint32_t* __restrict__ c_all) {
+    constexpr int kR = 1 << (kLogC - kLogF);  // fine blocks per coarse block edge
+    const uint64_t ncb = (uint64_t)n_levels * nbc * nbc * nbc;
+    const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool any = false, all = b < ncb;
+    if (b < ncb) {
+        const uint64_t per_level = (uint64_t)nbc * nbc * nbc;
+        const int l = (int)(b / per_level);
+        const uint32_t rem = (uint32_t)(b % per_level);
+        const int bx = rem / (nbc * nbc), by = (rem / nbc) % nbc, bz = rem % nbc;
+        for (int x = bx * kR; x < min(bx * kR + kR, nbf); ++x)
+            for (int y = by * kR; y < min(by * kR + kR, nbf); ++y)
+                for (int z = bz * kR; z < min(bz * kR + kR, nbf); ++z) {
+                    const uint32_t f = (((uint32_t)l * nbf + x) * nbf + y) * nbf + z;
+                    any = any || ((__ldg(&f_any[f >> 5]) >> (f & 31)) & 1u);
+                    all = all && ((__ldg(&f_all[f >> 5]) >> (f & 31)) & 1u);
+                }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, any);
+    const unsigned mf = __ballot_sync(0xffffffffu, all);
+    if ((threadIdx.x & 31) == 0 && b < ncb) {
+        c_any[b >> 5] = m;
+        c_all[b >> 5] = mf;
+    }
+}
+
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Points A's block summaries into `mem` (kBlockBitsBytes) and rebuilds them from the bits.
@@ -779,11 +810,12 @@ int build_summaries(MarchArgs& A, void* mem, cudaStream_t st) {
     A.c_all = c_all;
     A.f_any = f_any;
     A.f_all = f_all;
-    const uint64_t ncb = (uint64_t)A.g.n_levels * A.nbc * A.nbc * A.nbc;
-    k_block_summary<kLogC><<<(unsigned)((ncb + 255) / 256), 256, 0, st>>>(A.g, A.nbc, c_any, c_all);
-    NACC_LAUNCH_CHECK();
     const uint64_t nfb = (uint64_t)A.g.n_levels * A.nbf * A.nbf * A.nbf;
     k_block_summary<kLogF><<<(unsigned)((nfb + 255) / 256), 256, 0, st>>>(A.g, A.nbf, f_any, f_all);
+    NACC_LAUNCH_CHECK();
+    const uint64_t ncb = (uint64_t)A.g.n_levels * A.nbc * A.nbc * A.nbc;
+    k_coarse_summary<<<(unsigned)((ncb + 255) / 256), 256, 0, st>>>(A.g.n_levels, A.nbc, A.nbf, f_any, f_all, c_any,
+                                                                     c_all);
     NACC_LAUNCH_CHECK();
     return NACC_OK;
 }
