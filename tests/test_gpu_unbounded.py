@@ -394,3 +394,19 @@ def test_unbounded_full_size_sampled(nacc, orc):
         assert all(abs(int(gc[r]) - int(ec[r])) <= 1 for r in ties)
         del pk
         torch.cuda.empty_cache()
+
+
+def test_unbounded_early_stop_table_overflow_direct_sum(nacc, orc):
+    """320 wide blobs within radius 2: more than half the rays keep more than
+    the 256 table entries of the early-stop pass and sum every blob per point."""
+    w = workloads.c5_unbounded(n_cams=1, width=32, height=16, res=32)
+    blobs = workloads.ball_blob_field(320, 9, radius=2.0, std_lo=0.3, std_hi=0.5, peak=2.0)
+    w = workloads.dataclasses.replace(w, blobs=blobs)
+    o, d = w.rays_o.astype(np.float64), w.rays_d.astype(np.float64)
+    mu, sd, pk = blobs.mu.astype(np.float64), blobs.std.astype(np.float64), blobs.peak.astype(np.float64)
+    rel = mu[None] - o[:, None]
+    pp = (np.cross(rel, np.broadcast_to(d[:, None], rel.shape)) ** 2).sum(-1) / (d * d).sum(1)[:, None]
+    bound = pk[None] * np.exp(-pp / (2 * sd[None] ** 2)) * math.sqrt(2 * math.pi) * sd[None]
+    assert ((bound > 1e-7).sum(1) > 256).mean() > 0.3
+    bits, _ = orc.density_grid_contracted(w.grid, blobs)
+    _check_early_stop(nacc, orc, w, bits, 256)
