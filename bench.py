@@ -55,7 +55,7 @@ BYTES = {
     "render_fwd": (24, 32),
     "render_bwd": (40, 28),
 }
-KERNELS_PER_STEP = {"march": 4, "field": 1, "render_fwd": 1, "loss": 1, "render_bwd": 1}
+KERNELS_PER_STEP = {"march": 5, "field": 1, "render_fwd": 1, "loss": 1, "render_bwd": 1}
 
 
 def parse_args(argv=None):
