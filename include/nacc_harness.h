@@ -36,7 +36,7 @@ int nacc_harness_field(const float* rays_o, const float* rays_d, const int32_t* 
  * along the ray in the closed form peak_b 2^(A_b (t - t*_b)^2 + C_b) (t*_b
  * the closest approach, set up once per ray) with the hardware exp2; the
  * relative error is ~1e-5 (FP32 rounding of t - t*_b).  Fields of more than
- * 64 blobs keep, per ray, only the blobs whose integral along the whole ray
+ * 16 blobs keep, per ray, only the blobs whose integral along the whole ray
  * line exceeds 1e-7 (bound peak_b 2^C_b sqrt(2 pi) std_b / |d|), so each
  * dropped blob changes sigma by at most 1e-7 |d| / (sqrt(2 pi) std_b).  At
  * most 256 blobs; t_starts, t_ends, sigmas, rgbs 16-byte aligned.  Outputs

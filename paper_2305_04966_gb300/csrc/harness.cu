@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(256)
 // peak 2^C_b <= kCullEps |d| / (sqrt(2 pi) sd) at any point of the ray.
 constexpr int kFieldWarps = 8;
 constexpr int kFieldRayBlobs = 256;  // per-warp shared table limit
-constexpr int kCullAbove = 64;
+constexpr int kCullAbove = 16;
 constexpr float kCullEps = 1e-7f;
 
 // t0, t1 of positions p..p+3 of the ray's range [s, e) (zero outside it);

@@ -509,9 +509,19 @@ def test_field_eval_matches_oracle_field(nacc, orc, field_blobs, per_sample):
     sig, rgb = nacc.field_eval(field, T(w.rays_o), T(w.rays_d), pk, per_sample=per_sample)
     s64, c64 = orc.field_samples(w.rays_o, w.rays_d, ex["ray_indices"], ex["t_starts"], ex["t_ends"], w.blobs)
     sig, rgb = sig[:S].cpu().numpy(), rgb[:S].cpu().numpy()
-    np.testing.assert_allclose(sig, s64, rtol=1e-4, atol=1e-30)
-    ok = s64 > 1e-20
-    np.testing.assert_allclose(rgb[ok], c64[ok], rtol=1e-4, atol=1e-6)
+    if per_sample or field_blobs <= 16:  # every blob
+        np.testing.assert_allclose(sig, s64, rtol=1e-4, atol=1e-30)
+        ok = s64 > 1e-20
+        np.testing.assert_allclose(rgb[ok], c64[ok], rtol=1e-4, atol=1e-6)
+        return
+    # the warp-per-ray form culls blobs per ray above 16 blobs: each dropped
+    # blob changes sigma by at most 1e-7 |d| / (sqrt(2 pi) std)
+    dlen = np.linalg.norm(w.rays_d, axis=1)[ex["ray_indices"]]
+    cull = np.sum(1e-7 / (math.sqrt(2 * math.pi) * w.blobs.std.astype(np.float64))) * dlen
+    assert np.all(np.abs(sig - s64) <= 1e-4 * s64 + cull)
+    ok = s64 > 1.0
+    assert ok.sum() > 10000
+    np.testing.assert_allclose(rgb[ok], c64[ok], rtol=1e-3, atol=1e-4)
 
 
 def test_c2_pipeline_sampled_rays_vs_oracle(nacc, orc):
