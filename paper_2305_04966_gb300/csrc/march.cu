@@ -336,11 +336,18 @@ __device__ __forceinline__ void rec_run(RunRec& q, int k0, int k1) {
 // return when the buffer is full or the ray is finished.  With a recorder,
 // every occupied cell run is also recorded whole: the emitted points are the
 // first n points of the recorded ranges, in order.
+__device__ __forceinline__ bool cell_bit(const MarchArgs& A, int l, int x, int y, int z) {
+    const uint32_t res = (uint32_t)A.g.res;
+    const uint32_t idx = ((uint32_t)l * res + (uint32_t)x) * res * res + (uint32_t)y * res + (uint32_t)z;
+    return (__ldg(&A.g.bits[idx >> 5]) >> (idx & 31)) & 1u;
+}
+
 // The box of cells a run starting in cell ic of level l (occupancy occ)
 // may span: the cell's coarse block if all its cells share occ, else its
-// fine block if they do, else the cell alone.
-__device__ __forceinline__ void run_box(const MarchArgs& A, int l, const int ic[3], bool occ, int lo[3],
-                                        int hi[3]) {
+// fine block if they do, else the cell and, if it shares occ, the next cell
+// across the face the ray leaves through (32-bit cell indices only).
+__device__ __forceinline__ void run_box(const MarchArgs& A, const Ray& R, int l, const int ic[3], bool occ,
+                                        int lo[3], int hi[3]) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) lo[a] = hi[a] = ic[a];
     if (!A.c_any) return;
@@ -355,7 +362,39 @@ __device__ __forceinline__ void run_box(const MarchArgs& A, int l, const int ic[
             const uint32_t f = (((uint32_t)l * nbf + (uint32_t)(ic[0] >> kLogF)) * nbf + (uint32_t)(ic[1] >> kLogF)) *
                                    nbf + (uint32_t)(ic[2] >> kLogF);
             const uint32_t* fs = occ ? A.f_all : A.f_any;
-            if (occ != (bool)((__ldg(&fs[f >> 5]) >> (f & 31)) & 1u)) return;
+            if (occ != (bool)((__ldg(&fs[f >> 5]) >> (f & 31)) & 1u)) {
+                if (!A.idx32) return;
+                // the exit axis of the cell (any choice keeps the box uniform)
+                const Level& lv = A.g.lv[l];
+                int ax = -1;
+                float tx = INFINITY;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    if (R.d[a] == 0.0f) continue;
+                    const float face = lv.lmin[a] + (float)(R.d[a] > 0.0f ? ic[a] + 1 : ic[a]) * lv.width[a];
+                    const float t = (face - R.o[a]) * R.invd[a];
+                    if (t < tx) {
+                        tx = t;
+                        ax = a;
+                    }
+                }
+                if (ax < 0) return;
+                // the neighbour across that face (selects, not a run-time array index)
+                int nc[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) nc[a] = ic[a] + (a == ax ? (R.d[a] > 0.0f ? 1 : -1) : 0);
+                if (nc[0] < 0 || nc[0] >= A.g.res || nc[1] < 0 || nc[1] >= A.g.res || nc[2] < 0 ||
+                    nc[2] >= A.g.res)
+                    return;
+                if (cell_bit(A, l, nc[0], nc[1], nc[2]) == occ) {
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        lo[a] = min(ic[a], nc[a]);
+                        hi[a] = max(ic[a], nc[a]);
+                    }
+                }
+                return;
+            }
             log = kLogF;
         }
     }
@@ -384,7 +423,7 @@ __device__ void advance(const MarchArgs& A, Lane& s, int kend, int limit, int* b
             }
             if (l < L) {
                 int lo[3], hi[3];
-                run_box(A, l, ic, occ, lo, hi);  // a cell in a uniform block: the run spans the block
+                run_box(A, s.R, l, ic, occ, lo, hi);  // a cell in a uniform block: the run spans the block
                 s.run_end = skip_target(A, s.R, s.k, __fmul_rn(__fadd_rn(t0, t1), 0.5f), l, lo, hi, kend);
             } else {
                 s.run_end = s.k + 1;
@@ -744,7 +783,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_occupied_range(MarchArgs A, f
             int run_end = k + 1;
             if (l < L) {
                 int lo[3], hi[3];
-                run_box(A, l, ic, occ, lo, hi);
+                run_box(A, s.R, l, ic, occ, lo, hi);
                 run_end = skip_target(A, s.R, k, __fmul_rn(__fadd_rn(t0, t1), 0.5f), l, lo, hi, ke);
             }
             if (occ) {
