@@ -342,66 +342,79 @@ __device__ __forceinline__ bool cell_bit(const MarchArgs& A, int l, int x, int y
     return (__ldg(&A.g.bits[idx >> 5]) >> (idx & 31)) & 1u;
 }
 
+// Exit axis of the box [lo, hi] of level l along the ray (-1 if none): the
+// face reached first.  Any answer keeps a box extended across it uniform.
+__device__ __forceinline__ int exit_axis(const MarchArgs& A, const Ray& R, int l, const int lo[3], const int hi[3]) {
+    const Level& lv = A.g.lv[l];
+    int ax = -1;
+    float tx = INFINITY;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (R.d[a] == 0.0f) continue;
+        const float face = lv.lmin[a] + (float)(R.d[a] > 0.0f ? hi[a] + 1 : lo[a]) * lv.width[a];
+        const float t = (face - R.o[a]) * R.invd[a];
+        if (t < tx) {
+            tx = t;
+            ax = a;
+        }
+    }
+    return ax;
+}
+
+// Occupancy summary bit of block (bx, by, bz) of level l in a summary with nb blocks per axis.
+__device__ __forceinline__ bool summary_bit(const uint32_t* sum, int nb, int l, int bx, int by, int bz) {
+    const uint32_t n = (uint32_t)nb;
+    const uint32_t b = (((uint32_t)l * n + (uint32_t)bx) * n + (uint32_t)by) * n + (uint32_t)bz;
+    return (__ldg(&sum[b >> 5]) >> (b & 31)) & 1u;
+}
+
 // The box of cells a run starting in cell ic of level l (occupancy occ)
 // may span: the cell's coarse block if all its cells share occ, else its
-// fine block if they do, else the cell and, if it shares occ, the next cell
-// across the face the ray leaves through (32-bit cell indices only).
+// fine block if they do, else the cell; then, if the unit across the face
+// the ray leaves through (the next block of the same size, or the next
+// cell) shares occ too, the box spans it as well (32-bit cell indices only
+// for the cell case).
 __device__ __forceinline__ void run_box(const MarchArgs& A, const Ray& R, int l, const int ic[3], bool occ,
                                         int lo[3], int hi[3]) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) lo[a] = hi[a] = ic[a];
     if (!A.c_any) return;
-    int log = kLogC;
-    {
-        const uint32_t nbc = (uint32_t)A.nbc;
-        const uint32_t b = (((uint32_t)l * nbc + (uint32_t)(ic[0] >> kLogC)) * nbc + (uint32_t)(ic[1] >> kLogC)) * nbc +
-                           (uint32_t)(ic[2] >> kLogC);
-        const uint32_t* sum = occ ? A.c_all : A.c_any;
-        if (occ != (bool)((__ldg(&sum[b >> 5]) >> (b & 31)) & 1u)) {
-            const uint32_t nbf = (uint32_t)A.nbf;
-            const uint32_t f = (((uint32_t)l * nbf + (uint32_t)(ic[0] >> kLogF)) * nbf + (uint32_t)(ic[1] >> kLogF)) *
-                                   nbf + (uint32_t)(ic[2] >> kLogF);
-            const uint32_t* fs = occ ? A.f_all : A.f_any;
-            if (occ != (bool)((__ldg(&fs[f >> 5]) >> (f & 31)) & 1u)) {
-                if (!A.idx32) return;
-                // the exit axis of the cell (any choice keeps the box uniform)
-                const Level& lv = A.g.lv[l];
-                int ax = -1;
-                float tx = INFINITY;
+    int log = -1;  // unit of the box: 1 << log cells per edge; -1 a single cell
+    if (summary_bit(occ ? A.c_all : A.c_any, A.nbc, l, ic[0] >> kLogC, ic[1] >> kLogC, ic[2] >> kLogC) == occ)
+        log = kLogC;
+    else if (summary_bit(occ ? A.f_all : A.f_any, A.nbf, l, ic[0] >> kLogF, ic[1] >> kLogF, ic[2] >> kLogF) == occ)
+        log = kLogF;
+    if (log >= 0) {
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    if (R.d[a] == 0.0f) continue;
-                    const float face = lv.lmin[a] + (float)(R.d[a] > 0.0f ? ic[a] + 1 : ic[a]) * lv.width[a];
-                    const float t = (face - R.o[a]) * R.invd[a];
-                    if (t < tx) {
-                        tx = t;
-                        ax = a;
-                    }
-                }
-                if (ax < 0) return;
-                // the neighbour across that face (selects, not a run-time array index)
-                int nc[3];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) nc[a] = ic[a] + (a == ax ? (R.d[a] > 0.0f ? 1 : -1) : 0);
-                if (nc[0] < 0 || nc[0] >= A.g.res || nc[1] < 0 || nc[1] >= A.g.res || nc[2] < 0 ||
-                    nc[2] >= A.g.res)
-                    return;
-                if (cell_bit(A, l, nc[0], nc[1], nc[2]) == occ) {
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        lo[a] = min(ic[a], nc[a]);
-                        hi[a] = max(ic[a], nc[a]);
-                    }
-                }
-                return;
-            }
-            log = kLogF;
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = (ic[a] >> log) << log;
+            hi[a] = min(lo[a] + (1 << log), A.g.res) - 1;
         }
+    } else if (!A.idx32) {
+        return;
     }
+    const int ax = exit_axis(A, R, l, lo, hi);
+    if (ax < 0) return;
+    const int unit = log >= 0 ? 1 << log : 1;
+    // the unit across that face (selects, not a run-time array index)
+    int nlo[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) nlo[a] = lo[a] + (a == ax ? (R.d[a] > 0.0f ? unit : -unit) : 0);
+    if (nlo[0] < 0 || nlo[0] >= A.g.res || nlo[1] < 0 || nlo[1] >= A.g.res || nlo[2] < 0 || nlo[2] >= A.g.res)
+        return;
+    bool same;
+    if (log == kLogC)
+        same = summary_bit(occ ? A.c_all : A.c_any, A.nbc, l, nlo[0] >> kLogC, nlo[1] >> kLogC, nlo[2] >> kLogC) == occ;
+    else if (log == kLogF)
+        same = summary_bit(occ ? A.f_all : A.f_any, A.nbf, l, nlo[0] >> kLogF, nlo[1] >> kLogF, nlo[2] >> kLogF) == occ;
+    else
+        same = cell_bit(A, l, nlo[0], nlo[1], nlo[2]) == occ;
+    if (!same) return;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        lo[a] = (ic[a] >> log) << log;
-        hi[a] = min(lo[a] + (1 << log), A.g.res) - 1;
+        const int nhi = min(nlo[a] + unit, A.g.res) - 1;
+        lo[a] = min(lo[a], nlo[a]);
+        hi[a] = max(hi[a], nhi);
     }
 }
 
