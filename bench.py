@@ -569,6 +569,7 @@ def proposal_measure(torch, nacc, dev, flush, steps=5, train_steps=1024, batch=6
         return tot / steps, out
 
     grid_ms, T_grid = timed(grid_path)
+    grid_S = bufs.packed.n_samples()
     prop_ms, T_prop = timed(prop_path)
     comb_ms, T_comb = timed(comb_path)
     sel = np.linspace(0, n - 1, sample_rays).astype(np.int64)
@@ -606,7 +607,7 @@ def proposal_measure(torch, nacc, dev, flush, steps=5, train_steps=1024, batch=6
     return {
         "grid_sweep": grid_sweep, "proposal_sweep": prop_sweep,
         "workload": w.name, "n_rays": n,
-        "grid_path": {"rays/s": n / (grid_ms / 1e3), "ms": grid_ms, "samples": bufs.packed.n_samples(),
+        "grid_path": {"rays/s": n / (grid_ms / 1e3), "ms": grid_ms, "samples": grid_S,
                       "early_stop_eps": m.early_stop_eps},
         "proposal_path": {"rays/s": n / (prop_ms / 1e3), "ms": prop_ms, "samples": n * 32,
                           "rounds": [64, 32], "final_samples_per_ray": 32},
