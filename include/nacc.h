@@ -102,7 +102,9 @@ const char* nacc_last_error(void);
 /* Library version (major*10000 + minor*100 + patch). */
 int nacc_version(void);
 
-/* Scratch bytes nacc_march_grid needs for n_rays rays. */
+/* Scratch bytes nacc_march_grid needs for n_rays rays: per-ray counts,
+ * stops and run records (~150 bytes per ray) plus the grid's block
+ * summaries sized for the largest grid (8 levels of 1024^3 cells: 32.5 MiB). */
 size_t nacc_march_scratch_bytes(int64_t n_rays);
 
 /*

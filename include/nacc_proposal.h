@@ -105,7 +105,8 @@ int nacc_edges_to_packed(int64_t n_rays, int32_t n_bins, const float* edges, int
  * [n_rays] ([device]).  A ray with no occupied point gets t_lo = t_hi =
  * t_near, or max(t_min, 0) if it misses the grid.  params->early_stop_eps
  * is ignored.  scratch: [device] >= nacc_occupied_range_scratch_bytes(),
- * 256-byte aligned (the grid's block summaries).
+ * 256-byte aligned (the grid's block summaries, sized for the largest grid:
+ * 32.5 MiB).
  */
 size_t nacc_occupied_range_scratch_bytes(void);
 int nacc_occupied_range(const nacc_grid* grid, const float* rays_o, const float* rays_d, int64_t n_rays,
