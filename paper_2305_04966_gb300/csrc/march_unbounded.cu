@@ -73,8 +73,18 @@ __global__ void __launch_bounds__(256) k_unb_table(int K, float inv_tn, float in
 // Flat cell index of c(x), x = o + d tm on the ray, in the finest level whose
 // box holds it; -1 (all ones for unsigned I) outside every level.  I is
 // uint32_t when every cell index fits.
+__device__ __forceinline__ bool in_level(const Level& lv, const float c[3]) {
+    return c[0] >= lv.lmin[0] && c[0] <= lv.lmax[0] && c[1] >= lv.lmin[1] && c[1] <= lv.lmax[1] &&
+           c[2] >= lv.lmin[2] && c[2] <= lv.lmax[2];
+}
+
+// `hint`: a level to try first (the level of a nearby point); taken only
+// if the point lies in it and not in the next finer one -- the levels'
+// boxes are nested, so that is the finest level holding it.  The level
+// found (or L) goes to `lvl`.
 template <typename I>
-__device__ __forceinline__ I cell_index(const UArgs& A, const float o[3], const float d[3], float tm) {
+__device__ __forceinline__ I cell_index(const UArgs& A, const float o[3], const float d[3], float tm, int hint,
+                                        int& lvl) {
     float c[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) c[a] = __fadd_rn(o[a], __fmul_rn(d[a], tm));
@@ -86,13 +96,14 @@ __device__ __forceinline__ I cell_index(const UArgs& A, const float o[3], const 
         for (int a = 0; a < 3; ++a) c[a] = __fmul_rn(c[a], g);
     }
     const int L = A.g.n_levels;
-    int l = 0;
-    for (; l < L; ++l) {
-        const Level& lv = A.g.lv[l];
-        if (c[0] >= lv.lmin[0] && c[0] <= lv.lmax[0] && c[1] >= lv.lmin[1] && c[1] <= lv.lmax[1] &&
-            c[2] >= lv.lmin[2] && c[2] <= lv.lmax[2])
-            break;
+    int l;
+    if (in_level(A.g.lv[hint], c) && (hint == 0 || !in_level(A.g.lv[hint - 1], c))) {
+        l = hint;
+    } else {
+        for (l = 0; l < L; ++l)
+            if (in_level(A.g.lv[l], c)) break;
     }
+    lvl = l;
     if (l == L) return (I)-1;
     const Level& lv = A.g.lv[l];
     const I res = (I)A.g.res;
@@ -109,12 +120,21 @@ __device__ __forceinline__ I cell_index(const UArgs& A, const float o[3], const 
 // occupied; points >= K are not); t[0..kBatch] receives t_kb..t_(kb+kBatch).
 template <typename I>
 __device__ __forceinline__ unsigned batch_mask(const UArgs& A, const float o[3], const float d[3], int kb,
-                                               float t[kBatch + 1]) {
+                                               float t[kBatch + 1], int& hint) {
 #pragma unroll
     for (int j = 0; j <= kBatch; ++j) t[j] = __ldg(A.tt + min(kb + j, A.K));
     I idx[kBatch];
 #pragma unroll
-    for (int j = 0; j < kBatch; ++j) idx[j] = kb + j < A.K ? cell_index<I>(A, o, d, __ldg(A.tm + kb + j)) : (I)-1;
+    int lv[kBatch];
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j) {
+        lv[j] = hint;
+        idx[j] = kb + j < A.K ? cell_index<I>(A, o, d, __ldg(A.tm + kb + j), hint, lv[j]) : (I)-1;
+    }
+    // the next batch starts from the level of this batch's last point inside the grid
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j)
+        if (lv[j] < A.g.n_levels) hint = lv[j];
     unsigned m = 0;
 #pragma unroll
     for (int j = 0; j < kBatch; ++j) {
@@ -249,9 +269,10 @@ __global__ void __launch_bounds__(kThreads) k_unb_count(UArgs A, int32_t* __rest
         const float o[3] = {A.o[3 * r], A.o[3 * r + 1], A.o[3 * r + 2]};
         const float d[3] = {A.d[3 * r], A.d[3 * r + 1], A.d[3 * r + 2]};
         RunRec q{runs + r * kRunSlots, 0, -1, -1};
+        int hint = 0;  // level of the previous batch's last point in the grid
         for (int kb = 0; kb < A.K; kb += kBatch) {
             float t[kBatch + 1];
-            const unsigned m = batch_mask<I>(A, o, d, kb, t);
+            const unsigned m = batch_mask<I>(A, o, d, kb, t, hint);
 #pragma unroll
             for (int j = 0; j < kBatch; ++j) {
                 if (!((m >> j) & 1u)) continue;
@@ -365,7 +386,8 @@ __global__ void __launch_bounds__(kThreads) k_unb_stop(UArgs A, int32_t* __restr
                 const int k = kb + lane;
                 bool occ = false;
                 if (k < A.K) {
-                    const I idx = cell_index<I>(A, o, d, __ldg(A.tm + k));
+                    int lvl;
+                    const I idx = cell_index<I>(A, o, d, __ldg(A.tm + k), 0, lvl);
                     occ = idx != (I)-1 && ((__ldg(&A.g.bits[idx >> 5]) >> (idx & 31)) & 1u);
                 }
                 const unsigned m = __ballot_sync(0xffffffffu, occ);
@@ -528,10 +550,10 @@ __global__ void __launch_bounds__(kThreads) k_unb_fill(UArgs A, const int32_t* _
     const float o[3] = {A.o[3 * r], A.o[3 * r + 1], A.o[3 * r + 2]};
     const float d[3] = {A.d[3 * r], A.d[3 * r + 1], A.d[3 * r + 2]};
     const int kend = kstops[r];
-    int written = 0;
+    int written = 0, hint = 0;
     for (int kb = 0; kb < kend && written < cnt; kb += kBatch) {
         float t[kBatch + 1];
-        unsigned m = batch_mask<int64_t>(A, o, d, kb, t);
+        unsigned m = batch_mask<int64_t>(A, o, d, kb, t, hint);
         while (m && written < cnt) {
             const int j = __ffs(m) - 1;
             m &= m - 1;
