@@ -695,8 +695,13 @@ class UnboundedProposalSampler(ProposalSampler):
         self.t_near, self.t_far = float(t_near), float(t_far)
         self.contracted = True
 
-    def sample(self, rays_o, rays_d, stratified: bool = False, seed: int = 0) -> PackedSamples:
-        e = phi_edges(self.n_rays, self.rounds[0], self.t_near, self.t_far, out=self.edges[0])
+    def sample(self, rays_o, rays_d, t_min: float | None = None, t_max: float | None = None,
+               stratified: bool = False, seed: int = 0) -> PackedSamples:
+        """Same call as :meth:`ProposalSampler.sample`; ``t_min`` / ``t_max``, if
+        given, replace the sampler's t_near / t_far for this call."""
+        tn = self.t_near if t_min is None else float(t_min)
+        tf = self.t_far if t_max is None else float(t_max)
+        e = phi_edges(self.n_rays, self.rounds[0], tn, tf, out=self.edges[0])
         return self.resample(rays_o, rays_d, e, stratified, seed)
 
 
