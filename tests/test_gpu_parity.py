@@ -237,6 +237,38 @@ def test_march_c2_full_size_sampled(nacc, orc):
     assert np.array_equal(ri, np.repeat(np.arange(w.n_rays, dtype=np.int32), np.diff(go)))
 
 
+def test_march_c3_full_size_sampled(nacc, orc):
+    """The 262,144-ray training batch with its 64-blob field (the density read
+    per sample in the early stop), marched whole: per-ray exact against the
+    oracle on 2,000 strided rays, outside ties."""
+    w = workloads.c3_training()
+    g, m = w.grid, w.march
+    bits, _ = orc.density_grid(g, w.blobs)
+    grid = grid_from_bits(nacc, g.aabb_min, g.aabb_max, g.res, g.n_levels, bits)
+    got = run_march(nacc, grid, w.rays_o, w.rays_d, m.step, m.max_steps, m.t_min, m.t_max,
+                    field=nacc.BlobField.from_numpy(w.blobs), capacity=w.n_rays * m.max_steps)
+    sel = np.linspace(0, w.n_rays - 1, 2000).astype(np.int64)
+    o, d = w.rays_o[sel], w.rays_d[sel]
+    exp = orc.march(o, d, g.aabb_min, g.aabb_max, g.res, g.n_levels, bits, m.step, m.max_steps,
+                    m.t_min, m.t_max, blobs=w.blobs, eps=m.early_stop_eps)
+    full = orc.march(o, d, g.aabb_min, g.aabb_max, g.res, g.n_levels, bits, m.step, m.max_steps,
+                     m.t_min, m.t_max)
+    ties = _near_tie_rays(orc, workloads.Workload("sub", o, d, w.blobs, g, m), bits, full,
+                          -math.log(m.early_stop_eps))
+    assert len(ties) < 0.03 * len(sel)
+    go = got["offsets"]
+    for k, r in enumerate(sel):
+        gs, ge = go[r], go[r + 1]
+        es, ee = exp["offsets"][k], exp["offsets"][k + 1]
+        if k in ties:
+            assert abs((ge - gs) - (ee - es)) <= 1
+            continue
+        assert ge - gs == ee - es, f"ray {r}"
+        np.testing.assert_array_equal(got["t_starts"][gs:ge], exp["t_starts"][es:ee])
+        assert np.all(got["ray_indices"][gs:ge] == r)
+    assert go[-1] > 50 * w.n_rays
+
+
 def test_march_capacity_overflow_reports_and_recovers(nacc, orc):
     w = workloads.c1_forward(512)
     g, m = w.grid, w.march

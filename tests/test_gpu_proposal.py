@@ -308,3 +308,30 @@ def test_combined_sampler_matches_oracle_composition(nacc, P, orc):
     span = np.maximum(e[:, -1] - e[:, 0], 1e-6)[None, :, None]
     err = np.abs(got - exp) / span
     assert np.quantile(err, 0.99) < 2e-3 and err.mean() < 2e-4, (np.quantile(err, 0.99), err.mean(), err.max())
+
+
+def test_sampler_full_batch_sampled_rays(nacc, P, orc):
+    """The whole 262,144-ray training batch through the proposal rounds
+    (64 -> 32 -> 32) as the bench runs them; 1,000 strided rays against the
+    oracle chain (same tolerance as the small composition test)."""
+    w = workloads.c3_training()
+    n = w.n_rays
+    p = _params(P, 102)
+    p["b3"] = np.array([1.0], np.float32)
+    mlp = nacc.ProposalMLP(torch.as_tensor(_flat(p), device=DEV))
+    grid = nacc.OccupancyGrid.empty((-1.5,) * 3, (1.5,) * 3, 32, 1, DEV)
+    sampler = nacc.ProposalSampler(mlp, grid, n, rounds=(64, 32), n_final=32, device=DEV)
+    pk = sampler.sample(torch.as_tensor(w.rays_o, device=DEV), torch.as_tensor(w.rays_d, device=DEV))
+    sel = np.linspace(0, n - 1, 1000).astype(np.int64)
+    got = np.stack([pk.t_starts.reshape(n, 32)[sel].cpu().numpy(), pk.t_ends.reshape(n, 32)[sel].cpu().numpy()])
+    o, d = w.rays_o[sel], w.rays_d[sel]
+    e = _edges_oracle(orc, o, d, 64)
+    for nb, n_next in ((64, 32), (32, 32)):
+        s = P.forward(p, _midpoints(o, d, e))["sigma"]
+        off = np.arange(len(sel) + 1, dtype=np.int64) * nb
+        wts = orc.render_fwd(off, e[:, :-1].reshape(-1), e[:, 1:].reshape(-1), s, np.zeros((len(sel) * nb, 3)))
+        e = orc.sample_pdf(e, wts["weights"].reshape(len(sel), nb).astype(np.float32), n_next)
+    exp = np.stack([e[:, :-1], e[:, 1:]])
+    span = np.maximum(e[:, -1] - e[:, 0], 1e-6)[None, :, None]
+    err = np.abs(got - exp) / span
+    assert np.quantile(err, 0.99) < 2e-3 and err.mean() < 2e-4, (np.quantile(err, 0.99), err.mean(), err.max())
