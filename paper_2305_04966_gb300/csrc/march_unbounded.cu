@@ -124,7 +124,6 @@ __device__ __forceinline__ unsigned batch_mask(const UArgs& A, const float o[3],
 #pragma unroll
     for (int j = 0; j <= kBatch; ++j) t[j] = __ldg(A.tt + min(kb + j, A.K));
     I idx[kBatch];
-#pragma unroll
     int lv[kBatch];
 #pragma unroll
     for (int j = 0; j < kBatch; ++j) {
@@ -245,6 +244,18 @@ __device__ __forceinline__ float sigma_table(const float4* tab, int nt, float tm
     return s;
 }
 
+__device__ __forceinline__ void sigma_table2(const float4* tab, int nt, float tma, float tmb, float& sa, float& sb) {
+    float a = 0.0f, b = 0.0f;
+    for (int i = 0; i < nt; ++i) {
+        const float4 v = tab[i];
+        const float ua = tma - v.y, ub = tmb - v.y;
+        a += ex2_approx(fmaf(v.x * ua, ua, v.z));
+        b += ex2_approx(fmaf(v.x * ub, ub, v.z));
+    }
+    sa = a;
+    sb = b;
+}
+
 __device__ __forceinline__ float sigma_all(const nacc_blob_field& f, const float x[3]) {
     float s = 0.0f;
     for (int b = 0; b < f.n_blobs; ++b) {
@@ -343,39 +354,53 @@ __global__ void __launch_bounds__(kThreads) k_unb_stop(UArgs A, int32_t* __restr
                 if (lane >= o2) ex += y;
             }
             ex -= run.y;
-            for (int p0 = 0; p0 < cnt; p0 += 32) {
-                const int p = p0 + lane;
-                int k = 0;
+            // two consecutive points per lane (64 per pass): each table
+            // entry is read once for both
+            for (int p0 = 0; p0 < cnt; p0 += 64) {
+                const int pa = p0 + 2 * lane, pb = pa + 1;
+                int ka = 0, kb = 0;
                 for (int j = 0; j < nr; ++j) {
                     const int ej = __shfl_sync(0xffffffffu, ex, j);
                     const int kj = __shfl_sync(0xffffffffu, run.x, j);
-                    if (p >= ej) k = kj + (p - ej);
+                    if (pa >= ej) ka = kj + (pa - ej);
+                    if (pb >= ej) kb = kj + (pb - ej);
                 }
-                float tau = 0.0f;
-                if (p < cnt) {
-                    const float t0 = __ldg(A.tt + k), t1 = __ldg(A.tt + k + 1);
-                    float sg;
+                float taua = 0.0f, taub = 0.0f;
+                if (pa < cnt) {
+                    const float a0 = __ldg(A.tt + ka), a1 = __ldg(A.tt + ka + 1);
+                    const bool two = pb < cnt;
+                    const float b0 = two ? __ldg(A.tt + kb) : a0, b1 = two ? __ldg(A.tt + kb + 1) : a1;
+                    float sa, sb;
                     if (nt >= 0) {
-                        sg = sigma_table(tab, nt, 0.5f * (t0 + t1));
+                        sigma_table2(tab, nt, 0.5f * (a0 + a1), 0.5f * (b0 + b1), sa, sb);
                     } else {
-                        const float tm = __ldg(A.tm + k);
-                        const float x[3] = {__fadd_rn(o[0], __fmul_rn(d[0], tm)), __fadd_rn(o[1], __fmul_rn(d[1], tm)),
-                                            __fadd_rn(o[2], __fmul_rn(d[2], tm))};
-                        sg = sigma_all(A.field, x);
+                        const float tma = __ldg(A.tm + ka), tmb = __ldg(A.tm + (two ? kb : ka));
+                        const float xa[3] = {__fadd_rn(o[0], __fmul_rn(d[0], tma)), __fadd_rn(o[1], __fmul_rn(d[1], tma)),
+                                             __fadd_rn(o[2], __fmul_rn(d[2], tma))};
+                        const float xb[3] = {__fadd_rn(o[0], __fmul_rn(d[0], tmb)), __fadd_rn(o[1], __fmul_rn(d[1], tmb)),
+                                             __fadd_rn(o[2], __fmul_rn(d[2], tmb))};
+                        sa = sigma_all(A.field, xa);
+                        sb = sigma_all(A.field, xb);
                     }
-                    tau = __fmul_rn(sg, __fsub_rn(t1, t0));
+                    taua = __fmul_rn(sa, __fsub_rn(a1, a0));
+                    if (two) taub = __fmul_rn(sb, __fsub_rn(b1, b0));
                 }
-                float x = tau;
+                const float pair = taua + taub;
+                float x = pair;  // -> inclusive prefix over the lanes' pairs
 #pragma unroll
                 for (int o2 = 1; o2 < 32; o2 <<= 1) {
                     const float y = __shfl_up_sync(0xffffffffu, x, o2);
                     if (lane >= o2) x += y;
                 }
-                const unsigned over = __ballot_sync(0xffffffffu, p < cnt && carry + (x - tau) > A.thr);
-                if (over) {
-                    const int j = __ffs(over) - 1;
-                    cut = p0 + j;
-                    kstop = __shfl_sync(0xffffffffu, k, j);
+                const float before_a = carry + (x - pair), before_b = before_a + taua;
+                const unsigned over_a = __ballot_sync(0xffffffffu, pa < cnt && before_a > A.thr);
+                const unsigned over_b = __ballot_sync(0xffffffffu, pb < cnt && before_b > A.thr);
+                if (over_a | over_b) {  // the first point past the threshold, in lattice order
+                    const int ja = over_a ? __ffs(over_a) - 1 : 32, jb = over_b ? __ffs(over_b) - 1 : 32;
+                    const bool at_a = ja <= jb;
+                    const int j = at_a ? ja : jb;
+                    cut = p0 + 2 * j + (at_a ? 0 : 1);
+                    kstop = __shfl_sync(0xffffffffu, at_a ? ka : kb, j);
                     break;
                 }
                 carry += __shfl_sync(0xffffffffu, x, 31);
