@@ -11,9 +11,11 @@
 // point t of the tile): the thread encodes its point into row t of a
 // K-major, 128-byte-swizzled BF16 tile; one thread issues the four
 // K = 16 MMAs of a layer (M = 128 points, N = 64 units, K = 64); every warp
-// reads its 32 rows of the accumulator back from tensor memory, adds the
-// bias, applies ReLU and writes the next layer's BF16 input row; the last
-// layer (64 -> 1) is a dot product on the CUDA cores, then softplus.
+// reads its 32 rows of the accumulator back from tensor memory, applies ReLU
+// while packing the next layer's BF16 input row (layer 1's bias rides in the
+// MMA through the encoding's padding columns, layer 2's is added first); the
+// last layer (64 -> 1) is an N = 16 MMA with w3 in row 0 of its B tile, then
+// b3 and softplus on the CUDA cores.
 //
 // Adjoint (same tiles): delta3 = dL/dz3, delta2 = delta3 w3 * [h2 > 0] and
 // delta1 = (delta2 W2) * [h1 > 0] (an M = 128 MMA against W2^T); the weight
