@@ -156,10 +156,14 @@ size_t nacc_march_unbounded_scratch_bytes(int64_t n_rays, int32_t max_steps);
  * contracted cube (e.g. 4 levels around [-0.25, 0.25]^3 reach [-2, 2]^3).
  * There is no ray-box clip.  Early termination as in nacc_march_grid, with
  * the field at x; the early-stop density keeps the blobs whose integral
- * along the ray line exceeds 1e-7 (peak >= 0 expected).  Every lattice point
- * is tested (no skipping).  Outputs, scratch and capacity as
- * nacc_march_grid (scratch >= nacc_march_unbounded_scratch_bytes(n_rays,
- * max_steps)).
+ * along the ray line exceeds 1e-7 (peak >= 0 expected).  The output is that
+ * of testing every lattice point; runs of 32 points whose contracted segment
+ * is shown (by interval bounds with margins far above FP32 rounding) to lie
+ * within one level and one cell clear of every occupied cell are skipped
+ * without testing.  Outputs, scratch and capacity as nacc_march_grid
+ * (scratch >= nacc_march_unbounded_scratch_bytes(n_rays, max_steps); it
+ * includes 16.25 MiB of "any cell occupied" summaries of the bits over 4^3
+ * and 16^3 blocks, rebuilt by every call).
  */
 int nacc_march_unbounded(const nacc_grid* grid, const float* rays_o, const float* rays_d, int64_t n_rays,
                          const nacc_march_params* params, const nacc_blob_field* field, nacc_packed* out,

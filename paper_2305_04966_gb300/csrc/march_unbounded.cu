@@ -35,6 +35,11 @@ constexpr int kRunSlots = 16;  // recorded runs of consecutive lattice points pe
 constexpr int kBatch = 4;      // lattice points whose grid words are loaded together
 constexpr float kCullEps = 1e-7f;
 constexpr float kMaxContracted = 1.99999988f;  // largest float below 2
+constexpr int kChunk = 32;      // lattice points whose contracted box is tested for emptiness together
+constexpr int kLogF = 2, kLogC = 4;  // "any cell occupied" summaries over 4^3 and 16^3 cells
+constexpr size_t any_bytes(int log) {  // one summary bitfield, sized for 8 levels of 1024^3 cells
+    return size_t(NACC_MAX_LEVELS) * (size_t(1024) >> log) * (size_t(1024) >> log) * (size_t(1024) >> log) / 8;
+}
 
 struct UArgs {
     GridGeom g;
@@ -42,6 +47,9 @@ struct UArgs {
     const float* d;
     const float* tt;  // t_k = Phi(k / K), k = 0..K
     const float* tm;  // (t_k + t_k+1) * 0.5, k = 0..K-1
+    const uint32_t* f_any;  // bit set iff any cell of the 4^3 block is occupied (NULL: no culling)
+    const uint32_t* c_any;  // the same over 16^3 blocks
+    int nbf, nbc;           // blocks per axis
     int64_t n;
     int K;
     float thr;
@@ -267,8 +275,135 @@ __device__ __forceinline__ float sigma_all(const nacc_blob_field& f, const float
     return s;
 }
 
+// Any-occupied summaries: one bit per (1 << kLog)^3 block of cells of each
+// level (partial blocks at the high edge), from the bits, and the coarse one
+// from the fine one.
+__global__ void __launch_bounds__(256) k_unb_fine_summary(GridGeom g, int nb, uint32_t* __restrict__ any) {
+    constexpr int kB = 1 << kLogF;
+    const uint64_t nblocks = (uint64_t)g.n_levels * nb * nb * nb;
+    const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool occ = false;
+    if (b < nblocks) {
+        const int res = g.res;
+        const uint64_t per_level = (uint64_t)nb * nb * nb;
+        const int l = (int)(b / per_level);
+        const uint32_t rem = (uint32_t)(b % per_level);
+        const int bx = rem / (nb * nb), by = (rem / nb) % nb, bz = rem % nb;
+        const uint64_t r3 = (uint64_t)res * res * res;
+        for (int x = bx * kB; x < min(bx * kB + kB, res); ++x)
+            for (int y = by * kB; y < min(by * kB + kB, res); ++y)
+                for (int z = bz * kB; z < min(bz * kB + kB, res); ++z) {
+                    const uint64_t i = (uint64_t)l * r3 + ((uint64_t)x * res + y) * res + z;
+                    occ = occ || ((g.bits[i >> 5] >> (i & 31)) & 1u);
+                }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, occ);
+    if ((threadIdx.x & 31) == 0 && b < nblocks) any[b >> 5] = m;
+}
+
+__global__ void __launch_bounds__(256) k_unb_coarse_summary(int n_levels, int nbc, int nbf,
+                                                            const uint32_t* __restrict__ f_any,
+                                                            uint32_t* __restrict__ c_any) {
+    constexpr int kR = 1 << (kLogC - kLogF);
+    const uint64_t ncb = (uint64_t)n_levels * nbc * nbc * nbc;
+    const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool occ = false;
+    if (b < ncb) {
+        const uint64_t per_level = (uint64_t)nbc * nbc * nbc;
+        const int l = (int)(b / per_level);
+        const uint32_t rem = (uint32_t)(b % per_level);
+        const int bx = rem / (nbc * nbc), by = (rem / nbc) % nbc, bz = rem % nbc;
+        for (int x = bx * kR; x < min(bx * kR + kR, nbf); ++x)
+            for (int y = by * kR; y < min(by * kR + kR, nbf); ++y)
+                for (int z = bz * kR; z < min(bz * kR + kR, nbf); ++z) {
+                    const uint32_t f = (((uint32_t)l * nbf + x) * nbf + y) * nbf + z;
+                    occ = occ || ((__ldg(&f_any[f >> 5]) >> (f & 31)) & 1u);
+                }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, occ);
+    if ((threadIdx.x & 31) == 0 && b < ncb) c_any[b >> 5] = m;
+}
+
+// True if every block of the summary (nb blocks per axis, 1 << log cells)
+// covering cells [ilo, ihi] of level l is empty; false also when more than
+// `cap` blocks would have to be read.
+__device__ __forceinline__ bool blocks_empty(const uint32_t* any, int nb, int log, int l, const int ilo[3],
+                                             const int ihi[3], int cap) {
+    const int b0x = ilo[0] >> log, b1x = ihi[0] >> log, b0y = ilo[1] >> log, b1y = ihi[1] >> log,
+              b0z = ilo[2] >> log, b1z = ihi[2] >> log;
+    if ((b1x - b0x + 1) * (b1y - b0y + 1) * (b1z - b0z + 1) > cap) return false;
+    for (int x = b0x; x <= b1x; ++x)
+        for (int y = b0y; y <= b1y; ++y)
+            for (int z = b0z; z <= b1z; ++z) {
+                const uint32_t b = (((uint32_t)l * nb + x) * nb + y) * nb + z;
+                if ((__ldg(&any[b >> 5]) >> (b & 31)) & 1u) return false;
+            }
+    return true;
+}
+
+// The contraction's scale factor as a function of the max-norm: 1 inside the
+// unit cube, (2 - 1/m)/m beyond (continuous, non-increasing).
+__device__ __forceinline__ float contract_scale(float m) { return m <= 1.0f ? 1.0f : (2.0f - 1.0f / m) / m; }
+
+// True if no lattice point k0..k1 (midpoints tm_k0 <= tm_k <= tm_k1 on the
+// ray) can lie in an occupied cell: the exact contracted segment is bounded
+// per axis by interval products (x_a(t) is linear in t, the max-norm m(t) is
+// bounded by its endpoint values above and by max_a min_t |x_a(t)| below,
+// the scale factor is non-increasing in m), the box is grown by far more
+// than the FP32 rounding of the computed points (1e-5 absolute + 1e-5
+// relative), it must lie inside one level and clear of the next finer
+// level's box, and every cell of that level within one cell of it must be
+// empty.
+__device__ bool chunk_empty(const UArgs& A, const float o[3], const float d[3], float ta, float tb) {
+    float xlo[3], xhi[3], mlo = 0.0f, mhi = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float xa = fmaf(d[a], ta, o[a]), xb = fmaf(d[a], tb, o[a]);
+        const float e = 1e-5f * (fabsf(o[a]) + fabsf(d[a]) * fmaxf(fabsf(ta), fabsf(tb))) + 1e-5f;
+        xlo[a] = fminf(xa, xb) - e;
+        xhi[a] = fmaxf(xa, xb) + e;
+        mhi = fmaxf(mhi, fmaxf(fabsf(xlo[a]), fabsf(xhi[a])));
+        const float amin = (xlo[a] <= 0.0f && xhi[a] >= 0.0f) ? 0.0f : fminf(fabsf(xlo[a]), fabsf(xhi[a]));
+        mlo = fmaxf(mlo, amin);
+    }
+    const float glo = contract_scale(mhi) * (1.0f - 1e-5f), ghi = contract_scale(mlo) * (1.0f + 1e-5f);
+    float clo[3], chi[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float p0 = xlo[a] * glo, p1 = xlo[a] * ghi, p2 = xhi[a] * glo, p3 = xhi[a] * ghi;
+        clo[a] = fminf(fminf(p0, p1), fminf(p2, p3)) - 1e-5f;
+        chi[a] = fmaxf(fmaxf(p0, p1), fmaxf(p2, p3)) + 1e-5f;
+    }
+    const int L = A.g.n_levels;
+    int l = 0;
+    for (; l < L; ++l) {
+        const Level& lv = A.g.lv[l];
+        if (clo[0] >= lv.lmin[0] && chi[0] <= lv.lmax[0] && clo[1] >= lv.lmin[1] && chi[1] <= lv.lmax[1] &&
+            clo[2] >= lv.lmin[2] && chi[2] <= lv.lmax[2])
+            break;
+    }
+    if (l == L) return false;
+    if (l > 0) {  // the box must not reach the next finer level's box
+        const Level& fl = A.g.lv[l - 1];
+        if (chi[0] >= fl.lmin[0] && clo[0] <= fl.lmax[0] && chi[1] >= fl.lmin[1] && clo[1] <= fl.lmax[1] &&
+            chi[2] >= fl.lmin[2] && clo[2] <= fl.lmax[2])
+            return false;
+    }
+    const Level& lv = A.g.lv[l];
+    const int res = A.g.res;
+    int ilo[3], ihi[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        ilo[a] = max((int)floorf((clo[a] - lv.lmin[a]) * lv.scale[a]) - 1, 0);
+        ihi[a] = min((int)floorf((chi[a] - lv.lmin[a]) * lv.scale[a]) + 1, res - 1);
+    }
+    return blocks_empty(A.c_any, A.nbc, kLogC, l, ilo, ihi, 8) ||
+           blocks_empty(A.f_any, A.nbf, kLogF, l, ilo, ihi, 27);
+}
+
 // Count pass: per ray (one thread), the number of occupied lattice points
-// and their runs.
+// and their runs; chunks of kChunk points whose contracted box is empty are
+// skipped whole.
 template <typename I>
 __global__ void __launch_bounds__(kThreads) k_unb_count(UArgs A, int32_t* __restrict__ counts,
                                                         int32_t* __restrict__ kstops, int32_t* __restrict__ nruns,
@@ -281,14 +416,18 @@ __global__ void __launch_bounds__(kThreads) k_unb_count(UArgs A, int32_t* __rest
         const float d[3] = {A.d[3 * r], A.d[3 * r + 1], A.d[3 * r + 2]};
         RunRec q{runs + r * kRunSlots, 0, -1, -1};
         int hint = 0;  // level of the previous batch's last point in the grid
-        for (int kb = 0; kb < A.K; kb += kBatch) {
-            float t[kBatch + 1];
-            const unsigned m = batch_mask<I>(A, o, d, kb, t, hint);
+        for (int kc = 0; kc < A.K; kc += kChunk) {
+            const int ke = min(kc + kChunk, A.K);
+            if (A.f_any && chunk_empty(A, o, d, __ldg(A.tm + kc), __ldg(A.tm + ke - 1))) continue;
+            for (int kb = kc; kb < ke; kb += kBatch) {
+                float t[kBatch + 1];
+                const unsigned m = batch_mask<I>(A, o, d, kb, t, hint);
 #pragma unroll
-            for (int j = 0; j < kBatch; ++j) {
-                if (!((m >> j) & 1u)) continue;
-                rec_point(q, kb + j);
-                ++cnt;
+                for (int j = 0; j < kBatch; ++j) {
+                    if (!((m >> j) & 1u)) continue;
+                    rec_point(q, kb + j);
+                    ++cnt;
+                }
             }
         }
         rec_flush(q);
@@ -647,7 +786,7 @@ extern "C" size_t nacc_march_unbounded_scratch_bytes(int64_t n_rays, int32_t max
     const int64_t nb = (n_rays + kThreads - 1) / kThreads;
     return align256(4 * (size_t)n_rays) * 3 + align256(sizeof(int2) * kRunSlots * (size_t)n_rays) +
            align256(8 * (size_t)(nb > 0 ? nb : 1)) + align256(4 * ((size_t)max_steps + 1)) +
-           align256(4 * (size_t)max_steps);
+           align256(4 * (size_t)max_steps) + align256(any_bytes(kLogF)) + align256(any_bytes(kLogC));
 }
 
 extern "C" int nacc_march_unbounded(const nacc_grid* grid, const float* rays_o, const float* rays_d, int64_t n_rays,
@@ -702,8 +841,25 @@ extern "C" int nacc_march_unbounded(const nacc_grid* grid, const float* rays_o, 
     float* tt = reinterpret_cast<float*>(sp);
     sp += align256(4 * ((size_t)A.K + 1));
     float* tm = reinterpret_cast<float*>(sp);
+    sp += align256(4 * (size_t)A.K);
+    uint32_t* f_any = reinterpret_cast<uint32_t*>(sp);
+    sp += align256(any_bytes(kLogF));
+    uint32_t* c_any = reinterpret_cast<uint32_t*>(sp);
     A.tt = tt;
     A.tm = tm;
+    A.nbf = (A.g.res + (1 << kLogF) - 1) >> kLogF;
+    A.nbc = (A.g.res + (1 << kLogC) - 1) >> kLogC;
+    A.f_any = f_any;
+    A.c_any = c_any;
+    {
+        const int64_t nfb = (int64_t)A.g.n_levels * A.nbf * A.nbf * A.nbf;
+        k_unb_fine_summary<<<(unsigned)((nfb + 255) / 256), 256, 0, st>>>(A.g, A.nbf, f_any);
+        NACC_LAUNCH_CHECK();
+        const int64_t ncb = (int64_t)A.g.n_levels * A.nbc * A.nbc * A.nbc;
+        k_unb_coarse_summary<<<(unsigned)((ncb + 255) / 256), 256, 0, st>>>(A.g.n_levels, A.nbc, A.nbf, f_any,
+                                                                           c_any);
+        NACC_LAUNCH_CHECK();
+    }
     {
         const int K = A.K;
         const int blocks = (int)std::min<int64_t>(((int64_t)K + 1 + 255) / 256, (int64_t)sm_count() * 4);
