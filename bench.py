@@ -416,7 +416,8 @@ def alu_peak_tflops(torch, dev) -> float:
 
 
 def count_pass_flop(S: int, n_blobs: int) -> float:
-    """Algorithmic FP32 work of the march count pass: the early-stop density
+    """Algorithmic FP32 work of the march's count phase (the run walk and the
+    early-stop pass, timed together through the library's event hook): the early-stop density
     at every emitted sample, 11 FLOP per blob (3 differences, |x-mu|^2 as a
     multiply and two FMAs, the exponent scale, the accumulating FMA; the
     exponent itself runs on the special-function unit) plus 14 per sample
@@ -948,7 +949,7 @@ def run_ours(args):
     hbm = hbm or 6800.0
     path_bytes = sum(BYTES[s][0] * S + BYTES[s][1] * n for s in BYTES)
     path_ms = sum(stage_ms[s] for s in BYTES)
-    # the dominant kernel of the method's path: the march count pass (ALU-bound,
+    # the dominant kernel of the method's path: the march count phase (ALU-bound,
     # timed alone through the library's event hook) or an HBM-bound render kernel
     fp32_peak = alu_peak_tflops(torch, dev)
     count_flop = count_pass_flop(S, w.blobs.n)
@@ -956,7 +957,7 @@ def run_ours(args):
               key=lambda s: count_ms if s == "march_count" else stage_ms[s])
     if dom == "march_count":
         achieved = count_flop / (count_ms / 1000.0) / 1e12
-        roofline = {"bound": "alu", "kernel": "k_march_count", "achieved": achieved, "peak": fp32_peak,
+        roofline = {"bound": "alu", "kernel": "k_march_runs+k_march_stop", "achieved": achieved, "peak": fp32_peak,
                     "unit": "TFLOP/s", "frac": achieved / fp32_peak, "ms": count_ms,
                     "peak_source": "derived: SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz",
                     "traffic": recorded_traffic("march_count", S, n), "algorithmic_flop": count_flop}

@@ -27,14 +27,17 @@
 // block's exit -- its 16^3 block if that is uniform, else its 4^3 block if
 // that is (per-call summaries of the bits): the same argument holds for any
 // box of cells whose bits all agree.
-// Empty runs are skipped; occupied runs are emitted point by point with only
-// their t0 / t1 arithmetic (plus the field for early termination), so the
-// emitted set equals the dense march's at a fraction of its cost.  With a
-// field the optical depth of the emitted samples is accumulated in lattice
-// order with one FP32 add per sample (the definition's order); the count
-// pass records where each ray stopped so the fill pass never evaluates the
-// field.  The fill pass buffers each lane's samples in shared memory and
-// flushes the 32 lanes' runs warp-cooperatively as coalesced stores.
+// The count pass visits only run starts: it records each ray's occupied runs
+// and their total, so the emitted set equals the dense march's at a fraction
+// of its cost.  With a field, an early-stop pass gives each ray to a warp,
+// which evaluates the density at the emitted points in lattice order, 64 at
+// a time, and cuts the ray at the first point whose optical depth before it
+// exceeds the threshold (the depth is a warp scan of FP32 sigma dt: the
+// rounding order of the sum differs from a sequential one by a few ulps,
+// which moves only decisions within that of the threshold); the fill pass
+// never evaluates the field.  The fill pass expands the recorded runs
+// warp-cooperatively as coalesced stores (rays whose runs overflowed the
+// slots are re-marched per lane and flushed by the warp).
 #include "nacc_internal.cuh"
 
 namespace nacc {
@@ -213,60 +216,71 @@ __device__ __forceinline__ void sigma_early_stop2(const BlobS* s, int n, const f
     sb = acc_b;
 }
 
-// Early-stop density for fields of few blobs, set up per ray: along the ray
-// x(t) = o + t d, |x(t) - mu_b|^2 = |d|^2 (t - t*_b)^2 + p_b^2 with the
+// Early-stop density along one ray, set up per ray by its warp: along the
+// ray x(t) = o + t d, |x(t) - mu_b|^2 = |d|^2 (t - t*_b)^2 + p_b^2 with the
 // closest approach t*_b = (mu_b - o).d / |d|^2 and p_b^2 = |(mu_b - o) x d|^2
-// / |d|^2 (cross product: no cancellation near the centre).  Each lane keeps
+// / |d|^2 (cross product: no cancellation near the centre).  The table keeps
 // {A_b = c_b |d|^2, t*_b, C_b = c_b p_b^2, peak_b} (c_b the log2-scaled
-// coefficient) in shared memory, and a sample costs one 128-bit load, three
-// FP32 operations, one exp2 and one FMA per blob.  Rounding of t - t*_b is
-// of the order of that of the position in the direct form.
-constexpr int kRayBlobsMax = 16;
+// coefficient) in shared memory, and a sample costs one broadcast 128-bit
+// load, three FP32 operations, one exp2 and one FMA per kept blob.  Rounding
+// of t - t*_b is of the order of that of the position in the direct form.
+constexpr int kTab = 64;  // table entries per ray; a ray with more kept blobs uses the direct form
 
 // Blobs whose integral along the whole ray line is at most kCullEps
 // (bound peak 2^C sqrt(2 pi) std / |d|, C = c_b p_b^2) are left out of the
 // ray's table: each changes the optical depth by at most kCullEps.
 constexpr float kCullEps = 1e-7f;
 
-__device__ __forceinline__ int ray_blobs_setup(const BlobS* sb, int n, const float o[3], const float d[3],
-                                               float4* q) {
-    const int lane = threadIdx.x & 31;
+// Builds the table of one ray (o, d) from the n staged blobs, lane b0 + lane
+// handling blob b0 + lane, kept blobs compacted in blob order.  Returns the
+// number of kept blobs, or -1 if more than kTab are kept (no table).
+__device__ int build_ray_table(const BlobS* sb, int n, const float o[3], const float d[3], float4* tab, int lane) {
     const float dd = fmaf(d[2], d[2], fmaf(d[1], d[1], d[0] * d[0]));
     const float idd = dd > 0.0f ? 1.0f / dd : 0.0f;
     const float ilen = dd > 0.0f ? rsqrtf(dd) : 0.0f;
-    int nq = 0;
-    for (int b = 0; b < n; ++b) {
-        const BlobS v = sb[b];
-        const float m0 = v.mx - o[0], m1 = v.my - o[1], m2 = v.mz - o[2];
-        float ts, pp;
-        if (dd > 0.0f) {
-            const float md = fmaf(m2, d[2], fmaf(m1, d[1], m0 * d[0]));
-            const float cx = fmaf(m1, d[2], -m2 * d[1]);
-            const float cy = fmaf(m2, d[0], -m0 * d[2]);
-            const float cz = fmaf(m0, d[1], -m1 * d[0]);
-            ts = md * idd;
-            pp = fmaf(cz, cz, fmaf(cy, cy, cx * cx)) * idd;
-        } else {  // a ray that does not move: the distance is |mu - o|
-            ts = 0.0f;
-            pp = fmaf(m2, m2, fmaf(m1, m1, m0 * m0));
+    int nt = 0;
+    for (int b0 = 0; b0 < n; b0 += 32) {
+        const int b = b0 + lane;
+        bool keep = false;
+        float4 ent = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (b < n) {
+            const BlobS v = sb[b];
+            const float m0 = v.mx - o[0], m1 = v.my - o[1], m2 = v.mz - o[2];
+            float ts, pp;
+            if (dd > 0.0f) {
+                const float md = fmaf(m2, d[2], fmaf(m1, d[1], m0 * d[0]));
+                const float cx = fmaf(m1, d[2], -m2 * d[1]);
+                const float cy = fmaf(m2, d[0], -m0 * d[2]);
+                const float cz = fmaf(m0, d[1], -m1 * d[0]);
+                ts = md * idd;
+                pp = fmaf(cz, cz, fmaf(cy, cy, cx * cx)) * idd;
+            } else {  // a ray that does not move: the distance is |mu - o|
+                ts = 0.0f;
+                pp = fmaf(m2, m2, fmaf(m1, m1, m0 * m0));
+            }
+            const float C = v.coef * pp;
+            keep = true;
+            if (dd > 0.0f) {
+                const float sd = sqrtf(-0.72134752f / v.coef);  // coef = -log2(e) / (2 std^2)
+                keep = v.peak * ex2_approx(C) * 2.5066283f * sd * ilen > kCullEps;
+            }
+            ent = make_float4(v.coef * dd, ts, C, v.peak);
         }
-        const float C = v.coef * pp;
-        if (dd > 0.0f) {
-            const float sd = sqrtf(-0.72134752f / v.coef);  // coef = -log2(e) / (2 std^2)
-            if (!(v.peak * ex2_approx(C) * 2.5066283f * sd * ilen > kCullEps)) continue;
-        }
-        q[nq * 32 + lane] = make_float4(v.coef * dd, ts, C, v.peak);
-        ++nq;
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        const int pos = nt + __popc(bal & ((1u << lane) - 1u));
+        if (keep && pos < kTab) tab[pos] = ent;
+        nt += __popc(bal);
     }
-    return nq;
+    return nt <= kTab ? nt : -1;
 }
 
-__device__ __forceinline__ void sigma_ray2(const float4* q, int n, float ta, float tb, float& sa, float& sb) {
-    const int lane = threadIdx.x & 31;
+// Density at ray parameters ta, tb from the ray's table (every lane reads
+// the same entry: a shared-memory broadcast).
+__device__ __forceinline__ void sigma_tab2(const float4* tab, int nt, float ta, float tb, float& sa, float& sb) {
     float acc_a = 0.0f, acc_b = 0.0f;
 #pragma unroll 4
-    for (int b = 0; b < n; ++b) {
-        const float4 v = q[b * 32 + lane];
+    for (int b = 0; b < nt; ++b) {
+        const float4 v = tab[b];
         const float ua = ta - v.y, ub = tb - v.y;
         acc_a = fmaf(v.w, ex2_approx(fmaf(v.x * ua, ua, v.z)), acc_a);
         acc_b = fmaf(v.w, ex2_approx(fmaf(v.x * ub, ub, v.z)), acc_b);
@@ -331,11 +345,6 @@ __device__ __forceinline__ void rec_run(RunRec& q, int k0, int k1) {
     q.k1 = k1;
 }
 
-// Advance the march of one ray: append the lattice indices of its occupied
-// points k < kend, in order, to buf[0..kBuf) (at most `limit` in total) and
-// return when the buffer is full or the ray is finished.  With a recorder,
-// every occupied cell run is also recorded whole: the emitted points are the
-// first n points of the recorded ranges, in order.
 __device__ __forceinline__ bool cell_bit(const MarchArgs& A, int l, int x, int y, int z) {
     const uint32_t res = (uint32_t)A.g.res;
     const uint32_t idx = ((uint32_t)l * res + (uint32_t)x) * res * res + (uint32_t)y * res + (uint32_t)z;
@@ -418,8 +427,10 @@ __device__ __forceinline__ void run_box(const MarchArgs& A, const Ray& R, int l,
     }
 }
 
-template <bool kRec>
-__device__ void advance(const MarchArgs& A, Lane& s, int kend, int limit, int* buf, int& bn, RunRec* q) {
+// Advance the march of one ray: append the lattice indices of its occupied
+// points k < kend, in order, to buf[0..kBuf) (at most `limit` in total) and
+// return when the buffer is full or the ray is finished.
+__device__ void advance(const MarchArgs& A, Lane& s, int kend, int limit, int* buf, int& bn) {
     const int L = A.g.n_levels;
     while (!s.done && bn < kBuf) {
         if (s.k >= s.run_end) {  // start a new cell run at s.k
@@ -446,7 +457,6 @@ __device__ void advance(const MarchArgs& A, Lane& s, int kend, int limit, int* b
                 s.k = s.run_end;
                 continue;
             }
-            if (kRec) rec_run(*q, s.k, s.run_end);
         }
         // the points of the occupied run, as many as the buffer takes (one run
         // per outer iteration keeps the run starts of the warp's lanes aligned)
@@ -511,112 +521,230 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// Count pass.  Each lane marches into its buffer; with a field the warp
-// then evaluates the density of the buffered samples together (converged)
-// and each lane folds them into its optical depth in lattice order, stopping
-// at the first sample whose depth before it exceeds the threshold.
-// kField: 0 no field, 1 blobs read per sample, 2 per-ray closed form (few blobs).
-template <int kField>
-__global__ void __launch_bounds__(kBlockThreads, 32)
-    k_march_count(MarchArgs A, int32_t* __restrict__ counts, int32_t* __restrict__ kstops,
-                  int32_t* __restrict__ nruns, float* __restrict__ tnear, int2* __restrict__ runs,
-                  long long* __restrict__ block_sums) {
-    extern __shared__ BlobS s_blobs[];
-    __shared__ int s_buf[kBlockThreads][kBuf + 1];
-    float4* s_q = reinterpret_cast<float4*>(s_blobs + A.field.n_blobs);  // kField 2: [blob][lane]
-    if (kField) {
-        stage_blobs(s_blobs, A.field, false);
-        for (int b = threadIdx.x; b < A.field.n_blobs; b += blockDim.x)
-            s_blobs[b].coef *= 1.4426950408889634f;  // log2 e
+// K_end of a ray: the first lattice index k whose t0 = t_near + k dt is not
+// below t_far, or max_steps (t0 is monotone in k: binary search).
+__device__ __forceinline__ int lattice_end(const MarchArgs& A, const Ray& R) {
+    int lo = 0, hi = A.max_steps;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (__fadd_rn(R.tn, __fmul_rn((float)mid, A.step)) < R.tf)
+            lo = mid + 1;
+        else
+            hi = mid;
     }
-    __syncthreads();
-    const int64_t r = (int64_t)blockIdx.x * kBlockThreads + threadIdx.x;
-    Lane s;
-    s.done = true;
-    s.n = 0;
-    s.R.tn = 0.0f;
-    int nq = 0;  // kField 2: blobs in this ray's table
-    if (r < A.n && lane_init(A, r, s) && kField == 2)
-        nq = ray_blobs_setup(s_blobs, A.field.n_blobs, s.R.o, s.R.d, s_q);
-    RunRec q{runs + (r < A.n ? r : 0) * kRunSlots, 0, -1, -1};
-    int* buf = s_buf[threadIdx.x];
-    int cnt = 0, kstop = A.max_steps;
-    float tau = 0.0f;
-    bool stopped = false;
-    while (true) {
-        int bn = 0;
-        if (!s.done && !stopped) advance<true>(A, s, A.max_steps, 0x7fffffff, buf, bn, &q);
-        if (!kField) {
-            cnt += bn;
-        } else {
-            __syncwarp();
-            int nmax = bn;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
-            // two buffered samples per step; the depth is still folded in one
-            // sample at a time, in lattice order (a density evaluated for a
-            // sample past the stop is discarded)
-            for (int j = 0; j < nmax; j += 2) {
-                if (j < bn && !stopped) {
-                    const bool two = j + 1 < bn;
-                    const int ka = buf[j], kb = two ? buf[j + 1] : ka;
-                    const float ta0 = __fadd_rn(s.R.tn, __fmul_rn((float)ka, A.step));
-                    const float ta1 = __fadd_rn(ta0, A.step);
-                    const float tb0 = __fadd_rn(s.R.tn, __fmul_rn((float)kb, A.step));
-                    const float tb1 = __fadd_rn(tb0, A.step);
-                    const float tma = 0.5f * (ta0 + ta1), tmb = 0.5f * (tb0 + tb1);
-                    float sga, sgb;
-                    if (kField == 2) {
-                        sigma_ray2(s_q, nq, tma, tmb, sga, sgb);
-                    } else {
-                        float xa[3], xb[3];
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            xa[a] = fmaf(s.R.d[a], tma, s.R.o[a]);
-                            xb[a] = fmaf(s.R.d[a], tmb, s.R.o[a]);
-                        }
-                        sigma_early_stop2(s_blobs, A.field.n_blobs, xa, xb, sga, sgb);
-                    }
-                    if (tau > A.thr) {
-                        stopped = true;
-                        kstop = ka;
-                    } else {
-                        tau = __fadd_rn(tau, __fmul_rn(sga, __fsub_rn(ta1, ta0)));
-                        ++cnt;
-                        if (two) {
-                            if (tau > A.thr) {
-                                stopped = true;
-                                kstop = kb;
-                            } else {
-                                tau = __fadd_rn(tau, __fmul_rn(sgb, __fsub_rn(tb1, tb0)));
-                                ++cnt;
-                            }
-                        }
-                    }
+    return lo;
+}
+
+// Count pass: one thread per ray walks its cell runs up to K_end without
+// visiting the points inside a run, and records the occupied runs ({first
+// k, count}, merged when they continue one another) and their total.
+// kstops[r] = K_end; the per-32-ray totals go to block_sums.
+constexpr int kRunsThreads = 128;
+__global__ void __launch_bounds__(kRunsThreads)
+    k_march_runs(MarchArgs A, int32_t* __restrict__ counts, int32_t* __restrict__ kstops,
+                 int32_t* __restrict__ nruns, float* __restrict__ tnear, int2* __restrict__ runs,
+                 long long* __restrict__ block_sums) {
+    const int lane = threadIdx.x & 31;
+    const int64_t r = (int64_t)blockIdx.x * kRunsThreads + threadIdx.x;
+    int cnt = 0;
+    if (r < A.n) {
+        Lane s;
+        s.R.tn = 0.0f;
+        const bool hit = lane_init(A, r, s);
+        RunRec q{runs + r * kRunSlots, 0, -1, -1};
+        int ke = 0;
+        if (hit) {
+            ke = lattice_end(A, s.R);
+            const int L = A.g.n_levels;
+            int k = 0;
+            while (k < ke) {
+                float t0, t1, x[3];
+                int l, ic[3];
+                const bool occ = lattice_point(A, s.R, k, t0, t1, x, l, ic);
+                int run_end = k + 1;
+                if (l < L) {
+                    int lo[3], hi[3];
+                    run_box(A, s.R, l, ic, occ, lo, hi);  // a cell in a uniform block: the run spans the block
+                    run_end = skip_target(A, s.R, k, __fmul_rn(__fadd_rn(t0, t1), 0.5f), l, lo, hi, ke);
                 }
+                if (occ) {
+                    rec_run(q, k, run_end);
+                    cnt += run_end - k;
+                }
+                k = run_end;
             }
         }
-        if (__all_sync(0xffffffffu, s.done || stopped)) break;
-    }
-    if (r < A.n) {
         rec_flush(q);
         counts[r] = cnt;
-        kstops[r] = kstop;
+        kstops[r] = ke;
         nruns[r] = q.n;
         tnear[r] = s.R.tn;
     }
-    __shared__ int s_w[kWarpsPerBlock];
     int v = cnt;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
+    const int64_t r0 = r - lane;
+    if (lane == 0 && r0 < A.n) block_sums[r0 / kRaysPerBlock] = v;
+}
+
+// Early termination (with a field, after the count pass): each warp takes
+// the 32 rays of one block-sum entry in turn.  The lanes build the ray's
+// table, then visit its points in lattice order 64 at a time (two
+// consecutive points per lane, from the recorded runs; a ray whose runs
+// overflowed the slots walks the lattice 32 points at a time up to K_end);
+// each lane adds its points' sigma dt, a warp scan gives the optical depth
+// before each point, and the first point whose depth before it exceeds the
+// threshold cuts the ray: counts[r] and kstops[r] (its lattice index) are
+// rewritten, and so is the entry's total.
+constexpr int kStopThreads = 128;
+constexpr int kStopWarps = kStopThreads / 32;
+__global__ void __launch_bounds__(kStopThreads)
+    k_march_stop(MarchArgs A, int32_t* __restrict__ counts, int32_t* __restrict__ kstops,
+                 const int32_t* __restrict__ nruns, const float* __restrict__ tnear,
+                 const int2* __restrict__ runs, long long* __restrict__ block_sums) {
+    extern __shared__ BlobS s_blobs[];
+    __shared__ float4 s_tab[kStopWarps][kTab];
+    stage_blobs(s_blobs, A.field, false);
+    for (int b = threadIdx.x; b < A.field.n_blobs; b += blockDim.x)
+        s_blobs[b].coef *= 1.4426950408889634f;  // log2 e
     __syncthreads();
-    if (threadIdx.x == 0) {
-        long long t = 0;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t cb = (int64_t)blockIdx.x * kStopWarps + wid;  // this warp's block-sum entry
+    const int64_t rbase = cb * kRaysPerBlock;
+    if (rbase >= A.n) return;
+    float4* tab = s_tab[wid];
+    const int nblobs = A.field.n_blobs;
+    int wsum = 0;
+    for (int i = 0; i < kRaysPerBlock; ++i) {
+        const int64_t r = rbase + i;
+        if (r >= A.n) break;
+        const int cnt = counts[r];
+        if (cnt == 0) continue;
+        const float o[3] = {__ldg(A.o + 3 * r), __ldg(A.o + 3 * r + 1), __ldg(A.o + 3 * r + 2)};
+        const float d[3] = {__ldg(A.d + 3 * r), __ldg(A.d + 3 * r + 1), __ldg(A.d + 3 * r + 2)};
+        const int nt = build_ray_table(s_blobs, nblobs, o, d, tab, lane);
+        __syncwarp();
+        int cut = cnt, kstop = kstops[r];
+        if (nt != 0) {
+            const int nr = nruns[r];
+            const float tn = tnear[r];
+            float carry = 0.0f;
+            if (nr >= 0) {
+                const int2 run = lane < nr ? runs[r * kRunSlots + lane] : make_int2(0, 0);
+                int ex = run.y;  // -> exclusive prefix of the run lengths
 #pragma unroll
-        for (int w = 0; w < kWarpsPerBlock; ++w) t += s_w[w];
-        block_sums[blockIdx.x] = t;
+                for (int o2 = 1; o2 < 32; o2 <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, ex, o2);
+                    if (lane >= o2) ex += y;
+                }
+                ex -= run.y;
+                for (int p0 = 0; p0 < cnt; p0 += 64) {
+                    const int pa = p0 + 2 * lane, pb = pa + 1;
+                    int ka = 0, kb = 0;
+                    for (int j = 0; j < nr; ++j) {
+                        const int ej = __shfl_sync(0xffffffffu, ex, j);
+                        const int kj = __shfl_sync(0xffffffffu, run.x, j);
+                        if (pa >= ej) ka = kj + (pa - ej);
+                        if (pb >= ej) kb = kj + (pb - ej);
+                    }
+                    float taua = 0.0f, taub = 0.0f;
+                    if (pa < cnt) {
+                        const bool two = pb < cnt;
+                        const float a0 = __fadd_rn(tn, __fmul_rn((float)ka, A.step)), a1 = __fadd_rn(a0, A.step);
+                        const float b0 = __fadd_rn(tn, __fmul_rn((float)(two ? kb : ka), A.step)),
+                                    b1 = __fadd_rn(b0, A.step);
+                        const float tma = __fmul_rn(__fadd_rn(a0, a1), 0.5f), tmb = __fmul_rn(__fadd_rn(b0, b1), 0.5f);
+                        float sa, sb;
+                        if (nt > 0) {
+                            sigma_tab2(tab, nt, tma, tmb, sa, sb);
+                        } else {
+                            float xa[3], xb[3];
+#pragma unroll
+                            for (int a = 0; a < 3; ++a) {
+                                xa[a] = fmaf(d[a], tma, o[a]);
+                                xb[a] = fmaf(d[a], tmb, o[a]);
+                            }
+                            sigma_early_stop2(s_blobs, nblobs, xa, xb, sa, sb);
+                        }
+                        taua = __fmul_rn(sa, __fsub_rn(a1, a0));
+                        if (two) taub = __fmul_rn(sb, __fsub_rn(b1, b0));
+                    }
+                    const float pair = taua + taub;
+                    float x = pair;  // -> inclusive prefix over the lanes' pairs
+#pragma unroll
+                    for (int o2 = 1; o2 < 32; o2 <<= 1) {
+                        const float y = __shfl_up_sync(0xffffffffu, x, o2);
+                        if (lane >= o2) x += y;
+                    }
+                    const float before_a = carry + (x - pair), before_b = before_a + taua;
+                    const unsigned over_a = __ballot_sync(0xffffffffu, pa < cnt && before_a > A.thr);
+                    const unsigned over_b = __ballot_sync(0xffffffffu, pb < cnt && before_b > A.thr);
+                    if (over_a | over_b) {  // the first point past the threshold, in lattice order
+                        const int ja = over_a ? __ffs(over_a) - 1 : 32, jb = over_b ? __ffs(over_b) - 1 : 32;
+                        const bool at_a = ja <= jb;
+                        const int j = at_a ? ja : jb;
+                        cut = p0 + 2 * j + (at_a ? 0 : 1);
+                        kstop = __shfl_sync(0xffffffffu, at_a ? ka : kb, j);
+                        break;
+                    }
+                    carry += __shfl_sync(0xffffffffu, x, 31);
+                }
+            } else {
+                Lane s;
+                s.R.tn = 0.0f;
+                lane_init(A, r, s);  // the count pass found this ray inside the grid
+                const int ke = kstop;
+                int seen = 0;
+                for (int kb = 0; kb < ke && seen < cnt; kb += 32) {
+                    const int k = kb + lane;
+                    bool occ = false;
+                    float t0 = 0.0f, t1 = 0.0f, xp[3];
+                    if (k < ke) {
+                        int l, ic[3];
+                        occ = lattice_point(A, s.R, k, t0, t1, xp, l, ic);
+                    }
+                    const unsigned m = __ballot_sync(0xffffffffu, occ);
+                    if (!m) continue;
+                    float tau = 0.0f;
+                    if (occ) {
+                        const float tm = __fmul_rn(__fadd_rn(t0, t1), 0.5f);
+                        float sg, unused;
+                        if (nt > 0) {
+                            sigma_tab2(tab, nt, tm, tm, sg, unused);
+                        } else {
+                            float xa[3];
+#pragma unroll
+                            for (int a = 0; a < 3; ++a) xa[a] = fmaf(d[a], tm, o[a]);
+                            sigma_early_stop2(s_blobs, nblobs, xa, xa, sg, unused);
+                        }
+                        tau = __fmul_rn(sg, __fsub_rn(t1, t0));
+                    }
+                    float x = tau;
+#pragma unroll
+                    for (int o2 = 1; o2 < 32; o2 <<= 1) {
+                        const float y = __shfl_up_sync(0xffffffffu, x, o2);
+                        if (lane >= o2) x += y;
+                    }
+                    const unsigned over = __ballot_sync(0xffffffffu, occ && carry + (x - tau) > A.thr);
+                    if (over) {
+                        const int j = __ffs(over) - 1;
+                        cut = seen + __popc(m & ((1u << j) - 1u));
+                        kstop = kb + j;
+                        break;
+                    }
+                    seen += __popc(m);
+                    carry += __shfl_sync(0xffffffffu, x, 31);
+                }
+            }
+        }
+        if (lane == 0) {
+            counts[r] = cut;
+            kstops[r] = kstop;
+        }
+        wsum += cut;
+        __syncwarp();  // the next ray rewrites the table
     }
+    if (lane == 0) block_sums[cb] = wsum;
 }
 
 // Single block: exclusive scan of the per-block totals in place; writes the
@@ -741,7 +869,7 @@ __global__ void __launch_bounds__(kBlockThreads)
     const int kend = nr < 0 ? kstops[r] : 0;
     while (true) {
         int bn = 0;
-        if (!s.done) advance<false>(A, s, kend, cnt, buf, bn, nullptr);
+        if (!s.done) advance(A, s, kend, cnt, buf, bn);
         __syncwarp();
         unsigned m = __ballot_sync(0xffffffffu, bn > 0);
         while (m) {
@@ -781,12 +909,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_occupied_range(MarchArgs A, f
     const bool hit = lane_init(A, r, s);
     int first = -1, last = -1;
     if (hit) {
-        auto t0_of = [&](int k) { return __fadd_rn(s.R.tn, __fmul_rn((float)k, A.step)); };
-        // K_end = min(max_steps, first k with t0 >= t_far): estimate, then step (t0 is monotone in k)
-        const float q = (s.R.tf - s.R.tn) * A.inv_step;
-        int ke = q < (float)A.max_steps ? (int)fmaxf(floorf(q) - 2.0f, 0.0f) : A.max_steps;
-        for (int it = 0; it < 8 && ke > 0 && !(t0_of(ke - 1) < s.R.tf); ++it) --ke;
-        while (ke < A.max_steps && t0_of(ke) < s.R.tf) ++ke;
+        const int ke = lattice_end(A, s.R);
         const int L = A.g.n_levels;
         int k = 0;
         while (k < ke) {
@@ -969,19 +1092,17 @@ extern "C" int nacc_march_grid(const nacc_grid* grid, const float* rays_o, const
         if (rc != NACC_OK) return rc;
     }
     if (g_count_ev[0]) NACC_CUDA_TRY(cudaEventRecord(g_count_ev[0], st));
-    if (with_field && A.field.n_blobs <= kRayBlobsMax) {
-        const size_t shm = (sizeof(BlobS) + 32 * sizeof(float4)) * (size_t)A.field.n_blobs;
-        k_march_count<2><<<(unsigned)nb, kBlockThreads, shm, st>>>(A, counts, kstops, nruns, tnear, runs, bsums);
-    } else if (with_field) {
-        const size_t shm = sizeof(BlobS) * (size_t)A.field.n_blobs;
-        if (shm > 48 * 1024)
-            NACC_CUDA_TRY(cudaFuncSetAttribute(k_march_count<1>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-        k_march_count<1><<<(unsigned)nb, kBlockThreads, shm, st>>>(A, counts, kstops, nruns, tnear, runs, bsums);
-    } else {
-        k_march_count<0><<<(unsigned)nb, kBlockThreads, 0, st>>>(A, counts, kstops, nruns, tnear, runs, bsums);
-    }
+    k_march_runs<<<(unsigned)((n_rays + kRunsThreads - 1) / kRunsThreads), kRunsThreads, 0, st>>>(
+        A, counts, kstops, nruns, tnear, runs, bsums);
     NACC_LAUNCH_CHECK();
+    if (with_field) {
+        const size_t shm = sizeof(BlobS) * (size_t)A.field.n_blobs;
+        if (shm > 32 * 1024)
+            NACC_CUDA_TRY(cudaFuncSetAttribute(k_march_stop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+        k_march_stop<<<(unsigned)((nb + kStopWarps - 1) / kStopWarps), kStopThreads, shm, st>>>(A, counts, kstops, nruns,
+                                                                                             tnear, runs, bsums);
+        NACC_LAUNCH_CHECK();
+    }
     if (g_count_ev[1]) NACC_CUDA_TRY(cudaEventRecord(g_count_ev[1], st));
     k_scan_block_sums<<<1, 1024, 0, st>>>(bsums, nb, out->offsets + n_rays, out->n_samples);
     NACC_LAUNCH_CHECK();
