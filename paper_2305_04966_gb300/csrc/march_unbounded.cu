@@ -252,13 +252,40 @@ __device__ __forceinline__ float sigma_table(const float4* tab, int nt, float tm
     return s;
 }
 
-__device__ __forceinline__ void sigma_table2(const float4* tab, int nt, float tma, float tmb, float& sa, float& sb) {
+// A table entry contributes to the optical depth of a group of points whose
+// midpoints lie in [t_lo, t_hi] and whose intervals sum to at most span at
+// most (its density at the point of [t_lo, t_hi] nearest its closest
+// approach, the largest there) x span; entries below kGroupEps are left out
+// for that group.  Over a ray of at most 2^24 points in groups of 64, with
+// at most kStopTable entries, that moves the optical depth by at most
+// 6.7e-3 (and by 4.1e-7 at 1,024 points): only decisions within that of
+// the threshold.
+constexpr float kGroupEps = 1e-10f;
+
+// The table's density at two points, summing only the entries that the
+// bound above keeps for the warp's group (each lane tests one entry, the
+// warp takes the kept ones in table order); every lane of the warp calls
+// it, `active` lanes get sums.
+__device__ __forceinline__ void sigma_table2_group(const float4* tab, int nt, float t_lo, float t_hi, float span,
+                                                   float tma, float tmb, float& sa, float& sb, bool active,
+                                                   int lane) {
     float a = 0.0f, b = 0.0f;
-    for (int i = 0; i < nt; ++i) {
-        const float4 v = tab[i];
-        const float ua = tma - v.y, ub = tmb - v.y;
-        a += ex2_approx(fmaf(v.x * ua, ua, v.z));
-        b += ex2_approx(fmaf(v.x * ub, ub, v.z));
+    for (int e0 = 0; e0 < nt; e0 += 32) {
+        bool on = false;
+        if (e0 + lane < nt) {
+            const float4 v = tab[e0 + lane];
+            const float u = fminf(fmaxf(v.y, t_lo), t_hi) - v.y;
+            on = ex2_approx(fmaf(v.x * u, u, v.z)) * span > kGroupEps;
+        }
+        unsigned m = __ballot_sync(0xffffffffu, on);
+        if (!active) continue;
+        while (m) {
+            const float4 v = tab[e0 + __ffs(m) - 1];
+            m &= m - 1;
+            const float ua = tma - v.y, ub = tmb - v.y;
+            a += ex2_approx(fmaf(v.x * ua, ua, v.z));
+            b += ex2_approx(fmaf(v.x * ub, ub, v.z));
+        }
     }
     sa = a;
     sb = b;
@@ -505,14 +532,21 @@ __global__ void __launch_bounds__(kThreads) k_unb_stop(UArgs A, int32_t* __restr
                     if (pb >= ej) kb = kj + (pb - ej);
                 }
                 float taua = 0.0f, taub = 0.0f;
+                const bool two = pb < cnt;
+                const float a0 = __ldg(A.tt + ka), a1 = __ldg(A.tt + ka + 1);
+                const float b0 = two ? __ldg(A.tt + kb) : a0, b1 = two ? __ldg(A.tt + kb + 1) : a1;
+                const float tca = 0.5f * (a0 + a1), tcb = 0.5f * (b0 + b1);
+                float sa = 0.0f, sb = 0.0f;
+                if (nt > 0) {  // the group's midpoints span [first, last] (lattice order)
+                    const int last = min(cnt - p0, 64) - 1;
+                    const float t_lo = __shfl_sync(0xffffffffu, tca, 0);
+                    const float t_hi = __shfl_sync(0xffffffffu, (last & 1) ? tcb : tca, last >> 1);
+                    const float t_end = __shfl_sync(0xffffffffu, (last & 1) ? b1 : a1, last >> 1);
+                    const float span = t_end - __shfl_sync(0xffffffffu, a0, 0);
+                    sigma_table2_group(tab, nt, t_lo, t_hi, span, tca, tcb, sa, sb, pa < cnt, lane);
+                }
                 if (pa < cnt) {
-                    const float a0 = __ldg(A.tt + ka), a1 = __ldg(A.tt + ka + 1);
-                    const bool two = pb < cnt;
-                    const float b0 = two ? __ldg(A.tt + kb) : a0, b1 = two ? __ldg(A.tt + kb + 1) : a1;
-                    float sa, sb;
-                    if (nt >= 0) {
-                        sigma_table2(tab, nt, 0.5f * (a0 + a1), 0.5f * (b0 + b1), sa, sb);
-                    } else {
+                    if (nt < 0) {
                         const float tma = __ldg(A.tm + ka), tmb = __ldg(A.tm + (two ? kb : ka));
                         const float xa[3] = {__fadd_rn(o[0], __fmul_rn(d[0], tma)), __fadd_rn(o[1], __fmul_rn(d[1], tma)),
                                              __fadd_rn(o[2], __fmul_rn(d[2], tma))};
