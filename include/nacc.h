@@ -125,8 +125,10 @@ size_t nacc_march_scratch_bytes(int64_t n_rays);
  * accumulated optical depth sum(sigma*(t1-t0)) over the samples before it
  * exceeds -ln(eps) (T < eps).  Directions are used as given (not normalised).
  *
- * rays_o, rays_d: [device] [n_rays][3].  out: see nacc_packed.  scratch:
- * [device] >= nacc_march_scratch_bytes(n_rays) bytes, 256-byte aligned.
+ * rays_o, rays_d: [device] [n_rays][3].  out: see nacc_packed; t_starts,
+ * t_ends and ray_indices 16-byte aligned (the samples are written as 128-bit
+ * stores).  scratch: [device] >= nacc_march_scratch_bytes(n_rays) bytes,
+ * 256-byte aligned.
  * Capacity: if out->capacity >= n_rays*max_steps no overflow is possible and
  * the call never synchronises (CUDA-graph capturable).  Otherwise the call
  * synchronises `stream` after counting; if the total exceeds the capacity it
