@@ -728,18 +728,41 @@ __global__ void __launch_bounds__(kThreads) k_unb_fill(UArgs A, const int32_t* _
             if (lane >= o) ex += y;
         }
         ex -= run.y;
-        for (int p0 = 0; p0 < cj; p0 += 32) {
-            const int p = p0 + lane;
-            int k = p;
+        // lane l writes positions q..q+3, q = 4l + a multiple of 128 from pj
+        // rounded down to a multiple of 4: groups of four inside the ray as
+        // one 128-bit store per array, the ragged head and tail position by
+        // position (nothing outside the ray is read from the table or written)
+        const long long a4 = pj & ~3ll, pend = pj + cj;
+        for (long long q0 = a4; q0 < pend; q0 += 128) {
+            const long long q = q0 + 4 * lane;
+            const int p0 = (int)(q - pj);  // sample index of position q within the ray (may be < 0)
+            int k[4] = {p0, p0 + 1, p0 + 2, p0 + 3};
             for (int i = 0; i < nj; ++i) {
                 const int ei = __shfl_sync(0xffffffffu, ex, i);
                 const int ki = __shfl_sync(0xffffffffu, run.x, i);
-                if (p >= ei) k = ki + (p - ei);
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (p0 + u >= ei) k[u] = ki + (p0 + u - ei);
             }
-            if (p < cj) {
-                t0s[pj + p] = __ldg(A.tt + k);
-                t1s[pj + p] = __ldg(A.tt + k + 1);
-                if (ray_idx) ray_idx[pj + p] = (int32_t)rj;
+            float t0[4], t1[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const bool in = p0 + u >= 0 && p0 + u < cj;
+                t0[u] = in ? __ldg(A.tt + k[u]) : 0.0f;
+                t1[u] = in ? __ldg(A.tt + k[u] + 1) : 0.0f;
+            }
+            if (q >= pj && q + 4 <= pend) {
+                *reinterpret_cast<float4*>(t0s + q) = make_float4(t0[0], t0[1], t0[2], t0[3]);
+                *reinterpret_cast<float4*>(t1s + q) = make_float4(t1[0], t1[1], t1[2], t1[3]);
+                if (ray_idx) *reinterpret_cast<int4*>(ray_idx + q) = make_int4((int)rj, (int)rj, (int)rj, (int)rj);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (q + u < pj || q + u >= pend) continue;
+                    t0s[q + u] = t0[u];
+                    t1s[q + u] = t1[u];
+                    if (ray_idx) ray_idx[q + u] = (int32_t)rj;
+                }
             }
         }
     }
@@ -838,6 +861,9 @@ extern "C" int nacc_march_unbounded(const nacc_grid* grid, const float* rays_o, 
     NACC_CHECK_ARG(out->offsets && out->n_samples, "out->offsets / out->n_samples is NULL");
     NACC_CHECK_ARG(out->capacity >= 0 && (out->capacity == 0 || (out->t_starts && out->t_ends)),
                    "out->t_starts / out->t_ends is NULL");
+    NACC_CHECK_ARG(((reinterpret_cast<uintptr_t>(out->t_starts) | reinterpret_cast<uintptr_t>(out->t_ends) |
+                     reinterpret_cast<uintptr_t>(out->ray_indices)) & 15) == 0,
+                   "out->t_starts, t_ends and ray_indices must be 16-byte aligned");
     const bool with_field = field != nullptr && field->n_blobs > 0 && params->early_stop_eps > 0.0f;
     if (with_field) {
         NACC_CHECK_ARG(field->n_blobs <= kMaxBlobs, "n_blobs=%d > %d", field->n_blobs, kMaxBlobs);
