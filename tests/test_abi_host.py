@@ -88,6 +88,16 @@ def test_invalid_arguments_are_rejected_on_the_host(lib):
     assert lib.nacc_march_grid(ctypes.byref(g), None, None, 10, ctypes.byref(bad), None,
                                ctypes.byref(out), None, 0, None) == _abi.NACC_ERR_INVALID_ARG
     assert b"step" in lib.nacc_last_error()
+    # sample arrays not 16-byte aligned (the fill writes 128-bit stores): rejected before any launch
+    unaligned = _abi.Packed(256, 260, 512, 768, 10, 1024)
+    assert lib.nacc_march_grid(ctypes.byref(g), None, None, 10, ctypes.byref(p), None,
+                               ctypes.byref(unaligned), None, 0, None) == _abi.NACC_ERR_INVALID_ARG
+    assert b"16-byte" in lib.nacc_last_error()
+    up = _abi.MarchParams(0.01, 1024, 0.2, 1000.0, 1e-4)
+    unaligned = _abi.Packed(256, 256, 520, 768, 10, 1024)
+    assert lib.nacc_march_unbounded(ctypes.byref(g), None, None, 10, ctypes.byref(up), None,
+                                    ctypes.byref(unaligned), None, 0, None) == _abi.NACC_ERR_INVALID_ARG
+    assert b"16-byte" in lib.nacc_last_error()
     # render: NULL offsets / bg
     bg = (ctypes.c_float * 3)(1, 1, 1)
     assert lib.nacc_render_fwd(4, None, None, None, None, None, bg, 0.0, None, None, None, None, None,

@@ -15,6 +15,7 @@ Bars (see the design notes for the derivations):
 """
 import dataclasses
 import math
+import types
 
 import numpy as np
 import pytest
@@ -142,6 +143,42 @@ def test_march_many_lattice_ranges_bit_exact(nacc, orc):
     ranges = _lattice_ranges(exp, step)
     assert np.count_nonzero(ranges > 16) > 100 and np.count_nonzero((ranges > 0) & (ranges <= 16)) > 100
     assert_packed_equal(got, exp)
+
+
+@pytest.mark.parametrize("field_blobs", [8, 64])
+def test_march_many_lattice_ranges_with_field(nacc, orc, field_blobs):
+    """Early stop on rays split into many lattice ranges: rays whose ranges
+    overflow the per-ray record are cut by the early-stop pass's lattice walk,
+    the others from their recorded runs; 64 blobs also exercise the per-group
+    culling of tables with more than 16 entries.  Outside ties the packed
+    samples equal the definition's."""
+    res, L = 64, 2
+    g = workloads.rng(4244)
+    occ = g.random((L, res, res, res)) < 0.5
+    occ[:, : res // 2] = True
+    bits = workloads.pack_bits(occ.reshape(-1))
+    n = 2048
+    o = workloads._normalise(g.standard_normal((n, 3))) * 4.0
+    d = workloads._normalise(g.uniform(-1.2, 1.2, size=(n, 3)) - o)
+    o, d = o.astype(np.float32), d.astype(np.float32)
+    blobs = workloads.c1_forward().blobs if field_blobs == 8 else workloads.c3_training(64).blobs
+    assert blobs.n == field_blobs
+    step, eps = 3.0 / 256, 1e-4
+    grid = grid_from_bits(nacc, (-1.5,) * 3, (1.5,) * 3, res, L, bits)
+    got = run_march(nacc, grid, o, d, step, 1024, 0.0, 1e10, field=nacc.BlobField.from_numpy(blobs), eps=eps)
+    exp = orc.march(o, d, (-1.5,) * 3, (1.5,) * 3, res, L, bits, step, 1024, 0.0, 1e10, blobs=blobs, eps=eps)
+    full = orc.march(o, d, (-1.5,) * 3, (1.5,) * 3, res, L, bits, step, 1024, 0.0, 1e10)
+    ties = _near_tie_rays(orc, types.SimpleNamespace(rays_o=o, rays_d=d, blobs=blobs), bits, full, -math.log(eps))
+    assert len(ties) < 0.03 * n
+    exact = [r for r in range(n) if r not in ties]
+    assert_packed_equal(got, exp, exact)
+    gc, ec, fc = np.diff(got["offsets"]), np.diff(exp["offsets"]), np.diff(full["offsets"])
+    for r in ties:
+        assert abs(int(gc[r]) - int(ec[r])) <= 1
+    ranges = _lattice_ranges(full, step)
+    stopped = ec < fc
+    assert np.count_nonzero(stopped & (ranges > 16)) > 20  # cut by the lattice walk
+    assert np.count_nonzero(stopped & (ranges > 0) & (ranges <= 16)) > 20  # cut from the recorded runs
 
 
 def test_march_full_grid_is_uniform_sampling(nacc, orc):
