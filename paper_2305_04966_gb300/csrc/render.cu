@@ -22,7 +22,10 @@
 //     the suffix sums are formed directly as one reverse scan (no total -
 //     prefix cancellation): g_C and g_D are constant along a ray, so
 //     g_C . S^c_i + g_D S^m_i is the suffix sum of w_k (g_C . c_k + g_D m_k).  The forward pass's data is read again
-//     right away, so the second read hits L2 and DRAM sees each byte once.
+//     right away, so the second read hits L2 and DRAM sees each byte once;
+//     during the carry sweep each lane also names to L2 (prefetch hints) the
+//     line of its colours in the chunk and of its next chunk's intervals and
+//     densities, so the colours the reverse pass reads are on their way.
 //     A ray longer than 32 chunks repeats the carry sweep per group of 32.
 // The kernels hold no locks and wait on nothing; the file also carries the
 // device status word and the bounded-wait self-test of the library.
@@ -275,6 +278,11 @@ __device__ __forceinline__ float chunk_suffix(const float v[4], float carry, flo
     return carry + __shfl_sync(kFull, incl, 0);
 }
 
+// Ask L2 for the line holding p (a hint: no register, no completion).
+__device__ __forceinline__ void prefetch_line_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // Carry sweep of the adjoint over chunks [0, c_end): lane (c & 31) keeps the
 // carry before chunk c for c >= c_keep.  Stops at the mask cut (returned,
 // with the kept optical depth in `carry` and the chunks up to the cut in
@@ -291,6 +299,17 @@ __device__ __forceinline__ long long carry_sweep(const RArgs& A, long long a, lo
         load4(A.t0, g, t0);
         load4(A.t1, g, t1);
         load4(A.sg, g, sg);
+        // the colours of this chunk (read by the reverse pass) and the next
+        // chunk's intervals and densities start towards L2 now: each lane
+        // whose first position lies inside the ray names that position's line
+        // (consecutive lanes are 48 / 16 bytes apart, so the lines are covered)
+        if (g.p >= s && g.p < e) prefetch_line_l2(A.rgb + 3 * g.p);
+        const long long pn = g.p + kChunk;
+        if (c + 1 < c_end && pn >= s && pn < e) {
+            prefetch_line_l2(A.t0 + pn);
+            prefetch_line_l2(A.t1 + pn);
+            prefetch_line_l2(A.sg + pn);
+        }
         taus(g, t0, t1, sg, tau);
         const float next = chunk_prefix(tau, carry, P);
         float p_cut = 0.0f;
