@@ -77,10 +77,12 @@ int nacc_device_status(void* stream, int32_t* status_out);
 int nacc_selftest_wait_timeout(int64_t limit_ns, void* stream);
 
 /*
- * Diagnostics: timing of the count pass of nacc_march_grid.  While set (by
- * the calling host thread), every nacc_march_grid call of that thread records
- * `before` on its stream just before the count kernel and `after` just after
- * it, so the caller can read the kernel's duration with cudaEventElapsedTime.
+ * Diagnostics: timing of the count phase of nacc_march_grid (the run walk
+ * and, with a field, the early-stop pass).  While set (by the calling host
+ * thread), every nacc_march_grid call of that thread records `before` on its
+ * stream just before the run-walk kernel and `after` just after the
+ * early-stop kernel (or the walk, without a field), so the caller can read
+ * their duration with cudaEventElapsedTime.
  * before, after: cudaEvent_t handles created by the caller (NULL, NULL turns
  * the recording off).  The events are not owned by the library.
  */

@@ -1,5 +1,6 @@
 // march.cu -- occupancy-grid lattice marching into packed samples
-// (nacc_march_grid): count pass, block-offset scan, fill pass.
+// (nacc_march_grid): count pass (run walk), early-stop pass, block-offset
+// scan, fill pass.
 //
 // Table 1 "Spatial Skipping" (occupied <=> bit set), Sec. 3.1 (skip empty
 // space), Sec. 4.2 "Sample as Interval" / "Packed Tensor" / "No Gradient
@@ -1111,7 +1112,7 @@ int build_summaries(MarchArgs& A, void* mem, cudaStream_t st) {
     return NACC_OK;
 }
 
-// Caller-owned events recorded around the count kernel (diagnostics).
+// Caller-owned events recorded around the count phase (diagnostics).
 thread_local cudaEvent_t g_count_ev[2] = {nullptr, nullptr};
 
 }  // namespace
