@@ -15,7 +15,9 @@ Pins (``tests/test_oracle_pins.py``): closed-form uniform marching (Sec. 3.1
 "Uniform"), geometric single-cell marching, homogeneous-slab transmittance,
 Eq. 3 (sum of weights = 1 - T_N), the erf line integral of a Gaussian blob,
 finite differences for the gradient, published SplitMix64 outputs, analytic
-inversion of piecewise-constant CDFs.  Parity unpinned: none.
+inversion of piecewise-constant CDFs, the float64 slab clip.  Parity
+unpinned: none.  ``tests/test_oracle_mutants.py`` plants one-line mistakes in
+copies of this oracle and checks that the pins catch every one.
 """
 from __future__ import annotations
 
@@ -51,48 +53,55 @@ def _P(t):
     return ctypes.POINTER(t)
 
 
+def load(path: str):
+    """ctypes handle on a compiled copy of ``oracle.c`` at ``path``, with the
+    signatures of its entry points declared (``lib()`` loads the in-tree
+    build; the planted-mistake tests load mutated copies)."""
+    L = ctypes.CDLL(path)
+    i64, i32, f32, u64 = ctypes.c_int64, ctypes.c_int, ctypes.c_float, ctypes.c_uint64
+    vp = ctypes.c_void_p
+    L.orc_splitmix64_at.restype = u64
+    L.orc_splitmix64_at.argtypes = [u64, u64]
+    L.orc_march.restype = i32
+    L.orc_march.argtypes = [i64, vp, vp, vp, vp, i32, i32, vp, f32, i32, f32, f32, i32, vp, vp,
+                            vp, f32, vp, vp, vp, vp, vp, i32]
+    L.orc_ray_clip.restype = None
+    L.orc_ray_clip.argtypes = [i64, vp, vp, vp, vp, i32, i32, f32, f32, vp, vp, vp]
+    L.orc_level_geometry.restype = None
+    L.orc_level_geometry.argtypes = [vp, vp, i32, i32, vp]
+    L.orc_field_samples.restype = None
+    L.orc_field_samples.argtypes = [i64, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, i32]
+    L.orc_field_points.restype = None
+    L.orc_field_points.argtypes = [i64, vp, i32, vp, vp, vp, vp, vp, i32]
+    L.orc_render_fwd.restype = None
+    L.orc_render_fwd.argtypes = [i64, vp, vp, vp, vp, vp, vp, f32, vp, vp, vp, vp, vp, i32]
+    L.orc_render_bwd.restype = None
+    L.orc_render_bwd.argtypes = [i64, vp, vp, vp, vp, vp, vp, f32, vp, vp, vp, vp, vp, i32]
+    L.orc_grid_points.restype = None
+    L.orc_grid_points.argtypes = [vp, vp, i32, i32, u64, i64, i32, vp, i32]
+    L.orc_update_grid.restype = None
+    L.orc_update_grid.argtypes = [i64, vp, vp, f32, f32, f32, vp, vp]
+    L.orc_sample_pdf.restype = None
+    L.orc_sample_pdf.argtypes = [i64, i32, vp, vp, i32, i32, u64, vp, i32]
+    L.orc_march_unbounded.restype = i32
+    L.orc_march_unbounded.argtypes = [i64, vp, vp, vp, vp, i32, i32, vp, i32, f32, f32, i32, vp, vp, vp, f32,
+                                      vp, vp, vp, vp, vp, i32]
+    L.orc_s_to_t.restype = f32
+    L.orc_s_to_t.argtypes = [f32, f32, f32]
+    L.orc_contract_points.restype = None
+    L.orc_contract_points.argtypes = [i64, vp, vp]
+    L.orc_uncontract_points.restype = None
+    L.orc_uncontract_points.argtypes = [i64, vp, vp]
+    L.orc_max_threads.restype = i32
+    L.orc_max_threads.argtypes = []
+    return L
+
+
 def lib():
     global _lib
     if _lib is None:
         build()
-        L = ctypes.CDLL(_LIB_PATH)
-        i64, i32, f32, u64 = ctypes.c_int64, ctypes.c_int, ctypes.c_float, ctypes.c_uint64
-        vp = ctypes.c_void_p
-        L.orc_splitmix64_at.restype = u64
-        L.orc_splitmix64_at.argtypes = [u64, u64]
-        L.orc_march.restype = i32
-        L.orc_march.argtypes = [i64, vp, vp, vp, vp, i32, i32, vp, f32, i32, f32, f32, i32, vp, vp,
-                                vp, f32, vp, vp, vp, vp, vp, i32]
-        L.orc_ray_clip.restype = None
-        L.orc_ray_clip.argtypes = [i64, vp, vp, vp, vp, i32, i32, f32, f32, vp, vp, vp]
-        L.orc_level_geometry.restype = None
-        L.orc_level_geometry.argtypes = [vp, vp, i32, i32, vp]
-        L.orc_field_samples.restype = None
-        L.orc_field_samples.argtypes = [i64, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, i32]
-        L.orc_field_points.restype = None
-        L.orc_field_points.argtypes = [i64, vp, i32, vp, vp, vp, vp, vp, i32]
-        L.orc_render_fwd.restype = None
-        L.orc_render_fwd.argtypes = [i64, vp, vp, vp, vp, vp, vp, f32, vp, vp, vp, vp, vp, i32]
-        L.orc_render_bwd.restype = None
-        L.orc_render_bwd.argtypes = [i64, vp, vp, vp, vp, vp, vp, f32, vp, vp, vp, vp, vp, i32]
-        L.orc_grid_points.restype = None
-        L.orc_grid_points.argtypes = [vp, vp, i32, i32, u64, i64, i32, vp, i32]
-        L.orc_update_grid.restype = None
-        L.orc_update_grid.argtypes = [i64, vp, vp, f32, f32, f32, vp, vp]
-        L.orc_sample_pdf.restype = None
-        L.orc_sample_pdf.argtypes = [i64, i32, vp, vp, i32, i32, u64, vp, i32]
-        L.orc_march_unbounded.restype = i32
-        L.orc_march_unbounded.argtypes = [i64, vp, vp, vp, vp, i32, i32, vp, i32, f32, f32, i32, vp, vp, vp, f32,
-                                          vp, vp, vp, vp, vp, i32]
-        L.orc_s_to_t.restype = f32
-        L.orc_s_to_t.argtypes = [f32, f32, f32]
-        L.orc_contract_points.restype = None
-        L.orc_contract_points.argtypes = [i64, vp, vp]
-        L.orc_uncontract_points.restype = None
-        L.orc_uncontract_points.argtypes = [i64, vp, vp]
-        L.orc_max_threads.restype = i32
-        L.orc_max_threads.argtypes = []
-        _lib = L
+        _lib = load(_LIB_PATH)
     return _lib
 
 

@@ -227,6 +227,32 @@ def test_miss_and_inside_origin(orc):
     assert out["t_starts"][0] == 0.0
 
 
+def test_ray_clip_matches_float64_slab(orc):
+    """The clip range [t_near, t_far] of the outermost level's box (Sec. 3.1's
+    bounded range) equals the float64 slab intersection: random rays from outside
+    and inside, rays with zero direction components, misses, a t_min / t_max window."""
+    g = workloads.rng(95)
+    n = 400
+    o = g.uniform(-4.0, 4.0, size=(n, 3))
+    o[:50] = g.uniform(-1.0, 1.0, size=(50, 3))  # origins inside the box
+    d = workloads._normalise(g.standard_normal((n, 3)))
+    d[50:80, 0] = 0.0  # one zero component, some of these miss
+    d[80:90, :2] = 0.0
+    d[80:90, 2] = np.where(np.arange(10) % 2 == 0, 1.0, -1.0)
+    d[50:80] = workloads._normalise(d[50:80])
+    o, d = o.astype(np.float32), d.astype(np.float32)
+    for L, (t_min, t_max) in ((1, (0.0, 1e10)), (3, (0.0, 1e10)), (2, (1.0, 4.5))):
+        half = 1.5 * 2 ** (L - 1)
+        tn, tf, hit = orc.ray_clip(o, d, (-1.5,) * 3, (1.5,) * 3, 16, L, t_min, t_max)
+        etn, etf, ehit = slab64(o, d, (-half,) * 3, (half,) * 3, t_min, t_max)
+        grazing = np.abs(etf - etn) < 1e-4
+        np.testing.assert_array_equal(hit[~grazing], ehit[~grazing])
+        assert ehit.sum() > 60 and (L == 3 or (~ehit).sum() > 20)  # level 2's box holds every origin
+        m = ehit & ~grazing
+        np.testing.assert_allclose(tn[m], etn[m], rtol=1e-6, atol=1e-6)
+        np.testing.assert_allclose(tf[m], etf[m], rtol=1e-6, atol=1e-6)
+
+
 def test_early_termination_cut(orc):
     """No-gradient filtering (Sec. 4.2): the field-given march emits a prefix of the
     field-less march, cut where the float64 optical depth of the emitted samples
@@ -453,13 +479,15 @@ def test_update_grid_threshold_and_bit_layout(orc):
     layout: element c is bit c % 32 of word c // 32."""
     n = 8 ** 3 * 2
     dens = np.zeros(n, np.float32)
-    dens[[0, 33, 511, 700]] = [5.0, 1.0, 0.00005, 2.0]
+    dens[[0, 33, 511, 700, 900]] = [5.0, 1.0, 0.00005, 2.0, 0.001]
     e, bits, mean = orc.update_grid(np.zeros(n, np.float32), dens, 0.0, 0.01)
-    assert mean == pytest.approx(8.00005 / n, rel=1e-6)
-    thr = 0.01 * 8.00005 / n
+    assert mean == pytest.approx(8.00105 / n, rel=1e-6)
+    thr = 0.01 * 8.00105 / n
     assert thr > 0.00005  # cell 511 falls below 0.01 * mean
+    assert thr < 0.001 < mean  # cell 900 lies above 0.01 * mean but below the mean
     assert bits[0] == 1 and bits[1] == 2 and bits[15] == 0 and bits[21] == 1 << (700 % 32)
-    assert workloads.unpack_bits(bits).sum() == 3
+    assert bits[28] == 1 << (900 % 32)
+    assert workloads.unpack_bits(bits).sum() == 4
     _, bits_abs, _ = orc.update_grid(np.zeros(n, np.float32), dens, 0.0, 0.0, 1.5)
     assert workloads.unpack_bits(bits_abs).sum() == 2
 
@@ -551,17 +579,17 @@ def test_proposal_encoding_closed_forms():
 
 
 def test_proposal_forward_hand_built_network():
-    """W1 copies x, y, z, b1 = 1/2, W2 = identity, w3 sums the first three
-    units, b3 = -1: density = softplus(sum_j relu(x_j + 1/2) - 1)."""
+    """W1 copies x, y, z, b1 = 1/2, W2 = identity, b2 = -1/4, w3 sums the first
+    three units, b3 = -1: density = softplus(sum_j relu(relu(x_j + 1/2) - 1/4) - 1)."""
     from oracle import proposal as P
     W1 = np.zeros((64, 64), np.float32)
     W1[0, 0] = W1[1, 1] = W1[2, 2] = 1.0
     w3 = np.zeros(64, np.float32)
     w3[:3] = 1.0
     p = {"W1": W1, "b1": np.full(64, 0.5, np.float32), "W2": np.eye(64, dtype=np.float32),
-         "b2": np.zeros(64, np.float32), "w3": w3, "b3": np.array([-1.0], np.float32)}
+         "b2": np.full(64, -0.25, np.float32), "w3": w3, "b3": np.array([-1.0], np.float32)}
     x = np.array([[0.25, -0.5, 1.0], [-1.0, -0.75, 0.0], [0.5, 0.5, 0.5]])  # exact in bfloat16
-    z = np.maximum(x + 0.5, 0.0).sum(1) - 1.0
+    z = np.maximum(np.maximum(x + 0.5, 0.0) - 0.25, 0.0).sum(1) - 1.0
     np.testing.assert_allclose(P.forward(p, x)["sigma"], np.log1p(np.exp(z)), rtol=1e-15)
 
 
@@ -600,17 +628,21 @@ def test_proposal_adam_first_step_closed_form():
 
 def test_exact_optical_depth_matches_fine_quadrature(orc):
     """The closed-form line integral of the 8-blob field equals the oracle's
-    FP64 compositing of a fine lattice (Eq. 2, dt -> 0) on a few rays."""
+    FP64 compositing of a fine lattice (Eq. 2, dt -> 0) on a few rays; every
+    other ray's direction is scaled to length 1.7 (the integral is over t, not
+    arc length)."""
     from oracle import proposal as P
     w = workloads.c1_forward(6)
-    tn, tf, hit = orc.ray_clip(w.rays_o, w.rays_d, (-1.5,) * 3, (1.5,) * 3, 128, 1, 0.0, 1e10)
-    exact = P.exact_optical_depth(w.rays_o, w.rays_d, tn.astype(np.float64), tf.astype(np.float64),
+    rd = w.rays_d.copy()
+    rd[::2] *= np.float32(1.7)
+    tn, tf, hit = orc.ray_clip(w.rays_o, rd, (-1.5,) * 3, (1.5,) * 3, 128, 1, 0.0, 1e10)
+    exact = P.exact_optical_depth(w.rays_o, rd, tn.astype(np.float64), tf.astype(np.float64),
                                   w.blobs.mu, w.blobs.std, w.blobs.peak)
     for r in np.nonzero(hit)[0]:
         N = 40000
         ts = np.linspace(tn[r], tf[r], N + 1)
         t0, t1 = ts[:-1].astype(np.float32), ts[1:].astype(np.float32)
-        sig, rgb = orc.field_samples(w.rays_o[r:r + 1], w.rays_d[r:r + 1], np.zeros(N, np.int32), t0, t1, w.blobs)
+        sig, rgb = orc.field_samples(w.rays_o[r:r + 1], rd[r:r + 1], np.zeros(N, np.int32), t0, t1, w.blobs)
         out = orc.render_fwd(np.array([0, N]), t0, t1, sig, rgb)
         assert -math.log(out["trans"][0]) == pytest.approx(exact[r], rel=2e-4, abs=1e-6)
     assert hit.sum() >= 3
