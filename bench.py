@@ -303,14 +303,16 @@ def training_step_measure(torch, nacc, dev, flush, steps=10):
     gcc = torch.empty((cap, 3), device=dev)
     pts = torch.empty((grid.n_cells, 3), device=dev)
     dens = torch.empty(grid.n_cells, device=dev)
+    ck = nacc.render_ckpt_buffer(n, dev)
 
     def step():
         pk = nacc.march_grid(grid, o, d, m.step, m.max_steps, m.t_min, m.t_max, m.early_stop_eps, field=field,
                              buffers=bufs)
         nacc.field_eval(field, o, d, pk, out=(sig, rgbs))
-        rgb, _, _, _, _ = nacc.render_fwd(pk.offsets, pk.t_starts, pk.t_ends, sig, rgbs, w.bg, 0.0)
+        rgb, _, _, _, _ = nacc.render_fwd(pk.offsets, pk.t_starts, pk.t_ends, sig, rgbs, w.bg, 0.0, ckpt=ck)
         loss, g_rgb = nacc.l2_loss(rgb, tgt)
-        nacc.render_bwd(pk.offsets, pk.t_starts, pk.t_ends, sig, rgbs, g_rgb, None, None, w.bg, 0.0, out=(gsg, gcc))
+        nacc.render_bwd(pk.offsets, pk.t_starts, pk.t_ends, sig, rgbs, g_rgb, None, None, w.bg, 0.0, out=(gsg, gcc),
+                        ckpt=ck)
         nacc.grid_points(grid, seed=7, step=1, jitter=True, out=pts)
         nacc.field_points(field, pts, out=dens)
         nacc.update_grid(grid, dens, 0.95, 0.01, buffers=ubufs)
@@ -873,6 +875,7 @@ def run_ours(args):
     rgbs = torch.empty((cap, 3), dtype=torch.float32, device=dev)
     gsg = torch.empty(cap, dtype=torch.float32, device=dev)
     gcc = torch.empty((cap, 3), dtype=torch.float32, device=dev)
+    ck = nacc.render_ckpt_buffer(n, dev)  # per-ray records from render_fwd for render_bwd
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stages = ["march", "field", "render_fwd", "loss", "render_bwd"]
 
@@ -890,14 +893,14 @@ def run_ours(args):
         nacc.field_eval(field, o_, d_, pk, out=(sig, rgbs))
         if ev is not None:
             ev[2].record()
-        rgb, op, dep, tr, _ = nacc.render_fwd(pk.offsets, pk.t_starts, pk.t_ends, sig, rgbs, w.bg, 0.0)
+        rgb, op, dep, tr, _ = nacc.render_fwd(pk.offsets, pk.t_starts, pk.t_ends, sig, rgbs, w.bg, 0.0, ckpt=ck)
         if ev is not None:
             ev[3].record()
         loss, g_rgb = nacc.l2_loss(rgb, tgt_)
         if ev is not None:
             ev[4].record()
         nacc.render_bwd(pk.offsets, pk.t_starts, pk.t_ends, sig, rgbs, g_rgb, None, None, w.bg, 0.0,
-                        out=(gsg, gcc))
+                        out=(gsg, gcc), ckpt=ck)
         if ev is not None:
             ev[5].record()
         return rgb, loss

@@ -339,6 +339,38 @@ int nacc_render_bwd(int64_t n_rays, const int64_t* offsets, const float* t_start
                     float early_stop_eps, const float* g_rgb, const float* g_opacity,
                     const float* g_depth, float* g_sigmas, float* g_rgbs, void* stream);
 
+/*
+ * Checkpointed pair of nacc_render_fwd / nacc_render_bwd (Algorithm 1: the
+ * forward rendering, then gradients through it).  Results are bit-identical
+ * to the plain pair.  The forward pass also writes, per ray, a 64-byte record
+ * of what the adjoint would otherwise recompute in a first sweep over the
+ * ray's samples: the optical depth at the start of each 128-position chunk
+ * (the chunks the kernels cut a ray into, counted from the ray's first
+ * sample rounded down to a multiple of 4), the position of the mask cut
+ * (Sec. 4.2) and the kept optical depth (T_N = exp(-depth)).  This is not
+ * per-sample transmittance: 16 words per ray, whatever the ray's length.
+ * The adjoint reads the record and makes one pass over the samples instead
+ * of two.  Rays of more than 14 chunks (1,792 samples) get a record marked
+ * as absent, and the adjoint falls back to its own sweep for them.
+ * ckpt_out / ckpt: [device] nacc_render_ckpt_bytes(n_rays) bytes, 16-byte
+ * aligned, caller-owned; written by nacc_render_fwd_ckpt and read by
+ * nacc_render_bwd_ckpt, which must get the same offsets, sample arrays
+ * and early_stop_eps (a record whose chunk count exceeds its ray's is
+ * ignored; any other mismatch gives wrong gradients, never an access
+ * outside the arrays).  Other arguments and errors as the plain pair; NULL
+ * or misaligned ckpt -> NACC_ERR_INVALID_ARG.
+ */
+size_t nacc_render_ckpt_bytes(int64_t n_rays);
+int nacc_render_fwd_ckpt(int64_t n_rays, const int64_t* offsets, const float* t_starts,
+                         const float* t_ends, const float* sigmas, const float* rgbs, const float* bg,
+                         float early_stop_eps, float* rgb_out, float* opacity_out, float* depth_out,
+                         float* trans_out, float* weights_out, float* ckpt_out, void* stream);
+int nacc_render_bwd_ckpt(int64_t n_rays, const int64_t* offsets, const float* t_starts,
+                         const float* t_ends, const float* sigmas, const float* rgbs, const float* bg,
+                         float early_stop_eps, const float* g_rgb, const float* g_opacity,
+                         const float* g_depth, const float* ckpt, float* g_sigmas, float* g_rgbs,
+                         void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -11,7 +11,8 @@ from ._abi import NaccError, load as load_library
 from .api import (BlobField, CombinedSampler, MarchBuffers, OccupancyGrid, PackedSamples, ProposalMLP,
                   ProposalSampler, RenderFn, occupied_range, range_edges,
                   UpdateBuffers, dense_weights, density_grid, edges_to_packed, field_eval, field_points,
-                  grid_points, l2_loss, march_grid, mlp_encode, render, render_bwd, render_fwd, sample_pdf,
+                  grid_points, l2_loss, march_grid, mlp_encode, render, render_bwd, render_ckpt_buffer, render_fwd,
+                  sample_pdf,
                   uniform_edges, update_grid, update_grid_frames, grid_density_lookup, grid_density_backward,
                   update_grid_sgd, march_unbounded, uncontract_points, density_grid_unbounded,
                   contract_points, phi_edges, UnboundedProposalSampler)
@@ -19,7 +20,8 @@ from .api import (BlobField, CombinedSampler, MarchBuffers, OccupancyGrid, Packe
 __all__ = [
     "NaccError", "load_library", "BlobField", "MarchBuffers", "OccupancyGrid", "PackedSamples",
     "RenderFn", "UpdateBuffers", "density_grid", "field_eval", "field_points", "grid_points",
-    "l2_loss", "march_grid", "render", "render_bwd", "render_fwd", "sample_pdf", "update_grid",
+    "l2_loss", "march_grid", "render", "render_bwd", "render_ckpt_buffer", "render_fwd", "sample_pdf",
+    "update_grid",
     "ProposalMLP", "ProposalSampler", "mlp_encode", "uniform_edges", "dense_weights", "edges_to_packed",
     "CombinedSampler", "occupied_range", "range_edges", "update_grid_frames", "grid_density_lookup",
     "grid_density_backward", "update_grid_sgd", "march_unbounded", "uncontract_points",

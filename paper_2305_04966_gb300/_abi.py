@@ -68,6 +68,11 @@ SIGNATURES = {
                                 c_vp, c_vp, c_vp, c_vp]),
     "nacc_render_bwd": (c_i32, [c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, P(c_f32), c_f32, c_vp, c_vp,
                                 c_vp, c_vp, c_vp, c_vp]),
+    "nacc_render_ckpt_bytes": (c_sz, [c_i64]),
+    "nacc_render_fwd_ckpt": (c_i32, [c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, P(c_f32), c_f32, c_vp, c_vp,
+                                     c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "nacc_render_bwd_ckpt": (c_i32, [c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, P(c_f32), c_f32, c_vp, c_vp,
+                                     c_vp, c_vp, c_vp, c_vp, c_vp]),
     "nacc_harness_field": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, P(BlobField), c_vp, c_vp, c_vp]),
     "nacc_harness_field_points": (c_i32, [c_i64, c_vp, P(BlobField), c_vp, c_vp]),
     "nacc_harness_field_rays": (c_i32, [c_vp, c_vp, c_i64, c_vp, c_vp, c_vp, P(BlobField), c_vp, c_vp, c_vp]),

@@ -278,10 +278,18 @@ def _bg(bg):
     return (ctypes.c_float * 3)(*[float(v) for v in bg])
 
 
+def render_ckpt_buffer(n_rays: int, device) -> torch.Tensor:
+    """Device buffer for the per-ray checkpoint records of :func:`render_fwd` /
+    :func:`render_bwd` (16 words per ray)."""
+    words = int(_abi.load().nacc_render_ckpt_bytes(int(n_rays))) // 4
+    return torch.empty(words, dtype=_F32, device=device)
+
+
 def render_fwd(offsets, t_starts, t_ends, sigmas, rgbs, bg=(1.0, 1.0, 1.0), early_stop_eps=0.0,
-               want_weights=False):
+               want_weights=False, ckpt=None):
     """Composite packed samples.  Returns (rgb [n][3], opacity [n], depth [n], trans [n],
-    weights [S] or None)."""
+    weights [S] or None).  With ``ckpt`` (from :func:`render_ckpt_buffer`) the pass
+    also writes the per-ray records that let :func:`render_bwd` skip its first sweep."""
     dev = offsets.device
     _check(offsets, "offsets", _I64, dev)
     n = int(offsets.shape[0]) - 1
@@ -297,14 +305,21 @@ def render_fwd(offsets, t_starts, t_ends, sigmas, rgbs, bg=(1.0, 1.0, 1.0), earl
     dep = torch.empty(n, dtype=_F32, device=dev)
     tr = torch.empty(n, dtype=_F32, device=dev)
     w = torch.empty(sigmas.shape[0], dtype=_F32, device=dev) if want_weights else None
-    _abi.call("nacc_render_fwd", n, _ptr(offsets), _ptr(t_starts), _ptr(t_ends), _ptr(sigmas), _ptr(rgbs),
-              _bg(bg), float(early_stop_eps), _ptr(rgb), _ptr(op), _ptr(dep), _ptr(tr), _ptr(w), _stream(dev))
+    if ckpt is None:
+        _abi.call("nacc_render_fwd", n, _ptr(offsets), _ptr(t_starts), _ptr(t_ends), _ptr(sigmas), _ptr(rgbs),
+                  _bg(bg), float(early_stop_eps), _ptr(rgb), _ptr(op), _ptr(dep), _ptr(tr), _ptr(w), _stream(dev))
+    else:
+        _check(ckpt, "ckpt", _F32, dev, (16 * n,))
+        _abi.call("nacc_render_fwd_ckpt", n, _ptr(offsets), _ptr(t_starts), _ptr(t_ends), _ptr(sigmas),
+                  _ptr(rgbs), _bg(bg), float(early_stop_eps), _ptr(rgb), _ptr(op), _ptr(dep), _ptr(tr), _ptr(w),
+                  _ptr(ckpt), _stream(dev))
     return rgb, op, dep, tr, w
 
 
 def render_bwd(offsets, t_starts, t_ends, sigmas, rgbs, g_rgb, g_opacity, g_depth, bg=(1.0, 1.0, 1.0),
-               early_stop_eps=0.0, out=None):
-    """Adjoint of :func:`render_fwd`.  Returns (g_sigmas [S], g_rgbs [S][3])."""
+               early_stop_eps=0.0, out=None, ckpt=None):
+    """Adjoint of :func:`render_fwd`.  Returns (g_sigmas [S], g_rgbs [S][3]).  ``ckpt``:
+    the records a :func:`render_fwd` call on the same samples and eps wrote."""
     dev = offsets.device
     n = int(offsets.shape[0]) - 1
     for t, nm, shp in ((g_rgb, "g_rgb", (n, 3)), (g_opacity, "g_opacity", (n,)), (g_depth, "g_depth", (n,))):
@@ -315,29 +330,37 @@ def render_bwd(offsets, t_starts, t_ends, sigmas, rgbs, g_rgb, g_opacity, g_dept
         gc = torch.empty_like(rgbs)
     else:
         gs, gc = out
-    _abi.call("nacc_render_bwd", n, _ptr(offsets), _ptr(t_starts), _ptr(t_ends), _ptr(sigmas), _ptr(rgbs),
-              _bg(bg), float(early_stop_eps), _ptr(g_rgb), _ptr(g_opacity), _ptr(g_depth), _ptr(gs),
-              _ptr(gc), _stream(dev))
+    if ckpt is None:
+        _abi.call("nacc_render_bwd", n, _ptr(offsets), _ptr(t_starts), _ptr(t_ends), _ptr(sigmas), _ptr(rgbs),
+                  _bg(bg), float(early_stop_eps), _ptr(g_rgb), _ptr(g_opacity), _ptr(g_depth), _ptr(gs),
+                  _ptr(gc), _stream(dev))
+    else:
+        _check(ckpt, "ckpt", _F32, dev, (16 * n,))
+        _abi.call("nacc_render_bwd_ckpt", n, _ptr(offsets), _ptr(t_starts), _ptr(t_ends), _ptr(sigmas),
+                  _ptr(rgbs), _bg(bg), float(early_stop_eps), _ptr(g_rgb), _ptr(g_opacity), _ptr(g_depth),
+                  _ptr(ckpt), _ptr(gs), _ptr(gc), _stream(dev))
     return gs, gc
 
 
 class RenderFn(torch.autograd.Function):
     """Differentiable compositing: (sigmas, rgbs) -> (rgb, opacity, depth).  The
-    backward recomputes per-sample transmittance from the samples (none saved)."""
+    backward recomputes per-sample transmittance from the samples; the forward
+    saves only a 64-byte record per ray (chunk carries, mask cut, kept depth)."""
 
     @staticmethod
     def forward(ctx, sigmas, rgbs, offsets, t_starts, t_ends, bg=(1.0, 1.0, 1.0), early_stop_eps=0.0):
-        rgb, op, dep, _, _ = render_fwd(offsets, t_starts, t_ends, sigmas, rgbs, bg, early_stop_eps)
-        ctx.save_for_backward(sigmas, rgbs, offsets, t_starts, t_ends)
+        ckpt = render_ckpt_buffer(offsets.shape[0] - 1, offsets.device)
+        rgb, op, dep, _, _ = render_fwd(offsets, t_starts, t_ends, sigmas, rgbs, bg, early_stop_eps, ckpt=ckpt)
+        ctx.save_for_backward(sigmas, rgbs, offsets, t_starts, t_ends, ckpt)
         ctx.bg, ctx.eps = bg, early_stop_eps
         return rgb, op, dep
 
     @staticmethod
     def backward(ctx, g_rgb, g_op, g_dep):
-        sigmas, rgbs, offsets, t_starts, t_ends = ctx.saved_tensors
+        sigmas, rgbs, offsets, t_starts, t_ends, ckpt = ctx.saved_tensors
         c = lambda t: None if t is None else t.contiguous()
         gs, gc = render_bwd(offsets, t_starts, t_ends, sigmas, rgbs, c(g_rgb), c(g_op), c(g_dep),
-                            ctx.bg, ctx.eps)
+                            ctx.bg, ctx.eps, ckpt=ckpt)
         return gs, gc, None, None, None, None, None
 
 

@@ -63,7 +63,20 @@ struct RArgs {
     const float* g_dep;
     float* g_sg;
     float* g_c;
+    float* ckpt;  // per-ray checkpoint records (the _ckpt entry points), else NULL
 };
+
+// Checkpoint record of one ray (16 words, 64 bytes), written by the forward
+// pass and read by the adjoint instead of its carry sweep:
+//   [0] int: chunks up to and including the mask cut's chunk (all chunks if
+//       no cut), or -1 when the ray has more than kCkptChunks chunks (the
+//       adjoint then runs its carry sweep for that ray);
+//   [1] int: cut position - s (e - s if no cut);
+//   [2] float: optical depth of the kept samples (T_N = exp(-[2]));
+//   [2 + c] float: carry (exclusive optical depth) before chunk c, c = 1..13
+//       (chunk 0 starts at 0).
+constexpr int kCkpt = 16;
+constexpr int kCkptChunks = kCkpt - 2;
 
 // 1 - exp(-x) for x >= 0: Taylor series x(1 - x/2(1 - x/3(1 - x/4(1 - x/5))))
 // below 1/16 (truncation < 2e-9 relative), else 1 - exp(-x) directly.
@@ -197,6 +210,7 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
+template <bool kCk>
 __global__ void __launch_bounds__(kThreads, 4) k_render_fwd(RArgs A) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * kWarps;
@@ -206,9 +220,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_render_fwd(RArgs A) {
         const int nch = e > s ? (int)((e - a + kChunk - 1) / kChunk) : 0;
         float cr = 0.0f, cg = 0.0f, cb = 0.0f, op = 0.0f, dep = 0.0f;
         float carry = 0.0f;  // -> optical depth of the kept samples
+        float my_c = 0.0f;   // checkpoint: lane c keeps the carry before chunk c
         long long cut = e;
         int c = 0;
         for (; c < nch && cut == e; ++c) {
+            if (kCk && c == lane) my_c = carry;
             const Group g = group_of(a, c, s, e);
             float t0[4], t1[4], sg[4], rgb[12], tau[4], P[4];
             load4(A.t0, g, t0);
@@ -232,6 +248,16 @@ __global__ void __launch_bounds__(kThreads, 4) k_render_fwd(RArgs A) {
                 dep = fmaf(w[j], __fmul_rn(__fadd_rn(t0[j], t1[j]), 0.5f), dep);
             }
             if (A.w_out) store4(A.w_out, g, w);
+        }
+        if (kCk) {  // one coalesced 64-byte record per ray
+            const float mc = __shfl_sync(kFull, my_c, (lane - 2) & 31);
+            if (lane < kCkpt) {
+                float v = mc;
+                if (lane == 0) v = __int_as_float(nch <= kCkptChunks ? c : -1);
+                if (lane == 1) v = __int_as_float((int)(cut - s));
+                if (lane == 2) v = carry;
+                A.ckpt[r * kCkpt + lane] = v;
+            }
         }
         if (A.w_out) {  // chunks after the cut: zero weights
             const float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
@@ -324,8 +350,10 @@ __device__ __forceinline__ long long carry_sweep(const RArgs& A, long long a, lo
     return e;
 }
 
+template <bool kCk>
 __global__ void __launch_bounds__(kThreads, 4) k_render_bwd(RArgs A) {
     const int64_t warps = (int64_t)gridDim.x * kWarps;
+    const int lane = threadIdx.x & 31;
     for (int64_t r = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); r < A.n_rays; r += warps) {
         const long long s = A.off[r], e = A.off[r + 1];
         if (e <= s) continue;
@@ -337,9 +365,19 @@ __global__ void __launch_bounds__(kThreads, 4) k_render_bwd(RArgs A) {
         const float gA = A.g_op ? A.g_op[r] : 0.0f;
         const float gD = A.g_dep ? A.g_dep[r] : 0.0f;
 
-        float carry, my_carry = 0.0f;
-        int ncut;
-        const long long cut = carry_sweep(A, a, s, e, nch, ((nch - 1) >> 5) << 5, carry, my_carry, ncut);
+        float carry = 0.0f, my_carry = 0.0f;
+        int ncut = -1;
+        long long cut = e;
+        if (kCk) {  // the forward pass's record replaces the carry sweep
+            const float v = A.ckpt[r * kCkpt + (lane & (kCkpt - 1))];
+            ncut = __float_as_int(__shfl_sync(kFull, v, 0));
+            cut = s + __float_as_int(__shfl_sync(kFull, v, 1));
+            carry = __shfl_sync(kFull, v, 2);
+            const float mc = __shfl_sync(kFull, v, (lane + 2) & (kCkpt - 1));
+            my_carry = (lane >= 1 && lane < ncut) ? mc : 0.0f;
+            if (ncut > nch) ncut = -1;  // not a record of this ray: sweep instead
+        }
+        if (ncut < 0) cut = carry_sweep(A, a, s, e, nch, ((nch - 1) >> 5) << 5, carry, my_carry, ncut);
         const float TN = __expf(-carry);
         // g_A T_N - g_C . T_N bg: the part of every kept sample's gradient that
         // does not depend on the sample
@@ -366,6 +404,15 @@ __global__ void __launch_bounds__(kThreads, 4) k_render_bwd(RArgs A) {
             }
             for (int c = min(ncut, 32 * (gi + 1)) - 1; c >= 32 * gi; --c) {
                 const Group g = group_of(a, c, s, e);
+                if (kCk && c > 0) {  // the previous chunk's lines start towards L2
+                    const long long pp = g.p - kChunk;
+                    if (pp >= s && pp < e) {
+                        prefetch_line_l2(A.t0 + pp);
+                        prefetch_line_l2(A.t1 + pp);
+                        prefetch_line_l2(A.sg + pp);
+                        prefetch_line_l2(A.rgb + 3 * pp);
+                    }
+                }
                 float t0[4], t1[4], sg[4], rgb[12], tau[4], P[4];
                 load4(A.t0, g, t0);
                 load4(A.t1, g, t1);
@@ -442,12 +489,12 @@ int check_common(int64_t n_rays, const int64_t* offsets, const float* t_starts, 
 
 using namespace nacc;
 
-extern "C" int nacc_render_fwd(int64_t n_rays, const int64_t* offsets, const float* t_starts,
-                               const float* t_ends, const float* sigmas, const float* rgbs,
-                               const float* bg, float early_stop_eps, float* rgb_out,
-                               float* opacity_out, float* depth_out, float* trans_out,
-                               float* weights_out, void* stream) {
-    clear_error();
+namespace {
+
+int render_fwd_impl(int64_t n_rays, const int64_t* offsets, const float* t_starts, const float* t_ends,
+                    const float* sigmas, const float* rgbs, const float* bg, float early_stop_eps,
+                    float* rgb_out, float* opacity_out, float* depth_out, float* trans_out, float* weights_out,
+                    float* ckpt, void* stream) {
     int rc = check_common(n_rays, offsets, t_starts, t_ends, sigmas, rgbs, bg);
     if (rc != NACC_OK) return rc;
     NACC_CHECK_ARG(rgb_out && opacity_out && depth_out && trans_out, "an output array is NULL");
@@ -469,15 +516,15 @@ extern "C" int nacc_render_fwd(int64_t n_rays, const int64_t* offsets, const flo
     A.dep_out = depth_out;
     A.tr_out = trans_out;
     A.w_out = weights_out;
-    return launch_persistent(k_render_fwd, A, as_stream(stream));
+    A.ckpt = ckpt;
+    return ckpt ? launch_persistent(k_render_fwd<true>, A, as_stream(stream))
+                : launch_persistent(k_render_fwd<false>, A, as_stream(stream));
 }
 
-extern "C" int nacc_render_bwd(int64_t n_rays, const int64_t* offsets, const float* t_starts,
-                               const float* t_ends, const float* sigmas, const float* rgbs,
-                               const float* bg, float early_stop_eps, const float* g_rgb,
-                               const float* g_opacity, const float* g_depth, float* g_sigmas,
-                               float* g_rgbs, void* stream) {
-    clear_error();
+int render_bwd_impl(int64_t n_rays, const int64_t* offsets, const float* t_starts, const float* t_ends,
+                    const float* sigmas, const float* rgbs, const float* bg, float early_stop_eps,
+                    const float* g_rgb, const float* g_opacity, const float* g_depth, const float* ckpt,
+                    float* g_sigmas, float* g_rgbs, void* stream) {
     int rc = check_common(n_rays, offsets, t_starts, t_ends, sigmas, rgbs, bg);
     if (rc != NACC_OK) return rc;
     NACC_CHECK_ARG(g_sigmas && g_rgbs, "g_sigmas / g_rgbs is NULL");
@@ -499,7 +546,59 @@ extern "C" int nacc_render_bwd(int64_t n_rays, const int64_t* offsets, const flo
     A.g_dep = g_depth;
     A.g_sg = g_sigmas;
     A.g_c = g_rgbs;
-    return launch_persistent(k_render_bwd, A, as_stream(stream));
+    A.ckpt = const_cast<float*>(ckpt);  // read only by the adjoint
+    return ckpt ? launch_persistent(k_render_bwd<true>, A, as_stream(stream))
+                : launch_persistent(k_render_bwd<false>, A, as_stream(stream));
+}
+
+}  // namespace
+
+extern "C" int nacc_render_fwd(int64_t n_rays, const int64_t* offsets, const float* t_starts,
+                               const float* t_ends, const float* sigmas, const float* rgbs,
+                               const float* bg, float early_stop_eps, float* rgb_out,
+                               float* opacity_out, float* depth_out, float* trans_out,
+                               float* weights_out, void* stream) {
+    clear_error();
+    return render_fwd_impl(n_rays, offsets, t_starts, t_ends, sigmas, rgbs, bg, early_stop_eps, rgb_out,
+                           opacity_out, depth_out, trans_out, weights_out, nullptr, stream);
+}
+
+extern "C" int nacc_render_bwd(int64_t n_rays, const int64_t* offsets, const float* t_starts,
+                               const float* t_ends, const float* sigmas, const float* rgbs,
+                               const float* bg, float early_stop_eps, const float* g_rgb,
+                               const float* g_opacity, const float* g_depth, float* g_sigmas,
+                               float* g_rgbs, void* stream) {
+    clear_error();
+    return render_bwd_impl(n_rays, offsets, t_starts, t_ends, sigmas, rgbs, bg, early_stop_eps, g_rgb, g_opacity,
+                           g_depth, nullptr, g_sigmas, g_rgbs, stream);
+}
+
+extern "C" int nacc_render_fwd_ckpt(int64_t n_rays, const int64_t* offsets, const float* t_starts,
+                                    const float* t_ends, const float* sigmas, const float* rgbs,
+                                    const float* bg, float early_stop_eps, float* rgb_out,
+                                    float* opacity_out, float* depth_out, float* trans_out,
+                                    float* weights_out, float* ckpt_out, void* stream) {
+    clear_error();
+    NACC_CHECK_ARG(ckpt_out != nullptr, "ckpt_out is NULL");
+    NACC_CHECK_ARG(aligned16(ckpt_out), "ckpt_out must be 16-byte aligned");
+    return render_fwd_impl(n_rays, offsets, t_starts, t_ends, sigmas, rgbs, bg, early_stop_eps, rgb_out,
+                           opacity_out, depth_out, trans_out, weights_out, ckpt_out, stream);
+}
+
+extern "C" int nacc_render_bwd_ckpt(int64_t n_rays, const int64_t* offsets, const float* t_starts,
+                                    const float* t_ends, const float* sigmas, const float* rgbs,
+                                    const float* bg, float early_stop_eps, const float* g_rgb,
+                                    const float* g_opacity, const float* g_depth, const float* ckpt,
+                                    float* g_sigmas, float* g_rgbs, void* stream) {
+    clear_error();
+    NACC_CHECK_ARG(ckpt != nullptr, "ckpt is NULL");
+    NACC_CHECK_ARG(aligned16(ckpt), "ckpt must be 16-byte aligned");
+    return render_bwd_impl(n_rays, offsets, t_starts, t_ends, sigmas, rgbs, bg, early_stop_eps, g_rgb, g_opacity,
+                           g_depth, ckpt, g_sigmas, g_rgbs, stream);
+}
+
+extern "C" size_t nacc_render_ckpt_bytes(int64_t n_rays) {
+    return n_rays > 0 ? (size_t)n_rays * kCkpt * sizeof(float) : 0;
 }
 
 extern "C" int nacc_device_status(void* stream, int32_t* status_out) {

@@ -147,6 +147,26 @@ def test_render_rejects_misaligned_sample_arrays(lib):
     assert lib.nacc_selftest_wait_timeout(0, None) == _abi.NACC_ERR_INVALID_ARG
 
 
+def test_render_ckpt_arguments(lib):
+    """The checkpointed render pair: 64 bytes of record per ray; a NULL or
+    misaligned record buffer is rejected on the host before any launch."""
+    from paper_2305_04966_gb300 import _abi
+    assert lib.nacc_render_ckpt_bytes(0) == 0 and lib.nacc_render_ckpt_bytes(-3) == 0
+    assert lib.nacc_render_ckpt_bytes(640000) == 640000 * 64
+    bg = (ctypes.c_float * 3)(1, 1, 1)
+    ok, bad = 1 << 20, (1 << 20) + 4
+    rc = lib.nacc_render_fwd_ckpt(4, ok, ok, ok, ok, ok, bg, 0.0, ok, ok, ok, ok, None, None, None)
+    assert rc == _abi.NACC_ERR_INVALID_ARG and b"ckpt_out" in lib.nacc_last_error()
+    rc = lib.nacc_render_fwd_ckpt(4, ok, ok, ok, ok, ok, bg, 0.0, ok, ok, ok, ok, None, bad, None)
+    assert rc == _abi.NACC_ERR_INVALID_ARG and b"16-byte" in lib.nacc_last_error()
+    rc = lib.nacc_render_bwd_ckpt(4, ok, ok, ok, ok, ok, bg, 0.0, None, None, None, None, ok, ok, None)
+    assert rc == _abi.NACC_ERR_INVALID_ARG and b"ckpt" in lib.nacc_last_error()
+    rc = lib.nacc_render_bwd_ckpt(4, ok, ok, ok, ok, ok, bg, 0.0, None, None, None, bad, ok, ok, None)
+    assert rc == _abi.NACC_ERR_INVALID_ARG and b"16-byte" in lib.nacc_last_error()
+    rc = lib.nacc_render_bwd_ckpt(4, ok, bad, ok, ok, ok, bg, 0.0, None, None, None, ok, ok, ok, None)
+    assert rc == _abi.NACC_ERR_INVALID_ARG  # the plain pair's checks still apply
+
+
 def test_march_count_event_hook_arguments(lib):
     from paper_2305_04966_gb300 import _abi
     assert lib.nacc_set_march_count_events(1 << 20, None) == _abi.NACC_ERR_INVALID_ARG
