@@ -27,6 +27,13 @@
 //     line of its colours in the chunk and of its next chunk's intervals and
 //     densities, so the colours the reverse pass reads are on their way.
 //     A ray longer than 32 chunks repeats the carry sweep per group of 32.
+//   * checkpointed pair (the _ckpt entry points): the forward pass also
+//     writes a 64-byte record per ray -- the carry before each of the first
+//     14 chunks, the cut and the kept depth -- and the adjoint reads it in
+//     place of the carry sweep, so it makes one reverse pass over the
+//     samples, naming the previous chunk's lines to L2 as it goes; rays of
+//     more than 14 chunks are marked absent and still swept.  The carries
+//     come from the same routine in both, so the results are bit-identical.
 // The kernels hold no locks and wait on nothing; the file also carries the
 // device status word and the bounded-wait self-test of the library.
 #include "async_copy.cuh"
