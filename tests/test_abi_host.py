@@ -2,13 +2,14 @@
 every symbol the headers declare, and rejects invalid arguments before
 touching the device."""
 import ctypes
+import glob
 import os
 import re
 
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADERS = [os.path.join(ROOT, "include", h) for h in ("nacc.h", "nacc_harness.h")]
+HEADERS = sorted(glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
 def declared_symbols():
@@ -34,6 +35,8 @@ def test_headers_declare_the_boundary():
               "nacc_render_bwd", "nacc_grid_points", "nacc_last_error"):
         assert n in names
     assert len(names) >= 13
+    assert len(HEADERS) >= 3  # the method, the harness, the learned proposal
+    assert "nacc_mlp_forward" in names and "nacc_render_fwd_ckpt" in names
 
 
 def test_library_exports_every_declared_symbol(lib):
