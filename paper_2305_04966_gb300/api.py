@@ -90,6 +90,31 @@ class OccupancyGrid:
                    torch.zeros(n // 32, dtype=_I32, device=device),
                    torch.zeros(n, dtype=_F32, device=device))
 
+    def state_dict(self) -> dict:
+        """The estimator's state for a training checkpoint (the update runs every
+        few steps and carries the EMA across them): geometry, bits, EMA; copies."""
+        return {"aabb_min": [float(v) for v in self.aabb_min], "aabb_max": [float(v) for v in self.aabb_max],
+                "res": int(self.res), "n_levels": int(self.n_levels), "bits": self.bits.detach().clone(),
+                "ema": None if self.ema is None else self.ema.detach().clone()}
+
+    @classmethod
+    def from_state_dict(cls, state: dict, device=None) -> "OccupancyGrid":
+        """Rebuild a grid saved by :meth:`state_dict` (on ``device``, default the
+        device the tensors were saved on); checks the sizes against the geometry."""
+        res, levels = int(state["res"]), int(state["n_levels"])
+        n = levels * res ** 3
+        bits, ema = state["bits"], state.get("ema")
+        if res < 1 or levels < 1 or n % 32:
+            raise ValueError(f"grid of {levels} levels of {res}^3 cells cannot be bit-packed")
+        if bits.dtype != _I32 or tuple(bits.shape) != (n // 32,):
+            raise ValueError(f"bits must be int32 [{n // 32}], got {bits.dtype} {tuple(bits.shape)}")
+        if ema is not None and (ema.dtype != _F32 or tuple(ema.shape) != (n,)):
+            raise ValueError(f"ema must be float32 [{n}], got {ema.dtype} {tuple(ema.shape)}")
+        dev = bits.device if device is None else torch.device(device)
+        return cls(tuple(float(v) for v in state["aabb_min"]), tuple(float(v) for v in state["aabb_max"]), res,
+                   levels, bits.to(dev).contiguous().clone(),
+                   None if ema is None else ema.to(dev).contiguous().clone())
+
     def c_struct(self) -> _abi.Grid:
         g = _abi.Grid()
         g.aabb_min[:] = [float(v) for v in self.aabb_min]
