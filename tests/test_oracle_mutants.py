@@ -10,6 +10,7 @@ under a temporary name), points the oracle package at the copy, runs the pins
 that cover the edited function, and requires at least one of them to fail.
 Nothing here touches the CUDA library; every mistake is planted on the CPU.
 """
+import inspect
 import os
 import subprocess
 import types
@@ -136,6 +137,40 @@ C_MUTANTS = [
     ("field: colour not normalised by the density", "static void orc_field_f64(",
      "c[a] = s > 0.0 ? acc[a] / s : 0.0;", "c[a] = acc[a];",
      ["test_line_integral_of_gaussian_blob"]),
+    ("march field: FP32 Gaussian exponent without the 1/2", "static float orc_sigma_f32(",
+     "float coef = -0.5f / sd2;", "float coef = -1.0f / sd2;", ["test_early_termination_cut"]),
+    ("render: alpha linearised (tau instead of 1 - exp(-tau))", "void orc_render_fwd(",
+     "double w = T * -expm1(-tau);", "double w = T * tau;",
+     ["test_homogeneous_slab_closed_form", "test_weights_sum_to_one_minus_transmittance"]),
+    ("grid points: every level placed on level 0's lattice", "void orc_grid_points(",
+     "xyz_out[3 * c + a] = lv[l].lmin[a] + q * lv[l].width[a];",
+     "xyz_out[3 * c + a] = lv[0].lmin[a] + q * lv[0].width[a];", ["test_grid_points_centres_and_jitter"]),
+    ("EMA: mean over n - 1 cells", "void orc_update_grid(",
+     "double mean = n_cells > 0 ? sum / (double)n_cells : 0.0;",
+     "double mean = n_cells > 1 ? sum / (double)(n_cells - 1) : 0.0;",
+     ["test_update_grid_threshold_and_bit_layout"]),
+    ("inverse CDF: last CDF value not forced to 1", "void orc_sample_pdf(",
+     "F[n_bins] = 1.0f;", "F[n_bins] = F[n_bins - 1];",
+     ["test_sample_pdf_uniform_weights_give_linspace", "test_sample_pdf_piecewise_constant_inverse"]),
+    ("inverse CDF: zero total weight gives a degenerate CDF", "void orc_sample_pdf(",
+     "for (int j = 0; j <= n_bins; ++j) F[j] = (float)j / (float)n_bins;",
+     "for (int j = 0; j <= n_bins; ++j) F[j] = 0.0f;",
+     ["test_sample_pdf_uniform_weights_give_linspace"]),
+    ("inverse contraction: no clamp below m' = 2", "void orc_uncontract_points(",
+     "float mc = mp < mmax ? mp : mmax;", "float mc = mp;", ["test_uncontract32_inverts_the_contraction"]),
+]
+
+# mistakes planted in one function of the oracle package's numpy wrappers
+# (function, text replaced, replacement, pins that must catch it)
+WRAPPER_MUTANTS = [
+    ("density_grid", "words = occ.reshape(-1, 32).astype(np.uint64) << np.arange(32, dtype=np.uint64)",
+     "words = occ.reshape(-1, 32).astype(np.uint64) << (31 - np.arange(32, dtype=np.uint64))",
+     ["test_density_grid_cells_and_bit_layout"]),
+    ("density_grid", "occ = sig > thresh", "occ = sig > 10.0 * thresh", ["test_density_grid_cells_and_bit_layout"]),
+    ("density_grid_contracted", "sig = field_points(uncontract32(pts), blobs, n_threads)",
+     "sig = field_points(pts, blobs, n_threads)", ["test_density_grid_contracted_cells"]),
+    ("update_grid", "e = np.array(ema, dtype=np.float32, copy=True)", "e = np.zeros_like(np.asarray(ema, np.float32))",
+     ["test_update_grid_ema_closed_form"]),
 ]
 
 PY_MUTANTS = [
@@ -210,7 +245,8 @@ def orc_built():
 
 
 def test_unmutated_oracle_passes_every_listed_pin(orc_built):
-    names = sorted({n for m in C_MUTANTS for n in m[4]} | {n for m in PY_MUTANTS for n in m[4]})
+    names = sorted({n for m in C_MUTANTS for n in m[4]} | {n for m in PY_MUTANTS for n in m[4]}
+                   | {n for m in WRAPPER_MUTANTS for n in m[3]})
     assert _expect_caught(names, orc_built) == []
 
 
@@ -229,6 +265,18 @@ def test_planted_mistake_in_oracle_c_is_caught(case, orc_built, tmp_path, monkey
     monkeypatch.setattr(oracle, "_lib", oracle.load(str(so)))
     failed = _expect_caught(names, oracle)
     assert failed, f"planted mistake '{name}' passes every pin in {names}"
+
+
+@pytest.mark.parametrize("case", WRAPPER_MUTANTS, ids=[f"{m[0]}: {m[2][:40]}" for m in WRAPPER_MUTANTS])
+def test_planted_mistake_in_oracle_wrapper_is_caught(case, orc_built, monkeypatch):
+    fname, old, new, names = case
+    src = inspect.getsource(getattr(oracle, fname))
+    assert src.count(old) == 1, f"edit site in {fname} is not unique"
+    ns = dict(vars(oracle))
+    exec(compile(src.replace(old, new), oracle.__file__, "exec"), ns)
+    monkeypatch.setattr(oracle, fname, ns[fname])
+    failed = _expect_caught(names, oracle)
+    assert failed, f"planted mistake in {fname} passes every pin in {names}"
 
 
 @pytest.mark.parametrize("case", PY_MUTANTS, ids=[m[1] for m in PY_MUTANTS])

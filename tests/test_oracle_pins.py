@@ -458,6 +458,55 @@ def test_grid_points_centres_and_jitter(orc):
     assert j[0, 0] == pytest.approx(-1.5 + u0 * 3.0 / res, abs=1e-6)
 
 
+def _blob_density64(x, blobs):
+    """float64 blob density at points x [n][3], written from the field's definition."""
+    d2 = ((x[:, None, :] - blobs.mu.astype(np.float64)[None]) ** 2).sum(-1)
+    s = blobs.std.astype(np.float64)[None]
+    return (blobs.peak.astype(np.float64)[None] * np.exp(-d2 / (2 * s * s))).sum(1)
+
+
+def test_density_grid_cells_and_bit_layout(orc):
+    """Initial grid (cells occupied where the density at the cell centre exceeds
+    0.01): float64 centres from the level geometry, float64 density, and the bit
+    layout (cell c is bit c % 32 of word c // 32), away from threshold ties."""
+    blobs = workloads.blob_field(4, 91)
+    spec = workloads.GridSpec((-1.5,) * 3, (1.5,) * 3, 8, 2)
+    bits, sig = orc.density_grid(spec, blobs, 0.01)
+    res, L = spec.res, spec.n_levels
+    idx = np.arange(res ** 3)
+    i = np.stack([idx // (res * res), (idx // res) % res, idx % res], -1)
+    x = np.concatenate([-1.5 * 2 ** l + (i + 0.5) * (3.0 * 2 ** l / res) for l in range(L)])
+    dens = _blob_density64(x, blobs)
+    np.testing.assert_allclose(sig, dens, rtol=1e-5, atol=1e-30)
+    occ = workloads.unpack_bits(bits).astype(bool)
+    clear = np.abs(dens - 0.01) > 1e-6 * 0.01
+    np.testing.assert_array_equal(occ[clear], (dens > 0.01)[clear])
+    assert 0 < occ.sum() < occ.size
+
+
+def test_density_grid_contracted_cells(orc):
+    """Grid over the contracted cube: a cell is occupied where the density at the
+    scene point of its centre (the inverse contraction, float64 closed form
+    x = c / (m'(2 - m')) for m' = max|c_a| > 1) exceeds 0.01."""
+    blobs = workloads.Blobs(mu=np.array([[3.0, 0.5, -1.0], [0.2, 0.1, 0.0], [-6.0, 2.0, 1.0]], np.float32),
+                            std=np.array([0.8, 0.2, 1.5], np.float32), peak=np.array([5.0, 8.0, 3.0], np.float32),
+                            rgb=np.zeros((3, 3), np.float32))
+    spec = workloads.GridSpec((-0.5,) * 3, (0.5,) * 3, 8, 3)  # level 2 covers [-2, 2]^3
+    bits, sig = orc.density_grid_contracted(spec, blobs, 0.01)
+    res, L = spec.res, spec.n_levels
+    idx = np.arange(res ** 3)
+    i = np.stack([idx // (res * res), (idx // res) % res, idx % res], -1)
+    c = np.concatenate([-0.5 * 2 ** l + (i + 0.5) * (1.0 * 2 ** l / res) for l in range(L)])
+    mp = np.abs(c).max(1)
+    x = np.where((mp > 1)[:, None], c / (mp * (2 - mp))[:, None], c)
+    dens = _blob_density64(x, blobs)
+    occ = workloads.unpack_bits(bits).astype(bool)
+    clear = np.abs(dens - 0.01) > 1e-4 * 0.01
+    np.testing.assert_array_equal(occ[clear], (dens > 0.01)[clear])
+    outer = mp > 1
+    assert occ[outer].sum() > 5 and (~occ[outer]).sum() > 5  # the far blobs are found through the inverse
+
+
 def test_update_grid_ema_closed_form(orc):
     """EMA of Sec. 3.1 (Eq. 4): constant input d gives e_k = g^k e_0 + (1-g^k) d."""
     n = 64 * 32
