@@ -216,7 +216,7 @@ int nacc_update_grid(const nacc_grid* grid, float* ema, const float* density, fl
                      size_t scratch_bytes, void* stream);
 
 /*
- * Estimator update for dynamic scenes (Sec. 5 "Dynamic NeRFs": one grid
+ * Estimator update for dynamic scenes (Sec. 4.3 "Dynamic NeRFs": one grid
  * shared by all frames marks the maximum occupancy over the timestamps): as
  * nacc_update_grid with density[c] = max over f < n_frames of
  * densities[f * n_cells + c].  n_frames = 1 is nacc_update_grid.

@@ -1,6 +1,6 @@
 """Oracle of the estimator-update variants (TEST INFRASTRUCTURE ONLY).
 
-* Dynamic scenes (Sec. 5 "Dynamic NeRFs"): one occupancy grid for all frames
+* Dynamic scenes (Sec. 4.3 "Dynamic NeRFs"): one occupancy grid for all frames
   marks the maximum occupancy over the timestamps -- the EMA update of
   ``oracle.update_grid`` fed with the per-cell maximum over the frames.
 * Gradient-descent update (the Plenoxels variant named in Sec. 3.1 "Spatial
