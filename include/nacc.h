@@ -96,15 +96,18 @@ typedef struct nacc_packed {
     int64_t* n_samples;   /* [device] 1 element: total sample count, written */
 } nacc_packed;
 
-/* Message describing the last error on the calling thread ("" if none). */
+/* Message describing the last error on the calling thread ("" if none).
+ * Library plumbing, no passage of the paper. */
 const char* nacc_last_error(void);
 
-/* Library version (major*10000 + minor*100 + patch). */
+/* Library version (major*10000 + minor*100 + patch).  Library plumbing. */
 int nacc_version(void);
 
-/* Scratch bytes nacc_march_grid needs for n_rays rays: per-ray counts,
- * stops and run records (~150 bytes per ray) plus the grid's block
- * summaries sized for the largest grid (8 levels of 1024^3 cells: 32.5 MiB). */
+/* Scratch bytes nacc_march_grid needs for n_rays rays (the per-ray counts
+ * from which the packed tensor's offsets are built, Sec. 4.2 "Packed
+ * Tensor"): per-ray counts, stops and run records (~150 bytes per ray) plus
+ * the grid's block summaries sized for the largest grid (8 levels of 1024^3
+ * cells: 32.5 MiB).  Pure size arithmetic: no device work, no error status. */
 size_t nacc_march_scratch_bytes(int64_t n_rays);
 
 /*
@@ -141,7 +144,8 @@ int nacc_march_grid(const nacc_grid* grid, const float* rays_o, const float* ray
                     size_t scratch_bytes, void* stream);
 
 /* Scratch bytes nacc_march_unbounded needs for n_rays rays and a lattice of
- * max_steps points (0 for invalid arguments). */
+ * max_steps points (Sec. 3.2 "Handling Unbounded Scenes"; 0 for invalid
+ * arguments).  Pure size arithmetic. */
 size_t nacc_march_unbounded_scratch_bytes(int64_t n_rays, int32_t max_steps);
 
 /*
@@ -196,7 +200,9 @@ int nacc_uncontract_points(int64_t n, const float* c_in, float* x_out, void* str
 int nacc_grid_points(const nacc_grid* grid, uint64_t seed, int64_t step, int32_t jitter,
                      float* xyz_out, void* stream);
 
-/* Scratch bytes nacc_update_grid needs for n_cells cells. */
+/* Scratch bytes nacc_update_grid needs for n_cells cells (the FP64 partial
+ * sums of the mean that sets the threshold of Table 1's binarisation).  Pure
+ * size arithmetic. */
 size_t nacc_update_grid_scratch_bytes(int64_t n_cells);
 
 /*
@@ -244,9 +250,12 @@ int nacc_grid_density_backward(const nacc_grid* grid, const float* rays_o, const
                                const int64_t* n_samples, const float* g_sigma, float* g_density, void* stream);
 
 /*
- * One gradient step of that grid: density[c] = max(density[c] - lr *
- * g_density[c], 0) (FP32, rounded in this order), g_density[c] = 0, bit c of
- * bits_out = (density[c] > thresh).
+ * One gradient step of that grid (Sec. 3.1 "Spatial Skipping": Plenoxels
+ * updates the cached density by gradient descent through the rendering
+ * loss): density[c] = max(density[c] - lr * g_density[c], 0) (FP32, rounded
+ * in this order), g_density[c] = 0, bit c of bits_out = (density[c] >
+ * thresh).  density, g_density: [device] [n_levels*res^3]; bits_out:
+ * [device] n_cells/32 words.  Invalid sizes or NULL -> NACC_ERR_INVALID_ARG.
  */
 int nacc_update_grid_sgd(const nacc_grid* grid, float* density, float* g_density, float lr, float thresh,
                          uint32_t* bits_out, void* stream);

@@ -31,7 +31,8 @@ int nacc_harness_field(const float* rays_o, const float* rays_d, const int32_t* 
                        const nacc_blob_field* field, float* sigmas, float* rgbs, void* stream);
 
 /*
- * The same field for a packed sample set given by its CSR offsets
+ * The same field (harness: Algorithm 1's rgb_density_fn) for a packed sample
+ * set given by its CSR offsets
  * [n_rays+1] (no ray_indices needed): one warp per ray evaluates the blobs
  * along the ray in the closed form peak_b 2^(A_b (t - t*_b)^2 + C_b) (t*_b
  * the closest approach, set up once per ray) with the hardware exp2; the
@@ -46,12 +47,16 @@ int nacc_harness_field_rays(const float* rays_o, const float* rays_d, int64_t n_
                             const float* t_starts, const float* t_ends, const nacc_blob_field* field,
                             float* sigmas, float* rgbs, void* stream);
 
-/* Density of the blob field at n points xyz [n][3] -> sigma [n] (both [device]). */
+/* Density of the blob field (harness: Algorithm 1's density_fn, here for the
+ * estimator update's cell points) at n points xyz [n][3] -> sigma [n] (both
+ * [device]). */
 int nacc_harness_field_points(int64_t n, const float* xyz, const nacc_blob_field* field,
                               float* sigma, void* stream);
 
 /*
- * Mean squared error against a target image and its gradient:
+ * Harness loss (Algorithm 1's training loss, whose gradient rendering
+ * back-propagates): mean squared error against a target image and its
+ * gradient:
  *   loss = sum (rgb - target)^2 / (3 n),  g_rgb = 2 (rgb - target) / (3 n).
  * rgb, target, g_rgb: [device] [n][3]; loss: [device] 1 float.
  */
@@ -59,7 +64,8 @@ int nacc_harness_l2_loss(int64_t n, const float* rgb, const float* target, float
                          float* loss, void* stream);
 
 /*
- * Device status of the bounded waits inside the library's kernels (the
+ * Library plumbing, no passage of the paper.  Device status of the bounded
+ * waits inside the library's kernels (the
  * proposal network's tensor-core kernels and the wait self-test).  Every
  * wait on an mbarrier gives up after 2 s of GPU wall time; the kernel then
  * records the expiry in a device status word and returns instead of hanging.  This call synchronises `stream`, reads and
@@ -69,7 +75,8 @@ int nacc_harness_l2_loss(int64_t n, const float* rgb, const float* target, float
 int nacc_device_status(void* stream, int32_t* status_out);
 
 /*
- * Diagnostics: launches one tiny kernel that waits, with the library's
+ * Diagnostics (library plumbing): launches one tiny kernel that waits, with
+ * the library's
  * bounded-wait routine, on an mbarrier nothing will ever arrive on, giving up
  * after limit_ns nanoseconds (0 < limit_ns <= 1e8).  The expiry is reported
  * through nacc_device_status; the context stays usable.
@@ -77,7 +84,8 @@ int nacc_device_status(void* stream, int32_t* status_out);
 int nacc_selftest_wait_timeout(int64_t limit_ns, void* stream);
 
 /*
- * Diagnostics: timing of the count phase of nacc_march_grid (the run walk
+ * Diagnostics (library plumbing): timing of the count phase of
+ * nacc_march_grid (the run walk
  * and, with a field, the early-stop pass).  While set (by the calling host
  * thread), every nacc_march_grid call of that thread records `before` on its
  * stream just before the run-walk kernel and `after` just after the

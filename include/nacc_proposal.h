@@ -34,16 +34,22 @@ extern "C" {
 #define NACC_MLP_PARAMS 8385
 #define NACC_MLP_WEIGHTS 8256
 
-/* BF16 copies of the weights of `params` (round to nearest, ties to even). */
+/* BF16 copies of the weights of `params` (round to nearest, ties to even):
+ * the tensor-core operands of the proposal network (Sec. 3.1 "PDF
+ * Approaches").  params [NACC_MLP_PARAMS] FP32, weights [NACC_MLP_WEIGHTS]. */
 int nacc_mlp_sync(const float* params, uint16_t* weights, void* stream);
 
-/* Density at n points xyz [n][3] -> sigma [n]. */
+/* Density of the proposal network (Sec. 3.1 "PDF Approaches": a small MLP
+ * predicts the densities whose transmittance is the estimator) at n points
+ * xyz [n][3] -> sigma [n]. */
 int nacc_mlp_forward(int64_t n, const float* xyz, const float* params, const uint16_t* weights,
                      float* sigma, void* stream);
 
 /*
  * Training, fused forward + adjoint over a batch of n points with target
- * densities: loss L = (1/n) sum (density - target)^2.  Adds dL/dparams
+ * densities (the estimator update F of Eq. 4 by gradient descent, as the
+ * PDF approaches of Sec. 3.1 update theirs; the target here is the
+ * analytic field's density): loss L = (1/n) sum (density - target)^2.  Adds dL/dparams
  * (layout of `params`) into grads [NACC_MLP_PARAMS] and sum (density -
  * target)^2 into *loss_sum (both [device], accumulated: the caller zeroes
  * them, or nacc_mlp_adam does).  The weight gradients are tensor-core
@@ -53,7 +59,8 @@ int nacc_mlp_train_grads(int64_t n, const float* xyz, const float* target, const
                          const uint16_t* weights, float* grads, float* loss_sum, void* stream);
 
 /*
- * One Adam step on the FP32 master parameters (step = 1, 2, ...; bias
+ * The gradient-descent step of that update (Eq. 4 with SGD-type F, Sec. 3.1):
+ * one Adam step on the FP32 master parameters (step = 1, 2, ...; bias
  * correction 1 - beta^step), then writes the BF16 weights and zeroes grads.
  * m, v: [device] [NACC_MLP_PARAMS] moment estimates (zero before step 1).
  */
@@ -61,7 +68,8 @@ int nacc_mlp_adam(float* params, float* grads, float* m, float* v, int64_t step,
                   float beta2, float eps, uint16_t* weights, void* stream);
 
 /*
- * Density at the midpoints of the bins of rays: point (r, j) = o_r + t d_r
+ * Density at the midpoints of the bins of rays, the piecewise-constant
+ * densities of Sec. 3.1 "PDF Approaches": point (r, j) = o_r + t d_r
  * with t = (edges[r][j] + edges[r][j+1]) / 2 (FP32) -> sigma [n_rays][n_bins];
  * edges [n_rays][n_bins+1].  Same network and precision as nacc_mlp_forward.
  */
@@ -70,7 +78,8 @@ int nacc_mlp_forward_rays(int64_t n_rays, int32_t n_bins, const float* rays_o, c
                           void* stream);
 
 /*
- * Initial bins of the proposal estimator: [t_near, t_far] = slab clip of
+ * Initial bins of the proposal estimator over the bounded range [t_n, t_f]
+ * of Sec. 3.1 (Eq. 1): [t_near, t_far] = slab clip of
  * each ray against the box of the grid's level 0 (individually rounded FP32,
  * as in nacc_march_grid), intersected with [t_min, t_max], cut into n_bins
  * equal bins: edges[r][j] = t_near + (t_far - t_near) * (j / n_bins) (each
@@ -90,7 +99,8 @@ int nacc_dense_weights(int64_t n_rays, int32_t n_bins, const float* edges, const
                        float* trans_out, void* stream);
 
 /*
- * The bins as packed samples (nacc_packed layout without ray_indices):
+ * The bins as packed samples (Sec. 4.2 "Packed Tensor"; nacc_packed layout
+ * without ray_indices):
  * offsets[r] = r * n_bins, t_starts[r*n_bins + j] = edges[r][j], t_ends =
  * edges[r][j+1], *n_samples = n_rays * n_bins (all [device]).
  */
@@ -98,7 +108,8 @@ int nacc_edges_to_packed(int64_t n_rays, int32_t n_bins, const float* edges, int
                          float* t_ends, int64_t* n_samples, void* stream);
 
 /*
- * Combined estimator (the occupancy grid stacked on the proposal network):
+ * Combined estimator (the occupancy grid stacked on the proposal network,
+ * Sec. 3.3 "Insights from Unified Formulation", Sec. 4.4 "Combined Sampling"):
  * the occupied range of each ray -- t0 of its first and t1 of its last
  * occupied lattice point, i.e. of the samples nacc_march_grid would emit
  * without a field (same FP32 lattice definition) -- into t_lo, t_hi
@@ -114,8 +125,9 @@ int nacc_occupied_range(const nacc_grid* grid, const float* rays_o, const float*
                         size_t scratch_bytes, void* stream);
 
 /*
- * n_bins equal bins of [t_lo[r], t_hi[r]] per ray, the arithmetic of
- * nacc_uniform_edges -> edges [n_rays][n_bins+1].
+ * n_bins equal bins of [t_lo[r], t_hi[r]] per ray (the combined estimator's
+ * initial bins, Sec. 4.4), the arithmetic of nacc_uniform_edges -> edges
+ * [n_rays][n_bins+1].
  */
 int nacc_range_edges(int64_t n_rays, const float* t_lo, const float* t_hi, int32_t n_bins, float* edges,
                      void* stream);
@@ -132,22 +144,26 @@ int nacc_mlp_forward_rays_contracted(int64_t n_rays, int32_t n_bins, const float
                                      float* sigma, void* stream);
 
 /*
- * The contraction itself for n points (e.g. the training inputs of the
+ * The contraction itself (Sec. 3.2 "Handling Unbounded Scenes") for n
+ * points (e.g. the training inputs of the
  * proposal network for unbounded scenes): x_in, c_out [device] [n][3]
  * (may alias).
  */
 int nacc_contract_points(int64_t n, const float* x_in, float* c_out, void* stream);
 
 /*
- * Initial bins of the proposal estimator for unbounded scenes: uniform in
- * s, mapped to t by the disparity-linear Phi of nacc_march_unbounded:
+ * Initial bins of the proposal estimator for unbounded scenes (Sec. 3.2
+ * "Handling Unbounded Scenes": sampling uniform in s through a bijection
+ * Phi): uniform in s, mapped to t by the disparity-linear Phi of
+ * nacc_march_unbounded:
  * edges[r][j] = 1 / (a (1 - s_j) + b s_j), s_j = j / n_bins, a = 1/t_near,
  * b = 1/t_far (FP32, each operation rounded), the same row for every ray.
  * edges: [device] [n_rays][n_bins+1].  Requires 0 < t_near < t_far < inf.
  */
 int nacc_phi_edges(int64_t n_rays, int32_t n_bins, float t_near, float t_far, float* edges, void* stream);
 
-/* Diagnostics: the FP32 encoding e(x) of n points -> enc [n][64]. */
+/* Diagnostics: the FP32 frequency encoding e(x) that the proposal network
+ * (Sec. 3.1 "PDF Approaches") reads, for n points -> enc [n][64]. */
 int nacc_mlp_encode(int64_t n, const float* xyz, float* enc, void* stream);
 
 #ifdef __cplusplus

@@ -39,6 +39,23 @@ def test_headers_declare_the_boundary():
     assert "nacc_mlp_forward" in names and "nacc_render_fwd_ckpt" in names
 
 
+def test_every_declaration_cites_its_passage_or_says_it_has_none():
+    """Each entry point's comment names the passage of the paper it follows
+    (equation, section, table, algorithm, appendix), or says that it is
+    library plumbing, harness, size arithmetic, or has no counterpart."""
+    missing = []
+    for h in HEADERS:
+        src = open(h).read()
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(nacc_\w+)\s*\(", src, flags=re.M):
+            before = src[:m.start()]
+            j = before.rfind("*/")
+            com = before[before.rfind("/*", 0, j):j] if j >= 0 else ""
+            if not re.search(r"Eq\.|Sec\.|Table|Algorithm|Appendix|no counterpart|plumbing|harness|size arithmetic",
+                             com):
+                missing.append(f"{os.path.basename(h)}:{m.group(1)}")
+    assert not missing, missing
+
+
 def test_library_exports_every_declared_symbol(lib):
     from paper_2305_04966_gb300 import _abi
     for name in declared_symbols():
