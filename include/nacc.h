@@ -321,7 +321,7 @@ int nacc_sample_pdf(int64_t n_rays, int32_t n_bins, const float* edges, const fl
  * offsets: [device] [n_rays+1] CSR with offsets[0] = 0 (the total sample
  * count is read on the device from offsets[n_rays]); t_starts, t_ends,
  * sigmas: [device] [S]; rgbs: [device] [S][3], all four 16-byte aligned
- * (they are streamed with bulk asynchronous copies); bg: [host] 3 floats;
+ * (groups of four samples move as 128-bit loads); bg: [host] 3 floats;
  * outputs [device]: rgb_out [n_rays][3], opacity_out, depth_out, trans_out
  * [n_rays]; weights_out [S] or NULL.
  */

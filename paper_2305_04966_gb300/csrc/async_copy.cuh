@@ -1,6 +1,8 @@
-// async_copy.cuh -- inline-PTX helpers for bulk asynchronous copies (TMA
-// engine, 1-D `cp.async.bulk`) and shared-memory mbarriers on sm_100+/sm_103a,
-// with time-bounded waits.  Own wrappers over the PTX ISA instructions.
+// async_copy.cuh -- inline-PTX helpers for shared-memory mbarriers on
+// sm_100+/sm_103a with time-bounded waits: the completion waits of the
+// tensor-core kernels (tcgen05.commit arrives on an mbarrier) and the wait
+// self-test.  Own wrappers over the PTX ISA instructions.  (The file once
+// also held the bulk-copy helpers of an earlier render design.)
 #pragma once
 
 #include <stdint.h>
@@ -21,31 +23,16 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 
-// Make mbarrier initialisation visible to the asynchronous (copy engine) proxy.
+// Make mbarrier initialisation visible to the asynchronous proxy.
 __device__ __forceinline__ void fence_barrier_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 // Order this thread's generic shared-memory accesses before later
-// asynchronous-proxy accesses (bulk copies) to the same memory.
+// asynchronous-proxy accesses (tensor-core operand reads) to the same memory.
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-// Raise the barrier's expected transaction count without arriving.
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
@@ -69,21 +56,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
         if (mbar_try_wait(bar, parity)) return true;
         if (global_timer_ns() - t0 > limit_ns) return false;
     }
-}
-
-// 1-D bulk copy global -> shared (this CTA), completion counted in bytes on
-// `bar`.  dst, src 16-byte aligned; bytes a multiple of 16.
-__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-
-// Named barrier over `count` threads (a multiple of 32) of the CTA.
-__device__ __forceinline__ void named_barrier(int id, int count) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
 }  // namespace nacc
