@@ -194,6 +194,18 @@ PY_MUTANTS = [
     ("proposal", "Adam: no bias correction",
      "mh, vh = m / (1 - b1 ** t), v / (1 - b2 ** t)", "mh, vh = m, v",
      ["test_proposal_adam_first_step_closed_form"]),
+    ("proposal", "BF16: ties rounded away from zero",
+     "u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16", "u = ((u + 0x8000) >> 16) << 16",
+     ["test_bf16_rounding_matches_torch_bfloat16"]),
+    ("proposal", "BF16: truncation instead of rounding",
+     "u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16", "u = (u >> 16) << 16",
+     ["test_bf16_rounding_matches_torch_bfloat16", "test_proposal_forward_rounds_every_operand"]),
+    ("proposal", "network: first hidden layer not rounded to BF16",
+     "h1 = r(np.maximum(z1, 0.0))", "h1 = np.maximum(z1, 0.0)", ["test_proposal_forward_rounds_every_operand"]),
+    ("proposal", "network: weights not rounded to BF16",
+     'W1, W2, w3 = r(params["W1"]), r(params["W2"]), r(params["w3"])',
+     'W1, W2, w3 = (np.asarray(params[k], np.float64) for k in ("W1", "W2", "w3"))',
+     ["test_proposal_forward_rounds_every_operand"]),
     ("proposal", "exact depth: closest approach without the 1/|d|^2",
      "ts = (m @ d[i]) / dd", "ts = (m @ d[i])", ["test_exact_optical_depth_matches_fine_quadrature"]),
     ("grid_variants", "sample cells: the coarsest level wins",

@@ -642,6 +642,51 @@ def test_proposal_forward_hand_built_network():
     np.testing.assert_allclose(P.forward(p, x)["sigma"], np.log1p(np.exp(z)), rtol=1e-15)
 
 
+def test_bf16_rounding_matches_torch_bfloat16():
+    """The network's operand precision: round to the nearest bfloat16, ties to
+    even, bit for bit the same as torch's float32 -> bfloat16 conversion (an
+    independent library routine), on random values and on hand-picked ties."""
+    torch = pytest.importorskip("torch")
+    from oracle import proposal as P
+    g = workloads.rng(97)
+    x = np.concatenate([g.standard_normal(200_000) * 10.0 ** g.integers(-6, 6, 200_000),
+                        1.0 + np.array([2.0 ** -8, 3 * 2.0 ** -8, 2.0 ** -8 + 2.0 ** -20, -2.0 ** -9]),
+                        np.array([0.0, -0.0, 1e-40, 3.0e38])]).astype(np.float32)
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float32).numpy()
+    got = P.bf16(x).astype(np.float32)
+    np.testing.assert_array_equal(got.view(np.uint32), ref.view(np.uint32))
+    assert P.bf16(np.float32(1.0 + 2.0 ** -8)) == 1.0  # tie -> even mantissa
+    assert P.bf16(np.float32(1.0 + 3 * 2.0 ** -8)) == 1.0 + 2.0 ** -6
+
+
+def test_proposal_forward_rounds_every_operand():
+    """Inputs, weights and both hidden layers enter the products as bfloat16
+    (biases FP32): a hand-built network whose values are not representable in
+    bfloat16, against the same network evaluated with torch's bfloat16
+    conversion at each operand."""
+    torch = pytest.importorskip("torch")
+    from oracle import proposal as P
+
+    def tb(v):
+        return torch.tensor(np.asarray(v, np.float64), dtype=torch.float32).to(torch.bfloat16).double().numpy()
+
+    W1 = np.zeros((64, 64), np.float32)
+    W1[0, 0], W1[1, 1], W1[2, 2] = 1.0 + 2.0 ** -10, 0.7, 1.3
+    W2 = np.eye(64, dtype=np.float32) * np.float32(0.9)
+    w3 = np.zeros(64, np.float32)
+    w3[:3] = [1.1, 0.6, 0.85]
+    p = {"W1": W1, "b1": np.full(64, 1.0 / 3.0, np.float32), "W2": W2, "b2": np.full(64, -0.1, np.float32),
+         "w3": w3, "b3": np.array([-0.2], np.float32)}
+    x = np.array([[0.1234, -0.05, 0.77], [0.3, 0.3001, -0.2], [0.91, 0.42, 0.05]])
+    e = tb(x)  # the first three encoding entries are the coordinates
+    z1 = e * tb(np.diag(W1)[:3])[None] + np.float32(1.0 / 3.0)
+    h1 = tb(np.maximum(z1, 0.0))
+    z2 = h1 * tb(np.float32(0.9)) + np.float32(-0.1)
+    h2 = tb(np.maximum(z2, 0.0))
+    z3 = h2 @ tb(w3[:3]) + np.float32(-0.2)
+    np.testing.assert_allclose(P.forward(p, x)["sigma"], np.log1p(np.exp(z3)), rtol=1e-12)
+
+
 def test_proposal_gradients_match_finite_differences():
     from oracle import proposal as P
     g0 = np.random.default_rng(11)
