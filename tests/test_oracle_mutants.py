@@ -54,6 +54,9 @@ C_MUTANTS = [
     ("occupancy: coarsest level searched first", "static int orc_occupied(",
      "for (int l = 0; l < L; ++l) {", "for (int l = L - 1; l >= 0; --l) {",
      ["test_cascade_selects_finest_level"]),
+    ("occupancy: half-open level box", "static int orc_occupied(",
+     "if (!(x[a] >= lv[l].lmin[a] && x[a] <= lv[l].lmax[a])) inside = 0;",
+     "if (!(x[a] >= lv[l].lmin[a] && x[a] < lv[l].lmax[a])) inside = 0;", ["test_level_box_is_closed"]),
     ("occupancy: cell from the box width, not its scale", "static int orc_occupied(",
      "float u = (x[a] - lv[l].lmin[a]) * lv[l].scale[a];", "float u = (x[a] - lv[l].lmin[a]) * lv[l].width[a];",
      ["test_single_occupied_cell", "test_brute_force_random_grids"]),

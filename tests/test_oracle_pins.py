@@ -216,6 +216,23 @@ def test_cascade_selects_finest_level(orc):
     assert out["offsets"][-1] > 1000
 
 
+def test_level_box_is_closed(orc):
+    """A midpoint exactly on the face of level 0's box belongs to level 0 (the
+    finest level whose closed box holds it).  Axis-parallel ray from x = 1/8
+    with step 1/4: midpoints x = (k+1)/4 exactly in FP32, k = 5 on the face
+    x = 3/2.  Level 0 full, level 1 empty: k = 0..5 emitted, 6 samples, both
+    for the upper face (+x) and the lower face (-x)."""
+    res, L = 4, 2
+    occ = np.zeros(L * res ** 3, bool)
+    occ[:res ** 3] = True
+    bits = workloads.pack_bits(occ)
+    o = np.array([[0.125, 0.3, 0.2], [-0.125, 0.3, 0.2]], np.float32)
+    d = np.array([[1.0, 0.0, 0.0], [-1.0, 0.0, 0.0]], np.float32)
+    out = orc.march(o, d, (-1.5,) * 3, (1.5,) * 3, res, L, bits, 0.25, 64, 0.0, 1e10)
+    np.testing.assert_array_equal(np.diff(out["offsets"]), [6, 6])
+    np.testing.assert_array_equal(out["t_starts"][:6], 0.25 * np.arange(6))
+
+
 def test_miss_and_inside_origin(orc):
     bits = np.full(8 ** 3 // 32, 0xFFFFFFFF, np.uint32)
     o = np.array([[5.0, 5.0, 5.0], [0.0, 0.0, 0.0], [0.0, 3.0, 0.0]], np.float32)
