@@ -191,6 +191,9 @@ PY_MUTANTS = [
     ("proposal", "adjoint: softplus derivative with the wrong sign",
      "/ (1.0 + np.exp(-f[\"z3\"]))", "/ (1.0 + np.exp(f[\"z3\"]))",
      ["test_proposal_gradients_match_finite_differences"]),
+    ("proposal", "adjoint: bias gradient of the second layer averaged instead of summed",
+     'g["W2"], g["b2"] = d2.T @ f["h1"], d2.sum(0)', 'g["W2"], g["b2"] = d2.T @ f["h1"], d2.mean(0)',
+     ["test_proposal_gradients_match_finite_differences"]),
     ("proposal", "adjoint: ReLU mask of the first layer missing",
      "d1 = (d2 @ W2) * (f[\"z1\"] > 0)", "d1 = (d2 @ W2)",
      ["test_proposal_gradients_match_finite_differences"]),
