@@ -66,6 +66,14 @@ C_MUTANTS = [
     ("render: background dropped", "void orc_render_fwd(",
      "rgb_out[3 * r + a] = acc[a] + TN * bg[a];", "rgb_out[3 * r + a] = acc[a];",
      ["test_homogeneous_slab_closed_form", "test_weights_sum_to_one_minus_transmittance"]),
+    ("render: first background channel for all three", "void orc_render_fwd(",
+     "for (int a = 0; a < 3; ++a) rgb_out[3 * r + a] = acc[a] + TN * bg[a];",
+     "for (int a = 0; a < 3; ++a) rgb_out[3 * r + a] = acc[a] + TN * bg[0];",
+     ["test_homogeneous_slab_closed_form"]),
+    ("adjoint: first background channel for all three", "void orc_render_bwd(",
+     "g += gC[a] * (Tn * rgbs[3 * i + a] - Sc[a] - TN * bg[a]);",
+     "g += gC[a] * (Tn * rgbs[3 * i + a] - Sc[a] - TN * bg[0]);",
+     ["test_gradient_matches_finite_differences"]),
     ("render: inclusive instead of exclusive transmittance", "void orc_render_fwd(",
      "double T = exp(-P);", "double T = exp(-(P + tau));",
      ["test_homogeneous_slab_closed_form", "test_weights_sum_to_one_minus_transmittance"]),

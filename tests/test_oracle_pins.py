@@ -314,13 +314,13 @@ def test_homogeneous_slab_closed_form(orc):
     te = (ts.astype(np.float64) + dt).astype(np.float32)
     dts = te.astype(np.float64) - ts
     c = np.array([0.2, 0.5, 0.9])
-    out = orc.render_fwd(np.array([0, N]), ts, te, np.full(N, s0), np.tile(c, (N, 1)),
-                         bg=(1.0, 1.0, 1.0))
+    bg = np.array([0.7, 0.1, 0.4])
+    out = orc.render_fwd(np.array([0, N]), ts, te, np.full(N, s0), np.tile(c, (N, 1)), bg=tuple(bg))
     L = dts.sum()
     TN = math.exp(-s0 * L)
     assert out["trans"][0] == pytest.approx(TN, rel=1e-12)
     assert out["opacity"][0] == pytest.approx(1 - TN, rel=1e-12)
-    np.testing.assert_allclose(out["rgb"][0], c * (1 - TN) + TN, rtol=1e-12)
+    np.testing.assert_allclose(out["rgb"][0], c * (1 - TN) + TN * bg, rtol=1e-12)
     Ti = np.exp(-s0 * np.concatenate([[0.0], np.cumsum(dts)[:-1]]))
     wi = Ti * (1 - np.exp(-s0 * dts))
     np.testing.assert_allclose(out["weights"], wi, rtol=1e-11)
@@ -398,10 +398,11 @@ def _fd_check(orc, p, eps, rays):
     gD = g.standard_normal(n)
     sig = p["sigmas"].astype(np.float64)
     rgb = p["rgbs"].astype(np.float64)
-    gs, gr = orc.render_bwd(p["offsets"], p["t_starts"], p["t_ends"], sig, rgb, gC, gA, gD, eps=eps)
+    bg = (0.2, 0.5, 0.9)  # a coloured background, so each channel's term is checked on its own
+    gs, gr = orc.render_bwd(p["offsets"], p["t_starts"], p["t_ends"], sig, rgb, gC, gA, gD, bg=bg, eps=eps)
 
     def loss(s, c):
-        o = orc.render_fwd(p["offsets"], p["t_starts"], p["t_ends"], s, c, eps=eps)
+        o = orc.render_fwd(p["offsets"], p["t_starts"], p["t_ends"], s, c, bg=bg, eps=eps)
         return (o["rgb"] * gC).sum() + (o["opacity"] * gA).sum() + (o["depth"] * gD).sum()
 
     off = p["offsets"]
