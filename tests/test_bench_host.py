@@ -46,3 +46,21 @@ def test_committed_traffic_records_name_existing_sources():
         path = os.path.join(bench.ROOT, "paper_2305_04966_gb300", "csrc", r["source"])
         assert os.path.exists(path), stage
         assert r["dram_bytes_per_sample"] >= 0 and r.get("dram_bytes_per_ray", 0.0) >= 0
+
+
+def test_reference_arm_prints_one_json_line():
+    """`bench.py --impl reference` times the CPU oracle on the host (no GPU) and
+    prints one JSON line with the arm's metric, unit, e2e and CPU-baseline keys."""
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0", "--width", "160", "--height", "160"], capture_output=True, text=True,
+                       timeout=600, cwd=bench.ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    rec = json.loads(lines[0])
+    assert rec["impl"] == "reference" and rec["metric"] == bench.METRIC and rec["unit"] == "rays/s"
+    assert rec["value"] > 0 and rec["higher_is_better"] is True and rec["n_gpus"] == 1
+    assert rec["cpu_baseline"]["kind"] == "oracle" and rec["cpu_baseline"]["cores"] >= 1
+    assert rec["e2e"]["h2d_bytes_per_step"] == 0 and rec["e2e"]["value"] == rec["value"]
