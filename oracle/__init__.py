@@ -94,6 +94,8 @@ def load(path: str):
     L.orc_uncontract_points.argtypes = [i64, vp, vp]
     L.orc_max_threads.restype = i32
     L.orc_max_threads.argtypes = []
+    L.orc_exp_steps_array.restype = None
+    L.orc_exp_steps_array.argtypes = [i64, vp, vp]
     return L
 
 
@@ -119,6 +121,16 @@ def max_threads() -> int:
 
 def _threads(n):
     return max_threads() if n is None else int(n)
+
+
+def exp_steps(a):
+    """The early-stop density's exponential, defined by its steps (Cody-Waite
+    reduction, degree-7 Taylor polynomial, FP32; 0 below -86): float32 in,
+    float32 out."""
+    a = _c(a, np.float32)
+    out = np.empty_like(a)
+    lib().orc_exp_steps_array(a.size, _ptr(a), _ptr(out))
+    return out
 
 
 def splitmix64_at(seed: int, counter: int) -> int:

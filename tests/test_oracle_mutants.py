@@ -150,6 +150,18 @@ C_MUTANTS = [
      ["test_line_integral_of_gaussian_blob"]),
     ("march field: FP32 Gaussian exponent without the 1/2", "static float orc_sigma_f32(",
      "float coef = -0.5f / sd2;", "float coef = -1.0f / sd2;", ["test_early_termination_cut"]),
+    ("defined exponential: degree-6 Taylor polynomial", "float orc_exp_steps(",
+     "float p = c[7];", "float p = 0.0f;", ["test_exp_steps_against_float64_exp"]),
+    ("defined exponential: low part of ln 2 dropped", "float orc_exp_steps(",
+     "r = r - n * lo;", "r = r - 0.0f * lo;", ["test_exp_steps_against_float64_exp"]),
+    ("defined exponential: reduction by truncation, not rounding", "float orc_exp_steps(",
+     "float n = rintf(a * l2e);", "float n = truncf(a * l2e);", ["test_exp_steps_against_float64_exp"]),
+    ("defined exponential: scale off by one binade", "float orc_exp_steps(",
+     "uint32_t sb = (uint32_t)((int)n + 127) << 23;", "uint32_t sb = (uint32_t)((int)n + 126) << 23;",
+     ["test_exp_steps_against_float64_exp"]),
+    ("defined exponential: no cut below -86", "float orc_exp_steps(",
+     "if (!(a >= -86.0f)) return 0.0f;", "if (!(a >= -200.0f)) return 0.0f;",
+     ["test_exp_steps_against_float64_exp"]),
     ("render: alpha linearised (tau instead of 1 - exp(-tau))", "void orc_render_fwd(",
      "double w = T * -expm1(-tau);", "double w = T * tau;",
      ["test_homogeneous_slab_closed_form", "test_weights_sum_to_one_minus_transmittance"]),

@@ -270,6 +270,36 @@ def test_ray_clip_matches_float64_slab(orc):
         np.testing.assert_allclose(tf[m], etf[m], rtol=1e-6, atol=1e-6)
 
 
+def test_exp_steps_against_float64_exp(orc):
+    """The early-stop density's exponential (Cody-Waite reduction + degree-7
+    Taylor polynomial, FP32 steps) is within 2 units in the last place of the
+    float64 exponential on [-86, 0] (every 7th float of [-1, 0] and [-86, -80],
+    a dense sweep of [-86, 0], random arguments), exactly 1 at 0, and 0 below
+    -86 (its stated cut)."""
+    g = workloads.rng(9001)
+    parts = [np.linspace(-86.0, 0.0, 400_001).astype(np.float32),
+             (-np.abs(g.standard_normal(200_000)) * 20.0).astype(np.float32)]
+    for lo, hi in ((-1.0, 0.0), (-86.0, -80.0)):
+        b_hi = np.array([hi if hi != 0.0 else -0.0], np.float32).view(np.uint32)[0]
+        b_lo = np.array([lo], np.float32).view(np.uint32)[0]
+        parts.append(np.arange(b_hi, b_lo + 1, 7, dtype=np.uint32).view(np.float32))
+    a = np.concatenate(parts)
+    a = a[a >= -86.0]
+    e = orc.exp_steps(a)
+    ref = np.exp(a.astype(np.float64))
+    ulp = np.spacing(ref.astype(np.float32)).astype(np.float64)
+    err = np.abs(e.astype(np.float64) - ref) / ulp
+    assert err.max() <= 2.0, (a[np.argmax(err)], err.max())
+    assert orc.exp_steps(np.array([0.0, -0.0], np.float32)).tolist() == [1.0, 1.0]
+    below = np.array([-86.0001, -87.0, -100.0, -1e30, -np.inf, np.nan], np.float32)
+    assert np.all(orc.exp_steps(below) == 0.0)
+    # e^(-k ln 2) lands within the bound of 2^-k at every reduction boundary
+    k = np.arange(0, 124)
+    got = orc.exp_steps((-k * math.log(2)).astype(np.float32)).astype(np.float64)
+    exact = np.exp((-k * math.log(2)).astype(np.float32).astype(np.float64))
+    assert np.all(np.abs(got - exact) <= 2.0 * np.spacing(exact.astype(np.float32)))
+
+
 def test_early_termination_cut(orc):
     """No-gradient filtering (Sec. 4.2): the field-given march emits a prefix of the
     field-less march, cut where the float64 optical depth of the emitted samples
