@@ -55,8 +55,9 @@ BYTES = {
     "render_fwd": (24, 32),
     "render_bwd": (40, 28),
 }
-# march with a field: two block summaries, run walk, early-stop pass, scan, fill
-KERNELS_PER_STEP = {"march": 6, "field": 1, "render_fwd": 1, "loss": 1, "render_bwd": 1}
+# march with a field: two block summaries, run walk, early-stop pass, exact decisions of the rays it
+# queued, scan, fill (and a 24-byte memset of the work counters)
+KERNELS_PER_STEP = {"march": 7, "field": 1, "render_fwd": 1, "loss": 1, "render_bwd": 1}
 
 
 def parse_args(argv=None):

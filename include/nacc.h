@@ -65,16 +65,24 @@ typedef struct nacc_march_params {
     float t_min;          /* near plane: t_near = max(t_min, box entry) */
     float t_max;          /* far plane: t_far = min(t_max, box exit) */
     float early_stop_eps; /* with a field: stop once T < eps (Sec. 4.2, 1e-4); <= 0: never */
+    int32_t exact_stops;  /* 0 (default): each early-stop decision is taken from bounds or from the
+                             fast density where they prove the exact answer, else exactly; 1: every
+                             decision in the exact arithmetic (slow; for validation).  Same result. */
 } nacc_march_params;
 
 /* Analytic density field used for early termination inside the march (the
  * "density_fn" of Algorithm 1, here a sum of isotropic Gaussian blobs):
  *   sigma(x) = sum_b peak_b * exp(-|x - mu_b|^2 / (2 std_b^2)).
- * The march evaluates it with fused multiply-adds and the hardware exp2
- * (relative error a few 1e-6); for fields of at most 16 blobs each ray keeps
- * only the blobs whose integral along the ray line exceeds 1e-7, so a
- * dropped blob changes the optical depth by at most 1e-7.  These only move
- * stops whose depth lies within that of the threshold.
+ * The early-stop decision is defined on it in FP32 with a fixed operation
+ * order: x = o + d*tm; per blob in order r2 = (dx*dx + dy*dy) + dz*dz,
+ * s = s + peak * e(r2 * coef), coef = -0.5 / (std*std), where e is the
+ * exponential defined by its steps (Cody-Waite reduction, degree-7 Taylor
+ * polynomial, every operation one rounded FP32 operation; 0 below -86); the
+ * depth is the lattice-order FP32 sum of s * (t1 - t0).  The march reaches
+ * that decision exactly: from a bound on the ray's depth (sum over blobs of
+ * the line integral plus twice the line maximum times dt), from a fast
+ * closed-form depth with a proven error bound, or, near the threshold, in
+ * the definition's own arithmetic.
  * rgb is only used by the harness field kernel (nacc_harness.h). */
 typedef struct nacc_blob_field {
     int32_t n_blobs;    /* 0..1024 */
@@ -105,9 +113,10 @@ int nacc_version(void);
 
 /* Scratch bytes nacc_march_grid needs for n_rays rays (the per-ray counts
  * from which the packed tensor's offsets are built, Sec. 4.2 "Packed
- * Tensor"): per-ray counts, stops and run records (~150 bytes per ray) plus
- * the grid's block summaries sized for the largest grid (8 levels of 1024^3
- * cells: 32.5 MiB).  Pure size arithmetic: no device work, no error status. */
+ * Tensor"): per-ray counts, stops and run records (~150 bytes per ray), the
+ * grid's block summaries sized for the largest grid (8 levels of 1024^3
+ * cells: 32.5 MiB) and a work counter of the early-stop pass.  Pure size
+ * arithmetic: no device work, no error status. */
 size_t nacc_march_scratch_bytes(int64_t n_rays);
 
 /*

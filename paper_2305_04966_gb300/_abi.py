@@ -30,7 +30,7 @@ class Grid(ctypes.Structure):
 
 class MarchParams(ctypes.Structure):
     _fields_ = [("step", c_f32), ("max_steps", c_i32), ("t_min", c_f32), ("t_max", c_f32),
-                ("early_stop_eps", c_f32)]
+                ("early_stop_eps", c_f32), ("exact_stops", c_i32)]
 
 
 class BlobField(ctypes.Structure):

@@ -201,13 +201,14 @@ def march_grid(grid: OccupancyGrid, rays_o: torch.Tensor, rays_d: torch.Tensor, 
                max_steps: int = 1024, t_min: float = 0.0, t_max: float = 1e10,
                early_stop_eps: float = 1e-4, field: BlobField | None = None,
                capacity: int | None = None, buffers: MarchBuffers | None = None,
-               with_ray_indices: bool = True) -> PackedSamples:
+               with_ray_indices: bool = True, exact_stops: bool = False) -> PackedSamples:
     """Occupancy-grid lattice march into packed samples (``nacc_march_grid``).
 
     With ``field`` given, samples are filtered at T < early_stop_eps while
-    marching (Sec. 4.2 "No Gradient Filtering").  Without ``buffers``, a
-    capacity is chosen (worst case when it is small, else a guess that is
-    grown on NACC_ERR_CAPACITY)."""
+    marching (Sec. 4.2 "No Gradient Filtering"); ``exact_stops`` takes every
+    such decision in the exact arithmetic (same result, slower: validation).
+    Without ``buffers``, a capacity is chosen (worst case when it is small,
+    else a guess that is grown on NACC_ERR_CAPACITY)."""
     dev = rays_o.device
     _check(rays_o, "rays_o", _F32, dev)
     n = int(rays_o.shape[0])
@@ -216,7 +217,7 @@ def march_grid(grid: OccupancyGrid, rays_o: torch.Tensor, rays_d: torch.Tensor, 
         raise ValueError("rays_o must be [n][3]")
     _check(grid.bits, "grid.bits", _I32, dev, (grid.n_cells // 32,))
     params = _abi.MarchParams(float(step), int(max_steps), float(t_min), float(t_max),
-                              float(early_stop_eps))
+                              float(early_stop_eps), int(bool(exact_stops)))
     fs = field.c_struct() if field is not None else None
     worst = n * int(max_steps)
     while True:
@@ -247,16 +248,19 @@ def march_grid(grid: OccupancyGrid, rays_o: torch.Tensor, rays_d: torch.Tensor, 
 def march_unbounded(grid: OccupancyGrid, rays_o: torch.Tensor, rays_d: torch.Tensor, max_steps: int = 1024,
                     t_near: float = 0.2, t_far: float = 1000.0, early_stop_eps: float = 1e-4,
                     field: BlobField | None = None, capacity: int | None = None,
-                    buffers: MarchBuffers | None = None, with_ray_indices: bool = True) -> PackedSamples:
+                    buffers: MarchBuffers | None = None, with_ray_indices: bool = True,
+                    exact_stops: bool = False) -> PackedSamples:
     """Unbounded-scene march (``nacc_march_unbounded``): max_steps uniform
     steps in s mapped to [t_near, t_far] by the disparity-linear bijection,
-    occupancy of the contracted midpoint."""
+    occupancy of the contracted midpoint; ``exact_stops`` as in
+    ``march_grid``."""
     dev = rays_o.device
     n = int(rays_o.shape[0])
     _check(rays_o, "rays_o", _F32, dev, (n, 3))
     _check(rays_d, "rays_d", _F32, dev, (n, 3))
     _check(grid.bits, "grid.bits", _I32, dev, (grid.n_cells // 32,))
-    params = _abi.MarchParams(0.0, int(max_steps), float(t_near), float(t_far), float(early_stop_eps))
+    params = _abi.MarchParams(0.0, int(max_steps), float(t_near), float(t_far), float(early_stop_eps),
+                              int(bool(exact_stops)))
     fs = field.c_struct() if field is not None else None
     worst = n * int(max_steps)
     scratch = _scratch(_abi.load().nacc_march_unbounded_scratch_bytes(n, int(max_steps)), dev)

@@ -39,6 +39,9 @@
 // never evaluates the field.  The fill pass expands the recorded runs
 // warp-cooperatively as coalesced stores (rays whose runs overflowed the
 // slots are re-marched per lane and flushed by the warp).
+#include <algorithm>
+
+#include "early_stop.cuh"
 #include "nacc_internal.cuh"
 
 namespace nacc {
@@ -65,6 +68,7 @@ struct MarchArgs {
     int max_steps;
     float t_min, t_max;
     float thr;  // optical-depth threshold (+inf: no early stop)
+    int exact_all;  // every early-stop decision on the exact path (validation)
     float inv_step;  // 1/step, only for the conservative skip (never for lattice values)
     int idx32;       // every flat cell index fits 32 bits
     float skip_lim[NACC_MAX_LEVELS];  // skip allowed at level l iff max|o| <= skip_lim[l]
@@ -193,13 +197,36 @@ __device__ __forceinline__ float ex2_approx(float a) {
     return y;
 }
 
+// Blob parameters of the early-stop pass, staged in shared memory: centre,
+// c2 = coef * log2 e (the base-2 exponent's coefficient), peak, the
+// definition's coef = fl(-0.5 / fl(std * std)), std, 1/std.
+struct StopBlob {
+    float mx, my, mz, c2;
+    float peak, coef, sd, isd;
+};
+
+__device__ inline void stage_stop_blobs(StopBlob* s, const nacc_blob_field& f) {
+    for (int b = threadIdx.x; b < f.n_blobs; b += blockDim.x) {
+        StopBlob v;
+        v.mx = f.mu[3 * b + 0];
+        v.my = f.mu[3 * b + 1];
+        v.mz = f.mu[3 * b + 2];
+        v.sd = f.std[b];
+        v.coef = __fdiv_rn(-0.5f, __fmul_rn(v.sd, v.sd));
+        v.c2 = v.coef * 1.4426950408889634f;  // log2 e
+        v.peak = f.peak[b];
+        v.isd = 1.0f / v.sd;
+        s[b] = v;
+    }
+}
+
 // Early-stop density: the blob field of the harness evaluated with fused
-// multiply-adds and the hardware base-2 exponent (exp(a) = 2^(a log2 e), the
-// coefficient pre-scaled by log2 e at staging), at two points per blob load
-// (two buffered samples of a lane share every shared-memory read of the blob
-// parameters).  Its relative error, a few 1e-6, moves only stopping
-// decisions whose optical depth is within that of the threshold.
-__device__ __forceinline__ void sigma_early_stop2(const BlobS* s, int n, const float xa[3], const float xb[3],
+// multiply-adds and the hardware base-2 exponent (exp(a) = 2^(a log2 e)),
+// at two points per blob load (two buffered samples of a lane share every
+// shared-memory read of the blob parameters).  Used for rays whose table
+// would exceed kTab entries; its error is inside the per-ray bound of
+// early_stop.cuh.
+__device__ __forceinline__ void sigma_early_stop2(const StopBlob* s, int n, const float xa[3], const float xb[3],
                                                   float& sa, float& sb) {
     float acc_a = 0.0f, acc_b = 0.0f;
 #pragma unroll 2
@@ -232,22 +259,33 @@ constexpr int kTab = 64;  // table entries per ray; a ray with more kept blobs u
 // ray's table: each changes the optical depth by at most kCullEps.
 constexpr float kCullEps = 1e-7f;
 
-// Builds the table of one ray (o, d) from the n staged blobs, lane b0 + lane
-// handling blob b0 + lane, kept blobs compacted in blob order.  Returns the
-// number of kept blobs, or -1 if more than kTab are kept (no table).
-__device__ int build_ray_table(const BlobS* sb, int n, const float o[3], const float d[3], float4* tab, int lane) {
+// The ray's early-stop table and depth bound (early_stop.cuh), built by the
+// warp, lane b0 + lane handling blob b0 + lane: the per-ray closed form in
+// FP32; blobs whose line integral exceeds kCullEps are compacted in blob
+// order into the table (entry {c2 |d|^2, t*, C, peak}, blob index in tidx).
+// U bounds the definition's depth at every sample (every blob's weight, the
+// closed form's own FP32 rounding included); e_out is the error bound's
+// share of the blobs left out (their whole weight).  Returns the number of
+// kept blobs (the table holds the first kTab).  onorm = |o|, dnorm = |d|, tmax bounds |t| of every midpoint, cnt =
+// the ray's samples.  Every lattice interval is within 8u tmax of dt long,
+// and consecutive intervals, rounded apart, overlap by at most that much.
+__device__ int build_ray_table(const StopBlob* sb, int n, const float o[3], const float d[3], float onorm,
+                               float dnorm, float tmax, float dt, int cnt, float4* tab, uint16_t* tidx, float& U,
+                               float& e_out, int lane) {
     const float dd = fmaf(d[2], d[2], fmaf(d[1], d[1], d[0] * d[0]));
     const float idd = dd > 0.0f ? 1.0f / dd : 0.0f;
     const float ilen = dd > 0.0f ? rsqrtf(dd) : 0.0f;
+    const float dt_b = dt + 8.0f * kU * tmax, ov = (float)cnt * 8.0f * kU * tmax;
     int nt = 0;
+    float u = 0.0f, e = 0.0f;
     for (int b0 = 0; b0 < n; b0 += 32) {
         const int b = b0 + lane;
         bool keep = false;
         float4 ent = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         if (b < n) {
-            const BlobS v = sb[b];
+            const StopBlob v = sb[b];
             const float m0 = v.mx - o[0], m1 = v.my - o[1], m2 = v.mz - o[2];
-            float ts, pp;
+            float ts, pp, I;
             if (dd > 0.0f) {
                 const float md = fmaf(m2, d[2], fmaf(m1, d[1], m0 * d[0]));
                 const float cx = fmaf(m1, d[2], -m2 * d[1]);
@@ -259,20 +297,111 @@ __device__ int build_ray_table(const BlobS* sb, int n, const float o[3], const f
                 ts = 0.0f;
                 pp = fmaf(m2, m2, fmaf(m1, m1, m0 * m0));
             }
-            const float C = v.coef * pp;
-            keep = true;
+            const float C = v.c2 * pp;
+            const float S = v.peak * ex2_approx(C);  // largest density on the line
             if (dd > 0.0f) {
-                const float sd = sqrtf(-0.72134752f / v.coef);  // coef = -log2(e) / (2 std^2)
-                keep = v.peak * ex2_approx(C) * 2.5066283f * sd * ilen > kCullEps;
+                I = S * 2.5066283f * v.sd * ilen;  // integral along the line
+                keep = I > kCullEps;
+            } else {
+                I = S * dt_b * (float)cnt;  // every sample at the same point
+                keep = true;
             }
-            ent = make_float4(v.coef * dd, ts, C, v.peak);
+            if (S > 0.0f) {
+                // growth with the FP32 closed form's own error (within 11u |mu - o|) included
+                const float p = sqrtf(pp);
+                const float mn = sqrtf(fmaf(m2, m2, fmaf(m1, m1, m0 * m0)));
+                const float W = blob_weight(
+                    S, I, dt_b, dt_b, ov, blob_growth(p, v.isd, onorm + 2.5f * fabsf(ts) * dnorm + 16.0f * p + 12.0f * mn));
+                u += W;
+                if (!keep) e += W;
+            }
+            ent = make_float4(v.c2 * dd, ts, C, v.peak);
         }
         const unsigned bal = __ballot_sync(0xffffffffu, keep);
         const int pos = nt + __popc(bal & ((1u << lane) - 1u));
-        if (keep && pos < kTab) tab[pos] = ent;
+        if (keep && pos < kTab) {
+            tab[pos] = ent;
+            tidx[pos] = (uint16_t)b;
+        }
         nt += __popc(bal);
     }
-    return nt <= kTab ? nt : -1;
+    U = warp_sum(u);
+    e_out = warp_sum(e);
+    return nt;
+}
+
+// Error bound of the kept blobs (early_stop.cuh), one lane per kept blob:
+// t* and p^2 again by closest_approach, the table entry rewritten (when the
+// table holds the nt kept blobs; otherwise every kept blob is bounded from its
+// FP32 values, for the direct form).  Returns the whole-ray bound, and the
+// relative one in eps.  Arguments as build_ray_table.
+__device__ float refine_ray_table(const StopBlob* sb, int n, int nt, const float o[3], const float d[3], float onorm,
+                                  float dnorm, float tmax, float dt, int cnt, float4* tab, const uint16_t* tidx,
+                                  float& eps, int lane) {
+    const float dd = fmaf(d[2], d[2], fmaf(d[1], d[1], d[0] * d[0]));
+    const float idd = dd > 0.0f ? 1.0f / dd : 0.0f;
+    const float ilen = dd > 0.0f ? rsqrtf(dd) : 0.0f;
+    const float dt_b = dt + 8.0f * kU * tmax, ov = (float)cnt * 8.0f * kU * tmax;
+    const bool have_tab = nt <= kTab;
+    float e = 0.0f, em = 0.0f;
+    for (int i = lane; i < (have_tab ? nt : n); i += 32) {
+        const StopBlob v = sb[have_tab ? tidx[i] : i];
+        float ts, pp;
+        if (dd > 0.0f) {
+            const float mu[3] = {v.mx, v.my, v.mz};
+            closest_approach(mu, o, d, idd, ts, pp);
+        } else {
+            const float m0 = v.mx - o[0], m1 = v.my - o[1], m2 = v.mz - o[2];
+            ts = 0.0f;
+            pp = fmaf(m2, m2, fmaf(m1, m1, m0 * m0));
+        }
+        const float C = v.c2 * pp;
+        const float S = v.peak * ex2_approx(C);
+        const float I = dd > 0.0f ? S * 2.5066283f * v.sd * ilen : S * dt_b * (float)cnt;
+        if (!have_tab && !(I > kCullEps) && dd > 0.0f) continue;  // left out: counted whole in build_ray_table
+        const float p = sqrtf(pp);
+        const float pos0 = onorm + 2.5f * fabsf(ts) * dnorm + 16.0f * p;
+        const float gm1 = blob_growth(p, v.isd, pos0);
+        e += blob_error(blob_weight(S, I, dt_b, dt_b, ov, gm1), gm1, p * v.isd, n, true);
+        em = fmaxf(em, blob_rel_error(v.isd, pos0, n));
+        if (have_tab) tab[i] = make_float4(v.c2 * dd, ts, C, v.peak);
+    }
+    eps = warp_max(em);
+    return warp_sum(e);
+}
+
+// The ascending list of the blobs that may be non-zero somewhere on the ray
+// in the definition's arithmetic (early_stop.cuh, blob_may_count), built by
+// the warp; returns its length.  pos_far = |o| + t_max |d|.
+__device__ int build_exact_list(const StopBlob* sb, int n, const float o[3], const float d[3], float pos_far,
+                                uint16_t* ex_list, int lane) {
+    const float dd = fmaf(d[2], d[2], fmaf(d[1], d[1], d[0] * d[0]));
+    const float idd = dd > 0.0f ? 1.0f / dd : 0.0f;
+    int ne = 0;
+    for (int b0 = 0; b0 < n; b0 += 32) {
+        const int b = b0 + lane;
+        bool in_ex = false;
+        if (b < n) {
+            const StopBlob v = sb[b];
+            const float m0 = v.mx - o[0], m1 = v.my - o[1], m2 = v.mz - o[2];
+            float pp;
+            if (dd > 0.0f) {
+                const float cx = fmaf(m1, d[2], -m2 * d[1]), cy = fmaf(m2, d[0], -m0 * d[2]),
+                            cz = fmaf(m0, d[1], -m1 * d[0]);
+                pp = fmaf(cz, cz, fmaf(cy, cy, cx * cx)) * idd;
+            } else {
+                pp = fmaf(m2, m2, fmaf(m1, m1, m0 * m0));
+            }
+            // the FP32 distance is within 8u |mu - o| of exact; blob_may_count's
+            // margin is 8u pos_far, so widen it by |mu - o|
+            const float mn = sqrtf(fmaf(m2, m2, fmaf(m1, m1, m0 * m0)));
+            in_ex = blob_may_count(sqrtf(pp), v.sd, pos_far + mn);
+        }
+        const unsigned bex = __ballot_sync(0xffffffffu, in_ex);
+        if (in_ex) ex_list[ne + __popc(bex & ((1u << lane) - 1u))] = (uint16_t)b;
+        ne += __popc(bex);
+    }
+    return ne;
 }
 
 // Density at ray parameters ta, tb from the ray's table (every lane reads
@@ -626,209 +755,444 @@ __global__ void __launch_bounds__(kRunsThreads)
     if (lane == 0 && r0 < A.n) block_sums[r0 / kRaysPerBlock] = v;
 }
 
+// sigma*dt at lattice point k of the ray in the definition's arithmetic
+// (early_stop.cuh): the lattice interval, its rounded midpoint and point, the
+// density over the ray's exact blob list (entries that are 0 over the whole
+// chunk left out), the rounded interval length; 0 for lanes without a point
+// (`valid` false).  Every lane of the warp calls it.
+__device__ __forceinline__ float exact_tau(const MarchArgs& A, const StopBlob* sb, const uint16_t* ex_list,
+                                           int n_ex, const float o[3], const float d[3], float tn, int k, bool valid,
+                                           float pos_far, int lane) {
+    const float t0 = __fadd_rn(tn, __fmul_rn((float)k, A.step));
+    const float t1 = __fadd_rn(t0, A.step);
+    const float tm = __fmul_rn(__fadd_rn(t0, t1), 0.5f);
+    float x[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) x[a] = __fadd_rn(o[a], __fmul_rn(d[a], tm));
+    const unsigned vm = __ballot_sync(0xffffffffu, valid);
+    if (!vm) return 0.0f;
+    const float t_lo = __shfl_sync(0xffffffffu, tm, __ffs(vm) - 1);
+    const float t_hi = __shfl_sync(0xffffffffu, tm, 31 - __clz(vm));
+    const float dd = fmaf(d[2], d[2], fmaf(d[1], d[1], d[0] * d[0]));
+    const float s = exact_sigma_chunk(
+        x, ex_list, n_ex,
+        [sb](int b) {
+            const StopBlob& v = sb[b];
+            return ExactBlob{v.mx, v.my, v.mz, v.coef, v.peak};
+        },
+        o, d, dd, dd > 0.0f ? 1.0f / dd : 0.0f, t_lo, t_hi, pos_far, lane);
+    return valid ? __fmul_rn(s, __fsub_rn(t1, t0)) : 0.0f;
+}
+
+// The exact path of the early stop (early_stop.cuh): the ray's emitted
+// points in lattice order, 32 at a time (from its recorded runs, or by
+// walking the lattice up to K_end when the runs overflowed); each lane
+// evaluates one point's sigma*dt in the definition's arithmetic into the
+// warp's buffer `buf` (32 floats of shared memory), then lane 0 adds the
+// terms in order one at a time -- the definition's own sum -- and finds the
+// first point whose depth before it exceeds the threshold, which cuts the
+// ray.  cut / kstop are left as given if the ray never stops.
+__device__ __noinline__ void stop_exact(const MarchArgs& A, const StopBlob* sb, const uint16_t* ex_list, int n_ex,
+                                        int64_t r, const float o[3], const float d[3], float tn, int cnt, int nr,
+                                        int2 run, int ke, float pos_far, int lane, float* buf, int& cut, int& kstop) {
+    int ex = run.y;  // -> exclusive prefix of the run lengths
+#pragma unroll
+    for (int o2 = 1; o2 < 32; o2 <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, ex, o2);
+        if (lane >= o2) ex += y;
+    }
+    ex -= run.y;
+    float P = 0.0f;  // the sequential sum (lane 0's)
+    if (nr >= 0) {
+        for (int p0 = 0; p0 < cnt; p0 += 32) {
+            const int p = p0 + lane;
+            int k = 0;
+            for (int j = 0; j < nr; ++j) {
+                const int ej = __shfl_sync(0xffffffffu, ex, j);
+                const int kj = __shfl_sync(0xffffffffu, run.x, j);
+                if (p >= ej) k = kj + (p - ej);
+            }
+            buf[lane] = exact_tau(A, sb, ex_list, n_ex, o, d, tn, k, p < cnt, pos_far, lane);
+            __syncwarp();
+            int jc = -1;
+            if (lane == 0) {
+                const int nv = min(32, cnt - p0);
+                for (int j = 0; j < nv; ++j) {
+                    if (P > A.thr) {
+                        jc = j;
+                        break;
+                    }
+                    P = __fadd_rn(P, buf[j]);
+                }
+            }
+            jc = __shfl_sync(0xffffffffu, jc, 0);
+            const int kc = __shfl_sync(0xffffffffu, k, jc < 0 ? 0 : jc);
+            __syncwarp();
+            if (jc >= 0) {
+                cut = p0 + jc;
+                kstop = kc;
+                return;
+            }
+        }
+        return;
+    }
+    Lane s;
+    s.R.tn = 0.0f;
+    lane_init(A, r, s);  // the count pass found this ray inside the grid
+    int seen = 0;
+    for (int kb = 0; kb < ke && seen < cnt; kb += 32) {
+        const int k = kb + lane;
+        bool occ = false;
+        float t0 = 0.0f, t1 = 0.0f, xp[3];
+        if (k < ke) {
+            int l, ic[3];
+            occ = lattice_point(A, s.R, k, t0, t1, xp, l, ic);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, occ);
+        buf[lane] = exact_tau(A, sb, ex_list, n_ex, o, d, tn, k, occ, pos_far, lane);
+        __syncwarp();
+        int jc = -1, sc = seen;
+        if (lane == 0) {
+            unsigned mm = m;
+            while (mm && sc < cnt) {
+                const int j = __ffs(mm) - 1;
+                mm &= mm - 1;
+                if (P > A.thr) {
+                    jc = j;
+                    break;
+                }
+                P = __fadd_rn(P, buf[j]);
+                ++sc;
+            }
+        }
+        jc = __shfl_sync(0xffffffffu, jc, 0);
+        const int sc0 = __shfl_sync(0xffffffffu, sc, 0);
+        __syncwarp();
+        if (jc >= 0) {
+            cut = sc0;
+            kstop = kb + jc;
+            return;
+        }
+        seen = sc0;
+    }
+}
+
+// The fast depth of one ray (early_stop.cuh): the ray's table (nt entries; -1:
+// none, the direct form over every blob), its points in lattice order 64 at a
+// time (two consecutive points per lane, from the recorded runs; a ray whose
+// runs overflowed the slots walks the lattice 32 points at a time up to
+// K_end), each lane adding its points' sigma dt, a warp scan giving the
+// optical depth before each point.  Returns 0 if no point's fast depth comes
+// within the error bound rb of the threshold (no cut), 1 if the first one
+// that does passes it by more than the bound (cut / kstop set there), 2
+// otherwise (undecided).
+__device__ __forceinline__ int fast_cut(const MarchArgs& A, const StopBlob* s_blobs, int nblobs, const float4* tab,
+                                        int nt, const RayBound& rb, int64_t r, const float o[3], const float d[3],
+                                        float tn, int cnt, int nr, int2 run, int ke, int lane, int& cut, int& kstop) {
+    float Q = 0.0f;  // sum of the depths before the points visited
+    float carry = 0.0f;
+    if (nr >= 0) {
+        int ex = run.y;  // -> exclusive prefix of the run lengths
+#pragma unroll
+        for (int o2 = 1; o2 < 32; o2 <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, ex, o2);
+            if (lane >= o2) ex += y;
+        }
+        ex -= run.y;
+        for (int p0 = 0; p0 < cnt; p0 += 64) {
+            const int pa = p0 + 2 * lane, pb = pa + 1;
+            int ka = 0, kb = 0;
+            for (int j = 0; j < nr; ++j) {
+                const int ej = __shfl_sync(0xffffffffu, ex, j);
+                const int kj = __shfl_sync(0xffffffffu, run.x, j);
+                if (pa >= ej) ka = kj + (pa - ej);
+                if (pb >= ej) kb = kj + (pb - ej);
+            }
+            float taua = 0.0f, taub = 0.0f;
+            const bool two = pb < cnt;
+            const float a0 = __fadd_rn(tn, __fmul_rn((float)ka, A.step)), a1 = __fadd_rn(a0, A.step);
+            const float b0 = __fadd_rn(tn, __fmul_rn((float)(two ? kb : ka), A.step)),
+                        b1 = __fadd_rn(b0, A.step);
+            const float tma = __fmul_rn(__fadd_rn(a0, a1), 0.5f), tmb = __fmul_rn(__fadd_rn(b0, b1), 0.5f);
+            float sa = 0.0f, sb = 0.0f;
+            if (nt > 0 && nt <= kGroupMin) {
+                if (pa < cnt) sigma_tab2(tab, nt, tma, tmb, sa, sb);
+            } else if (nt > 0) {  // the group's midpoints span [first, last] (lattice order)
+                const int last = min(cnt - p0, 64) - 1;
+                const float t_lo = __shfl_sync(0xffffffffu, tma, 0);
+                const float t_hi = __shfl_sync(0xffffffffu, (last & 1) ? tmb : tma, last >> 1);
+                const float t_end = __shfl_sync(0xffffffffu, (last & 1) ? b1 : a1, last >> 1);
+                const float span = t_end - __shfl_sync(0xffffffffu, a0, 0);
+                sigma_tab2_group(tab, nt, t_lo, t_hi, span, tma, tmb, sa, sb, pa < cnt);
+            }
+            if (pa < cnt) {
+                if (nt < 0) {
+                    float xa[3], xb[3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        xa[a] = fmaf(d[a], tma, o[a]);
+                        xb[a] = fmaf(d[a], tmb, o[a]);
+                    }
+                    sigma_early_stop2(s_blobs, nblobs, xa, xb, sa, sb);
+                }
+                taua = __fmul_rn(sa, __fsub_rn(a1, a0));
+                if (two) taub = __fmul_rn(sb, __fsub_rn(b1, b0));
+            }
+            const float pair = taua + taub;
+            float x = pair;  // -> inclusive prefix over the lanes' pairs
+#pragma unroll
+            for (int o2 = 1; o2 < 32; o2 <<= 1) {
+                const float y = __shfl_up_sync(0xffffffffu, x, o2);
+                if (lane >= o2) x += y;
+            }
+            const float before_a = carry + (x - pair), before_b = before_a + taua;
+            const float Qc = Q + warp_sum((pa < cnt ? before_a : 0.0f) + (pb < cnt ? before_b : 0.0f));
+            const float lo_thr = A.thr - depth_error(rb, cnt, Qc, A.thr);
+            const unsigned over_a = __ballot_sync(0xffffffffu, pa < cnt && before_a > lo_thr);
+            const unsigned over_b = __ballot_sync(0xffffffffu, pb < cnt && before_b > lo_thr);
+            if (over_a | over_b) {  // the first point near or past the threshold, in lattice order
+                const int ja = over_a ? __ffs(over_a) - 1 : 32, jb = over_b ? __ffs(over_b) - 1 : 32;
+                const bool at_a = ja <= jb;
+                const int j = at_a ? ja : jb;
+                const float bc = __shfl_sync(0xffffffffu, at_a ? before_a : before_b, j);
+                const int kc = __shfl_sync(0xffffffffu, at_a ? ka : kb, j);
+                if (bc - depth_error(rb, cnt, Qc, bc) > A.thr) {
+                    cut = p0 + 2 * j + (at_a ? 0 : 1);
+                    kstop = kc;
+                    return 1;
+                }
+                return 2;
+            }
+            Q = Qc;
+            carry += __shfl_sync(0xffffffffu, x, 31);
+        }
+    } else {
+        Lane s;
+        s.R.tn = 0.0f;
+        lane_init(A, r, s);  // the count pass found this ray inside the grid
+        int seen = 0;
+        for (int kb = 0; kb < ke && seen < cnt; kb += 32) {
+            const int k = kb + lane;
+            bool occ = false;
+            float t0 = 0.0f, t1 = 0.0f, xp[3];
+            if (k < ke) {
+                int l, ic[3];
+                occ = lattice_point(A, s.R, k, t0, t1, xp, l, ic);
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, occ);
+            if (!m) continue;
+            float tau = 0.0f;
+            if (occ) {
+                const float tm = __fmul_rn(__fadd_rn(t0, t1), 0.5f);
+                float sg, unused;
+                if (nt >= 0) {
+                    sigma_tab2(tab, nt, tm, tm, sg, unused);
+                } else {
+                    float xa[3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) xa[a] = fmaf(d[a], tm, o[a]);
+                    sigma_early_stop2(s_blobs, nblobs, xa, xa, sg, unused);
+                }
+                tau = __fmul_rn(sg, __fsub_rn(t1, t0));
+            }
+            float x = tau;
+#pragma unroll
+            for (int o2 = 1; o2 < 32; o2 <<= 1) {
+                const float y = __shfl_up_sync(0xffffffffu, x, o2);
+                if (lane >= o2) x += y;
+            }
+            const float before = carry + (x - tau);
+            const float Qc = Q + warp_sum(occ ? before : 0.0f);
+            const float lo_thr = A.thr - depth_error(rb, cnt, Qc, A.thr);
+            const unsigned over = __ballot_sync(0xffffffffu, occ && before > lo_thr);
+            if (over) {
+                const int j = __ffs(over) - 1;
+                const float bc = __shfl_sync(0xffffffffu, before, j);
+                if (bc - depth_error(rb, cnt, Qc, bc) > A.thr) {
+                    cut = seen + __popc(m & ((1u << j) - 1u));
+                    kstop = kb + j;
+                    return 1;
+                }
+                return 2;
+            }
+            seen += __popc(m);
+            Q = Qc;
+            carry += __shfl_sync(0xffffffffu, x, 31);
+        }
+    }
+    return 0;
+}
+
 // Early termination (with a field, after the count pass): each warp takes
-// the 32 rays of one block-sum entry in turn.  The lanes build the ray's
-// table, then visit its points in lattice order 64 at a time (two
-// consecutive points per lane, from the recorded runs; a ray whose runs
-// overflowed the slots walks the lattice 32 points at a time up to K_end);
-// each lane adds its points' sigma dt, a warp scan gives the optical depth
-// before each point, and the first point whose depth before it exceeds the
-// threshold cuts the ray: counts[r] and kstops[r] (its lattice index) are
+// the 32 rays of one block-sum entry in turn and decides each ray's cut as
+// early_stop.cuh describes: no density at all when the ray's depth bound
+// stays below the threshold; else the fast depth -- the ray's table, its
+// points in lattice order 64 at a time (two consecutive points per lane, from
+// the recorded runs; a ray whose runs overflowed the slots walks the lattice
+// 32 points at a time up to K_end), each lane adding its points' sigma dt, a
+// warp scan giving the optical depth before each point -- and the cut at the
+// first point whose fast depth passes the threshold by more than the bound;
+// else (a fast depth within the bound of the threshold, or A.exact_all) the
+// exact path.  counts[r] and kstops[r] (the cut's lattice index) are
 // rewritten, and so is the entry's total.
 constexpr int kStopThreads = 128;
 constexpr int kStopWarps = kStopThreads / 32;
-__global__ void __launch_bounds__(kStopThreads)
+__global__ void __launch_bounds__(kStopThreads, 7)
     k_march_stop(MarchArgs A, int32_t* __restrict__ counts, int32_t* __restrict__ kstops,
                  const int32_t* __restrict__ nruns, const float* __restrict__ tnear,
-                 const int2* __restrict__ runs, long long* __restrict__ block_sums) {
-    extern __shared__ BlobS s_blobs[];
+                 const int2* __restrict__ runs, long long* __restrict__ block_sums,
+                 unsigned long long* __restrict__ ticket, long long* __restrict__ queue,
+                 unsigned long long* __restrict__ qlen) {
+    extern __shared__ StopBlob s_blobs[];
     __shared__ float4 s_tab[kStopWarps][kTab];
-    stage_blobs(s_blobs, A.field, false);
-    for (int b = threadIdx.x; b < A.field.n_blobs; b += blockDim.x)
-        s_blobs[b].coef *= 1.4426950408889634f;  // log2 e
+    __shared__ uint16_t s_tidx[kStopWarps][kTab];
+    stage_stop_blobs(s_blobs, A.field);
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t cb = (int64_t)blockIdx.x * kStopWarps + wid;  // this warp's block-sum entry
-    const int64_t rbase = cb * kRaysPerBlock;
-    if (rbase >= A.n) return;
     float4* tab = s_tab[wid];
+    uint16_t* tidx = s_tidx[wid];
     const int nblobs = A.field.n_blobs;
-    // lane i loads the header of ray rbase + i (coalesced); the rays are then
-    // taken in turn, their values broadcast by shuffles, and lane i keeps the
-    // results of ray i
-    const int64_t rl = rbase + lane;
-    const bool lv = rl < A.n;
-    const int l_cnt = lv ? counts[rl] : 0;
-    const int l_nr = lv ? nruns[rl] : 0;
-    const float l_tn = lv ? tnear[rl] : 0.0f;
-    const int l_ke = lv ? kstops[rl] : 0;
-    float l_o[3], l_d[3];
+    const int64_t n_entries = (A.n + kRaysPerBlock - 1) / kRaysPerBlock;
+    for (;;) {  // entries of 32 rays by ticket: rays that stop cost far more than rays that cannot
+        unsigned long long tk = 0;
+        if (lane == 0) tk = atomicAdd(ticket, 1ull);
+        const int64_t cb = (int64_t)__shfl_sync(0xffffffffu, tk, 0);  // this warp's block-sum entry
+        if (cb >= n_entries) break;
+        const int64_t rbase = cb * kRaysPerBlock;
+        // lane i loads the header of ray rbase + i (coalesced); the rays are then
+        // taken in turn, their values broadcast by shuffles, and lane i keeps the
+        // results of ray i
+        const int64_t rl = rbase + lane;
+        const bool lv = rl < A.n;
+        const int l_cnt = lv ? counts[rl] : 0;
+        const int l_nr = lv ? nruns[rl] : 0;
+        const float l_tn = lv ? tnear[rl] : 0.0f;
+        const int l_ke = lv ? kstops[rl] : 0;
+        float l_o[3], l_d[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        l_o[a] = lv ? __ldg(A.o + 3 * rl + a) : 0.0f;
-        l_d[a] = lv ? __ldg(A.d + 3 * rl + a) : 0.0f;
+        for (int a = 0; a < 3; ++a) {
+            l_o[a] = lv ? __ldg(A.o + 3 * rl + a) : 0.0f;
+            l_d[a] = lv ? __ldg(A.d + 3 * rl + a) : 0.0f;
+        }
+        int l_cut = l_cnt, l_kstop = l_ke;
+        unsigned todo = __ballot_sync(0xffffffffu, l_cnt > 0);
+        // the next ray's runs are loaded while the current one is evaluated
+        int2 run_next = make_int2(0, 0);
+        if (todo) {
+            const int i0 = __ffs(todo) - 1;
+            if (lane < __shfl_sync(0xffffffffu, l_nr, i0)) run_next = runs[(rbase + i0) * kRunSlots + lane];
+        }
+        while (todo) {
+            const int i = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int64_t r = rbase + i;
+            const int cnt = __shfl_sync(0xffffffffu, l_cnt, i);
+            const int nr = __shfl_sync(0xffffffffu, l_nr, i);
+            const float tn = __shfl_sync(0xffffffffu, l_tn, i);
+            const int ke = __shfl_sync(0xffffffffu, l_ke, i);
+            float o[3], d[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                o[a] = __shfl_sync(0xffffffffu, l_o[a], i);
+                d[a] = __shfl_sync(0xffffffffu, l_d[a], i);
+            }
+            const int2 run = run_next;
+            if (todo) {
+                const int in = __ffs(todo) - 1;
+                run_next = lane < __shfl_sync(0xffffffffu, l_nr, in) ? runs[(rbase + in) * kRunSlots + lane]
+                                                                    : make_int2(0, 0);
+            }
+            // bounds of the ray (every sample's midpoint lies before t_near + (K_end + 1) dt)
+            const float tmax = fabsf(tn) + (float)(ke + 1) * A.step * 1.0001f;
+            const float onorm = sqrtf(o[0] * o[0] + o[1] * o[1] + o[2] * o[2]) * 1.0001f;
+            const float dnorm = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) * 1.0001f;
+            int cut = cnt, kstop = ke;
+            float U, e_out;
+            const int nk = build_ray_table(s_blobs, nblobs, o, d, onorm, dnorm, tmax, A.step, cnt, tab, tidx, U, e_out,
+                                           lane);
+            if (A.exact_all != 0 || !(depth_upper(U, cnt, nblobs) <= A.thr)) {  // the ray may stop
+                __syncwarp();
+                const int nt = nk <= kTab ? nk : -1;
+                const float e_grp = nt > kGroupMin ? 2.0f * kGroupEps * (float)nt * (float)((cnt + 63) / 64) : 0.0f;
+                // the refined table and its (tight) error bound
+                float eps;
+                const float ek = refine_ray_table(s_blobs, nblobs, nk, o, d, onorm, dnorm, tmax, A.step, cnt, tab, tidx,
+                                                  eps, lane);
+                const RayBound rb{U, ek, eps, e_out + e_grp};
+                __syncwarp();
+                const int st = A.exact_all != 0 || !bounds_usable(rb, cnt, A.thr)
+                                   ? 2
+                                   : fast_cut(A, s_blobs, nblobs, tab, nt, rb, r, o, d, tn, cnt, nr, run, ke, lane,
+                                              cut, kstop);
+                const bool exact = st == 2;
+                if (exact && lane == 0) queue[atomicAdd(qlen, 1ull)] = r;  // decided exactly by k_march_stop_exact
+            }
+            if (lane == i) {
+                l_cut = cut;
+                l_kstop = kstop;
+            }
+            __syncwarp();  // the next ray rewrites the table
+        }
+        if (lv) {
+            counts[rl] = l_cut;
+            kstops[rl] = l_kstop;
+        }
+        int wsum = l_cut;
+#pragma unroll
+        for (int o2 = 16; o2 > 0; o2 >>= 1) wsum += __shfl_down_sync(0xffffffffu, wsum, o2);
+        if (lane == 0) block_sums[cb] = wsum;
     }
-    int l_cut = l_cnt, l_kstop = l_ke;
-    unsigned todo = __ballot_sync(0xffffffffu, l_cnt > 0);
-    // the next ray's runs are loaded while the current one is evaluated
-    int2 run_next = make_int2(0, 0);
-    if (todo) {
-        const int i0 = __ffs(todo) - 1;
-        if (lane < __shfl_sync(0xffffffffu, l_nr, i0)) run_next = runs[(rbase + i0) * kRunSlots + lane];
-    }
-    while (todo) {
-        const int i = __ffs(todo) - 1;
-        todo &= todo - 1;
-        const int64_t r = rbase + i;
-        const int cnt = __shfl_sync(0xffffffffu, l_cnt, i);
-        const int nr = __shfl_sync(0xffffffffu, l_nr, i);
-        const float tn = __shfl_sync(0xffffffffu, l_tn, i);
+}
+
+// Exact decisions of the rays the early-stop pass queued (early_stop.cuh):
+// persistent warps take queued rays one at a time (ticket `qhead` over the
+// `*qlen` entries), build the ray's exact blob list and run the exact path;
+// the cut and its lattice index replace the ray's count and K_end, and the
+// change of the count is added to its 32-ray entry's total.
+__global__ void __launch_bounds__(kStopThreads)
+    k_march_stop_exact(MarchArgs A, int32_t* __restrict__ counts, int32_t* __restrict__ kstops,
+                       const int32_t* __restrict__ nruns, const float* __restrict__ tnear,
+                       const int2* __restrict__ runs, long long* __restrict__ block_sums,
+                       const long long* __restrict__ queue, const unsigned long long* __restrict__ qlen,
+                       unsigned long long* __restrict__ qhead) {
+    extern __shared__ StopBlob s_blobs[];
+    __shared__ uint16_t s_ex[kStopWarps][kMaxBlobs];
+    __shared__ float s_seq[kStopWarps][32];
+    stage_stop_blobs(s_blobs, A.field);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned long long nq = *qlen;
+    for (;;) {
+        unsigned long long tk = 0;
+        if (lane == 0) tk = atomicAdd(qhead, 1ull);
+        tk = __shfl_sync(0xffffffffu, tk, 0);
+        if (tk >= nq) break;
+        const int64_t r = queue[tk];
+        const int cnt = counts[r], nr = nruns[r], ke = kstops[r];
+        const float tn = tnear[r];
         float o[3], d[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            o[a] = __shfl_sync(0xffffffffu, l_o[a], i);
-            d[a] = __shfl_sync(0xffffffffu, l_d[a], i);
+            o[a] = __ldg(A.o + 3 * r + a);
+            d[a] = __ldg(A.d + 3 * r + a);
         }
-        const int2 run = run_next;
-        if (todo) {
-            const int in = __ffs(todo) - 1;
-            run_next = lane < __shfl_sync(0xffffffffu, l_nr, in) ? runs[(rbase + in) * kRunSlots + lane]
-                                                                : make_int2(0, 0);
-        }
-        const int nt = build_ray_table(s_blobs, nblobs, o, d, tab, lane);
+        const int2 run = (nr >= 0 && lane < nr) ? runs[r * kRunSlots + lane] : make_int2(0, 0);
+        const float tmax = fabsf(tn) + (float)(ke + 1) * A.step * 1.0001f;
+        const float pos_far = (sqrtf(o[0] * o[0] + o[1] * o[1] + o[2] * o[2]) +
+                               tmax * sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2])) * 1.0002f;
+        const int n_ex = build_exact_list(s_blobs, A.field.n_blobs, o, d, pos_far, s_ex[wid], lane);
         __syncwarp();
-        int cut = cnt, kstop = __shfl_sync(0xffffffffu, l_ke, i);
-        if (nt != 0) {
-            float carry = 0.0f;
-            if (nr >= 0) {
-                int ex = run.y;  // -> exclusive prefix of the run lengths
-#pragma unroll
-                for (int o2 = 1; o2 < 32; o2 <<= 1) {
-                    const int y = __shfl_up_sync(0xffffffffu, ex, o2);
-                    if (lane >= o2) ex += y;
-                }
-                ex -= run.y;
-                for (int p0 = 0; p0 < cnt; p0 += 64) {
-                    const int pa = p0 + 2 * lane, pb = pa + 1;
-                    int ka = 0, kb = 0;
-                    for (int j = 0; j < nr; ++j) {
-                        const int ej = __shfl_sync(0xffffffffu, ex, j);
-                        const int kj = __shfl_sync(0xffffffffu, run.x, j);
-                        if (pa >= ej) ka = kj + (pa - ej);
-                        if (pb >= ej) kb = kj + (pb - ej);
-                    }
-                    float taua = 0.0f, taub = 0.0f;
-                    const bool two = pb < cnt;
-                    const float a0 = __fadd_rn(tn, __fmul_rn((float)ka, A.step)), a1 = __fadd_rn(a0, A.step);
-                    const float b0 = __fadd_rn(tn, __fmul_rn((float)(two ? kb : ka), A.step)),
-                                b1 = __fadd_rn(b0, A.step);
-                    const float tma = __fmul_rn(__fadd_rn(a0, a1), 0.5f), tmb = __fmul_rn(__fadd_rn(b0, b1), 0.5f);
-                    float sa = 0.0f, sb = 0.0f;
-                    if (nt > 0 && nt <= kGroupMin) {
-                        if (pa < cnt) sigma_tab2(tab, nt, tma, tmb, sa, sb);
-                    } else if (nt > 0) {  // the group's midpoints span [first, last] (lattice order)
-                        const int last = min(cnt - p0, 64) - 1;
-                        const float t_lo = __shfl_sync(0xffffffffu, tma, 0);
-                        const float t_hi = __shfl_sync(0xffffffffu, (last & 1) ? tmb : tma, last >> 1);
-                        const float t_end = __shfl_sync(0xffffffffu, (last & 1) ? b1 : a1, last >> 1);
-                        const float span = t_end - __shfl_sync(0xffffffffu, a0, 0);
-                        sigma_tab2_group(tab, nt, t_lo, t_hi, span, tma, tmb, sa, sb, pa < cnt);
-                    }
-                    if (pa < cnt) {
-                        if (nt < 0) {
-                            float xa[3], xb[3];
-#pragma unroll
-                            for (int a = 0; a < 3; ++a) {
-                                xa[a] = fmaf(d[a], tma, o[a]);
-                                xb[a] = fmaf(d[a], tmb, o[a]);
-                            }
-                            sigma_early_stop2(s_blobs, nblobs, xa, xb, sa, sb);
-                        }
-                        taua = __fmul_rn(sa, __fsub_rn(a1, a0));
-                        if (two) taub = __fmul_rn(sb, __fsub_rn(b1, b0));
-                    }
-                    const float pair = taua + taub;
-                    float x = pair;  // -> inclusive prefix over the lanes' pairs
-#pragma unroll
-                    for (int o2 = 1; o2 < 32; o2 <<= 1) {
-                        const float y = __shfl_up_sync(0xffffffffu, x, o2);
-                        if (lane >= o2) x += y;
-                    }
-                    const float before_a = carry + (x - pair), before_b = before_a + taua;
-                    const unsigned over_a = __ballot_sync(0xffffffffu, pa < cnt && before_a > A.thr);
-                    const unsigned over_b = __ballot_sync(0xffffffffu, pb < cnt && before_b > A.thr);
-                    if (over_a | over_b) {  // the first point past the threshold, in lattice order
-                        const int ja = over_a ? __ffs(over_a) - 1 : 32, jb = over_b ? __ffs(over_b) - 1 : 32;
-                        const bool at_a = ja <= jb;
-                        const int j = at_a ? ja : jb;
-                        cut = p0 + 2 * j + (at_a ? 0 : 1);
-                        kstop = __shfl_sync(0xffffffffu, at_a ? ka : kb, j);
-                        break;
-                    }
-                    carry += __shfl_sync(0xffffffffu, x, 31);
-                }
-            } else {
-                Lane s;
-                s.R.tn = 0.0f;
-                lane_init(A, r, s);  // the count pass found this ray inside the grid
-                const int ke = kstop;
-                int seen = 0;
-                for (int kb = 0; kb < ke && seen < cnt; kb += 32) {
-                    const int k = kb + lane;
-                    bool occ = false;
-                    float t0 = 0.0f, t1 = 0.0f, xp[3];
-                    if (k < ke) {
-                        int l, ic[3];
-                        occ = lattice_point(A, s.R, k, t0, t1, xp, l, ic);
-                    }
-                    const unsigned m = __ballot_sync(0xffffffffu, occ);
-                    if (!m) continue;
-                    float tau = 0.0f;
-                    if (occ) {
-                        const float tm = __fmul_rn(__fadd_rn(t0, t1), 0.5f);
-                        float sg, unused;
-                        if (nt > 0) {
-                            sigma_tab2(tab, nt, tm, tm, sg, unused);
-                        } else {
-                            float xa[3];
-#pragma unroll
-                            for (int a = 0; a < 3; ++a) xa[a] = fmaf(d[a], tm, o[a]);
-                            sigma_early_stop2(s_blobs, nblobs, xa, xa, sg, unused);
-                        }
-                        tau = __fmul_rn(sg, __fsub_rn(t1, t0));
-                    }
-                    float x = tau;
-#pragma unroll
-                    for (int o2 = 1; o2 < 32; o2 <<= 1) {
-                        const float y = __shfl_up_sync(0xffffffffu, x, o2);
-                        if (lane >= o2) x += y;
-                    }
-                    const unsigned over = __ballot_sync(0xffffffffu, occ && carry + (x - tau) > A.thr);
-                    if (over) {
-                        const int j = __ffs(over) - 1;
-                        cut = seen + __popc(m & ((1u << j) - 1u));
-                        kstop = kb + j;
-                        break;
-                    }
-                    seen += __popc(m);
-                    carry += __shfl_sync(0xffffffffu, x, 31);
-                }
-            }
+        int cut = cnt, kstop = ke;
+        stop_exact(A, s_blobs, s_ex[wid], n_ex, r, o, d, tn, cnt, nr, run, ke, pos_far, lane, s_seq[wid], cut, kstop);
+        if (lane == 0) {
+            counts[r] = cut;
+            kstops[r] = kstop;
+            if (cut != cnt)
+                atomicAdd(reinterpret_cast<unsigned long long*>(block_sums + r / kRaysPerBlock),
+                          (unsigned long long)(long long)(cut - cnt));
         }
-        if (lane == i) {
-            l_cut = cut;
-            l_kstop = kstop;
-        }
-        __syncwarp();  // the next ray rewrites the table
+        __syncwarp();  // the next ray rewrites the list
     }
-    if (lv) {
-        counts[rl] = l_cut;
-        kstops[rl] = l_kstop;
-    }
-    int wsum = l_cut;
-#pragma unroll
-    for (int o2 = 16; o2 > 0; o2 >>= 1) wsum += __shfl_down_sync(0xffffffffu, wsum, o2);
-    if (lane == 0) block_sums[cb] = wsum;
 }
 
 // Single block: exclusive scan of the per-block totals in place; writes the
@@ -1125,7 +1489,8 @@ extern "C" size_t nacc_march_scratch_bytes(int64_t n_rays) {
     const int64_t nb = (n_rays + kRaysPerBlock - 1) / kRaysPerBlock;
     // counts, kstops, nruns, tnear, block sums, run slots
     return align256(4 * (size_t)n_rays) * 4 + align256(8 * (size_t)(nb > 0 ? nb : 1)) +
-           align256(sizeof(int2) * kRunSlots * (size_t)n_rays) + kBlockBitsBytes;
+           align256(sizeof(int2) * kRunSlots * (size_t)n_rays) + kBlockBitsBytes + 256 +  // + work tickets
+           align256(8 * (size_t)n_rays);                                                       // + exact queue
 }
 
 extern "C" int nacc_march_grid(const nacc_grid* grid, const float* rays_o, const float* rays_d,
@@ -1176,6 +1541,7 @@ extern "C" int nacc_march_grid(const nacc_grid* grid, const float* rays_o, const
     A.t_min = params->t_min;
     A.t_max = params->t_max;
     A.thr = with_field ? tau_threshold(params->early_stop_eps) : INFINITY;
+    A.exact_all = params->exact_stops != 0 ? 1 : 0;
     A.inv_step = 1.0f / params->step;
     A.idx32 = ((uint64_t)A.g.n_levels * A.g.res * A.g.res * A.g.res) <= 0xffffffffull ? 1 : 0;
     A.field = with_field ? *field : nacc_blob_field{0, nullptr, nullptr, nullptr, nullptr};
@@ -1216,11 +1582,30 @@ extern "C" int nacc_march_grid(const nacc_grid* grid, const float* rays_o, const
         A, counts, kstops, nruns, tnear, runs, bsums);
     NACC_LAUNCH_CHECK();
     if (with_field) {
-        const size_t shm = sizeof(BlobS) * (size_t)A.field.n_blobs;
+        const size_t shm = sizeof(StopBlob) * (size_t)A.field.n_blobs;
         if (shm > 32 * 1024)
             NACC_CUDA_TRY(cudaFuncSetAttribute(k_march_stop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-        k_march_stop<<<(unsigned)((nb + kStopWarps - 1) / kStopWarps), kStopThreads, shm, st>>>(A, counts, kstops, nruns,
-                                                                                             tnear, runs, bsums);
+        // persistent warps taking 32-ray entries by ticket; rays they cannot
+        // decide from bounds go to a queue decided exactly by a second kernel
+        unsigned long long* tickets = reinterpret_cast<unsigned long long*>(sp + kBlockBitsBytes);  // ticket, qlen, qhead
+        long long* queue = reinterpret_cast<long long*>(sp + kBlockBitsBytes + 256);
+        NACC_CUDA_TRY(cudaMemsetAsync(tickets, 0, 3 * sizeof(unsigned long long), st));
+        int per_sm = 0;
+        NACC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_march_stop, kStopThreads, shm));
+        const int64_t want = (nb + kStopWarps - 1) / kStopWarps;
+        const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sm_count() * std::max(per_sm, 1)));
+        k_march_stop<<<(unsigned)blocks, kStopThreads, shm, st>>>(A, counts, kstops, nruns, tnear, runs, bsums,
+                                                                   tickets, queue, tickets + 1);
+        NACC_LAUNCH_CHECK();
+        if (shm > 32 * 1024 - 8192)
+            NACC_CUDA_TRY(cudaFuncSetAttribute(k_march_stop_exact, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)shm));
+        int per_sm_x = 0;
+        NACC_CUDA_TRY(
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_x, k_march_stop_exact, kStopThreads, shm));
+        const int64_t blocks_x = std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sm_count() * std::max(per_sm_x, 1)));
+        k_march_stop_exact<<<(unsigned)blocks_x, kStopThreads, shm, st>>>(A, counts, kstops, nruns, tnear, runs, bsums,
+                                                                           queue, tickets + 1, tickets + 2);
         NACC_LAUNCH_CHECK();
     }
     if (g_count_ev[1]) NACC_CUDA_TRY(cudaEventRecord(g_count_ev[1], st));
@@ -1273,6 +1658,7 @@ extern "C" int nacc_occupied_range(const nacc_grid* grid, const float* rays_o, c
     A.t_min = params->t_min;
     A.t_max = params->t_max;
     A.thr = INFINITY;
+    A.exact_all = 0;
     A.inv_step = 1.0f / params->step;
     A.idx32 = ((uint64_t)A.g.n_levels * A.g.res * A.g.res * A.g.res) <= 0xffffffffull ? 1 : 0;
     A.field = nacc_blob_field{0, nullptr, nullptr, nullptr, nullptr};

@@ -23,6 +23,7 @@
 // blobs sums every blob directly.
 #include <algorithm>
 
+#include "early_stop.cuh"
 #include "nacc_internal.cuh"
 
 namespace nacc {
@@ -53,6 +54,7 @@ struct UArgs {
     int64_t n;
     int K;
     float thr;
+    int exact_all;  // every early-stop decision on the exact path (validation)
     nacc_blob_field field;
 };
 
@@ -188,30 +190,51 @@ __device__ __forceinline__ void rec_flush(RunRec& q) {
 // sqrt(2 pi) std} (peak <= 0: log2 peak = -inf, never kept).
 constexpr int kStageBlobs = 256;  // blobs staged in shared memory; more are read from global memory
 
-__device__ __forceinline__ void blob_consts(const nacc_blob_field& f, int b, float4& m, float2& k) {
+__device__ __forceinline__ void blob_consts(const nacc_blob_field& f, int b, float4& m, float4& k) {
     const float sd = __ldg(f.std + b), pk = __ldg(f.peak + b);
     m = make_float4(__ldg(f.mu + 3 * b), __ldg(f.mu + 3 * b + 1), __ldg(f.mu + 3 * b + 2), -0.72134752f / (sd * sd));
-    k = make_float2(pk > 0.0f ? __log2f(pk) : -INFINITY, 2.5066283f * sd);
+    k = make_float4(pk > 0.0f ? __log2f(pk) : -INFINITY, 2.5066283f * sd, 1.0f / sd, sd);
 }
 
-// The early-stop table of one ray, built by its warp: the blobs whose
-// integral along the whole ray line exceeds kCullEps (bound peak 2^C
-// sqrt(2 pi) sd / |d|), as {A_b, t*_b, C_b + log2 peak_b} (log2-scaled:
-// density peak_b 2^(A_b (t - t*_b)^2 + C_b)), in blob order.  Returns the
-// count, or -1 if more than kStopTable blobs qualify.
-__device__ int build_warp_table(const nacc_blob_field& f, const float4* sm, const float2* sk, const float o[3],
-                                const float d[3], float4* tab, int lane) {
+// The longest lattice interval within 4 std of a blob's closest approach
+// t*: the lattice's intervals grow with t (1/t falls by the same `dinv` =
+// (1/t_near - 1/t_far) / K per step), so the interval holding t ends before
+// 1 / (1/t - dinv) and is at most that squared times dinv; dt_max = t_far -
+// t_near bounds every interval.  The intervals [t_k, t_k+1] of the table are
+// contiguous (no overlap).
+__device__ __forceinline__ float blob_interval(float ts, float sd, float ilen, float dinv, float dt_max) {
+    const float t_hi = (fabsf(ts) + 4.0f * sd * ilen) * 1.0001f;
+    // fast reciprocals (within 2 ulp) with margins that keep the result an upper bound
+    const float den = __fdividef(1.0f, t_hi) * (1.0f - 1e-5f) - 2.0f * dinv;
+    return den > 0.0f ? fminf(dt_max, dinv * __fdividef(1.0f, den * den) * 1.01f) : dt_max;
+}
+
+// The ray's early-stop table and depth bound (early_stop.cuh), built by the
+// warp, lane b0 + lane handling blob b0 + lane: the per-ray closed form in
+// FP32; the blobs whose integral along the whole ray line exceeds kCullEps
+// (bound peak 2^C sqrt(2 pi) sd / |d|) are compacted in blob order into the
+// table as {A_b, t*_b, C_b + log2 peak_b} (log2-scaled: density peak_b
+// 2^(A_b (t - t*_b)^2 + C_b); blob index in tidx).  U bounds the
+// definition's depth at every sample (every blob's weight, the closed
+// form's own FP32 rounding included); e_out is the error bound's share of
+// the blobs left out (their whole weight).  Returns the number of kept blobs
+// (the table holds the first kStopTable).  onorm =
+// |o|, dnorm = |d|, cnt = the ray's samples, dinv and dt_max as in
+// blob_interval.
+__device__ int build_warp_table(const nacc_blob_field& f, const float4* sm, const float4* sk, const float o[3],
+                                const float d[3], float onorm, float dnorm, float dinv, float dt_max, int cnt,
+                                float4* tab, uint16_t* tidx, float& U, float& e_out, int lane) {
     const float dd = fmaf(d[2], d[2], fmaf(d[1], d[1], d[0] * d[0]));
     const float idd = dd > 0.0f ? 1.0f / dd : 0.0f;
     const float ilen = dd > 0.0f ? rsqrtf(dd) : 0.0f;
     int n = 0;
+    float u = 0.0f, e = 0.0f;
     for (int b0 = 0; b0 < f.n_blobs; b0 += 32) {
         const int b = b0 + lane;
         bool keep = false;
         float4 ent = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         if (b < f.n_blobs) {
-            float4 mc;
-            float2 kc;
+            float4 mc, kc;
             if (b < kStageBlobs) {
                 mc = sm[b];
                 kc = sk[b];
@@ -230,16 +253,128 @@ __device__ int build_warp_table(const nacc_blob_field& f, const float4* sm, cons
                 pp = fmaf(m2, m2, fmaf(m1, m1, m0 * m0));
             }
             const float C = fmaf(mc.w, pp, kc.x);
-            const float bound = dd > 0.0f ? ex2_approx(C) * kc.y * ilen : ex2_approx(C) * 1e30f;
-            keep = bound > kCullEps;
+            const float S = ex2_approx(C);  // largest density on the line
+            float I;                         // integral along the line
+            if (dd > 0.0f) {
+                I = S * kc.y * ilen;
+                keep = I > kCullEps;
+            } else {
+                I = S * dt_max * (float)cnt;
+                keep = true;
+            }
+            if (S > 0.0f) {
+                // growth with the FP32 closed form's own error (within 11u |mu - o|) included
+                const float sd = kc.w * 1.0001f;
+                const float p = sqrtf(pp);
+                const float mn = sqrtf(fmaf(m2, m2, fmaf(m1, m1, m0 * m0)));
+                const float dt_b = dd > 0.0f ? blob_interval(ts, sd, ilen, dinv, dt_max) : dt_max;
+                const float W = blob_weight(
+                    S, I, dt_b, dt_max, 0.0f,
+                    blob_growth(p, kc.z, onorm + 2.5f * fabsf(ts) * dnorm + 16.0f * p + 12.0f * mn));
+                u += W;
+                if (!keep) e += W;
+            }
             ent = make_float4(mc.w * dd, ts, C, 0.0f);
         }
         const unsigned bal = __ballot_sync(0xffffffffu, keep);
         const int pos = n + __popc(bal & ((1u << lane) - 1u));
-        if (keep && pos < kStopTable) tab[pos] = ent;
+        if (keep && pos < kStopTable) {
+            tab[pos] = ent;
+            tidx[pos] = (uint16_t)b;
+        }
         n += __popc(bal);
     }
-    return n <= kStopTable ? n : -1;
+    U = warp_sum(u);
+    e_out = warp_sum(e);
+    return n;
+}
+
+// Error bound of the kept blobs (early_stop.cuh), one lane per kept blob:
+// t* and p^2 again by closest_approach, the table entry rewritten (when the
+// table holds the nt kept blobs; otherwise every kept blob is bounded from
+// its FP32 values, for the direct form).  Returns the whole-ray bound, and
+// the relative one in eps.  Arguments as build_warp_table.
+__device__ float refine_warp_table(const nacc_blob_field& f, const float4* sm, const float4* sk, int nt,
+                                   const float o[3], const float d[3], float onorm, float dnorm, float dinv,
+                                   float dt_max, int cnt, float4* tab, const uint16_t* tidx, float& eps, int lane) {
+    const float dd = fmaf(d[2], d[2], fmaf(d[1], d[1], d[0] * d[0]));
+    const float idd = dd > 0.0f ? 1.0f / dd : 0.0f;
+    const float ilen = dd > 0.0f ? rsqrtf(dd) : 0.0f;
+    const bool have_tab = nt <= kStopTable;
+    float e = 0.0f, em = 0.0f;
+    for (int i = lane; i < (have_tab ? nt : f.n_blobs); i += 32) {
+        const int b = have_tab ? tidx[i] : i;
+        float4 mc, kc;
+        if (b < kStageBlobs) {
+            mc = sm[b];
+            kc = sk[b];
+        } else {
+            blob_consts(f, b, mc, kc);
+        }
+        float ts, pp;
+        if (dd > 0.0f) {
+            const float mu[3] = {mc.x, mc.y, mc.z};
+            closest_approach(mu, o, d, idd, ts, pp);
+        } else {
+            const float m0 = mc.x - o[0], m1 = mc.y - o[1], m2 = mc.z - o[2];
+            ts = 0.0f;
+            pp = fmaf(m2, m2, fmaf(m1, m1, m0 * m0));
+        }
+        const float C = fmaf(mc.w, pp, kc.x);
+        const float S = ex2_approx(C);
+        const float I = dd > 0.0f ? S * kc.y * ilen : S * dt_max * (float)cnt;
+        if (!have_tab && !(I > kCullEps) && dd > 0.0f) continue;  // left out: counted whole in build_warp_table
+        const float sd = kc.w * 1.0001f;
+        const float dt_b = dd > 0.0f ? blob_interval(ts, sd, ilen, dinv, dt_max) : dt_max;
+        const float p = sqrtf(pp);
+        const float pos0 = onorm + 2.5f * fabsf(ts) * dnorm + 16.0f * p;
+        const float gm1 = blob_growth(p, kc.z, pos0);
+        e += blob_error(blob_weight(S, I, dt_b, dt_max, 0.0f, gm1), gm1, p * kc.z, f.n_blobs, true);
+        em = fmaxf(em, blob_rel_error(kc.z, pos0, f.n_blobs));
+        if (have_tab) tab[i] = make_float4(mc.w * dd, ts, C, 0.0f);
+    }
+    eps = warp_max(em);
+    return warp_sum(e);
+}
+
+// The ascending list of the blobs that may be non-zero somewhere on the ray
+// in the definition's arithmetic (early_stop.cuh, blob_may_count), built by
+// the warp; returns its length.  pos_far = |o| + t_far |d|.
+__device__ int build_exact_list(const nacc_blob_field& f, const float4* sm, const float4* sk, const float o[3],
+                                const float d[3], float pos_far, uint16_t* ex_list, int lane) {
+    const float dd = fmaf(d[2], d[2], fmaf(d[1], d[1], d[0] * d[0]));
+    const float idd = dd > 0.0f ? 1.0f / dd : 0.0f;
+    int ne = 0;
+    for (int b0 = 0; b0 < f.n_blobs; b0 += 32) {
+        const int b = b0 + lane;
+        bool in_ex = false;
+        if (b < f.n_blobs) {
+            float4 mc;
+            float4 kc;
+            if (b < kStageBlobs) {
+                mc = sm[b];
+                kc = sk[b];
+            } else {
+                blob_consts(f, b, mc, kc);
+            }
+            const float m0 = mc.x - o[0], m1 = mc.y - o[1], m2 = mc.z - o[2];
+            float pp;
+            if (dd > 0.0f) {
+                const float cx = fmaf(m1, d[2], -m2 * d[1]), cy = fmaf(m2, d[0], -m0 * d[2]),
+                            cz = fmaf(m0, d[1], -m1 * d[0]);
+                pp = fmaf(cz, cz, fmaf(cy, cy, cx * cx)) * idd;
+            } else {
+                pp = fmaf(m2, m2, fmaf(m1, m1, m0 * m0));
+            }
+            // the FP32 distance is within 8u |mu - o| of exact: widen the margin by |mu - o|
+            const float mn = sqrtf(fmaf(m2, m2, fmaf(m1, m1, m0 * m0)));
+            in_ex = blob_may_count(sqrtf(pp), kc.w * 1.0001f, pos_far + mn);
+        }
+        const unsigned bex = __ballot_sync(0xffffffffu, in_ex);
+        if (in_ex) ex_list[ne + __popc(bex & ((1u << lane) - 1u))] = (uint16_t)b;
+        ne += __popc(bex);
+    }
+    return ne;
 }
 
 __device__ __forceinline__ float sigma_table(const float4* tab, int nt, float tm) {
@@ -476,165 +611,381 @@ __global__ void __launch_bounds__(kThreads) k_unb_count(UArgs A, int32_t* __rest
     }
 }
 
-// Early stop (after the count pass): one warp per ray, the block's rays in
-// turn.  The ray's occupied points are visited 32 at a time in lattice order
-// (from the recorded runs, or by walking the lattice when the runs
-// overflowed); each lane adds one point's sigma dt, a warp scan gives the
-// optical depth before each point, and the first point whose depth before
-// it exceeds the threshold ends the ray: its count and stop index are cut
-// there and the block's total is rewritten.
+// sigma*dt at lattice point k of the ray in the definition's arithmetic
+// (early_stop.cuh): t from the lattice table, the blob parameters from
+// global memory, entries that are 0 over the whole chunk left out; 0 for
+// lanes without a point (`valid` false).  Every lane of the warp calls it.
+__device__ __forceinline__ float unb_exact_tau(const UArgs& A, const uint16_t* ex_list, int n_ex, const float o[3],
+                                               const float d[3], int k, bool valid, float pos_far, int lane) {
+    const nacc_blob_field& f = A.field;
+    const int kk = valid ? k : 0;
+    const float t0 = __ldg(A.tt + kk), t1 = __ldg(A.tt + kk + 1), tm = __ldg(A.tm + kk);
+    float x[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) x[a] = __fadd_rn(o[a], __fmul_rn(d[a], tm));
+    const unsigned vm = __ballot_sync(0xffffffffu, valid);
+    if (!vm) return 0.0f;
+    const float t_lo = __shfl_sync(0xffffffffu, tm, __ffs(vm) - 1);
+    const float t_hi = __shfl_sync(0xffffffffu, tm, 31 - __clz(vm));
+    const float dd = fmaf(d[2], d[2], fmaf(d[1], d[1], d[0] * d[0]));
+    const float s = exact_sigma_chunk(
+        x, ex_list, n_ex,
+        [&f](int b) {
+            const float sd = __ldg(f.std + b);
+            return ExactBlob{__ldg(f.mu + 3 * b), __ldg(f.mu + 3 * b + 1), __ldg(f.mu + 3 * b + 2),
+                             __fdiv_rn(-0.5f, __fmul_rn(sd, sd)), __ldg(f.peak + b)};
+        },
+        o, d, dd, dd > 0.0f ? 1.0f / dd : 0.0f, t_lo, t_hi, pos_far, lane);
+    return valid ? __fmul_rn(s, __fsub_rn(t1, t0)) : 0.0f;
+}
+
+// Occupancy of lattice point k (the lattice walk of rays whose runs overflowed).
 template <typename I>
-__global__ void __launch_bounds__(kThreads) k_unb_stop(UArgs A, int32_t* __restrict__ counts,
+__device__ __forceinline__ bool unb_occupied(const UArgs& A, const float o[3], const float d[3], int k) {
+    int lvl;
+    const I idx = cell_index<I>(A, o, d, __ldg(A.tm + k), 0, lvl);
+    return idx != (I)-1 && ((__ldg(&A.g.bits[idx >> 5]) >> (idx & 31)) & 1u);
+}
+
+// The exact path of the early stop (early_stop.cuh): the ray's occupied
+// points in lattice order, 32 at a time (from the recorded runs, or by
+// walking the lattice when the runs overflowed); each lane evaluates one
+// point's sigma*dt in the definition's arithmetic into the warp's buffer
+// `buf` (32 floats of shared memory), then lane 0 adds the terms in order
+// one at a time -- the definition's own sum -- and finds the first point
+// whose depth before it exceeds the threshold, which cuts the ray.  cut /
+// kstop are left as given if the ray never stops.
+template <typename I>
+__device__ __forceinline__ void unb_stop_exact(const UArgs& A, const uint16_t* ex_list, int n_ex, const float o[3],
+                                              const float d[3], int cnt, int nr, int2 run, float pos_far, int lane,
+                                              float* buf, int& cut, int& kstop) {
+    int ex = run.y;  // -> exclusive prefix of the run lengths
+#pragma unroll
+    for (int o2 = 1; o2 < 32; o2 <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, ex, o2);
+        if (lane >= o2) ex += y;
+    }
+    ex -= run.y;
+    const int kend = nr >= 0 ? cnt : A.K;  // positions (runs) or lattice indices (walk)
+    float P = 0.0f;                       // the sequential sum (lane 0's)
+    int seen = 0;
+    for (int q0 = 0; q0 < kend && seen < cnt; q0 += 32) {
+        const int q = q0 + lane;
+        int k = 0;
+        bool on;
+        if (nr >= 0) {
+            for (int j = 0; j < nr; ++j) {
+                const int ej = __shfl_sync(0xffffffffu, ex, j);
+                const int kj = __shfl_sync(0xffffffffu, run.x, j);
+                if (q >= ej) k = kj + (q - ej);
+            }
+            on = q < cnt;
+        } else {
+            k = q;
+            on = q < A.K && unb_occupied<I>(A, o, d, q);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, on);
+        if (!m) continue;
+        buf[lane] = unb_exact_tau(A, ex_list, n_ex, o, d, k, on, pos_far, lane);
+        __syncwarp();
+        int jc = -1, sc = seen;
+        if (lane == 0) {
+            unsigned mm = m;
+            while (mm && sc < cnt) {
+                const int j = __ffs(mm) - 1;
+                mm &= mm - 1;
+                if (P > A.thr) {
+                    jc = j;
+                    break;
+                }
+                P = __fadd_rn(P, buf[j]);
+                ++sc;
+            }
+        }
+        jc = __shfl_sync(0xffffffffu, jc, 0);
+        const int sc0 = __shfl_sync(0xffffffffu, sc, 0);
+        const int kc = __shfl_sync(0xffffffffu, k, jc < 0 ? 0 : jc);
+        __syncwarp();
+        if (jc >= 0) {
+            cut = sc0;
+            kstop = kc;
+            return;
+        }
+        seen = sc0;
+    }
+}
+
+// The fast depth of one ray (early_stop.cuh): its occupied points in lattice
+// order, 64 (runs) or 32 (lattice walk when the runs overflowed) at a time,
+// each lane adding its points' sigma dt from the ray's table (nt entries; -1:
+// none, every blob directly), a warp scan giving the optical depth before
+// each point.  Returns 0 if no point's fast depth comes within the error
+// bound rb of the threshold (no cut), 1 if the first one that does passes it
+// by more than the bound (cut / kstop set there), 2 otherwise (undecided).
+template <typename I>
+__device__ __forceinline__ int unb_fast_cut(const UArgs& A, const float4* tab, int nt, const RayBound& rb,
+                                            const float o[3], const float d[3], int cnt, int nr, int2 run, int lane,
+                                            int& cut, int& kstop) {
+    float Q = 0.0f;  // sum of the depths before the points visited
+    float carry = 0.0f;
+    if (nr >= 0) {
+        int ex = run.y;
+#pragma unroll
+        for (int o2 = 1; o2 < 32; o2 <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, ex, o2);
+            if (lane >= o2) ex += y;
+        }
+        ex -= run.y;
+        // two consecutive points per lane (64 per pass): each table
+        // entry is read once for both
+        for (int p0 = 0; p0 < cnt; p0 += 64) {
+            const int pa = p0 + 2 * lane, pb = pa + 1;
+            int ka = 0, kb = 0;
+            for (int j = 0; j < nr; ++j) {
+                const int ej = __shfl_sync(0xffffffffu, ex, j);
+                const int kj = __shfl_sync(0xffffffffu, run.x, j);
+                if (pa >= ej) ka = kj + (pa - ej);
+                if (pb >= ej) kb = kj + (pb - ej);
+            }
+            float taua = 0.0f, taub = 0.0f;
+            const bool two = pb < cnt;
+            const float a0 = __ldg(A.tt + ka), a1 = __ldg(A.tt + ka + 1);
+            const float b0 = two ? __ldg(A.tt + kb) : a0, b1 = two ? __ldg(A.tt + kb + 1) : a1;
+            const float tca = 0.5f * (a0 + a1), tcb = 0.5f * (b0 + b1);
+            float sa = 0.0f, sb = 0.0f;
+            if (nt > 0) {  // the group's midpoints span [first, last] (lattice order)
+                const int last = min(cnt - p0, 64) - 1;
+                const float t_lo = __shfl_sync(0xffffffffu, tca, 0);
+                const float t_hi = __shfl_sync(0xffffffffu, (last & 1) ? tcb : tca, last >> 1);
+                const float t_end = __shfl_sync(0xffffffffu, (last & 1) ? b1 : a1, last >> 1);
+                const float span = t_end - __shfl_sync(0xffffffffu, a0, 0);
+                sigma_table2_group(tab, nt, t_lo, t_hi, span, tca, tcb, sa, sb, pa < cnt, lane);
+            }
+            if (pa < cnt) {
+                if (nt < 0) {
+                    const float tma = __ldg(A.tm + ka), tmb = __ldg(A.tm + (two ? kb : ka));
+                    const float xa[3] = {__fadd_rn(o[0], __fmul_rn(d[0], tma)), __fadd_rn(o[1], __fmul_rn(d[1], tma)),
+                                         __fadd_rn(o[2], __fmul_rn(d[2], tma))};
+                    const float xb[3] = {__fadd_rn(o[0], __fmul_rn(d[0], tmb)), __fadd_rn(o[1], __fmul_rn(d[1], tmb)),
+                                         __fadd_rn(o[2], __fmul_rn(d[2], tmb))};
+                    sa = sigma_all(A.field, xa);
+                    sb = sigma_all(A.field, xb);
+                }
+                taua = __fmul_rn(sa, __fsub_rn(a1, a0));
+                if (two) taub = __fmul_rn(sb, __fsub_rn(b1, b0));
+            }
+            const float pair = taua + taub;
+            float x = pair;  // -> inclusive prefix over the lanes' pairs
+#pragma unroll
+            for (int o2 = 1; o2 < 32; o2 <<= 1) {
+                const float y = __shfl_up_sync(0xffffffffu, x, o2);
+                if (lane >= o2) x += y;
+            }
+            const float before_a = carry + (x - pair), before_b = before_a + taua;
+            const float Qc = Q + warp_sum((pa < cnt ? before_a : 0.0f) + (pb < cnt ? before_b : 0.0f));
+            const float lo_thr = A.thr - depth_error(rb, cnt, Qc, A.thr);
+            const unsigned over_a = __ballot_sync(0xffffffffu, pa < cnt && before_a > lo_thr);
+            const unsigned over_b = __ballot_sync(0xffffffffu, pb < cnt && before_b > lo_thr);
+            if (over_a | over_b) {  // the first point near or past the threshold, in lattice order
+                const int ja = over_a ? __ffs(over_a) - 1 : 32, jb = over_b ? __ffs(over_b) - 1 : 32;
+                const bool at_a = ja <= jb;
+                const int j = at_a ? ja : jb;
+                const float bc = __shfl_sync(0xffffffffu, at_a ? before_a : before_b, j);
+                const int kc = __shfl_sync(0xffffffffu, at_a ? ka : kb, j);
+                if (bc - depth_error(rb, cnt, Qc, bc) > A.thr) {
+                    cut = p0 + 2 * j + (at_a ? 0 : 1);
+                    kstop = kc;
+                    return 1;
+                }
+                return 2;
+            }
+            Q = Qc;
+            carry += __shfl_sync(0xffffffffu, x, 31);
+        }
+    } else {
+        int seen = 0;
+        for (int kb = 0; kb < A.K && seen < cnt; kb += 32) {
+            const int k = kb + lane;
+            bool occ = false;
+            if (k < A.K) {
+                int lvl;
+                const I idx = cell_index<I>(A, o, d, __ldg(A.tm + k), 0, lvl);
+                occ = idx != (I)-1 && ((__ldg(&A.g.bits[idx >> 5]) >> (idx & 31)) & 1u);
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, occ);
+            if (!m) continue;
+            float tau = 0.0f;
+            if (occ) {
+                const float t0 = __ldg(A.tt + k), t1 = __ldg(A.tt + k + 1);
+                float sg;
+                if (nt >= 0) {
+                    sg = sigma_table(tab, nt, 0.5f * (t0 + t1));
+                } else {
+                    const float tm = __ldg(A.tm + k);
+                    const float x[3] = {__fadd_rn(o[0], __fmul_rn(d[0], tm)), __fadd_rn(o[1], __fmul_rn(d[1], tm)),
+                                        __fadd_rn(o[2], __fmul_rn(d[2], tm))};
+                    sg = sigma_all(A.field, x);
+                }
+                tau = __fmul_rn(sg, __fsub_rn(t1, t0));
+            }
+            float x = tau;
+#pragma unroll
+            for (int o2 = 1; o2 < 32; o2 <<= 1) {
+                const float y = __shfl_up_sync(0xffffffffu, x, o2);
+                if (lane >= o2) x += y;
+            }
+            const float before = carry + (x - tau);
+            const float Qc = Q + warp_sum(occ ? before : 0.0f);
+            const float lo_thr = A.thr - depth_error(rb, cnt, Qc, A.thr);
+            const unsigned over = __ballot_sync(0xffffffffu, occ && before > lo_thr);
+            if (over) {
+                const int j = __ffs(over) - 1;
+                const float bc = __shfl_sync(0xffffffffu, before, j);
+                if (bc - depth_error(rb, cnt, Qc, bc) > A.thr) {
+                    cut = seen + __popc(m & ((1u << j) - 1u));
+                    kstop = kb + j;
+                    return 1;
+                }
+                return 2;
+            }
+            seen += __popc(m);
+            Q = Qc;
+            carry += __shfl_sync(0xffffffffu, x, 31);
+        }
+    }
+    return 0;
+}
+
+// Early stop (after the count pass): one warp per ray, the block's rays in
+// turn, each decided as early_stop.cuh describes: no density at all when the
+// ray's depth bound stays below the threshold; else the fast depth -- the
+// ray's occupied points visited 64 (runs) or 32 (lattice walk when the runs
+// overflowed) at a time in lattice order, each lane adding its points'
+// sigma dt from the ray's table, a warp scan giving the optical depth
+// before each point -- cut at the first point whose fast depth passes the
+// threshold by more than the bound; else (a fast depth within the bound of
+// the threshold, or A.exact_all) the exact path.  The count and stop index
+// are cut there and the block's total is rewritten.
+template <typename I>
+__global__ void __launch_bounds__(kThreads, 5) k_unb_stop(UArgs A, int32_t* __restrict__ counts,
                                                        int32_t* __restrict__ kstops,
                                                        const int32_t* __restrict__ nruns,
                                                        const int2* __restrict__ runs,
-                                                       long long* __restrict__ block_sums) {
+                                                       long long* __restrict__ block_sums,
+                                                       unsigned long long* __restrict__ ticket,
+                                                       long long* __restrict__ queue,
+                                                       unsigned long long* __restrict__ qlen) {
     __shared__ float4 s_tab[kWarps][kStopTable];
+    __shared__ uint16_t s_tidx[kWarps][kStopTable];
     __shared__ float4 s_bm[kStageBlobs];
-    __shared__ float2 s_bk[kStageBlobs];
-    __shared__ int s_w[kWarps];
+    __shared__ float4 s_bk[kStageBlobs];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     float4* tab = s_tab[wid];
+    uint16_t* tidx = s_tidx[wid];
     for (int b = tid; b < min(A.field.n_blobs, kStageBlobs); b += kThreads) blob_consts(A.field, b, s_bm[b], s_bk[b]);
     __syncthreads();
-    const int64_t rbase = (int64_t)blockIdx.x * kThreads + wid * 32;
-    int wsum = 0;
-    for (int i = 0; i < 32; ++i) {
-        const int64_t r = rbase + i;
-        if (r >= A.n) break;
-        const int cnt = counts[r];
-        if (cnt == 0) continue;
+    const float t_near = __ldg(A.tt), t_far = __ldg(A.tt + A.K);
+    const float dinv = (1.0f / t_near - 1.0f / t_far) / (float)A.K * 1.01f;
+    const float dt_max = (t_far - t_near) * 1.0001f;
+    const int nblobs = A.field.n_blobs;
+    const int64_t n_groups = (A.n + 31) / 32;
+    for (;;) {  // groups of 32 rays by ticket: rays that stop cost far more than rays that cannot
+        unsigned long long tk = 0;
+        if (lane == 0) tk = atomicAdd(ticket, 1ull);
+        const int64_t grp = (int64_t)__shfl_sync(0xffffffffu, tk, 0);
+        if (grp >= n_groups) break;
+        const int64_t rbase = grp * 32;
+        long long delta = 0;  // change of the block's total
+        for (int i = 0; i < 32; ++i) {
+            const int64_t r = rbase + i;
+            if (r >= A.n) break;
+            const int cnt = counts[r];
+            if (cnt == 0) continue;
+            const float o[3] = {A.o[3 * r], A.o[3 * r + 1], A.o[3 * r + 2]};
+            const float d[3] = {A.d[3 * r], A.d[3 * r + 1], A.d[3 * r + 2]};
+            const float onorm = sqrtf(o[0] * o[0] + o[1] * o[1] + o[2] * o[2]) * 1.0001f;
+            const float dnorm = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) * 1.0001f;
+            int cut = cnt, kstop = A.K;
+            float U, e_out;
+            const int nk = build_warp_table(A.field, s_bm, s_bk, o, d, onorm, dnorm, dinv, dt_max, cnt, tab, tidx, U,
+                                            e_out, lane);
+            __syncwarp();
+            if (A.exact_all != 0 || !(depth_upper(U, cnt, nblobs) <= A.thr)) {  // the ray may stop
+                const int nt = nk <= kStopTable ? nk : -1;
+                const float e_grp = nt > 0 ? 2.0f * kGroupEps * (float)nt * (float)((cnt + 63) / 64) : 0.0f;
+                // the refined table and its error bound
+                float eps;
+                const float ek = refine_warp_table(A.field, s_bm, s_bk, nk, o, d, onorm, dnorm, dinv, dt_max, cnt, tab,
+                                                   tidx, eps, lane);
+                __syncwarp();
+                const RayBound rb{U, ek, eps, e_out + e_grp};
+                const int nr = nruns[r];
+                const int2 run = (nr >= 0 && lane < nr) ? runs[r * kRunSlots + lane] : make_int2(0, 0);
+                const int st = A.exact_all != 0 || !bounds_usable(rb, cnt, A.thr)
+                                   ? 2
+                                   : unb_fast_cut<I>(A, tab, nt, rb, o, d, cnt, nr, run, lane, cut, kstop);
+                const bool exact = st == 2;
+                if (exact && lane == 0) queue[atomicAdd(qlen, 1ull)] = r;  // decided exactly by k_unb_stop_exact
+            }
+            if (lane == 0) {
+                counts[r] = cut;
+                kstops[r] = kstop;
+            }
+            delta += cut - cnt;
+            __syncwarp();  // the next ray rewrites the table
+        }
+        if (lane == 0 && delta != 0)
+            atomicAdd(reinterpret_cast<unsigned long long*>(block_sums + rbase / kThreads), (unsigned long long)delta);
+    }
+}
+
+// Exact decisions of the rays the early-stop pass queued (early_stop.cuh):
+// persistent warps take queued rays one at a time (ticket `qhead` over the
+// `*qlen` entries), build the ray's exact blob list and run the exact path;
+// the cut and its lattice index replace the ray's count and stop, and the
+// change of the count is added to its block's total.
+template <typename I>
+__global__ void __launch_bounds__(kThreads) k_unb_stop_exact(UArgs A, int32_t* __restrict__ counts,
+                                                             int32_t* __restrict__ kstops,
+                                                             const int32_t* __restrict__ nruns,
+                                                             const int2* __restrict__ runs,
+                                                             long long* __restrict__ block_sums,
+                                                             const long long* __restrict__ queue,
+                                                             const unsigned long long* __restrict__ qlen,
+                                                             unsigned long long* __restrict__ qhead) {
+    __shared__ float4 s_bm[kStageBlobs];
+    __shared__ float4 s_bk[kStageBlobs];
+    __shared__ uint16_t s_ex[kWarps][kMaxBlobs];
+    __shared__ float s_seq[kWarps][32];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int b = tid; b < min(A.field.n_blobs, kStageBlobs); b += kThreads) blob_consts(A.field, b, s_bm[b], s_bk[b]);
+    __syncthreads();
+    const float t_far = __ldg(A.tt + A.K);
+    const unsigned long long nq = *qlen;
+    for (;;) {
+        unsigned long long tk = 0;
+        if (lane == 0) tk = atomicAdd(qhead, 1ull);
+        tk = __shfl_sync(0xffffffffu, tk, 0);
+        if (tk >= nq) break;
+        const int64_t r = queue[tk];
+        const int cnt = counts[r], nr = nruns[r];
         const float o[3] = {A.o[3 * r], A.o[3 * r + 1], A.o[3 * r + 2]};
         const float d[3] = {A.d[3 * r], A.d[3 * r + 1], A.d[3 * r + 2]};
-        const int nt = build_warp_table(A.field, s_bm, s_bk, o, d, tab, lane);
+        const int2 run = (nr >= 0 && lane < nr) ? runs[r * kRunSlots + lane] : make_int2(0, 0);
+        const float pos_far = (sqrtf(o[0] * o[0] + o[1] * o[1] + o[2] * o[2]) +
+                               t_far * sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2])) * 1.0002f;
+        const int n_ex = build_exact_list(A.field, s_bm, s_bk, o, d, pos_far, s_ex[wid], lane);
         __syncwarp();
-        const int nr = nruns[r];
         int cut = cnt, kstop = A.K;
-        float carry = 0.0f;
-        if (nr >= 0) {
-            const int2 run = lane < nr ? runs[r * kRunSlots + lane] : make_int2(0, 0);
-            int ex = run.y;
-#pragma unroll
-            for (int o2 = 1; o2 < 32; o2 <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, ex, o2);
-                if (lane >= o2) ex += y;
-            }
-            ex -= run.y;
-            // two consecutive points per lane (64 per pass): each table
-            // entry is read once for both
-            for (int p0 = 0; p0 < cnt; p0 += 64) {
-                const int pa = p0 + 2 * lane, pb = pa + 1;
-                int ka = 0, kb = 0;
-                for (int j = 0; j < nr; ++j) {
-                    const int ej = __shfl_sync(0xffffffffu, ex, j);
-                    const int kj = __shfl_sync(0xffffffffu, run.x, j);
-                    if (pa >= ej) ka = kj + (pa - ej);
-                    if (pb >= ej) kb = kj + (pb - ej);
-                }
-                float taua = 0.0f, taub = 0.0f;
-                const bool two = pb < cnt;
-                const float a0 = __ldg(A.tt + ka), a1 = __ldg(A.tt + ka + 1);
-                const float b0 = two ? __ldg(A.tt + kb) : a0, b1 = two ? __ldg(A.tt + kb + 1) : a1;
-                const float tca = 0.5f * (a0 + a1), tcb = 0.5f * (b0 + b1);
-                float sa = 0.0f, sb = 0.0f;
-                if (nt > 0) {  // the group's midpoints span [first, last] (lattice order)
-                    const int last = min(cnt - p0, 64) - 1;
-                    const float t_lo = __shfl_sync(0xffffffffu, tca, 0);
-                    const float t_hi = __shfl_sync(0xffffffffu, (last & 1) ? tcb : tca, last >> 1);
-                    const float t_end = __shfl_sync(0xffffffffu, (last & 1) ? b1 : a1, last >> 1);
-                    const float span = t_end - __shfl_sync(0xffffffffu, a0, 0);
-                    sigma_table2_group(tab, nt, t_lo, t_hi, span, tca, tcb, sa, sb, pa < cnt, lane);
-                }
-                if (pa < cnt) {
-                    if (nt < 0) {
-                        const float tma = __ldg(A.tm + ka), tmb = __ldg(A.tm + (two ? kb : ka));
-                        const float xa[3] = {__fadd_rn(o[0], __fmul_rn(d[0], tma)), __fadd_rn(o[1], __fmul_rn(d[1], tma)),
-                                             __fadd_rn(o[2], __fmul_rn(d[2], tma))};
-                        const float xb[3] = {__fadd_rn(o[0], __fmul_rn(d[0], tmb)), __fadd_rn(o[1], __fmul_rn(d[1], tmb)),
-                                             __fadd_rn(o[2], __fmul_rn(d[2], tmb))};
-                        sa = sigma_all(A.field, xa);
-                        sb = sigma_all(A.field, xb);
-                    }
-                    taua = __fmul_rn(sa, __fsub_rn(a1, a0));
-                    if (two) taub = __fmul_rn(sb, __fsub_rn(b1, b0));
-                }
-                const float pair = taua + taub;
-                float x = pair;  // -> inclusive prefix over the lanes' pairs
-#pragma unroll
-                for (int o2 = 1; o2 < 32; o2 <<= 1) {
-                    const float y = __shfl_up_sync(0xffffffffu, x, o2);
-                    if (lane >= o2) x += y;
-                }
-                const float before_a = carry + (x - pair), before_b = before_a + taua;
-                const unsigned over_a = __ballot_sync(0xffffffffu, pa < cnt && before_a > A.thr);
-                const unsigned over_b = __ballot_sync(0xffffffffu, pb < cnt && before_b > A.thr);
-                if (over_a | over_b) {  // the first point past the threshold, in lattice order
-                    const int ja = over_a ? __ffs(over_a) - 1 : 32, jb = over_b ? __ffs(over_b) - 1 : 32;
-                    const bool at_a = ja <= jb;
-                    const int j = at_a ? ja : jb;
-                    cut = p0 + 2 * j + (at_a ? 0 : 1);
-                    kstop = __shfl_sync(0xffffffffu, at_a ? ka : kb, j);
-                    break;
-                }
-                carry += __shfl_sync(0xffffffffu, x, 31);
-            }
-        } else {
-            int seen = 0;
-            for (int kb = 0; kb < A.K && seen < cnt; kb += 32) {
-                const int k = kb + lane;
-                bool occ = false;
-                if (k < A.K) {
-                    int lvl;
-                    const I idx = cell_index<I>(A, o, d, __ldg(A.tm + k), 0, lvl);
-                    occ = idx != (I)-1 && ((__ldg(&A.g.bits[idx >> 5]) >> (idx & 31)) & 1u);
-                }
-                const unsigned m = __ballot_sync(0xffffffffu, occ);
-                if (!m) continue;
-                float tau = 0.0f;
-                if (occ) {
-                    const float t0 = __ldg(A.tt + k), t1 = __ldg(A.tt + k + 1);
-                    float sg;
-                    if (nt >= 0) {
-                        sg = sigma_table(tab, nt, 0.5f * (t0 + t1));
-                    } else {
-                        const float tm = __ldg(A.tm + k);
-                        const float x[3] = {__fadd_rn(o[0], __fmul_rn(d[0], tm)), __fadd_rn(o[1], __fmul_rn(d[1], tm)),
-                                            __fadd_rn(o[2], __fmul_rn(d[2], tm))};
-                        sg = sigma_all(A.field, x);
-                    }
-                    tau = __fmul_rn(sg, __fsub_rn(t1, t0));
-                }
-                float x = tau;
-#pragma unroll
-                for (int o2 = 1; o2 < 32; o2 <<= 1) {
-                    const float y = __shfl_up_sync(0xffffffffu, x, o2);
-                    if (lane >= o2) x += y;
-                }
-                const unsigned over = __ballot_sync(0xffffffffu, occ && carry + (x - tau) > A.thr);
-                if (over) {
-                    const int j = __ffs(over) - 1;
-                    cut = seen + __popc(m & ((1u << j) - 1u));
-                    kstop = kb + j;
-                    break;
-                }
-                seen += __popc(m);
-                carry += __shfl_sync(0xffffffffu, x, 31);
-            }
-        }
+        unb_stop_exact<I>(A, s_ex[wid], n_ex, o, d, cnt, nr, run, pos_far, lane, s_seq[wid], cut, kstop);
         if (lane == 0) {
             counts[r] = cut;
             kstops[r] = kstop;
+            if (cut != cnt)
+                atomicAdd(reinterpret_cast<unsigned long long*>(block_sums + r / kThreads),
+                          (unsigned long long)(long long)(cut - cnt));
         }
-        wsum += cut;
-        __syncwarp();  // the next ray rewrites the table
-    }
-    if (lane == 0) s_w[wid] = wsum;
-    __syncthreads();
-    if (tid == 0) {
-        long long t = 0;
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) t += s_w[w];
-        block_sums[blockIdx.x] = t;
+        __syncwarp();  // the next ray rewrites the list
     }
 }
 
@@ -843,7 +1194,8 @@ extern "C" size_t nacc_march_unbounded_scratch_bytes(int64_t n_rays, int32_t max
     const int64_t nb = (n_rays + kThreads - 1) / kThreads;
     return align256(4 * (size_t)n_rays) * 3 + align256(sizeof(int2) * kRunSlots * (size_t)n_rays) +
            align256(8 * (size_t)(nb > 0 ? nb : 1)) + align256(4 * ((size_t)max_steps + 1)) +
-           align256(4 * (size_t)max_steps) + align256(any_bytes(kLogF)) + align256(any_bytes(kLogC));
+           align256(4 * (size_t)max_steps) + align256(any_bytes(kLogF)) + align256(any_bytes(kLogC)) +
+           256 + align256(8 * (size_t)n_rays);  // work tickets and exact queue of the early-stop pass
 }
 
 extern "C" int nacc_march_unbounded(const nacc_grid* grid, const float* rays_o, const float* rays_d, int64_t n_rays,
@@ -886,6 +1238,7 @@ extern "C" int nacc_march_unbounded(const nacc_grid* grid, const float* rays_o, 
     A.n = n_rays;
     A.K = params->max_steps;
     A.thr = with_field ? tau_threshold(params->early_stop_eps) : INFINITY;
+    A.exact_all = params->exact_stops != 0 ? 1 : 0;
     A.field = with_field ? *field : nacc_blob_field{0, nullptr, nullptr, nullptr, nullptr};
     char* sp = static_cast<char*>(scratch);
     int32_t* counts = reinterpret_cast<int32_t*>(sp);
@@ -905,6 +1258,10 @@ extern "C" int nacc_march_unbounded(const nacc_grid* grid, const float* rays_o, 
     uint32_t* f_any = reinterpret_cast<uint32_t*>(sp);
     sp += align256(any_bytes(kLogF));
     uint32_t* c_any = reinterpret_cast<uint32_t*>(sp);
+    sp += align256(any_bytes(kLogC));
+    unsigned long long* tickets = reinterpret_cast<unsigned long long*>(sp);  // ticket, qlen, qhead
+    sp += 256;
+    long long* queue = reinterpret_cast<long long*>(sp);
     A.tt = tt;
     A.tm = tm;
     A.nbf = (A.g.res + (1 << kLogF) - 1) >> kLogF;
@@ -934,10 +1291,36 @@ extern "C" int nacc_march_unbounded(const nacc_grid* grid, const float* rays_o, 
         k_unb_count<int64_t><<<(unsigned)nb, kThreads, 0, st>>>(A, counts, kstops, nruns, runs, bsums);
     NACC_LAUNCH_CHECK();
     if (with_field) {
-        if (idx32)
-            k_unb_stop<uint32_t><<<(unsigned)nb, kThreads, 0, st>>>(A, counts, kstops, nruns, runs, bsums);
-        else
-            k_unb_stop<int64_t><<<(unsigned)nb, kThreads, 0, st>>>(A, counts, kstops, nruns, runs, bsums);
+        // persistent warps taking 32-ray groups by ticket; rays they cannot
+        // decide from bounds go to a queue decided exactly by a second kernel
+        NACC_CUDA_TRY(cudaMemsetAsync(tickets, 0, 3 * sizeof(unsigned long long), st));
+        int per_sm = 0, per_sm_x = 0;
+        if (idx32) {
+            NACC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_unb_stop<uint32_t>, kThreads, 0));
+            NACC_CUDA_TRY(
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_x, k_unb_stop_exact<uint32_t>, kThreads, 0));
+        } else {
+            NACC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_unb_stop<int64_t>, kThreads, 0));
+            NACC_CUDA_TRY(
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_x, k_unb_stop_exact<int64_t>, kThreads, 0));
+        }
+        const unsigned blocks =
+            (unsigned)std::max<int64_t>(1, std::min<int64_t>(nb, (int64_t)sm_count() * std::max(per_sm, 1)));
+        const unsigned blocks_x =
+            (unsigned)std::max<int64_t>(1, std::min<int64_t>(nb, (int64_t)sm_count() * std::max(per_sm_x, 1)));
+        if (idx32) {
+            k_unb_stop<uint32_t><<<blocks, kThreads, 0, st>>>(A, counts, kstops, nruns, runs, bsums, tickets, queue,
+                                                             tickets + 1);
+            NACC_LAUNCH_CHECK();
+            k_unb_stop_exact<uint32_t><<<blocks_x, kThreads, 0, st>>>(A, counts, kstops, nruns, runs, bsums, queue,
+                                                                     tickets + 1, tickets + 2);
+        } else {
+            k_unb_stop<int64_t><<<blocks, kThreads, 0, st>>>(A, counts, kstops, nruns, runs, bsums, tickets, queue,
+                                                            tickets + 1);
+            NACC_LAUNCH_CHECK();
+            k_unb_stop_exact<int64_t><<<blocks_x, kThreads, 0, st>>>(A, counts, kstops, nruns, runs, bsums, queue,
+                                                                    tickets + 1, tickets + 2);
+        }
         NACC_LAUNCH_CHECK();
     }
     k_unb_scan<<<1, 1024, 0, st>>>(bsums, nb, out->offsets + n_rays, out->n_samples);

@@ -66,7 +66,7 @@ def test_library_exports_every_declared_symbol(lib):
 def test_struct_layouts_match_header(lib):
     from paper_2305_04966_gb300 import _abi
     assert ctypes.sizeof(_abi.Grid) == 6 * 4 + 2 * 4 + 8
-    assert ctypes.sizeof(_abi.MarchParams) == 20
+    assert ctypes.sizeof(_abi.MarchParams) == 24
     assert ctypes.sizeof(_abi.BlobField) == 8 + 4 * 8
     assert ctypes.sizeof(_abi.Packed) == 6 * 8
 

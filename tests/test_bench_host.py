@@ -20,7 +20,7 @@ def test_algorithmic_bytes_and_flop_per_unit():
     # read + per-ray outputs; the same read + gradients written + upstream gradients
     assert bench.BYTES == {"march": (12, 32), "render_fwd": (24, 32), "render_bwd": (40, 28)}
     assert bench.count_pass_flop(1000, 8) == 1000 * (11 * 8 + 14)
-    assert sum(bench.KERNELS_PER_STEP.values()) == 10  # six march kernels with a field + four
+    assert sum(bench.KERNELS_PER_STEP.values()) == 11  # seven march kernels with a field + four
 
 
 def test_recorded_traffic_follows_the_kernel_source(tmp_path, monkeypatch):
