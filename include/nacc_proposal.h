@@ -59,6 +59,21 @@ int nacc_mlp_train_grads(int64_t n, const float* xyz, const float* target, const
                          const uint16_t* weights, float* grads, float* loss_sum, void* stream);
 
 /*
+ * The same network on rows that are already its layer-1 input: the encoding
+ * in the operand precision, enc [n][64] BF16 (bit patterns, 16-byte aligned
+ * rows; columns 51..63, the encoding's zero padding, are ignored).  Sec. 3.1
+ * "PDF Approaches" (the proposal network).  These let a caller (the parity
+ * tests) feed both this library and a reference the identical operands;
+ * nacc_mlp_forward_encoded -> sigma [n] as nacc_mlp_forward,
+ * nacc_mlp_train_grads_encoded accumulates as nacc_mlp_train_grads.
+ * Errors: n < 0, NULL pointers, enc misaligned.
+ */
+int nacc_mlp_forward_encoded(int64_t n, const uint16_t* enc, const float* params, const uint16_t* weights,
+                             float* sigma, void* stream);
+int nacc_mlp_train_grads_encoded(int64_t n, const uint16_t* enc, const float* target, const float* params,
+                                 const uint16_t* weights, float* grads, float* loss_sum, void* stream);
+
+/*
  * The gradient-descent step of that update (Eq. 4 with SGD-type F, Sec. 3.1):
  * one Adam step on the FP32 master parameters (step = 1, 2, ...; bias
  * correction 1 - beta^step), then writes the BF16 weights and zeroes grads.

@@ -87,9 +87,10 @@ def forward(params: dict, xyz, round_bf16: bool = True, enc=None) -> dict:
     return {"e": e, "z1": z1, "h1": h1, "z2": z2, "h2": h2, "z3": z3, "sigma": _softplus(z3)}
 
 
-def loss_and_grads(params: dict, xyz, target, round_bf16: bool = True) -> tuple[float, dict]:
-    """L = mean (sigma - target)^2 and dL/d(parameter) (FP64)."""
-    f = forward(params, xyz, round_bf16)
+def loss_and_grads(params: dict, xyz, target, round_bf16: bool = True, enc=None) -> tuple[float, dict]:
+    """L = mean (sigma - target)^2 and dL/d(parameter) (FP64); ``enc`` as in
+    :func:`forward`."""
+    f = forward(params, xyz, round_bf16, enc=enc)
     t = np.asarray(target, np.float64)
     B = t.shape[0]
     r = bf16 if round_bf16 else (lambda a: np.asarray(a, np.float64))

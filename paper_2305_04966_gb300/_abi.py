@@ -83,6 +83,8 @@ SIGNATURES = {
     "nacc_mlp_sync": (c_i32, [c_vp, c_vp, c_vp]),
     "nacc_mlp_forward": (c_i32, [c_i64, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "nacc_mlp_train_grads": (c_i32, [c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "nacc_mlp_forward_encoded": (c_i32, [c_i64, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "nacc_mlp_train_grads_encoded": (c_i32, [c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "nacc_mlp_adam": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, c_f32, c_f32, c_f32, c_f32, c_vp, c_vp]),
     "nacc_mlp_encode": (c_i32, [c_i64, c_vp, c_vp, c_vp]),
     "nacc_mlp_forward_rays": (c_i32, [c_i64, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),

@@ -614,6 +614,26 @@ class ProposalMLP:
                   _ptr(sig), _stream(dev))
         return sig
 
+    def forward_encoded(self, enc: torch.Tensor, out=None) -> torch.Tensor:
+        """The network on rows that are already its layer-1 input: enc [n][64]
+        int16 holding BF16 bit patterns (``nacc_mlp_forward_encoded``)."""
+        dev = enc.device
+        n = int(enc.shape[0])
+        _check(enc, "enc", torch.int16, dev, (n, 64))
+        sig = out if out is not None else torch.empty(n, dtype=_F32, device=dev)
+        _abi.call("nacc_mlp_forward_encoded", n, _ptr(enc), _ptr(self.params), _ptr(self.weights), _ptr(sig),
+                  _stream(dev))
+        return sig
+
+    def accumulate_grads_encoded(self, enc: torch.Tensor, target: torch.Tensor):
+        """As :meth:`accumulate_grads` on encoded rows (``nacc_mlp_train_grads_encoded``)."""
+        dev = enc.device
+        n = int(enc.shape[0])
+        _check(enc, "enc", torch.int16, dev, (n, 64))
+        _check(target, "target", _F32, dev, (n,))
+        _abi.call("nacc_mlp_train_grads_encoded", n, _ptr(enc), _ptr(target), _ptr(self.params),
+                  _ptr(self.weights), _ptr(self.grads), _ptr(self.loss_sum), _stream(dev))
+
     def accumulate_grads(self, xyz: torch.Tensor, target: torch.Tensor):
         """Adds dL/dparams of L = mean (density - target)^2 into ``grads``
         and sum (density - target)^2 into ``loss_sum``."""

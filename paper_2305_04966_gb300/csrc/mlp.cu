@@ -114,6 +114,43 @@ __device__ __forceinline__ void store_col(uint8_t* tile2, int p, const float v[6
         *reinterpret_cast<__nv_bfloat16*>(sub + tc::sw128_offset(i, p & 63)) = __float2bfloat16_rn(v[i]);
 }
 
+// A value as the sum of two BF16 numbers: hi = bf16(v), lo = bf16(v - hi)
+// (v - hi is exact in FP32), within 2^-18 |v| of v.  The training kernel's
+// error terms go to the tensor cores as both parts, so its products carry
+// about 16 significant bits of the FP32 terms instead of 8.
+__device__ __forceinline__ float bf16_lo(float v) { return v - __bfloat162float(__float2bfloat16_rn(v)); }
+
+// Row r of the heads and of the tails of v into two K-major SW128 tiles.
+__device__ __forceinline__ void store_row_split(uint8_t* tile_hi, uint8_t* tile_lo, int r, const float v[64]) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        uint4 q, w;
+        q.x = pack_bf16x2(v[8 * c + 0], v[8 * c + 1]);
+        q.y = pack_bf16x2(v[8 * c + 2], v[8 * c + 3]);
+        q.z = pack_bf16x2(v[8 * c + 4], v[8 * c + 5]);
+        q.w = pack_bf16x2(v[8 * c + 6], v[8 * c + 7]);
+        w.x = pack_bf16x2(bf16_lo(v[8 * c + 0]), bf16_lo(v[8 * c + 1]));
+        w.y = pack_bf16x2(bf16_lo(v[8 * c + 2]), bf16_lo(v[8 * c + 3]));
+        w.z = pack_bf16x2(bf16_lo(v[8 * c + 4]), bf16_lo(v[8 * c + 5]));
+        w.w = pack_bf16x2(bf16_lo(v[8 * c + 6]), bf16_lo(v[8 * c + 7]));
+        const uint32_t off = (r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4);
+        *reinterpret_cast<uint4*>(tile_hi + off) = q;
+        *reinterpret_cast<uint4*>(tile_lo + off) = w;
+    }
+}
+
+// Column p of the heads and of the tails (see store_col).
+__device__ __forceinline__ void store_col_split(uint8_t* tile2_hi, uint8_t* tile2_lo, int p, const float v[64]) {
+    const uint32_t sub = (p >> 6) * kWBytes;
+#pragma unroll
+    for (int i = 0; i < 64; ++i) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(v[i]);
+        const uint32_t off = sub + tc::sw128_offset(i, p & 63);
+        *reinterpret_cast<__nv_bfloat16*>(tile2_hi + off) = h;
+        *reinterpret_cast<__nv_bfloat16*>(tile2_lo + off) = __float2bfloat16_rn(v[i] - __bfloat162float(h));
+    }
+}
+
 __device__ __forceinline__ float load_elem(const uint8_t* tile, int r, int k) {
     return __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(tile + tc::sw128_offset(r, k)));
 }
@@ -167,7 +204,23 @@ struct PointSrc {
     int nb;
     int contract;  // rays: feed c(x), the L-infinity contraction of the bin midpoint
     int p32;       // rays: n_rays * nb < 2^32
+    const uint16_t* enc = nullptr;  // rows already encoded (BF16, [n][64]): replaces the encoding
 };
+
+// Row p of an encoded input (64 BF16 values, 16-byte aligned rows).
+__device__ __forceinline__ void load_enc_row(const uint16_t* enc, int64_t p, float v[64]) {
+    const uint4* q = reinterpret_cast<const uint4*>(enc + 64 * p);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const uint4 w = q[c];
+        const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[8 * c + 2 * k] = __uint_as_float(u[k] << 16);
+            v[8 * c + 2 * k + 1] = __uint_as_float(u[k] & 0xffff0000u);
+        }
+    }
+}
 
 __device__ __forceinline__ void point_of(const PointSrc& S, int64_t p, float& x, float& y, float& z) {
     if (S.xyz) {
@@ -245,6 +298,7 @@ __device__ __forceinline__ void relu_pack32(uint32_t taddr, const float* bias, u
 // Forward.  Per tile: encode -> MMA (layer 1, bias folded) -> ReLU/BF16 ->
 // MMA (layer 2) -> + b2, ReLU/BF16 -> MMA (64 -> 1 as N = 16 with w3 in row
 // 0 of the B tile) -> + b3, softplus.
+template <bool kEnc>  // kEnc: the rows come encoded (S.enc)
 __global__ void __launch_bounds__(kThreads) k_mlp_forward(int64_t n, PointSrc S, const float* __restrict__ P,
                                                           const uint16_t* __restrict__ Wb,
                                                           float* __restrict__ sigma) {
@@ -286,7 +340,11 @@ __global__ void __launch_bounds__(kThreads) k_mlp_forward(int64_t n, PointSrc S,
         const int64_t p = tile * kTile + t;
         {
             float v[64];
-            if (p < n) {
+            if (kEnc && p < n) {  // the padding columns 51 and 52 carry the folded bias
+                load_enc_row(S.enc, p, v);
+                v[51] = 1.0f;
+                v[52] = 1.0f;
+            } else if (p < n) {
                 float x, y, z;
                 point_of(S, p, x, y, z);
                 encode_point(x, y, z, v, 1.0f);
@@ -339,15 +397,18 @@ constexpr uint32_t tE = 24576;                              // 128 x 64: e, late
 constexpr uint32_t tET = tE + kTileBytes;                   // 64 x 128: e^T
 constexpr uint32_t tH1 = tET + kTileBytes;                  // 128 x 64: h1
 constexpr uint32_t tH1T = tH1 + kTileBytes;                 // 64 x 128: h1^T
-constexpr uint32_t tD2 = tH1T + kTileBytes;                 // 128 x 64: delta2, later delta1
-constexpr uint32_t tD2T = tD2 + kTileBytes;                 // 64 x 128: delta2^T
-constexpr uint32_t tD1T = tD2T + kTileBytes;                // 64 x 128: delta1^T
-constexpr uint32_t kTrainSmem = tD1T + kTileBytes + 1024;   // + alignment slack
+constexpr uint32_t tD2 = tH1T + kTileBytes;                 // 128 x 64: delta2, later delta1 (heads)
+constexpr uint32_t tD2T = tD2 + kTileBytes;                 // 64 x 128: delta2^T (heads)
+constexpr uint32_t tD1T = tD2T + kTileBytes;                // 64 x 128: delta1^T (heads)
+constexpr uint32_t tD2L = tD1T + kTileBytes;                // the same three for the tails
+constexpr uint32_t tD2LT = tD2L + kTileBytes;
+constexpr uint32_t tD1LT = tD2LT + kTileBytes;
+constexpr uint32_t kTrainSmem = tD1LT + kTileBytes + 1024;  // + alignment slack
 
 __global__ void __launch_bounds__(kThreads, 1)
-    k_mlp_train(int64_t n, const float* __restrict__ xyz, const float* __restrict__ target,
-                const float* __restrict__ P, const uint16_t* __restrict__ Wb, float* __restrict__ G,
-                float* __restrict__ loss_sum, float two_over_n) {
+    k_mlp_train(int64_t n, const float* __restrict__ xyz, const uint16_t* __restrict__ enc,
+                const float* __restrict__ target, const float* __restrict__ P, const uint16_t* __restrict__ Wb,
+                float* __restrict__ G, float* __restrict__ loss_sum, float two_over_n) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = align1024(smem_raw);
     __shared__ float sB1[64], sB2[64], sW3[64], sD3[kTile];
@@ -377,8 +438,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tm = tbase, row = tm + ((uint32_t)(warp * 32) << 16);
     const uint32_t id128 = tc::idesc_bf16_f32(128, 64), id64 = tc::idesc_bf16_f32(64, 64);
     const uint64_t dE = tc::sw128_desc(smem_u32(base + tE)), dH1 = tc::sw128_desc(smem_u32(base + tH1)),
-                   dD2 = tc::sw128_desc(smem_u32(base + tD2)), dW1 = tc::sw128_desc(smem_u32(base + tW1)),
-                   dW2 = tc::sw128_desc(smem_u32(base + tW2)), dW2T = tc::sw128_desc(smem_u32(base + tW2T));
+                   dD2 = tc::sw128_desc(smem_u32(base + tD2)), dD2L = tc::sw128_desc(smem_u32(base + tD2L)),
+                   dW1 = tc::sw128_desc(smem_u32(base + tW1)), dW2 = tc::sw128_desc(smem_u32(base + tW2)),
+                   dW2T = tc::sw128_desc(smem_u32(base + tW2T));
     const int j = t & 63, half = t >> 6;  // column-sum role: unit j over points [64 half, 64 half + 64)
     float acc_w3 = 0.0f, acc_b2 = 0.0f, acc_b1 = 0.0f, acc_b3 = 0.0f, acc_loss = 0.0f;
     uint32_t phase = 0;
@@ -388,7 +450,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int64_t p = tile * kTile + t;
         const bool valid = p < n;
         float v[64], h[64];
-        if (valid)
+        if (valid && enc)
+            load_enc_row(enc, p, v);
+        else if (valid)
             encode_point(xyz[3 * p], xyz[3 * p + 1], xyz[3 * p + 2], v);
         else
 #pragma unroll
@@ -432,18 +496,21 @@ __global__ void __launch_bounds__(kThreads, 1)
         store_row(base + tE, t, h);  // h2 (e's tile is free: layer 1 has completed)
 #pragma unroll
         for (int i = 0; i < 64; ++i) v[i] = h[i] > 0.0f ? d3 * sW3[i] : 0.0f;  // delta2
-        store_row(base + tD2, t, v);
-        store_col(base + tD2T, t, v);
+        store_row_split(base + tD2, base + tD2L, t, v);
+        store_col_split(base + tD2T, base + tD2LT, t, v);
         sync_for_mma();
         if (t == 0) {
-            // delta1 before the mask: delta2 W2  (B = W2^T, K-major over layer-2 units)
+            // delta1 before the mask: delta2 W2  (B = W2^T, K-major over layer-2 units), heads then tails
 #pragma unroll
             for (int ks = 0; ks < 4; ++ks) tc::mma_bf16(tm + 64, dD2 + 2 * ks, dW2T + 2 * ks, id128, ks > 0);
-            // dW2 += delta2^T h1 over the tile's 128 points (M = 64 units, K = points)
 #pragma unroll
-            for (int ks = 0; ks < 8; ++ks) {
-                const uint32_t sub = (uint32_t)(ks >> 2) * kWBytes;
-                tc::mma_bf16(tm + 128, tc::sw128_desc(smem_u32(base + tD2T + sub)) + 2 * (ks & 3),
+            for (int ks = 0; ks < 4; ++ks) tc::mma_bf16(tm + 64, dD2L + 2 * ks, dW2T + 2 * ks, id128, true);
+            // dW2 += delta2^T h1 over the tile's 128 points (M = 64 units, K = points), heads and tails
+#pragma unroll
+            for (int ks = 0; ks < 16; ++ks) {
+                const uint32_t sub = (uint32_t)((ks >> 2) & 1) * kWBytes;
+                const uint32_t dt = ks < 8 ? tD2T : tD2LT;
+                tc::mma_bf16(tm + 128, tc::sw128_desc(smem_u32(base + dt + sub)) + 2 * (ks & 3),
                              tc::sw128_desc(smem_u32(base + tH1T + sub)) + 2 * (ks & 3), id64, !first || ks > 0);
             }
             tc::mma_commit(&bar);
@@ -451,7 +518,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // column sums while the tensor cores work: dw3_j = sum delta3 h2_j, db2_j = sum delta2_j
         for (int q = 64 * half; q < 64 * half + 64; ++q) {
             acc_w3 = fmaf(sD3[q], load_elem(base + tE, q, j), acc_w3);
-            acc_b2 += load_elem(base + tD2, q, j);
+            acc_b2 += load_elem(base + tD2, q, j) + load_elem(base + tD2L, q, j);
         }
         if (!(ok = wait_mma(&bar, phase))) break;
         tmem_row64(row + 64, v);
@@ -459,19 +526,21 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int i = 0; i < 64; ++i) v[i] = load_elem(h1row, t, i) > 0.0f ? v[i] : 0.0f;  // delta1
         __syncthreads();  // every column-sum read of delta2 is done before delta1 overwrites it
-        store_row(base + tD2, t, v);
-        store_col(base + tD1T, t, v);
+        store_row_split(base + tD2, base + tD2L, t, v);
+        store_col_split(base + tD1T, base + tD1LT, t, v);
         sync_for_mma();
-        if (t == 0) {  // dW1 += delta1^T e
+        if (t == 0) {  // dW1 += delta1^T e, heads and tails
 #pragma unroll
-            for (int ks = 0; ks < 8; ++ks) {
-                const uint32_t sub = (uint32_t)(ks >> 2) * kWBytes;
-                tc::mma_bf16(tm + 192, tc::sw128_desc(smem_u32(base + tD1T + sub)) + 2 * (ks & 3),
+            for (int ks = 0; ks < 16; ++ks) {
+                const uint32_t sub = (uint32_t)((ks >> 2) & 1) * kWBytes;
+                const uint32_t dt = ks < 8 ? tD1T : tD1LT;
+                tc::mma_bf16(tm + 192, tc::sw128_desc(smem_u32(base + dt + sub)) + 2 * (ks & 3),
                              tc::sw128_desc(smem_u32(base + tET + sub)) + 2 * (ks & 3), id64, !first || ks > 0);
             }
             tc::mma_commit(&bar);
         }
-        for (int q = 64 * half; q < 64 * half + 64; ++q) acc_b1 += load_elem(base + tD2, q, j);
+        for (int q = 64 * half; q < 64 * half + 64; ++q)
+            acc_b1 += load_elem(base + tD2, q, j) + load_elem(base + tD2L, q, j);
         if (!(ok = wait_mma(&bar, phase))) break;
         first = false;
     }
@@ -609,14 +678,15 @@ namespace {
 int launch_forward(int64_t n, const PointSrc& S, const float* params, const uint16_t* weights, float* sigma,
                    cudaStream_t st) {
     const size_t shm = 2 * kWBytes + kTileBytes + kW3Bytes + 1024;
-    NACC_CUDA_TRY(cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-    NACC_CUDA_TRY(cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributePreferredSharedMemoryCarveout,
+    const auto kern = S.enc ? k_mlp_forward<true> : k_mlp_forward<false>;
+    NACC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    NACC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                        (int)cudaSharedmemCarveoutMaxShared));
     const int64_t tiles = (n + kTile - 1) / kTile;
     // at most 8 CTAs of 64 tensor-memory columns share an SM's 512 columns
-    const int grid = persistent_ctas((const void*)k_mlp_forward, kThreads, shm, tiles, 8);
+    const int grid = persistent_ctas((const void*)kern, kThreads, shm, tiles, 8);
     if (grid == 0) return NACC_ERR_CUDA;
-    k_mlp_forward<<<grid, kThreads, shm, st>>>(n, S, params, weights, sigma);
+    kern<<<grid, kThreads, shm, st>>>(n, S, params, weights, sigma);
     NACC_LAUNCH_CHECK();
     return NACC_OK;
 }
@@ -660,21 +730,52 @@ extern "C" int nacc_mlp_forward(int64_t n, const float* xyz, const float* params
     return launch_forward(n, S, params, weights, sigma, as_stream(stream));
 }
 
+namespace nacc {
+namespace {
+int launch_train(int64_t n, const float* xyz, const uint16_t* enc, const float* target, const float* params,
+                 const uint16_t* weights, float* grads, float* loss_sum, cudaStream_t st) {
+    NACC_CUDA_TRY(
+        cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrainSmem));
+    const int64_t tiles = (n + kTile - 1) / kTile;
+    // one CTA per SM (256 tensor-memory columns each, 138 KiB of shared memory)
+    const int grid = (int)min64((int64_t)sm_count(), tiles);
+    k_mlp_train<<<grid, kThreads, kTrainSmem, st>>>(n, xyz, enc, target, params, weights, grads, loss_sum,
+                                                    (float)(2.0 / (double)n));
+    NACC_LAUNCH_CHECK();
+    return NACC_OK;
+}
+}  // namespace
+}  // namespace nacc
+
 extern "C" int nacc_mlp_train_grads(int64_t n, const float* xyz, const float* target, const float* params,
                                     const uint16_t* weights, float* grads, float* loss_sum, void* stream) {
     clear_error();
     NACC_CHECK_ARG(n >= 0 && n < (int64_t(1) << 40), "n=%lld out of range", (long long)n);
     if (n == 0) return NACC_OK;
     NACC_CHECK_ARG(xyz && target && params && weights && grads && loss_sum, "a pointer argument is NULL");
-    NACC_CUDA_TRY(
-        cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrainSmem));
-    const int64_t tiles = (n + kTile - 1) / kTile;
-    // one CTA per SM (256 tensor-memory columns each, 138 KiB of shared memory)
-    const int grid = (int)min64((int64_t)sm_count(), tiles);
-    k_mlp_train<<<grid, kThreads, kTrainSmem, as_stream(stream)>>>(n, xyz, target, params, weights, grads,
-                                                                   loss_sum, (float)(2.0 / (double)n));
-    NACC_LAUNCH_CHECK();
-    return NACC_OK;
+    return launch_train(n, xyz, nullptr, target, params, weights, grads, loss_sum, as_stream(stream));
+}
+
+extern "C" int nacc_mlp_forward_encoded(int64_t n, const uint16_t* enc, const float* params,
+                                        const uint16_t* weights, float* sigma, void* stream) {
+    clear_error();
+    NACC_CHECK_ARG(n >= 0 && n < (int64_t(1) << 40), "n=%lld out of range", (long long)n);
+    if (n == 0) return NACC_OK;
+    NACC_CHECK_ARG(enc && params && weights && sigma, "a pointer argument is NULL");
+    NACC_CHECK_ARG((reinterpret_cast<uintptr_t>(enc) & 15) == 0, "enc must be 16-byte aligned");
+    PointSrc S{nullptr, nullptr, nullptr, nullptr, 1, 0, 1, enc};
+    return launch_forward(n, S, params, weights, sigma, as_stream(stream));
+}
+
+extern "C" int nacc_mlp_train_grads_encoded(int64_t n, const uint16_t* enc, const float* target,
+                                            const float* params, const uint16_t* weights, float* grads,
+                                            float* loss_sum, void* stream) {
+    clear_error();
+    NACC_CHECK_ARG(n >= 0 && n < (int64_t(1) << 40), "n=%lld out of range", (long long)n);
+    if (n == 0) return NACC_OK;
+    NACC_CHECK_ARG(enc && target && params && weights && grads && loss_sum, "a pointer argument is NULL");
+    NACC_CHECK_ARG((reinterpret_cast<uintptr_t>(enc) & 15) == 0, "enc must be 16-byte aligned");
+    return launch_train(n, nullptr, enc, target, params, weights, grads, loss_sum, as_stream(stream));
 }
 
 extern "C" int nacc_mlp_adam(float* params, float* grads, float* m, float* v, int64_t step, float lr, float beta1,

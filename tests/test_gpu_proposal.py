@@ -70,22 +70,114 @@ def test_forward_matches_oracle(nacc, P, n):
     assert np.median(rel) < 1e-4 and np.mean(rel) < 2e-3 and rel.max() < 3e-2, (np.median(rel), rel.mean(), rel.max())
 
 
-def test_train_gradients_match_oracle(nacc, P):
-    p = _params(P, 93)
-    n = 5000
-    x = _points(n, 94)
-    t = workloads.rng(95).uniform(0.0, 3.0, n).astype(np.float32)
+U32 = 2.0 ** -24  # FP32 unit roundoff
+
+
+def _bf16_bits(a):
+    """float64 values that are BF16 numbers -> their 16-bit patterns (int16)."""
+    f = np.ascontiguousarray(np.asarray(a, np.float64).astype(np.float32))
+    return (f.view(np.uint32) >> 16).astype(np.uint16).view(np.int16)
+
+
+def _exact_case(P, n, seed):
+    """Encoded rows and parameters on dyadic grids that make layers 1 and 2
+    exact in FP32 whatever the order of the sums (every partial sum is a
+    multiple of 2^-16 or 2^-20 below 2^8 or 2^4: at most 24 bits), so the GPU
+    and the oracle take every BF16 rounding and ReLU decision of the hidden
+    layers on the same values: rows k/256 in [-1, 1] (columns 51..63 zero,
+    the encoding's padding), W1 in multiples of 2^-8 within 1/32, b1 in
+    multiples of 2^-16 within 1/2 (hi + lo BF16 is then b1 itself), W2 in
+    {-1/16, 0, 1/16}, b2 in multiples of 2^-20 within 1/2; w3, b3 and the
+    targets unconstrained (no rounding decision follows them)."""
+    g = workloads.rng(seed)
+    enc = np.zeros((n, 64))
+    enc[:, :51] = g.integers(-256, 257, (n, 51)) / 256.0
+    p = {"W1": np.zeros((64, 64), np.float32)}
+    p["W1"][:, :51] = g.integers(-8, 9, (64, 51)) / 256.0
+    p["b1"] = (g.integers(-2 ** 15, 2 ** 15, 64) / 2.0 ** 16).astype(np.float32)
+    p["W2"] = (g.integers(-1, 2, (64, 64)) / 16.0).astype(np.float32)
+    p["b2"] = (g.integers(-2 ** 19, 2 ** 19, 64) / 2.0 ** 20).astype(np.float32)
+    p["w3"] = P.bf16(g.standard_normal(64) * 0.3).astype(np.float32)
+    p["b3"] = np.array([0.3], np.float32)
+    t = g.uniform(0.0, 3.0, n).astype(np.float32)
+    f = P.forward(p, None, enc=enc)
+    for z in (f["z1"], f["z2"]):  # the sums are FP32 numbers: exact in FP32
+        assert np.array_equal(z.astype(np.float32).astype(np.float64), z)
+    assert 0.2 < (f["z1"] > 0).mean() < 0.8 and 0.2 < (f["z2"] > 0).mean() < 0.8  # the ReLUs bind both ways
+    return p, enc, t, f
+
+
+def test_forward_encoded_elementwise(nacc, P):
+    """The forward on identical BF16 layer-1 inputs whose hidden layers are
+    exact (_exact_case): every density within the FP32 error of the last
+    layer's sum (64 products and b3, at most 2u per addition) through
+    softplus, and 16 ulp of softplus itself."""
+    p, enc, _, f = _exact_case(P, 3000, 101)
     mlp = nacc.ProposalMLP(torch.as_tensor(_flat(p), device=DEV))
-    mlp.accumulate_grads(torch.as_tensor(x, device=DEV), torch.as_tensor(t, device=DEV))
+    got = mlp.forward_encoded(torch.as_tensor(_bf16_bits(enc), device=DEV)).cpu().numpy().astype(np.float64)
+    w3 = P.bf16(p["w3"])
+    d3 = 160 * U32 * (np.abs(f["h2"]) @ np.abs(w3) + abs(float(p["b3"][0])))
+    sig = 1.0 / (1.0 + np.exp(-f["z3"]))
+    tol = sig * d3 * 1.1 + 16 * U32 * np.abs(f["sigma"]) + 1e-30
+    err = np.abs(got - f["sigma"])
+    assert np.all(err <= tol), (int((err > tol).sum()), float(np.max(err / tol)))
+    assert np.median(err) < 1e-6 * np.median(f["sigma"])
+
+
+def test_train_gradients_match_oracle(nacc, P):
+    """The fused adjoint on identical BF16 layer-1 inputs whose hidden layers
+    are exact (_exact_case): the loss and all 8,385 gradient entries element
+    by element.  Each entry's
+    bound is the FP32 error of its computation on the GPU: the FP32 output
+    error d3 of every point (its sum of 64 products, softplus and logistic)
+    carried through the adjoint by absolute values, the error terms' split
+    into two BF16 parts (2^-18 relative), and 2 (n + 32) u times the sum of
+    the absolute terms of every accumulation over the batch (2u per
+    addition: tensor-core accumulation need not round to nearest)."""
+    n = 1024
+    p, enc, t, f = _exact_case(P, n, 93)
+    mlp = nacc.ProposalMLP(torch.as_tensor(_flat(p), device=DEV))
+    mlp.accumulate_grads_encoded(torch.as_tensor(_bf16_bits(enc), device=DEV), torch.as_tensor(t, device=DEV))
     got = _unflat(mlp.grads.cpu().numpy())
-    loss = mlp.loss_sum.item() / n
-    L, exp = P.loss_and_grads(p, x, t)
-    assert loss == pytest.approx(L, rel=2e-3)
+    loss = mlp.loss_sum.item()
+    L, exp = P.loss_and_grads(p, None, t, enc=enc)
+    W2, w3 = P.bf16(p["W2"]), P.bf16(p["w3"])
+    t64 = t.astype(np.float64)
+    z3, sp = f["z3"], f["sigma"]
+    sig = 1.0 / (1.0 + np.exp(-z3))
+    dz3 = 160 * U32 * (np.abs(f["h2"]) @ np.abs(w3) + abs(float(p["b3"][0])))
+    d3 = (2.0 / n) * (sp - t64) * sig
+    # FP32 error of d3 per point: z3's sum through softplus and the logistic, their own rounding
+    e_sp = sig * dz3 + 16 * U32 * (np.abs(sp) + np.abs(t64))
+    e_sig = sig * (1 - sig) * dz3 + 16 * U32 * sig
+    e_d3 = (2.0 / n) * (e_sp * sig + np.abs(sp - t64) * e_sig) + 8 * U32 * np.abs(d3)
+    m2 = (f["z2"] > 0).astype(np.float64)
+    m1 = (f["z1"] > 0).astype(np.float64)
+    D2 = d3[:, None] * w3[None, :] * m2
+    e_D2 = (e_d3[:, None] * np.abs(w3)[None, :] + (2.0 ** -18 + 2 * U32) * np.abs(D2)) * m2
+    D1 = (D2 @ W2) * m1
+    e_D1 = (e_D2 @ np.abs(W2) + 160 * U32 * (np.abs(D2) @ np.abs(W2))) * m1 + 2.0 ** -18 * np.abs(D1)
+    acc = 2 * (n + 32) * U32  # accumulations: at most 2u per addition (the tensor cores may truncate)
+    tol = {
+        "b3": np.array([e_d3.sum() + acc * np.abs(d3).sum()]),
+        "w3": e_d3 @ np.abs(f["h2"]) + acc * (np.abs(d3) @ np.abs(f["h2"])),
+        "b2": e_D2.sum(0) + acc * np.abs(D2).sum(0),
+        "W2": e_D2.T @ np.abs(f["h1"]) + acc * (np.abs(D2).T @ np.abs(f["h1"])),
+        "b1": e_D1.sum(0) + acc * np.abs(D1).sum(0),
+        "W1": e_D1.T @ np.abs(enc) + acc * (np.abs(D1).T @ np.abs(enc)),
+    }
+    n_checked = 0
     for k in exp:
-        e, g = np.asarray(exp[k]).reshape(-1), got[k].reshape(-1)
-        scale = np.abs(e).max()
-        cos = float(e @ g / (np.linalg.norm(e) * np.linalg.norm(g) + 1e-30))
-        assert cos > 0.999 and np.abs(g - e).max() < 3e-2 * scale, (k, cos, np.abs(g - e).max(), scale)
+        e, g, tk = (np.asarray(a, np.float64).reshape(-1) for a in (exp[k], got[k], tol[k]))
+        bad = np.abs(g - e) > tk * 1.05 + 1e-30
+        assert not bad.any(), (k, int(bad.sum()), float(np.max(np.abs(g - e) / (tk + 1e-30))))
+        n_checked += e.size
+    assert n_checked == 8385
+    # the loss: n squared differences, FP32
+    e_loss = np.sum(2 * np.abs(sp - t64) * e_sp) + acc * np.sum((sp - t64) ** 2)
+    assert abs(loss - L * n) <= e_loss * 1.05, (loss, L * n, e_loss)
+    # the comparison is not vacuous: gradients well above their bounds
+    assert np.median(np.abs(np.asarray(exp["W2"])).reshape(-1) / (tol["W2"].reshape(-1) + 1e-30)) > 10
 
 
 def test_adam_matches_oracle(nacc, P):
