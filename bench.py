@@ -78,6 +78,11 @@ def parse_args(argv=None):
     ap.add_argument("--unbounded-cams", type=int, default=16,
                     help="cameras of the unbounded-scene leg (16 = the 4,194,304-ray workload)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target oracle CPU time")
+    ap.add_argument("--profile", choices=["image", "training", "unbounded"], default=None,
+                    help="run only --warmup + --steps eager steps of one workload's training step (march, field, "
+                         "render fwd, L2 loss, render bwd; the training batch adds the grid update; the unbounded "
+                         "scene at K = 512) and print their mean time: the command the launch lists under "
+                         "profiles/ are taken on")
     return ap.parse_args(argv)
 
 
@@ -281,11 +286,12 @@ def cpu_baseline_unbounded(n_cams=16, target_seconds=5.0, res=64):
             "stage_s": pipe.stage_s}
 
 
-def training_step_measure(torch, nacc, dev, flush, steps=10):
+def training_step_measure(torch, nacc, dev, flush, hbm, peak_src, steps=10):
     """The training batch's whole step -- march (early stop) -> field ->
     render_fwd -> L2 -> render_bwd -> grid points -> field at the points ->
     grid update (EMA, threshold, bits) -- captured as one CUDA graph and
-    replayed; eager launches timed beside it.  262,144 rays, 64 blobs,
+    replayed; eager launches timed beside it, and once more with events at
+    the stage boundaries for the path roofline.  262,144 rays, 64 blobs,
     4 x 128^3 grid."""
     w = workloads.c3_training()
     g, m = w.grid, w.march
@@ -307,18 +313,30 @@ def training_step_measure(torch, nacc, dev, flush, steps=10):
     dens = torch.empty(grid.n_cells, device=dev)
     ck = nacc.render_ckpt_buffer(n, dev)
 
-    def step():
+    def staged(mark, count):
+        mark(0)
+        count(True)
         pk = nacc.march_grid(grid, o, d, m.step, m.max_steps, m.t_min, m.t_max, m.early_stop_eps, field=field,
                              buffers=bufs)
+        count(False)
+        mark(1)
         nacc.field_eval(field, o, d, pk, out=(sig, rgbs))
+        mark(2)
         rgb, _, _, _, _ = nacc.render_fwd(pk.offsets, pk.t_starts, pk.t_ends, sig, rgbs, w.bg, 0.0, ckpt=ck)
+        mark(3)
         loss, g_rgb = nacc.l2_loss(rgb, tgt)
+        mark(4)
         nacc.render_bwd(pk.offsets, pk.t_starts, pk.t_ends, sig, rgbs, g_rgb, None, None, w.bg, 0.0, out=(gsg, gcc),
                         ckpt=ck)
+        mark(5)
         nacc.grid_points(grid, seed=7, step=1, jitter=True, out=pts)
         nacc.field_points(field, pts, out=dens)
         nacc.update_grid(grid, dens, 0.95, 0.01, buffers=ubufs)
+        mark(6)
         return loss
+
+    def step():
+        return staged(lambda i: None, lambda on: None)
 
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
@@ -346,10 +364,15 @@ def training_step_measure(torch, nacc, dev, flush, steps=10):
         step()
     graph_ms = timed(gph.replay)
     S = bufs.packed.n_samples()
+    names = ["march", "field", "render_fwd", "loss", "render_bwd", "grid_update"]
+    stage_ms, staged_ms, count_ms, _ = staged_timing(torch, nacc._abi.load(), flush, staged, names, steps=steps)
     out = {"workload": w.name, "n_rays": n, "samples": S, "cells": grid.n_cells,
            "kernels_per_step": KERNELS_PER_STEP["march"] + 4 + 5,
            "graph": {"ms": graph_ms, "rays/s": n / (graph_ms / 1e3), "samples/s": S / (graph_ms / 1e3)},
-           "eager": {"ms": eager_ms, "rays/s": n / (eager_ms / 1e3)}}
+           "eager": {"ms": eager_ms, "rays/s": n / (eager_ms / 1e3)},
+           "stage_ms": stage_ms, "staged_step_ms": staged_ms,
+           "path_roofline": path_roofline(stage_ms, S, n, hbm, peak_src, count_ms, w.blobs.n,
+                                          alu_peak_tflops(torch, dev))}
     del gph, bufs, sig, rgbs, gsg, gcc, pts, dens
     torch.cuda.empty_cache()
     return out
@@ -430,6 +453,67 @@ def count_pass_flop(S: int, n_blobs: int) -> float:
     return float(S) * (11 * n_blobs + 14)
 
 
+def staged_timing(torch, lib, flush, run, names, steps=5, warmup=2):
+    """Mean time of each stage of `run` and of the whole call, with CUDA events
+    on the current stream (L2 flushed before each call, outside the events).
+    run(mark, count) executes one step: mark(i) records the event at stage
+    boundary i (0 .. len(names)); count(True/False) turns the library's
+    count-phase events of the marches on and off around a march call.
+    Returns ({name: ms}, total ms, count-phase ms, run's last result)."""
+    for _ in range(warmup):
+        run(lambda i: None, lambda on: None)
+    torch.cuda.synchronize()
+    recs, out = [], None
+    for _ in range(steps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
+        cev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        for e in cev:  # create the CUDA events behind the handles passed to the library
+            e.record()
+        flush.zero_()
+
+        def count(on, cev=cev):
+            if on:
+                lib.nacc_set_march_count_events(cev[0].cuda_event, cev[1].cuda_event)
+            else:
+                lib.nacc_set_march_count_events(None, None)
+
+        out = run(lambda i, ev=ev: ev[i].record(), count)
+        recs.append((ev, cev))
+    torch.cuda.synchronize()
+    k = len(recs)
+    stage = {nm: sum(ev[j].elapsed_time(ev[j + 1]) for ev, _ in recs) / k for j, nm in enumerate(names)}
+    total = sum(ev[0].elapsed_time(ev[-1]) for ev, _ in recs) / k
+    count_ms = sum(c[0].elapsed_time(c[1]) for _, c in recs) / k
+    return stage, total, count_ms, out
+
+
+def path_roofline(stage_ms, S, R, hbm, peak_src, count_ms=None, n_blobs=None, fp32_peak=None):
+    """The method's path (march + render_fwd + render_bwd): its algorithmic
+    bytes (BYTES per sample and per ray) over the sum of the three measured
+    stage times, against the HBM peak; with each stage's own fraction, the
+    DRAM traffic recorded by ncu for the three kernels (null when any record
+    is missing or stale), and, given the count phase's time, its FP32 work
+    (count_pass_flop) against the FP32 peak."""
+    nbytes = sum(BYTES[s][0] * S + BYTES[s][1] * R for s in BYTES)
+    ms = sum(stage_ms[s] for s in BYTES)
+    ach = nbytes / (ms / 1000.0) / 1e9
+    tr = [recorded_traffic(s, S, R) for s in BYTES]
+    out = {"bound": "hbm", "kernel": "march + render_fwd + render_bwd", "achieved": ach, "peak": hbm,
+           "unit": "GB/s", "frac": ach / hbm, "peak_source": peak_src, "ms": ms, "algorithmic_bytes": nbytes,
+           "samples": S, "rays": R, "bytes_per_sample": {s: BYTES[s][0] for s in BYTES},
+           "bytes_per_ray": {s: BYTES[s][1] for s in BYTES},
+           "traffic": None if any(t is None for t in tr) else float(sum(tr)),
+           "stages": {s: {"ms": stage_ms[s], "frac": (BYTES[s][0] * S + BYTES[s][1] * R) / (stage_ms[s] / 1e3) / 1e9
+                          / hbm} for s in BYTES}}
+    if count_ms is not None and count_ms > 0 and n_blobs is not None and fp32_peak:
+        fl = count_pass_flop(S, n_blobs)
+        out["count_phase"] = {"bound": "alu", "ms": count_ms, "algorithmic_flop": fl,
+                              "achieved": fl / (count_ms / 1e3) / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                              "frac": fl / (count_ms / 1e3) / 1e12 / fp32_peak,
+                              "peak_source": "derived: SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz"}
+    return out
+
+
 def aux_measure(torch, nacc, dev, flush, hbm, steps=10):
     """The path's other boundary calls at the C3 / C4 sizes, each timed alone
     with CUDA events (L2 flushed before each call): the jittered cell points
@@ -482,19 +566,67 @@ def aux_measure(torch, nacc, dev, flush, hbm, steps=10):
     }
 
 
-def proposal_measure(torch, nacc, dev, flush, steps=5, train_steps=1024, batch=65536, n_pairs=1 << 24,
+def weighted_points(torch, nacc, field, o, d, pk, bg, n_pts, gen):
+    """n_pts points drawn along the rays with probability proportional to the
+    rendering weights of a sample set (the grid path's): where the
+    transmittance drops, each point uniform inside its sample's interval."""
+    sig, rgbs = nacc.field_eval(field, o, d, pk)
+    wts = nacc.render_fwd(pk.offsets, pk.t_starts, pk.t_ends, sig, rgbs, bg, 0.0, want_weights=True)[4]
+    S = pk.n_samples()
+    cdf = torch.cumsum(wts[:S].double(), 0)
+    del sig, rgbs, wts
+    u = torch.rand(n_pts, generator=gen, device=o.device, dtype=torch.float64) * cdf[-1]
+    idx = torch.searchsorted(cdf, u).clamp_(max=S - 1)
+    del cdf, u
+    a = torch.rand(n_pts, generator=gen, device=o.device)
+    t = pk.t_starts[idx] + a * (pk.t_ends[idx] - pk.t_starts[idx])
+    ri = pk.ray_indices[idx].long()
+    return (o[ri] + d[ri] * t[:, None]).contiguous()
+
+
+def train_proposal(torch, mlp, x, target, steps, batch, lr0, gen, windows=16):
+    """Adam on (x, target) pairs, batches of a fresh permutation per epoch,
+    learning rate cosine-annealed from lr0 to 1e-5.  Returns the time and the
+    loss curve (mean batch MSE over `windows` equal stretches of the steps)."""
+    import math as _m
+    npairs = x.shape[0]
+    perm = torch.randperm(npairs, generator=gen, device=x.device)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    losses = []
+    a.record()
+    j = 0
+    for it in range(steps):
+        if j + batch > npairs:
+            perm = torch.randperm(npairs, generator=gen, device=x.device)
+            j = 0
+        idx = perm[j:j + batch]
+        j += batch
+        lr = 1e-5 + 0.5 * (lr0 - 1e-5) * (1.0 + _m.cos(_m.pi * it / steps))
+        losses.append(mlp.train_step(x[idx].contiguous(), target[idx].contiguous(), lr=lr))
+    b.record()
+    torch.cuda.synchronize()
+    L = torch.stack(losses).cpu().numpy()
+    win = max(1, steps // windows)
+    return a.elapsed_time(b), [float(L[i:i + win].mean()) for i in range(0, steps, win)]
+
+
+def proposal_measure(torch, nacc, dev, flush, steps=5, train_steps=4096, batch=65536, n_pairs=1 << 24,
                      sample_rays=2000):
     """The learned-proposal path and the combined path (grid range + proposal)
     beside the plain grid path on the 262,144-ray training batch (100
     cameras, 64-blob field).  The proposal network is
     first trained (timed, outside the step) on n_pairs (xyz, density) pairs
     drawn along the batch's rays -- uniform t in each ray's clip of the scene
-    box for half of them, in its occupied grid range for the other half --
-    with the density of the analytic field; train_steps Adam steps of batch
-    points.  Then each path renders the batch: grid = march with early stop
-    + field + render_fwd; proposal = two rounds (64 -> 32 -> 32 bins) + field
-    + render_fwd.  Returns rays/s of both, and their final transmittance on
-    a fixed sample of rays (the exact values come from the CPU leg)."""
+    box for a quarter of them, in its occupied grid range for another
+    quarter, by the grid path's rendering weights for the other half -- with
+    the density of the analytic field; train_steps Adam steps of batch
+    points, learning rate cosine-annealed.  Then each path runs the training step on the batch: sampling
+    (grid = march with early stop; proposal = two rounds, 64 -> 32 -> 32
+    bins; combined = the proposal rounds over the grid's occupied range),
+    field, checkpointed render forward, L2 loss against the batch's target,
+    checkpointed adjoint.  Returns rays/s of each, and their final
+    transmittance on a fixed sample of rays (the exact values come from the
+    CPU leg)."""
     w = workloads.c3_training()
     g, m = w.grid, w.march
     n = w.n_rays
@@ -507,58 +639,64 @@ def proposal_measure(torch, nacc, dev, flush, steps=5, train_steps=1024, batch=6
     # training pairs
     gen = torch.Generator(device=dev)
     gen.manual_seed(0x5EED + 4)
-    # half of the pairs along each ray's scene-box range (where the proposal
-    # path samples), half along its occupied grid range (where the combined
-    # path samples: the cascade reaches past the scene box)
+    # a quarter of the pairs along each ray's scene-box range (where the
+    # proposal path samples), a quarter along its occupied grid range (where
+    # the combined path samples: the cascade reaches past the scene box), half
+    # where the grid path's rendering weights are (where the transmittance
+    # drops)
     e1 = nacc.uniform_edges(box, o, d, 1, m.t_min, m.t_max)
     lo, hi = nacc.occupied_range(grid, o, d, m.step, m.max_steps, m.t_min, m.t_max)
-    ri = torch.randint(0, n, (n_pairs,), generator=gen, device=dev)
-    u = torch.rand(n_pairs, generator=gen, device=dev)
-    a0 = torch.where(torch.arange(n_pairs, device=dev) < n_pairs // 2, e1[ri, 0], lo[ri])
-    a1 = torch.where(torch.arange(n_pairs, device=dev) < n_pairs // 2, e1[ri, 1], hi[ri])
+    nu = n_pairs // 2
+    ri = torch.randint(0, n, (nu,), generator=gen, device=dev)
+    u = torch.rand(nu, generator=gen, device=dev)
+    first = torch.arange(nu, device=dev) < nu // 2
+    a0 = torch.where(first, e1[ri, 0], lo[ri])
+    a1 = torch.where(first, e1[ri, 1], hi[ri])
     t = a0 + u * (a1 - a0)
-    xyz = (o[ri] + d[ri] * t[:, None]).contiguous()
+    pk = nacc.march_grid(grid, o, d, m.step, m.max_steps, m.t_min, m.t_max, m.early_stop_eps, field=field)
+    xyz = torch.cat([(o[ri] + d[ri] * t[:, None]), weighted_points(torch, nacc, field, o, d, pk, w.bg,
+                                                                   n_pairs - nu, gen)]).contiguous()
+    del pk, ri, u, t, a0, a1, first
+    torch.cuda.empty_cache()
     sig = nacc.field_points(field, xyz)
     mlp = nacc.ProposalMLP.init(seed=11, device=dev)
-    perm = torch.randperm(n_pairs, generator=gen, device=dev)
+    train_ms, curve = train_proposal(torch, mlp, xyz, sig, train_steps, batch, 3e-3, gen)
+    target_var = float(sig.var())
+    del xyz, sig
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    losses = []
-    for it in range(train_steps):
-        j = (it * batch) % n_pairs
-        idx = perm[j:j + batch]
-        lr = 3e-3 if it < train_steps // 2 else 1e-3
-        losses.append(mlp.train_step(xyz[idx].contiguous(), sig[idx].contiguous(), lr=lr))
-    b.record()
-    torch.cuda.synchronize()
-    train_ms = a.elapsed_time(b)
-    loss_first, loss_last = float(losses[0].item()), float(torch.stack(losses[-16:]).mean().item())
-    del xyz, sig, ri, u, t, perm, a0, a1
 
     bufs = nacc.MarchBuffers(n, n * m.max_steps, dev)
     fs = torch.empty(n * m.max_steps, device=dev)
     fc = torch.empty((n * m.max_steps, 3), device=dev)
+    gfs, gfc = torch.empty_like(fs), torch.empty_like(fc)
     sampler = nacc.ProposalSampler(mlp, box, n, rounds=(64, 32), n_final=32, device=dev)
     combined = nacc.CombinedSampler(mlp, grid, n, m.step, m.max_steps, rounds=(64, 32), n_final=32, device=dev)
     ps = torch.empty(n * 32, device=dev)
     pc = torch.empty((n * 32, 3), device=dev)
     bg = w.bg
+    tgt = torch.as_tensor(w.target).to(dev)
+    ck = nacc.render_ckpt_buffer(n, dev)  # per-ray records from render_fwd for render_bwd
+
+    def tail(pk, sig, rgbs, gs, gc):
+        """field, checkpointed render forward, L2 loss, checkpointed adjoint;
+        returns the final transmittance."""
+        nacc.field_eval(field, o, d, pk, out=(sig, rgbs))
+        rgb, _, _, tr, _ = nacc.render_fwd(pk.offsets, pk.t_starts, pk.t_ends, sig, rgbs, bg, 0.0, ckpt=ck)
+        _, g_rgb = nacc.l2_loss(rgb, tgt)
+        nacc.render_bwd(pk.offsets, pk.t_starts, pk.t_ends, sig, rgbs, g_rgb, None, None, bg, 0.0, out=(gs, gc),
+                        ckpt=ck)
+        return tr
 
     def grid_path():
         pk = nacc.march_grid(grid, o, d, m.step, m.max_steps, m.t_min, m.t_max, m.early_stop_eps, field=field,
                              buffers=bufs)
-        nacc.field_eval(field, o, d, pk, out=(fs, fc))
-        return nacc.render_fwd(pk.offsets, pk.t_starts, pk.t_ends, fs, fc, bg, 0.0)[3]
+        return tail(pk, fs, fc, gfs, gfc)
 
     def prop_path():
-        pk = sampler.sample(o, d, m.t_min, m.t_max)
-        nacc.field_eval(field, o, d, pk, out=(ps, pc))
-        return nacc.render_fwd(pk.offsets, pk.t_starts, pk.t_ends, ps, pc, bg, 0.0)[3]
+        return tail(sampler.sample(o, d, m.t_min, m.t_max), ps, pc, gfs, gfc)
 
     def comb_path():
-        pk = combined.sample(o, d, m.t_min, m.t_max)
-        nacc.field_eval(field, o, d, pk, out=(ps, pc))
-        return nacc.render_fwd(pk.offsets, pk.t_starts, pk.t_ends, ps, pc, bg, 0.0)[3]
+        return tail(combined.sample(o, d, m.t_min, m.t_max), ps, pc, gfs, gfc)
 
     def timed(fn):
         for _ in range(2):
@@ -588,8 +726,7 @@ def proposal_measure(torch, nacc, dev, flush, steps=5, train_steps=1024, batch=6
 
         def gp():
             pk = nacc.march_grid(grid, o, d, st, ks, m.t_min, m.t_max, m.early_stop_eps, field=field, buffers=bufs)
-            nacc.field_eval(field, o, d, pk, out=(fs, fc))
-            return nacc.render_fwd(pk.offsets, pk.t_starts, pk.t_ends, fs, fc, bg, 0.0)[3]
+            return tail(pk, fs, fc, gfs, gfc)
 
         ms_, T_ = timed(gp)
         grid_sweep.append({"step": st, "max_steps": ks, "samples": bufs.packed.n_samples(), "ms": ms_,
@@ -601,9 +738,7 @@ def proposal_measure(torch, nacc, dev, flush, steps=5, train_steps=1024, batch=6
         pc2 = torch.empty((n * nf, 3), device=dev)
 
         def pp():
-            pk = smp.sample(o, d, m.t_min, m.t_max)
-            nacc.field_eval(field, o, d, pk, out=(ps2, pc2))
-            return nacc.render_fwd(pk.offsets, pk.t_starts, pk.t_ends, ps2, pc2, bg, 0.0)[3]
+            return tail(smp.sample(o, d, m.t_min, m.t_max), ps2, pc2, gfs, gfc)
 
         ms_, T_ = timed(pp)
         prop_sweep.append({"rounds": list(rounds), "final_samples_per_ray": nf, "ms": ms_, "rays/s": n / (ms_ / 1e3)})
@@ -620,7 +755,10 @@ def proposal_measure(torch, nacc, dev, flush, steps=5, train_steps=1024, batch=6
                           "rounds": [64, 32], "final_samples_per_ray": 32,
                           "initial_range": "first to last occupied lattice point of the grid"},
         "training": {"pairs": n_pairs, "steps": train_steps, "batch": batch, "ms": train_ms,
-                     "mse_first": loss_first, "mse_last": loss_last},
+                     "schedule": "Adam, lr cosine 3e-3 -> 1e-5", "loss_curve": curve,
+                     "mse_first": curve[0], "mse_last": curve[-1], "target_variance": target_var,
+                     "points": "1/4 uniform in the scene-box range, 1/4 in the occupied grid range, 1/2 "
+                               "by the grid path's rendering weights"},
         # the two paths integrate over different ranges (cascade vs scene box):
         # this difference includes the density outside the scene box
         "T_abs_diff_proposal_vs_grid": {"mean": float((T_prop - T_grid).abs().mean()),
@@ -680,19 +818,24 @@ def proposal_exact_error(prop):
     prop["equal_error"] = eq
 
 
-def unbounded_measure(torch, nacc, dev, flush, n_cams=16, steps=3, grid_K=(512, 1024, 2048),
-                      prop_cfg=(((64, 32), 32), ((128, 64), 64), ((256, 128), 128)), train_steps=2048,
+def unbounded_measure(torch, nacc, dev, flush, hbm, peak_src, n_cams=16, steps=3,
+                      grid_K=(128, 256, 512, 1024, 2048),
+                      prop_cfg=(((64, 32), 32), ((128, 64), 64), ((256, 128), 128)), train_steps=32768,
                       batch=65536, n_pairs=1 << 24, sample_rays=1500):
     """Unbounded scenes: 4,194,304 rays from 16 inward-facing 1024x256 cameras
     over 256 blobs spread across radius 20, space contracted into [-2, 2]^3.
-    Both estimators run the whole training step (sampling + field + render
-    fwd + L2 loss + render bwd):
+    Both estimators run the whole training step (sampling + field + the
+    checkpointed render fwd + L2 loss + the checkpointed render bwd), timed
+    whole and once more with events at the stage boundaries (grid
+    configurations also report the path roofline of march + render fwd +
+    bwd and the count phase's FP32 fraction):
       grid: the 4x256^3 grid over the contracted space (initialised from the
             field at the cell centres' scene points), the s-lattice march with
             early stop, at several lattice sizes K;
       proposal: the proposal network (trained first on (contracted point,
-            density) pairs uniform in s along the rays, timed outside the
-            step), rounds of inverse-CDF resampling from bins uniform in s, at
+            density) pairs, half uniform in s along the rays and half where
+            the grid path's rendering weights are, timed outside the step),
+            rounds of inverse-CDF resampling from bins uniform in s, at
             several bin counts.
     Each configuration's final transmittance on a fixed sample of rays is
     compared (CPU leg) with the exact line integral over [t_near, t_far]; the
@@ -728,12 +871,32 @@ def unbounded_measure(torch, nacc, dev, flush, n_cams=16, steps=3, grid_K=(512, 
             tot += a.elapsed_time(b)
         return tot / steps, out
 
-    def train_tail(pk, sig, rgbs, gs, gc):
+    ck = nacc.render_ckpt_buffer(n, dev)  # per-ray records from render_fwd for render_bwd
+    lib = nacc._abi.load()
+    fp32_peak = alu_peak_tflops(torch, dev)
+    names = ["sampling", "field", "render_fwd", "loss", "render_bwd"]
+
+    def train_step(sample, sig, rgbs, gs, gc, mark=lambda i: None, count=lambda on: None):
+        mark(0)
+        count(True)
+        pk = sample()
+        count(False)
+        mark(1)
         nacc.field_eval(field, o, d, pk, out=(sig, rgbs))
-        rgb, _, _, tr, _ = nacc.render_fwd(pk.offsets, pk.t_starts, pk.t_ends, sig, rgbs, w.bg, 0.0)
+        mark(2)
+        rgb, _, _, tr, _ = nacc.render_fwd(pk.offsets, pk.t_starts, pk.t_ends, sig, rgbs, w.bg, 0.0, ckpt=ck)
+        mark(3)
         _, g_rgb = nacc.l2_loss(rgb, tgt)
-        nacc.render_bwd(pk.offsets, pk.t_starts, pk.t_ends, sig, rgbs, g_rgb, None, None, w.bg, 0.0, out=(gs, gc))
+        mark(4)
+        nacc.render_bwd(pk.offsets, pk.t_starts, pk.t_ends, sig, rgbs, g_rgb, None, None, w.bg, 0.0, out=(gs, gc),
+                        ckpt=ck)
+        mark(5)
         return tr
+
+    def stages(sample, sig, rgbs, gs, gc):
+        st, tot, cnt, tr = staged_timing(torch, lib, flush, lambda mk, ct: train_step(sample, sig, rgbs, gs, gc, mk, ct),
+                                         names, steps=steps)
+        return st, tot, cnt, tr
 
     out = {"workload": w.name, "n_rays": n, "grid_spec": f"{w.grid.n_levels}x{w.grid.res}^3 over [-2,2]^3",
            "t_near": m.t_min, "t_far": m.t_max, "grid_init_ms": init_ms,
@@ -751,39 +914,41 @@ def unbounded_measure(torch, nacc, dev, flush, n_cams=16, steps=3, grid_K=(512, 
             return nacc.march_unbounded(grid, o, d, K, m.t_min, m.t_max, m.early_stop_eps, field=field,
                                         buffers=bufs)
 
-        ms, tr = timed(lambda: train_tail(march(), sig, rgbs, gs, gc))
+        ms, tr = timed(lambda: train_step(march, sig, rgbs, gs, gc))
         march_ms, _ = timed(march)
+        st, _, cnt, _ = stages(march, sig, rgbs, gs, gc)
+        st["march"] = st.pop("sampling")
         out["grid"].append({"K": K, "samples": S, "samples_per_ray": S / n, "step_ms": ms, "march_ms": march_ms,
-                            "rays/s": n / (ms / 1e3)})
+                            "rays/s": n / (ms / 1e3), "stage_ms": st,
+                            "path_roofline": path_roofline(st, S, n, hbm, peak_src, cnt, w.blobs.n, fp32_peak)})
         out["_T"][f"grid K={K}"] = tr.cpu().numpy()[sel]
         del bufs, sig, rgbs, gs, gc
         torch.cuda.empty_cache()
 
-    # training pairs: uniform s along random rays, density of the field there
+    # training pairs: half uniform in s along random rays, half by the
+    # rendering weights of the grid path at K = 1024 (where the transmittance
+    # drops); the density of the field there, the network at the contracted point
     gen = torch.Generator(device=dev)
     gen.manual_seed(0x5EED + 5)
-    ri = torch.randint(0, n, (n_pairs,), generator=gen, device=dev)
-    s = torch.rand(n_pairs, generator=gen, device=dev)
+    nu = n_pairs // 2
+    ri = torch.randint(0, n, (nu,), generator=gen, device=dev)
+    s = torch.rand(nu, generator=gen, device=dev)
     t = 1.0 / ((1.0 / m.t_min) * (1.0 - s) + (1.0 / m.t_max) * s)
-    x = (o[ri] + d[ri] * t[:, None]).contiguous()
+    pk = nacc.march_unbounded(grid, o, d, 1024, m.t_min, m.t_max, m.early_stop_eps, field=field)
+    x = torch.cat([o[ri] + d[ri] * t[:, None], weighted_points(torch, nacc, field, o, d, pk, w.bg, n_pairs - nu,
+                                                                gen)]).contiguous()
+    del pk, ri, s, t
+    torch.cuda.empty_cache()
     target = nacc.field_points(field, x)
     c = nacc.contract_points(x)
-    del x, ri, s, t
-    perm = torch.randperm(n_pairs, generator=gen, device=dev)
+    del x
     mlp = nacc.ProposalMLP.init(seed=12, device=dev)
-    losses = []
-    a.record()
-    for it in range(train_steps):
-        j = (it * batch) % n_pairs
-        idx = perm[j:j + batch]
-        losses.append(mlp.train_step(c[idx].contiguous(), target[idx].contiguous(),
-                                     lr=3e-3 if it < train_steps // 2 else 1e-3))
-    b.record()
-    torch.cuda.synchronize()
-    out["training"] = {"pairs": n_pairs, "steps": train_steps, "batch": batch, "ms": a.elapsed_time(b),
-                       "mse_first": float(losses[0].item()), "mse_last": float(torch.stack(losses[-16:]).mean()),
-                       "target_variance": float(target.var())}
-    del c, target, perm, losses
+    train_ms, curve = train_proposal(torch, mlp, c, target, train_steps, batch, 1e-2, gen)
+    out["training"] = {"pairs": n_pairs, "steps": train_steps, "batch": batch, "ms": train_ms,
+                       "schedule": "Adam, lr cosine 1e-2 -> 1e-5", "loss_curve": curve,
+                       "mse_first": curve[0], "mse_last": curve[-1], "target_variance": float(target.var()),
+                       "points": "1/2 uniform in s, 1/2 by the grid path's rendering weights (K = 1024)"}
+    del c, target
 
     for rounds, nf in prop_cfg:
         sampler = nacc.UnboundedProposalSampler(mlp, n, m.t_min, m.t_max, rounds=rounds, n_final=nf, device=dev)
@@ -791,11 +956,12 @@ def unbounded_measure(torch, nacc, dev, flush, n_cams=16, steps=3, grid_K=(512, 
         sig = torch.empty(S, device=dev)
         rgbs = torch.empty((S, 3), device=dev)
         gs, gc = torch.empty_like(sig), torch.empty_like(rgbs)
-        ms, tr = timed(lambda: train_tail(sampler.sample(o, d), sig, rgbs, gs, gc))
+        ms, tr = timed(lambda: train_step(lambda: sampler.sample(o, d), sig, rgbs, gs, gc))
         samp_ms, _ = timed(lambda: sampler.sample(o, d))
+        st, _, _, _ = stages(lambda: sampler.sample(o, d), sig, rgbs, gs, gc)
         name = f"proposal {list(rounds)}->{nf}"
         out["proposal"].append({"rounds": list(rounds), "final_samples_per_ray": nf, "samples": S, "step_ms": ms,
-                                "sampler_ms": samp_ms, "rays/s": n / (ms / 1e3)})
+                                "sampler_ms": samp_ms, "rays/s": n / (ms / 1e3), "stage_ms": st})
         out["_T"][name] = tr.cpu().numpy()[sel]
         # the same rounds driven by the exact density at the bin midpoints
         e = nacc.phi_edges(n, rounds[0], m.t_min, m.t_max, dev)
@@ -822,7 +988,7 @@ def unbounded_exact_error(unb):
     """CPU leg: the exact transmittance of the sampled rays over [t_near,
     t_far] (oracle closed form), each configuration's error against it, and
     the fastest configuration of each estimator within the error of the grid
-    at K = 1024."""
+    at K = 1024, and within the best error the proposal reaches."""
     from oracle import proposal as P
     s = unb.pop("_sample")
     Ts = unb.pop("_T")
@@ -838,15 +1004,20 @@ def unbounded_exact_error(unb):
         row["T_mean_abs_err"] = err[f"grid K={row['K']}"]["mean_abs"]
     for row in unb["proposal"]:
         row["T_mean_abs_err"] = err[f"proposal {row['rounds']}->{row['final_samples_per_ray']}"]["mean_abs"]
-    target = next((r["T_mean_abs_err"] for r in unb["grid"] if r["K"] == 1024), None)
-    eq = {"target_T_mean_abs_err": target}
-    for est in ("grid", "proposal"):
-        ok = [r for r in unb[est] if target is not None and r["T_mean_abs_err"] <= target * 1.0001]
-        best = max(ok, key=lambda r: r["rays/s"]) if ok else None
-        eq[est] = None if best is None else {"rays/s": best["rays/s"], "T_mean_abs_err": best["T_mean_abs_err"],
-                                             "config": {kk: best[kk] for kk in best if kk in ("K", "rounds",
-                                                        "final_samples_per_ray")}}
-    unb["equal_error"] = eq
+    def at_error(target):
+        eq = {"target_T_mean_abs_err": target}
+        for est in ("grid", "proposal"):
+            ok = [r for r in unb[est] if target is not None and r["T_mean_abs_err"] <= target * 1.0001]
+            best = max(ok, key=lambda r: r["rays/s"]) if ok else None
+            eq[est] = None if best is None else {"rays/s": best["rays/s"], "T_mean_abs_err": best["T_mean_abs_err"],
+                                                 "config": {kk: best[kk] for kk in best if kk in ("K", "rounds",
+                                                            "final_samples_per_ray")}}
+        return eq
+
+    # at the error of the grid at K = 1024, and at the proposal's best error
+    unb["equal_error"] = at_error(next((r["T_mean_abs_err"] for r in unb["grid"] if r["K"] == 1024), None))
+    if unb["proposal"]:
+        unb["equal_error_at_proposal_best"] = at_error(min(r["T_mean_abs_err"] for r in unb["proposal"]))
 
 
 def run_ours(args):
@@ -952,8 +1123,6 @@ def run_ours(args):
     hbm = peaks.get("hbm_gbs")
     peak_src = "measured" if hbm else "fallback"
     hbm = hbm or 6800.0
-    path_bytes = sum(BYTES[s][0] * S + BYTES[s][1] * n for s in BYTES)
-    path_ms = sum(stage_ms[s] for s in BYTES)
     # the dominant kernel of the method's path: the march count phase (ALU-bound,
     # timed alone through the library's event hook) or an HBM-bound render kernel
     fp32_peak = alu_peak_tflops(torch, dev)
@@ -972,12 +1141,10 @@ def run_ours(args):
         roofline = {"bound": "hbm", "kernel": "k_" + dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                     "frac": achieved / hbm, "ms": stage_ms[dom], "peak_source": peak_src,
                     "traffic": recorded_traffic(dom, S, n), "algorithmic_bytes": dom_bytes}
-    path_ach = path_bytes / (path_ms / 1000.0) / 1e9
-    # the target is stated for the whole path (march + render_fwd + render_bwd): report it next to the
-    # dominant kernel's figure so that the kernel fraction is not read as the path's
-    roofline["scope"] = "dominant kernel of the path; path_frac: march + render_fwd + render_bwd"
-    roofline["path_frac"] = path_ach / hbm
-    roofline["path_ms"] = path_ms
+    # the headline roofline is the whole path's (march + render_fwd + render_bwd), the quantity the
+    # target is stated for; the dominant kernel's own figure is reported beside it
+    path_roof = path_roofline(stage_ms, S, n, hbm, peak_src, count_ms, w.blobs.n, fp32_peak)
+    kernel_roof = roofline
     stage_roof = {}
     for s in BYTES:
         b = BYTES[s][0] * S + BYTES[s][1] * n
@@ -992,7 +1159,7 @@ def run_ours(args):
         legs = set(filter(None, args.aux_legs.split(",")))
         aux = aux_measure(torch, nacc, dev, flush, hbm) if "update" in legs else {}
         if "step" in legs:
-            aux["training_step"] = training_step_measure(torch, nacc, dev, flush)
+            aux["training_step"] = training_step_measure(torch, nacc, dev, flush, hbm, peak_src)
         if "proposal" in legs:
             aux["proposal"] = proposal_measure(torch, nacc, dev, flush)
             if args.no_cpu_baseline:
@@ -1000,7 +1167,7 @@ def run_ours(args):
             else:
                 proposal_exact_error(aux["proposal"])
         if "unbounded" in legs:
-            aux["unbounded"] = unbounded_measure(torch, nacc, dev, flush, n_cams=args.unbounded_cams)
+            aux["unbounded"] = unbounded_measure(torch, nacc, dev, flush, hbm, peak_src, n_cams=args.unbounded_cams)
             if args.no_cpu_baseline:
                 aux["unbounded"].pop("_sample")
                 aux["unbounded"].pop("_T")
@@ -1023,10 +1190,8 @@ def run_ours(args):
                        "parallelism": f"dp{world} (one view per GPU)"},
             "samples_per_s": samples_total / (ms / 1000.0),
             "stage_ms": stage_ms,
-            "roofline": roofline,
-            "path_roofline": {"bound": "hbm", "achieved": path_ach, "peak": hbm, "unit": "GB/s",
-                              "frac": path_ach / hbm, "stages": list(BYTES), "ms": path_ms,
-                              "algorithmic_bytes": path_bytes, "peak_source": peak_src},
+            "roofline": path_roof,
+            "kernel_roofline": kernel_roof,
             "stage_roofline": stage_roof,
             "aux": aux,
             "cpu_baseline": cpu,
@@ -1076,10 +1241,85 @@ def e2e_measure(args, torch, nacc, step, w, dev, n, flush, dist):
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": K}
 
 
+def profile_run(args):
+    """One workload's training step, eagerly, --warmup + --steps times (for an
+    ncu launch list: every launch of a step is one of the library's kernels or
+    the L2 loss's)."""
+    import torch
+    import paper_2305_04966_gb300 as nacc
+    nacc.load_library()
+    dev = torch.device("cuda", 0)
+    if args.profile == "unbounded":
+        w = workloads.c5_unbounded(n_cams=args.unbounded_cams)
+    elif args.profile == "training":
+        w = workloads.c3_training()
+    else:
+        w = workloads.c2_image(args.width, args.height)
+    g, m = w.grid, w.march
+    n = w.n_rays
+    field = nacc.BlobField.from_numpy(w.blobs, dev)
+    grid = nacc.OccupancyGrid.empty(g.aabb_min, g.aabb_max, g.res, g.n_levels, dev)
+    o = torch.as_tensor(w.rays_o).to(dev)
+    d = torch.as_tensor(w.rays_d).to(dev)
+    tgt = torch.as_tensor(w.target).to(dev)
+    if args.profile == "unbounded":
+        nacc.density_grid_unbounded(grid, field, 0.01)
+        K = 512
+        S = nacc.march_unbounded(grid, o, d, K, m.t_min, m.t_max, m.early_stop_eps, field=field).n_samples()
+        bufs = nacc.MarchBuffers(n, S, dev)
+
+        def march():
+            return nacc.march_unbounded(grid, o, d, K, m.t_min, m.t_max, m.early_stop_eps, field=field,
+                                        buffers=bufs)
+    else:
+        nacc.density_grid(grid, field, 0.01)
+        bufs = nacc.MarchBuffers(n, n * m.max_steps, dev)
+        S = n * m.max_steps
+
+        def march():
+            return nacc.march_grid(grid, o, d, m.step, m.max_steps, m.t_min, m.t_max, m.early_stop_eps,
+                                   field=field, buffers=bufs)
+    sig, rgbs = torch.empty(S, device=dev), torch.empty((S, 3), device=dev)
+    gs, gc = torch.empty_like(sig), torch.empty_like(rgbs)
+    ck = nacc.render_ckpt_buffer(n, dev)
+    if args.profile == "training":
+        ubufs = nacc.UpdateBuffers(grid.n_cells, dev)
+        pts = torch.empty((grid.n_cells, 3), device=dev)
+        dens = torch.empty(grid.n_cells, device=dev)
+
+    def step():
+        pk = march()
+        nacc.field_eval(field, o, d, pk, out=(sig, rgbs))
+        rgb = nacc.render_fwd(pk.offsets, pk.t_starts, pk.t_ends, sig, rgbs, w.bg, 0.0, ckpt=ck)[0]
+        _, g_rgb = nacc.l2_loss(rgb, tgt)
+        nacc.render_bwd(pk.offsets, pk.t_starts, pk.t_ends, sig, rgbs, g_rgb, None, None, w.bg, 0.0, out=(gs, gc),
+                        ckpt=ck)
+        if args.profile == "training":
+            nacc.grid_points(grid, seed=7, step=1, jitter=True, out=pts)
+            nacc.field_points(field, pts, out=dens)
+            nacc.update_grid(grid, dens, 0.95, 0.01, buffers=ubufs)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        step()
+    b.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": args.profile, "workload": w.name, "rays": n, "samples": bufs.packed.n_samples(),
+                      "ms_per_step": a.elapsed_time(b) / max(args.steps, 1), "steps": args.steps,
+                      "warmup": args.warmup}))
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile:
+        return profile_run(args)
     return run_ours(args)
 
 

@@ -284,9 +284,10 @@ int nacc_update_grid_sgd(const nacc_grid* grid, float* density, float* g_density
  *    message naming the limit.
  *  - The array (512 KiB + 24 B) is held by every GPU that loads the library,
  *    until the process exits.
- *  - The first call on each device looks up the array's device address for
- *    that device (with the device current); make that first call before any
- *    stream capture on that device.
+ *  - The first call in each CUDA context (per device, and again after a
+ *    device reset or a new primary context) looks up the array's device
+ *    address in that context; make that first call before any stream
+ *    capture in it.
  *  - All calls share the one array and it keeps the last call's contents;
  *    every element a call reads is written earlier in the same call.  Calls
  *    whose GPU work overlaps (e.g. on two streams) race on the array: order

@@ -85,12 +85,12 @@ int nacc_selftest_wait_timeout(int64_t limit_ns, void* stream);
 
 /*
  * Diagnostics (library plumbing): timing of the count phase of
- * nacc_march_grid (the run walk
- * and, with a field, the early-stop pass).  While set (by the calling host
- * thread), every nacc_march_grid call of that thread records `before` on its
- * stream just before the run-walk kernel and `after` just after the
- * early-stop kernel (or the walk, without a field), so the caller can read
- * their duration with cudaEventElapsedTime.
+ * nacc_march_grid and nacc_march_unbounded (the run walk and, with a field,
+ * the early-stop pass).  While set (by the calling host thread), every
+ * nacc_march_grid or nacc_march_unbounded call of that thread records
+ * `before` on its stream just before the run-walk kernel and `after` just
+ * after the early-stop kernels (or the walk, without a field), so the caller
+ * can read their duration with cudaEventElapsedTime.
  * before, after: cudaEvent_t handles created by the caller (NULL, NULL turns
  * the recording off).  The events are not owned by the library.
  */

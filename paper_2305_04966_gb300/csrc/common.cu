@@ -20,6 +20,10 @@ void set_error(const char* fmt, ...) {
 
 void clear_error() { g_err[0] = '\0'; }
 
+thread_local cudaEvent_t g_count_ev[2] = {nullptr, nullptr};
+
+cudaEvent_t* march_count_events() { return g_count_ev; }
+
 int sm_count() {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 1;

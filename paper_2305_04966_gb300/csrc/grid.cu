@@ -5,6 +5,8 @@
 // Three kernels: EMA + per-block FP64 partial sums, a one-block reduction to
 // the FP64 mean and threshold, and a warp-ballot bit packer (32 cells = one
 // word per warp).  No atomics: the mean is deterministic.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "nacc_internal.cuh"
@@ -359,7 +361,6 @@ namespace nacc {
 namespace {
 constexpr int64_t kNoAllocMaxCells = int64_t(1) << 27;             // 134,217,728 cells
 constexpr int64_t kNoAllocMaxBlocks = kNoAllocMaxCells / kEmaCells;  // 65,536 partial sums
-constexpr int kNoAllocMaxDevices = 64;
 }  // namespace
 }  // namespace nacc
 
@@ -368,11 +369,48 @@ static __device__ __align__(256) double nacc_update_noalloc_scratch[nacc::kNoAll
 
 namespace nacc {
 namespace {
+constexpr int kNoAllocMaxDevices = 64;
 std::mutex g_noalloc_mu;
-double* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+struct NoAllocEntry {
+    unsigned long long ctx_id;  // unique per context for the life of the process (never reused)
+    double* ptr;
+};
+NoAllocEntry g_noalloc[kNoAllocMaxDevices] = {};
 
-// Device address of the array on the current device, looked up once per
-// device (the host-side name of a __device__ variable is not a device address).
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+// Unique id of the current context (0 if the driver cannot say).  The two
+// driver calls are resolved through the runtime, so the library does not
+// link the driver library itself.
+unsigned long long current_ctx_id() {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
+// Device address of the array in the current context (the host-side name of
+// a __device__ variable is not a device address).  Cached per device together
+// with the id of the context it was taken in, and looked up again when that
+// context changes: after a device reset, or when the primary context is torn
+// down and created again, the module (and the array) can load at another
+// address.  Without a context id every call looks the address up.
 int noalloc_scratch(double** out) {
     int dev = 0;
     NACC_CUDA_TRY(cudaGetDevice(&dev));
@@ -380,18 +418,19 @@ int noalloc_scratch(double** out) {
         set_error("device %d is beyond the %d devices this entry point supports", dev, kNoAllocMaxDevices);
         return NACC_ERR_UNSUPPORTED;
     }
+    const unsigned long long id = current_ctx_id();
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
+    if (id == 0 || g_noalloc[dev].ctx_id != id || !g_noalloc[dev].ptr) {
         void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, nacc_update_noalloc_scratch);
+        const cudaError_t e = cudaGetSymbolAddress(&p, nacc_update_noalloc_scratch);
         if (e != cudaSuccess || p == nullptr) {
             set_error("cudaGetSymbolAddress(nacc_update_noalloc_scratch) failed on device %d: %s", dev,
                       cudaGetErrorString(e));
             return NACC_ERR_CUDA;
         }
-        g_noalloc_ptr[dev] = static_cast<double*>(p);
+        g_noalloc[dev] = NoAllocEntry{id, static_cast<double*>(p)};
     }
-    *out = g_noalloc_ptr[dev];
+    *out = g_noalloc[dev].ptr;
     return NACC_OK;
 }
 }  // namespace

@@ -1476,9 +1476,6 @@ int build_summaries(MarchArgs& A, void* mem, cudaStream_t st) {
     return NACC_OK;
 }
 
-// Caller-owned events recorded around the count phase (diagnostics).
-thread_local cudaEvent_t g_count_ev[2] = {nullptr, nullptr};
-
 }  // namespace
 }  // namespace nacc
 
@@ -1577,7 +1574,7 @@ extern "C" int nacc_march_grid(const nacc_grid* grid, const float* rays_o, const
         const int rc = build_summaries(A, sp, st);
         if (rc != NACC_OK) return rc;
     }
-    if (g_count_ev[0]) NACC_CUDA_TRY(cudaEventRecord(g_count_ev[0], st));
+    if (cudaEvent_t e = march_count_events()[0]) NACC_CUDA_TRY(cudaEventRecord(e, st));
     k_march_runs<<<(unsigned)((n_rays + kRunsThreads - 1) / kRunsThreads), kRunsThreads, 0, st>>>(
         A, counts, kstops, nruns, tnear, runs, bsums);
     NACC_LAUNCH_CHECK();
@@ -1608,7 +1605,7 @@ extern "C" int nacc_march_grid(const nacc_grid* grid, const float* rays_o, const
                                                                            queue, tickets + 1, tickets + 2);
         NACC_LAUNCH_CHECK();
     }
-    if (g_count_ev[1]) NACC_CUDA_TRY(cudaEventRecord(g_count_ev[1], st));
+    if (cudaEvent_t e = march_count_events()[1]) NACC_CUDA_TRY(cudaEventRecord(e, st));
     k_scan_block_sums<<<1, 1024, 0, st>>>(bsums, nb, out->offsets + n_rays, out->n_samples);
     NACC_LAUNCH_CHECK();
     k_march_fill<<<(unsigned)nb, kBlockThreads, 0, st>>>(A, counts, kstops, nruns, tnear, runs, bsums,
@@ -1688,7 +1685,7 @@ extern "C" int nacc_occupied_range(const nacc_grid* grid, const float* rays_o, c
 extern "C" int nacc_set_march_count_events(void* before, void* after) {
     clear_error();
     NACC_CHECK_ARG((before == nullptr) == (after == nullptr), "give both events or neither");
-    g_count_ev[0] = static_cast<cudaEvent_t>(before);
-    g_count_ev[1] = static_cast<cudaEvent_t>(after);
+    march_count_events()[0] = static_cast<cudaEvent_t>(before);
+    march_count_events()[1] = static_cast<cudaEvent_t>(after);
     return NACC_OK;
 }

@@ -1285,6 +1285,7 @@ extern "C" int nacc_march_unbounded(const nacc_grid* grid, const float* rays_o, 
     }
     // 32-bit cell indices when every index (and the all-ones "outside") fits
     const bool idx32 = (int64_t)A.g.n_levels * A.g.res * A.g.res * A.g.res < (int64_t(1) << 32) - 1;
+    if (cudaEvent_t e = march_count_events()[0]) NACC_CUDA_TRY(cudaEventRecord(e, st));
     if (idx32)
         k_unb_count<uint32_t><<<(unsigned)nb, kThreads, 0, st>>>(A, counts, kstops, nruns, runs, bsums);
     else
@@ -1323,6 +1324,7 @@ extern "C" int nacc_march_unbounded(const nacc_grid* grid, const float* rays_o, 
         }
         NACC_LAUNCH_CHECK();
     }
+    if (cudaEvent_t e = march_count_events()[1]) NACC_CUDA_TRY(cudaEventRecord(e, st));
     k_unb_scan<<<1, 1024, 0, st>>>(bsums, nb, out->offsets + n_rays, out->n_samples);
     NACC_LAUNCH_CHECK();
     k_unb_fill<<<(unsigned)nb, kThreads, 0, st>>>(A, counts, kstops, nruns, runs, bsums, out->n_samples,

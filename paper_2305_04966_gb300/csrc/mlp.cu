@@ -57,32 +57,53 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 }
 
 // e(x): [x, y, z, (sin, cos)(2^k pi x_a) for k = 0..7, a = 0..2], padded to 64
-// with `pad` (0; the forward kernel puts ones in columns 51 and 52, which
-// carry layer 1's bias).  sin(2^k pi x) = sin(2 pi f) with f the phase
-// 2^(k-1) x reduced exactly to [-1/2, 1/2] (power-of-two scaling and
-// u - rint(u) are exact in FP32); the hardware sine and cosine of 2 pi f
-// (|2 pi f| <= pi) then have an absolute error below 1e-6.
-__device__ __forceinline__ void encode_point(float x, float y, float z, float e[64], float pad51 = 0.0f) {
-    e[0] = x;
-    e[1] = y;
-    e[2] = z;
+// with `pad` in columns 51 and 52 (0; the forward kernel puts ones there,
+// which carry layer 1's bias) and zeros after.  Half H of the row (columns
+// 32H .. 32H+31) needs the bands k = 0..4 (H = 0) or 4..7 (H = 1).  The
+// even bands of each half are evaluated directly: sin(2^k pi x) = sin(2 pi f)
+// with f the phase 2^(k-1) x reduced exactly to [-1/2, 1/2] (power-of-two
+// scaling and u - rint(u) are exact in FP32), then the hardware sine and
+// cosine of 2 pi f (|2 pi f| <= pi: absolute error below 4.3e-7).  The odd
+// bands come from the band below by the double-angle identities sin 2a =
+// 2 sin a cos a, cos 2a = (cos a - sin a)(cos a + sin a), which at most
+// double that error and add a few roundings: below 1.3e-6 in every column.
+template <int H>
+__device__ __forceinline__ void encode_half(float x, float y, float z, float e[32], float pad = 0.0f) {
+    constexpr int k0 = H == 0 ? 0 : 4, k1 = H == 0 ? 4 : 7;
     const float c[3] = {x, y, z};
+    float sn[8][3], cs[8][3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
+    for (int k = k0; k <= k1; ++k) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const float u = c[a] * (0.5f * (float)(1 << k));
-            const float f = u - rintf(u);
-            float s, co;
-            __sincosf(6.28318531f * f, &s, &co);
-            e[3 + 6 * k + 2 * a] = s;
-            e[4 + 6 * k + 2 * a] = co;
+        for (int a = 0; a < 3; ++a) {
+            if (((k - k0) & 1) == 0) {
+                const float u = c[a] * (0.5f * (float)(1 << k));
+                const float f = u - rintf(u);
+                __sincosf(6.28318531f * f, &sn[k][a], &cs[k][a]);
+            } else {
+                const float s0 = sn[k - 1][a], c0 = cs[k - 1][a];
+                sn[k][a] = (s0 + s0) * c0;
+                cs[k][a] = (c0 - s0) * (c0 + s0);
+            }
         }
     }
-    e[51] = pad51;
-    e[52] = pad51;
 #pragma unroll
-    for (int i = 53; i < 64; ++i) e[i] = 0.0f;
+    for (int i = 0; i < 32; ++i) {
+        const int col = 32 * H + i;
+        if (col < 3) {
+            e[i] = c[col];
+        } else if (col < 51) {
+            const int q = col - 3, k = q / 6, a = (q % 6) / 2;
+            e[i] = (q & 1) ? cs[k][a] : sn[k][a];
+        } else {
+            e[i] = col < 53 ? pad : 0.0f;
+        }
+    }
+}
+
+__device__ __forceinline__ void encode_point(float x, float y, float z, float e[64], float pad51 = 0.0f) {
+    encode_half<0>(x, y, z, e, pad51);
+    encode_half<1>(x, y, z, e + 32, pad51);
 }
 
 // Two FP32 values -> BF16x2 (round to nearest even) with ReLU: lo in the low half.

@@ -19,6 +19,9 @@ namespace nacc {
 void set_error(const char* fmt, ...);
 void clear_error();
 int sm_count();  // multiprocessors of the current device (cached per device)
+// Caller-owned events that the marches record around their count phase on
+// the calling host thread (diagnostics; both null when off).
+cudaEvent_t* march_count_events();
 unsigned int mlp_take_status();  // reads and clears the proposal network's device status word
 
 #define NACC_CHECK_ARG(cond, ...)                      \

@@ -550,10 +550,13 @@ def test_initial_density_grid_matches_oracle(nacc, orc):
     assert ref.sum() > 10000
 
 
-@pytest.mark.parametrize("nb,no,strat", [(64, 32, False), (32, 32, False), (64, 32, True), (7, 100, False),
-                                         (300, 17, True), (1, 4, False)])
-def test_sample_pdf_bit_exact(nacc, orc, nb, no, strat):
-    n = 20000
+@pytest.mark.parametrize("nb,no,strat,n", [(64, 32, False, 20000), (32, 32, False, 20000), (64, 32, True, 20001),
+                                           (7, 100, False, 20000), (300, 17, True, 20000), (1, 4, False, 20000),
+                                           (4096, 4096, True, 300), (128, 64, False, 1), (33, 31, True, 20003)])
+def test_sample_pdf_bit_exact(nacc, orc, nb, no, strat, n):
+    """Every output bit-exact, including all-zero rows (uniform), single-bin
+    mass, CDFs that reach 1 before the last bin (a dominant weight followed
+    by ones too small to move the sum), and denormal weights."""
     g = workloads.rng(90 + nb)
     edges = np.sort(g.uniform(2.0, 6.0, (n, nb + 1)), axis=1).astype(np.float32)
     wts = g.uniform(0, 1, (n, nb)).astype(np.float32)
@@ -561,6 +564,10 @@ def test_sample_pdf_bit_exact(nacc, orc, nb, no, strat):
     wts[:50] = 0  # all-zero rows: uniform
     wts[50:60, :] = 0
     wts[50:60, nb // 2] = 1.0  # single-bin mass
+    if nb > 2 and n > 80:
+        wts[60:70, : nb // 3] = 1e8  # F_j = 1 well before the last bin
+        wts[60:70, nb // 3:] = 1e-3
+        wts[70:80] = np.float32(1e-41) * (wts[70:80] > 0)  # denormal weights
     got = nacc.sample_pdf(T(edges), T(wts), no, stratified=strat, seed=4242).cpu().numpy()
     exp = orc.sample_pdf(edges, wts, no, stratified=strat, seed=4242)
     np.testing.assert_array_equal(got, exp)

@@ -7,7 +7,8 @@ the same FP32 operations, so every output must be bit-identical to the plain
 pair's, which the parity tests hold against the oracle.  Covered: empty rays,
 short rays, rays across the record's 14-chunk limit (where the adjoint falls
 back to its own sweep), rays far beyond it, masked and unmasked rendering,
-and the full 800x800 image step that the benchmark times.
+the full 800x800 image step that the benchmark times, the proposal paths'
+short rays, and the unbounded scene's long rays.
 """
 import numpy as np
 import pytest
@@ -44,15 +45,16 @@ def _ragged():
     return workloads.random_packed(n, 67, lengths=lengths, sigma_hi=0.4)
 
 
-def _both(nacc, p, eps, grads):
-    off, t0, t1, sg, c = (T(p[k]) for k in ("offsets", "t_starts", "t_ends", "sigmas", "rgbs"))
+def _both(nacc, p, eps, grads, bg=(1.0, 0.5, 0.25)):
+    off, t0, t1, sg, c = (x if torch.is_tensor(x) else T(x)
+                          for x in (p[k] for k in ("offsets", "t_starts", "t_ends", "sigmas", "rgbs")))
     n = off.shape[0] - 1
     ck = nacc.render_ckpt_buffer(n, off.device)
-    plain = nacc.render_fwd(off, t0, t1, sg, c, (1.0, 0.5, 0.25), eps, want_weights=True)
-    chk = nacc.render_fwd(off, t0, t1, sg, c, (1.0, 0.5, 0.25), eps, want_weights=True, ckpt=ck)
+    plain = nacc.render_fwd(off, t0, t1, sg, c, bg, eps, want_weights=True)
+    chk = nacc.render_fwd(off, t0, t1, sg, c, bg, eps, want_weights=True, ckpt=ck)
     gC, gA, gD = grads
-    gp = nacc.render_bwd(off, t0, t1, sg, c, gC, gA, gD, (1.0, 0.5, 0.25), eps)
-    gk = nacc.render_bwd(off, t0, t1, sg, c, gC, gA, gD, (1.0, 0.5, 0.25), eps, ckpt=ck)
+    gp = nacc.render_bwd(off, t0, t1, sg, c, gC, gA, gD, bg, eps)
+    gk = nacc.render_bwd(off, t0, t1, sg, c, gC, gA, gD, bg, eps, ckpt=ck)
     torch.cuda.synchronize()
     return plain, chk, gp, gk, ck
 
@@ -177,3 +179,76 @@ def test_ckpt_pair_full_image_against_oracle(nacc, orc):
     bad = np.abs(gs - es) > tol
     assert not bad.any(), f"{bad.sum()} sigma gradients off; worst excess {np.max(np.abs(gs - es) - tol)}"
     np.testing.assert_allclose(gc, ec, rtol=1e-4, atol=1e-6)
+
+
+def _assert_pair_identical(nacc, o, d, field, pk, bg, eps, seed):
+    """Field at the samples, then the plain and the checkpointed pair on them
+    with seeded upstream gradients of colour, opacity and depth: every output
+    bit-identical.  Returns the per-ray sample counts."""
+    pk = pk.trimmed()
+    sig, rgbs = nacc.field_eval(field, o, d, pk)
+    n = pk.offsets.shape[0] - 1
+    g = workloads.rng(seed)
+    grads = (T(g.standard_normal((n, 3)).astype(np.float32)), T(g.standard_normal(n).astype(np.float32)),
+             T(g.standard_normal(n).astype(np.float32)))
+    plain, chk, gp, gk, _ = _both(nacc, dict(offsets=pk.offsets, t_starts=pk.t_starts, t_ends=pk.t_ends,
+                                             sigmas=sig, rgbs=rgbs), eps, grads, bg=bg)
+    for a, b, name in zip(plain, chk, ("rgb", "opacity", "depth", "trans", "weights")):
+        assert torch.equal(a, b), f"forward {name} differs with the checkpoint"
+    assert torch.equal(gp[0], gk[0]) and torch.equal(gp[1], gk[1])
+    return np.diff(pk.offsets.cpu().numpy())
+
+
+@pytest.mark.parametrize("eps", [0.0, 1e-4])
+def test_ckpt_pair_on_proposal_rays(nacc, eps):
+    """Short rays of the learned-proposal paths (32 and 128 final samples per
+    ray, scene-box bins and the grid's occupied range) on 32,768 rays of the
+    training batch with its 64-blob field."""
+    w = workloads.c3_training(32768)
+    g, m = w.grid, w.march
+    field = nacc.BlobField.from_numpy(w.blobs)
+    grid = nacc.OccupancyGrid.empty(g.aabb_min, g.aabb_max, g.res, g.n_levels)
+    nacc.density_grid(grid, field, 0.01)
+    box = nacc.OccupancyGrid.empty(g.aabb_min, g.aabb_max, 32, 1)
+    mlp = nacc.ProposalMLP.init(seed=11)
+    o, d = T(w.rays_o), T(w.rays_d)
+    n = w.n_rays
+    for rounds, nf in (((64, 32), 32), ((256, 128), 128)):
+        smp = nacc.ProposalSampler(mlp, box, n, rounds=rounds, n_final=nf)
+        lens = _assert_pair_identical(nacc, o, d, field, smp.sample(o, d, m.t_min, m.t_max), w.bg, eps, 92)
+        assert (lens == nf).all()
+    comb = nacc.CombinedSampler(mlp, grid, n, m.step, m.max_steps, rounds=(64, 32), n_final=32)
+    lens = _assert_pair_identical(nacc, o, d, field, comb.sample(o, d, m.t_min, m.t_max), w.bg, eps, 93)
+    assert set(np.unique(lens)) <= {0, 32}
+
+
+def test_ckpt_pair_on_unbounded_long_rays(nacc):
+    """One 1024x256 camera of the unbounded scene (256 blobs over radius 20,
+    4x256^3 grid over the contracted space): the s-lattice march at K = 2048
+    with the early stop on the grid from the field, and on a fully occupied
+    grid without it, whose 2048-sample rays run past the record's 14-chunk
+    limit (the adjoint's own sweep); and the unbounded proposal sampler's
+    128-sample rays."""
+    w = workloads.c5_unbounded(n_cams=1)
+    g, m = w.grid, w.march
+    field = nacc.BlobField.from_numpy(w.blobs)
+    grid = nacc.OccupancyGrid.empty(g.aabb_min, g.aabb_max, g.res, g.n_levels)
+    nacc.density_grid_unbounded(grid, field, 0.01)
+    o, d = T(w.rays_o), T(w.rays_d)
+    # the grid from the field, with the early stop, at K = 2048
+    pk = nacc.march_unbounded(grid, o, d, 2048, m.t_min, m.t_max, m.early_stop_eps, field=field)
+    lens = _assert_pair_identical(nacc, o, d, field, pk, w.bg, 0.0, 94)
+    assert (lens > 128).sum() > 1000  # several chunks
+    del pk
+    # every cell occupied, no early stop: all 2048 lattice points of every
+    # ray, 16 chunks, past the record's 14-chunk limit
+    full = nacc.OccupancyGrid.empty(g.aabb_min, g.aabb_max, g.res, g.n_levels)
+    full.bits.fill_(-1)
+    pk = nacc.march_unbounded(full, o, d, 2048, m.t_min, m.t_max, m.early_stop_eps)
+    lens = _assert_pair_identical(nacc, o, d, field, pk, w.bg, 1e-4, 96)
+    assert (lens == 2048).all()
+    del pk, full
+    mlp = nacc.ProposalMLP.init(seed=12)
+    smp = nacc.UnboundedProposalSampler(mlp, w.n_rays, m.t_min, m.t_max, rounds=(256, 128), n_final=128)
+    lens = _assert_pair_identical(nacc, o, d, field, smp.sample(o, d), w.bg, 1e-4, 95)
+    assert (lens == 128).all()

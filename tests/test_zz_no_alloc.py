@@ -51,6 +51,42 @@ def test_noalloc_update_matches_update_grid_on_consecutive_calls():
         assert 0 < int(workloads.unpack_bits(alt.bits.cpu().numpy().view(np.uint32)).sum()) < n
 
 
+def test_noalloc_update_at_its_limit():
+    """Exactly 2^27 cells (8 levels of 256^3): the 65,536 partial sums fill the
+    whole array and the (mean, threshold) words sit right after them.  EMA
+    and bits equal nacc_update_grid's on two consecutive calls."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2305_04966_gb300 as nacc
+    from paper_2305_04966_gb300 import _abi
+
+    lib = nacc.load_library()
+    res, L = 256, 8
+    n = L * res ** 3
+    assert n == 1 << 27
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(501)
+    ref = nacc.OccupancyGrid.empty((-1.5,) * 3, (1.5,) * 3, res, L)
+    alt = nacc.OccupancyGrid.empty((-1.5,) * 3, (1.5,) * 3, res, L)
+    ref.ema.copy_(-torch.log1p(-torch.rand(n, generator=gen, device="cuda") * 0.999))
+    alt.ema.copy_(ref.ema)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for call in range(2):
+        dens = torch.rand(n, generator=gen, device="cuda") * (torch.rand(n, generator=gen, device="cuda") < 0.3)
+        nacc.update_grid(ref, dens, decay=0.95, thresh_frac=0.01)
+        rc = lib.nacc_update_grid_noalloc(ctypes.byref(alt.c_struct()), _ptr(alt.ema), _ptr(dens),
+                                          0.95, 0.01, 0.0, _ptr(alt.bits), stream)
+        assert rc == _abi.NACC_OK, lib.nacc_last_error()
+        torch.cuda.synchronize()
+        assert torch.equal(alt.ema, ref.ema), f"EMA differs on call {call}"
+        assert torch.equal(alt.bits, ref.bits), f"occupancy bits differ on call {call}"
+        del dens
+    words = alt.bits.view(torch.int32)
+    assert bool((words != 0).any()) and bool((words != -1).any())  # some cells occupied, some not
+    del ref, alt
+    torch.cuda.empty_cache()
+
+
 def test_noalloc_update_rejects_grids_beyond_its_limit():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
