@@ -220,17 +220,19 @@ __device__ __forceinline__ float blob_interval(float ts, float sd, float ilen, f
 // the blobs left out (their whole weight).  Returns the number of kept blobs
 // (the table holds the first kStopTable).  onorm =
 // |o|, dnorm = |d|, cnt = the ray's samples, dinv and dt_max as in
-// blob_interval.
-__device__ int build_warp_table(const nacc_blob_field& f, const float4* sm, const float4* sk, const float o[3],
-                                const float d[3], float onorm, float dnorm, float dinv, float dt_max, int cnt,
-                                float4* tab, uint16_t* tidx, float& U, float& e_out, int lane) {
+// blob_interval.  The blobs visited are cand[0 .. n_cand) (ascending; NULL:
+// all blobs): any other blob must give S = 0 on this ray (group_candidates).
+__device__ int build_warp_table(const nacc_blob_field& f, const float4* sm, const float4* sk, const uint16_t* cand,
+                                int n_cand, const float o[3], const float d[3], float onorm, float dnorm, float dinv,
+                                float dt_max, int cnt, float4* tab, uint16_t* tidx, float& U, float& e_out,
+                                int lane) {
     const float dd = fmaf(d[2], d[2], fmaf(d[1], d[1], d[0] * d[0]));
     const float idd = dd > 0.0f ? 1.0f / dd : 0.0f;
     const float ilen = dd > 0.0f ? rsqrtf(dd) : 0.0f;
     int n = 0;
     float u = 0.0f, e = 0.0f;
-    for (int b0 = 0; b0 < f.n_blobs; b0 += 32) {
-        const int b = b0 + lane;
+    for (int i0 = 0; i0 < n_cand; i0 += 32) {
+        const int b = i0 + lane < n_cand ? (cand ? (int)cand[i0 + lane] : i0 + lane) : f.n_blobs;
         bool keep = false;
         float4 ent = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         if (b < f.n_blobs) {
@@ -856,6 +858,76 @@ __device__ __forceinline__ int unb_fast_cut(const UArgs& A, const float4* tab, i
     return 0;
 }
 
+// The blobs that can have S > 0 (a density above 2^-126 somewhere on the
+// line) on some ray of a group of rays, as an ascending list; every other
+// blob gives S = 0 exactly in build_warp_table on each of the group's rays,
+// so leaving it out changes no result.  With c = the line of the group's
+// first ray (origin o_c, unit direction d_c), delta = the largest distance of
+// a group ray's origin from o_c and s_max = the largest sine of the angle of
+// a group ray's direction to d_c, the distance of blob centre mu from ray i's
+// line is at least p_c - delta - (|mu - o_c| + delta) s_max (p_c its distance
+// from line c; the closest point of line i lies within |mu - o_i| of o_i).
+// S = 0 once C = log2 peak - log2(e) p^2 / (2 std^2) < -140, i.e. p above
+// R_b = std sqrt((141 + log2 peak) / 0.7213) (one unit of slack in the
+// exponent for the FP32 rounding of C), with relative slack 1e-4 for the
+// FP32 distances.  Returns the list length; -1 (use every blob) when a ray
+// of the group has a zero or non-finite direction.
+// oi, di: this lane's ray (lv: the lane has one; lane 0 always has).
+__device__ int group_candidates(const nacc_blob_field& f, const float4* sm, const float4* sk, const float oi[3],
+                                const float di[3], bool lv, uint16_t* cand, int lane) {
+    float oc[3], dc[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        oc[a] = __shfl_sync(0xffffffffu, oi[a], 0);
+        dc[a] = __shfl_sync(0xffffffffu, di[a], 0);
+    }
+    const float lc = sqrtf(fmaf(dc[2], dc[2], fmaf(dc[1], dc[1], dc[0] * dc[0])));
+    const float li = sqrtf(fmaf(di[2], di[2], fmaf(di[1], di[1], di[0] * di[0])));
+    const bool bad = lv && !(li > 0.0f && li < 1e30f);
+    if (__any_sync(0xffffffffu, bad) || !(lc > 0.0f && lc < 1e30f)) return -1;
+    float sn = 0.0f, dl = 0.0f;
+    if (lv) {
+        const float cx = fmaf(di[1], dc[2], -di[2] * dc[1]), cy = fmaf(di[2], dc[0], -di[0] * dc[2]),
+                    cz = fmaf(di[0], dc[1], -di[1] * dc[0]);
+        sn = sqrtf(fmaf(cz, cz, fmaf(cy, cy, cx * cx))) / (li * lc) * 1.0001f + 1e-6f;
+        const float e0 = oi[0] - oc[0], e1 = oi[1] - oc[1], e2 = oi[2] - oc[2];
+        dl = sqrtf(fmaf(e2, e2, fmaf(e1, e1, e0 * e0))) * 1.0001f;
+    }
+    const float s_max = warp_max(sn), delta = warp_max(dl);
+    if (!(s_max < 1e30f && delta < 1e30f)) return -1;
+    const float u0 = dc[0] / lc, u1 = dc[1] / lc, u2 = dc[2] / lc;
+    int nc = 0;
+    for (int b0 = 0; b0 < f.n_blobs; b0 += 32) {
+        const int b = b0 + lane;
+        bool keep = false;
+        if (b < f.n_blobs) {
+            float4 mc, kc;
+            if (b < kStageBlobs) {
+                mc = sm[b];
+                kc = sk[b];
+            } else {
+                blob_consts(f, b, mc, kc);
+            }
+            keep = true;
+            if (!(kc.x > -141.0f)) {
+                keep = false;  // peak below 2^-141 (or none): C < -140 everywhere
+            } else {
+                const float m0 = mc.x - oc[0], m1 = mc.y - oc[1], m2 = mc.z - oc[2];
+                const float cx = fmaf(m1, u2, -m2 * u1), cy = fmaf(m2, u0, -m0 * u2), cz = fmaf(m0, u1, -m1 * u0);
+                const float pc = sqrtf(fmaf(cz, cz, fmaf(cy, cy, cx * cx)));
+                const float mn = sqrtf(fmaf(m2, m2, fmaf(m1, m1, m0 * m0)));
+                const float rb = kc.w * sqrtf((141.0f + kc.x) * 1.38629436f);  // std sqrt((141 + log2 peak) / 0.7213)
+                const float lower = pc - delta - (mn + delta) * s_max - 1e-4f * (mn + delta + 1.0f);
+                keep = !(lower > rb * 1.0001f + 1e-5f * (mn + delta));
+            }
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (keep) cand[nc + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)b;
+        nc += __popc(bal);
+    }
+    return nc;
+}
+
 // Early stop (after the count pass): one warp per ray, the block's rays in
 // turn, each decided as early_stop.cuh describes: no density at all when the
 // ray's depth bound stays below the threshold; else the fast depth -- the
@@ -879,6 +951,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_unb_stop(UArgs A, int32_t* __re
     __shared__ uint16_t s_tidx[kWarps][kStopTable];
     __shared__ float4 s_bm[kStageBlobs];
     __shared__ float4 s_bk[kStageBlobs];
+    __shared__ uint16_t s_cand[kWarps][kMaxBlobs];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     float4* tab = s_tab[wid];
     uint16_t* tidx = s_tidx[wid];
@@ -896,19 +969,58 @@ __global__ void __launch_bounds__(kThreads, 5) k_unb_stop(UArgs A, int32_t* __re
         if (grp >= n_groups) break;
         const int64_t rbase = grp * 32;
         long long delta = 0;  // change of the block's total
-        for (int i = 0; i < 32; ++i) {
+        // lane i loads the header of ray rbase + i (coalesced); the rays are then
+        // taken in turn, their values broadcast by shuffles, and lane i keeps the
+        // results of ray i
+        const int64_t rl = rbase + lane;
+        const bool lv = rl < A.n;
+        const int l_cnt = lv ? counts[rl] : 0;
+        const int l_nr = lv ? nruns[rl] : 0;
+        float l_o[3] = {0.0f, 0.0f, 0.0f}, l_d[3] = {0.0f, 0.0f, 0.0f};
+        if (lv) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                l_o[a] = A.o[3 * rl + a];
+                l_d[a] = A.d[3 * rl + a];
+            }
+        }
+        const int n_cand = group_candidates(A.field, s_bm, s_bk, l_o, l_d, lv, s_cand[wid], lane);
+        __syncwarp();
+        const uint16_t* cand = n_cand >= 0 ? s_cand[wid] : nullptr;
+        const int nc = n_cand >= 0 ? n_cand : nblobs;
+        int l_cut = l_cnt, l_kstop = A.K;
+        unsigned todo = __ballot_sync(0xffffffffu, l_cnt > 0);
+        // the next ray's runs are loaded while the current one is evaluated
+        int2 run_next = make_int2(0, 0);
+        if (todo) {
+            const int i0 = __ffs(todo) - 1;
+            const int nr0 = __shfl_sync(0xffffffffu, l_nr, i0);
+            if (nr0 >= 0 && lane < nr0) run_next = runs[(rbase + i0) * kRunSlots + lane];
+        }
+        while (todo) {
+            const int i = __ffs(todo) - 1;
+            todo &= todo - 1;
             const int64_t r = rbase + i;
-            if (r >= A.n) break;
-            const int cnt = counts[r];
-            if (cnt == 0) continue;
-            const float o[3] = {A.o[3 * r], A.o[3 * r + 1], A.o[3 * r + 2]};
-            const float d[3] = {A.d[3 * r], A.d[3 * r + 1], A.d[3 * r + 2]};
+            const int cnt = __shfl_sync(0xffffffffu, l_cnt, i);
+            const int nr = __shfl_sync(0xffffffffu, l_nr, i);
+            float o[3], d[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                o[a] = __shfl_sync(0xffffffffu, l_o[a], i);
+                d[a] = __shfl_sync(0xffffffffu, l_d[a], i);
+            }
+            const int2 run = run_next;
+            if (todo) {
+                const int in = __ffs(todo) - 1;
+                const int nrn = __shfl_sync(0xffffffffu, l_nr, in);
+                run_next = nrn >= 0 && lane < nrn ? runs[(rbase + in) * kRunSlots + lane] : make_int2(0, 0);
+            }
             const float onorm = sqrtf(o[0] * o[0] + o[1] * o[1] + o[2] * o[2]) * 1.0001f;
             const float dnorm = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) * 1.0001f;
             int cut = cnt, kstop = A.K;
             float U, e_out;
-            const int nk = build_warp_table(A.field, s_bm, s_bk, o, d, onorm, dnorm, dinv, dt_max, cnt, tab, tidx, U,
-                                            e_out, lane);
+            const int nk = build_warp_table(A.field, s_bm, s_bk, cand, nc, o, d, onorm, dnorm, dinv, dt_max, cnt, tab,
+                                            tidx, U, e_out, lane);
             __syncwarp();
             if (A.exact_all != 0 || !(depth_upper(U, cnt, nblobs) <= A.thr)) {  // the ray may stop
                 const int nt = nk <= kStopTable ? nk : -1;
@@ -919,23 +1031,26 @@ __global__ void __launch_bounds__(kThreads, 5) k_unb_stop(UArgs A, int32_t* __re
                                                    tidx, eps, lane);
                 __syncwarp();
                 const RayBound rb{U, ek, eps, e_out + e_grp};
-                const int nr = nruns[r];
-                const int2 run = (nr >= 0 && lane < nr) ? runs[r * kRunSlots + lane] : make_int2(0, 0);
                 const int st = A.exact_all != 0 || !bounds_usable(rb, cnt, A.thr)
                                    ? 2
                                    : unb_fast_cut<I>(A, tab, nt, rb, o, d, cnt, nr, run, lane, cut, kstop);
                 const bool exact = st == 2;
                 if (exact && lane == 0) queue[atomicAdd(qlen, 1ull)] = r;  // decided exactly by k_unb_stop_exact
             }
-            if (lane == 0) {
-                counts[r] = cut;
-                kstops[r] = kstop;
+            if (lane == i) {
+                l_cut = cut;
+                l_kstop = kstop;
             }
             delta += cut - cnt;
             __syncwarp();  // the next ray rewrites the table
         }
+        if (lv && l_cnt > 0) {
+            counts[rl] = l_cut;
+            kstops[rl] = l_kstop;
+        }
         if (lane == 0 && delta != 0)
             atomicAdd(reinterpret_cast<unsigned long long*>(block_sums + rbase / kThreads), (unsigned long long)delta);
+        __syncwarp();  // the next group rewrites the candidate list
     }
 }
 
