@@ -78,6 +78,9 @@ def parse_args(argv=None):
     ap.add_argument("--unbounded-cams", type=int, default=16,
                     help="cameras of the unbounded-scene leg (16 = the 4,194,304-ray workload)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target oracle CPU time")
+    ap.add_argument("--shard", choices=["view", "batch"], default="view",
+                    help="N > 1: every rank renders its own camera view (weak scaling), or the ranks split the "
+                         "rays of one view into contiguous ranges (strong scaling); no collective either way")
     ap.add_argument("--profile", choices=["image", "training", "unbounded"], default=None,
                     help="run only --warmup + --steps eager steps of one workload's training step (march, field, "
                          "render fwd, L2 loss, render bwd; the training batch adds the grid update; the unbounded "
@@ -100,6 +103,28 @@ def dist_env():
 def view_for_rank(rank: int) -> int:
     """Each rank renders its own camera view; rank 0 renders the reference view."""
     return rank
+
+
+def ray_range(n: int, rank: int, world: int) -> tuple[int, int]:
+    """The contiguous shard [lo, hi) of n rays that rank takes when one batch is
+    split over the ranks (sizes differ by at most one; rays are independent, so
+    the shards need no exchange)."""
+    base, extra = divmod(n, world)
+    lo = rank * base + min(rank, extra)
+    return lo, lo + base + (1 if rank < extra else 0)
+
+
+def rank_workload(args, rank: int, world: int):
+    """The bench workload of one rank: its own camera view (--shard view, weak
+    scaling) or its contiguous range of the rays of view 0 (--shard batch,
+    strong scaling)."""
+    if args.shard == "batch" and world > 1:
+        w = workloads.c2_image(args.width, args.height, view=0)
+        lo, hi = ray_range(w.n_rays, rank, world)
+        return workloads.dataclasses.replace(
+            w, name=f"{w.name}_rays{lo}-{hi}", rays_o=np.ascontiguousarray(w.rays_o[lo:hi]),
+            rays_d=np.ascontiguousarray(w.rays_d[lo:hi]), target=np.ascontiguousarray(w.target[lo:hi]))
+    return workloads.c2_image(args.width, args.height, view=view_for_rank(rank))
 
 
 def reduce_max(value: float, dist=None) -> float:
@@ -1033,7 +1058,7 @@ def run_ours(args):
     import paper_2305_04966_gb300 as nacc
     nacc.load_library()
 
-    w = workloads.c2_image(args.width, args.height, view=view_for_rank(rank))
+    w = rank_workload(args, rank, world)
     g, m = w.grid, w.march
     n = w.n_rays
     field = nacc.BlobField.from_numpy(w.blobs, dev)
@@ -1182,12 +1207,15 @@ def run_ours(args):
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "strong" if args.shard == "batch" and world > 1 else "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "n_rays_per_gpu": n, "grid": f"{g.n_levels}x{g.res}^3",
                        "max_steps": m.max_steps, "blobs": w.blobs.n, "early_stop_eps": m.early_stop_eps,
                        "samples_per_gpu": S, "l2": "flushed between timed steps (512 MB write)",
-                       "parallelism": f"dp{world} (one view per GPU)"},
+                       "parallelism": f"dp{world} ("
+                                      + ("contiguous ray ranges of one view" if args.shard == "batch" and world > 1
+                                         else "one view per GPU") + ")"},
             "samples_per_s": samples_total / (ms / 1000.0),
             "stage_ms": stage_ms,
             "roofline": path_roof,
