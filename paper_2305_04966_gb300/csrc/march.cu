@@ -1145,10 +1145,15 @@ __global__ void __launch_bounds__(kStopThreads, 7)
 }
 
 // Exact decisions of the rays the early-stop pass queued (early_stop.cuh):
-// persistent warps take queued rays one at a time (ticket `qhead` over the
-// `*qlen` entries), build the ray's exact blob list and run the exact path;
-// the cut and its lattice index replace the ray's count and K_end, and the
-// change of the count is added to its 32-ray entry's total.
+// persistent CTAs take queued rays one at a time (ticket `qhead` over the
+// `*qlen` entries); warp 0 builds the ray's exact blob list, then the four
+// warps evaluate the definition's sigma*dt at 128 consecutive points at a
+// time (32 each, exact_tau) into shared memory and thread 0 adds them in
+// order one at a time -- the definition's own sum -- stopping at the first
+// point whose depth before it exceeds the threshold.  Rays whose runs
+// overflowed walk the lattice on warp 0 alone (stop_exact).  The cut and its
+// lattice index replace the ray's count and K_end, and the change of the
+// count is added to its 32-ray entry's total.
 __global__ void __launch_bounds__(kStopThreads)
     k_march_stop_exact(MarchArgs A, int32_t* __restrict__ counts, int32_t* __restrict__ kstops,
                        const int32_t* __restrict__ nruns, const float* __restrict__ tnear,
@@ -1156,17 +1161,21 @@ __global__ void __launch_bounds__(kStopThreads)
                        const long long* __restrict__ queue, const unsigned long long* __restrict__ qlen,
                        unsigned long long* __restrict__ qhead) {
     extern __shared__ StopBlob s_blobs[];
-    __shared__ uint16_t s_ex[kStopWarps][kMaxBlobs];
-    __shared__ float s_seq[kStopWarps][32];
+    __shared__ uint16_t s_ex[kMaxBlobs];
+    __shared__ float s_tau[kStopThreads];
+    __shared__ int s_k[kStopThreads];
+    __shared__ float s_seq[32];
+    __shared__ unsigned long long s_tk;
+    __shared__ int s_nex, s_jc;
     stage_stop_blobs(s_blobs, A.field);
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const unsigned long long nq = *qlen;
     for (;;) {
-        unsigned long long tk = 0;
-        if (lane == 0) tk = atomicAdd(qhead, 1ull);
-        tk = __shfl_sync(0xffffffffu, tk, 0);
-        if (tk >= nq) break;
+        if (threadIdx.x == 0) s_tk = atomicAdd(qhead, 1ull);
+        __syncthreads();
+        const unsigned long long tk = s_tk;
+        if (tk >= nq) break;  // the same for the whole CTA
         const int64_t r = queue[tk];
         const int cnt = counts[r], nr = nruns[r], ke = kstops[r];
         const float tn = tnear[r];
@@ -1180,18 +1189,64 @@ __global__ void __launch_bounds__(kStopThreads)
         const float tmax = fabsf(tn) + (float)(ke + 1) * A.step * 1.0001f;
         const float pos_far = (sqrtf(o[0] * o[0] + o[1] * o[1] + o[2] * o[2]) +
                                tmax * sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2])) * 1.0002f;
-        const int n_ex = build_exact_list(s_blobs, A.field.n_blobs, o, d, pos_far, s_ex[wid], lane);
-        __syncwarp();
+        if (wid == 0) {
+            const int n = build_exact_list(s_blobs, A.field.n_blobs, o, d, pos_far, s_ex, lane);
+            if (lane == 0) s_nex = n;
+        }
+        __syncthreads();
+        const int n_ex = s_nex;
         int cut = cnt, kstop = ke;
-        stop_exact(A, s_blobs, s_ex[wid], n_ex, r, o, d, tn, cnt, nr, run, ke, pos_far, lane, s_seq[wid], cut, kstop);
-        if (lane == 0) {
+        if (nr >= 0) {
+            int ex = run.y;  // -> exclusive prefix of the run lengths
+#pragma unroll
+            for (int o2 = 1; o2 < 32; o2 <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, ex, o2);
+                if (lane >= o2) ex += y;
+            }
+            ex -= run.y;
+            float P = 0.0f;  // the sequential sum (thread 0's)
+            for (int pr = 0; pr < cnt; pr += kStopThreads) {
+                const int p = pr + (int)threadIdx.x;
+                int k = 0;
+                for (int j = 0; j < nr; ++j) {
+                    const int ej = __shfl_sync(0xffffffffu, ex, j);
+                    const int kj = __shfl_sync(0xffffffffu, run.x, j);
+                    if (p >= ej) k = kj + (p - ej);
+                }
+                s_tau[threadIdx.x] = exact_tau(A, s_blobs, s_ex, n_ex, o, d, tn, k, p < cnt, pos_far, lane);
+                s_k[threadIdx.x] = k;
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    int jc = -1;
+                    const int nv = min(kStopThreads, cnt - pr);
+                    for (int j = 0; j < nv; ++j) {
+                        if (P > A.thr) {
+                            jc = j;
+                            break;
+                        }
+                        P = __fadd_rn(P, s_tau[j]);
+                    }
+                    s_jc = jc;
+                }
+                __syncthreads();
+                const int jc = s_jc;
+                if (jc >= 0) {
+                    cut = pr + jc;
+                    kstop = s_k[jc];
+                    break;
+                }
+            }
+        } else if (wid == 0) {  // runs overflowed: the lattice walk, on one warp
+            stop_exact(A, s_blobs, s_ex, n_ex, r, o, d, tn, cnt, nr, run, ke, pos_far, lane, s_seq, cut, kstop);
+        }
+        if (threadIdx.x == 0) {
             counts[r] = cut;
             kstops[r] = kstop;
             if (cut != cnt)
                 atomicAdd(reinterpret_cast<unsigned long long*>(block_sums + r / kRaysPerBlock),
                           (unsigned long long)(long long)(cut - cnt));
         }
-        __syncwarp();  // the next ray rewrites the list
+        __syncthreads();  // the next ray rewrites the list, the buffers and the ticket
     }
 }
 

@@ -617,9 +617,23 @@ __global__ void __launch_bounds__(kThreads) k_unb_count(UArgs A, int32_t* __rest
 // (early_stop.cuh): t from the lattice table, the blob parameters from
 // global memory, entries that are 0 over the whole chunk left out; 0 for
 // lanes without a point (`valid` false).  Every lane of the warp calls it.
-__device__ __forceinline__ float unb_exact_tau(const UArgs& A, const uint16_t* ex_list, int n_ex, const float o[3],
-                                               const float d[3], int k, bool valid, float pos_far, int lane) {
-    const nacc_blob_field& f = A.field;
+// The definition's per-blob constants (centre, coefficient -1/2 / std^2 as
+// the definition rounds it, peak), staged once per CTA of the exact kernel.
+struct UExact {
+    float mx, my, mz, coef, peak;
+};
+
+__device__ __forceinline__ void stage_exact_blobs(UExact* eb, const nacc_blob_field& f) {
+    for (int b = threadIdx.x; b < f.n_blobs; b += blockDim.x) {
+        const float sd = __ldg(f.std + b);
+        eb[b] = UExact{__ldg(f.mu + 3 * b), __ldg(f.mu + 3 * b + 1), __ldg(f.mu + 3 * b + 2),
+                       __fdiv_rn(-0.5f, __fmul_rn(sd, sd)), __ldg(f.peak + b)};
+    }
+}
+
+__device__ __forceinline__ float unb_exact_tau(const UArgs& A, const UExact* eb, const uint16_t* ex_list, int n_ex,
+                                               const float o[3], const float d[3], int k, bool valid, float pos_far,
+                                               int lane) {
     const int kk = valid ? k : 0;
     const float t0 = __ldg(A.tt + kk), t1 = __ldg(A.tt + kk + 1), tm = __ldg(A.tm + kk);
     float x[3];
@@ -632,10 +646,9 @@ __device__ __forceinline__ float unb_exact_tau(const UArgs& A, const uint16_t* e
     const float dd = fmaf(d[2], d[2], fmaf(d[1], d[1], d[0] * d[0]));
     const float s = exact_sigma_chunk(
         x, ex_list, n_ex,
-        [&f](int b) {
-            const float sd = __ldg(f.std + b);
-            return ExactBlob{__ldg(f.mu + 3 * b), __ldg(f.mu + 3 * b + 1), __ldg(f.mu + 3 * b + 2),
-                             __fdiv_rn(-0.5f, __fmul_rn(sd, sd)), __ldg(f.peak + b)};
+        [eb](int b) {
+            const UExact& v = eb[b];
+            return ExactBlob{v.mx, v.my, v.mz, v.coef, v.peak};
         },
         o, d, dd, dd > 0.0f ? 1.0f / dd : 0.0f, t_lo, t_hi, pos_far, lane);
     return valid ? __fmul_rn(s, __fsub_rn(t1, t0)) : 0.0f;
@@ -658,7 +671,8 @@ __device__ __forceinline__ bool unb_occupied(const UArgs& A, const float o[3], c
 // whose depth before it exceeds the threshold, which cuts the ray.  cut /
 // kstop are left as given if the ray never stops.
 template <typename I>
-__device__ __forceinline__ void unb_stop_exact(const UArgs& A, const uint16_t* ex_list, int n_ex, const float o[3],
+__device__ __forceinline__ void unb_stop_exact(const UArgs& A, const UExact* eb, const uint16_t* ex_list, int n_ex,
+                                              const float o[3],
                                               const float d[3], int cnt, int nr, int2 run, float pos_far, int lane,
                                               float* buf, int& cut, int& kstop) {
     int ex = run.y;  // -> exclusive prefix of the run lengths
@@ -688,7 +702,7 @@ __device__ __forceinline__ void unb_stop_exact(const UArgs& A, const uint16_t* e
         }
         const unsigned m = __ballot_sync(0xffffffffu, on);
         if (!m) continue;
-        buf[lane] = unb_exact_tau(A, ex_list, n_ex, o, d, k, on, pos_far, lane);
+        buf[lane] = unb_exact_tau(A, eb, ex_list, n_ex, o, d, k, on, pos_far, lane);
         __syncwarp();
         int jc = -1, sc = seen;
         if (lane == 0) {
@@ -1055,10 +1069,16 @@ __global__ void __launch_bounds__(kThreads, 5) k_unb_stop(UArgs A, int32_t* __re
 }
 
 // Exact decisions of the rays the early-stop pass queued (early_stop.cuh):
-// persistent warps take queued rays one at a time (ticket `qhead` over the
-// `*qlen` entries), build the ray's exact blob list and run the exact path;
-// the cut and its lattice index replace the ray's count and stop, and the
-// change of the count is added to its block's total.
+// persistent CTAs take queued rays one at a time (ticket `qhead` over the
+// `*qlen` entries); warp 0 builds the ray's exact blob list, then the four
+// warps evaluate the definition's sigma*dt at 128 consecutive points at a
+// time (32 each) into shared memory and thread 0 adds them in order one at a
+// time -- the definition's own sum -- stopping at the first point whose depth
+// before it exceeds the threshold.  Rays whose runs overflowed walk the
+// lattice on warp 0 alone (unb_stop_exact).  The cut and its lattice index
+// replace the ray's count and stop, and the change of the count is added to
+// its block's total.  Dynamic shared memory: the blobs' exact constants
+// (UExact, n_blobs of them).
 template <typename I>
 __global__ void __launch_bounds__(kThreads) k_unb_stop_exact(UArgs A, int32_t* __restrict__ counts,
                                                              int32_t* __restrict__ kstops,
@@ -1068,20 +1088,26 @@ __global__ void __launch_bounds__(kThreads) k_unb_stop_exact(UArgs A, int32_t* _
                                                              const long long* __restrict__ queue,
                                                              const unsigned long long* __restrict__ qlen,
                                                              unsigned long long* __restrict__ qhead) {
+    extern __shared__ UExact s_eb[];
     __shared__ float4 s_bm[kStageBlobs];
     __shared__ float4 s_bk[kStageBlobs];
-    __shared__ uint16_t s_ex[kWarps][kMaxBlobs];
-    __shared__ float s_seq[kWarps][32];
+    __shared__ uint16_t s_ex[kMaxBlobs];
+    __shared__ float s_tau[kThreads];
+    __shared__ int s_k[kThreads];
+    __shared__ float s_seq[32];
+    __shared__ unsigned long long s_tk;
+    __shared__ int s_nex, s_jc;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     for (int b = tid; b < min(A.field.n_blobs, kStageBlobs); b += kThreads) blob_consts(A.field, b, s_bm[b], s_bk[b]);
+    stage_exact_blobs(s_eb, A.field);
     __syncthreads();
     const float t_far = __ldg(A.tt + A.K);
     const unsigned long long nq = *qlen;
     for (;;) {
-        unsigned long long tk = 0;
-        if (lane == 0) tk = atomicAdd(qhead, 1ull);
-        tk = __shfl_sync(0xffffffffu, tk, 0);
-        if (tk >= nq) break;
+        if (tid == 0) s_tk = atomicAdd(qhead, 1ull);
+        __syncthreads();
+        const unsigned long long tk = s_tk;
+        if (tk >= nq) break;  // the same for the whole CTA
         const int64_t r = queue[tk];
         const int cnt = counts[r], nr = nruns[r];
         const float o[3] = {A.o[3 * r], A.o[3 * r + 1], A.o[3 * r + 2]};
@@ -1089,18 +1115,64 @@ __global__ void __launch_bounds__(kThreads) k_unb_stop_exact(UArgs A, int32_t* _
         const int2 run = (nr >= 0 && lane < nr) ? runs[r * kRunSlots + lane] : make_int2(0, 0);
         const float pos_far = (sqrtf(o[0] * o[0] + o[1] * o[1] + o[2] * o[2]) +
                                t_far * sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2])) * 1.0002f;
-        const int n_ex = build_exact_list(A.field, s_bm, s_bk, o, d, pos_far, s_ex[wid], lane);
-        __syncwarp();
+        if (wid == 0) {
+            const int n = build_exact_list(A.field, s_bm, s_bk, o, d, pos_far, s_ex, lane);
+            if (lane == 0) s_nex = n;
+        }
+        __syncthreads();
+        const int n_ex = s_nex;
         int cut = cnt, kstop = A.K;
-        unb_stop_exact<I>(A, s_ex[wid], n_ex, o, d, cnt, nr, run, pos_far, lane, s_seq[wid], cut, kstop);
-        if (lane == 0) {
+        if (nr >= 0) {
+            int ex = run.y;  // -> exclusive prefix of the run lengths
+#pragma unroll
+            for (int o2 = 1; o2 < 32; o2 <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, ex, o2);
+                if (lane >= o2) ex += y;
+            }
+            ex -= run.y;
+            float P = 0.0f;  // the sequential sum (thread 0's)
+            for (int pr = 0; pr < cnt; pr += kThreads) {
+                const int p = pr + tid;
+                int k = 0;
+                for (int j = 0; j < nr; ++j) {
+                    const int ej = __shfl_sync(0xffffffffu, ex, j);
+                    const int kj = __shfl_sync(0xffffffffu, run.x, j);
+                    if (p >= ej) k = kj + (p - ej);
+                }
+                s_tau[tid] = unb_exact_tau(A, s_eb, s_ex, n_ex, o, d, k, p < cnt, pos_far, lane);
+                s_k[tid] = k;
+                __syncthreads();
+                if (tid == 0) {
+                    int jc = -1;
+                    const int nv = min(kThreads, cnt - pr);
+                    for (int j = 0; j < nv; ++j) {
+                        if (P > A.thr) {
+                            jc = j;
+                            break;
+                        }
+                        P = __fadd_rn(P, s_tau[j]);
+                    }
+                    s_jc = jc;
+                }
+                __syncthreads();
+                const int jc = s_jc;
+                if (jc >= 0) {
+                    cut = pr + jc;
+                    kstop = s_k[jc];
+                    break;
+                }
+            }
+        } else if (wid == 0) {  // runs overflowed: the lattice walk, on one warp
+            unb_stop_exact<I>(A, s_eb, s_ex, n_ex, o, d, cnt, nr, run, pos_far, lane, s_seq, cut, kstop);
+        }
+        if (tid == 0) {
             counts[r] = cut;
             kstops[r] = kstop;
             if (cut != cnt)
                 atomicAdd(reinterpret_cast<unsigned long long*>(block_sums + r / kThreads),
                           (unsigned long long)(long long)(cut - cnt));
         }
-        __syncwarp();  // the next ray rewrites the list
+        __syncthreads();  // the next ray rewrites the list, the buffers and the ticket
     }
 }
 
@@ -1411,14 +1483,15 @@ extern "C" int nacc_march_unbounded(const nacc_grid* grid, const float* rays_o, 
         // decide from bounds go to a queue decided exactly by a second kernel
         NACC_CUDA_TRY(cudaMemsetAsync(tickets, 0, 3 * sizeof(unsigned long long), st));
         int per_sm = 0, per_sm_x = 0;
+        const size_t shm_x = sizeof(UExact) * (size_t)A.field.n_blobs;  // <= 20 KiB (kMaxBlobs blobs)
         if (idx32) {
             NACC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_unb_stop<uint32_t>, kThreads, 0));
             NACC_CUDA_TRY(
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_x, k_unb_stop_exact<uint32_t>, kThreads, 0));
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_x, k_unb_stop_exact<uint32_t>, kThreads, shm_x));
         } else {
             NACC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_unb_stop<int64_t>, kThreads, 0));
             NACC_CUDA_TRY(
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_x, k_unb_stop_exact<int64_t>, kThreads, 0));
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_x, k_unb_stop_exact<int64_t>, kThreads, shm_x));
         }
         const unsigned blocks =
             (unsigned)std::max<int64_t>(1, std::min<int64_t>(nb, (int64_t)sm_count() * std::max(per_sm, 1)));
@@ -1428,13 +1501,13 @@ extern "C" int nacc_march_unbounded(const nacc_grid* grid, const float* rays_o, 
             k_unb_stop<uint32_t><<<blocks, kThreads, 0, st>>>(A, counts, kstops, nruns, runs, bsums, tickets, queue,
                                                              tickets + 1);
             NACC_LAUNCH_CHECK();
-            k_unb_stop_exact<uint32_t><<<blocks_x, kThreads, 0, st>>>(A, counts, kstops, nruns, runs, bsums, queue,
+            k_unb_stop_exact<uint32_t><<<blocks_x, kThreads, shm_x, st>>>(A, counts, kstops, nruns, runs, bsums, queue,
                                                                      tickets + 1, tickets + 2);
         } else {
             k_unb_stop<int64_t><<<blocks, kThreads, 0, st>>>(A, counts, kstops, nruns, runs, bsums, tickets, queue,
                                                             tickets + 1);
             NACC_LAUNCH_CHECK();
-            k_unb_stop_exact<int64_t><<<blocks_x, kThreads, 0, st>>>(A, counts, kstops, nruns, runs, bsums, queue,
+            k_unb_stop_exact<int64_t><<<blocks_x, kThreads, shm_x, st>>>(A, counts, kstops, nruns, runs, bsums, queue,
                                                                     tickets + 1, tickets + 2);
         }
         NACC_LAUNCH_CHECK();
