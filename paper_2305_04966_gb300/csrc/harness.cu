@@ -60,6 +60,10 @@ __global__ void __launch_bounds__(256)
 // integral along the whole ray line is above kCullEps (bound: peak 2^C_b
 // sqrt(2 pi) sd / |d|); each dropped blob changes sigma by at most
 // peak 2^C_b <= kCullEps |d| / (sqrt(2 pi) sd) at any point of the ray.
+// Fields of at least kGroupAbove blobs first list, per group of kFieldGroup
+// consecutive rays, the blobs any of them may keep (field_group_candidates),
+// so each ray's table is built from that list: the same tables, in the same
+// order, for less work.
 constexpr int kFieldWarps = 8;
 constexpr int kFieldRayBlobs = 256;  // per-warp shared table limit
 constexpr int kCullAbove = 16;
@@ -86,22 +90,99 @@ __device__ __forceinline__ bool load_t4(const float* __restrict__ t0, const floa
     return whole;
 }
 
-__global__ void __launch_bounds__(kFieldWarps * 32, 4)
-    k_field_rays(const float* __restrict__ o, const float* __restrict__ d, int64_t n_rays,
-                 const int64_t* __restrict__ off, const float* __restrict__ t0, const float* __restrict__ t1,
-                 nacc_blob_field f, float* __restrict__ sig, float* __restrict__ rgb) {
-    extern __shared__ float4 s_dyn[];
-    const int nb = f.n_blobs;
-    BlobS* sb = reinterpret_cast<BlobS*>(s_dyn + kFieldWarps * nb);
-    stage_blobs(sb, f, true);
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) sb[b].coef *= 1.4426950408889634f;  // log2 e
-    __syncthreads();
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    float4* q = s_dyn + wid * nb;
-    const int64_t warps = (int64_t)gridDim.x * kFieldWarps;
-    for (int64_t r = (int64_t)blockIdx.x * kFieldWarps + wid; r < n_rays; r += warps) {
+constexpr int kFieldGroup = 8;    // consecutive rays sharing one candidate list
+constexpr int kGroupAbove = 128;  // fields of at least this many blobs use the lists
+
+// The blobs some ray of the group rbase .. rbase+kFieldGroup-1 may keep in its table
+// (integral bound along the line above kCullEps), as an ascending list in
+// cand; returns its length, or -1 (every blob) when a ray of the group has a
+// zero direction.  With c = the first ray's line (origin o_c, unit direction
+// u_c), delta the largest distance of a group ray's origin from o_c and s the
+// largest sine of a group direction's angle to u_c, blob b lies at least
+// p_lo = p_c - delta - (|mu - o_c| + delta) s from every group ray's line
+// (the closest point of line i lies within |mu - o_i| of o_i), so each ray's
+// bound is at most peak 2^(coef p_lo^2) sqrt(2 pi) sd / min |d|; a blob whose
+// bound is below kCullEps / 4 (slack for the FP32 distances and exponential)
+// is kept by none of them.
+__device__ int field_group_candidates(const BlobS* sb, int nb, const float* __restrict__ ro,
+                                      const float* __restrict__ rd, int64_t rbase, int64_t n, uint16_t* cand,
+                                      int lane) {
+    const int64_t r = rbase + lane;
+    const bool lv = lane < kFieldGroup && r < n;
+    float oi[3] = {0.0f, 0.0f, 0.0f}, di[3] = {0.0f, 0.0f, 0.0f};
+    if (lv) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            oi[a] = __ldg(ro + 3 * r + a);
+            di[a] = __ldg(rd + 3 * r + a);
+        }
+    }
+    float oc[3], dc[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        oc[a] = __shfl_sync(0xffffffffu, oi[a], 0);
+        dc[a] = __shfl_sync(0xffffffffu, di[a], 0);
+    }
+    const float lc = sqrtf(fmaf(dc[2], dc[2], fmaf(dc[1], dc[1], dc[0] * dc[0])));
+    const float li = sqrtf(fmaf(di[2], di[2], fmaf(di[1], di[1], di[0] * di[0])));
+    const bool bad = lv && !(li > 0.0f && li < 1e30f);
+    if (__any_sync(0xffffffffu, bad) || !(lc > 0.0f && lc < 1e30f)) return -1;
+    float sn = 0.0f, dl = 0.0f, il = 0.0f;
+    if (lv) {
+        const float cx = fmaf(di[1], dc[2], -di[2] * dc[1]), cy = fmaf(di[2], dc[0], -di[0] * dc[2]),
+                    cz = fmaf(di[0], dc[1], -di[1] * dc[0]);
+        sn = sqrtf(fmaf(cz, cz, fmaf(cy, cy, cx * cx))) / (li * lc) * 1.0001f + 1e-6f;
+        const float e0 = oi[0] - oc[0], e1 = oi[1] - oc[1], e2 = oi[2] - oc[2];
+        dl = sqrtf(fmaf(e2, e2, fmaf(e1, e1, e0 * e0))) * 1.0001f;
+        il = 1.0001f / li;
+    }
+    float s_max = sn, delta = dl, ilen = il;
+#pragma unroll
+    for (int o2 = 16; o2 > 0; o2 >>= 1) {
+        s_max = fmaxf(s_max, __shfl_xor_sync(0xffffffffu, s_max, o2));
+        delta = fmaxf(delta, __shfl_xor_sync(0xffffffffu, delta, o2));
+        ilen = fmaxf(ilen, __shfl_xor_sync(0xffffffffu, ilen, o2));
+    }
+    if (!(s_max < 1e30f && delta < 1e30f && ilen < 1e30f)) return -1;
+    const float u0 = dc[0] / lc, u1 = dc[1] / lc, u2 = dc[2] / lc;
+    const float lim = __log2f(kCullEps) - 2.0f;
+    int nc = 0;
+    for (int b0 = 0; b0 < nb; b0 += 32) {
+        const int b = b0 + lane;
+        bool keep = false;
+        if (b < nb) {
+            const BlobS v = sb[b];
+            keep = v.peak > 0.0f;
+            if (keep) {
+                const float m0 = v.mx - oc[0], m1 = v.my - oc[1], m2 = v.mz - oc[2];
+                const float cx = fmaf(m1, u2, -m2 * u1), cy = fmaf(m2, u0, -m0 * u2), cz = fmaf(m0, u1, -m1 * u0);
+                const float pc = sqrtf(fmaf(cz, cz, fmaf(cy, cy, cx * cx)));
+                const float mn = sqrtf(fmaf(m2, m2, fmaf(m1, m1, m0 * m0)));
+                const float plo = fmaxf(0.0f, pc - delta - (mn + delta) * s_max - 1e-4f * (mn + delta + 1.0f));
+                const float sd = sqrtf(-0.72134752f / v.coef);  // coef = -log2(e) / (2 sd^2)
+                const float lb = __log2f(v.peak * 2.5066283f * sd * ilen) + v.coef * (plo * plo) * 0.9998f;
+                keep = !(lb < lim);
+            }
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (keep) cand[nc + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)b;
+        nc += __popc(bal);
+    }
+    return nc;
+}
+
+// One ray of k_field_rays: its table {A_b, t*_b, C_b, b} from the blobs
+// cand[0 .. nc) (ascending; NULL or !kGroups: blobs 0 .. nc-1), culled per
+// ray when kCull, then its samples, four consecutive ones per lane per chunk
+// of 128.
+template <bool kCull, bool kGroups>
+__device__ __forceinline__ void field_ray(int64_t r, const uint16_t* cand, int nc, const float* __restrict__ o,
+                                          const float* __restrict__ d, const int64_t* __restrict__ off,
+                                          const float* __restrict__ t0, const float* __restrict__ t1,
+                                          const BlobS* sb, int nb, float4* q, float* __restrict__ sig,
+                                          float* __restrict__ rgb, int lane) {
         const long long s = off[r], e = off[r + 1];
-        if (e <= s) continue;
+        if (e <= s) return;
         // the first chunk's loads are in flight during the table set-up; each
         // chunk's compute overlaps the next chunk's loads
         long long p = (s & ~3ll) + 4 * lane;
@@ -114,8 +195,8 @@ __global__ void __launch_bounds__(kFieldWarps * 32, 4)
         const float ilen = dd > 0.0f ? rsqrtf(dd) : 0.0f;
         // table entries {A_b, t*_b, C_b, b}, compacted in blob order
         int nt = 0;
-        for (int b0 = 0; b0 < nb; b0 += 32) {
-            const int b = b0 + lane;
+        for (int i0 = 0; i0 < nc; i0 += 32) {
+            const int b = kGroups ? (i0 + lane < nc ? (cand ? (int)cand[i0 + lane] : i0 + lane) : nb) : i0 + lane;
             bool keep = false;
             float4 ent;
             if (b < nb) {
@@ -190,6 +271,42 @@ __global__ void __launch_bounds__(kFieldWarps * 32, 4)
             }
         }
         __syncwarp();  // the next ray's set-up rewrites q
+}
+
+// kCull: fields of more than kCullAbove blobs (tables culled per ray); kGroups:
+// of at least kGroupAbove blobs (candidate lists per group of rays first)
+template <bool kCull, bool kGroups>
+__global__ void __launch_bounds__(kFieldWarps * 32, 4)
+    k_field_rays(const float* __restrict__ o, const float* __restrict__ d, int64_t n_rays,
+                 const int64_t* __restrict__ off, const float* __restrict__ t0, const float* __restrict__ t1,
+                 nacc_blob_field f, float* __restrict__ sig, float* __restrict__ rgb) {
+    extern __shared__ float4 s_dyn[];
+    const int nb = f.n_blobs;
+    BlobS* sb = reinterpret_cast<BlobS*>(s_dyn + kFieldWarps * nb);
+    stage_blobs(sb, f, true);
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) sb[b].coef *= 1.4426950408889634f;  // log2 e
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float4* q = s_dyn + wid * nb;
+    const int64_t warps = (int64_t)gridDim.x * kFieldWarps;
+
+    if (kGroups) {
+        // groups of kFieldGroup consecutive rays: the blobs none of the group's
+        // rays can keep are left out of every table before the rays are set up
+        uint16_t* cand = reinterpret_cast<uint16_t*>(sb + nb) + (size_t)wid * nb;
+        const int64_t n_groups = (n_rays + kFieldGroup - 1) / kFieldGroup;
+        for (int64_t grp = (int64_t)blockIdx.x * kFieldWarps + wid; grp < n_groups; grp += warps) {
+            const int64_t rbase = grp * kFieldGroup;
+            const int nc = field_group_candidates(sb, nb, o, d, rbase, n_rays, cand, lane);
+            __syncwarp();
+            for (int i = 0; i < kFieldGroup && rbase + i < n_rays; ++i)
+                field_ray<kCull, true>(rbase + i, nc >= 0 ? cand : nullptr, nc >= 0 ? nc : nb, o, d, off, t0, t1, sb,
+                                       nb, q, sig, rgb, lane);
+            __syncwarp();  // the next group rewrites the candidate list
+        }
+    } else {
+        for (int64_t r = (int64_t)blockIdx.x * kFieldWarps + wid; r < n_rays; r += warps)
+            field_ray<kCull, false>(r, nullptr, nb, o, d, off, t0, t1, sb, nb, q, sig, rgb, lane);
     }
 }
 
@@ -253,15 +370,20 @@ extern "C" int nacc_harness_field_rays(const float* rays_o, const float* rays_d,
     auto a16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
     NACC_CHECK_ARG(a16(t_starts) && a16(t_ends) && a16(sigmas) && a16(rgbs),
                    "t_starts, t_ends, sigmas and rgbs must be 16-byte aligned");
-    const size_t shm = (sizeof(float4) * kFieldWarps + sizeof(BlobS)) * (size_t)field->n_blobs;
+    // per-warp tables, the staged blobs, per-warp candidate lists (culled fields)
+    const size_t shm = (sizeof(float4) * kFieldWarps + sizeof(BlobS) + sizeof(uint16_t) * kFieldWarps) *
+                       (size_t)field->n_blobs;
+    const int nbl = field->n_blobs;
+    const auto kern = nbl >= kGroupAbove ? k_field_rays<true, true>
+                                         : (nbl > kCullAbove ? k_field_rays<true, false> : k_field_rays<false, false>);
     if (shm > 48 * 1024)
-        NACC_CUDA_TRY(cudaFuncSetAttribute(k_field_rays, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+        NACC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
     int per_sm = 1;
-    NACC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_field_rays, kFieldWarps * 32, shm));
+    NACC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kFieldWarps * 32, shm));
     if (per_sm < 1) per_sm = 1;
     const int64_t grid = min64((int64_t)per_sm * sm_count(), (n_rays + kFieldWarps - 1) / kFieldWarps);
-    k_field_rays<<<(unsigned)grid, kFieldWarps * 32, shm, as_stream(stream)>>>(
-        rays_o, rays_d, n_rays, offsets, t_starts, t_ends, *field, sigmas, rgbs);
+    kern<<<(unsigned)grid, kFieldWarps * 32, shm, as_stream(stream)>>>(rays_o, rays_d, n_rays, offsets, t_starts,
+                                                                      t_ends, *field, sigmas, rgbs);
     NACC_LAUNCH_CHECK();
     return NACC_OK;
 }
