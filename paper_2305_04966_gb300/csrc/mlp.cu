@@ -13,9 +13,9 @@
 // K = 16 MMAs of a layer (M = 128 points, N = 64 units, K = 64); every warp
 // reads its 32 rows of the accumulator back from tensor memory, applies ReLU
 // while packing the next layer's BF16 input row (layer 1's bias rides in the
-// MMA through the encoding's padding columns, layer 2's is added first); the
-// last layer (64 -> 1) is an N = 16 MMA with w3 in row 0 of its B tile, then
-// b3 and softplus on the CUDA cores.
+// MMA through the encoding's padding columns); layer 2's output gets b2, ReLU
+// and BF16 rounding and goes straight into the last layer (64 -> 1) as FP32
+// FMAs on the CUDA cores, then b3 and softplus.
 //
 // Adjoint (same tiles): delta3 = dL/dz3, delta2 = delta3 w3 * [h2 > 0] and
 // delta1 = (delta2 W2) * [h1 > 0] (an M = 128 MMA against W2^T); the weight
@@ -43,7 +43,6 @@ constexpr int oW1 = 0, oB1 = 4096, oW2 = 4160, oB2 = 8256, oW3 = 8320, oB3 = 838
 constexpr int wW1 = 0, wW2 = 4096, wW3 = 8192;
 constexpr uint32_t kTileBytes = 16384;  // 128 rows x 128 bytes
 constexpr uint32_t kWBytes = 8192;      // 64 rows x 128 bytes
-constexpr uint32_t kW3Bytes = 2048;     // 16 rows x 128 bytes (N = 16 tile of the 64 -> 1 layer)
 
 __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
     return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
@@ -316,9 +315,25 @@ __device__ __forceinline__ void relu_pack32(uint32_t taddr, const float* bias, u
     }
 }
 
+// z3 += sum over 32 accumulator columns (this thread's row) of
+// bf16(relu(acc + b2)) * w3, in column order (FP32 FMAs).
+__device__ __forceinline__ float head_dot32(uint32_t taddr, const float* b2, const float* w3, float z) {
+    float v[32];
+    tc::tmem_ld16(taddr, v);
+    tc::tmem_ld16(taddr + 16, v + 16);
+    tc::tmem_wait_ld();
+#pragma unroll
+    for (int i = 0; i < 32; i += 2) {
+        const uint32_t h = pack_relu_bf16x2(v[i] + b2[i], v[i + 1] + b2[i + 1]);
+        z = fmaf(__uint_as_float(h << 16), w3[i], z);
+        z = fmaf(__uint_as_float(h & 0xffff0000u), w3[i + 1], z);
+    }
+    return z;
+}
+
 // Forward.  Per tile: encode -> MMA (layer 1, bias folded) -> ReLU/BF16 ->
-// MMA (layer 2) -> + b2, ReLU/BF16 -> MMA (64 -> 1 as N = 16 with w3 in row
-// 0 of the B tile) -> + b3, softplus.
+// MMA (layer 2) -> + b2, ReLU/BF16 and the 64 -> 1 head on the CUDA cores
+// (FP32 FMAs in column order) -> + b3, softplus.
 template <bool kEnc>  // kEnc: the rows come encoded (S.enc)
 __global__ void __launch_bounds__(kThreads) k_mlp_forward(int64_t n, PointSrc S, const float* __restrict__ P,
                                                           const uint16_t* __restrict__ Wb,
@@ -328,18 +343,18 @@ __global__ void __launch_bounds__(kThreads) k_mlp_forward(int64_t n, PointSrc S,
     uint8_t* sW1 = base;
     uint8_t* sW2 = base + kWBytes;
     uint8_t* sX = base + 2 * kWBytes;
-    uint8_t* sW3 = sX + kTileBytes;  // 16 rows x 128 bytes
     __shared__ float sB2[64];
+    __shared__ float sW3[64];
     __shared__ float sB3;
     __shared__ uint64_t bar;
     __shared__ uint32_t tbase;
     const int t = threadIdx.x, warp = t >> 5;
     load_w1_bias_tile(sW1, Wb + wW1, P);
     load_weight_tile(sW2, Wb + wW2, false);
-    for (int i = t; i < 64; i += blockDim.x)
-        *reinterpret_cast<uint16_t*>(sW3 + tc::sw128_offset(0, i)) = Wb[wW3 + i];
-    for (int i = 128 / 4 + t; i < (int)kW3Bytes / 4; i += blockDim.x) reinterpret_cast<uint32_t*>(sW3)[i] = 0u;
-    if (t < 64) sB2[t] = P[oB2 + t];
+    if (t < 64) {
+        sB2[t] = P[oB2 + t];
+        sW3[t] = __uint_as_float((uint32_t)Wb[wW3 + t] << 16);  // the BF16 w3
+    }
     if (t == 0) {
         sB3 = P[oB3];
         mbar_init(&bar, 1);
@@ -351,9 +366,9 @@ __global__ void __launch_bounds__(kThreads) k_mlp_forward(int64_t n, PointSrc S,
     }
     sync_for_mma();
     const uint32_t tm = tbase, row = tm + ((uint32_t)(warp * 32) << 16);
-    const uint32_t idesc = tc::idesc_bf16_f32(128, 64), idesc3 = tc::idesc_bf16_f32(128, 16);
+    const uint32_t idesc = tc::idesc_bf16_f32(128, 64);
     const uint64_t dX = tc::sw128_desc(smem_u32(sX)), dW1 = tc::sw128_desc(smem_u32(sW1)),
-                   dW2 = tc::sw128_desc(smem_u32(sW2)), dW3 = tc::sw128_desc(smem_u32(sW3));
+                   dW2 = tc::sw128_desc(smem_u32(sW2));
     uint32_t phase = 0;
     bool ok = true;
     const int64_t ntiles = (n + kTile - 1) / kTile;
@@ -391,17 +406,8 @@ __global__ void __launch_bounds__(kThreads) k_mlp_forward(int64_t n, PointSrc S,
             tc::mma_commit(&bar);
         }
         if (!(ok = wait_mma(&bar, phase))) break;
-        relu_pack32(row, sB2, sX, t, 0);
-        relu_pack32(row + 32, sB2 + 32, sX, t, 4);
-        sync_for_mma();
-        if (t == 0) {
-#pragma unroll
-            for (int ks = 0; ks < 4; ++ks) tc::mma_bf16(tm, dX + 2 * ks, dW3 + 2 * ks, idesc3, ks > 0);
-            tc::mma_commit(&bar);
-        }
-        if (!(ok = wait_mma(&bar, phase))) break;
-        const float z = tc::tmem_ld1(row);
-        tc::tmem_wait_ld();
+        float z = head_dot32(row, sB2, sW3, 0.0f);
+        z = head_dot32(row + 32, sB2 + 32, sW3 + 32, z);
         if (p < n) sigma[p] = softplus(z + sB3);
         tc::fence_before_sync();
     }
@@ -698,7 +704,7 @@ namespace nacc {
 namespace {
 int launch_forward(int64_t n, const PointSrc& S, const float* params, const uint16_t* weights, float* sigma,
                    cudaStream_t st) {
-    const size_t shm = 2 * kWBytes + kTileBytes + kW3Bytes + 1024;
+    const size_t shm = 2 * kWBytes + kTileBytes + 1024;
     const auto kern = S.enc ? k_mlp_forward<true> : k_mlp_forward<false>;
     NACC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
     NACC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
