@@ -329,10 +329,13 @@ __device__ __forceinline__ float warp_max(float v) {
 // its terms; Q (the sum of the depths before every sample up to the one
 // tested, from the warp scan, which is within E of the definition's) bounds
 // that sum with cnt * E for the difference.  The warp scan itself is
-// within u (8 + chunks) P of its terms' exact sum.
+// within u (16 + chunks) P of its terms' exact sum: a lane's up to three
+// sequential additions of its own points, the five levels of the scan, the
+// subtraction of the lane's total, the carry, and one addition per earlier
+// chunk of at least 32 points.
 __device__ __forceinline__ float sum_bound(int cnt, float Q, float E, float P) {
     const float n = (float)cnt;
-    return kU * ((Q + n * E) * 1.01f + (n * (1.0f / 32.0f) + 8.0f) * P * 1.01f);
+    return kU * ((Q + n * E) * 1.01f + (n * (1.0f / 32.0f) + 16.0f) * P * 1.01f);
 }
 
 // Bound on |fast - definition| of the density terms before a sample whose

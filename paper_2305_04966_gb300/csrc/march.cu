@@ -426,6 +426,8 @@ __device__ __forceinline__ void sigma_tab2(const float4* tab, int nt, float ta, 
 // for that group.  Over a ray of at most 2^24 points in groups of 64, with
 // at most kTab entries, that moves the optical depth by at most 1.7e-3 (and
 // by 1.0e-7 at 1,024 points): only decisions within that of the threshold.
+// (The fast depth takes groups of 128 points: half as many groups, so the
+// error bound's count of groups of 64 over-estimates.)
 constexpr float kGroupEps = 1e-10f;
 constexpr int kGroupMin = 16;  // tables of at most this many entries are summed whole (cheaper)
 
@@ -455,6 +457,49 @@ __device__ __forceinline__ void sigma_tab2_group(const float4* tab, int nt, floa
     }
     sa = acc_a;
     sb = acc_b;
+}
+
+// The same densities at four points of a lane (each table entry read once).
+__device__ __forceinline__ void sigma_tab4(const float4* tab, int nt, const float t[4], float sg[4]) {
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll 2
+    for (int b = 0; b < nt; ++b) {
+        const float4 v = tab[b];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float d = t[u] - v.y;
+            acc[u] = fmaf(v.w, ex2_approx(fmaf(v.x * d, d, v.z)), acc[u]);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) sg[u] = acc[u];
+}
+
+__device__ __forceinline__ void sigma_tab4_group(const float4* tab, int nt, float t_lo, float t_hi, float span,
+                                                 const float t[4], float sg[4], bool active) {
+    const int lane = threadIdx.x & 31;
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int e0 = 0; e0 < nt; e0 += 32) {
+        bool on = false;
+        if (e0 + lane < nt) {
+            const float4 v = tab[e0 + lane];
+            const float u = fminf(fmaxf(v.y, t_lo), t_hi) - v.y;
+            on = v.w * ex2_approx(fmaf(v.x * u, u, v.z)) * span > kGroupEps;
+        }
+        unsigned m = __ballot_sync(0xffffffffu, on);
+        if (!active) continue;
+        while (m) {
+            const float4 v = tab[e0 + __ffs(m) - 1];
+            m &= m - 1;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float d = t[u] - v.y;
+                acc[u] = fmaf(v.w, ex2_approx(fmaf(v.x * d, d, v.z)), acc[u]);
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) sg[u] = acc[u];
 }
 
 // Per-thread march state of one ray.
@@ -899,65 +944,83 @@ __device__ __forceinline__ int fast_cut(const MarchArgs& A, const StopBlob* s_bl
             if (lane >= o2) ex += y;
         }
         ex -= run.y;
-        for (int p0 = 0; p0 < cnt; p0 += 64) {
-            const int pa = p0 + 2 * lane, pb = pa + 1;
-            int ka = 0, kb = 0;
+        // four consecutive points per lane (128 per pass): each table entry
+        // is read once for all four
+        for (int p0 = 0; p0 < cnt; p0 += 128) {
+            const int pq = p0 + 4 * lane;
+            int kq[4] = {0, 0, 0, 0};
             for (int j = 0; j < nr; ++j) {
                 const int ej = __shfl_sync(0xffffffffu, ex, j);
                 const int kj = __shfl_sync(0xffffffffu, run.x, j);
-                if (pa >= ej) ka = kj + (pa - ej);
-                if (pb >= ej) kb = kj + (pb - ej);
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (pq + u >= ej) kq[u] = kj + (pq + u - ej);
             }
-            float taua = 0.0f, taub = 0.0f;
-            const bool two = pb < cnt;
-            const float a0 = __fadd_rn(tn, __fmul_rn((float)ka, A.step)), a1 = __fadd_rn(a0, A.step);
-            const float b0 = __fadd_rn(tn, __fmul_rn((float)(two ? kb : ka), A.step)),
-                        b1 = __fadd_rn(b0, A.step);
-            const float tma = __fmul_rn(__fadd_rn(a0, a1), 0.5f), tmb = __fmul_rn(__fadd_rn(b0, b1), 0.5f);
-            float sa = 0.0f, sb = 0.0f;
+            float t0[4], t1[4], tm[4], sg[4] = {0.0f, 0.0f, 0.0f, 0.0f}, tau[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int k = pq + u < cnt ? kq[u] : kq[0];
+                t0[u] = __fadd_rn(tn, __fmul_rn((float)k, A.step));
+                t1[u] = __fadd_rn(t0[u], A.step);
+                tm[u] = __fmul_rn(__fadd_rn(t0[u], t1[u]), 0.5f);
+            }
             if (nt > 0 && nt <= kGroupMin) {
-                if (pa < cnt) sigma_tab2(tab, nt, tma, tmb, sa, sb);
-            } else if (nt > 0) {  // the group's midpoints span [first, last] (lattice order)
-                const int last = min(cnt - p0, 64) - 1;
-                const float t_lo = __shfl_sync(0xffffffffu, tma, 0);
-                const float t_hi = __shfl_sync(0xffffffffu, (last & 1) ? tmb : tma, last >> 1);
-                const float t_end = __shfl_sync(0xffffffffu, (last & 1) ? b1 : a1, last >> 1);
-                const float span = t_end - __shfl_sync(0xffffffffu, a0, 0);
-                sigma_tab2_group(tab, nt, t_lo, t_hi, span, tma, tmb, sa, sb, pa < cnt);
+                if (pq < cnt) sigma_tab4(tab, nt, tm, sg);
+            } else if (nt > 0) {  // the pass's midpoints span [first, last] (lattice order)
+                const int last = min(cnt - p0, 128) - 1, ll = last >> 2, lu = last & 3;
+                const float t_lo = __shfl_sync(0xffffffffu, tm[0], 0);
+                const float tm_l = lu == 0 ? tm[0] : lu == 1 ? tm[1] : lu == 2 ? tm[2] : tm[3];
+                const float t1_l = lu == 0 ? t1[0] : lu == 1 ? t1[1] : lu == 2 ? t1[2] : t1[3];
+                const float t_hi = __shfl_sync(0xffffffffu, tm_l, ll);
+                const float t_end = __shfl_sync(0xffffffffu, t1_l, ll);
+                const float span = t_end - __shfl_sync(0xffffffffu, t0[0], 0);
+                sigma_tab4_group(tab, nt, t_lo, t_hi, span, tm, sg, pq < cnt);
             }
-            if (pa < cnt) {
-                if (nt < 0) {
+            if (pq < cnt && nt < 0) {
+#pragma unroll
+                for (int u = 0; u < 4; u += 2) {
                     float xa[3], xb[3];
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
-                        xa[a] = fmaf(d[a], tma, o[a]);
-                        xb[a] = fmaf(d[a], tmb, o[a]);
+                        xa[a] = fmaf(d[a], tm[u], o[a]);
+                        xb[a] = fmaf(d[a], tm[u + 1], o[a]);
                     }
-                    sigma_early_stop2(s_blobs, nblobs, xa, xb, sa, sb);
+                    sigma_early_stop2(s_blobs, nblobs, xa, xb, sg[u], sg[u + 1]);
                 }
-                taua = __fmul_rn(sa, __fsub_rn(a1, a0));
-                if (two) taub = __fmul_rn(sb, __fsub_rn(b1, b0));
             }
-            const float pair = taua + taub;
-            float x = pair;  // -> inclusive prefix over the lanes' pairs
+#pragma unroll
+            for (int u = 0; u < 4; ++u) tau[u] = pq + u < cnt ? __fmul_rn(sg[u], __fsub_rn(t1[u], t0[u])) : 0.0f;
+            const float l1 = tau[0], l2 = l1 + tau[1], l3 = l2 + tau[2], quad = l3 + tau[3];
+            float x = quad;  // -> inclusive prefix over the lanes' quads
 #pragma unroll
             for (int o2 = 1; o2 < 32; o2 <<= 1) {
                 const float y = __shfl_up_sync(0xffffffffu, x, o2);
                 if (lane >= o2) x += y;
             }
-            const float before_a = carry + (x - pair), before_b = before_a + taua;
-            const float Qc = Q + warp_sum((pa < cnt ? before_a : 0.0f) + (pb < cnt ? before_b : 0.0f));
+            float before[4];
+            before[0] = carry + (x - quad);
+            before[1] = before[0] + tau[0];
+            before[2] = before[1] + tau[1];
+            before[3] = before[2] + tau[2];
+            float qs = 0.0f;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) qs += pq + u < cnt ? before[u] : 0.0f;
+            const float Qc = Q + warp_sum(qs);
             const float lo_thr = A.thr - depth_error(rb, cnt, Qc, A.thr);
-            const unsigned over_a = __ballot_sync(0xffffffffu, pa < cnt && before_a > lo_thr);
-            const unsigned over_b = __ballot_sync(0xffffffffu, pb < cnt && before_b > lo_thr);
-            if (over_a | over_b) {  // the first point near or past the threshold, in lattice order
-                const int ja = over_a ? __ffs(over_a) - 1 : 32, jb = over_b ? __ffs(over_b) - 1 : 32;
-                const bool at_a = ja <= jb;
-                const int j = at_a ? ja : jb;
-                const float bc = __shfl_sync(0xffffffffu, at_a ? before_a : before_b, j);
-                const int kc = __shfl_sync(0xffffffffu, at_a ? ka : kb, j);
+            int first = 128;  // the first point near or past the threshold, in lattice order
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const unsigned ov = __ballot_sync(0xffffffffu, pq + u < cnt && before[u] > lo_thr);
+                if (ov) first = min(first, 4 * (__ffs(ov) - 1) + u);
+            }
+            if (first < 128) {
+                const int jl = first >> 2, ju = first & 3;
+                const float bsel = ju == 0 ? before[0] : ju == 1 ? before[1] : ju == 2 ? before[2] : before[3];
+                const int ksel = ju == 0 ? kq[0] : ju == 1 ? kq[1] : ju == 2 ? kq[2] : kq[3];
+                const float bc = __shfl_sync(0xffffffffu, bsel, jl);
+                const int kc = __shfl_sync(0xffffffffu, ksel, jl);
                 if (bc - depth_error(rb, cnt, Qc, bc) > A.thr) {
-                    cut = p0 + 2 * j + (at_a ? 0 : 1);
+                    cut = p0 + first;
                     kstop = kc;
                     return 1;
                 }
