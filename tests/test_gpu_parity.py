@@ -552,11 +552,14 @@ def test_initial_density_grid_matches_oracle(nacc, orc):
 
 @pytest.mark.parametrize("nb,no,strat,n", [(64, 32, False, 20000), (32, 32, False, 20000), (64, 32, True, 20001),
                                            (7, 100, False, 20000), (300, 17, True, 20000), (1, 4, False, 20000),
-                                           (4096, 4096, True, 300), (128, 64, False, 1), (33, 31, True, 20003)])
+                                           (4096, 4096, True, 300), (128, 64, False, 1), (33, 31, True, 20003),
+                                           (64, 64, True, 5000), (65, 32, False, 5000), (2, 40, True, 333)])
 def test_sample_pdf_bit_exact(nacc, orc, nb, no, strat, n):
     """Every output bit-exact, including all-zero rows (uniform), single-bin
     mass, CDFs that reach 1 before the last bin (a dominant weight followed
-    by ones too small to move the sum), and denormal weights."""
+    by ones too small to move the sum), and denormal weights; row counts that
+    are not multiples of the 32 rays a warp takes, and bin counts on both
+    sides of the 64-bin switch between the staged-row and streamed kernels."""
     g = workloads.rng(90 + nb)
     edges = np.sort(g.uniform(2.0, 6.0, (n, nb + 1)), axis=1).astype(np.float32)
     wts = g.uniform(0, 1, (n, nb)).astype(np.float32)
