@@ -1442,9 +1442,9 @@ __global__ void __launch_bounds__(kBlockThreads)
                 t1[u] = __fadd_rn(t0[u], A.step);
             }
             if (q >= pj && q + 4 <= pend) {
-                *reinterpret_cast<float4*>(t0s + q) = make_float4(t0[0], t0[1], t0[2], t0[3]);
-                *reinterpret_cast<float4*>(t1s + q) = make_float4(t1[0], t1[1], t1[2], t1[3]);
-                if (ray_idx) *reinterpret_cast<int4*>(ray_idx + q) = make_int4((int)rj, (int)rj, (int)rj, (int)rj);
+                __stcs(reinterpret_cast<float4*>(t0s + q), make_float4(t0[0], t0[1], t0[2], t0[3]));
+                __stcs(reinterpret_cast<float4*>(t1s + q), make_float4(t1[0], t1[1], t1[2], t1[3]));
+                if (ray_idx) __stcs(reinterpret_cast<int4*>(ray_idx + q), make_int4((int)rj, (int)rj, (int)rj, (int)rj));
             } else {
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
