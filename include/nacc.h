@@ -38,7 +38,7 @@ extern "C" {
 #define NACC_ERR_CAPACITY (-2)    /* packed output too small; required size reported */
 #define NACC_ERR_CUDA (-3)        /* a CUDA runtime call failed (launch or sync) */
 #define NACC_ERR_TIMEOUT (-4)     /* reserved: a bounded device wait expired */
-#define NACC_ERR_UNSUPPORTED (-5) /* valid request this build does not implement */
+#define NACC_ERR_UNSUPPORTED (-5) /* valid request this library does not implement */
 
 #define NACC_MAX_LEVELS 8
 

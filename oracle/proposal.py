@@ -1,7 +1,7 @@
 """Oracle of the learned density proposal (TEST INFRASTRUCTURE ONLY).
 
-Plain numpy restatement of the proposal estimator's network as this build
-reads it for the paper's learned-proposal sampler (Table 1 "PDF
+Plain numpy restatement of the proposal estimator's network, in the reading
+this library takes of the paper's learned-proposal sampler (Table 1 "PDF
 Approaches", Sec. 3.2: a small network predicts density, its transmittance
 gives the PDF that inverse transform sampling, Eq. 1, resamples):
 
