@@ -49,7 +49,6 @@ namespace {
 
 constexpr int kBlockThreads = 32;               // one ray per thread; one warp per block
 constexpr int kRaysPerBlock = kBlockThreads;    // rays per block-sum entry
-constexpr int kWarpsPerBlock = kBlockThreads / 32;
 constexpr int kBuf = 32;                        // lattice indices buffered per lane
 constexpr int kRunSlots = 16;                   // recorded lattice runs per ray
 constexpr int kLogC = 4, kLogF = 2;             // block summaries: coarse 16^3 and fine 4^3 cells
@@ -430,34 +429,6 @@ __device__ __forceinline__ void sigma_tab2(const float4* tab, int nt, float ta, 
 // error bound's count of groups of 64 over-estimates.)
 constexpr float kGroupEps = 1e-10f;
 constexpr int kGroupMin = 16;  // tables of at most this many entries are summed whole (cheaper)
-
-// The same density, summing only the entries that the bound above keeps for
-// the warp's group [t_lo, t_hi] (each lane tests one entry, the warp takes
-// the kept ones in table order).
-__device__ __forceinline__ void sigma_tab2_group(const float4* tab, int nt, float t_lo, float t_hi, float span,
-                                                 float ta, float tb, float& sa, float& sb, bool active) {
-    const int lane = threadIdx.x & 31;
-    float acc_a = 0.0f, acc_b = 0.0f;
-    for (int e0 = 0; e0 < nt; e0 += 32) {
-        bool on = false;
-        if (e0 + lane < nt) {
-            const float4 v = tab[e0 + lane];
-            const float u = fminf(fmaxf(v.y, t_lo), t_hi) - v.y;
-            on = v.w * ex2_approx(fmaf(v.x * u, u, v.z)) * span > kGroupEps;
-        }
-        unsigned m = __ballot_sync(0xffffffffu, on);
-        if (!active) continue;
-        while (m) {
-            const float4 v = tab[e0 + __ffs(m) - 1];
-            m &= m - 1;
-            const float ua = ta - v.y, ub = tb - v.y;
-            acc_a = fmaf(v.w, ex2_approx(fmaf(v.x * ua, ua, v.z)), acc_a);
-            acc_b = fmaf(v.w, ex2_approx(fmaf(v.x * ub, ub, v.z)), acc_b);
-        }
-    }
-    sa = acc_a;
-    sb = acc_b;
-}
 
 // The same densities at four points of a lane (each table entry read once).
 __device__ __forceinline__ void sigma_tab4(const float4* tab, int nt, const float t[4], float sg[4]) {
@@ -1357,115 +1328,18 @@ __global__ void __launch_bounds__(1024)
     }
 }
 
-// Fill pass.  Rays whose runs were recorded are expanded warp-cooperatively,
-// one ray at a time: sample p of the ray is point p of its concatenated
-// ranges, written as coalesced stores.  Rays whose runs overflowed the slots
-// are re-marched per lane up to their recorded stop, without the field, and
-// flushed lane by lane with the whole warp.
-__global__ void __launch_bounds__(kBlockThreads)
-    k_march_fill(MarchArgs A, const int32_t* __restrict__ counts, const int32_t* __restrict__ kstops,
-                 const int32_t* __restrict__ nruns, const float* __restrict__ tnear,
-                 const int2* __restrict__ runs, const long long* __restrict__ block_off,
-                 const int64_t* __restrict__ n_samples, int64_t capacity, int64_t* __restrict__ offsets,
-                 int32_t* __restrict__ ray_idx, float* __restrict__ t0s, float* __restrict__ t1s) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t r = (int64_t)blockIdx.x * kBlockThreads + threadIdx.x;
-    const int cnt = r < A.n ? counts[r] : 0;
-    // block exclusive scan of the counts -> CSR offsets
-    __shared__ int s_w[kWarpsPerBlock];
-    int x = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) s_w[wid] = x;
-    __syncthreads();
-    int wbase = 0;
-    for (int w = 0; w < wid; ++w) wbase += s_w[w];
-    long long pos = block_off[blockIdx.x] + wbase + x - cnt;
-    if (r < A.n) offsets[r] = pos;
-    if (*n_samples > capacity) return;  // overflow: offsets only (the whole grid agrees)
-    const int nr = cnt > 0 ? nruns[r] : 0;
-    const float tn = cnt > 0 ? tnear[r] : 0.0f;
-    const int64_t r_lane0 = r - lane;
-
-    unsigned todo = __ballot_sync(0xffffffffu, nr > 0);
-    // the next ray's ranges are loaded while the current one is written
-    int2 run_next = make_int2(0, 0);
-    if (todo) {
-        const int j = __ffs(todo) - 1;
-        if (lane < __shfl_sync(0xffffffffu, nr, j)) run_next = runs[(r_lane0 + j) * kRunSlots + lane];
-    }
-    while (todo) {
-        const int j = __ffs(todo) - 1;
-        todo &= todo - 1;
-        const int cj = __shfl_sync(0xffffffffu, cnt, j);
-        const int nj = __shfl_sync(0xffffffffu, nr, j);
-        const long long pj = __shfl_sync(0xffffffffu, pos, j);
-        const float tnj = __shfl_sync(0xffffffffu, tn, j);
-        const int64_t rj = r_lane0 + j;
-        const int2 run = run_next;
-        if (todo) {
-            const int jn = __ffs(todo) - 1;
-            run_next = lane < __shfl_sync(0xffffffffu, nr, jn) ? runs[(r_lane0 + jn) * kRunSlots + lane]
-                                                               : make_int2(0, 0);
-        }
-        int ex = run.y;  // -> exclusive prefix of the range lengths
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, ex, o);
-            if (lane >= o) ex += y;
-        }
-        ex -= run.y;
-        // lane l writes positions q..q+3 of the sample arrays, q = 4l + a
-        // multiple of 128 from pj rounded down to a multiple of 4: groups of
-        // four inside the ray as one 128-bit store per array, the ray's
-        // ragged head and tail position by position (nothing outside the
-        // ray is written)
-        const long long a4 = pj & ~3ll, pend = pj + cj;
-        for (long long q0 = a4; q0 < pend; q0 += 128) {
-            const long long q = q0 + 4 * lane;
-            const int p0 = (int)(q - pj);  // sample index of position q within the ray (may be < 0)
-            int k[4] = {p0, p0 + 1, p0 + 2, p0 + 3};
-            for (int i = 0; i < nj; ++i) {
-                const int ei = __shfl_sync(0xffffffffu, ex, i);
-                const int ki = __shfl_sync(0xffffffffu, run.x, i);
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (p0 + u >= ei) k[u] = ki + (p0 + u - ei);
-            }
-            float t0[4], t1[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                t0[u] = __fadd_rn(tnj, __fmul_rn((float)k[u], A.step));
-                t1[u] = __fadd_rn(t0[u], A.step);
-            }
-            if (q >= pj && q + 4 <= pend) {
-                __stcs(reinterpret_cast<float4*>(t0s + q), make_float4(t0[0], t0[1], t0[2], t0[3]));
-                __stcs(reinterpret_cast<float4*>(t1s + q), make_float4(t1[0], t1[1], t1[2], t1[3]));
-                if (ray_idx) __stcs(reinterpret_cast<int4*>(ray_idx + q), make_int4((int)rj, (int)rj, (int)rj, (int)rj));
-            } else {
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    if (q + u < pj || q + u >= pend) continue;
-                    t0s[q + u] = t0[u];
-                    t1s[q + u] = t1[u];
-                    if (ray_idx) ray_idx[q + u] = (int)rj;
-                }
-            }
-        }
-    }
-
-    if (!__any_sync(0xffffffffu, nr < 0)) return;
-    // per-lane buffers of lattice indices (row stride kBuf+1: conflict-free appends)
-    __shared__ int s_buf[kBlockThreads][kBuf + 1];
-    int* buf = s_buf[threadIdx.x];
+// A warp's re-marched rays (lane flag `mine`): each such lane walks its ray
+// up to the recorded stop kend, emitting cnt points from offset pos into its
+// buffer `buf` (row of wbuf), which the whole warp flushes, lane by lane.
+__device__ __forceinline__ void fill_long_group(const MarchArgs& A, int64_t r, bool mine, int cnt, int kend,
+                                                long long pos, int* buf, const int (*wbuf)[kBuf + 1],
+                                                int32_t* __restrict__ ray_idx, float* __restrict__ t0s,
+                                                float* __restrict__ t1s) {
+    const int lane = threadIdx.x & 31;
     Lane s;
     s.done = true;
     s.R.tn = 0.0f;
-    if (nr < 0) lane_init(A, r, s);
-    const int kend = nr < 0 ? kstops[r] : 0;
+    if (mine) lane_init(A, r, s);
     while (true) {
         int bn = 0;
         if (!s.done) advance(A, s, kend, cnt, buf, bn);
@@ -1479,7 +1353,7 @@ __global__ void __launch_bounds__(kBlockThreads)
             const int rj = __shfl_sync(0xffffffffu, (int)r, j);
             const float tnj = __shfl_sync(0xffffffffu, s.R.tn, j);
             if (lane < nj) {
-                const int k = s_buf[(wid << 5) + j][lane];
+                const int k = wbuf[j][lane];
                 const float t0 = __fadd_rn(tnj, __fmul_rn((float)k, A.step));
                 t0s[pj + lane] = t0;
                 t1s[pj + lane] = __fadd_rn(t0, A.step);
@@ -1489,6 +1363,116 @@ __global__ void __launch_bounds__(kBlockThreads)
         __syncwarp();
         pos += bn;
         if (__all_sync(0xffffffffu, s.done)) break;
+    }
+}
+
+// Expansion of a ray whose runs were recorded (whole warp; run = slot `lane`
+// of its record, or zero): sample p of the ray is point p of its
+// concatenated ranges.  Lane l writes positions q..q+3 of the sample arrays,
+// q = 4l + a multiple of 128 from pj rounded down to a multiple of 4: groups
+// of four inside the ray as one 128-bit store per array, the ray's ragged
+// head and tail position by position (nothing outside the ray is written).
+__device__ __forceinline__ void fill_runs(const MarchArgs& A, int64_t r, int cj, long long pj, int nr, float tn,
+                                          int2 run, int32_t* __restrict__ ray_idx, float* __restrict__ t0s,
+                                          float* __restrict__ t1s) {
+    const int lane = threadIdx.x & 31;
+    if (lane >= nr) run = make_int2(0, 0);
+    int ex = run.y;  // -> exclusive prefix of the range lengths
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, ex, o);
+        if (lane >= o) ex += y;
+    }
+    ex -= run.y;
+    const long long a4 = pj & ~3ll, pend = pj + cj;
+    for (long long q0 = a4; q0 < pend; q0 += 128) {
+        const long long q = q0 + 4 * lane;
+        const int p0 = (int)(q - pj);  // sample index of position q within the ray (may be < 0)
+        int k[4] = {p0, p0 + 1, p0 + 2, p0 + 3};
+        for (int i = 0; i < nr; ++i) {
+            const int ei = __shfl_sync(0xffffffffu, ex, i);
+            const int ki = __shfl_sync(0xffffffffu, run.x, i);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (p0 + u >= ei) k[u] = ki + (p0 + u - ei);
+        }
+        float t0[4], t1[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            t0[u] = __fadd_rn(tn, __fmul_rn((float)k[u], A.step));
+            t1[u] = __fadd_rn(t0[u], A.step);
+        }
+        if (q >= pj && q + 4 <= pend) {
+            __stcs(reinterpret_cast<float4*>(t0s + q), make_float4(t0[0], t0[1], t0[2], t0[3]));
+            __stcs(reinterpret_cast<float4*>(t1s + q), make_float4(t1[0], t1[1], t1[2], t1[3]));
+            if (ray_idx) __stcs(reinterpret_cast<int4*>(ray_idx + q), make_int4((int)r, (int)r, (int)r, (int)r));
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (q + u < pj || q + u >= pend) continue;
+                t0s[q + u] = t0[u];
+                t1s[q + u] = t1[u];
+                if (ray_idx) ray_idx[q + u] = (int)r;
+            }
+        }
+    }
+}
+
+// Fill pass: each warp takes kFillRays consecutive rays, the blocks in ray
+// order, so that the warps in flight write neighbouring stretches of the
+// packed arrays (scattered concurrent write streams cost DRAM efficiency).
+// All loads of the warp's rays are issued before the first is used; the
+// rays' CSR offsets come from their 32-ray entry's start and the counts
+// before them.  A ray whose runs were recorded is expanded from them
+// (fill_runs); a ray whose runs overflowed the slots is re-marched by lane 0
+// up to its recorded stop, without the field, and flushed by the whole warp.
+// Four-warp blocks at 40 registers keep 48 warps per SM (32 or 64 per SM
+// measured slower: too few rays in flight, or spills in the expansion).
+constexpr int kFillWarps = 4;
+constexpr int kFillRays = 1;  // 2 and 4 measured slower (registers spill around the re-march)
+static_assert(32 % kFillRays == 0, "a warp's rays share one 32-ray entry");
+__global__ void __launch_bounds__(kFillWarps * 32, 12)
+    k_march_fill(MarchArgs A, const int32_t* __restrict__ counts, const int32_t* __restrict__ kstops,
+                 const int32_t* __restrict__ nruns, const float* __restrict__ tnear,
+                 const int2* __restrict__ runs, const long long* __restrict__ block_off,
+                 const int64_t* __restrict__ n_samples, int64_t capacity, int64_t* __restrict__ offsets,
+                 int32_t* __restrict__ ray_idx, float* __restrict__ t0s, float* __restrict__ t1s) {
+    __shared__ int s_lb[kFillWarps][kBuf + 1];  // lattice indices of a re-marched ray
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t r0 = ((int64_t)blockIdx.x * kFillWarps + wid) * kFillRays;
+    if (r0 >= A.n) return;  // whole warp
+    const int64_t g0 = r0 & ~31ll;
+    const int j0 = (int)(r0 - g0);
+    const int c = g0 + lane < A.n ? counts[g0 + lane] : 0;
+    const long long base = block_off[g0 / kRaysPerBlock];
+    const bool hl = lane < kFillRays && r0 + lane < A.n;  // lane i holds ray r0 + i's header
+    const int nr_l = hl ? nruns[r0 + lane] : 0;
+    const float tn_l = hl ? tnear[r0 + lane] : 0.0f;
+    int2 run0[kFillRays];
+#pragma unroll
+    for (int i = 0; i < kFillRays; ++i)
+        run0[i] = lane < kRunSlots && r0 + i < A.n ? runs[(r0 + i) * kRunSlots + lane] : make_int2(0, 0);
+    const bool over = *n_samples > capacity;
+    int x = c;  // -> inclusive prefix of the entry's counts
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+#pragma unroll
+    for (int i = 0; i < kFillRays; ++i) {
+        const int64_t r = r0 + i;
+        if (r >= A.n) break;  // whole warp
+        const int cj = __shfl_sync(0xffffffffu, c, j0 + i);
+        const long long pj = base + (__shfl_sync(0xffffffffu, x, j0 + i) - cj);
+        const int nr = __shfl_sync(0xffffffffu, nr_l, i);
+        const float tn = __shfl_sync(0xffffffffu, tn_l, i);
+        if (lane == 0) offsets[r] = pj;
+        if (over || cj == 0) continue;  // overflow: offsets only (the whole grid agrees)
+        if (nr < 0)
+            fill_long_group(A, r, lane == 0, cj, kstops[r], pj, s_lb[wid], &s_lb[wid], ray_idx, t0s, t1s);
+        else
+            fill_runs(A, r, cj, pj, nr, tn, run0[i], ray_idx, t0s, t1s);
     }
 }
 
@@ -1726,9 +1710,10 @@ extern "C" int nacc_march_grid(const nacc_grid* grid, const float* rays_o, const
     if (cudaEvent_t e = march_count_events()[1]) NACC_CUDA_TRY(cudaEventRecord(e, st));
     k_scan_block_sums<<<1, 1024, 0, st>>>(bsums, nb, out->offsets + n_rays, out->n_samples);
     NACC_LAUNCH_CHECK();
-    k_march_fill<<<(unsigned)nb, kBlockThreads, 0, st>>>(A, counts, kstops, nruns, tnear, runs, bsums,
-                                                         out->n_samples, out->capacity, out->offsets,
-                                                         out->ray_indices, out->t_starts, out->t_ends);
+    k_march_fill<<<(unsigned)((n_rays + kFillWarps * kFillRays - 1) / (kFillWarps * kFillRays)), kFillWarps * 32, 0,
+                   st>>>(
+        A, counts, kstops, nruns, tnear, runs, bsums, out->n_samples, out->capacity, out->offsets, out->ray_indices,
+        out->t_starts, out->t_ends);
     NACC_LAUNCH_CHECK();
     // Overflow is impossible when the capacity covers every lattice point.
     const bool may_overflow = (double)out->capacity < (double)n_rays * (double)params->max_steps;
