@@ -368,4 +368,35 @@ __device__ __forceinline__ bool bounds_usable(const RayBound& rb, int cnt, float
     return cnt < 16384 && density_error(rb, thr) < 0.25f * thr && rb.eps < 1e-2f && rb.U < 3.0e38f;
 }
 
+// The definition's sequential depth over one round of n <= N terms (tau in
+// shared memory, 16-byte aligned), added one at a time onto P in order:
+// returns the first j whose depth before it (P plus tau[0..j)) exceeds thr,
+// or -1.  The adds run to the end of the round without a branch (P's later
+// value is unused once a cut is found), so only their own latency chains.
+template <int N>
+__device__ __forceinline__ int seq_depth_cut(const float* tau, int n, float thr, float& P) {
+    int jc = -1;
+    if (n == N) {
+#pragma unroll
+        for (int j = 0; j < N; j += 4) {
+            const float4 v = *reinterpret_cast<const float4*>(tau + j);
+            jc = (jc < 0 && P > thr) ? j : jc;
+            P = __fadd_rn(P, v.x);
+            jc = (jc < 0 && P > thr) ? j + 1 : jc;
+            P = __fadd_rn(P, v.y);
+            jc = (jc < 0 && P > thr) ? j + 2 : jc;
+            P = __fadd_rn(P, v.z);
+            jc = (jc < 0 && P > thr) ? j + 3 : jc;
+            P = __fadd_rn(P, v.w);
+        }
+    } else {
+#pragma unroll 4
+        for (int j = 0; j < n; ++j) {
+            jc = (jc < 0 && P > thr) ? j : jc;
+            P = __fadd_rn(P, tau[j]);
+        }
+    }
+    return jc;
+}
+
 }  // namespace nacc

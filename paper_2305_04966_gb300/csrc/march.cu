@@ -1196,7 +1196,7 @@ __global__ void __launch_bounds__(kStopThreads)
                        unsigned long long* __restrict__ qhead) {
     extern __shared__ StopBlob s_blobs[];
     __shared__ uint16_t s_ex[kMaxBlobs];
-    __shared__ float s_tau[kStopThreads];
+    __shared__ __align__(16) float s_tau[kStopThreads];
     __shared__ int s_k[kStopThreads];
     __shared__ float s_seq[32];
     __shared__ unsigned long long s_tk;
@@ -1250,18 +1250,7 @@ __global__ void __launch_bounds__(kStopThreads)
                 s_tau[threadIdx.x] = exact_tau(A, s_blobs, s_ex, n_ex, o, d, tn, k, p < cnt, pos_far, lane);
                 s_k[threadIdx.x] = k;
                 __syncthreads();
-                if (threadIdx.x == 0) {
-                    int jc = -1;
-                    const int nv = min(kStopThreads, cnt - pr);
-                    for (int j = 0; j < nv; ++j) {
-                        if (P > A.thr) {
-                            jc = j;
-                            break;
-                        }
-                        P = __fadd_rn(P, s_tau[j]);
-                    }
-                    s_jc = jc;
-                }
+                if (threadIdx.x == 0) s_jc = seq_depth_cut<kStopThreads>(s_tau, min(kStopThreads, cnt - pr), A.thr, P);
                 __syncthreads();
                 const int jc = s_jc;
                 if (jc >= 0) {

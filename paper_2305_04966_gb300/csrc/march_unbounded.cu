@@ -1092,7 +1092,7 @@ __global__ void __launch_bounds__(kThreads) k_unb_stop_exact(UArgs A, int32_t* _
     __shared__ float4 s_bm[kStageBlobs];
     __shared__ float4 s_bk[kStageBlobs];
     __shared__ uint16_t s_ex[kMaxBlobs];
-    __shared__ float s_tau[kThreads];
+    __shared__ __align__(16) float s_tau[kThreads];
     __shared__ int s_k[kThreads];
     __shared__ float s_seq[32];
     __shared__ unsigned long long s_tk;
@@ -1142,18 +1142,7 @@ __global__ void __launch_bounds__(kThreads) k_unb_stop_exact(UArgs A, int32_t* _
                 s_tau[tid] = unb_exact_tau(A, s_eb, s_ex, n_ex, o, d, k, p < cnt, pos_far, lane);
                 s_k[tid] = k;
                 __syncthreads();
-                if (tid == 0) {
-                    int jc = -1;
-                    const int nv = min(kThreads, cnt - pr);
-                    for (int j = 0; j < nv; ++j) {
-                        if (P > A.thr) {
-                            jc = j;
-                            break;
-                        }
-                        P = __fadd_rn(P, s_tau[j]);
-                    }
-                    s_jc = jc;
-                }
+                if (tid == 0) s_jc = seq_depth_cut<kThreads>(s_tau, min(kThreads, cnt - pr), A.thr, P);
                 __syncthreads();
                 const int jc = s_jc;
                 if (jc >= 0) {
