@@ -268,6 +268,48 @@ constexpr float kCullEps = 1e-7f;
 // kept blobs (the table holds the first kTab).  onorm = |o|, dnorm = |d|, tmax bounds |t| of every midpoint, cnt =
 // the ray's samples.  Every lattice interval is within 8u tmax of dt long,
 // and consecutive intervals, rounded apart, overlap by at most that much.
+// One blob's part of the table and bound of a ray (below): its entry, whether
+// it is kept, and its weight in U and in e_out.  dd = |d|^2, idd = 1/dd,
+// ilen = 1/|d| (0 for a ray that does not move), dt_b and ov as below.
+__device__ __forceinline__ void ray_blob_entry(const StopBlob& v, const float o[3], const float d[3], float dd,
+                                               float idd, float ilen, float onorm, float dnorm, float dt_b, float ov,
+                                               int cnt, float4& ent, bool& keep, float& u, float& e) {
+    const float m0 = v.mx - o[0], m1 = v.my - o[1], m2 = v.mz - o[2];
+    float ts, pp, I;
+    if (dd > 0.0f) {
+        const float md = fmaf(m2, d[2], fmaf(m1, d[1], m0 * d[0]));
+        const float cx = fmaf(m1, d[2], -m2 * d[1]);
+        const float cy = fmaf(m2, d[0], -m0 * d[2]);
+        const float cz = fmaf(m0, d[1], -m1 * d[0]);
+        ts = md * idd;
+        pp = fmaf(cz, cz, fmaf(cy, cy, cx * cx)) * idd;
+    } else {  // a ray that does not move: the distance is |mu - o|
+        ts = 0.0f;
+        pp = fmaf(m2, m2, fmaf(m1, m1, m0 * m0));
+    }
+    const float C = v.c2 * pp;
+    const float S = v.peak * ex2_approx(C);  // largest density on the line
+    if (dd > 0.0f) {
+        I = S * 2.5066283f * v.sd * ilen;  // integral along the line
+        keep = I > kCullEps;
+    } else {
+        I = S * dt_b * (float)cnt;  // every sample at the same point
+        keep = true;
+    }
+    u = 0.0f;
+    e = 0.0f;
+    if (S > 0.0f) {
+        // growth with the FP32 closed form's own error (within 11u |mu - o|) included
+        const float p = sqrtf(pp);
+        const float mn = sqrtf(fmaf(m2, m2, fmaf(m1, m1, m0 * m0)));
+        const float W = blob_weight(
+            S, I, dt_b, dt_b, ov, blob_growth(p, v.isd, onorm + 2.5f * fabsf(ts) * dnorm + 16.0f * p + 12.0f * mn));
+        u = W;
+        if (!keep) e = W;
+    }
+    ent = make_float4(v.c2 * dd, ts, C, v.peak);
+}
+
 __device__ int build_ray_table(const StopBlob* sb, int n, const float o[3], const float d[3], float onorm,
                                float dnorm, float tmax, float dt, int cnt, float4* tab, uint16_t* tidx, float& U,
                                float& e_out, int lane) {
@@ -282,39 +324,10 @@ __device__ int build_ray_table(const StopBlob* sb, int n, const float o[3], cons
         bool keep = false;
         float4 ent = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         if (b < n) {
-            const StopBlob v = sb[b];
-            const float m0 = v.mx - o[0], m1 = v.my - o[1], m2 = v.mz - o[2];
-            float ts, pp, I;
-            if (dd > 0.0f) {
-                const float md = fmaf(m2, d[2], fmaf(m1, d[1], m0 * d[0]));
-                const float cx = fmaf(m1, d[2], -m2 * d[1]);
-                const float cy = fmaf(m2, d[0], -m0 * d[2]);
-                const float cz = fmaf(m0, d[1], -m1 * d[0]);
-                ts = md * idd;
-                pp = fmaf(cz, cz, fmaf(cy, cy, cx * cx)) * idd;
-            } else {  // a ray that does not move: the distance is |mu - o|
-                ts = 0.0f;
-                pp = fmaf(m2, m2, fmaf(m1, m1, m0 * m0));
-            }
-            const float C = v.c2 * pp;
-            const float S = v.peak * ex2_approx(C);  // largest density on the line
-            if (dd > 0.0f) {
-                I = S * 2.5066283f * v.sd * ilen;  // integral along the line
-                keep = I > kCullEps;
-            } else {
-                I = S * dt_b * (float)cnt;  // every sample at the same point
-                keep = true;
-            }
-            if (S > 0.0f) {
-                // growth with the FP32 closed form's own error (within 11u |mu - o|) included
-                const float p = sqrtf(pp);
-                const float mn = sqrtf(fmaf(m2, m2, fmaf(m1, m1, m0 * m0)));
-                const float W = blob_weight(
-                    S, I, dt_b, dt_b, ov, blob_growth(p, v.isd, onorm + 2.5f * fabsf(ts) * dnorm + 16.0f * p + 12.0f * mn));
-                u += W;
-                if (!keep) e += W;
-            }
-            ent = make_float4(v.c2 * dd, ts, C, v.peak);
+            float ub, eb;
+            ray_blob_entry(sb[b], o, d, dd, idd, ilen, onorm, dnorm, dt_b, ov, cnt, ent, keep, ub, eb);
+            u += ub;
+            e += eb;
         }
         const unsigned bal = __ballot_sync(0xffffffffu, keep);
         const int pos = nt + __popc(bal & ((1u << lane) - 1u));
@@ -327,6 +340,64 @@ __device__ int build_ray_table(const StopBlob* sb, int n, const float o[3], cons
     U = warp_sum(u);
     e_out = warp_sum(e);
     return nt;
+}
+
+// The tables of a whole 32-ray entry when the field has at most kSmallBlobs
+// blobs: eight lanes per ray, four rays per pass (lane 8s + b takes blob b of
+// ray 4 pass + s), each ray's kept blobs compacted in blob order into its
+// own kSmallBlobs entries of tab8, and U / e_out summed over the eight lanes
+// in the order warp_sum takes for blobs 0..7 (the other lanes hold zeros
+// there), so that every ray's table, nt, U and e_out are those
+// build_ray_table gives.  Ray i's values come from lane i (l_*).
+constexpr int kSmallBlobs = 8;
+__device__ __forceinline__ void build_entry_tables(const StopBlob* sb, int n, const float l_o[3],
+                                                   const float l_d[3], int l_cnt, float l_tn, int l_ke, float dt,
+                                                   float4* tab8, uint16_t* tidx8, float* s_U, float* s_e, int* s_nt,
+                                                   int lane) {
+    const int slot = lane >> 3, b = lane & 7;
+#pragma unroll 1
+    for (int pass = 0; pass < 32 / 4; ++pass) {
+        const int i = 4 * pass + slot;
+        const int cnt = __shfl_sync(0xffffffffu, l_cnt, i);
+        if (!__any_sync(0xffffffffu, cnt > 0)) continue;
+        const float tn = __shfl_sync(0xffffffffu, l_tn, i);
+        const int ke = __shfl_sync(0xffffffffu, l_ke, i);
+        float o[3], d[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            o[a] = __shfl_sync(0xffffffffu, l_o[a], i);
+            d[a] = __shfl_sync(0xffffffffu, l_d[a], i);
+        }
+        // the per-ray values as the ray loop forms them
+        const float tmax = fabsf(tn) + (float)(ke + 1) * dt * 1.0001f;
+        const float onorm = sqrtf(o[0] * o[0] + o[1] * o[1] + o[2] * o[2]) * 1.0001f;
+        const float dnorm = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) * 1.0001f;
+        const float dd = fmaf(d[2], d[2], fmaf(d[1], d[1], d[0] * d[0]));
+        const float idd = dd > 0.0f ? 1.0f / dd : 0.0f;
+        const float ilen = dd > 0.0f ? rsqrtf(dd) : 0.0f;
+        const float dt_b = dt + 8.0f * kU * tmax, ov = (float)cnt * 8.0f * kU * tmax;
+        bool keep = false;
+        float4 ent = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        float u = 0.0f, e = 0.0f;
+        if (b < n && cnt > 0) ray_blob_entry(sb[b], o, d, dd, idd, ilen, onorm, dnorm, dt_b, ov, cnt, ent, keep, u, e);
+        const unsigned grp = (__ballot_sync(0xffffffffu, keep) >> (8 * slot)) & 0xffu;
+        if (keep) {
+            const int pos = __popc(grp & ((1u << b) - 1u));
+            tab8[i * kSmallBlobs + pos] = ent;
+            tidx8[i * kSmallBlobs + pos] = (uint16_t)b;
+        }
+#pragma unroll
+        for (int o2 = 4; o2 > 0; o2 >>= 1) {
+            u += __shfl_xor_sync(0xffffffffu, u, o2);
+            e += __shfl_xor_sync(0xffffffffu, e, o2);
+        }
+        if (b == 0) {
+            s_U[i] = u;
+            s_e[i] = e;
+            s_nt[i] = __popc(grp);
+        }
+    }
+    __syncwarp();
 }
 
 // Error bound of the kept blobs (early_stop.cuh), one lane per kept blob:
@@ -1078,8 +1149,11 @@ __global__ void __launch_bounds__(kStopThreads, 7)
                  unsigned long long* __restrict__ ticket, long long* __restrict__ queue,
                  unsigned long long* __restrict__ qlen) {
     extern __shared__ StopBlob s_blobs[];
-    __shared__ float4 s_tab[kStopWarps][kTab];
-    __shared__ uint16_t s_tidx[kStopWarps][kTab];
+    constexpr int kTabWarp = kTab > 32 * kSmallBlobs ? kTab : 32 * kSmallBlobs;
+    __shared__ float4 s_tab[kStopWarps][kTabWarp];  // one ray's table, or a small field's 32
+    __shared__ uint16_t s_tidx[kStopWarps][kTabWarp];
+    __shared__ float s_U[kStopWarps][32], s_eo[kStopWarps][32];
+    __shared__ int s_nt[kStopWarps][32];
     stage_stop_blobs(s_blobs, A.field);
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -1110,6 +1184,10 @@ __global__ void __launch_bounds__(kStopThreads, 7)
         }
         int l_cut = l_cnt, l_kstop = l_ke;
         unsigned todo = __ballot_sync(0xffffffffu, l_cnt > 0);
+        const bool small = nblobs <= kSmallBlobs;  // every ray's table built up front, 8 lanes per ray
+        if (small && todo)
+            build_entry_tables(s_blobs, nblobs, l_o, l_d, l_cnt, l_tn, l_ke, A.step, tab, tidx, s_U[wid], s_eo[wid],
+                               s_nt[wid], lane);
         // the next ray's runs are loaded while the current one is evaluated
         int2 run_next = make_int2(0, 0);
         if (todo) {
@@ -1142,21 +1220,31 @@ __global__ void __launch_bounds__(kStopThreads, 7)
             const float dnorm = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) * 1.0001f;
             int cut = cnt, kstop = ke;
             float U, e_out;
-            const int nk = build_ray_table(s_blobs, nblobs, o, d, onorm, dnorm, tmax, A.step, cnt, tab, tidx, U, e_out,
-                                           lane);
+            int nk;
+            float4* tab_r = tab;
+            uint16_t* tidx_r = tidx;
+            if (small) {
+                tab_r = tab + i * kSmallBlobs;
+                tidx_r = tidx + i * kSmallBlobs;
+                nk = s_nt[wid][i];
+                U = s_U[wid][i];
+                e_out = s_eo[wid][i];
+            } else {
+                nk = build_ray_table(s_blobs, nblobs, o, d, onorm, dnorm, tmax, A.step, cnt, tab, tidx, U, e_out, lane);
+            }
             if (A.exact_all != 0 || !(depth_upper(U, cnt, nblobs) <= A.thr)) {  // the ray may stop
                 __syncwarp();
                 const int nt = nk <= kTab ? nk : -1;
                 const float e_grp = nt > kGroupMin ? 2.0f * kGroupEps * (float)nt * (float)((cnt + 63) / 64) : 0.0f;
                 // the refined table and its (tight) error bound
                 float eps;
-                const float ek = refine_ray_table(s_blobs, nblobs, nk, o, d, onorm, dnorm, tmax, A.step, cnt, tab, tidx,
-                                                  eps, lane);
+                const float ek = refine_ray_table(s_blobs, nblobs, nk, o, d, onorm, dnorm, tmax, A.step, cnt, tab_r,
+                                                  tidx_r, eps, lane);
                 const RayBound rb{U, ek, eps, e_out + e_grp};
                 __syncwarp();
                 const int st = A.exact_all != 0 || !bounds_usable(rb, cnt, A.thr)
                                    ? 2
-                                   : fast_cut(A, s_blobs, nblobs, tab, nt, rb, r, o, d, tn, cnt, nr, run, ke, lane,
+                                   : fast_cut(A, s_blobs, nblobs, tab_r, nt, rb, r, o, d, tn, cnt, nr, run, ke, lane,
                                               cut, kstop);
                 const bool exact = st == 2;
                 if (exact && lane == 0) queue[atomicAdd(qlen, 1ull)] = r;  // decided exactly by k_march_stop_exact
