@@ -342,17 +342,76 @@ __device__ int build_ray_table(const StopBlob* sb, int n, const float o[3], cons
     return nt;
 }
 
+// Error bound of the kept blobs (early_stop.cuh), one lane per kept blob:
+// t* and p^2 again by closest_approach, the table entry rewritten (when the
+// table holds the nt kept blobs; otherwise every kept blob is bounded from its
+// FP32 values, for the direct form).  Returns the whole-ray bound, and the
+// relative one in eps.  Arguments as build_ray_table.
+// One kept blob's refined table entry and its terms of the ray's error
+// bounds (absolute eb, relative er); false for a blob the direct form leaves
+// out (only without a table: it is counted whole in the table build).
+__device__ __forceinline__ bool refine_blob(const StopBlob& v, const float o[3], const float d[3], float dd, float idd,
+                                            float ilen, float onorm, float dnorm, float dt_b, float ov, int cnt, int n,
+                                            bool have_tab, float4& ent, float& eb, float& er) {
+    float ts, pp;
+    if (dd > 0.0f) {
+        const float mu[3] = {v.mx, v.my, v.mz};
+        closest_approach(mu, o, d, idd, ts, pp);
+    } else {
+        const float m0 = v.mx - o[0], m1 = v.my - o[1], m2 = v.mz - o[2];
+        ts = 0.0f;
+        pp = fmaf(m2, m2, fmaf(m1, m1, m0 * m0));
+    }
+    const float C = v.c2 * pp;
+    const float S = v.peak * ex2_approx(C);
+    const float I = dd > 0.0f ? S * 2.5066283f * v.sd * ilen : S * dt_b * (float)cnt;
+    if (!have_tab && !(I > kCullEps) && dd > 0.0f) return false;
+    const float p = sqrtf(pp);
+    const float pos0 = onorm + 2.5f * fabsf(ts) * dnorm + 16.0f * p;
+    const float gm1 = blob_growth(p, v.isd, pos0);
+    eb = blob_error(blob_weight(S, I, dt_b, dt_b, ov, gm1), gm1, p * v.isd, n, true);
+    er = blob_rel_error(v.isd, pos0, n);
+    ent = make_float4(v.c2 * dd, ts, C, v.peak);
+    return true;
+}
+
+__device__ float refine_ray_table(const StopBlob* sb, int n, int nt, const float o[3], const float d[3], float onorm,
+                                  float dnorm, float tmax, float dt, int cnt, float4* tab, const uint16_t* tidx,
+                                  float& eps, int lane) {
+    const float dd = fmaf(d[2], d[2], fmaf(d[1], d[1], d[0] * d[0]));
+    const float idd = dd > 0.0f ? 1.0f / dd : 0.0f;
+    const float ilen = dd > 0.0f ? rsqrtf(dd) : 0.0f;
+    const float dt_b = dt + 8.0f * kU * tmax, ov = (float)cnt * 8.0f * kU * tmax;
+    const bool have_tab = nt <= kTab;
+    float e = 0.0f, em = 0.0f;
+    for (int i = lane; i < (have_tab ? nt : n); i += 32) {
+        float4 ent;
+        float eb, er;
+        if (!refine_blob(sb[have_tab ? tidx[i] : i], o, d, dd, idd, ilen, onorm, dnorm, dt_b, ov, cnt, n, have_tab, ent,
+                         eb, er))
+            continue;  // left out: counted whole in build_ray_table
+        e += eb;
+        em = fmaxf(em, er);
+        if (have_tab) tab[i] = ent;
+    }
+    eps = warp_max(em);
+    return warp_sum(e);
+}
+
 // The tables of a whole 32-ray entry when the field has at most kSmallBlobs
 // blobs: eight lanes per ray, four rays per pass (lane 8s + b takes blob b of
 // ray 4 pass + s), each ray's kept blobs compacted in blob order into its
 // own kSmallBlobs entries of tab8, and U / e_out summed over the eight lanes
 // in the order warp_sum takes for blobs 0..7 (the other lanes hold zeros
 // there), so that every ray's table, nt, U and e_out are those
-// build_ray_table gives.  Ray i's values come from lane i (l_*).
+// build_ray_table gives; for a ray that may stop, the refined entries and
+// bounds as refine_ray_table gives them, the same way.  Ray i's values come
+// from lane i (l_*).
 constexpr int kSmallBlobs = 8;
 __device__ __forceinline__ void build_entry_tables(const StopBlob* sb, int n, const float l_o[3],
                                                    const float l_d[3], int l_cnt, float l_tn, int l_ke, float dt,
-                                                   float4* tab8, uint16_t* tidx8, float* s_U, float* s_e, int* s_nt,
+                                                   bool exact_all, float thr, float4* tab8, uint16_t* tidx8,
+                                                   float* s_U, float* s_e, int* s_nt, float* s_ek, float* s_eps,
                                                    int lane) {
     const int slot = lane >> 3, b = lane & 7;
 #pragma unroll 1
@@ -391,53 +450,33 @@ __device__ __forceinline__ void build_entry_tables(const StopBlob* sb, int n, co
             u += __shfl_xor_sync(0xffffffffu, u, o2);
             e += __shfl_xor_sync(0xffffffffu, e, o2);
         }
+        // the refined table and bounds of a ray that may stop (the ray loop's
+        // condition), lane 8s + j taking the ray's j-th kept blob as
+        // refine_ray_table's lane j does
+        const int nt = __popc(grp);
+        const bool may = cnt > 0 && (exact_all || !(depth_upper(u, cnt, n) <= thr));
+        __syncwarp();  // this pass's blob indices are in place
+        float eb = 0.0f, er = 0.0f;
+        if (may && b < nt) {
+            float4 ent2;
+            refine_blob(sb[tidx8[i * kSmallBlobs + b]], o, d, dd, idd, ilen, onorm, dnorm, dt_b, ov, cnt, n, true, ent2,
+                        eb, er);
+            tab8[i * kSmallBlobs + b] = ent2;
+        }
+#pragma unroll
+        for (int o2 = 4; o2 > 0; o2 >>= 1) {
+            eb += __shfl_xor_sync(0xffffffffu, eb, o2);
+            er = fmaxf(er, __shfl_xor_sync(0xffffffffu, er, o2));
+        }
         if (b == 0) {
             s_U[i] = u;
             s_e[i] = e;
-            s_nt[i] = __popc(grp);
+            s_nt[i] = nt;
+            s_ek[i] = eb;
+            s_eps[i] = er;
         }
     }
     __syncwarp();
-}
-
-// Error bound of the kept blobs (early_stop.cuh), one lane per kept blob:
-// t* and p^2 again by closest_approach, the table entry rewritten (when the
-// table holds the nt kept blobs; otherwise every kept blob is bounded from its
-// FP32 values, for the direct form).  Returns the whole-ray bound, and the
-// relative one in eps.  Arguments as build_ray_table.
-__device__ float refine_ray_table(const StopBlob* sb, int n, int nt, const float o[3], const float d[3], float onorm,
-                                  float dnorm, float tmax, float dt, int cnt, float4* tab, const uint16_t* tidx,
-                                  float& eps, int lane) {
-    const float dd = fmaf(d[2], d[2], fmaf(d[1], d[1], d[0] * d[0]));
-    const float idd = dd > 0.0f ? 1.0f / dd : 0.0f;
-    const float ilen = dd > 0.0f ? rsqrtf(dd) : 0.0f;
-    const float dt_b = dt + 8.0f * kU * tmax, ov = (float)cnt * 8.0f * kU * tmax;
-    const bool have_tab = nt <= kTab;
-    float e = 0.0f, em = 0.0f;
-    for (int i = lane; i < (have_tab ? nt : n); i += 32) {
-        const StopBlob v = sb[have_tab ? tidx[i] : i];
-        float ts, pp;
-        if (dd > 0.0f) {
-            const float mu[3] = {v.mx, v.my, v.mz};
-            closest_approach(mu, o, d, idd, ts, pp);
-        } else {
-            const float m0 = v.mx - o[0], m1 = v.my - o[1], m2 = v.mz - o[2];
-            ts = 0.0f;
-            pp = fmaf(m2, m2, fmaf(m1, m1, m0 * m0));
-        }
-        const float C = v.c2 * pp;
-        const float S = v.peak * ex2_approx(C);
-        const float I = dd > 0.0f ? S * 2.5066283f * v.sd * ilen : S * dt_b * (float)cnt;
-        if (!have_tab && !(I > kCullEps) && dd > 0.0f) continue;  // left out: counted whole in build_ray_table
-        const float p = sqrtf(pp);
-        const float pos0 = onorm + 2.5f * fabsf(ts) * dnorm + 16.0f * p;
-        const float gm1 = blob_growth(p, v.isd, pos0);
-        e += blob_error(blob_weight(S, I, dt_b, dt_b, ov, gm1), gm1, p * v.isd, n, true);
-        em = fmaxf(em, blob_rel_error(v.isd, pos0, n));
-        if (have_tab) tab[i] = make_float4(v.c2 * dd, ts, C, v.peak);
-    }
-    eps = warp_max(em);
-    return warp_sum(e);
 }
 
 // The ascending list of the blobs that may be non-zero somewhere on the ray
@@ -1152,7 +1191,7 @@ __global__ void __launch_bounds__(kStopThreads, 7)
     constexpr int kTabWarp = kTab > 32 * kSmallBlobs ? kTab : 32 * kSmallBlobs;
     __shared__ float4 s_tab[kStopWarps][kTabWarp];  // one ray's table, or a small field's 32
     __shared__ uint16_t s_tidx[kStopWarps][kTabWarp];
-    __shared__ float s_U[kStopWarps][32], s_eo[kStopWarps][32];
+    __shared__ float s_U[kStopWarps][32], s_eo[kStopWarps][32], s_ek[kStopWarps][32], s_eps[kStopWarps][32];
     __shared__ int s_nt[kStopWarps][32];
     stage_stop_blobs(s_blobs, A.field);
     __syncthreads();
@@ -1186,8 +1225,8 @@ __global__ void __launch_bounds__(kStopThreads, 7)
         unsigned todo = __ballot_sync(0xffffffffu, l_cnt > 0);
         const bool small = nblobs <= kSmallBlobs;  // every ray's table built up front, 8 lanes per ray
         if (small && todo)
-            build_entry_tables(s_blobs, nblobs, l_o, l_d, l_cnt, l_tn, l_ke, A.step, tab, tidx, s_U[wid], s_eo[wid],
-                               s_nt[wid], lane);
+            build_entry_tables(s_blobs, nblobs, l_o, l_d, l_cnt, l_tn, l_ke, A.step, A.exact_all != 0, A.thr, tab, tidx,
+                               s_U[wid], s_eo[wid], s_nt[wid], s_ek[wid], s_eps[wid], lane);
         // the next ray's runs are loaded while the current one is evaluated
         int2 run_next = make_int2(0, 0);
         if (todo) {
@@ -1238,8 +1277,10 @@ __global__ void __launch_bounds__(kStopThreads, 7)
                 const float e_grp = nt > kGroupMin ? 2.0f * kGroupEps * (float)nt * (float)((cnt + 63) / 64) : 0.0f;
                 // the refined table and its (tight) error bound
                 float eps;
-                const float ek = refine_ray_table(s_blobs, nblobs, nk, o, d, onorm, dnorm, tmax, A.step, cnt, tab_r,
-                                                  tidx_r, eps, lane);
+                const float ek = small ? s_ek[wid][i]
+                                       : refine_ray_table(s_blobs, nblobs, nk, o, d, onorm, dnorm, tmax, A.step, cnt,
+                                                          tab_r, tidx_r, eps, lane);
+                if (small) eps = s_eps[wid][i];
                 const RayBound rb{U, ek, eps, e_out + e_grp};
                 __syncwarp();
                 const int st = A.exact_all != 0 || !bounds_usable(rb, cnt, A.thr)
