@@ -247,6 +247,30 @@ def test_march_c1_with_field_early_stop(nacc, orc, field_blobs):
     assert (np.diff(exp["offsets"]) < np.diff(full["offsets"])).sum() > 100  # early stop happened
 
 
+@pytest.mark.parametrize("n_blobs", [1, 3, 8, 9])
+def test_march_small_fields_early_stop(nacc, orc, n_blobs):
+    """Fields of at most 8 blobs have each 32-ray entry's early-stop tables built
+    together, eight lanes per ray; 9 blobs take the per-ray build.  Both sides
+    of that boundary, and fields that leave most of the eight lanes idle, give
+    every ray the definition's samples, by default and all-exact."""
+    w = workloads.c1_forward()
+    w = dataclasses.replace(w, blobs=workloads.blob_field(n_blobs, 90 + n_blobs, std_lo=0.2, std_hi=0.4))
+    g, m = w.grid, w.march
+    bits, _ = orc.density_grid(g, w.blobs)
+    grid = grid_from_bits(nacc, g.aabb_min, g.aabb_max, g.res, g.n_levels, bits)
+    field = nacc.BlobField.from_numpy(w.blobs)
+    got = run_march(nacc, grid, w.rays_o, w.rays_d, m.step, m.max_steps, m.t_min, m.t_max, field=field)
+    got_x = run_march(nacc, grid, w.rays_o, w.rays_d, m.step, m.max_steps, m.t_min, m.t_max, field=field,
+                      exact_stops=True)
+    exp = orc.march(w.rays_o, w.rays_d, g.aabb_min, g.aabb_max, g.res, g.n_levels, bits, m.step,
+                    m.max_steps, m.t_min, m.t_max, blobs=w.blobs, eps=m.early_stop_eps)
+    full = orc.march(w.rays_o, w.rays_d, g.aabb_min, g.aabb_max, g.res, g.n_levels, bits, m.step,
+                     m.max_steps, m.t_min, m.t_max)
+    assert_packed_equal(got, exp)
+    assert_packed_equal(got_x, exp)
+    assert (np.diff(exp["offsets"]) < np.diff(full["offsets"])).sum() > 20  # early stop happened
+
+
 def test_march_c2_full_size_sampled(nacc, orc):
     """640,000-ray image, 4-level grid, with field: per-ray exact on a seeded
     sample of rays computed one by one by the oracle (every sampled ray)."""
