@@ -171,7 +171,7 @@ __device__ int field_group_candidates(const BlobS* sb, int nb, const float* __re
     return nc;
 }
 
-// One ray of k_field_rays: its table {A_b, t*_b, C_b, b} from the blobs
+// One ray of k_field_rays: its table {A_b, t*_b, C_b + log2 peak_b, b} from the blobs
 // cand[0 .. nc) (ascending; NULL or !kGroups: blobs 0 .. nc-1), culled per
 // ray when kCull, then its samples, four consecutive ones per lane per chunk
 // of 128.
@@ -212,11 +212,12 @@ __device__ __forceinline__ void field_ray(int64_t r, const uint16_t* cand, int n
                     ts = 0.0f;
                     pp = fmaf(m2, m2, fmaf(m1, m1, m0 * m0));
                 }
-                ent = make_float4(v.coef * dd, ts, v.coef * pp, __int_as_float(b));
+                // the peak rides in the exponent: density 2^(A (t - t*)^2 + C + log2 peak)
+                ent = make_float4(v.coef * dd, ts, fmaf(v.coef, pp, __log2f(v.peak)), __int_as_float(b));
                 keep = true;
                 if (nb > kCullAbove) {
                     const float sd = sqrtf(-0.72134752f / v.coef);  // coef = -log2(e) / (2 sd^2)
-                    const float peak_line = v.peak * ex2_approx(ent.z);
+                    const float peak_line = ex2_approx(ent.z);
                     const float bound = dd > 0.0f ? peak_line * 2.5066283f * sd * ilen : peak_line * 1e30f;
                     keep = bound > kCullEps;
                 }
@@ -238,7 +239,7 @@ __device__ __forceinline__ void field_ray(int64_t r, const uint16_t* cand, int n
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const float u = tm[j] - v.y;
-                    const float sj = w.peak * ex2_approx(fmaf(v.x * u, u, v.z));
+                    const float sj = ex2_approx(fmaf(v.x * u, u, v.z));
                     sg[j] += sj;
                     c[3 * j] = fmaf(sj, w.r, c[3 * j]);
                     c[3 * j + 1] = fmaf(sj, w.g, c[3 * j + 1]);
@@ -247,7 +248,7 @@ __device__ __forceinline__ void field_ray(int64_t r, const uint16_t* cand, int n
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const float inv = sg[j] > 0.0f ? 1.0f / sg[j] : 0.0f;
+                const float inv = sg[j] > 0.0f ? __frcp_rn(sg[j]) : 0.0f;
                 c[3 * j] *= inv;
                 c[3 * j + 1] *= inv;
                 c[3 * j + 2] *= inv;
